@@ -1,0 +1,314 @@
+"""Pins for the CPU oracle: checks against facts fixed by mathematics, not by
+the oracle itself -- exact rational arithmetic (Python integers/Fractions),
+error bounds of the algorithms, EFT identities, special cases that reduce to a
+single EFT, hand-derived worked results (tests/golden) and the closed form of
+the Sec. 3 test product.
+
+Every function takes a loaded oracle library ``L`` (so the mutation test can
+run them against deliberately broken copies) and raises AssertionError on a
+violation.  ``n`` scales the number of random cases.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+
+import oracle
+from oracle import exact as X
+from paper_2101_06584_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+U = Fraction(1, 2 ** 53)
+
+# error bounds: relative to |x|+|y| for additions, to |x*y| for products.
+# Each sits a few bits above the worst case seen over thousands of random
+# normalised operands (DD add 2^-105.5, DD mul 2^-104.5, TD addq 2^-161,
+# TD mul 2^-158, merge TDadd 2^-159, QD add 2^-215, QD mul 2^-210); a dropped
+# or misplaced term moves the error by many binades.
+BOUND = {("dd", "add"): 2.0 ** -103, ("dd", "mul"): 2.0 ** -103,
+         ("td", "add"): 2.0 ** -157, ("td", "addm"): 2.0 ** -155, ("td", "mul"): 2.0 ** -155,
+         ("qd", "add"): 2.0 ** -211, ("qd", "mul"): 2.0 ** -207}
+GEMM_P = {"dd": 100, "td": 150, "qd": 200}
+
+
+def F(x):
+    return Fraction(float(x))
+
+
+def _pairs(rng, n, spread):
+    """Random binary64 pairs: mixed exponents, equal magnitudes, opposite
+    signs, far-apart exponents."""
+    out = []
+    for t in range(n):
+        kind = t % 5
+        a = math.ldexp(rng.uniform(-1, 1), int(rng.integers(-spread, spread + 1)))
+        if kind == 0:
+            b = math.ldexp(rng.uniform(-1, 1), int(rng.integers(-spread, spread + 1)))
+        elif kind == 1:
+            b = -a
+        elif kind == 2:
+            b = a
+        elif kind == 3:
+            b = math.ldexp(rng.uniform(-1, 1), int(rng.integers(-80, 80))) * a
+        else:
+            b = -a * (1 + math.ldexp(float(rng.integers(1, 1 << 20)), -52))
+        out.append((a, b))
+    return out
+
+
+# ------------------------------------------------------------------ EFTs
+
+def pin_two_sum(L, n=2000):
+    rng = np.random.default_rng(11)
+    for a, b in _pairs(rng, n, 60) + [(1.0, 2.0 ** -53), (1.0, -2.0 ** -54), (0.0, -0.0)]:
+        s, e = oracle.two_sum(a, b, L)
+        assert s == float(F(a) + F(b)), ("two_sum s", a, b, s)
+        assert F(s) + F(e) == F(a) + F(b), ("two_sum exact", a, b, s, e)
+        if s != 0:
+            assert abs(F(e)) <= X.ulp(s) / 2
+
+
+def pin_quick_two_sum(L, n=2000):
+    rng = np.random.default_rng(12)
+    for a, b in _pairs(rng, n, 60):
+        if abs(a) < abs(b):
+            a, b = b, a
+        s, e = oracle.quick_two_sum(a, b, L)
+        assert s == float(F(a) + F(b)), ("quick_two_sum s", a, b)
+        assert F(s) + F(e) == F(a) + F(b), ("quick_two_sum exact", a, b, s, e)
+
+
+def pin_two_prod(L, n=2000):
+    rng = np.random.default_rng(13)
+    for a, b in _pairs(rng, n, 200) + [(1 + 2.0 ** -52, 1 + 2.0 ** -52), (3.0, 1 / 3.0)]:
+        p, e = oracle.two_prod(a, b, L)
+        assert p == float(F(a) * F(b)), ("two_prod p", a, b)
+        if p == 0 or abs(p) > 2.0 ** -960:          # error term representable
+            assert F(p) + F(e) == F(a) * F(b), ("two_prod exact", a, b, p, e)
+
+
+def pin_three_sums(L, n=1000):
+    rng = np.random.default_rng(14)
+    for t in range(n):
+        a, b, c = (math.ldexp(rng.uniform(-1, 1), int(rng.integers(-60, 60))) for _ in range(3))
+        x, y, z = oracle.three_sum(a, b, c, L)
+        assert F(x) + F(y) + F(z) == F(a) + F(b) + F(c), ("three_sum", a, b, c)
+        x2, y2 = oracle.three_sum2(a, b, c, L)
+        assert x2 == x, "three_sum2 leading part"
+        assert y2 == float(F(y) + F(z)) or abs(F(y2) - (F(y) + F(z))) <= X.ulp(y2) / 2
+
+
+def pin_vec_sum(L, n=500):
+    rng = np.random.default_rng(15)
+    for t in range(n):
+        k = 3 + t % 4
+        xs = [math.ldexp(rng.uniform(-1, 1), int(rng.integers(-100, 100))) for _ in range(k)]
+        e = oracle.vec_sum(xs, L)
+        assert sum(map(F, e)) == sum(map(F, xs)), ("vec_sum exact", xs, e)
+        # the chain runs from the last term up: e0 is the rounded sum of x0 and
+        # the rounded partial sum of the rest
+        s = xs[-1]
+        for x in reversed(xs[:-1]):
+            s = float(F(x) + F(s))
+        assert e[0] == s, ("vec_sum order", xs, e)
+
+
+def pin_vseb(L, n=500):
+    rng = np.random.default_rng(16)
+    # nonoverlapping inputs that fit in k components come back exactly
+    for t in range(n):
+        a = math.ldexp(rng.uniform(0.5, 1) * (1 if t % 2 else -1), int(rng.integers(-20, 20)))
+        b = math.ldexp(rng.uniform(-1, 1), -60) * abs(a)
+        c = math.ldexp(rng.uniform(-1, 1), -60) * abs(b)
+        assert oracle.vseb([a, b, 0.0], 2, L) == (a, b), "vseb (a,b,0)"
+        assert oracle.vseb([a, 0.0, b], 2, L) == (a, b), "vseb (a,0,b)"
+        assert oracle.vseb([a, b, c], 2, L) == (a, b), "vseb stops after k components"
+        assert oracle.vseb([a, b, c], 3, L) == (a, b, c), "vseb (a,b,c) k=3"
+        assert oracle.vseb([0.0, a, b], 2, L) == (a, b), "vseb leading zero"
+    # VecSum outputs compacted to two components keep the value to 2^-104
+    for t in range(n):
+        xs = [math.ldexp(rng.uniform(-1, 1), int(rng.integers(-30, 30))) for _ in range(3)]
+        e = oracle.vec_sum(xs, L)
+        r = oracle.vseb(list(e), 2, L)
+        tot = sum(map(F, xs))
+        if tot:
+            assert abs(sum(map(F, r)) - tot) <= Fraction(2) ** -103 * abs(tot) + X.ulp(r[0]) * U
+
+
+def pin_renorm(L, n=1000):
+    """Five terms of decreasing size with gaps of 40-60 bits (now and then a
+    larger one), as QDadd/QDmul hand them over: the value is kept to 2^-212
+    (worst seen over 30000 cases: 2^-215) and each output component is at
+    most one ulp of the one above it."""
+    rng = np.random.default_rng(17)
+    for t in range(n):
+        c = [math.ldexp(rng.uniform(-1, 1), -int(rng.integers(0, 4)))]
+        for _ in range(4):
+            gap = math.ldexp(rng.uniform(-1, 1), -int(rng.integers(40, 60)))
+            if rng.uniform() >= 0.8:
+                gap *= 2.0 ** int(rng.integers(1, 30))
+            c.append(gap * abs(c[-1]))
+        r = oracle.renorm5(c, L)
+        tot = sum(map(F, c))
+        assert abs(sum(map(F, r)) - tot) <= Fraction(2) ** -212 * abs(tot), ("renorm value", c, r)
+        for i in range(3):
+            if r[i + 1] != 0:
+                assert abs(F(r[i + 1])) <= X.ulp(r[i]), ("renorm nonoverlap", c, r)
+
+
+# ------------------------------------------------------------ DD/TD/QD ops
+
+def _check_bound(prec, name, x, y, r, L):
+    P = oracle.P_OF[prec]
+    xv, yv, rv = X.value(x), X.value(y), X.value(r)
+    if name == "mul":
+        exact, scale = xv * yv, abs(xv * yv)
+    else:
+        exact, scale = xv + yv, abs(xv) + abs(yv)
+    err = abs(rv - exact)
+    assert err <= Fraction(BOUND[(prec, name)]) * scale, (prec, name, list(x), list(y), r,
+                                                           float(err / scale) if scale else err)
+    for i in range(P - 1):                        # output normalised
+        if r[i + 1] != 0:
+            assert abs(F(r[i + 1])) <= X.ulp(r[i]), (prec, name, "overlap", r)
+
+
+def pin_op_bounds(L, n=1500, precs=("dd", "td", "qd")):
+    rng = np.random.default_rng(18)
+    for prec in precs:
+        P = oracle.P_OF[prec]
+        names = ("add", "mul", "addm") if prec == "td" else ("add", "mul")
+        for name in names:
+            xs = I.random_mp(P, n, rng, spread=6)
+            ys = I.random_mp(P, n, rng, spread=6)
+            # a third of the additions nearly cancel in the leading component
+            if name != "mul":
+                cut = n // 3
+                ys[:, :cut] = I.expand(-xs[0, :cut] * (1 + 2.0 ** -40), P, rng)
+            for t in range(n):
+                r = oracle.op(prec, name, xs[:, t], ys[:, t], L)
+                _check_bound(prec, name, xs[:, t], ys[:, t], r, L)
+
+
+def pin_op_special(L, n=400):
+    """Ops on plain doubles reduce to a single EFT."""
+    rng = np.random.default_rng(19)
+    for a, b in _pairs(rng, n, 40):
+        s, e = oracle.two_sum(a, b, L)
+        p, q = oracle.two_prod(a, b, L)
+        for prec in ("dd", "td", "qd"):
+            P = oracle.P_OF[prec]
+            z = [0.0] * (P - 1)
+            names = ("add", "addm") if prec == "td" else ("add",)
+            for name in names:
+                r = oracle.op(prec, name, [a] + z, [b] + z, L)
+                assert list(r) == [s, e] + [0.0] * (P - 2), (prec, name, a, b, r, s, e)
+            r = oracle.op(prec, "mul", [a] + z, [b] + z, L)
+            if abs(p) > 2.0 ** -900 or p == 0:
+                assert list(r) == [p, q] + [0.0] * (P - 2), (prec, "mul", a, b, r, p, q)
+
+
+def _golden_lines():
+    with open(os.path.join(GOLDEN, "worked_examples.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                yield [s.strip() for s in line.split("|")]
+
+
+def pin_worked(L):
+    for f in _golden_lines():
+        opn = f[0]
+        x = [float(eval(v)) for v in f[1].split(",")]
+        want = [float(eval(v)) for v in f[3].split(",")]
+        if opn == "renorm5":
+            got = oracle.renorm5(x, L)
+        else:
+            prec, name = opn.split("_")
+            y = [float(eval(v)) for v in f[2].split(",")]
+            got = oracle.op(prec, name, x, y, L)
+        assert list(got) == want, (opn, f[1], f[2], got, want, f[4])
+
+
+# ------------------------------------------------------------------ GEMM
+
+def pin_gemm_integer(L, size=24):
+    """Integer matrices with |a|,|b| < 2^20 and k <= 2^10: every partial sum is
+    an exactly representable integer, so C is exact with zero lower parts."""
+    rng = np.random.default_rng(20)
+    for prec in ("dd", "td", "qd"):
+        P = oracle.P_OF[prec]
+        m, n, k = size, size + 3, size + 5
+        A = np.zeros((P, m, k))
+        B = np.zeros((P, k, n))
+        A[0] = rng.integers(-(1 << 19), 1 << 19, size=(m, k))
+        B[0] = rng.integers(-(1 << 19), 1 << 19, size=(k, n))
+        C = oracle.gemm(prec, A, B, L=L)
+        want = A[0].astype(object).dot(B[0].astype(object))
+        assert (C[0] == want.astype(np.float64)).all(), prec
+        assert (C[1:] == 0).all(), prec
+
+
+def pin_gemm_bound(L, size=20):
+    """Random and cancelling products against the exact product (Eq. 1):
+    normwise error within n 2^-p of || |A||B| ||."""
+    for prec in ("dd", "td", "qd"):
+        P = oracle.P_OF[prec]
+        rng = np.random.default_rng(21 + P)
+        m, n, k = size, size + 1, size + 2
+        for A, B in ((I.uniform(P, (m, k), rng), I.uniform(P, (k, n), rng)),
+                     I.cancelling_pair(P, m, n, k, rng)):
+            C = oracle.gemm(prec, A, B, L=L)
+            ent = [(i, j) for i in range(m) for j in range(n)]
+            err = X.gemm_error(C, A, B, ent)
+            assert err["err_abs"] <= k * 2.0 ** -GEMM_P[prec], (prec, err)
+
+
+def pin_gemm_structure(L, size=9):
+    """A I = A, A with permuted columns = A times a permutation, B^T handled as
+    a separate matrix, and k = 1 equal to the elementwise product."""
+    rng = np.random.default_rng(22)
+    for prec in ("dd", "td", "qd"):
+        P = oracle.P_OF[prec]
+        A = I.uniform(P, (size, size + 2), rng)
+        Id = np.zeros((P, size + 2, size + 2))
+        Id[0] = np.eye(size + 2)
+        C = oracle.gemm(prec, A, Id, L=L)
+        assert (C == A).all(), (prec, "identity")
+        perm = rng.permutation(size + 2)
+        Pm = np.zeros((P, size + 2, size + 2))
+        Pm[0][perm, np.arange(size + 2)] = 1.0
+        C = oracle.gemm(prec, A, Pm, L=L)
+        assert (C == A[:, :, perm]).all(), (prec, "permutation")
+        a = I.uniform(P, (size, 1), rng)
+        b = I.uniform(P, (1, size + 1), rng)
+        C = oracle.gemm(prec, a, b, L=L)
+        for i in range(size):
+            for j in range(size + 1):
+                want = oracle.op(prec, "mul", a[:, i, 0], b[:, 0, j], L)
+                assert tuple(C[:, i, j]) == want, (prec, "k=1 is one mul (x = A side)")
+
+
+def pin_gemm_paper(L, n=17):
+    """Sec. 3 test matrices: every c_ij equals sqrt(15) N_i within the rounding
+    of the inputs and the bound; also exact against the rounded inputs."""
+    for prec in ("dd", "td", "qd"):
+        P = oracle.P_OF[prec]
+        A, B = I.paper_matrices(P, n)
+        C = oracle.gemm(prec, A, B, L=L)
+        p = GEMM_P[prec]
+        for i in range(n):
+            Ni = I.paper_closed_form(n, i + 1)
+            # sqrt(15) N_i to many bits, from an exact integer square root
+            s15 = Fraction(math.isqrt(15 * Ni * Ni << 800), 1 << 400)
+            for j in (0, n // 2, n - 1):
+                got = X.value(C[:, i, j])
+                assert abs(got - s15) <= Fraction(n) * Fraction(2) ** (-p + 2) * s15 + \
+                    Fraction(2) ** -390, (prec, i, j)
+        ent = [(i, j) for i in range(n) for j in (0, n - 1)]
+        assert X.gemm_error(C, A, B, ent)["err_abs"] <= n * 2.0 ** -p
+
+
+ALL_PINS = [pin_two_sum, pin_quick_two_sum, pin_two_prod, pin_three_sums, pin_vec_sum,
+            pin_vseb, pin_renorm, pin_worked, pin_op_special, pin_op_bounds,
+            pin_gemm_integer, pin_gemm_bound, pin_gemm_structure, pin_gemm_paper]
