@@ -1,0 +1,172 @@
+/*
+ * mpgemm.h -- C ABI of the GB300 multi-component (DD/TD/QD) GEMM library.
+ *
+ * Implements the hot path of T. Kouya, "Acceleration of multiple precision
+ * matrix multiplication based on multi-component floating-point arithmetic
+ * using AVX2" (arXiv 2101.06584): the matrix product C := A B of Sec. 3,
+ * Eq. 1, in double-double (DD, 2 components), triple-double (TD, 3) and
+ * quad-double (QD, 4) arithmetic, built from the error-free transformations
+ * of Sec. 2.1 and the additions/multiplications of Sec. 2.2-2.4 (Alg. 1-6).
+ *
+ * Data layout (Sec. 2.5, Fig. 1; Sec. 3 row-major): a P-component vector or
+ * matrix is P separate planes of binary64, plane 0 the most significant
+ * component.  A matrix plane is row-major: element (i, j) of plane c of X is
+ * X[c][i * ldx + j].  Arguments of the form `const double *const X[P]` are
+ * host arrays of P DEVICE pointers.
+ *
+ * Ownership: every pointer is owned by the caller.  The library allocates no
+ * device memory; calls that need scratch take a caller-provided workspace.
+ * Kernels run asynchronously on the calling thread's current stream (see
+ * mpgemm_set_stream); a call returns once the work is enqueued.
+ *
+ * Errors: every entry point returns an mpg_status.  Invalid arguments are
+ * detected on the host and return MPG_EINVAL without launching anything; a
+ * failed launch returns MPG_ECUDA.  mpgemm_last_error() gives a message for
+ * the calling thread's most recent failure.  Faults during asynchronous
+ * execution surface at the caller's next synchronisation.
+ *
+ * Numerics: inputs are finite binary64 components; the results of the
+ * elementwise operations and of the k-sequential GEMM are the exact bits of
+ * the paper's algorithms (round to nearest even, no contraction other than
+ * the algorithms' own FMAs).  Non-finite inputs give unspecified output.
+ */
+#ifndef MPGEMM_H
+#define MPGEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum mpg_status {
+    MPG_OK = 0,
+    MPG_EINVAL = -1,       /* invalid argument; nothing was launched */
+    MPG_ECUDA = -2,        /* a CUDA call or launch failed */
+    MPG_EWORKSPACE = -3,   /* workspace missing, too small or misaligned */
+    MPG_EUNSUPPORTED = -4  /* valid request this build does not provide */
+} mpg_status;
+
+/* Message describing the calling thread's most recent failure ("" if none). */
+const char *mpgemm_last_error(void);
+
+/* Set / get the CUDA stream (a cudaStream_t, NULL = legacy default stream)
+ * on which the calling thread's subsequent calls enqueue their kernels. */
+int mpgemm_set_stream(void *stream);
+void *mpgemm_get_stream(void);
+
+/* Library ABI version (major * 100 + minor). */
+int mpgemm_version(void);
+
+/* ---------------------------------------------------------------------
+ * Elementwise error-free transformations, Sec. 2.1, over n-vectors:
+ *   QuickTwoSum: s_i = fl(a_i + b_i), e_i = b_i - (s_i - a_i)
+ *   TwoSum:      s_i = fl(a_i + b_i), e_i = (a_i + b_i) - s_i exactly
+ *   TwoProd:     s_i = fl(a_i b_i),   e_i = fma(a_i, b_i, -s_i)
+ * a, b, s, e: device arrays of n binary64; s and e must not overlap a or b
+ * unless identical to them.  n = 0 is a no-op; n < 0 or a NULL pointer with
+ * n > 0 is MPG_EINVAL.
+ * ------------------------------------------------------------------- */
+int mp_quick_two_sum(int64_t n, const double *a, const double *b, double *s, double *e);
+int mp_two_sum(int64_t n, const double *a, const double *b, double *s, double *e);
+int mp_two_prod(int64_t n, const double *a, const double *b, double *s, double *e);
+
+/* ---------------------------------------------------------------------
+ * Elementwise multi-component add/mul of SoA vectors (Sec. 2.5):
+ * r_i = x_i (+|*) y_i for i < n.
+ *   mp_dd_add  Alg. 1        mp_dd_mul  Alg. 2
+ *   mp_td_add  TDaddq, Sec. 2.3 (QDadd with zero fourth components; the
+ *              paper's default TD addition)
+ *   mp_td_add_merge  Alg. 3 (Merge, VecSum, VSEB(3))
+ *   mp_td_mul  Alg. 4        mp_qd_add  Alg. 5        mp_qd_mul  Alg. 6
+ * x, y, r: host arrays of P device pointers to n binary64 each.  r may
+ * alias x or y exactly (in place); partial overlap is not allowed.
+ * ------------------------------------------------------------------- */
+int mp_dd_add(int64_t n, const double *const x[2], const double *const y[2], double *const r[2]);
+int mp_dd_mul(int64_t n, const double *const x[2], const double *const y[2], double *const r[2]);
+int mp_td_add(int64_t n, const double *const x[3], const double *const y[3], double *const r[3]);
+int mp_td_add_merge(int64_t n, const double *const x[3], const double *const y[3], double *const r[3]);
+int mp_td_mul(int64_t n, const double *const x[3], const double *const y[3], double *const r[3]);
+int mp_qd_add(int64_t n, const double *const x[4], const double *const y[4], double *const r[4]);
+int mp_qd_mul(int64_t n, const double *const x[4], const double *const y[4], double *const r[4]);
+
+/* ---------------------------------------------------------------------
+ * GEMM, Sec. 3, Eq. 1: C := A B with A m x k, B k x n, C m x n, each a set
+ * of P row-major device planes.  C is overwritten (there is no alpha/beta,
+ * as in the paper).  Requirements: m, n, k >= 0; lda >= max(1, k),
+ * ldb >= max(1, n), ldc >= max(1, n); no NULL plane where the matrix is
+ * non-empty; C must not overlap A or B.  k = 0 sets C to zero; m = 0 or
+ * n = 0 is a no-op.
+ *
+ * These calls run the k-sequential FP64-EFT kernel: every c_ij is
+ * accumulated by one thread as acc = add(acc, mul(a_ip, b_pj)) for
+ * p = 0, 1, ..., k-1 from acc = 0, with mul/add the paper's DD (Alg. 1-2),
+ * TD (Alg. 4, TDaddq) or QD (Alg. 5-6) operations, a_ip the left operand.
+ * The result is bit-identical to that sequence evaluated anywhere else.
+ * ------------------------------------------------------------------- */
+int mpgemm_dd(int64_t m, int64_t n, int64_t k,
+              const double *const A[2], int64_t lda,
+              const double *const B[2], int64_t ldb,
+              double *const C[2], int64_t ldc);
+int mpgemm_td(int64_t m, int64_t n, int64_t k,
+              const double *const A[3], int64_t lda,
+              const double *const B[3], int64_t ldb,
+              double *const C[3], int64_t ldc);
+int mpgemm_qd(int64_t m, int64_t n, int64_t k,
+              const double *const A[4], int64_t lda,
+              const double *const B[4], int64_t ldb,
+              double *const C[4], int64_t ldc);
+
+/* Algorithms selectable through mpgemm_ex. */
+typedef enum mpg_algo {
+    MPG_ALGO_AUTO = 0,       /* the FP64-EFT kernel (k-sequential unless split_k > 1) */
+    MPG_ALGO_FP64_EFT = 1,   /* FP64 error-free transformations on the CUDA cores */
+    MPG_ALGO_INT8_OZAKI = 2  /* DD only: error-free INT8 slicing on the tensor cores */
+} mpg_algo;
+
+/* Options of mpgemm_ex.  Zero-initialised options give the plain call. */
+typedef struct mpgemm_opts {
+    int trans_a;    /* 1: A is given as its k x m transpose (element (i,p) at A[c][p*lda+i]) */
+    int trans_b;    /* 1: B is given as its n x k transpose (element (p,j) at B[c][j*ldb+p]) */
+    int algo;       /* an mpg_algo */
+    int split_k;    /* 0/1: k-sequential.  s > 1: the k range is cut into s contiguous
+                       chunks, summed separately and combined with the precision's
+                       add in a fixed tree order (not bit-identical to k-sequential;
+                       within the same error bound) */
+    int slices;     /* INT8_OZAKI: slices per operand, 0 = default */
+    int tile;       /* FP64_EFT: tile configuration id 1..mpgemm_num_tiles(P); 0 or -1 =
+                       library choice */
+    void *workspace;          /* device scratch for algorithms that need it */
+    size_t workspace_bytes;
+} mpgemm_opts;
+
+/* C := op(A) op(B) with the options above; P in {2, 3, 4}; lda/ldb must
+ * cover the stored (possibly transposed) shapes. */
+int mpgemm_ex(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k,
+              const double *const *A, int64_t lda,
+              const double *const *B, int64_t ldb,
+              double *const *C, int64_t ldc);
+
+/* Bytes of workspace mpgemm_ex needs for these options and sizes (0 if none). */
+size_t mpgemm_workspace_size(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k);
+
+/* Number of FP64-EFT tile configurations for precision P, and a description
+ * of configuration id (BM, BN, BK, TM, TN, threads); returns MPG_EINVAL for
+ * an unknown id. */
+int mpgemm_num_tiles(int P);
+int mpgemm_tile_info(int P, int id, int info[6]);
+
+/* ---------------------------------------------------------------------
+ * Measurement aid (no counterpart in the paper): FP64 pipe throughput probe.
+ * Launches `blocks` CTAs of 256 threads, each thread running `iters` rounds
+ * of 8 independent binary64 operations (kind 0 add, 1 mul, 2 fma) and
+ * writing one double to out[blocks * 256] (device, caller-owned).  The caller
+ * times the launch; lane-operations = blocks * 256 * iters * 8.
+ * ------------------------------------------------------------------- */
+int mpgemm_fp64_probe(int kind, int blocks, int iters, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPGEMM_H */

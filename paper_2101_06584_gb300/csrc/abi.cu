@@ -1,0 +1,295 @@
+// abi.cu -- the extern "C" entry points of include/mpgemm.h: argument
+// validation on the host (no launch on a bad argument), dispatch to the
+// kernels on the calling thread's stream, and error reporting.
+#include "mpgemm.h"
+#include "internal.h"
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+namespace mpg {
+
+namespace {
+thread_local char g_err[512] = "";
+thread_local cudaStream_t g_stream = nullptr;
+
+int fail(int code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where)
+{
+    return fail(MPG_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// Byte range [lo, hi) touched by a rows x cols plane with leading dimension ld.
+struct Range {
+    uintptr_t lo, hi;
+};
+Range plane_range(const void* p, int64_t rows, int64_t cols, int64_t ld)
+{
+    if (!p || rows <= 0 || cols <= 0) return {0, 0};
+    const uintptr_t lo = reinterpret_cast<uintptr_t>(p);
+    const uint64_t elems = static_cast<uint64_t>(rows - 1) * static_cast<uint64_t>(ld) +
+                           static_cast<uint64_t>(cols);
+    return {lo, lo + elems * sizeof(double)};
+}
+bool overlap(Range a, Range b)
+{
+    return a.lo < a.hi && b.lo < b.hi && a.lo < b.hi && b.lo < a.hi;
+}
+}  // namespace
+
+int num_sms()
+{
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (!cache[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+            v = 152;
+        cache[dev] = v;
+    }
+    return cache[dev];
+}
+
+cudaStream_t current_stream() { return g_stream; }
+void clear_error() { g_err[0] = '\0'; }
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
+// ------------------------------------------------------------ validation
+
+static int check_vec(int P, int64_t n, const double* const* x, const double* const* y,
+                     double* const* r)
+{
+    if (n < 0) return fail(MPG_EINVAL, "n must be >= 0 (got %lld)", (long long)n);
+    if (n == 0) return MPG_OK;
+    if (!x || !y || !r) return fail(MPG_EINVAL, "plane pointer arrays must not be NULL");
+    for (int c = 0; c < P; ++c)
+        if (!x[c] || !y[c] || !r[c])
+            return fail(MPG_EINVAL, "component plane %d is NULL", c);
+    for (int c = 0; c < P; ++c) {
+        const Range rc = plane_range(r[c], 1, n, n);
+        for (int d = 0; d < P; ++d) {
+            if (d != c && overlap(rc, plane_range(r[d], 1, n, n)))
+                return fail(MPG_EINVAL, "output planes %d and %d overlap", c, d);
+            for (const double* in : {x[d], y[d]}) {
+                const Range ri = plane_range(in, 1, n, n);
+                const bool same = (d == c && in == r[c]);
+                if (!same && overlap(rc, ri))
+                    return fail(MPG_EINVAL, "output plane %d partially overlaps an input plane", c);
+            }
+        }
+    }
+    return MPG_OK;
+}
+
+template <int P>
+static int vec_call(int op, int64_t n, const double* const* x, const double* const* y,
+                    double* const* r)
+{
+    clear_error();
+    int rc = check_vec(P, n, x, y, r);
+    if (rc != MPG_OK || n == 0) return rc;
+    cudaError_t e = launch_vec<P>(op, n, x, y, r, g_stream);
+    return e == cudaSuccess ? MPG_OK : cuda_fail(e, "elementwise launch");
+}
+
+static int eft_call(int which, int64_t n, const double* a, const double* b, double* s, double* e)
+{
+    clear_error();
+    if (n < 0) return fail(MPG_EINVAL, "n must be >= 0 (got %lld)", (long long)n);
+    if (n == 0) return MPG_OK;
+    if (!a || !b || !s || !e) return fail(MPG_EINVAL, "NULL pointer with n > 0");
+    const Range rs = plane_range(s, 1, n, n), re = plane_range(e, 1, n, n);
+    if (overlap(rs, re)) return fail(MPG_EINVAL, "s and e overlap");
+    for (const double* in : {a, b}) {
+        const Range ri = plane_range(in, 1, n, n);
+        if ((overlap(rs, ri) && in != s) || (overlap(re, ri) && in != e))
+            return fail(MPG_EINVAL, "an output partially overlaps an input");
+    }
+    cudaError_t err = launch_eft(which, n, a, b, s, e, g_stream);
+    return err == cudaSuccess ? MPG_OK : cuda_fail(err, "eft launch");
+}
+
+template <int P>
+int check_gemm(const GemmArgs<P>& g)
+{
+    if (g.m < 0 || g.n < 0 || g.k < 0)
+        return fail(MPG_EINVAL, "m, n, k must be >= 0 (got %lld, %lld, %lld)", (long long)g.m,
+                    (long long)g.n, (long long)g.k);
+    // stored shapes of A and B
+    const int64_t ar = g.trans_a ? g.k : g.m, ac = g.trans_a ? g.m : g.k;
+    const int64_t br = g.trans_b ? g.n : g.k, bc = g.trans_b ? g.k : g.n;
+    const int64_t one = 1;
+    if (g.lda < (ac > one ? ac : one))
+        return fail(MPG_EINVAL, "lda (%lld) must be >= max(1, %lld)", (long long)g.lda, (long long)ac);
+    if (g.ldb < (bc > one ? bc : one))
+        return fail(MPG_EINVAL, "ldb (%lld) must be >= max(1, %lld)", (long long)g.ldb, (long long)bc);
+    if (g.ldc < (g.n > one ? g.n : one))
+        return fail(MPG_EINVAL, "ldc (%lld) must be >= max(1, %lld)", (long long)g.ldc, (long long)g.n);
+    const bool needA = g.m > 0 && g.k > 0 && g.n > 0;
+    const bool needB = needA;
+    const bool needC = g.m > 0 && g.n > 0;
+    for (int c = 0; c < P; ++c) {
+        if (needA && !g.A[c]) return fail(MPG_EINVAL, "A plane %d is NULL", c);
+        if (needB && !g.B[c]) return fail(MPG_EINVAL, "B plane %d is NULL", c);
+        if (needC && !g.C[c]) return fail(MPG_EINVAL, "C plane %d is NULL", c);
+    }
+    if (!needC) return MPG_OK;
+    for (int c = 0; c < P; ++c) {
+        const Range rc = plane_range(g.C[c], g.m, g.n, g.ldc);
+        for (int d = 0; d < P; ++d) {
+            if (d != c && overlap(rc, plane_range(g.C[d], g.m, g.n, g.ldc)))
+                return fail(MPG_EINVAL, "C planes %d and %d overlap", c, d);
+            if (needA && overlap(rc, plane_range(g.A[d], ar, ac, g.lda)))
+                return fail(MPG_EINVAL, "C plane %d overlaps A plane %d", c, d);
+            if (needB && overlap(rc, plane_range(g.B[d], br, bc, g.ldb)))
+                return fail(MPG_EINVAL, "C plane %d overlaps B plane %d", c, d);
+        }
+    }
+    return MPG_OK;
+}
+
+template <int P>
+static int gemm_call(const mpgemm_opts* o, int64_t m, int64_t n, int64_t k,
+                     const double* const* A, int64_t lda, const double* const* B, int64_t ldb,
+                     double* const* C, int64_t ldc)
+{
+    clear_error();
+    if (!A || !B || !C) return fail(MPG_EINVAL, "plane pointer arrays must not be NULL");
+    GemmArgs<P> g;
+    for (int c = 0; c < P; ++c) {
+        g.A[c] = A[c];
+        g.B[c] = B[c];
+        g.C[c] = C[c];
+    }
+    g.m = m; g.n = n; g.k = k; g.lda = lda; g.ldb = ldb; g.ldc = ldc;
+    g.trans_a = o ? (o->trans_a != 0) : 0;
+    g.trans_b = o ? (o->trans_b != 0) : 0;
+    int rc = check_gemm<P>(g);
+    if (rc != MPG_OK) return rc;
+    if (m == 0 || n == 0) return MPG_OK;
+    const int algo = o ? o->algo : MPG_ALGO_AUTO;
+    if (algo != MPG_ALGO_AUTO && algo != MPG_ALGO_FP64_EFT)
+        return fail(MPG_EUNSUPPORTED, "algorithm %d is not available for P = %d here", algo, P);
+    cudaError_t e;
+    if (k == 0) {
+        e = launch_zero<P>(g, g_stream);
+        return e == cudaSuccess ? MPG_OK : cuda_fail(e, "zero launch");
+    }
+    const int split = o ? o->split_k : 0;
+    if (split > 1) {
+        if (split != 2 && split != 4 && split != 8 && split != 16 && split != 32)
+            return fail(MPG_EINVAL, "split_k must be 0, 1, 2, 4, 8, 16 or 32 (got %d)", split);
+        e = launch_gemm_splitk<P>(g, split, g_stream);
+        return e == cudaSuccess ? MPG_OK : cuda_fail(e, "split-k gemm launch");
+    }
+    if (split < 0) return fail(MPG_EINVAL, "split_k must be >= 0 (got %d)", split);
+    int tile = o ? o->tile : 0;
+    if (tile <= 0) tile = default_tile<P>(m, n, k);
+    else tile -= 1;
+    if (tile >= num_tiles<P>()) return fail(MPG_EINVAL, "tile id %d out of range", tile + 1);
+    const TileInfo ti = tile_info<P>(tile);
+    if ((n + ti.bn - 1) / ti.bn > 2147483647LL || (m + ti.bm - 1) / ti.bm > 65535LL)
+        return fail(MPG_EINVAL, "matrix too large for the grid of tile %d", tile + 1);
+    e = launch_gemm_kseq<P>(g, tile, g_stream);
+    return e == cudaSuccess ? MPG_OK : cuda_fail(e, "gemm launch");
+}
+
+}  // namespace mpg
+
+using namespace mpg;
+
+extern "C" {
+
+const char* mpgemm_last_error(void) { return g_err; }
+
+int mpgemm_set_stream(void* stream)
+{
+    g_stream = static_cast<cudaStream_t>(stream);
+    return MPG_OK;
+}
+
+void* mpgemm_get_stream(void) { return static_cast<void*>(g_stream); }
+
+int mpgemm_version(void) { return 100; }
+
+int mp_quick_two_sum(int64_t n, const double* a, const double* b, double* s, double* e)
+{ return eft_call(0, n, a, b, s, e); }
+int mp_two_sum(int64_t n, const double* a, const double* b, double* s, double* e)
+{ return eft_call(1, n, a, b, s, e); }
+int mp_two_prod(int64_t n, const double* a, const double* b, double* s, double* e)
+{ return eft_call(2, n, a, b, s, e); }
+
+int mp_dd_add(int64_t n, const double* const x[2], const double* const y[2], double* const r[2])
+{ return vec_call<2>(0, n, x, y, r); }
+int mp_dd_mul(int64_t n, const double* const x[2], const double* const y[2], double* const r[2])
+{ return vec_call<2>(1, n, x, y, r); }
+int mp_td_add(int64_t n, const double* const x[3], const double* const y[3], double* const r[3])
+{ return vec_call<3>(0, n, x, y, r); }
+int mp_td_add_merge(int64_t n, const double* const x[3], const double* const y[3], double* const r[3])
+{ return vec_call<3>(2, n, x, y, r); }
+int mp_td_mul(int64_t n, const double* const x[3], const double* const y[3], double* const r[3])
+{ return vec_call<3>(1, n, x, y, r); }
+int mp_qd_add(int64_t n, const double* const x[4], const double* const y[4], double* const r[4])
+{ return vec_call<4>(0, n, x, y, r); }
+int mp_qd_mul(int64_t n, const double* const x[4], const double* const y[4], double* const r[4])
+{ return vec_call<4>(1, n, x, y, r); }
+
+int mpgemm_dd(int64_t m, int64_t n, int64_t k, const double* const A[2], int64_t lda,
+              const double* const B[2], int64_t ldb, double* const C[2], int64_t ldc)
+{ return gemm_call<2>(nullptr, m, n, k, A, lda, B, ldb, C, ldc); }
+int mpgemm_td(int64_t m, int64_t n, int64_t k, const double* const A[3], int64_t lda,
+              const double* const B[3], int64_t ldb, double* const C[3], int64_t ldc)
+{ return gemm_call<3>(nullptr, m, n, k, A, lda, B, ldb, C, ldc); }
+int mpgemm_qd(int64_t m, int64_t n, int64_t k, const double* const A[4], int64_t lda,
+              const double* const B[4], int64_t ldb, double* const C[4], int64_t ldc)
+{ return gemm_call<4>(nullptr, m, n, k, A, lda, B, ldb, C, ldc); }
+
+int mpgemm_ex(int P, const mpgemm_opts* opts, int64_t m, int64_t n, int64_t k,
+              const double* const* A, int64_t lda, const double* const* B, int64_t ldb,
+              double* const* C, int64_t ldc)
+{
+    switch (P) {
+    case 2: return gemm_call<2>(opts, m, n, k, A, lda, B, ldb, C, ldc);
+    case 3: return gemm_call<3>(opts, m, n, k, A, lda, B, ldb, C, ldc);
+    case 4: return gemm_call<4>(opts, m, n, k, A, lda, B, ldb, C, ldc);
+    default: clear_error(); return fail(MPG_EINVAL, "P must be 2, 3 or 4 (got %d)", P);
+    }
+}
+
+size_t mpgemm_workspace_size(int P, const mpgemm_opts* opts, int64_t m, int64_t n, int64_t k)
+{
+    (void)P; (void)opts; (void)m; (void)n; (void)k;
+    return 0;
+}
+
+int mpgemm_num_tiles(int P)
+{
+    switch (P) {
+    case 2: return num_tiles<2>();
+    case 3: return num_tiles<3>();
+    case 4: return num_tiles<4>();
+    default: return 0;
+    }
+}
+
+int mpgemm_tile_info(int P, int id, int info[6])
+{
+    clear_error();
+    const int nt = mpgemm_num_tiles(P);
+    if (nt == 0 || id < 1 || id > nt || !info) return fail(MPG_EINVAL, "unknown tile %d for P = %d", id, P);
+    TileInfo t = P == 2 ? tile_info<2>(id - 1) : P == 3 ? tile_info<3>(id - 1) : tile_info<4>(id - 1);
+    info[0] = t.bm; info[1] = t.bn; info[2] = t.bk; info[3] = t.tm; info[4] = t.tn; info[5] = t.threads;
+    return MPG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,109 @@
+// elementwise.cu -- elementwise EFTs and DD/TD/QD add/mul over SoA vectors
+// (Sec. 2.1-2.5).  Each element is independent; a grid-stride loop with one
+// element per thread per iteration keeps loads coalesced per plane.  Every
+// kernel here is FP64-bound on GB300 (e.g. a DD add is 11 FP64 operations for
+// 48 bytes of traffic), so there is no staging.
+#include "internal.h"
+#include "mp_arith.cuh"
+
+namespace mpg {
+
+template <int P>
+struct VecArgs {
+    const double* x[P];
+    const double* y[P];
+    double* r[P];
+    int64_t n;
+};
+
+template <int P, int OP>
+__global__ void __launch_bounds__(256) vec_kernel(const VecArgs<P> a)
+{
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < a.n;
+         i += stride) {
+        double x[P], y[P], r[P];
+#pragma unroll
+        for (int c = 0; c < P; ++c) {
+            x[c] = a.x[c][i];
+            y[c] = a.y[c][i];
+        }
+        if constexpr (OP == 0) {
+            mp::Ops<P>::add(x, y, r);
+        } else if constexpr (OP == 1) {
+            mp::Ops<P>::mul(x, y, r);
+        } else {
+            static_assert(P == 3, "merge-based add is the TD addition of Alg. 3");
+            mp::td_add_merge(x, y, r);
+        }
+#pragma unroll
+        for (int c = 0; c < P; ++c) a.r[c][i] = r[c];
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(256)
+eft_kernel(int64_t n, const double* a, const double* b, double* s,
+           double* e)
+{
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += stride) {
+        double hi, lo;
+        if constexpr (W == 0) mp::quick_two_sum(a[i], b[i], hi, lo);
+        else if constexpr (W == 1) mp::two_sum(a[i], b[i], hi, lo);
+        else mp::two_prod(a[i], b[i], hi, lo);
+        s[i] = hi;
+        e[i] = lo;
+    }
+}
+
+static unsigned grid_for(int64_t n)
+{
+    int64_t blocks = (n + 255) / 256;
+    const int64_t cap = static_cast<int64_t>(num_sms()) * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    return static_cast<unsigned>(blocks);
+}
+
+template <int P>
+cudaError_t launch_vec(int op, int64_t n, const double* const* x, const double* const* y,
+                       double* const* r, cudaStream_t s)
+{
+    VecArgs<P> a;
+    for (int c = 0; c < P; ++c) {
+        a.x[c] = x[c];
+        a.y[c] = y[c];
+        a.r[c] = r[c];
+    }
+    a.n = n;
+    const unsigned grid = grid_for(n);
+    if (op == 0) vec_kernel<P, 0><<<grid, 256, 0, s>>>(a);
+    else if (op == 1) vec_kernel<P, 1><<<grid, 256, 0, s>>>(a);
+    else if constexpr (P == 3) vec_kernel<P, 2><<<grid, 256, 0, s>>>(a);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_vec<2>(int, int64_t, const double* const*, const double* const*,
+                                   double* const*, cudaStream_t);
+template cudaError_t launch_vec<3>(int, int64_t, const double* const*, const double* const*,
+                                   double* const*, cudaStream_t);
+template cudaError_t launch_vec<4>(int, int64_t, const double* const*, const double* const*,
+                                   double* const*, cudaStream_t);
+
+cudaError_t launch_eft(int which, int64_t n, const double* a, const double* b, double* s,
+                       double* e, cudaStream_t st)
+{
+    const unsigned grid = grid_for(n);
+    switch (which) {
+    case 0: eft_kernel<0><<<grid, 256, 0, st>>>(n, a, b, s, e); break;
+    case 1: eft_kernel<1><<<grid, 256, 0, st>>>(n, a, b, s, e); break;
+    case 2: eft_kernel<2><<<grid, 256, 0, st>>>(n, a, b, s, e); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace mpg

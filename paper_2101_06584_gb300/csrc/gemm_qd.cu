@@ -1,0 +1,47 @@
+// gemm_qd.cu -- instantiations of the FP64-EFT GEMM kernels for P = 4.
+#include "gemm_kernel.cuh"
+
+namespace mpg {
+namespace {
+constexpr int P = 4;
+const TileInfo kTiles[] = {
+    {16, 16, 16, 1, 1, 256},
+    {32, 16, 16, 2, 1, 256},
+    {32, 32, 16, 2, 2, 256},
+};
+constexpr int kNumTiles = static_cast<int>(sizeof(kTiles) / sizeof(kTiles[0]));
+}  // namespace
+
+template <>
+int num_tiles<P>() { return kNumTiles; }
+
+template <>
+TileInfo tile_info<P>(int t) { return kTiles[t]; }
+
+template <>
+int default_tile<P>(int64_t, int64_t, int64_t) { return 0; }
+
+template <>
+cudaError_t launch_gemm_kseq<P>(const GemmArgs<P>& g, int tile, cudaStream_t s)
+{
+    switch (tile) {
+    case 0: return launch_kseq_cfg<P, 16, 16, 16, 1, 1>(g, s);
+    case 1: return launch_kseq_cfg<P, 32, 16, 16, 2, 1>(g, s);
+    case 2: return launch_kseq_cfg<P, 32, 32, 16, 2, 2>(g, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <>
+cudaError_t launch_gemm_splitk<P>(const GemmArgs<P>& g, int split, cudaStream_t s)
+{
+    return launch_splitk_impl<P>(g, split, s);
+}
+
+template <>
+cudaError_t launch_zero<P>(const GemmArgs<P>& g, cudaStream_t s)
+{
+    return launch_zero_impl<P>(g, s);
+}
+
+}  // namespace mpg

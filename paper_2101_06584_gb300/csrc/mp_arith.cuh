@@ -1,0 +1,376 @@
+// mp_arith.cuh -- device-side multi-component (DD/TD/QD) arithmetic.
+//
+// The operations of Kouya, arXiv 2101.06584, Sec. 2: error-free
+// transformations (Sec. 2.1), DDadd/DDmul (Alg. 1-2), TDadd (Alg. 3),
+// TDaddq (Sec. 2.3), TDmul (Alg. 4), QDadd/QDmul (Alg. 5-6) with the
+// renormalisation of the QD library and VecSum/VSEB of Fabiano, Muller and
+// Picot, which the paper uses without restating.
+//
+// Every rounded operation is an explicit __dadd_rn/__dsub_rn/__dmul_rn/__fma_rn
+// intrinsic, so the compiler cannot contract or reorder them: each function
+// performs the same sequence of IEEE binary64 operations as the paper's
+// algorithm and therefore returns the same bits as any other faithful
+// implementation.  Data-dependent branches (the nonzero tests of VSEB and
+// Renorm) are written as selects that pick exactly the value the branch
+// would; the tests themselves look at the bit pattern with integer
+// instructions so they do not occupy the FP64 pipe.
+#pragma once
+#include <cstdint>
+
+namespace mp {
+
+__device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// x != 0 (true for every value but +0 and -0), tested on the bit pattern.
+__device__ __forceinline__ bool nonzero(double x)
+{
+    return (static_cast<unsigned long long>(__double_as_longlong(x)) << 1) != 0ull;
+}
+
+// |a| >= |b| for finite a, b, compared as integers.
+__device__ __forceinline__ bool abs_ge(double a, double b)
+{
+    const unsigned long long m = 0x7fffffffffffffffull;
+    return (static_cast<unsigned long long>(__double_as_longlong(a)) & m) >=
+           (static_cast<unsigned long long>(__double_as_longlong(b)) & m);
+}
+
+// ------------------------------------------------------------- Sec. 2.1
+
+// QuickTwoSum: s = fl(a + b), e = b - (s - a).
+__device__ __forceinline__ void quick_two_sum(double a, double b, double& s, double& e)
+{
+    const double sum = add(a, b);
+    e = sub(b, sub(sum, a));
+    s = sum;
+}
+
+// TwoSum: s = fl(a + b) and e = (a + b) - s exactly.
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e)
+{
+    const double sum = add(a, b);
+    const double bv = sub(sum, a);
+    const double av = sub(sum, bv);
+    e = add(sub(a, av), sub(b, bv));
+    s = sum;
+}
+
+// TwoProd with FMA: p = fl(a b), e = a b - p exactly.
+__device__ __forceinline__ void two_prod(double a, double b, double& p, double& e)
+{
+    const double prod = mul(a, b);
+    e = fma(a, b, -prod);
+    p = prod;
+}
+
+// ------------------------------------------------- helpers of Alg. 3 - 6
+
+// ThreeSum: (a, b, c) -> (a', b', c'), same exact sum.
+__device__ __forceinline__ void three_sum(double& a, double& b, double& c)
+{
+    double t1, t2, t3;
+    two_sum(a, b, t1, t2);
+    two_sum(c, t1, a, t3);
+    two_sum(t2, t3, b, c);
+}
+
+// ThreeSum2: as ThreeSum with the two low terms added in one rounding.
+__device__ __forceinline__ void three_sum2(double& a, double& b, double c)
+{
+    double t1, t2, t3;
+    two_sum(a, b, t1, t2);
+    two_sum(c, t1, a, t3);
+    b = add(t2, t3);
+}
+
+// Renorm of five terms into four: a bottom-up QuickTwoSum pass, then a
+// top-down pass that emits a component whenever the QuickTwoSum error is
+// nonzero, folding everything after the third emitted component into the
+// fourth.  k counts emitted components; r_k selects stand in for indexing.
+__device__ __forceinline__ void renorm5(double c0, double c1, double c2, double c3, double c4,
+                                        double& r0, double& r1, double& r2, double& r3)
+{
+    double s, t0, t1, t2, t3, t4;
+    quick_two_sum(c3, c4, s, t4);
+    quick_two_sum(c2, s, s, t3);
+    quick_two_sum(c1, s, s, t2);
+    quick_two_sum(c0, s, t0, t1);
+
+    r0 = 0.0; r1 = 0.0; r2 = 0.0; r3 = 0.0;
+    int k = 0;
+    double hi, lo;
+    bool emit;
+
+    // term 1 (k == 0 here)
+    quick_two_sum(t0, t1, hi, lo);
+    emit = nonzero(lo);
+    r0 = emit ? hi : r0;
+    k = emit ? 1 : 0;
+    s = emit ? lo : hi;
+
+    // term 2 (k <= 1)
+    quick_two_sum(s, t2, hi, lo);
+    emit = nonzero(lo);
+    r0 = (emit && k == 0) ? hi : r0;
+    r1 = (emit && k == 1) ? hi : r1;
+    k += emit ? 1 : 0;
+    s = emit ? lo : hi;
+
+    // term 3 (k <= 2)
+    quick_two_sum(s, t3, hi, lo);
+    emit = nonzero(lo);
+    r0 = (emit && k == 0) ? hi : r0;
+    r1 = (emit && k == 1) ? hi : r1;
+    r2 = (emit && k == 2) ? hi : r2;
+    k += emit ? 1 : 0;
+    s = emit ? lo : hi;
+
+    // term 4: with three components out, the sum is a plain add, which is
+    // exactly the QuickTwoSum's rounded sum
+    quick_two_sum(s, t4, hi, lo);
+    emit = nonzero(lo) && k < 3;
+    r0 = (emit && k == 0) ? hi : r0;
+    r1 = (emit && k == 1) ? hi : r1;
+    r2 = (emit && k == 2) ? hi : r2;
+    k += emit ? 1 : 0;
+    s = emit ? lo : hi;
+
+    r0 = (k == 0) ? s : r0;
+    r1 = (k == 1) ? s : r1;
+    r2 = (k == 2) ? s : r2;
+    r3 = (k == 3) ? s : r3;
+}
+
+// VecSum of three / four terms: TwoSum chain from the last term up.
+__device__ __forceinline__ void vec_sum3(double x0, double x1, double x2,
+                                         double& e0, double& e1, double& e2)
+{
+    double s;
+    two_sum(x1, x2, s, e2);
+    two_sum(x0, s, e0, e1);
+}
+
+__device__ __forceinline__ void vec_sum4(double x0, double x1, double x2, double x3,
+                                         double& e0, double& e1, double& e2, double& e3)
+{
+    double s;
+    two_sum(x2, x3, s, e3);
+    two_sum(x1, s, s, e2);
+    two_sum(x0, s, e0, e1);
+}
+
+// VSEB(2) on three terms.  Following the loop: the first QuickTwoSum writes
+// r0 and either moves to r1 (nonzero error) or carries its sum on; the second
+// writes the current slot; after it the loop returns if both slots are done,
+// otherwise a nonzero remainder lands in the current slot.
+__device__ __forceinline__ void vseb2_of3(double e0, double e1, double e2, double& r0, double& r1)
+{
+    double h1, l1, h2, l2;
+    quick_two_sum(e0, e1, h1, l1);
+    const bool nz1 = nonzero(l1);
+    quick_two_sum(nz1 ? l1 : h1, e2, h2, l2);
+    const bool nz2 = nonzero(l2);
+    r0 = nz1 ? h1 : h2;
+    r1 = nz1 ? h2 : (nz2 ? l2 : 0.0);
+}
+
+// VSEB(3) on six terms (used by the merge-based TDadd).
+__device__ __forceinline__ void vseb3_of6(const double e[6], double& r0, double& r1, double& r2)
+{
+    r0 = 0.0; r1 = 0.0; r2 = 0.0;
+    int j = 0;
+    bool done = false;
+    double eps = e[0];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        double hi, lo;
+        quick_two_sum(eps, e[i + 1], hi, lo);
+        const bool w = !done;
+        r0 = (w && j == 0) ? hi : r0;
+        r1 = (w && j == 1) ? hi : r1;
+        r2 = (w && j == 2) ? hi : r2;
+        const bool nz = nonzero(lo);
+        const bool finish = w && nz && j >= 2;
+        const bool adv = w && nz && j < 2;
+        eps = w ? (nz ? lo : hi) : eps;
+        j += adv ? 1 : 0;
+        done = done || finish;
+    }
+    const bool tail = !done && nonzero(eps);
+    r0 = (tail && j == 0) ? eps : r0;
+    r1 = (tail && j == 1) ? eps : r1;
+    r2 = (tail && j == 2) ? eps : r2;
+}
+
+// ------------------------------------------------------------- Sec. 2.2
+
+// Alg. 1, DDadd.
+__device__ __forceinline__ void dd_add(const double x[2], const double y[2], double r[2])
+{
+    double s, e;
+    two_sum(x[0], y[0], s, e);
+    const double w = add(x[1], y[1]);
+    e = add(e, w);
+    quick_two_sum(s, e, r[0], r[1]);
+}
+
+// Alg. 2, DDmul.
+__device__ __forceinline__ void dd_mul(const double x[2], const double y[2], double r[2])
+{
+    double p1, p2;
+    two_prod(x[0], y[0], p1, p2);
+    const double w1 = mul(x[0], y[1]);
+    const double w2 = mul(x[1], y[0]);
+    const double w3 = add(w1, w2);
+    p2 = add(p2, w3);
+    quick_two_sum(p1, p2, r[0], r[1]);
+}
+
+// ------------------------------------------------------------- Sec. 2.3
+
+// Alg. 4, TDmul (the "fast" triple-word product).
+__device__ __forceinline__ void td_mul(const double x[3], const double y[3], double r[3])
+{
+    double z00up, z00lo, z01up, z01lo, z10up, z10lo;
+    two_prod(x[0], y[0], z00up, z00lo);
+    two_prod(x[0], y[1], z01up, z01lo);
+    two_prod(x[1], y[0], z10up, z10lo);
+    double b0, b1, b2;
+    vec_sum3(z00lo, z01up, z10up, b0, b1, b2);
+    const double c = fma(x[1], y[1], b2);
+    const double z31 = fma(x[0], y[2], z10lo);
+    const double z32 = fma(x[2], y[0], z01lo);
+    const double z3 = add(z31, z32);
+    const double s3 = add(c, z3);
+    double e0, e1, e2, e3;
+    vec_sum4(z00up, b0, b1, s3, e0, e1, e2, e3);
+    r[0] = e0;
+    vseb2_of3(e1, e2, e3, r[1], r[2]);
+}
+
+// ------------------------------------------------------------- Sec. 2.4
+
+// Alg. 5, QDadd (sloppy); t3 is the error of the fourth componentwise sum.
+__device__ __forceinline__ void qd_add(const double x[4], const double y[4], double r[4])
+{
+    double s0 = add(x[0], y[0]);
+    double s1 = add(x[1], y[1]);
+    double s2 = add(x[2], y[2]);
+    double s3 = add(x[3], y[3]);
+    const double v0 = sub(s0, x[0]);
+    const double v1 = sub(s1, x[1]);
+    const double v2 = sub(s2, x[2]);
+    const double v3 = sub(s3, x[3]);
+    const double w0 = sub(x[0], sub(s0, v0));
+    const double w1 = sub(x[1], sub(s1, v1));
+    const double w2 = sub(x[2], sub(s2, v2));
+    const double w3 = sub(x[3], sub(s3, v3));
+    double t0 = add(w0, sub(y[0], v0));
+    double t1 = add(w1, sub(y[1], v1));
+    double t2 = add(w2, sub(y[2], v2));
+    const double t3 = add(w3, sub(y[3], v3));
+    two_sum(s1, t0, s1, t0);
+    three_sum(s2, t0, t1);
+    three_sum2(s3, t0, t2);
+    t0 = add(add(t0, t1), t3);
+    renorm5(s0, s1, s2, s3, t0, r[0], r[1], r[2], r[3]);
+}
+
+// TDaddq (Sec. 2.3): QDadd on operands padded with a zero fourth component,
+// the fourth result component dropped.
+__device__ __forceinline__ void td_addq(const double x[3], const double y[3], double r[3])
+{
+    const double x4[4] = {x[0], x[1], x[2], 0.0};
+    const double y4[4] = {y[0], y[1], y[2], 0.0};
+    double r4[4];
+    qd_add(x4, y4, r4);
+    r[0] = r4[0];
+    r[1] = r4[1];
+    r[2] = r4[2];
+}
+
+// Alg. 3, TDadd: Merge (by decreasing magnitude, x first on ties), VecSum,
+// VSEB(3).
+__device__ __forceinline__ void td_add_merge(const double x[3], const double y[3], double r[3])
+{
+    double z[6];
+    int i = 0, j = 0;
+#pragma unroll
+    for (int o = 0; o < 6; ++o) {
+        const double xi = (i == 0) ? x[0] : (i == 1) ? x[1] : x[2];
+        const double yj = (j == 0) ? y[0] : (j == 1) ? y[1] : y[2];
+        const bool takex = (j >= 3) || (i < 3 && abs_ge(xi, yj));
+        z[o] = takex ? xi : yj;
+        i += takex ? 1 : 0;
+        j += takex ? 0 : 1;
+    }
+    double e[6];
+    double s = z[5];
+#pragma unroll
+    for (int t = 4; t >= 0; --t)
+        two_sum(z[t], s, s, e[t + 1]);
+    e[0] = s;
+    vseb3_of6(e, r[0], r[1], r[2]);
+}
+
+// Alg. 6, QDmul (sloppy).  The listing's first line is dead and omitted.
+__device__ __forceinline__ void qd_mul(const double x[4], const double y[4], double r[4])
+{
+    double p0, p1, p2, p3, p4, p5, q0, q1, q2, q3, q4, q5;
+    two_prod(x[0], y[0], p0, q0);
+    two_prod(x[0], y[1], p1, q1);
+    two_prod(x[1], y[0], p2, q2);
+    two_prod(x[0], y[2], p3, q3);
+    two_prod(x[1], y[1], p4, q4);
+    two_prod(x[2], y[0], p5, q5);
+    three_sum(p1, p2, q0);
+    three_sum(p2, q1, q2);
+    three_sum(p3, p4, p5);
+    double s0, s1, s2, t0, t1;
+    two_sum(p2, p3, s0, t0);
+    two_sum(q1, p4, s1, t1);
+    s2 = add(q2, p5);
+    two_sum(s1, t0, s1, t0);
+    s2 = add(s2, add(t0, t1));
+    s1 = add(s1, mul(x[0], y[3]));
+    s1 = add(s1, mul(x[1], y[2]));
+    s1 = add(s1, mul(x[2], y[1]));
+    s1 = add(s1, mul(x[3], y[0]));
+    s1 = add(s1, q0);
+    s1 = add(s1, q3);
+    s1 = add(s1, q4);
+    s1 = add(s1, q5);
+    renorm5(p0, p1, s0, s1, s2, r[0], r[1], r[2], r[3]);
+}
+
+// ------------------------------------------------ generic by component count
+
+template <int P> struct Ops;
+template <> struct Ops<2> {
+    static __device__ __forceinline__ void mul(const double* x, const double* y, double* r) { dd_mul(x, y, r); }
+    static __device__ __forceinline__ void add(const double* x, const double* y, double* r) { dd_add(x, y, r); }
+};
+template <> struct Ops<3> {
+    static __device__ __forceinline__ void mul(const double* x, const double* y, double* r) { td_mul(x, y, r); }
+    static __device__ __forceinline__ void add(const double* x, const double* y, double* r) { td_addq(x, y, r); }
+};
+template <> struct Ops<4> {
+    static __device__ __forceinline__ void mul(const double* x, const double* y, double* r) { qd_mul(x, y, r); }
+    static __device__ __forceinline__ void add(const double* x, const double* y, double* r) { qd_add(x, y, r); }
+};
+
+// acc = add(acc, mul(a, b)): one multiply-add of the GEMM, a from A, b from B.
+template <int P>
+__device__ __forceinline__ void mad(double* acc, const double* a, const double* b)
+{
+    double prod[P], sum[P];
+    Ops<P>::mul(a, b, prod);
+    Ops<P>::add(acc, prod, sum);
+#pragma unroll
+    for (int c = 0; c < P; ++c) acc[c] = sum[c];
+}
+
+}  // namespace mp

@@ -1,0 +1,49 @@
+// probe.cu -- FP64 pipe throughput probe used as the roofline denominator.
+//
+// GB300 executes binary64 add/mul/fma at roughly two lanes per clock per SM;
+// this kernel measures that ceiling at the clocks of the calling run.  Each
+// thread runs 8 independent chains of the chosen instruction so latency is
+// hidden; the caller times the launch with events and divides the lane
+// operations (blocks * 256 * iters * 8) by the elapsed time.
+#include "mpgemm.h"
+#include "internal.h"
+
+namespace mpg {
+
+template <int KIND>
+__global__ void __launch_bounds__(256) fp64_probe_kernel(int iters, double a, double b, double* out)
+{
+    double x[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = threadIdx.x * 1e-3 + j;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if constexpr (KIND == 0) x[j] = __dadd_rn(x[j], b);
+            else if constexpr (KIND == 1) x[j] = __dmul_rn(x[j], a);
+            else x[j] = __fma_rn(x[j], a, b);
+        }
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s = __dadd_rn(s, x[j]);
+    out[static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace mpg
+
+extern "C" int mpgemm_fp64_probe(int kind, int blocks, int iters, double* out)
+{
+    using namespace mpg;
+    if (kind < 0 || kind > 2 || blocks < 1 || iters < 1 || !out)
+        return set_error(MPG_EINVAL, "mpgemm_fp64_probe: kind 0..2, blocks >= 1, iters >= 1, out non-NULL");
+    clear_error();
+    cudaStream_t s = current_stream();
+    switch (kind) {
+    case 0: fp64_probe_kernel<0><<<blocks, 256, 0, s>>>(iters, 0.9999999, 1e-7, out); break;
+    case 1: fp64_probe_kernel<1><<<blocks, 256, 0, s>>>(iters, 0.9999999, 1e-7, out); break;
+    default: fp64_probe_kernel<2><<<blocks, 256, 0, s>>>(iters, 0.9999999, 1e-7, out); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MPG_OK : set_error(MPG_ECUDA, cudaGetErrorString(e));
+}

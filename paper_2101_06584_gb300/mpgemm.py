@@ -1,0 +1,207 @@
+"""Thin Python binding of libmpgemm.so (include/mpgemm.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Tensors are torch float64 CUDA tensors of shape (P, rows, cols)
+(structure-of-arrays planes, row-major, plane 0 most significant) or, for
+vectors, (P, n).  Calls are enqueued on torch's current CUDA stream.  There is
+no CPU fallback: if the library is missing or a tensor is not on a CUDA
+device, the call raises.
+"""
+import ctypes
+import os
+
+import torch
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libmpgemm.so")
+P_OF = {"dd": 2, "td": 3, "qd": 4}
+ALGO = {"auto": 0, "fp64": 1, "int8": 2}
+
+_lib = None
+
+
+class MPGError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("mpgemm error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("trans_a", ctypes.c_int), ("trans_b", ctypes.c_int), ("algo", ctypes.c_int),
+                ("split_k", ctypes.c_int), ("slices", ctypes.c_int), ("tile", ctypes.c_int),
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libmpgemm.so is not built (run paper_2101_06584_gb300.build.build())")
+        _lib = _declare(ctypes.CDLL(LIB_PATH))
+    return _lib
+
+
+def _declare(L):
+    i64, vp, i = ctypes.c_int64, ctypes.c_void_p, ctypes.c_int
+    L.mpgemm_last_error.restype = ctypes.c_char_p
+    L.mpgemm_set_stream.argtypes = [vp]
+    L.mpgemm_get_stream.restype = vp
+    for f in ("mp_quick_two_sum", "mp_two_sum", "mp_two_prod"):
+        getattr(L, f).argtypes = [i64, vp, vp, vp, vp]
+    for f in ("mp_dd_add", "mp_dd_mul", "mp_td_add", "mp_td_add_merge", "mp_td_mul",
+              "mp_qd_add", "mp_qd_mul"):
+        getattr(L, f).argtypes = [i64, vp, vp, vp]
+    for f in ("mpgemm_dd", "mpgemm_td", "mpgemm_qd"):
+        getattr(L, f).argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64]
+    L.mpgemm_ex.argtypes = [i, ctypes.POINTER(Opts), i64, i64, i64, vp, i64, vp, i64, vp, i64]
+    L.mpgemm_workspace_size.argtypes = [i, ctypes.POINTER(Opts), i64, i64, i64]
+    L.mpgemm_workspace_size.restype = ctypes.c_size_t
+    L.mpgemm_num_tiles.argtypes = [i]
+    L.mpgemm_tile_info.argtypes = [i, i, ctypes.POINTER(ctypes.c_int * 6)]
+    return L
+
+
+def check(rc):
+    if rc != 0:
+        raise MPGError(rc, lib().mpgemm_last_error().decode())
+
+
+def _bind_stream():
+    lib().mpgemm_set_stream(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
+def _require(t, name, P=None, ndim=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch tensor" % name)
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor (the library has no CPU path)" % name)
+    if t.dtype != torch.float64:
+        raise ValueError("%s must be float64" % name)
+    if P is not None and t.shape[0] != P:
+        raise ValueError("%s must have %d component planes, got %d" % (name, P, t.shape[0]))
+    if ndim is not None and t.dim() != ndim:
+        raise ValueError("%s must have %d dimensions" % (name, ndim))
+    if t.stride(-1) != 1:
+        raise ValueError("%s planes must be row-major with unit column stride" % name)
+
+
+def planes(t):
+    """Host array of the device pointers of the component planes of t."""
+    P = t.shape[0]
+    return (ctypes.c_void_p * P)(*[t[c].data_ptr() for c in range(P)])
+
+
+def _ld(t):
+    return t.stride(1) if t.shape[1] > 1 else max(t.shape[2], 1)
+
+
+def gemm(prec, A, B, out=None, trans_a=False, trans_b=False, algo="auto", split_k=0, tile=0,
+         slices=0, workspace=None):
+    """C = op(A) op(B) for (P, rows, cols) planes; op = transpose when trans_*.
+
+    A is (P, m, k) or, with trans_a, (P, k, m); B is (P, k, n) or, with
+    trans_b, (P, n, k).  Returns C (P, m, n) (``out`` if given)."""
+    P = P_OF[prec]
+    _require(A, "A", P, 3)
+    _require(B, "B", P, 3)
+    m, k = (A.shape[2], A.shape[1]) if trans_a else (A.shape[1], A.shape[2])
+    kb, n = (B.shape[2], B.shape[1]) if trans_b else (B.shape[1], B.shape[2])
+    if kb != k:
+        raise ValueError("inner dimensions differ: %d vs %d" % (k, kb))
+    if out is None:
+        out = torch.empty((P, m, n), dtype=torch.float64, device=A.device)
+    _require(out, "out", P, 3)
+    if tuple(out.shape[1:]) != (m, n):
+        raise ValueError("out must be (P, %d, %d)" % (m, n))
+    o = Opts(int(trans_a), int(trans_b), ALGO[algo], int(split_k), int(slices), int(tile),
+             None, 0)
+    if workspace is not None:
+        _require_ws(workspace)
+        o.workspace = workspace.data_ptr()
+        o.workspace_bytes = workspace.numel() * workspace.element_size()
+    _bind_stream()
+    check(lib().mpgemm_ex(P, ctypes.byref(o), m, n, k, planes(A), _ld(A), planes(B), _ld(B),
+                          planes(out), _ld(out)))
+    return out
+
+
+def _require_ws(w):
+    if not isinstance(w, torch.Tensor) or not w.is_cuda or not w.is_contiguous():
+        raise ValueError("workspace must be a contiguous CUDA tensor")
+
+
+def workspace_size(prec, m, n, k, algo="auto", slices=0, split_k=0, trans_a=False, trans_b=False):
+    o = Opts(int(trans_a), int(trans_b), ALGO[algo], int(split_k), int(slices), 0, None, 0)
+    return int(lib().mpgemm_workspace_size(P_OF[prec], ctypes.byref(o), m, n, k))
+
+
+def gemm_plain(prec, A, B, out=None):
+    """C = A B through mpgemm_dd/td/qd (the paper's call, k-sequential)."""
+    P = P_OF[prec]
+    _require(A, "A", P, 3)
+    _require(B, "B", P, 3)
+    m, k = A.shape[1], A.shape[2]
+    n = B.shape[2]
+    if B.shape[1] != k:
+        raise ValueError("inner dimensions differ")
+    if out is None:
+        out = torch.empty((P, m, n), dtype=torch.float64, device=A.device)
+    _require(out, "out", P, 3)
+    _bind_stream()
+    fn = getattr(lib(), "mpgemm_" + prec)
+    check(fn(m, n, k, planes(A), _ld(A), planes(B), _ld(B), planes(out), _ld(out)))
+    return out
+
+
+_VEC = {("dd", "add"): "mp_dd_add", ("dd", "mul"): "mp_dd_mul", ("td", "add"): "mp_td_add",
+        ("td", "addm"): "mp_td_add_merge", ("td", "mul"): "mp_td_mul",
+        ("qd", "add"): "mp_qd_add", ("qd", "mul"): "mp_qd_mul"}
+
+
+def vec(prec, op, x, y, out=None):
+    """Elementwise r = x (add|mul) y over (P, n) SoA vectors (``addm``: Alg. 3 TD add)."""
+    P = P_OF[prec]
+    _require(x, "x", P, 2)
+    _require(y, "y", P, 2)
+    if x.shape != y.shape:
+        raise ValueError("x and y differ in shape")
+    if out is None:
+        out = torch.empty_like(x)
+    _require(out, "out", P, 2)
+    _bind_stream()
+    check(getattr(lib(), _VEC[(prec, op)])(x.shape[1], planes(x), planes(y), planes(out)))
+    return out
+
+
+def eft(which, a, b):
+    """Elementwise EFT (quick_two_sum | two_sum | two_prod) of 1-D tensors; returns (s, e)."""
+    for t, nm in ((a, "a"), (b, "b")):
+        _require(t, nm)
+    if a.shape != b.shape or a.dim() != 1:
+        raise ValueError("a and b must be 1-D of equal length")
+    s, e = torch.empty_like(a), torch.empty_like(a)
+    _bind_stream()
+    check(getattr(lib(), "mp_" + which)(a.numel(), a.data_ptr(), b.data_ptr(), s.data_ptr(),
+                                        e.data_ptr()))
+    return s, e
+
+
+def num_tiles(prec):
+    return lib().mpgemm_num_tiles(P_OF[prec])
+
+
+def tile_info(prec, tile):
+    info = (ctypes.c_int * 6)()
+    check(lib().mpgemm_tile_info(P_OF[prec], tile, ctypes.byref(info)))
+    return dict(zip(("bm", "bn", "bk", "tm", "tn", "threads"), list(info)))
+
+
+def fp64_probe(kind, blocks, iters, out):
+    """Launch the FP64 throughput probe (kind 0 add, 1 mul, 2 fma) writing to
+    ``out`` (a CUDA float64 tensor of blocks*256 elements)."""
+    if out.numel() < blocks * 256 or not out.is_cuda or out.dtype != torch.float64:
+        raise ValueError("out must be a CUDA float64 tensor of at least blocks*256 elements")
+    lib().mpgemm_fp64_probe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+    _bind_stream()
+    check(lib().mpgemm_fp64_probe(int(kind), int(blocks), int(iters), out.data_ptr()))

@@ -1,0 +1,137 @@
+"""The C-ABI library builds, loads and exports every function that
+include/*.h declares; host-side argument validation rejects bad calls with
+MPG_EINVAL and a message, without launching anything (no GPU needed: the
+plane addresses below are never dereferenced)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2101_06584_gb300 import build, mpgemm
+    build.build()
+    return mpgemm.lib()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b([A-Za-z_]\w*)\s*\(", text, flags=re.M):
+            name = m.group(1)
+            if name not in ("if", "while", "return", "sizeof", "defined"):
+                names.add(name)
+    return sorted(names)
+
+
+def test_header_declares_the_paper_calls():
+    names = declared_functions()
+    for f in ("mpgemm_dd", "mpgemm_td", "mpgemm_qd", "mp_two_sum", "mp_two_prod",
+              "mp_quick_two_sum", "mp_dd_add", "mp_qd_mul", "mpgemm_ex"):
+        assert f in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    missing = [f for f in declared_functions() if not hasattr(L, f)]
+    assert not missing, missing
+
+
+FAKE = 1 << 40       # plausible-looking device addresses, never dereferenced
+
+
+def ptrs(*addrs):
+    return (ctypes.c_void_p * len(addrs))(*addrs)
+
+
+def planes(base, P, stride=1 << 30):
+    return ptrs(*[base + c * stride for c in range(P)])
+
+
+def err(L):
+    return L.mpgemm_last_error().decode()
+
+
+def test_gemm_rejects_negative_dims(L):
+    A, B, C = planes(FAKE, 2), planes(2 * FAKE, 2), planes(3 * FAKE, 2)
+    assert L.mpgemm_dd(-1, 4, 4, A, 4, B, 4, C, 4) == -1
+    assert "m, n, k" in err(L)
+    assert L.mpgemm_dd(4, 4, -2, A, 4, B, 4, C, 4) == -1
+
+
+def test_gemm_rejects_small_leading_dims(L):
+    A, B, C = planes(FAKE, 3), planes(2 * FAKE, 3), planes(3 * FAKE, 3)
+    assert L.mpgemm_td(8, 9, 10, A, 9, B, 9, C, 9) == -1
+    assert "lda" in err(L)
+    assert L.mpgemm_td(8, 9, 10, A, 10, B, 8, C, 9) == -1
+    assert "ldb" in err(L)
+    assert L.mpgemm_td(8, 9, 10, A, 10, B, 9, C, 8) == -1
+    assert "ldc" in err(L)
+
+
+def test_gemm_rejects_null_planes(L):
+    A, B, C = planes(FAKE, 4), planes(2 * FAKE, 4), planes(3 * FAKE, 4)
+    A[2] = None
+    assert L.mpgemm_qd(8, 8, 8, A, 8, B, 8, C, 8) == -1
+    assert "A plane 2" in err(L)
+    assert L.mpgemm_qd(8, 8, 8, None, 8, B, 8, C, 8) == -1
+
+
+def test_gemm_rejects_overlap(L):
+    A, B = planes(FAKE, 2), planes(2 * FAKE, 2)
+    C = ptrs(FAKE + 64, 3 * FAKE)                       # C[0] inside A[0]
+    assert L.mpgemm_dd(8, 8, 8, A, 8, B, 8, C, 8) == -1
+    assert "overlaps A" in err(L)
+    C = ptrs(3 * FAKE, 3 * FAKE + 8 * 8)                # C planes overlap each other
+    assert L.mpgemm_dd(8, 8, 8, A, 8, B, 8, C, 8) == -1
+    assert "C planes" in err(L)
+
+
+def test_gemm_empty_is_a_noop(L):
+    A, B, C = planes(FAKE, 2), planes(2 * FAKE, 2), planes(3 * FAKE, 2)
+    assert L.mpgemm_dd(0, 8, 8, A, 8, B, 8, C, 8) == 0
+    assert L.mpgemm_dd(8, 0, 8, A, 8, B, 1, C, 1) == 0
+
+
+def test_ex_rejects_bad_options(L):
+    from paper_2101_06584_gb300.mpgemm import Opts
+    A, B, C = planes(FAKE, 2), planes(2 * FAKE, 2), planes(3 * FAKE, 2)
+    o = Opts(0, 0, 0, 3, 0, 0, None, 0)
+    assert L.mpgemm_ex(2, ctypes.byref(o), 8, 8, 8, A, 8, B, 8, C, 8) == -1
+    assert "split_k" in err(L)
+    o = Opts(0, 0, 0, 0, 0, 99, None, 0)
+    assert L.mpgemm_ex(2, ctypes.byref(o), 8, 8, 8, A, 8, B, 8, C, 8) == -1
+    assert "tile" in err(L)
+    assert L.mpgemm_ex(5, None, 8, 8, 8, A, 8, B, 8, C, 8) == -1
+    o = Opts(1, 0, 0, 0, 0, 0, None, 0)                  # trans_a: A stored k x m
+    assert L.mpgemm_ex(2, ctypes.byref(o), 8, 8, 16, A, 4, B, 8, C, 8) == -1
+    assert "lda" in err(L)
+
+
+def test_vector_validation(L):
+    x, y, r = planes(FAKE, 2), planes(2 * FAKE, 2), planes(3 * FAKE, 2)
+    assert L.mp_dd_add(-5, x, y, r) == -1
+    assert L.mp_dd_add(0, None, None, None) == 0
+    bad = ptrs(FAKE + 8, 3 * FAKE)                       # partial overlap with x[0]
+    assert L.mp_dd_mul(100, x, y, bad) == -1
+    assert "overlap" in err(L)
+    assert L.mp_two_sum(10, FAKE, 2 * FAKE, 3 * FAKE, 3 * FAKE + 8) == -1
+
+
+def test_tile_table(L):
+    for P in (2, 3, 4):
+        nt = L.mpgemm_num_tiles(P)
+        assert nt >= 3
+        for t in range(1, nt + 1):
+            info = (ctypes.c_int * 6)()
+            assert L.mpgemm_tile_info(P, t, ctypes.byref(info)) == 0
+            bm, bn, bk, tm, tn, threads = list(info)
+            assert bm % tm == 0 and bn % tn == 0 and (bm // tm) * (bn // tn) == threads
+        info = (ctypes.c_int * 6)()
+        assert L.mpgemm_tile_info(P, nt + 1, ctypes.byref(info)) == -1
