@@ -19,6 +19,7 @@ struct VecArgs {
 template <int P, int OP>
 __global__ void __launch_bounds__(256) vec_kernel(const VecArgs<P> a)
 {
+    const mp::Rn f = mp::make_rn();
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < a.n;
          i += stride) {
@@ -29,12 +30,12 @@ __global__ void __launch_bounds__(256) vec_kernel(const VecArgs<P> a)
             y[c] = a.y[c][i];
         }
         if constexpr (OP == 0) {
-            mp::Ops<P>::add(x, y, r);
+            mp::Ops<P>::add(f, x, y, r);
         } else if constexpr (OP == 1) {
-            mp::Ops<P>::mul(x, y, r);
+            mp::Ops<P>::mul(f, x, y, r);
         } else {
             static_assert(P == 3, "merge-based add is the TD addition of Alg. 3");
-            mp::td_add_merge(x, y, r);
+            mp::td_add_merge(f, x, y, r);
         }
 #pragma unroll
         for (int c = 0; c < P; ++c) a.r[c][i] = r[c];
@@ -46,13 +47,14 @@ __global__ void __launch_bounds__(256)
 eft_kernel(int64_t n, const double* a, const double* b, double* s,
            double* e)
 {
+    const mp::Rn f = mp::make_rn();
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
          i += stride) {
         double hi, lo;
-        if constexpr (W == 0) mp::quick_two_sum(a[i], b[i], hi, lo);
-        else if constexpr (W == 1) mp::two_sum(a[i], b[i], hi, lo);
-        else mp::two_prod(a[i], b[i], hi, lo);
+        if constexpr (W == 0) mp::quick_two_sum(f, a[i], b[i], hi, lo);
+        else if constexpr (W == 1) mp::two_sum(f, a[i], b[i], hi, lo);
+        else mp::two_prod(f, a[i], b[i], hi, lo);
         s[i] = hi;
         e[i] = lo;
     }

@@ -31,6 +31,7 @@ gemm_kseq_kernel(const GemmArgs<P> g)
     __shared__ double As[P][BK][BM + 1];
     __shared__ double Bs[P][BK][BN];
 
+    const mp::Rn f = mp::make_rn();
     const int tid = threadIdx.x;
     const int tx = tid % TX;
     const int ty = tid / TX;
@@ -83,7 +84,7 @@ gemm_kseq_kernel(const GemmArgs<P> g)
 #pragma unroll
             for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < TN; ++j) mp::mad<P>(acc[i][j], a[i], b[j]);
+                for (int j = 0; j < TN; ++j) mp::mad<P>(f, acc[i][j], a[i], b[j]);
         }
         __syncthreads();
     }
@@ -107,6 +108,7 @@ __global__ void __launch_bounds__(256)
 gemm_splitk_warp_kernel(const GemmArgs<P> g)
 {
     constexpr int OUT_PER_WARP = 32 / S;
+    const mp::Rn f = mp::make_rn();
     const int lane = threadIdx.x & 31;
     const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t out = warp * OUT_PER_WARP + lane / S;
@@ -133,7 +135,7 @@ gemm_splitk_warp_kernel(const GemmArgs<P> g)
             a[c] = g.A[c][offa];
             b[c] = g.B[c][offb];
         }
-        mp::mad<P>(acc, a, b);
+        mp::mad<P>(f, acc, a, b);
     }
 
     // butterfly over the S lanes of this output: at each level the lane whose
@@ -150,7 +152,7 @@ gemm_splitk_warp_kernel(const GemmArgs<P> g)
             lo[c] = lower ? acc[c] : other[c];
             hi[c] = lower ? other[c] : acc[c];
         }
-        mp::Ops<P>::add(lo, hi, sum);
+        mp::Ops<P>::add(f, lo, hi, sum);
 #pragma unroll
         for (int c = 0; c < P; ++c) acc[c] = sum[c];
     }

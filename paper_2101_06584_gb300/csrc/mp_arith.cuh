@@ -19,10 +19,30 @@
 
 namespace mp {
 
-__device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
-__device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+// Rounded binary64 operations.  On GB300 a DFMA instruction issues at about
+// 1.19x the rate of DADD or DMUL, so every operation is issued as a fused
+// multiply-add that rounds to exactly the same value:
+//   a + b = f.fma(a, 1, b),   a - b = f.fma(b, -1, a),   a * b = f.fma(a, b, -0)
+// (the product with +-1 is exact; adding -0 changes no value and keeps the
+// sign of a zero product).  `one` and `neg_zero` come from a kernel argument
+// so the compiler cannot fold the FMAs back into DADD/DMUL.
+struct Rn {
+    double one;       // +1.0
+    double neg_zero;  // -0.0
+    __device__ __forceinline__ double add(double a, double b) const { return __fma_rn(a, one, b); }
+    __device__ __forceinline__ double sub(double a, double b) const { return __fma_rn(b, -one, a); }
+    __device__ __forceinline__ double mul(double a, double b) const { return __fma_rn(a, b, neg_zero); }
+    __device__ __forceinline__ double fma(double a, double b, double c) const { return __fma_rn(a, b, c); }
+};
+
+static __device__ double rn_constants[2] = {1.0, -0.0};
+
+// The Rn constants, read through a volatile pointer into registers.
+__device__ __forceinline__ Rn make_rn()
+{
+    const volatile double* p = rn_constants;
+    return Rn{p[0], p[1]};
+}
 
 // x != 0 (true for every value but +0 and -0), tested on the bit pattern.
 __device__ __forceinline__ bool nonzero(double x)
@@ -41,63 +61,63 @@ __device__ __forceinline__ bool abs_ge(double a, double b)
 // ------------------------------------------------------------- Sec. 2.1
 
 // QuickTwoSum: s = fl(a + b), e = b - (s - a).
-__device__ __forceinline__ void quick_two_sum(double a, double b, double& s, double& e)
+__device__ __forceinline__ void quick_two_sum(const Rn& f, double a, double b, double& s, double& e)
 {
-    const double sum = add(a, b);
-    e = sub(b, sub(sum, a));
+    const double sum = f.add(a, b);
+    e = f.sub(b, f.sub(sum, a));
     s = sum;
 }
 
 // TwoSum: s = fl(a + b) and e = (a + b) - s exactly.
-__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e)
+__device__ __forceinline__ void two_sum(const Rn& f, double a, double b, double& s, double& e)
 {
-    const double sum = add(a, b);
-    const double bv = sub(sum, a);
-    const double av = sub(sum, bv);
-    e = add(sub(a, av), sub(b, bv));
+    const double sum = f.add(a, b);
+    const double bv = f.sub(sum, a);
+    const double av = f.sub(sum, bv);
+    e = f.add(f.sub(a, av), f.sub(b, bv));
     s = sum;
 }
 
 // TwoProd with FMA: p = fl(a b), e = a b - p exactly.
-__device__ __forceinline__ void two_prod(double a, double b, double& p, double& e)
+__device__ __forceinline__ void two_prod(const Rn& f, double a, double b, double& p, double& e)
 {
-    const double prod = mul(a, b);
-    e = fma(a, b, -prod);
+    const double prod = f.mul(a, b);
+    e = f.fma(a, b, -prod);
     p = prod;
 }
 
 // ------------------------------------------------- helpers of Alg. 3 - 6
 
 // ThreeSum: (a, b, c) -> (a', b', c'), same exact sum.
-__device__ __forceinline__ void three_sum(double& a, double& b, double& c)
+__device__ __forceinline__ void three_sum(const Rn& f, double& a, double& b, double& c)
 {
     double t1, t2, t3;
-    two_sum(a, b, t1, t2);
-    two_sum(c, t1, a, t3);
-    two_sum(t2, t3, b, c);
+    two_sum(f, a, b, t1, t2);
+    two_sum(f, c, t1, a, t3);
+    two_sum(f, t2, t3, b, c);
 }
 
 // ThreeSum2: as ThreeSum with the two low terms added in one rounding.
-__device__ __forceinline__ void three_sum2(double& a, double& b, double c)
+__device__ __forceinline__ void three_sum2(const Rn& f, double& a, double& b, double c)
 {
     double t1, t2, t3;
-    two_sum(a, b, t1, t2);
-    two_sum(c, t1, a, t3);
-    b = add(t2, t3);
+    two_sum(f, a, b, t1, t2);
+    two_sum(f, c, t1, a, t3);
+    b = f.add(t2, t3);
 }
 
 // Renorm of five terms into four: a bottom-up QuickTwoSum pass, then a
 // top-down pass that emits a component whenever the QuickTwoSum error is
 // nonzero, folding everything after the third emitted component into the
 // fourth.  k counts emitted components; r_k selects stand in for indexing.
-__device__ __forceinline__ void renorm5(double c0, double c1, double c2, double c3, double c4,
+__device__ __forceinline__ void renorm5(const Rn& f, double c0, double c1, double c2, double c3, double c4,
                                         double& r0, double& r1, double& r2, double& r3)
 {
     double s, t0, t1, t2, t3, t4;
-    quick_two_sum(c3, c4, s, t4);
-    quick_two_sum(c2, s, s, t3);
-    quick_two_sum(c1, s, s, t2);
-    quick_two_sum(c0, s, t0, t1);
+    quick_two_sum(f, c3, c4, s, t4);
+    quick_two_sum(f, c2, s, s, t3);
+    quick_two_sum(f, c1, s, s, t2);
+    quick_two_sum(f, c0, s, t0, t1);
 
     r0 = 0.0; r1 = 0.0; r2 = 0.0; r3 = 0.0;
     int k = 0;
@@ -105,14 +125,14 @@ __device__ __forceinline__ void renorm5(double c0, double c1, double c2, double 
     bool emit;
 
     // term 1 (k == 0 here)
-    quick_two_sum(t0, t1, hi, lo);
+    quick_two_sum(f, t0, t1, hi, lo);
     emit = nonzero(lo);
     r0 = emit ? hi : r0;
     k = emit ? 1 : 0;
     s = emit ? lo : hi;
 
     // term 2 (k <= 1)
-    quick_two_sum(s, t2, hi, lo);
+    quick_two_sum(f, s, t2, hi, lo);
     emit = nonzero(lo);
     r0 = (emit && k == 0) ? hi : r0;
     r1 = (emit && k == 1) ? hi : r1;
@@ -120,7 +140,7 @@ __device__ __forceinline__ void renorm5(double c0, double c1, double c2, double 
     s = emit ? lo : hi;
 
     // term 3 (k <= 2)
-    quick_two_sum(s, t3, hi, lo);
+    quick_two_sum(f, s, t3, hi, lo);
     emit = nonzero(lo);
     r0 = (emit && k == 0) ? hi : r0;
     r1 = (emit && k == 1) ? hi : r1;
@@ -130,7 +150,7 @@ __device__ __forceinline__ void renorm5(double c0, double c1, double c2, double 
 
     // term 4: with three components out, the sum is a plain add, which is
     // exactly the QuickTwoSum's rounded sum
-    quick_two_sum(s, t4, hi, lo);
+    quick_two_sum(f, s, t4, hi, lo);
     emit = nonzero(lo) && k < 3;
     r0 = (emit && k == 0) ? hi : r0;
     r1 = (emit && k == 1) ? hi : r1;
@@ -145,40 +165,40 @@ __device__ __forceinline__ void renorm5(double c0, double c1, double c2, double 
 }
 
 // VecSum of three / four terms: TwoSum chain from the last term up.
-__device__ __forceinline__ void vec_sum3(double x0, double x1, double x2,
+__device__ __forceinline__ void vec_sum3(const Rn& f, double x0, double x1, double x2,
                                          double& e0, double& e1, double& e2)
 {
     double s;
-    two_sum(x1, x2, s, e2);
-    two_sum(x0, s, e0, e1);
+    two_sum(f, x1, x2, s, e2);
+    two_sum(f, x0, s, e0, e1);
 }
 
-__device__ __forceinline__ void vec_sum4(double x0, double x1, double x2, double x3,
+__device__ __forceinline__ void vec_sum4(const Rn& f, double x0, double x1, double x2, double x3,
                                          double& e0, double& e1, double& e2, double& e3)
 {
     double s;
-    two_sum(x2, x3, s, e3);
-    two_sum(x1, s, s, e2);
-    two_sum(x0, s, e0, e1);
+    two_sum(f, x2, x3, s, e3);
+    two_sum(f, x1, s, s, e2);
+    two_sum(f, x0, s, e0, e1);
 }
 
 // VSEB(2) on three terms.  Following the loop: the first QuickTwoSum writes
 // r0 and either moves to r1 (nonzero error) or carries its sum on; the second
 // writes the current slot; after it the loop returns if both slots are done,
 // otherwise a nonzero remainder lands in the current slot.
-__device__ __forceinline__ void vseb2_of3(double e0, double e1, double e2, double& r0, double& r1)
+__device__ __forceinline__ void vseb2_of3(const Rn& f, double e0, double e1, double e2, double& r0, double& r1)
 {
     double h1, l1, h2, l2;
-    quick_two_sum(e0, e1, h1, l1);
+    quick_two_sum(f, e0, e1, h1, l1);
     const bool nz1 = nonzero(l1);
-    quick_two_sum(nz1 ? l1 : h1, e2, h2, l2);
+    quick_two_sum(f, nz1 ? l1 : h1, e2, h2, l2);
     const bool nz2 = nonzero(l2);
     r0 = nz1 ? h1 : h2;
     r1 = nz1 ? h2 : (nz2 ? l2 : 0.0);
 }
 
 // VSEB(3) on six terms (used by the merge-based TDadd).
-__device__ __forceinline__ void vseb3_of6(const double e[6], double& r0, double& r1, double& r2)
+__device__ __forceinline__ void vseb3_of6(const Rn& f, const double e[6], double& r0, double& r1, double& r2)
 {
     r0 = 0.0; r1 = 0.0; r2 = 0.0;
     int j = 0;
@@ -187,7 +207,7 @@ __device__ __forceinline__ void vseb3_of6(const double e[6], double& r0, double&
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
         double hi, lo;
-        quick_two_sum(eps, e[i + 1], hi, lo);
+        quick_two_sum(f, eps, e[i + 1], hi, lo);
         const bool w = !done;
         r0 = (w && j == 0) ? hi : r0;
         r1 = (w && j == 1) ? hi : r1;
@@ -208,85 +228,97 @@ __device__ __forceinline__ void vseb3_of6(const double e[6], double& r0, double&
 // ------------------------------------------------------------- Sec. 2.2
 
 // Alg. 1, DDadd.
-__device__ __forceinline__ void dd_add(const double x[2], const double y[2], double r[2])
+__device__ __forceinline__ void dd_add(const Rn& f, const double x[2], const double y[2], double r[2])
 {
     double s, e;
-    two_sum(x[0], y[0], s, e);
-    const double w = add(x[1], y[1]);
-    e = add(e, w);
-    quick_two_sum(s, e, r[0], r[1]);
+    two_sum(f, x[0], y[0], s, e);
+    const double w = f.add(x[1], y[1]);
+    e = f.add(e, w);
+    quick_two_sum(f, s, e, r[0], r[1]);
 }
 
 // Alg. 2, DDmul.
-__device__ __forceinline__ void dd_mul(const double x[2], const double y[2], double r[2])
+__device__ __forceinline__ void dd_mul(const Rn& f, const double x[2], const double y[2], double r[2])
 {
     double p1, p2;
-    two_prod(x[0], y[0], p1, p2);
-    const double w1 = mul(x[0], y[1]);
-    const double w2 = mul(x[1], y[0]);
-    const double w3 = add(w1, w2);
-    p2 = add(p2, w3);
-    quick_two_sum(p1, p2, r[0], r[1]);
+    two_prod(f, x[0], y[0], p1, p2);
+    const double w1 = f.mul(x[0], y[1]);
+    const double w2 = f.mul(x[1], y[0]);
+    const double w3 = f.add(w1, w2);
+    p2 = f.add(p2, w3);
+    quick_two_sum(f, p1, p2, r[0], r[1]);
 }
 
 // ------------------------------------------------------------- Sec. 2.3
 
 // Alg. 4, TDmul (the "fast" triple-word product).
-__device__ __forceinline__ void td_mul(const double x[3], const double y[3], double r[3])
+__device__ __forceinline__ void td_mul(const Rn& f, const double x[3], const double y[3], double r[3])
 {
     double z00up, z00lo, z01up, z01lo, z10up, z10lo;
-    two_prod(x[0], y[0], z00up, z00lo);
-    two_prod(x[0], y[1], z01up, z01lo);
-    two_prod(x[1], y[0], z10up, z10lo);
+    two_prod(f, x[0], y[0], z00up, z00lo);
+    two_prod(f, x[0], y[1], z01up, z01lo);
+    two_prod(f, x[1], y[0], z10up, z10lo);
     double b0, b1, b2;
-    vec_sum3(z00lo, z01up, z10up, b0, b1, b2);
-    const double c = fma(x[1], y[1], b2);
-    const double z31 = fma(x[0], y[2], z10lo);
-    const double z32 = fma(x[2], y[0], z01lo);
-    const double z3 = add(z31, z32);
-    const double s3 = add(c, z3);
+    vec_sum3(f, z00lo, z01up, z10up, b0, b1, b2);
+    const double c = f.fma(x[1], y[1], b2);
+    const double z31 = f.fma(x[0], y[2], z10lo);
+    const double z32 = f.fma(x[2], y[0], z01lo);
+    const double z3 = f.add(z31, z32);
+    const double s3 = f.add(c, z3);
     double e0, e1, e2, e3;
-    vec_sum4(z00up, b0, b1, s3, e0, e1, e2, e3);
+    vec_sum4(f, z00up, b0, b1, s3, e0, e1, e2, e3);
     r[0] = e0;
-    vseb2_of3(e1, e2, e3, r[1], r[2]);
+    vseb2_of3(f, e1, e2, e3, r[1], r[2]);
 }
 
 // ------------------------------------------------------------- Sec. 2.4
 
 // Alg. 5, QDadd (sloppy); t3 is the error of the fourth componentwise sum.
-__device__ __forceinline__ void qd_add(const double x[4], const double y[4], double r[4])
+// With ZERO4 the fourth components of both operands are +0 (TDaddq): then
+// s3, v3, u3, w3 and t3 are all exactly +0 in round-to-nearest, and those six
+// operations are replaced by the constant.
+template <bool ZERO4>
+__device__ __forceinline__ void qd_add_impl(const Rn& f, const double x[4], const double y[4], double r[4])
 {
-    double s0 = add(x[0], y[0]);
-    double s1 = add(x[1], y[1]);
-    double s2 = add(x[2], y[2]);
-    double s3 = add(x[3], y[3]);
-    const double v0 = sub(s0, x[0]);
-    const double v1 = sub(s1, x[1]);
-    const double v2 = sub(s2, x[2]);
-    const double v3 = sub(s3, x[3]);
-    const double w0 = sub(x[0], sub(s0, v0));
-    const double w1 = sub(x[1], sub(s1, v1));
-    const double w2 = sub(x[2], sub(s2, v2));
-    const double w3 = sub(x[3], sub(s3, v3));
-    double t0 = add(w0, sub(y[0], v0));
-    double t1 = add(w1, sub(y[1], v1));
-    double t2 = add(w2, sub(y[2], v2));
-    const double t3 = add(w3, sub(y[3], v3));
-    two_sum(s1, t0, s1, t0);
-    three_sum(s2, t0, t1);
-    three_sum2(s3, t0, t2);
-    t0 = add(add(t0, t1), t3);
-    renorm5(s0, s1, s2, s3, t0, r[0], r[1], r[2], r[3]);
+    double s0 = f.add(x[0], y[0]);
+    double s1 = f.add(x[1], y[1]);
+    double s2 = f.add(x[2], y[2]);
+    double s3 = ZERO4 ? 0.0 : f.add(x[3], y[3]);
+    const double v0 = f.sub(s0, x[0]);
+    const double v1 = f.sub(s1, x[1]);
+    const double v2 = f.sub(s2, x[2]);
+    const double w0 = f.sub(x[0], f.sub(s0, v0));
+    const double w1 = f.sub(x[1], f.sub(s1, v1));
+    const double w2 = f.sub(x[2], f.sub(s2, v2));
+    double t0 = f.add(w0, f.sub(y[0], v0));
+    double t1 = f.add(w1, f.sub(y[1], v1));
+    double t2 = f.add(w2, f.sub(y[2], v2));
+    double t3 = 0.0;
+    if (!ZERO4) {
+        const double v3 = f.sub(s3, x[3]);
+        const double w3 = f.sub(x[3], f.sub(s3, v3));
+        t3 = f.add(w3, f.sub(y[3], v3));
+    }
+    two_sum(f, s1, t0, s1, t0);
+    three_sum(f, s2, t0, t1);
+    three_sum2(f, s3, t0, t2);
+    t0 = f.add(f.add(t0, t1), t3);
+    renorm5(f, s0, s1, s2, s3, t0, r[0], r[1], r[2], r[3]);
+}
+
+__device__ __forceinline__ void qd_add(const Rn& f, const double x[4], const double y[4], double r[4])
+{
+    qd_add_impl<false>(f, x, y, r);
 }
 
 // TDaddq (Sec. 2.3): QDadd on operands padded with a zero fourth component,
 // the fourth result component dropped.
-__device__ __forceinline__ void td_addq(const double x[3], const double y[3], double r[3])
+__device__ __forceinline__ void td_addq(const Rn& f, const double x[3], const double y[3], double r[3])
 {
     const double x4[4] = {x[0], x[1], x[2], 0.0};
     const double y4[4] = {y[0], y[1], y[2], 0.0};
     double r4[4];
-    qd_add(x4, y4, r4);
+    qd_add_impl<true>(f, x4, y4, r4);
     r[0] = r4[0];
     r[1] = r4[1];
     r[2] = r4[2];
@@ -294,7 +326,7 @@ __device__ __forceinline__ void td_addq(const double x[3], const double y[3], do
 
 // Alg. 3, TDadd: Merge (by decreasing magnitude, x first on ties), VecSum,
 // VSEB(3).
-__device__ __forceinline__ void td_add_merge(const double x[3], const double y[3], double r[3])
+__device__ __forceinline__ void td_add_merge(const Rn& f, const double x[3], const double y[3], double r[3])
 {
     double z[6];
     int i = 0, j = 0;
@@ -311,64 +343,64 @@ __device__ __forceinline__ void td_add_merge(const double x[3], const double y[3
     double s = z[5];
 #pragma unroll
     for (int t = 4; t >= 0; --t)
-        two_sum(z[t], s, s, e[t + 1]);
+        two_sum(f, z[t], s, s, e[t + 1]);
     e[0] = s;
-    vseb3_of6(e, r[0], r[1], r[2]);
+    vseb3_of6(f, e, r[0], r[1], r[2]);
 }
 
 // Alg. 6, QDmul (sloppy).  The listing's first line is dead and omitted.
-__device__ __forceinline__ void qd_mul(const double x[4], const double y[4], double r[4])
+__device__ __forceinline__ void qd_mul(const Rn& f, const double x[4], const double y[4], double r[4])
 {
     double p0, p1, p2, p3, p4, p5, q0, q1, q2, q3, q4, q5;
-    two_prod(x[0], y[0], p0, q0);
-    two_prod(x[0], y[1], p1, q1);
-    two_prod(x[1], y[0], p2, q2);
-    two_prod(x[0], y[2], p3, q3);
-    two_prod(x[1], y[1], p4, q4);
-    two_prod(x[2], y[0], p5, q5);
-    three_sum(p1, p2, q0);
-    three_sum(p2, q1, q2);
-    three_sum(p3, p4, p5);
+    two_prod(f, x[0], y[0], p0, q0);
+    two_prod(f, x[0], y[1], p1, q1);
+    two_prod(f, x[1], y[0], p2, q2);
+    two_prod(f, x[0], y[2], p3, q3);
+    two_prod(f, x[1], y[1], p4, q4);
+    two_prod(f, x[2], y[0], p5, q5);
+    three_sum(f, p1, p2, q0);
+    three_sum(f, p2, q1, q2);
+    three_sum(f, p3, p4, p5);
     double s0, s1, s2, t0, t1;
-    two_sum(p2, p3, s0, t0);
-    two_sum(q1, p4, s1, t1);
-    s2 = add(q2, p5);
-    two_sum(s1, t0, s1, t0);
-    s2 = add(s2, add(t0, t1));
-    s1 = add(s1, mul(x[0], y[3]));
-    s1 = add(s1, mul(x[1], y[2]));
-    s1 = add(s1, mul(x[2], y[1]));
-    s1 = add(s1, mul(x[3], y[0]));
-    s1 = add(s1, q0);
-    s1 = add(s1, q3);
-    s1 = add(s1, q4);
-    s1 = add(s1, q5);
-    renorm5(p0, p1, s0, s1, s2, r[0], r[1], r[2], r[3]);
+    two_sum(f, p2, p3, s0, t0);
+    two_sum(f, q1, p4, s1, t1);
+    s2 = f.add(q2, p5);
+    two_sum(f, s1, t0, s1, t0);
+    s2 = f.add(s2, f.add(t0, t1));
+    s1 = f.add(s1, f.mul(x[0], y[3]));
+    s1 = f.add(s1, f.mul(x[1], y[2]));
+    s1 = f.add(s1, f.mul(x[2], y[1]));
+    s1 = f.add(s1, f.mul(x[3], y[0]));
+    s1 = f.add(s1, q0);
+    s1 = f.add(s1, q3);
+    s1 = f.add(s1, q4);
+    s1 = f.add(s1, q5);
+    renorm5(f, p0, p1, s0, s1, s2, r[0], r[1], r[2], r[3]);
 }
 
 // ------------------------------------------------ generic by component count
 
 template <int P> struct Ops;
 template <> struct Ops<2> {
-    static __device__ __forceinline__ void mul(const double* x, const double* y, double* r) { dd_mul(x, y, r); }
-    static __device__ __forceinline__ void add(const double* x, const double* y, double* r) { dd_add(x, y, r); }
+    static __device__ __forceinline__ void mul(const Rn& f, const double* x, const double* y, double* r) { dd_mul(f, x, y, r); }
+    static __device__ __forceinline__ void add(const Rn& f, const double* x, const double* y, double* r) { dd_add(f, x, y, r); }
 };
 template <> struct Ops<3> {
-    static __device__ __forceinline__ void mul(const double* x, const double* y, double* r) { td_mul(x, y, r); }
-    static __device__ __forceinline__ void add(const double* x, const double* y, double* r) { td_addq(x, y, r); }
+    static __device__ __forceinline__ void mul(const Rn& f, const double* x, const double* y, double* r) { td_mul(f, x, y, r); }
+    static __device__ __forceinline__ void add(const Rn& f, const double* x, const double* y, double* r) { td_addq(f, x, y, r); }
 };
 template <> struct Ops<4> {
-    static __device__ __forceinline__ void mul(const double* x, const double* y, double* r) { qd_mul(x, y, r); }
-    static __device__ __forceinline__ void add(const double* x, const double* y, double* r) { qd_add(x, y, r); }
+    static __device__ __forceinline__ void mul(const Rn& f, const double* x, const double* y, double* r) { qd_mul(f, x, y, r); }
+    static __device__ __forceinline__ void add(const Rn& f, const double* x, const double* y, double* r) { qd_add(f, x, y, r); }
 };
 
 // acc = add(acc, mul(a, b)): one multiply-add of the GEMM, a from A, b from B.
 template <int P>
-__device__ __forceinline__ void mad(double* acc, const double* a, const double* b)
+__device__ __forceinline__ void mad(const Rn& f, double* acc, const double* a, const double* b)
 {
     double prod[P], sum[P];
-    Ops<P>::mul(a, b, prod);
-    Ops<P>::add(acc, prod, sum);
+    Ops<P>::mul(f, a, b, prod);
+    Ops<P>::add(f, acc, prod, sum);
 #pragma unroll
     for (int c = 0; c < P; ++c) acc[c] = sum[c];
 }
