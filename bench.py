@@ -344,6 +344,18 @@ def extras(torch, mm, I):
     C = torch.empty((P, n, n), dtype=torch.float64, device="cuda")
     ms = _time_call(torch, lambda: mm.gemm_plain("dd", Ad, Bd, out=C), reps=1)
     out["dd_4096_fp64_eft"] = {"mad_s": n ** 3 / (ms * 1e-3), "ms": ms}
+    # the same product through the INT8 error-free slicing form
+    for S in (13, 14):
+        ws = torch.empty(mm.workspace_size("dd", n, n, n, algo="int8", slices=S),
+                         dtype=torch.uint8, device="cuda")
+        C8 = torch.empty_like(C)
+        ms8 = _time_call(torch, lambda: mm.gemm("dd", Ad, Bd, out=C8, algo="int8", slices=S,
+                                                workspace=ws), reps=3)
+        pairs = S * (S + 1) // 2
+        out["dd_4096_int8_s%d" % S] = {
+            "mad_s": n ** 3 / (ms8 * 1e-3), "ms": ms8, "speedup_vs_fp64_eft": ms / ms8,
+            "int8_tops": 2.0 * pairs * n ** 3 / (ms8 * 1e-3) / 1e12}
+        del ws
     return out
 
 

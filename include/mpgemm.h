@@ -148,6 +148,24 @@ int mpgemm_ex(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k,
               const double *const *B, int64_t ldb,
               double *const *C, int64_t ldc);
 
+/* MPG_ALGO_INT8_OZAKI (DD only; not in the paper).  C := op(A) op(B) via an
+ * error-free splitting whose products run on the tensor cores:
+ *   sigma_i = ilogb(max_p |a_ip[0]|) + 2 per row of op(A) (0 for a zero row),
+ *   tau_j likewise per column of op(B); S = opts->slices (default 14, 1..16)
+ *   balanced base-2^7 digits of a 2^-sigma, each the nearest integer (ties to
+ *   even) of the exact scaled remainder; for w = S+1 down to 2 the int32 sum
+ *   P_w of the slice products with s + t = w (exact: requires
+ *   S * k * 4096 < 2^31, else MPG_EUNSUPPORTED); acc = DDadd(acc,
+ *   (P_w 2^(sigma_i + tau_j - 7w), 0)) (Alg. 1) from acc = 0.
+ * The result is deterministic and bit-identical to those steps evaluated
+ * anywhere; its error against the exact product shrinks by ~2^-7 per slice.
+ * Needs opts->workspace: 256-byte aligned, mpgemm_workspace_size() bytes, not
+ * overlapping A, B or C.  Layout (mp, np, kp = m, n, k rounded up to 64,
+ * padding zero; each region starts on a 256-byte boundary):
+ *   int8  [S][mp][kp]  slices of op(A);   int8 [S][np][kp] slices of op(B)^T;
+ *   int32 [mp] sigma;                     int32 [np] tau.
+ * The workspace holds these values after the call. */
+
 /* Bytes of workspace mpgemm_ex needs for these options and sizes (0 if none). */
 size_t mpgemm_workspace_size(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k);
 

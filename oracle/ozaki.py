@@ -1,0 +1,126 @@
+"""Oracle for the INT8 error-free slicing form of the DD GEMM -- TEST
+INFRASTRUCTURE ONLY (tests, smoke check and the benchmark's CPU leg).
+
+The paper's DD GEMM (Sec. 3, Eq. 1) computed through an Ozaki-style
+error-free splitting; every step is the plain definition, in Python
+integers, so a reader can check it line by line:
+
+  scale    sigma_i = ilogb(max_p |hi(a_ip)|) + 2 for row i of A (0 for an
+           all-zero row); tau_j likewise for column j of B.  Then
+           |a_ip| 2^-sigma_i < 1/2.
+  slices   x_0 = a 2^-sigma exactly; for s = 1..S: y = 2^7 x_{s-1},
+           d_s = nearest integer to y (ties to even), x_s = y - d_s.
+           Every |d_s| <= 64.  a = 2^sigma (sum_s d_s 2^-7s + 2^-7S x_S).
+  products P_w = sum over s + t = w (1 <= s, t <= S) of A^(s) B^(t), for
+           w = 2..S+1, computed exactly in integers.
+  accumulate  acc = (0, 0); for w = S+1 down to 2:
+           acc = DDadd(acc, (P_w[i,j] 2^(sigma_i + tau_j - 7w), 0))
+           with the oracle's DDadd (Alg. 1).  The scaled value is an exact
+           binary64 for the sizes this form accepts.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+
+from . import op as _op
+
+BASE_BITS = 7
+
+
+def _exact_int(x):
+    """(M, E) with x == M * 2**E exactly, M an int."""
+    if x == 0.0:
+        return 0, 0
+    f, e = math.frexp(x)
+    return int(f * (1 << 53)), e - 53
+
+
+def ilogb(x):
+    return math.frexp(abs(x))[1] - 1
+
+
+def scale_exponent(hi_values):
+    """sigma for a row (or column) given its leading components."""
+    mx = max((abs(float(v)) for v in hi_values), default=0.0)
+    return 0 if mx == 0.0 else ilogb(mx) + 2
+
+
+def digits(components, sigma, S):
+    """The S balanced base-2^7 digits of (sum of components) * 2^-sigma and
+    the exact remainder x_S (a Fraction)."""
+    x = sum((Fraction(float(c)) for c in components), Fraction(0)) * Fraction(2) ** (-sigma)
+    out = []
+    for _ in range(S):
+        y = x * (1 << BASE_BITS)
+        d = round(y)              # Fraction.__round__: nearest, ties to even
+        out.append(int(d))
+        x = y - d
+    return out, x
+
+
+def slice_rows(planes, S, rows=None):
+    """planes (P, m, k).  Returns sigma (list per row) and D with
+    D[s-1][r][p] the s-th digit of element (rows[r], p)."""
+    planes = np.asarray(planes)
+    rows = range(planes.shape[1]) if rows is None else rows
+    sig, D = [], np.zeros((S, len(rows), planes.shape[2]), dtype=np.int64)
+    for r, i in enumerate(rows):
+        sg = scale_exponent(planes[0, i, :])
+        sig.append(sg)
+        for p in range(planes.shape[2]):
+            ds, _ = digits(planes[:, i, p], sg, S)
+            D[:, r, p] = ds
+    return sig, D
+
+
+def slice_cols(planes, S, cols=None):
+    """planes (P, k, n): slices of the columns of B (as rows of B^T)."""
+    planes = np.asarray(planes)
+    return slice_rows(np.ascontiguousarray(planes.transpose(0, 2, 1)), S, cols)
+
+
+def weight_products(DA, DB, S):
+    """P_w for w = 2..S+1: dict w -> integer matrix (rows of DA x rows of DB)."""
+    out = {}
+    for w in range(2, S + 2):
+        acc = np.zeros((DA.shape[1], DB.shape[1]), dtype=object)
+        for s in range(max(1, w - S), min(S, w - 1) + 1):
+            t = w - s
+            acc = acc + DA[s - 1].astype(object).dot(DB[t - 1].astype(object).T)
+        out[w] = acc
+    return out
+
+
+def gemm(A, B, S, rows=None, cols=None, L=None):
+    """DD C = A B through S-slice error-free splitting, for the selected rows
+    of A and columns of B (all by default).  A (2, m, k), B (2, k, n).
+    Returns C (2, len(rows), len(cols)), sigma, tau."""
+    A = np.asarray(A)
+    B = np.asarray(B)
+    rows = list(range(A.shape[1])) if rows is None else list(rows)
+    cols = list(range(B.shape[2])) if cols is None else list(cols)
+    sig, DA = slice_rows(A, S, rows)
+    tau, DB = slice_cols(B, S, cols)
+    Pw = weight_products(DA, DB, S)
+    C = np.zeros((2, len(rows), len(cols)))
+    for r in range(len(rows)):
+        for c in range(len(cols)):
+            acc = (0.0, 0.0)
+            for w in range(S + 1, 1, -1):
+                v = math.ldexp(float(int(Pw[w][r, c])), sig[r] + tau[c] - BASE_BITS * w)
+                assert Fraction(v) == Fraction(int(Pw[w][r, c])) * Fraction(2) ** (
+                    sig[r] + tau[c] - BASE_BITS * w), "scaled product not exact"
+                acc = _op("dd", "add", acc, (v, 0.0), L)
+            C[:, r, c] = acc
+    return C, sig, tau
+
+
+def max_pairs(S):
+    return S
+
+
+def k_limit(S):
+    """Largest k for which every weight's INT32 sum is exact:
+    pairs * k * 64 * 64 < 2^31."""
+    return (2 ** 31 - 1) // (max_pairs(S) * 64 * 64)

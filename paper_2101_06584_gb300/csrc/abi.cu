@@ -3,6 +3,7 @@
 // kernels on the calling thread's stream, and error reporting.
 #include "mpgemm.h"
 #include "internal.h"
+#include "ozaki.h"
 
 #include <cstdarg>
 #include <cstdio>
@@ -159,6 +160,43 @@ int check_gemm(const GemmArgs<P>& g)
 }
 
 template <int P>
+static int ozaki_call(const GemmArgs<P>&, const mpgemm_opts*)
+{
+    return fail(MPG_EUNSUPPORTED, "the INT8 slicing form is provided for DD (P = 2) only");
+}
+
+template <>
+int ozaki_call<2>(const GemmArgs<2>& g, const mpgemm_opts* o)
+{
+    const int S = o->slices ? o->slices : kOzakiDefaultSlices;
+    if (S < 1 || S > kOzakiMaxSlices)
+        return fail(MPG_EINVAL, "slices must be in 1..%d (got %d)", kOzakiMaxSlices, S);
+    if (g.k > ozaki_k_limit(S))
+        return fail(MPG_EUNSUPPORTED, "k = %lld exceeds %lld, the largest k whose %d-slice int32 "
+                    "sums are exact", (long long)g.k, (long long)ozaki_k_limit(S), S);
+    const OzakiLayout L = ozaki_layout(S, g.m, g.n, g.k);
+    if (L.mp / 64 > 65535) return fail(MPG_EINVAL, "m too large for the INT8 form's grid");
+    if (!o->workspace) return fail(MPG_EWORKSPACE, "the INT8 form needs a workspace of %lld bytes",
+                                   (long long)L.total);
+    if (reinterpret_cast<uintptr_t>(o->workspace) % 256)
+        return fail(MPG_EWORKSPACE, "workspace must be 256-byte aligned");
+    if (o->workspace_bytes < static_cast<size_t>(L.total))
+        return fail(MPG_EWORKSPACE, "workspace of %zu bytes is smaller than the %lld needed",
+                    o->workspace_bytes, (long long)L.total);
+    const Range rw{reinterpret_cast<uintptr_t>(o->workspace),
+                   reinterpret_cast<uintptr_t>(o->workspace) + static_cast<uintptr_t>(L.total)};
+    const int64_t ar = g.trans_a ? g.k : g.m, ac = g.trans_a ? g.m : g.k;
+    const int64_t br = g.trans_b ? g.n : g.k, bc = g.trans_b ? g.k : g.n;
+    for (int c = 0; c < 2; ++c) {
+        if (overlap(rw, plane_range(g.A[c], ar, ac, g.lda)) || overlap(rw, plane_range(g.B[c], br, bc, g.ldb)) ||
+            overlap(rw, plane_range(g.C[c], g.m, g.n, g.ldc)))
+            return fail(MPG_EWORKSPACE, "workspace overlaps an operand");
+    }
+    cudaError_t e = launch_ozaki_dd(g, S, o->workspace, g_stream);
+    return e == cudaSuccess ? MPG_OK : cuda_fail(e, "INT8 slicing gemm launch");
+}
+
+template <int P>
 static int gemm_call(const mpgemm_opts* o, int64_t m, int64_t n, int64_t k,
                      const double* const* A, int64_t lda, const double* const* B, int64_t ldb,
                      double* const* C, int64_t ldc)
@@ -178,13 +216,16 @@ static int gemm_call(const mpgemm_opts* o, int64_t m, int64_t n, int64_t k,
     if (rc != MPG_OK) return rc;
     if (m == 0 || n == 0) return MPG_OK;
     const int algo = o ? o->algo : MPG_ALGO_AUTO;
-    if (algo != MPG_ALGO_AUTO && algo != MPG_ALGO_FP64_EFT)
-        return fail(MPG_EUNSUPPORTED, "algorithm %d is not available for P = %d here", algo, P);
+    if (algo != MPG_ALGO_AUTO && algo != MPG_ALGO_FP64_EFT && algo != MPG_ALGO_INT8_OZAKI)
+        return fail(MPG_EINVAL, "unknown algorithm %d", algo);
+    if (algo == MPG_ALGO_INT8_OZAKI && P != 2)
+        return fail(MPG_EUNSUPPORTED, "the INT8 slicing form is provided for DD (P = 2) only");
     cudaError_t e;
     if (k == 0) {
         e = launch_zero<P>(g, g_stream);
         return e == cudaSuccess ? MPG_OK : cuda_fail(e, "zero launch");
     }
+    if (algo == MPG_ALGO_INT8_OZAKI) return ozaki_call(g, o);
     const int split = o ? o->split_k : 0;
     if (split > 1) {
         if (split != 2 && split != 4 && split != 8 && split != 16 && split != 32)
@@ -268,8 +309,10 @@ int mpgemm_ex(int P, const mpgemm_opts* opts, int64_t m, int64_t n, int64_t k,
 
 size_t mpgemm_workspace_size(int P, const mpgemm_opts* opts, int64_t m, int64_t n, int64_t k)
 {
-    (void)P; (void)opts; (void)m; (void)n; (void)k;
-    return 0;
+    if (!opts || opts->algo != MPG_ALGO_INT8_OZAKI || P != 2 || m < 0 || n < 0 || k < 0) return 0;
+    const int S = opts->slices ? opts->slices : kOzakiDefaultSlices;
+    if (S < 1 || S > kOzakiMaxSlices) return 0;
+    return static_cast<size_t>(ozaki_layout(S, m, n, k).total);
 }
 
 int mpgemm_num_tiles(int P)

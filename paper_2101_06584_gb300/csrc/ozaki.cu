@@ -1,0 +1,498 @@
+// ozaki.cu -- the INT8 error-free slicing form of the DD GEMM, C := op(A) op(B).
+//
+// Not in the paper: the product of Sec. 3 (Eq. 1) in DD computed with an
+// Ozaki-style error-free splitting so that the multiplications run on the
+// tensor cores, with binary64 kept to the slicing and to the error-free
+// accumulation of the slice products into DD.
+//
+//   scale   sigma_i = ilogb(max_p |hi(a_ip)|) + 2 for row i of op(A), tau_j for
+//           column j of op(B) (0 for an all-zero vector): |a| 2^-sigma < 1/2.
+//   slice   x_0 = a 2^-sigma; for s = 1..S: y = 2^7 x_{s-1}, d_s = nearest
+//           integer to y (ties to even), x_s = y - d_s.  |d_s| <= 64, so the
+//           digits are int8.  Computed exactly in 128-bit fixed point.
+//   product for w = S+1 down to 2: P_w = sum over s + t = w of A^(s) B^(t),
+//           int8 x int8 -> int32 on the tensor cores (mma.sync m16n8k32 s8;
+//           GB300's tcgen05 has no int8 kind).  Exact while
+//           S * k * 64 * 64 < 2^31.
+//   accumulate  acc = DDadd(acc, (P_w 2^(sigma_i + tau_j - 7w), 0)) (Alg. 1),
+//           the int32 turned into that exact binary64 with integer operations.
+//
+// Workspace (caller-provided, 256-byte aligned), with mp, np, kp the sizes
+// rounded up to 64 and the padding zero:
+//   [S][mp][kp] int8 slices of op(A), row-major;
+//   [S][np][kp] int8 slices of op(B)^T (column j of op(B) as a row);
+//   [mp] int32 sigma; [np] int32 tau.
+#include "mp_arith.cuh"
+#include "ozaki.h"
+
+#include <cstdint>
+
+namespace mpg {
+
+namespace {
+
+constexpr int TILE = 64;         // CTA tile of C and k-step, in elements / bytes
+constexpr int SROW = TILE + 16;  // smem row stride in bytes (bank-conflict-free fragments)
+constexpr int STAGES = 3;
+
+__device__ __forceinline__ uint64_t abs_bits(double x)
+{
+    return static_cast<uint64_t>(__double_as_longlong(x)) & 0x7fffffffffffffffull;
+}
+
+// ilogb of a positive finite binary64 given by its magnitude bits.
+__device__ __forceinline__ int ilogb_bits(uint64_t b)
+{
+    const int E = static_cast<int>(b >> 52);
+    if (E) return E - 1023;
+    const uint64_t frac = b & ((1ull << 52) - 1);
+    return (63 - __clzll(static_cast<long long>(frac))) - 1074;
+}
+
+// Signed integer mantissa and exponent: x = M * 2^e (M = 0 for +-0).
+__device__ __forceinline__ void decompose(double x, int64_t& M, int& e)
+{
+    const uint64_t b = static_cast<uint64_t>(__double_as_longlong(x));
+    const int E = static_cast<int>((b >> 52) & 0x7ff);
+    const uint64_t frac = b & ((1ull << 52) - 1);
+    int64_t m;
+    if (E == 0) { m = static_cast<int64_t>(frac); e = -1074; }
+    else        { m = static_cast<int64_t>(frac | (1ull << 52)); e = E - 1075; }
+    M = (b >> 63) ? -m : m;
+}
+
+// floor(W * 2^sh) and whether bits were dropped, for sh < 0.
+__device__ __forceinline__ __int128 floor_shift(__int128 W, int sh, bool& frac)
+{
+    if (sh >= 0) { frac = false; return W << sh; }
+    if (sh <= -127) { frac = (W != 0); return W < 0 ? -1 : 0; }
+    const int r = -sh;
+    const __int128 mask = (static_cast<__int128>(1) << r) - 1;
+    frac = (W & mask) != 0;
+    return W >> r;   // arithmetic shift: floor
+}
+
+// X = floor((hi + lo) 2^(F - sigma)) exactly, sticky = whether X is inexact.
+__device__ __forceinline__ __int128 fixed_point(double hi, double lo, int sigma, int F, bool& sticky)
+{
+    int64_t Mh, Ml;
+    int eh, el;
+    decompose(hi, Mh, eh);
+    decompose(lo, Ml, el);
+    if (Mh == 0 && Ml != 0) { Mh = Ml; eh = el; Ml = 0; }
+    int sh = eh - sigma + F, sl = el - sigma + F;
+    if (Ml != 0 && sl > sh) {        // unnormalised input: larger exponent first
+        const int64_t tm = Mh; Mh = Ml; Ml = tm;
+        const int ts = sh; sh = sl; sl = ts;
+    }
+    if (Mh == 0) { sticky = false; return 0; }
+    if (Ml == 0) return floor_shift(Mh, sh, sticky);
+    if (sh >= 0) {
+        bool f;
+        const __int128 lowp = floor_shift(Ml, sl, f);
+        sticky = f;
+        return (static_cast<__int128>(Mh) << sh) + lowp;
+    }
+    const int d = sh - sl;            // > 0 here: lo below hi
+    if (d <= 74) {
+        const __int128 W = (static_cast<__int128>(Mh) << d) + Ml;
+        return floor_shift(W, sl, sticky);
+    }
+    // lo lies more than 74 bits below hi's last bit: it only decides the
+    // floor when hi is itself an integer in these units
+    bool fh;
+    __int128 X = floor_shift(Mh, sh, fh);
+    if (!fh && Ml < 0) X -= 1;
+    sticky = true;
+    return X;
+}
+
+}  // namespace
+
+// The S digits of (hi + lo) 2^-sigma (nearest, ties to even).
+__device__ __forceinline__ void ozaki_digits(double hi, double lo, int sigma, int S, int8_t* out)
+{
+    const int F = 7 * S + 12;
+    bool sticky;
+    __int128 R = fixed_point(hi, lo, sigma, F, sticky);
+    for (int s = 1; s <= S; ++s) {
+        const int q = F - 7 * s;
+        const __int128 U = static_cast<__int128>(1) << q;
+        const __int128 half = U >> 1;
+        __int128 dd = (R + half) >> q;                       // nearest, ties up
+        if (!sticky && (R & (U - 1)) == half && (dd & 1)) dd -= 1;   // ties to even
+        R -= dd << q;
+        out[s - 1] = static_cast<int8_t>(static_cast<int>(dd));
+    }
+}
+
+// ------------------------------------------------------------------ scale
+
+// One warp per vector whose elements are contiguous (stride 1, vectors ld apart).
+__global__ void ozaki_scale_contig(const double* __restrict__ hi, int64_t count, int64_t len,
+                                   int64_t ld, int* __restrict__ out)
+{
+    const int64_t v = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (v >= count) return;
+    uint64_t mx = 0;
+    for (int64_t p = lane; p < len; p += 32) {
+        const uint64_t b = abs_bits(hi[v * ld + p]);
+        mx = b > mx ? b : mx;
+    }
+    for (int off = 16; off; off >>= 1) {
+        const uint64_t o = __shfl_xor_sync(0xffffffffu, mx, off);
+        mx = o > mx ? o : mx;
+    }
+    if (lane == 0) out[v] = mx ? ilogb_bits(mx) + 2 : 0;
+}
+
+// One thread per vector whose elements are ld apart (vectors adjacent).
+__global__ void ozaki_scale_strided(const double* __restrict__ hi, int64_t count, int64_t len,
+                                    int64_t ld, int* __restrict__ out)
+{
+    const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (v >= count) return;
+    uint64_t mx = 0;
+    for (int64_t p = 0; p < len; ++p) {
+        const uint64_t b = abs_bits(hi[p * ld + v]);
+        mx = b > mx ? b : mx;
+    }
+    out[v] = mx ? ilogb_bits(mx) + 2 : 0;
+}
+
+// Zero the exponent padding [count, padded).
+__global__ void ozaki_fill_int(int* out, int64_t from, int64_t to)
+{
+    const int64_t i = from + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < to) out[i] = 0;
+}
+
+// ------------------------------------------------------------------ slice
+
+// Rows of the sliced operand are contiguous in memory (element (r, p) at
+// base[r*ld + p]).  One thread per 4 consecutive p; rows up to `rows_pad`,
+// columns up to kp, zero outside [rows) x [len).
+__global__ void ozaki_slice_rows(const double* __restrict__ hi, const double* __restrict__ lo,
+                                 int64_t rows, int64_t len, int64_t ld, const int* __restrict__ sig,
+                                 int S, int64_t rows_pad, int64_t kp, int8_t* __restrict__ out)
+{
+    const int64_t quads = kp / 4;
+    const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= rows_pad * quads) return;
+    const int64_t r = t / quads;
+    const int64_t p0 = (t % quads) * 4;
+    int8_t dg[4][16];
+    const int sg = r < rows ? sig[r] : 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int64_t p = p0 + u;
+        if (r < rows && p < len) {
+            ozaki_digits(hi[r * ld + p], lo[r * ld + p], sg, S, dg[u]);
+        } else {
+            for (int s = 0; s < S; ++s) dg[u][s] = 0;
+        }
+    }
+    for (int s = 0; s < S; ++s) {
+        const uint32_t w = static_cast<uint32_t>(static_cast<uint8_t>(dg[0][s])) |
+                           (static_cast<uint32_t>(static_cast<uint8_t>(dg[1][s])) << 8) |
+                           (static_cast<uint32_t>(static_cast<uint8_t>(dg[2][s])) << 16) |
+                           (static_cast<uint32_t>(static_cast<uint8_t>(dg[3][s])) << 24);
+        *reinterpret_cast<uint32_t*>(out + (static_cast<int64_t>(s) * rows_pad + r) * kp + p0) = w;
+    }
+}
+
+// Rows of the sliced operand are strided (element (r, p) at base[p*ld + r]):
+// a 32 x 32 tile is read with r fastest, sliced, transposed through shared
+// memory and written with p fastest.
+__global__ void __launch_bounds__(256)
+ozaki_slice_cols(const double* __restrict__ hi, const double* __restrict__ lo, int64_t rows,
+                 int64_t len, int64_t ld, const int* __restrict__ sig, int S, int64_t rows_pad,
+                 int64_t kp, int8_t* __restrict__ out)
+{
+    __shared__ int8_t tile[16][32][36];
+    const int64_t r0 = static_cast<int64_t>(blockIdx.x) * 32;
+    const int64_t p0 = static_cast<int64_t>(blockIdx.y) * 32;
+    const int tr = threadIdx.x & 31;        // r within the tile
+    const int tp = threadIdx.x >> 5;        // 0..7
+    const int64_t r = r0 + tr;
+    const int sg = r < rows ? sig[r] : 0;
+    for (int pp = tp; pp < 32; pp += 8) {
+        const int64_t p = p0 + pp;
+        int8_t dg[16];
+        if (r < rows && p < len) {
+            ozaki_digits(hi[p * ld + r], lo[p * ld + r], sg, S, dg);
+        } else {
+            for (int s = 0; s < S; ++s) dg[s] = 0;
+        }
+        for (int s = 0; s < S; ++s) tile[s][tr][pp] = dg[s];
+    }
+    __syncthreads();
+    // write: each thread writes 4 consecutive p of one row r
+    const int wr = threadIdx.x >> 3;        // 0..31 row within tile
+    const int wq = (threadIdx.x & 7) * 4;   // p offset
+    const int64_t row = r0 + wr;
+    if (row < rows_pad && p0 + wq < kp) {
+        for (int s = 0; s < S; ++s) {
+            const uint32_t w = static_cast<uint32_t>(static_cast<uint8_t>(tile[s][wr][wq])) |
+                               (static_cast<uint32_t>(static_cast<uint8_t>(tile[s][wr][wq + 1])) << 8) |
+                               (static_cast<uint32_t>(static_cast<uint8_t>(tile[s][wr][wq + 2])) << 16) |
+                               (static_cast<uint32_t>(static_cast<uint8_t>(tile[s][wr][wq + 3])) << 24);
+            *reinterpret_cast<uint32_t*>(out + (static_cast<int64_t>(s) * rows_pad + row) * kp +
+                                         p0 + wq) = w;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ product
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__device__ __forceinline__ void mma_s8(int (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// v * 2^e as a binary64, exactly (v an int32, result in the normal range),
+// built with integer operations.
+__device__ __forceinline__ double scaled_int(int v, int e)
+{
+    if (v == 0) return 0.0;
+    const unsigned u = v < 0 ? 0u - static_cast<unsigned>(v) : static_cast<unsigned>(v);
+    const int lz = __clz(static_cast<int>(u));
+    const int ex = 31 - lz + e;
+    const uint64_t mant = (static_cast<uint64_t>(u) << (21 + lz)) & ((1ull << 52) - 1);
+    const uint64_t bits = (static_cast<uint64_t>(v < 0) << 63) |
+                          (static_cast<uint64_t>(ex + 1023) << 52) | mant;
+    return __longlong_as_double(static_cast<long long>(bits));
+}
+
+struct OzakiGemmArgs {
+    const int8_t* sa;   // [S][mp][kp]
+    const int8_t* sb;   // [S][np][kp]
+    const int* sig;     // [mp]
+    const int* tau;     // [np]
+    double* C0;
+    double* C1;
+    int64_t ldc, m, n, mp, np, kp;
+    int S;
+};
+
+// Iteration cursor over (weight w, pair s, k tile), weights from S+1 down to 2.
+struct Cursor {
+    int w, s, kt;
+    __device__ __forceinline__ void advance(int S, int KT)
+    {
+        if (++kt < KT) return;
+        kt = 0;
+        const int smax = w - 1 < S ? w - 1 : S;
+        if (++s <= smax) return;
+        --w;
+        s = w - S > 1 ? w - S : 1;
+    }
+};
+
+__global__ void __launch_bounds__(128) ozaki_gemm_kernel(const OzakiGemmArgs g)
+{
+    __shared__ __align__(16) int8_t As[STAGES][TILE * SROW];
+    __shared__ __align__(16) int8_t Bs[STAGES][TILE * SROW];
+
+    const mp::Rn f = mp::make_rn();
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int gq = lane >> 2, tq = lane & 3;
+    const int wm = warp >> 1, wn = warp & 1;
+    const int64_t m0 = static_cast<int64_t>(blockIdx.y) * TILE;
+    const int64_t n0 = static_cast<int64_t>(blockIdx.x) * TILE;
+    const int S = g.S;
+    const int KT = static_cast<int>(g.kp / TILE);
+    const int total = (S * (S + 1) / 2) * KT;
+
+    // exponents of this thread's rows and columns
+    int sg[2][2], tu[4][2];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) sg[mt][h] = g.sig[m0 + wm * 32 + mt * 16 + gq + h * 8];
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) tu[nt][h] = g.tau[n0 + wn * 32 + nt * 8 + 2 * tq + h];
+
+    double acc0[2][4][4], acc1[2][4][4];
+    int ci[2][4][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) { acc0[mt][nt][r] = 0.0; acc1[mt][nt][r] = 0.0; ci[mt][nt][r] = 0; }
+
+    auto load = [&](int stage, const Cursor& c) {
+        const int t = S + 1 - c.w + 0;            // unused helper to keep names clear
+        (void)t;
+        const int8_t* a = g.sa + ((static_cast<int64_t>(c.s - 1) * g.mp + m0) * g.kp) +
+                          static_cast<int64_t>(c.kt) * TILE;
+        const int8_t* b = g.sb + ((static_cast<int64_t>(c.w - c.s - 1) * g.np + n0) * g.kp) +
+                          static_cast<int64_t>(c.kt) * TILE;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int chunk = tid + i * 128;      // 256 chunks of 16 B per operand
+            const int row = chunk >> 2, col = (chunk & 3) * 16;
+            cp_async16(&As[stage][row * SROW + col], a + static_cast<int64_t>(row) * g.kp + col);
+            cp_async16(&Bs[stage][row * SROW + col], b + static_cast<int64_t>(row) * g.kp + col);
+        }
+    };
+
+    Cursor ld{S + 1, 1, 0}, cm{S + 1, 1, 0};
+#pragma unroll
+    for (int st = 0; st < STAGES - 1; ++st) {
+        if (st < total) load(st, ld);
+        ld.advance(S, KT);
+        cp_async_commit();
+    }
+
+    for (int it = 0; it < total; ++it) {
+        cp_async_wait<STAGES - 2>();
+        __syncthreads();
+        {
+            const int nxt = it + STAGES - 1;
+            if (nxt < total) load(nxt % STAGES, ld);
+            ld.advance(S, KT);
+            cp_async_commit();
+        }
+        const int8_t* as = As[it % STAGES];
+        const int8_t* bs = Bs[it % STAGES];
+#pragma unroll
+        for (int kk = 0; kk < TILE; kk += 32) {
+            uint32_t af[2][4], bf[4][2];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const int r = wm * 32 + mt * 16 + gq;
+                af[mt][0] = *reinterpret_cast<const uint32_t*>(as + r * SROW + kk + 4 * tq);
+                af[mt][1] = *reinterpret_cast<const uint32_t*>(as + (r + 8) * SROW + kk + 4 * tq);
+                af[mt][2] = *reinterpret_cast<const uint32_t*>(as + r * SROW + kk + 16 + 4 * tq);
+                af[mt][3] = *reinterpret_cast<const uint32_t*>(as + (r + 8) * SROW + kk + 16 + 4 * tq);
+            }
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const int c = wn * 32 + nt * 8 + gq;
+                bf[nt][0] = *reinterpret_cast<const uint32_t*>(bs + c * SROW + kk + 4 * tq);
+                bf[nt][1] = *reinterpret_cast<const uint32_t*>(bs + c * SROW + kk + 16 + 4 * tq);
+            }
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) mma_s8(ci[mt][nt], af[mt], bf[nt]);
+        }
+        // end of a weight: fold its exact integer sums into the DD accumulators
+        const int w = cm.w;
+        cm.advance(S, KT);
+        if (cm.w != w || it == total - 1) {
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int e = sg[mt][r >> 1] + tu[nt][r & 1] - 7 * w;
+                        const double x[2] = {acc0[mt][nt][r], acc1[mt][nt][r]};
+                        const double y[2] = {scaled_int(ci[mt][nt][r], e), 0.0};
+                        double z[2];
+                        mp::dd_add(f, x, y, z);
+                        acc0[mt][nt][r] = z[0];
+                        acc1[mt][nt][r] = z[1];
+                        ci[mt][nt][r] = 0;
+                    }
+        }
+    }
+    cp_async_wait<0>();
+
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int64_t row = m0 + wm * 32 + mt * 16 + gq + (r >> 1) * 8;
+                const int64_t col = n0 + wn * 32 + nt * 8 + 2 * tq + (r & 1);
+                if (row < g.m && col < g.n) {
+                    g.C0[row * g.ldc + col] = acc0[mt][nt][r];
+                    g.C1[row * g.ldc + col] = acc1[mt][nt][r];
+                }
+            }
+}
+
+// ------------------------------------------------------------------ host
+
+static int64_t round_up(int64_t x, int64_t r) { return (x + r - 1) / r * r; }
+
+OzakiLayout ozaki_layout(int S, int64_t m, int64_t n, int64_t k)
+{
+    OzakiLayout L;
+    L.S = S;
+    L.mp = round_up(m > 0 ? m : 1, TILE);
+    L.np = round_up(n > 0 ? n : 1, TILE);
+    L.kp = round_up(k > 0 ? k : 1, TILE);
+    L.offA = 0;
+    L.offB = round_up(static_cast<int64_t>(S) * L.mp * L.kp, 256);
+    L.offSig = L.offB + round_up(static_cast<int64_t>(S) * L.np * L.kp, 256);
+    L.offTau = L.offSig + round_up(L.mp * 4, 256);
+    L.total = L.offTau + round_up(L.np * 4, 256);
+    return L;
+}
+
+static unsigned blocks_for(int64_t threads, int per) { return static_cast<unsigned>((threads + per - 1) / per); }
+
+// Slice one operand: vectors (rows of op(A) or columns of op(B)) of length
+// len; `contig` says whether a vector's elements are adjacent in memory.
+static cudaError_t slice_operand(const double* hi, const double* lo, int64_t count, int64_t len,
+                                 int64_t ld, bool contig, int S, int64_t count_pad, int64_t kp,
+                                 int8_t* out, int* sig, cudaStream_t s)
+{
+    if (contig) ozaki_scale_contig<<<blocks_for(count * 32, 256), 256, 0, s>>>(hi, count, len, ld, sig);
+    else ozaki_scale_strided<<<blocks_for(count, 256), 256, 0, s>>>(hi, count, len, ld, sig);
+    if (count_pad > count)
+        ozaki_fill_int<<<blocks_for(count_pad - count, 256), 256, 0, s>>>(sig, count, count_pad);
+    if (contig) {
+        ozaki_slice_rows<<<blocks_for(count_pad * (kp / 4), 128), 128, 0, s>>>(hi, lo, count, len, ld,
+                                                                               sig, S, count_pad, kp, out);
+    } else {
+        const dim3 grid(static_cast<unsigned>(count_pad / 32), static_cast<unsigned>(kp / 32));
+        ozaki_slice_cols<<<grid, 256, 0, s>>>(hi, lo, count, len, ld, sig, S, count_pad, kp, out);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ozaki_dd(const GemmArgs<2>& g, int S, void* ws, cudaStream_t s)
+{
+    const OzakiLayout L = ozaki_layout(S, g.m, g.n, g.k);
+    int8_t* base = static_cast<int8_t*>(ws);
+    int8_t* sa = base + L.offA;
+    int8_t* sb = base + L.offB;
+    int* sig = reinterpret_cast<int*>(base + L.offSig);
+    int* tau = reinterpret_cast<int*>(base + L.offTau);
+    // op(A) row i: contiguous unless A is stored transposed
+    cudaError_t e = slice_operand(g.A[0], g.A[1], g.m, g.k, g.lda, !g.trans_a, S, L.mp, L.kp, sa, sig, s);
+    if (e != cudaSuccess) return e;
+    // op(B) column j: contiguous only if B is stored transposed
+    e = slice_operand(g.B[0], g.B[1], g.n, g.k, g.ldb, g.trans_b != 0, S, L.np, L.kp, sb, tau, s);
+    if (e != cudaSuccess) return e;
+    OzakiGemmArgs a{sa, sb, sig, tau, g.C[0], g.C[1], g.ldc, g.m, g.n, L.mp, L.np, L.kp, S};
+    const dim3 grid(static_cast<unsigned>(L.np / TILE), static_cast<unsigned>(L.mp / TILE));
+    ozaki_gemm_kernel<<<grid, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace mpg

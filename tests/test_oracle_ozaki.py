@@ -1,0 +1,147 @@
+"""Pins for the oracle of the INT8 error-free slicing form (CPU only): the
+digits reconstruct each entry exactly, stay in [-64, 64] and round ties to
+even; the scale keeps |a| 2^-sigma < 1/2; small-integer matrices come out
+exact; the error against the exact product falls by ~2^-7 per slice and meets
+k 2^-100 at 14 slices; and planted mistakes are caught."""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import exact as X
+from oracle import ozaki as OZ
+from paper_2101_06584_gb300 import inputs as I
+
+
+def check_digits(components, S, sigma=None):
+    comps = [float(c) for c in components]
+    sg = OZ.scale_exponent([comps[0]]) if sigma is None else sigma
+    ds, rem = OZ.digits(comps, sg, S)
+    a = sum(map(Fraction, comps), Fraction(0))
+    recon = sum((Fraction(d) * Fraction(2) ** (-7 * (s + 1)) for s, d in enumerate(ds)), Fraction(0))
+    recon = (recon + rem * Fraction(2) ** (-7 * S)) * Fraction(2) ** sg
+    assert recon == a
+    assert all(-64 <= d <= 64 for d in ds)
+    assert abs(rem) <= Fraction(1, 2)
+    return ds
+
+
+def test_digits_reconstruct_exactly():
+    rng = np.random.default_rng(500)
+    x = I.random_mp(2, 400, rng, spread=40)
+    for t in range(x.shape[1]):
+        for S in (1, 5, 14, 16):
+            check_digits(x[:, t], S)
+
+
+def test_scale_exponent_bounds():
+    rng = np.random.default_rng(501)
+    for _ in range(300):
+        row = I.random_mp(2, 17, rng, spread=30)
+        sg = OZ.scale_exponent(row[0])
+        for p in range(row.shape[1]):
+            assert abs(X.value(row[:, p])) * Fraction(2) ** (-sg) < Fraction(1, 2)
+        assert max(abs(v) for v in row[0]) * 2.0 ** (-sg) >= 0.25
+    assert OZ.scale_exponent([0.0, -0.0]) == 0
+
+
+def test_ties_round_to_even():
+    # a 2^-sigma = 3/256: y = 1.5 -> digit 2, remainder -1/2; then -64
+    sg = 0
+    ds, rem = OZ.digits([3.0 / 256.0, 0.0], sg, 3)
+    assert ds == [2, -64, 0] and rem == 0
+    ds, _ = OZ.digits([5.0 / 256.0, 0.0], sg, 2)          # y = 2.5 -> 2
+    assert ds == [2, 64]
+    ds, _ = OZ.digits([5.0 / 256.0, 2.0 ** -80], sg, 2)   # just above the tie -> 3
+    assert ds[0] == 3
+    ds, _ = OZ.digits([-3.0 / 256.0, 0.0], sg, 2)         # y = -1.5 -> -2
+    assert ds == [-2, 64]
+
+
+def test_small_integer_matrices_are_exact():
+    rng = np.random.default_rng(502)
+    m, n, k = 6, 7, 33
+    A = np.zeros((2, m, k))
+    B = np.zeros((2, k, n))
+    A[0] = rng.integers(-63, 64, (m, k))
+    B[0] = rng.integers(-63, 64, (k, n))
+    A[0][:, 0] = 63                         # every row / column reaches 2^5..2^6
+    B[0][0, :] = -40
+    C, _, _ = OZ.gemm(A, B, 3)
+    want = A[0].astype(object).dot(B[0].astype(object))
+    assert (C[0] == want.astype(np.float64)).all() and (C[1] == 0).all()
+
+
+@pytest.mark.parametrize("gen", ["uniform", "cancelling"])
+def test_error_shrinks_per_slice_and_meets_bound(gen):
+    rng = np.random.default_rng(503)
+    m, n, k = 10, 9, 40
+    if gen == "uniform":
+        A, B = I.uniform(2, (m, k), rng), I.uniform(2, (k, n), rng)
+    else:
+        A, B = I.cancelling_pair(2, m, n, k, rng)
+    ent = [(i, j) for i in range(m) for j in range(n)]
+    errs = {}
+    for S in (8, 10, 14, 16):
+        C, _, _ = OZ.gemm(A, B, S)
+        errs[S] = X.gemm_error(C, A, B, ent)["err_abs"]
+    # entries spread over 2^+-20 within a row need more slices than uniform ones
+    assert errs[16 if gen == "cancelling" else 14] <= k * 2.0 ** -100
+    assert errs[10] < errs[8] * 2.0 ** -10
+
+
+def test_matches_plain_definition_of_weights():
+    """The weight sums equal the full double sum over slice pairs with s+t=w."""
+    rng = np.random.default_rng(504)
+    A, B = I.uniform(2, (3, 12), rng), I.uniform(2, (12, 4), rng)
+    S = 4
+    _, DA = OZ.slice_rows(A, S)
+    _, DB = OZ.slice_cols(B, S)
+    Pw = OZ.weight_products(DA, DB, S)
+    for w in range(2, S + 2):
+        for i in range(3):
+            for j in range(4):
+                tot = 0
+                for s in range(1, S + 1):
+                    for t in range(1, S + 1):
+                        if s + t == w:
+                            tot += sum(int(DA[s - 1, i, p]) * int(DB[t - 1, j, p]) for p in range(12))
+                assert Pw[w][i, j] == tot
+
+
+MUTANTS = [
+    ("ties away from zero", "digits",
+     lambda comps, sigma, S: _digits_mut(comps, sigma, S, tie="away")),
+    ("scale one too small", "scale_exponent",
+     lambda hv: (lambda mx: 0 if mx == 0 else OZ.ilogb(mx) + 1)(max(abs(float(v)) for v in hv))),
+    ("drops the least significant weight", "weight_products",
+     lambda DA, DB, S: {w: (v if w < S + 1 else v * 0) for w, v in _orig_wp(DA, DB, S).items()}),
+]
+_orig_digits = OZ.digits
+_orig_wp = OZ.weight_products
+
+
+def _digits_mut(comps, sigma, S, tie):
+    x = sum((Fraction(float(c)) for c in comps), Fraction(0)) * Fraction(2) ** (-sigma)
+    out = []
+    for _ in range(S):
+        y = x * 128
+        d = math.floor(y + Fraction(1, 2)) if y >= 0 else -math.floor(-y + Fraction(1, 2))
+        out.append(int(d))
+        x = y - d
+    return out, x
+
+
+@pytest.mark.parametrize("name,attr,fn", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_caught(monkeypatch, name, attr, fn):
+    monkeypatch.setattr(OZ, attr, fn)
+    failures = 0
+    for t in (test_ties_round_to_even, test_scale_exponent_bounds,
+              lambda: test_error_shrinks_per_slice_and_meets_bound("uniform")):
+        try:
+            t()
+        except AssertionError:
+            failures += 1
+    assert failures, name
