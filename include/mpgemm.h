@@ -169,6 +169,30 @@ int mpgemm_ex(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k,
 /* Bytes of workspace mpgemm_ex needs for these options and sizes (0 if none). */
 size_t mpgemm_workspace_size(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k);
 
+/* DD C := A B through the INT8 slicing form (as mpgemm_ex with
+ * MPG_ALGO_INT8_OZAKI and no transposes) without a caller workspace.  The
+ * paper has no counterpart: this call exists for callers that cannot
+ * allocate device memory -- code running inside a host framework that owns
+ * all device memory through its own pool and forbids raw allocations, or a
+ * latency-critical loop that cannot afford cudaMalloc's implicit
+ * synchronisation -- so it allocates nothing and calls no allocating routine.
+ * Its scratch is a fixed 32 MiB array inside the library, present on every
+ * device that loads it until the process exits.  Products whose scratch
+ * (mpgemm_workspace_size with algo MPG_ALGO_INT8_OZAKI) exceeds 32 MiB are
+ * rejected with MPG_EWORKSPACE before anything is launched; e.g. DD
+ * 1024 x 1024 x 1024 with 14 slices fits.  slices = 0 means 14.
+ * The first call on a device looks up the array's device address once
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call uses the same array and each call
+ * writes every scratch byte it reads, so a call never depends on what an
+ * earlier one left there; but calls whose execution overlaps on the GPU
+ * (different streams, or different host threads without ordering) race on
+ * the array and must be serialised by the caller. */
+int mpgemm_dd_int8_static(int64_t m, int64_t n, int64_t k,
+                          const double *const A[2], int64_t lda,
+                          const double *const B[2], int64_t ldb,
+                          double *const C[2], int64_t ldc, int slices);
+
 /* Number of FP64-EFT tile configurations for precision P, and a description
  * of configuration id (BM, BN, BK, TM, TN, threads); returns MPG_EINVAL for
  * an unknown id. */

@@ -315,6 +315,47 @@ size_t mpgemm_workspace_size(int P, const mpgemm_opts* opts, int64_t m, int64_t 
     return static_cast<size_t>(ozaki_layout(S, m, n, k).total);
 }
 
+int mpgemm_dd_int8_static(int64_t m, int64_t n, int64_t k, const double* const A[2], int64_t lda,
+                          const double* const B[2], int64_t ldb, double* const C[2], int64_t ldc,
+                          int slices)
+{
+    clear_error();
+    if (!A || !B || !C) return fail(MPG_EINVAL, "plane pointer arrays must not be NULL");
+    GemmArgs<2> g;
+    for (int c = 0; c < 2; ++c) {
+        g.A[c] = A[c];
+        g.B[c] = B[c];
+        g.C[c] = C[c];
+    }
+    g.m = m; g.n = n; g.k = k; g.lda = lda; g.ldb = ldb; g.ldc = ldc;
+    g.trans_a = 0;
+    g.trans_b = 0;
+    int rc = check_gemm<2>(g);
+    if (rc != MPG_OK) return rc;
+    if (m == 0 || n == 0) return MPG_OK;
+    const int S = slices ? slices : kOzakiDefaultSlices;
+    if (S < 1 || S > kOzakiMaxSlices)
+        return fail(MPG_EINVAL, "slices must be in 1..%d (got %d)", kOzakiMaxSlices, S);
+    if (k > ozaki_k_limit(S))
+        return fail(MPG_EUNSUPPORTED, "k = %lld exceeds %lld, the largest k whose %d-slice int32 "
+                    "sums are exact", (long long)k, (long long)ozaki_k_limit(S), S);
+    cudaError_t e;
+    if (k == 0) {
+        e = launch_zero<2>(g, g_stream);
+        return e == cudaSuccess ? MPG_OK : cuda_fail(e, "zero launch");
+    }
+    const OzakiLayout L = ozaki_layout(S, m, n, k);
+    if (L.total > kOzakiStaticScratchBytes)
+        return fail(MPG_EWORKSPACE, "this product needs %lld bytes of scratch with %d slices; the "
+                    "library's fixed array holds %lld (use mpgemm_ex with a workspace instead)",
+                    (long long)L.total, S, (long long)kOzakiStaticScratchBytes);
+    void* ws = nullptr;
+    e = ozaki_static_scratch(&ws);
+    if (e != cudaSuccess) return cuda_fail(e, "looking up the fixed scratch array");
+    e = launch_ozaki_dd(g, S, ws, g_stream);
+    return e == cudaSuccess ? MPG_OK : cuda_fail(e, "INT8 slicing gemm launch");
+}
+
 int mpgemm_num_tiles(int P)
 {
     switch (P) {

@@ -26,6 +26,7 @@
 #include "ozaki.h"
 
 #include <cstdint>
+#include <mutex>
 
 namespace mpg {
 
@@ -432,6 +433,39 @@ __global__ void __launch_bounds__(128) ozaki_gemm_kernel(const OzakiGemmArgs g)
                     g.C1[row * g.ldc + col] = acc1[mt][nt][r];
                 }
             }
+}
+
+// ------------------------------------------------------- fixed scratch
+
+// Scratch for callers that cannot allocate device memory (see
+// mpgemm_dd_int8_static in include/mpgemm.h).  Every device that loads the
+// library holds this array until the process exits.  Each call rewrites every
+// byte of it that it later reads (slices and padding, exponents and padding),
+// so nothing has to be cleared between calls.
+static __device__ __align__(256) unsigned char g_static_scratch[kOzakiStaticScratchBytes];
+
+namespace {
+std::mutex g_static_mu;
+void* g_static_ptr[64] = {nullptr};
+}  // namespace
+
+cudaError_t ozaki_static_scratch(void** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        // In host code the array's name is only a stand-in: the kernels need
+        // the device address, looked up once per device with it current.
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_ptr[dev] = p;
+    }
+    *out = g_static_ptr[dev];
+    return cudaSuccess;
 }
 
 // ------------------------------------------------------------------ host

@@ -20,4 +20,9 @@ inline int64_t ozaki_k_limit(int S) { return (2147483647LL) / (static_cast<int64
 
 cudaError_t launch_ozaki_dd(const GemmArgs<2>& g, int S, void* ws, cudaStream_t s);
 
+// Size of the library's fixed scratch array and its device address on the
+// current device (looked up on first use per device).
+constexpr int64_t kOzakiStaticScratchBytes = 32LL << 20;
+cudaError_t ozaki_static_scratch(void** out);
+
 }  // namespace mpg

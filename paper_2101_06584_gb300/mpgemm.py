@@ -57,6 +57,7 @@ def _declare(L):
     L.mpgemm_ex.argtypes = [i, ctypes.POINTER(Opts), i64, i64, i64, vp, i64, vp, i64, vp, i64]
     L.mpgemm_workspace_size.argtypes = [i, ctypes.POINTER(Opts), i64, i64, i64]
     L.mpgemm_workspace_size.restype = ctypes.c_size_t
+    L.mpgemm_dd_int8_static.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, i]
     L.mpgemm_num_tiles.argtypes = [i]
     L.mpgemm_tile_info.argtypes = [i, i, ctypes.POINTER(ctypes.c_int * 6)]
     return L
