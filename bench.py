@@ -1,17 +1,25 @@
 #!/usr/bin/env python3
 """Benchmark: multi-component (DD/TD/QD) GEMM on one GB300 (or N independent
-replicas), reported as multiply-adds per second and as a fraction of the FP64
-roofline, with the CPU oracle timed beside it.
+replicas), reported as multiply-adds per second and as a fraction of the
+roofline of the dominant kernel, with the CPU oracle timed beside it.
 
-Default workload (one "step"): the TD GEMM and the QD GEMM, m = n = k = 1024,
-on seeded ill-scaled inputs whose inner dimension is built to cancel (the
-k-sequential FP64-EFT kernels, bit-identical to the oracle).  Other
-workloads are measured once each and reported under "configs".
+Workloads (one "step" = one pass of the workload's kernels over its inputs):
+  td_qd     (default) TD GEMM + QD GEMM, m = n = k = 1024, seeded ill-scaled
+            inputs whose inner dimension cancels; k-sequential FP64-EFT kernels
+            (bit-identical to the oracle)
+  dd_small  DD GEMM 128^3, uniform inputs
+  dd_int8   DD GEMM 4096^3 through the INT8 error-free slicing form (slicing +
+            tensor-core slice products + EFT accumulation), S = 13 slices
+  batched   512 DD and 512 QD problems, m, n, k log-uniform in [16, 512], each
+            precision one persistent launch replayed from a CUDA graph
+  autograd  DDMatmul forward + backward (3 DD GEMMs), m = n = k = 2048
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME]
 
-Under torchrun each rank runs its own independent problem (weak scaling);
-only host-side timing is reduced across ranks.
+The default line also carries, under "configs", one measurement of every
+other workload.  Under torchrun each rank runs its own independent problem
+(weak scaling); only timings are reduced across ranks.
 """
 import argparse
 import json
@@ -36,6 +44,7 @@ UNIT = "mad/s"
 # QD = QDmul 123 + QDadd 87.
 FP64_OPS_PER_MAD = {"dd": 20, "td": 128, "qd": 210}
 L2_FLUSH_BYTES = 256 << 20          # larger than the 129 MB L2
+INT8_SLICES = 13
 
 
 def parse_args():
@@ -44,8 +53,10 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--size", type=int, default=1024, help="m = n = k of the TD/QD workload")
-    ap.add_argument("--no-extras", action="store_true", help="skip the other configurations")
+    ap.add_argument("--workload", default="td_qd",
+                    choices=["td_qd", "dd_small", "dd_int8", "batched", "autograd"])
+    ap.add_argument("--size", type=int, default=None, help="override the workload's m = n = k")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other workloads")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     return ap.parse_args()
 
@@ -53,13 +64,11 @@ def parse_args():
 # ------------------------------------------------------------------ helpers
 
 def dist_env():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def max_over_ranks(value, world):
+def reduce_max(value, world):
     if world == 1:
         return value
     import torch
@@ -83,7 +92,6 @@ class ClockSampler:
 
     def __init__(self, local_rank):
         self.proc = None
-        self.path = None
         self.index = str(local_rank)
         vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
         if vis:
@@ -121,58 +129,321 @@ class ClockSampler:
         os.unlink(self.path)
         if not rows:
             return None
-        sm = [float(r[0]) for r in rows]
-        smax = max(float(r[1]) for r in rows)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": reasons,
-                "samples": len(rows), "power_w_max": max(float(r[2]) for r in rows
-                                                          if r[2].replace(".", "").isdigit())}
+        power = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(float(r[0]) for r in rows),
+                "sm_max_mhz": max(float(r[1]) for r in rows), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(power) if power else None}
 
 
-# ------------------------------------------------------------ CPU baseline
-
-def cpu_sample_rate(prec_list, size, rows, cfg=1):
-    """Oracle (as it stands) on all host cores: mad/s over the first ``rows``
-    rows of C for each precision, same inputs as the GPU workload."""
-    import oracle
-    from paper_2101_06584_gb300 import inputs as I
-    cores = oracle.num_cpus()
-    mads = 0
-    secs = 0.0
-    for prec in prec_list:
-        P = I.P_OF[prec]
-        A, B = I.cancelling_pair(P, size, size, size, I.rng_for(cfg))
-        A = np.ascontiguousarray(A[:, :rows, :])
-        t0 = time.perf_counter()
-        oracle.gemm(prec, A, B, nthreads=cores)
-        secs += time.perf_counter() - t0
-        mads += rows * size * size
-    return mads / secs, cores, secs
-
-
-# ------------------------------------------------------------------ GPU arm
-
-def fp64_peaks(torch, mm):
-    """Measured FP64 lane-operation rate of the probe kernel (add and fma),
-    at this run's clocks."""
-    from paper_2101_06584_gb300 import mpgemm
+def peaks(torch, mm):
+    """Measured pipe rates at this run's clocks (the roofline denominators):
+    FP64 lane-operations/s for add, mul, fma and int8 ops/s of mma.sync s8."""
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     blocks = sms * 8
     out = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
     res = {}
-    for kind, name in ((0, "dadd"), (1, "dmul"), (2, "dfma")):
-        iters = 2048
-        mpgemm.fp64_probe(kind, blocks, 64, out)
+    for kind, name, iters, ops in ((0, "dadd", 2048, 8), (1, "dmul", 2048, 8), (2, "dfma", 2048, 8),
+                                   (3, "mma_s8", 4096, 4 * 8192 / 32)):
+        mm.peak_probe(kind, blocks, 16, out)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        mpgemm.fp64_probe(kind, blocks, iters, out)
+        mm.peak_probe(kind, blocks, iters, out)
         e1.record()
         torch.cuda.synchronize()
-        ops = blocks * 256 * iters * 8
-        res[name] = ops / (e0.elapsed_time(e1) * 1e-3)
+        res[name] = blocks * 256 * iters * ops / (e0.elapsed_time(e1) * 1e-3)
     return res
+
+
+# --------------------------------------------------------------- workloads
+
+class Workload:
+    """One benchmark workload: device inputs, a step, and its dominant kernel."""
+    name = ""
+    launches_per_step = 1
+
+    def timed_step(self, stream):
+        """Run one step; returns [(start, end)] events around each dominant launch."""
+        raise NotImplementedError
+
+
+class TdQd(Workload):
+    name = "td_qd"
+
+    def __init__(self, torch, mm, I, rank, n=1024):
+        self.torch, self.mm, self.n = torch, mm, n
+        self.precs = ("td", "qd")
+        rng = np.random.Generator(np.random.PCG64(I.SEED_BASE + 1 + 1000 * rank))
+        self.host = {}
+        self.dev = {}
+        for prec in self.precs:
+            P = I.P_OF[prec]
+            A, B = I.cancelling_pair(P, n, n, n, rng)
+            self.host[prec] = (A, B)
+            self.dev[prec] = (torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(),
+                              torch.empty((P, n, n), dtype=torch.float64, device="cuda"))
+        self.mads = len(self.precs) * n ** 3
+        self.launches_per_step = 2
+        self.dominant = "qd"
+        self.config = {"workload": "TD GEMM + QD GEMM, m=n=k=%d, k-sequential FP64-EFT" % n,
+                       "m": n, "n": n, "k": n, "precisions": list(self.precs)}
+
+    def timed_step(self, stream):
+        torch = self.torch
+        evs = {}
+        for prec in self.precs:
+            A, B, C = self.dev[prec]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            self.mm.gemm_plain(prec, A, B, out=C)
+            e1.record(stream)
+            evs[prec] = (e0, e1)
+        return evs
+
+    def roofline(self, launch_ms, pk):
+        n = self.n
+        ops = n ** 3 * FP64_OPS_PER_MAD["qd"]
+        ach = ops / (statistics.mean(launch_ms["qd"]) * 1e-3)
+        return {"bound": "alu", "kernel": "gemm_kseq_kernel<4,16,16,16,1,1> (QD)",
+                "achieved": ach / 1e12, "peak": pk["dfma"] / 1e12, "unit": "TFP64op/s",
+                "frac": ach / pk["dfma"], "traffic": None, "ops_per_unit": FP64_OPS_PER_MAD["qd"],
+                "unit_of_work": "QD multiply-add", "units_per_launch": n ** 3,
+                "peak_source": "measured FP64 FMA probe with register operands at this run's clocks",
+                "per_precision_mad_s": {p: n ** 3 / (statistics.mean(launch_ms[p]) * 1e-3)
+                                        for p in self.precs}}
+
+    def e2e(self, steps, world):
+        torch = self.torch
+        pinned = {p: tuple(torch.from_numpy(x).pin_memory() for x in self.host[p]) for p in self.precs}
+        outs = {p: torch.empty(self.dev[p][2].shape, dtype=torch.float64).pin_memory()
+                for p in self.precs}
+        h2d = sum(x.numel() * 8 for p in self.precs for x in pinned[p])
+        d2h = sum(outs[p].numel() * 8 for p in self.precs)
+
+        def one():
+            for p in self.precs:
+                A, B, C = self.dev[p]
+                A.copy_(pinned[p][0], non_blocking=True)
+                B.copy_(pinned[p][1], non_blocking=True)
+                self.mm.gemm_plain(p, A, B, out=C)
+                outs[p].copy_(C, non_blocking=True)
+            torch.cuda.synchronize()
+        one()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            one()
+        barrier(world)
+        secs = reduce_max(time.perf_counter() - t0, world)
+        return {"value": world * self.mads * steps / secs, "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+class DdSmall(Workload):
+    name = "dd_small"
+
+    def __init__(self, torch, mm, I, rank, n=128):
+        self.torch, self.mm, self.n = torch, mm, n
+        rng = np.random.Generator(np.random.PCG64(I.SEED_BASE + 0 + 1000 * rank))
+        self.A = torch.from_numpy(I.uniform(2, (n, n), rng)).cuda()
+        self.B = torch.from_numpy(I.uniform(2, (n, n), rng)).cuda()
+        self.C = torch.empty((2, n, n), dtype=torch.float64, device="cuda")
+        self.mads = n ** 3
+        self.config = {"workload": "DD GEMM m=n=k=%d, k-sequential FP64-EFT" % n, "m": n, "n": n, "k": n}
+
+    def timed_step(self, stream):
+        e0, e1 = self.torch.cuda.Event(enable_timing=True), self.torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        self.mm.gemm_plain("dd", self.A, self.B, out=self.C)
+        e1.record(stream)
+        return {"dd": (e0, e1)}
+
+    def roofline(self, launch_ms, pk):
+        ach = self.mads * 20 / (statistics.mean(launch_ms["dd"]) * 1e-3)
+        # the split-K variant for reference (not bit-identical, within bound)
+        ms = _time_call(self.torch, lambda: self.mm.gemm("dd", self.A, self.B, out=self.C, split_k=8), 20)
+        return {"bound": "alu", "kernel": "gemm_kseq_kernel<2,32,32,16,2,2> (DD)",
+                "achieved": ach / 1e12, "peak": pk["dfma"] / 1e12, "unit": "TFP64op/s",
+                "frac": ach / pk["dfma"], "traffic": None, "ops_per_unit": 20,
+                "unit_of_work": "DD multiply-add", "units_per_launch": self.mads,
+                "note": "16 CTAs for 152 SMs: latency-bound; warp split-K 8 runs at %.3g mad/s" % (
+                    self.mads / (ms * 1e-3))}
+
+
+class DdInt8(Workload):
+    name = "dd_int8"
+
+    def __init__(self, torch, mm, I, rank, n=4096, S=INT8_SLICES):
+        self.torch, self.mm, self.n, self.S = torch, mm, n, S
+        rng = np.random.Generator(np.random.PCG64(I.SEED_BASE + 2 + 1000 * rank))
+        self.hA = I.uniform(2, (n, n), rng)
+        self.hB = I.uniform(2, (n, n), rng)
+        self.A = torch.from_numpy(self.hA).cuda()
+        self.B = torch.from_numpy(self.hB).cuda()
+        self.C = torch.empty((2, n, n), dtype=torch.float64, device="cuda")
+        self.ws = torch.empty(mm.workspace_size("dd", n, n, n, algo="int8", slices=S),
+                              dtype=torch.uint8, device="cuda")
+        self.mads = n ** 3
+        # scale + slice for each operand (+ exponent padding when n % 64 != 0) and the product
+        self.launches_per_step = 5 if n % 64 == 0 else 7
+        self.config = {"workload": "DD GEMM m=n=k=%d, INT8 error-free slicing form, S=%d" % (n, S),
+                       "m": n, "n": n, "k": n, "slices": S}
+
+    def timed_step(self, stream):
+        e0, e1 = self.torch.cuda.Event(enable_timing=True), self.torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        self.mm.gemm("dd", self.A, self.B, out=self.C, algo="int8", slices=self.S, workspace=self.ws)
+        e1.record(stream)
+        return {"int8": (e0, e1)}
+
+    def roofline(self, launch_ms, pk):
+        S, n = self.S, self.n
+        pairs = S * (S + 1) // 2
+        ops = 2.0 * pairs * n ** 3
+        ms = statistics.mean(launch_ms["int8"])
+        ach = ops / (ms * 1e-3)
+        plain_ms = _time_call(self.torch, lambda: self.mm.gemm_plain("dd", self.A, self.B), 1)
+        return {"bound": "tensor", "kernel": "ozaki_gemm_kernel (mma.sync m16n8k32 s8) incl. slicing",
+                "achieved": ach / 1e12, "peak": pk["mma_s8"] / 1e12, "unit": "Tint8op/s",
+                "frac": ach / pk["mma_s8"], "traffic": None, "ops_per_unit": 2 * pairs,
+                "unit_of_work": "DD multiply-add (%d slice-pair int8 MACs)" % pairs,
+                "units_per_launch": n ** 3,
+                "peak_source": "measured mma.sync s8 probe at this run's clocks "
+                               "(tcgen05 has no int8 kind on sm_103a)",
+                "fp64_eft_ms": plain_ms, "speedup_vs_fp64_eft": plain_ms / ms}
+
+
+class Batched(Workload):
+    name = "batched"
+
+    def __init__(self, torch, mm, I, rank, count=512):
+        self.torch, self.mm = torch, mm
+        rng = np.random.Generator(np.random.PCG64(I.SEED_BASE + 3 + 1000 * rank))
+        self.shapes = I.batch_shapes(count, rng)
+        self.plans = {}
+        self.keep = []
+        for prec in ("dd", "qd"):
+            P = I.P_OF[prec]
+            triples = []
+            for (m, n, k) in self.shapes:
+                A = torch.from_numpy(I.uniform(P, (m, k), rng)).cuda()
+                B = torch.from_numpy(I.uniform(P, (k, n), rng)).cuda()
+                C = torch.empty((P, m, n), dtype=torch.float64, device="cuda")
+                triples.append((A, B, C))
+            self.keep.append(triples)
+            self.plans[prec] = mm.BatchPlan(prec, triples, policy=None, reps=1)
+        self.mads_per = sum(m * n * k for (m, n, k) in self.shapes)
+        self.mads = 2 * self.mads_per
+        self.launches_per_step = 2
+        self.config = {"workload": "batched DD + QD, %d problems each, m,n,k log-uniform [16,512], "
+                                   "one persistent launch per precision replayed from a CUDA graph"
+                                   % count, "problems": count, "sum_mnk": self.mads_per,
+                       "policy": {p: self.plans[p].policy for p in self.plans},
+                       "tiles": {p: self.plans[p].info()["tiles"] for p in self.plans}}
+
+    def timed_step(self, stream):
+        evs = {}
+        for prec in ("dd", "qd"):
+            e0, e1 = self.torch.cuda.Event(enable_timing=True), self.torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            self.plans[prec].run()
+            e1.record(stream)
+            evs[prec] = (e0, e1)
+        return evs
+
+    def roofline(self, launch_ms, pk):
+        ms = statistics.mean(launch_ms["qd"])
+        ach = self.mads_per * FP64_OPS_PER_MAD["qd"] / (ms * 1e-3)
+        return {"bound": "alu", "kernel": "batched_kernel<4> (QD, persistent)",
+                "achieved": ach / 1e12, "peak": pk["dfma"] / 1e12, "unit": "TFP64op/s",
+                "frac": ach / pk["dfma"], "traffic": None, "ops_per_unit": FP64_OPS_PER_MAD["qd"],
+                "unit_of_work": "QD multiply-add", "units_per_launch": self.mads_per,
+                "per_precision_mad_s": {p: self.mads_per / (statistics.mean(launch_ms[p]) * 1e-3)
+                                        for p in ("dd", "qd")}}
+
+
+class Autograd(Workload):
+    name = "autograd"
+
+    def __init__(self, torch, mm, I, rank, n=2048):
+        from paper_2101_06584_gb300.autograd import dd_matmul
+        self.torch, self.mm, self.n, self.f = torch, mm, n, dd_matmul
+        rng = np.random.Generator(np.random.PCG64(I.SEED_BASE + 4 + 1000 * rank))
+        self.A = torch.from_numpy(I.uniform(2, (n, n), rng)).cuda().requires_grad_(True)
+        self.B = torch.from_numpy(I.uniform(2, (n, n), rng)).cuda().requires_grad_(True)
+        self.W = torch.from_numpy(I.uniform(2, (n, n), rng)).cuda()
+        self.mads = 3 * n ** 3
+        self.launches_per_step = 3
+        self.config = {"workload": "DDMatmul forward + backward (dA = dC B^T, dB = A^T dC), "
+                                   "m=n=k=%d, loss = sum(W*C)" % n, "m": n, "n": n, "k": n}
+
+    def timed_step(self, stream):
+        torch = self.torch
+        self.A.grad = None
+        self.B.grad = None
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        C = self.f(self.A, self.B)
+        e1.record(stream)
+        C.backward(self.W)
+        return {"fwd": (e0, e1)}
+
+    def roofline(self, launch_ms, pk):
+        ach = self.n ** 3 * 20 / (statistics.mean(launch_ms["fwd"]) * 1e-3)
+        return {"bound": "alu", "kernel": "gemm_kseq_kernel<2,32,32,16,2,2> (DD forward)",
+                "achieved": ach / 1e12, "peak": pk["dfma"] / 1e12, "unit": "TFP64op/s",
+                "frac": ach / pk["dfma"], "traffic": None, "ops_per_unit": 20,
+                "unit_of_work": "DD multiply-add", "units_per_launch": self.n ** 3}
+
+
+WORKLOADS = {"td_qd": TdQd, "dd_small": DdSmall, "dd_int8": DdInt8, "batched": Batched,
+             "autograd": Autograd}
+
+
+def _time_call(torch, fn, reps=1):
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def measure(torch, w, steps, warmup, world, local, flush, sample_clocks=True):
+    """Warm up, then time exactly `steps` steps (L2 flushed before each, not
+    timed), with a barrier and a synchronize on both sides."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        w.timed_step(stream)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local) if sample_clocks else None
+    launch_ms, step_ms = {}, []
+    barrier(world)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        flush.zero_()
+        evs = w.timed_step(stream)
+        end = torch.cuda.Event(enable_timing=True)
+        end.record(stream)
+        torch.cuda.synchronize()
+        start = next(iter(evs.values()))[0]          # first launch of the step
+        step_ms.append(start.elapsed_time(end))
+        for k, (a, b) in evs.items():
+            launch_ms.setdefault(k, []).append(a.elapsed_time(b))
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop() if sampler else None
+    total_ms = reduce_max(sum(step_ms), world)
+    return total_ms, launch_ms, clocks, wall
 
 
 def run_ours(args):
@@ -189,123 +460,39 @@ def run_ours(args):
     from paper_2101_06584_gb300 import inputs as I
     from paper_2101_06584_gb300 import mpgemm as mm
 
-    n = args.size
-    precs = ("td", "qd")
-    rng = np.random.Generator(np.random.PCG64(I.SEED_BASE + 1 + 1000 * rank))
-    host_in = {}
-    dev_in = {}
-    for prec in precs:
-        P = I.P_OF[prec]
-        A, B = I.cancelling_pair(P, n, n, n, rng)
-        host_in[prec] = (A, B)
-        dev_in[prec] = (torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(),
-                        torch.empty((P, n, n), dtype=torch.float64, device="cuda"))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
-    peaks = fp64_peaks(torch, mm)
-
-    def step(events=None):
-        for prec in precs:
-            A, B, C = dev_in[prec]
-            if events is not None:
-                events[prec][0].record(stream)
-            mm.gemm_plain(prec, A, B, out=C)
-            if events is not None:
-                events[prec][1].record(stream)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
-    sampler = ClockSampler(local)
-    launch_ms = {p: [] for p in precs}
-    step_ms = []
-    barrier(world)
-    torch.cuda.synchronize()
-    sampler.start()
-    t_wall = time.perf_counter()
-    for _ in range(args.steps):
-        flush.zero_()                                   # evict L2 between steps (untimed)
-        ev = {p: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for p in precs}
-        step(ev)
-        torch.cuda.synchronize()
-        for p in precs:
-            launch_ms[p].append(ev[p][0].elapsed_time(ev[p][1]))
-        step_ms.append(ev[precs[0]][0].elapsed_time(ev[precs[-1]][1]))
-    torch.cuda.synchronize()
-    barrier(world)
-    wall = time.perf_counter() - t_wall
-    clocks = sampler.stop()
-
-    total_ms = max_over_ranks(sum(step_ms), world)
-    mads_per_step = len(precs) * n * n * n
-    value = world * mads_per_step * args.steps / (total_ms * 1e-3)
-
-    # dominant kernel: the one with the larger share of the step
-    avg = {p: statistics.mean(launch_ms[p]) for p in precs}
-    dom = max(precs, key=lambda p: avg[p])
-    ops_per_launch = n * n * n * FP64_OPS_PER_MAD[dom]
-    achieved = ops_per_launch / (avg[dom] * 1e-3)
-    peak = peaks["dfma"]
-
-    # end to end through the public API: pinned host -> device, GEMM, device -> host
-    pinned = {p: tuple(torch.from_numpy(x).pin_memory() for x in host_in[p]) for p in precs}
-    out_host = {p: torch.empty((I.P_OF[p], n, n), dtype=torch.float64).pin_memory() for p in precs}
-    h2d = sum(x.numel() * 8 for p in precs for x in pinned[p])
-    d2h = sum(out_host[p].numel() * 8 for p in precs)
-
-    def e2e_step():
-        for p in precs:
-            A, B, C = dev_in[p]
-            A.copy_(pinned[p][0], non_blocking=True)
-            B.copy_(pinned[p][1], non_blocking=True)
-            mm.gemm_plain(p, A, B, out=C)
-            out_host[p].copy_(C, non_blocking=True)
-        torch.cuda.synchronize()
-
-    e2e_step()
-    barrier(world)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        e2e_step()
-    barrier(world)
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
-    e2e_value = world * mads_per_step * args.steps / e2e_s
-
-    # consistency: the timed results equal a fresh call (deterministic kernels)
+    pk = peaks(torch, mm)
+    kw = {} if args.size is None else {"n": args.size}
+    w = WORKLOADS[args.workload](torch, mm, I, rank, **kw)
+    total_ms, launch_ms, clocks, wall = measure(torch, w, args.steps, args.warmup, world, local, flush)
+    value = world * w.mads * args.steps / (total_ms * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded PCG64; ill-scaled TD/QD entries with cancelling inner halves)",
-        "config": {"workload": "TD GEMM + QD GEMM, m=n=k=%d, k-sequential FP64-EFT" % n,
-                   "precisions": list(precs), "m": n, "n": n, "k": n,
-                   "mads_per_step": mads_per_step, "l2": "flushed between steps (256 MB write)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
-        "per_precision_mad_s": {p: n ** 3 / (statistics.mean(launch_ms[p]) * 1e-3) for p in precs},
-        "roofline": {"bound": "alu", "kernel": "gemm_kseq_kernel<%s>" % dom.upper(),
-                     "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFP64op/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "ops_per_mad": FP64_OPS_PER_MAD[dom],
-                     "peak_source": "measured FP64 FMA probe at this run's clocks "
-                                    "(dadd %.1f, dmul %.1f, dfma %.1f G lane-op/s)" % (
-                                        peaks["dadd"] / 1e9, peaks["dmul"] / 1e9, peaks["dfma"] / 1e9)},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
-        "gpu_launches": len(precs) * args.steps,
+        "data": "synthetic (seeded PCG64, shapes and value ranges of the workload)",
+        "config": dict(w.config, l2="flushed between steps (256 MB write)",
+                       mads_per_step=w.mads,
+                       parallelism="%d independent replicas" % world if world > 1 else "single GPU"),
+        "roofline": w.roofline(launch_ms, pk),
+        "gpu_launches": w.launches_per_step * args.steps,
         "clocks": clocks,
+        "peaks_measured": {k: v for k, v in pk.items()},
         "wall_s": wall,
     }
-    if not args.no_extras and rank == 0:
-        line["configs"] = extras(torch, mm, I)
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if hasattr(w, "e2e"):
+        line["e2e"] = w.e2e(args.steps, world)
+    else:
+        line["e2e"] = None
+    if not args.no_extras and rank == 0 and args.workload == "td_qd":
+        line["configs"] = extras(torch, mm, I, pk, flush)
+    if rank == 0 and world == 1 and not args.no_cpu and args.workload == "td_qd":
         import oracle
-        rows = max(oracle.num_cpus(), n // 16)
-        rate, cores, secs = cpu_sample_rate(precs, n, rows=rows)
+        rows = max(oracle.num_cpus(), w.n // 16)
+        rate, cores, secs = cpu_sample_rate(w.precs, w.n, rows=rows)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": "first %d rows of C for TD and QD at m=n=k=%d "
-                                          "(%.1f s on %d threads)" % (rows, n, secs, cores)}
+                                          "(%.1f s on %d threads)" % (rows, w.n, secs, cores)}
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -313,73 +500,57 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
 
 
-def _time_call(torch, fn, reps=1):
-    fn()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(reps):
-        fn()
-    e1.record()
-    torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / reps
-
-
-def extras(torch, mm, I):
-    """The other workloads, each measured once after the main timing."""
+def extras(torch, mm, I, pk, flush):
+    """One short measurement of each other workload (rank 0, after the main one)."""
     out = {}
-    # DD m=n=k=128, uniform inputs
-    P = 2
-    A, B = I.uniform(P, (128, 128), I.rng_for(0)), I.uniform(P, (128, 128), I.rng_for(0))
-    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
-    C = torch.empty((P, 128, 128), dtype=torch.float64, device="cuda")
-    ms = _time_call(torch, lambda: mm.gemm_plain("dd", Ad, Bd, out=C), reps=20)
-    ms_sk = _time_call(torch, lambda: mm.gemm("dd", Ad, Bd, out=C, split_k=8), reps=20)
-    out["dd_128"] = {"mad_s_kseq": 128 ** 3 / (ms * 1e-3), "mad_s_splitk8": 128 ** 3 / (ms_sk * 1e-3)}
-    # DD m=n=k=4096, plain FP64-EFT
-    n = 4096
-    rng = I.rng_for(2)
-    A, B = I.uniform(P, (n, n), rng), I.uniform(P, (n, n), rng)
-    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
-    C = torch.empty((P, n, n), dtype=torch.float64, device="cuda")
-    ms = _time_call(torch, lambda: mm.gemm_plain("dd", Ad, Bd, out=C), reps=1)
-    out["dd_4096_fp64_eft"] = {"mad_s": n ** 3 / (ms * 1e-3), "ms": ms}
-    # the same product through the INT8 error-free slicing form
-    for S in (13, 14):
-        ws = torch.empty(mm.workspace_size("dd", n, n, n, algo="int8", slices=S),
-                         dtype=torch.uint8, device="cuda")
-        C8 = torch.empty_like(C)
-        ms8 = _time_call(torch, lambda: mm.gemm("dd", Ad, Bd, out=C8, algo="int8", slices=S,
-                                                workspace=ws), reps=3)
-        pairs = S * (S + 1) // 2
-        out["dd_4096_int8_s%d" % S] = {
-            "mad_s": n ** 3 / (ms8 * 1e-3), "ms": ms8, "speedup_vs_fp64_eft": ms / ms8,
-            "int8_tops": 2.0 * pairs * n ** 3 / (ms8 * 1e-3) / 1e12}
-        del ws
+    for name in ("dd_small", "dd_int8", "batched", "autograd"):
+        w = WORKLOADS[name](torch, mm, I, 0)
+        steps = 2 if name != "dd_small" else 10
+        total_ms, launch_ms, _, _ = measure(torch, w, steps, 1, 1, 0, flush, sample_clocks=False)
+        out[name] = {"config": w.config, "mad_s": w.mads * steps / (total_ms * 1e-3),
+                     "ms_per_step": total_ms / steps, "roofline": w.roofline(launch_ms, pk)}
+        del w
+        torch.cuda.empty_cache()
     return out
 
 
-# --------------------------------------------------------- reference arm
+# ------------------------------------------------------------ CPU baseline
+
+def cpu_sample_rate(prec_list, size, rows, cfg=1):
+    """Oracle (as it stands) on all host cores: mad/s over the first ``rows``
+    rows of C for each precision, same inputs as the GPU workload."""
+    import oracle
+    from paper_2101_06584_gb300 import inputs as I
+    cores = oracle.num_cpus()
+    mads, secs = 0, 0.0
+    for prec in prec_list:
+        P = I.P_OF[prec]
+        A, B = I.cancelling_pair(P, size, size, size, I.rng_for(cfg))
+        A = np.ascontiguousarray(A[:, :rows, :])
+        t0 = time.perf_counter()
+        oracle.gemm(prec, A, B, nthreads=cores)
+        secs += time.perf_counter() - t0
+        mads += rows * size * size
+    return mads / secs, cores, secs
+
 
 def run_reference(args):
-    """The oracle (CPU, as it stands) on a bounded sample of the same workload."""
+    """The oracle (CPU, as it stands) on a bounded sample of the td_qd workload."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    precs = ("td", "qd")
-    n = args.size
     import oracle
+    precs = ("td", "qd")
+    n = args.size or 1024
     rows = max(oracle.num_cpus(), n // 64)
     for _ in range(args.warmup):
         cpu_sample_rate(precs, n, rows=1)
-    rates, secs_all = [], 0.0
-    cores = 1
+    rates, secs_all, cores = [], 0.0, 1
     for _ in range(args.steps):
         r, cores, secs = cpu_sample_rate(precs, n, rows=rows)
         rates.append(r)
         secs_all += secs
     value = statistics.mean(rates)
-    sample = "first %d rows of C for TD and QD at m=n=k=%d per step" % (rows, n)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * secs_all / args.steps, "higher_is_better": True,
@@ -387,7 +558,7 @@ def run_reference(args):
             "data": "synthetic (seeded PCG64; ill-scaled TD/QD entries with cancelling inner halves)",
             "config": {"workload": "TD GEMM + QD GEMM, m=n=k=%d, k-sequential (CPU oracle)" % n},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": sample},
+                             "sample": "first %d rows of C for TD and QD at m=n=k=%d per step" % (rows, n)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

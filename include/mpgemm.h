@@ -169,6 +169,55 @@ int mpgemm_ex(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k,
 /* Bytes of workspace mpgemm_ex needs for these options and sizes (0 if none). */
 size_t mpgemm_workspace_size(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k);
 
+/* ---------------------------------------------------------------------
+ * Batched GEMM (not in the paper): many independent k-sequential products
+ * C_i := op(A_i) op(B_i) of Sec. 3, Eq. 1, all in precision P, executed by
+ * one persistent kernel launch that the plan captures in a CUDA graph.
+ * Each C_i is bit-identical to mpgemm_ex on that problem alone.
+ * ------------------------------------------------------------------- */
+typedef struct mpgemm_problem {
+    int64_t m, n, k;
+    const double *A[4];   /* first P entries used; stored shapes as in mpgemm_ex */
+    int64_t lda;
+    const double *B[4];
+    int64_t ldb;
+    double *C[4];
+    int64_t ldc;
+    int trans_a, trans_b;
+} mpgemm_problem;
+
+typedef struct mpgemm_batch_plan mpgemm_batch_plan;
+
+/* Workspace bytes a plan over these problems may need (any policy). */
+size_t mpgemm_batch_workspace_size(int P, int count, const mpgemm_problem *problems);
+
+/* Validate every problem (as mpgemm_ex; a bad one fails the whole call with
+ * its message), split them into output tiles -- 16 x 16 for problems with
+ * m*n below the policy's threshold, 32 x 32 otherwise; policy 0..4 =
+ * threshold 0, 2048, 8192, 32768, never -- sort the tiles by decreasing work,
+ * copy the descriptors into `workspace` (device, 256-byte aligned, caller-
+ * owned, kept alive and unmodified while the plan is used) on the current
+ * stream and wait for that copy, and capture one persistent launch in a CUDA
+ * graph.  The problems' matrices are not read until mpgemm_batch_run.
+ * *out receives a host-side handle (free with mpgemm_batch_plan_destroy). */
+int mpgemm_batch_plan_create(int P, int count, const mpgemm_problem *problems, int policy,
+                             void *workspace, size_t workspace_bytes, mpgemm_batch_plan **out);
+
+/* Replay the plan's graph on the calling thread's current stream.  Runs of
+ * one plan must not overlap on the GPU (they share the tile counter). */
+int mpgemm_batch_run(const mpgemm_batch_plan *plan);
+
+/* info = {tiles, CTAs in the persistent grid, policy, problem count}. */
+int mpgemm_batch_plan_info(const mpgemm_batch_plan *plan, int64_t info[4]);
+
+int mpgemm_batch_plan_destroy(mpgemm_batch_plan *plan);
+
+/* Autotuner: build a plan for every policy, time `reps` graph replays of
+ * each on the current stream (writing the problems' C), and return the
+ * fastest policy and its time per run in milliseconds. */
+int mpgemm_batch_autotune(int P, int count, const mpgemm_problem *problems, void *workspace,
+                          size_t workspace_bytes, int reps, int *best_policy, float *best_ms);
+
 /* DD C := A B through the INT8 slicing form (as mpgemm_ex with
  * MPG_ALGO_INT8_OZAKI and no transposes) without a caller workspace.  The
  * paper has no counterpart: this call exists for callers that cannot
@@ -200,13 +249,16 @@ int mpgemm_num_tiles(int P);
 int mpgemm_tile_info(int P, int id, int info[6]);
 
 /* ---------------------------------------------------------------------
- * Measurement aid (no counterpart in the paper): FP64 pipe throughput probe.
- * Launches `blocks` CTAs of 256 threads, each thread running `iters` rounds
- * of 8 independent binary64 operations (kind 0 add, 1 mul, 2 fma) and
- * writing one double to out[blocks * 256] (device, caller-owned).  The caller
- * times the launch; lane-operations = blocks * 256 * iters * 8.
+ * Measurement aid (no counterpart in the paper): pipe throughput probes used
+ * as roofline denominators.  Launches `blocks` CTAs of 256 threads and writes
+ * one double per thread to out[blocks * 256] (device, caller-owned); the
+ * caller times the launch.
+ *   kind 0/1/2: `iters` rounds of 8 independent binary64 add / mul / fma per
+ *     thread with register operands; lane-operations = blocks*256*iters*8.
+ *   kind 3: `iters` rounds of 4 independent mma.sync.m16n8k32 s8 per warp;
+ *     int8 operations = blocks*8*iters*4*8192.
  * ------------------------------------------------------------------- */
-int mpgemm_fp64_probe(int kind, int blocks, int iters, double *out);
+int mpgemm_peak_probe(int kind, int blocks, int iters, double *out);
 
 #ifdef __cplusplus
 }

@@ -159,6 +159,10 @@ int check_gemm(const GemmArgs<P>& g)
     return MPG_OK;
 }
 
+template int check_gemm<2>(const GemmArgs<2>&);
+template int check_gemm<3>(const GemmArgs<3>&);
+template int check_gemm<4>(const GemmArgs<4>&);
+
 template <int P>
 static int ozaki_call(const GemmArgs<P>&, const mpgemm_opts*)
 {

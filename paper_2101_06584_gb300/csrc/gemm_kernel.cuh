@@ -21,22 +21,29 @@
 
 namespace mpg {
 
+// Shared-memory staging of one k-sequential tile: all P planes of a BK-wide
+// slab of A (k-major, padded) and of B.
+template <int P, int BM, int BN, int BK>
+struct KseqSmem {
+    double As[P][BK][BM + 1];
+    double Bs[P][BK][BN];
+};
+
+// One BM x BN tile of C = op(A) op(B) at (m0, n0), computed by a CTA of
+// (BM/TM)*(BN/TN) threads.  Every entry is accumulated by one thread over
+// p = 0..k-1 in order.  Threads none of whose entries lie inside C skip the
+// arithmetic (they still take part in staging and barriers).
 template <int P, int BM, int BN, int BK, int TM, int TN>
-__global__ void __launch_bounds__((BM / TM) * (BN / TN))
-gemm_kseq_kernel(const GemmArgs<P> g)
+__device__ __forceinline__ void kseq_tile(const GemmArgs<P>& g, int64_t m0, int64_t n0,
+                                          KseqSmem<P, BM, BN, BK>& sm, const mp::Rn& f)
 {
     constexpr int NT = (BM / TM) * (BN / TN);
     constexpr int TX = BN / TN;
     constexpr int TY = BM / TM;
-    __shared__ double As[P][BK][BM + 1];
-    __shared__ double Bs[P][BK][BN];
-
-    const mp::Rn f = mp::make_rn();
     const int tid = threadIdx.x;
     const int tx = tid % TX;
     const int ty = tid / TX;
-    const int64_t m0 = static_cast<int64_t>(blockIdx.y) * BM;
-    const int64_t n0 = static_cast<int64_t>(blockIdx.x) * BN;
+    const bool active = (m0 + ty < g.m) && (n0 + tx < g.n);
 
     double acc[TM][TN][P];
 #pragma unroll
@@ -55,7 +62,7 @@ gemm_kseq_kernel(const GemmArgs<P> g)
             const bool ok = gi < g.m && gk < g.k;
             const int64_t off = g.trans_a ? gk * g.lda + gi : gi * g.lda + gk;
 #pragma unroll
-            for (int c = 0; c < P; ++c) As[c][kk][i] = ok ? g.A[c][off] : 0.0;
+            for (int c = 0; c < P; ++c) sm.As[c][kk][i] = ok ? g.A[c][off] : 0.0;
         }
         for (int e = tid; e < BK * BN; e += NT) {
             int kk, j;
@@ -65,26 +72,28 @@ gemm_kseq_kernel(const GemmArgs<P> g)
             const bool ok = gj < g.n && gk < g.k;
             const int64_t off = g.trans_b ? gj * g.ldb + gk : gk * g.ldb + gj;
 #pragma unroll
-            for (int c = 0; c < P; ++c) Bs[c][kk][j] = ok ? g.B[c][off] : 0.0;
+            for (int c = 0; c < P; ++c) sm.Bs[c][kk][j] = ok ? g.B[c][off] : 0.0;
         }
         __syncthreads();
 
-        const int kmax = static_cast<int>(g.k - k0 < BK ? g.k - k0 : BK);
+        if (active) {
+            const int kmax = static_cast<int>(g.k - k0 < BK ? g.k - k0 : BK);
 #pragma unroll 1
-        for (int kk = 0; kk < kmax; ++kk) {
-            double a[TM][P], b[TN][P];
+            for (int kk = 0; kk < kmax; ++kk) {
+                double a[TM][P], b[TN][P];
 #pragma unroll
-            for (int i = 0; i < TM; ++i)
+                for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int c = 0; c < P; ++c) a[i][c] = As[c][kk][ty + i * TY];
+                    for (int c = 0; c < P; ++c) a[i][c] = sm.As[c][kk][ty + i * TY];
 #pragma unroll
-            for (int j = 0; j < TN; ++j)
+                for (int j = 0; j < TN; ++j)
 #pragma unroll
-                for (int c = 0; c < P; ++c) b[j][c] = Bs[c][kk][tx + j * TX];
+                    for (int c = 0; c < P; ++c) b[j][c] = sm.Bs[c][kk][tx + j * TX];
 #pragma unroll
-            for (int i = 0; i < TM; ++i)
+                for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < TN; ++j) mp::mad<P>(f, acc[i][j], a[i], b[j]);
+                    for (int j = 0; j < TN; ++j) mp::mad<P>(f, acc[i][j], a[i], b[j]);
+            }
         }
         __syncthreads();
     }
@@ -101,6 +110,16 @@ gemm_kseq_kernel(const GemmArgs<P> g)
             }
         }
     }
+}
+
+template <int P, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+gemm_kseq_kernel(const GemmArgs<P> g)
+{
+    __shared__ KseqSmem<P, BM, BN, BK> sm;
+    const mp::Rn f = mp::make_rn();
+    kseq_tile<P, BM, BN, BK, TM, TN>(g, static_cast<int64_t>(blockIdx.y) * BM,
+                                     static_cast<int64_t>(blockIdx.x) * BN, sm, f);
 }
 
 template <int P, int S>

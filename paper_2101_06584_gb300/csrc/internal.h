@@ -36,6 +36,11 @@ int default_tile(int64_t m, int64_t n, int64_t k);
 template <int P>
 cudaError_t launch_gemm_splitk(const GemmArgs<P>& g, int split, cudaStream_t s);
 
+// Host-side validation of a GEMM's arguments (MPG_OK or an error code with
+// the thread's message set).
+template <int P>
+int check_gemm(const GemmArgs<P>& g);
+
 // C := 0 (all planes), for k == 0.
 template <int P>
 cudaError_t launch_zero(const GemmArgs<P>& g, cudaStream_t s);

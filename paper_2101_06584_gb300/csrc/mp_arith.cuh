@@ -19,29 +19,41 @@
 
 namespace mp {
 
-// Rounded binary64 operations.  On GB300 a DFMA instruction issues at about
-// 1.19x the rate of DADD or DMUL, so every operation is issued as a fused
+// Rounded binary64 operations.  On GB300 a DFMA whose operands are ordinary
+// registers issues at about 1.19x the rate of DADD or DMUL (or of a DFMA with
+// a compile-time-constant operand), so every operation is issued as a fused
 // multiply-add that rounds to exactly the same value:
-//   a + b = f.fma(a, 1, b),   a - b = f.fma(b, -1, a),   a * b = f.fma(a, b, -0)
+//   a + b = fma(a, 1, b),   a - b = fma(b, -1, a),   a * b = fma(a, b, -0)
 // (the product with +-1 is exact; adding -0 changes no value and keeps the
-// sign of a zero product).  `one` and `neg_zero` come from a kernel argument
-// so the compiler cannot fold the FMAs back into DADD/DMUL.
+// sign of a zero product).  `one`, `neg_zero` and `zero` (+0, used wherever
+// an algorithm adds a constant zero) are loaded at run time from a table
+// indexed by the lane (make_rn), so they live in per-thread registers and no
+// compiler stage can fold them or treat them as uniform constants.
 struct Rn {
     double one;       // +1.0
     double neg_zero;  // -0.0
+    double zero;      // +0.0
     __device__ __forceinline__ double add(double a, double b) const { return __fma_rn(a, one, b); }
     __device__ __forceinline__ double sub(double a, double b) const { return __fma_rn(b, -one, a); }
     __device__ __forceinline__ double mul(double a, double b) const { return __fma_rn(a, b, neg_zero); }
     __device__ __forceinline__ double fma(double a, double b, double c) const { return __fma_rn(a, b, c); }
 };
 
-static __device__ double rn_constants[2] = {1.0, -0.0};
+static __device__ double rn_constants[96] = {
+    1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0,
+    1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0,
+    -0.0, -0.0, -0.0, -0.0, -0.0, -0.0, -0.0, -0.0, -0.0, -0.0, -0.0, -0.0, -0.0, -0.0, -0.0, -0.0,
+    -0.0, -0.0, -0.0, -0.0, -0.0, -0.0, -0.0, -0.0, -0.0, -0.0, -0.0, -0.0, -0.0, -0.0, -0.0, -0.0,
+    0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0,
+    0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
 
-// The Rn constants, read through a volatile pointer into registers.
+// The Rn constants, read through a volatile pointer at a lane-dependent
+// address into per-thread registers.
 __device__ __forceinline__ Rn make_rn()
 {
     const volatile double* p = rn_constants;
-    return Rn{p[0], p[1]};
+    const int lane = static_cast<int>(threadIdx.x & 31u);
+    return Rn{p[lane], p[32 + lane], p[64 + lane]};
 }
 
 // x != 0 (true for every value but +0 and -0), tested on the bit pattern.
@@ -283,7 +295,7 @@ __device__ __forceinline__ void qd_add_impl(const Rn& f, const double x[4], cons
     double s0 = f.add(x[0], y[0]);
     double s1 = f.add(x[1], y[1]);
     double s2 = f.add(x[2], y[2]);
-    double s3 = ZERO4 ? 0.0 : f.add(x[3], y[3]);
+    double s3 = ZERO4 ? f.zero : f.add(x[3], y[3]);
     const double v0 = f.sub(s0, x[0]);
     const double v1 = f.sub(s1, x[1]);
     const double v2 = f.sub(s2, x[2]);
@@ -293,7 +305,7 @@ __device__ __forceinline__ void qd_add_impl(const Rn& f, const double x[4], cons
     double t0 = f.add(w0, f.sub(y[0], v0));
     double t1 = f.add(w1, f.sub(y[1], v1));
     double t2 = f.add(w2, f.sub(y[2], v2));
-    double t3 = 0.0;
+    double t3 = f.zero;
     if (!ZERO4) {
         const double v3 = f.sub(s3, x[3]);
         const double w3 = f.sub(x[3], f.sub(s3, v3));
@@ -315,8 +327,8 @@ __device__ __forceinline__ void qd_add(const Rn& f, const double x[4], const dou
 // the fourth result component dropped.
 __device__ __forceinline__ void td_addq(const Rn& f, const double x[3], const double y[3], double r[3])
 {
-    const double x4[4] = {x[0], x[1], x[2], 0.0};
-    const double y4[4] = {y[0], y[1], y[2], 0.0};
+    const double x4[4] = {x[0], x[1], x[2], f.zero};
+    const double y4[4] = {y[0], y[1], y[2], f.zero};
     double r4[4];
     qd_add_impl<true>(f, x4, y4, r4);
     r[0] = r4[0];

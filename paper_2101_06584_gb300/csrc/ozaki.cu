@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(128) ozaki_gemm_kernel(const OzakiGemmArgs g)
                     for (int r = 0; r < 4; ++r) {
                         const int e = sg[mt][r >> 1] + tu[nt][r & 1] - 7 * w;
                         const double x[2] = {acc0[mt][nt][r], acc1[mt][nt][r]};
-                        const double y[2] = {scaled_int(ci[mt][nt][r], e), 0.0};
+                        const double y[2] = {scaled_int(ci[mt][nt][r], e), f.zero};
                         double z[2];
                         mp::dd_add(f, x, y, z);
                         acc0[mt][nt][r] = z[0];

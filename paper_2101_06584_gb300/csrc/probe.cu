@@ -1,4 +1,4 @@
-// probe.cu -- FP64 pipe throughput probe used as the roofline denominator.
+// probe.cu -- pipe throughput probes used as roofline denominators.
 //
 // GB300 executes binary64 add/mul/fma at roughly two lanes per clock per SM;
 // this kernel measures that ceiling at the clocks of the calling run.  Each
@@ -36,19 +36,47 @@ __global__ void __launch_bounds__(256) fp64_probe_kernel(int iters, double* out)
     out[static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x] = s;
 }
 
+// The int8 tensor-pipe rate of the warp-level MMA the INT8 slicing form
+// uses: each warp issues `iters` rounds of 4 independent
+// mma.sync.m16n8k32.s8 (8192 int8 operations each).
+__global__ void __launch_bounds__(256) mma_s8_probe_kernel(int iters, double* out)
+{
+    const volatile double* pc = probe_constants;
+    unsigned a0 = threadIdx.x + static_cast<unsigned>(pc[0] > 2.0), a1 = a0 * 3u, a2 = a0 * 5u,
+             a3 = a0 * 7u, b0 = a0 * 11u, b1 = a0 * 13u;
+    int d[4][4] = {};
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            asm volatile(
+                "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+                "{%8,%9}, {%0,%1,%2,%3};\n"
+                : "+r"(d[c][0]), "+r"(d[c][1]), "+r"(d[c][2]), "+r"(d[c][3])
+                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+        }
+    }
+    int s = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s += d[c][j];
+    out[static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x] = static_cast<double>(s);
+}
+
 }  // namespace mpg
 
-extern "C" int mpgemm_fp64_probe(int kind, int blocks, int iters, double* out)
+extern "C" int mpgemm_peak_probe(int kind, int blocks, int iters, double* out)
 {
     using namespace mpg;
-    if (kind < 0 || kind > 2 || blocks < 1 || iters < 1 || !out)
-        return set_error(MPG_EINVAL, "mpgemm_fp64_probe: kind 0..2, blocks >= 1, iters >= 1, out non-NULL");
+    if (kind < 0 || kind > 3 || blocks < 1 || iters < 1 || !out)
+        return set_error(MPG_EINVAL, "mpgemm_peak_probe: kind 0..3, blocks >= 1, iters >= 1, out non-NULL");
     clear_error();
     cudaStream_t s = current_stream();
     switch (kind) {
     case 0: fp64_probe_kernel<0><<<blocks, 256, 0, s>>>(iters, out); break;
     case 1: fp64_probe_kernel<1><<<blocks, 256, 0, s>>>(iters, out); break;
-    default: fp64_probe_kernel<2><<<blocks, 256, 0, s>>>(iters, out); break;
+    case 2: fp64_probe_kernel<2><<<blocks, 256, 0, s>>>(iters, out); break;
+    default: mma_s8_probe_kernel<<<blocks, 256, 0, s>>>(iters, out); break;
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MPG_OK : set_error(MPG_ECUDA, cudaGetErrorString(e));

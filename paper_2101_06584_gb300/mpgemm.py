@@ -32,6 +32,14 @@ class Opts(ctypes.Structure):
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
+                ("A", ctypes.c_void_p * 4), ("lda", ctypes.c_int64),
+                ("B", ctypes.c_void_p * 4), ("ldb", ctypes.c_int64),
+                ("C", ctypes.c_void_p * 4), ("ldc", ctypes.c_int64),
+                ("trans_a", ctypes.c_int), ("trans_b", ctypes.c_int)]
+
+
 def lib():
     """The loaded library; raises if it has not been built."""
     global _lib
@@ -58,6 +66,15 @@ def _declare(L):
     L.mpgemm_workspace_size.argtypes = [i, ctypes.POINTER(Opts), i64, i64, i64]
     L.mpgemm_workspace_size.restype = ctypes.c_size_t
     L.mpgemm_dd_int8_static.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, i]
+    PP = ctypes.POINTER(Problem)
+    L.mpgemm_batch_workspace_size.argtypes = [i, i, PP]
+    L.mpgemm_batch_workspace_size.restype = ctypes.c_size_t
+    L.mpgemm_batch_plan_create.argtypes = [i, i, PP, i, vp, ctypes.c_size_t, ctypes.POINTER(vp)]
+    L.mpgemm_batch_run.argtypes = [vp]
+    L.mpgemm_batch_plan_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int64 * 4)]
+    L.mpgemm_batch_plan_destroy.argtypes = [vp]
+    L.mpgemm_batch_autotune.argtypes = [i, i, PP, vp, ctypes.c_size_t, i, ctypes.POINTER(i),
+                                        ctypes.POINTER(ctypes.c_float)]
     L.mpgemm_num_tiles.argtypes = [i]
     L.mpgemm_tile_info.argtypes = [i, i, ctypes.POINTER(ctypes.c_int * 6)]
     return L
@@ -83,7 +100,7 @@ def _require(t, name, P=None, ndim=None):
         raise ValueError("%s must have %d component planes, got %d" % (name, P, t.shape[0]))
     if ndim is not None and t.dim() != ndim:
         raise ValueError("%s must have %d dimensions" % (name, ndim))
-    if t.stride(-1) != 1:
+    if t.numel() > 0 and t.stride(-1) != 1:
         raise ValueError("%s planes must be row-major with unit column stride" % name)
 
 
@@ -94,7 +111,10 @@ def planes(t):
 
 
 def _ld(t):
-    return t.stride(1) if t.shape[1] > 1 else max(t.shape[2], 1)
+    """Leading dimension of the planes of t (rows apart, in elements)."""
+    if t.numel() == 0 or t.shape[1] <= 1:
+        return max(t.shape[2], 1)
+    return t.stride(1)
 
 
 def gemm(prec, A, B, out=None, trans_a=False, trans_b=False, algo="auto", split_k=0, tile=0,
@@ -198,11 +218,83 @@ def tile_info(prec, tile):
     return dict(zip(("bm", "bn", "bk", "tm", "tn", "threads"), list(info)))
 
 
-def fp64_probe(kind, blocks, iters, out):
-    """Launch the FP64 throughput probe (kind 0 add, 1 mul, 2 fma) writing to
-    ``out`` (a CUDA float64 tensor of blocks*256 elements)."""
+def peak_probe(kind, blocks, iters, out):
+    """Launch a throughput probe (kind 0 FP64 add, 1 mul, 2 fma, 3 mma.sync s8)
+    writing to ``out`` (a CUDA float64 tensor of blocks*256 elements)."""
     if out.numel() < blocks * 256 or not out.is_cuda or out.dtype != torch.float64:
         raise ValueError("out must be a CUDA float64 tensor of at least blocks*256 elements")
-    lib().mpgemm_fp64_probe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+    lib().mpgemm_peak_probe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
     _bind_stream()
-    check(lib().mpgemm_fp64_probe(int(kind), int(blocks), int(iters), out.data_ptr()))
+    check(lib().mpgemm_peak_probe(int(kind), int(blocks), int(iters), out.data_ptr()))
+
+
+def _problem(prec, A, B, C, trans_a=False, trans_b=False):
+    P = P_OF[prec]
+    for t, nm in ((A, "A"), (B, "B"), (C, "C")):
+        _require(t, nm, P, 3)
+    m, k = (A.shape[2], A.shape[1]) if trans_a else (A.shape[1], A.shape[2])
+    kb, n = (B.shape[2], B.shape[1]) if trans_b else (B.shape[1], B.shape[2])
+    if kb != k or tuple(C.shape[1:]) != (m, n):
+        raise ValueError("inconsistent problem shapes")
+    q = Problem()
+    q.m, q.n, q.k = m, n, k
+    for c in range(P):
+        q.A[c] = A[c].data_ptr()
+        q.B[c] = B[c].data_ptr()
+        q.C[c] = C[c].data_ptr()
+    q.lda, q.ldb, q.ldc = _ld(A), _ld(B), _ld(C)
+    q.trans_a, q.trans_b = int(trans_a), int(trans_b)
+    return q
+
+
+class BatchPlan:
+    """A batch of independent products (A_i, B_i, C_i) in precision ``prec``,
+    run as one persistent kernel replayed from a CUDA graph.  ``policy`` None
+    runs the library's autotuner first.  The tensors must stay alive while the
+    plan is used (the plan keeps references)."""
+
+    def __init__(self, prec, triples, policy=None, reps=3):
+        P = P_OF[prec]
+        self.P = P
+        self._keep = list(triples)
+        self._probs = (Problem * max(1, len(triples)))(*[_problem(prec, *t) for t in triples])
+        n = len(triples)
+        nbytes = lib().mpgemm_batch_workspace_size(P, n, self._probs)
+        dev = triples[0][0].device if triples else torch.device("cuda")
+        self.workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=dev)
+        self.tune_ms = None
+        _bind_stream()
+        if policy is None:
+            best = ctypes.c_int()
+            ms = ctypes.c_float()
+            check(lib().mpgemm_batch_autotune(P, n, self._probs, self.workspace.data_ptr(),
+                                              self.workspace.numel(), int(reps), ctypes.byref(best),
+                                              ctypes.byref(ms)))
+            policy = best.value
+            self.tune_ms = ms.value
+        self.policy = policy
+        h = ctypes.c_void_p()
+        check(lib().mpgemm_batch_plan_create(P, n, self._probs, int(policy),
+                                             self.workspace.data_ptr(), self.workspace.numel(),
+                                             ctypes.byref(h)))
+        self._h = h
+
+    def run(self):
+        _bind_stream()
+        check(lib().mpgemm_batch_run(self._h))
+
+    def info(self):
+        v = (ctypes.c_int64 * 4)()
+        check(lib().mpgemm_batch_plan_info(self._h, ctypes.byref(v)))
+        return dict(zip(("tiles", "grid", "policy", "count"), list(v)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mpgemm_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -135,3 +135,24 @@ def test_tile_table(L):
             assert bm % tm == 0 and bn % tn == 0 and (bm // tm) * (bn // tn) == threads
         info = (ctypes.c_int * 6)()
         assert L.mpgemm_tile_info(P, nt + 1, ctypes.byref(info)) == -1
+
+
+def test_batch_plan_rejects_bad_problem(L):
+    from paper_2101_06584_gb300.mpgemm import Problem
+    probs = (Problem * 2)()
+    for q in probs:
+        q.m, q.n, q.k = 8, 8, 8
+        q.lda, q.ldb, q.ldc = 8, 8, 8
+        for c in range(2):
+            q.A[c] = FAKE + c * (1 << 30)
+            q.B[c] = 2 * FAKE + c * (1 << 30)
+            q.C[c] = 3 * FAKE + c * (1 << 30)
+    probs[1].ldb = 4                                   # too small
+    h = ctypes.c_void_p()
+    rc = L.mpgemm_batch_plan_create(2, 2, probs, 0, ctypes.c_void_p(4 * FAKE), 1 << 20, ctypes.byref(h))
+    assert rc == -1 and "ldb" in err(L) and not h.value
+    rc = L.mpgemm_batch_plan_create(2, 2, probs, 7, ctypes.c_void_p(4 * FAKE), 1 << 20, ctypes.byref(h))
+    assert rc == -1 and "policy" in err(L)
+    rc = L.mpgemm_batch_plan_create(2, 2, probs, 0, ctypes.c_void_p(4 * FAKE + 8), 1 << 20, ctypes.byref(h))
+    assert rc == -3
+    assert L.mpgemm_batch_workspace_size(2, 2, probs) > 256
