@@ -45,6 +45,35 @@ UNIT = "mad/s"
 FP64_OPS_PER_MAD = {"dd": 20, "td": 128, "qd": 210}
 L2_FLUSH_BYTES = 256 << 20          # larger than the 129 MB L2
 INT8_SLICES = 13
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def kernel_source_hash():
+    """SHA-256 over the CUDA sources and the C header, in name order."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2101_06584_gb300", "csrc")
+    files = sorted(os.path.join(csrc, f) for f in os.listdir(csrc)) + [
+        os.path.join(ROOT, "include", "mpgemm.h")]
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(key):
+    """DRAM bytes per launch (read + write) recorded from an ncu capture of the
+    current kernel sources, or None when the sources changed since."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_sha256") != kernel_source_hash():
+        return None
+    ent = rec.get("kernels", {}).get(key)
+    return None if ent is None else ent.get("bytes_per_launch")
 
 
 def parse_args():
@@ -58,6 +87,14 @@ def parse_args():
     ap.add_argument("--size", type=int, default=None, help="override the workload's m = n = k")
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--record-traffic", metavar="NCU_CSV",
+                    help="record DRAM bytes per launch from an ncu --csv log (dram__bytes_read.sum, "
+                         "dram__bytes_write.sum) into profiles/traffic.json and exit")
+    ap.add_argument("--traffic-key", help="key to record under (e.g. td_qd_1024:qd)")
+    ap.add_argument("--kernel-regex", help="kernels of the log that make up one launch/call")
+    ap.add_argument("--per-call", type=int, default=1,
+                    help="matching launches per call (their bytes are summed)")
+    ap.add_argument("--command", default="", help="the ncu command, stored with the record")
     return ap.parse_args()
 
 
@@ -208,7 +245,8 @@ class TdQd(Workload):
         ach = ops / (statistics.mean(launch_ms["qd"]) * 1e-3)
         return {"bound": "alu", "kernel": "gemm_kseq_kernel<4,16,16,16,1,1> (QD)",
                 "achieved": ach / 1e12, "peak": pk["dfma"] / 1e12, "unit": "TFP64op/s",
-                "frac": ach / pk["dfma"], "traffic": None, "ops_per_unit": FP64_OPS_PER_MAD["qd"],
+                "frac": ach / pk["dfma"], "traffic": recorded_traffic("td_qd_%d:qd" % n),
+                "ops_per_unit": FP64_OPS_PER_MAD["qd"],
                 "unit_of_work": "QD multiply-add", "units_per_launch": n ** 3,
                 "peak_source": "measured FP64 FMA probe with register operands at this run's clocks",
                 "per_precision_mad_s": {p: n ** 3 / (statistics.mean(launch_ms[p]) * 1e-3)
@@ -307,7 +345,8 @@ class DdInt8(Workload):
         plain_ms = _time_call(self.torch, lambda: self.mm.gemm_plain("dd", self.A, self.B), 1)
         return {"bound": "tensor", "kernel": "ozaki_gemm_kernel (mma.sync m16n8k32 s8) incl. slicing",
                 "achieved": ach / 1e12, "peak": pk["mma_s8"] / 1e12, "unit": "Tint8op/s",
-                "frac": ach / pk["mma_s8"], "traffic": None, "ops_per_unit": 2 * pairs,
+                "frac": ach / pk["mma_s8"], "traffic": recorded_traffic("dd_int8_%d_s%d:call" % (n, S)),
+                "ops_per_unit": 2 * pairs,
                 "unit_of_work": "DD multiply-add (%d slice-pair int8 MACs)" % pairs,
                 "units_per_launch": n ** 3,
                 "peak_source": "measured mma.sync s8 probe at this run's clocks "
@@ -563,8 +602,44 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def record_traffic(args):
+    """Average DRAM bytes (read + write) per call of the kernels matching
+    --kernel-regex in an ncu CSV log, stored with the current source hash."""
+    import csv
+    import re
+    rows = list(csv.reader(open(args.record_traffic)))
+    hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    hdr = rows[hi]
+    ki, ii, mi, vi = (hdr.index("Kernel Name"), hdr.index("ID"), hdr.index("Metric Name"),
+                      hdr.index("Metric Value"))
+    per_launch = {}
+    pat = re.compile(args.kernel_regex)
+    for r in rows[hi + 1:]:
+        if len(r) > vi and pat.search(r[ki]) and r[mi] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            per_launch[r[ii]] = per_launch.get(r[ii], 0.0) + float(r[vi].replace(",", ""))
+    if not per_launch:
+        raise SystemExit("no matching launches with DRAM byte metrics in %s" % args.record_traffic)
+    calls = len(per_launch) / args.per_call
+    value = sum(per_launch.values()) / calls
+    try:
+        rec = json.load(open(TRAFFIC_FILE))
+    except (OSError, ValueError):
+        rec = {}
+    h = kernel_source_hash()
+    if rec.get("source_sha256") != h:
+        rec = {"source_sha256": h, "kernels": {}}
+    rec["kernels"][args.traffic_key] = {"bytes_per_launch": value, "launches": len(per_launch),
+                                        "per_call": args.per_call, "command": args.command}
+    with open(TRAFFIC_FILE, "w") as f:
+        json.dump(rec, f, indent=1)
+    print(json.dumps(rec["kernels"][args.traffic_key]))
+
+
 def main():
     args = parse_args()
+    if args.record_traffic:
+        record_traffic(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
