@@ -48,32 +48,36 @@ INT8_SLICES = 13
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 
-def kernel_source_hash():
-    """SHA-256 over the CUDA sources and the C header, in name order."""
+# the sources each recorded kernel is compiled from
+TRAFFIC_SOURCES = {
+    "td_qd": ["mp_arith.cuh", "gemm_kernel.cuh", "gemm_qd.cu", "internal.h"],
+    "dd_int8": ["mp_arith.cuh", "ozaki.cu", "ozaki.h", "internal.h"],
+}
+
+
+def kernel_source_hash(key):
+    """SHA-256 over the sources of the kernel recorded under `key`."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2101_06584_gb300", "csrc")
-    files = sorted(os.path.join(csrc, f) for f in os.listdir(csrc)) + [
-        os.path.join(ROOT, "include", "mpgemm.h")]
-    for f in files:
-        h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
+    for f in TRAFFIC_SOURCES[key.split("_")[0] + "_" + key.split("_")[1]]:
+        h.update(f.encode())
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
 def recorded_traffic(key):
     """DRAM bytes per launch (read + write) recorded from an ncu capture of the
-    current kernel sources, or None when the sources changed since."""
+    current kernel sources, or None when those sources changed since."""
     try:
         with open(TRAFFIC_FILE) as f:
-            rec = json.load(f)
+            ent = json.load(f).get(key)
     except (OSError, ValueError):
         return None
-    if rec.get("source_sha256") != kernel_source_hash():
+    if ent is None or ent.get("source_sha256") != kernel_source_hash(key):
         return None
-    ent = rec.get("kernels", {}).get(key)
-    return None if ent is None else ent.get("bytes_per_launch")
+    return ent.get("bytes_per_launch")
 
 
 def parse_args():
@@ -625,14 +629,12 @@ def record_traffic(args):
         rec = json.load(open(TRAFFIC_FILE))
     except (OSError, ValueError):
         rec = {}
-    h = kernel_source_hash()
-    if rec.get("source_sha256") != h:
-        rec = {"source_sha256": h, "kernels": {}}
-    rec["kernels"][args.traffic_key] = {"bytes_per_launch": value, "launches": len(per_launch),
-                                        "per_call": args.per_call, "command": args.command}
+    rec[args.traffic_key] = {"bytes_per_launch": value, "launches": len(per_launch),
+                             "per_call": args.per_call, "command": args.command,
+                             "source_sha256": kernel_source_hash(args.traffic_key)}
     with open(TRAFFIC_FILE, "w") as f:
         json.dump(rec, f, indent=1)
-    print(json.dumps(rec["kernels"][args.traffic_key]))
+    print(json.dumps(rec[args.traffic_key]))
 
 
 def main():
