@@ -110,13 +110,27 @@ def dist_env():
 
 
 def reduce_max(value, world):
+    """Max of a host-side value over ranks (timings only; no data path)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_rng(cfg, rank):
+    """The generator of rank `rank`'s independent problem for workload `cfg`
+    (rank 0 uses the workload's own seed)."""
+    from paper_2101_06584_gb300 import inputs as I
+    return np.random.Generator(np.random.PCG64(I.SEED_BASE + cfg + 1000 * rank))
+
+
+def aggregate_value(world, mads_per_step, steps, max_total_ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * mads_per_step * steps / (max_total_ms * 1e-3)
 
 
 def barrier(world):
@@ -216,7 +230,7 @@ class TdQd(Workload):
     def __init__(self, torch, mm, I, rank, n=1024):
         self.torch, self.mm, self.n = torch, mm, n
         self.precs = ("td", "qd")
-        rng = np.random.Generator(np.random.PCG64(I.SEED_BASE + 1 + 1000 * rank))
+        rng = replica_rng(1, rank)
         self.host = {}
         self.dev = {}
         for prec in self.precs:
@@ -288,7 +302,7 @@ class DdSmall(Workload):
 
     def __init__(self, torch, mm, I, rank, n=128):
         self.torch, self.mm, self.n = torch, mm, n
-        rng = np.random.Generator(np.random.PCG64(I.SEED_BASE + 0 + 1000 * rank))
+        rng = replica_rng(0, rank)
         self.A = torch.from_numpy(I.uniform(2, (n, n), rng)).cuda()
         self.B = torch.from_numpy(I.uniform(2, (n, n), rng)).cuda()
         self.C = torch.empty((2, n, n), dtype=torch.float64, device="cuda")
@@ -319,7 +333,7 @@ class DdInt8(Workload):
 
     def __init__(self, torch, mm, I, rank, n=4096, S=INT8_SLICES):
         self.torch, self.mm, self.n, self.S = torch, mm, n, S
-        rng = np.random.Generator(np.random.PCG64(I.SEED_BASE + 2 + 1000 * rank))
+        rng = replica_rng(2, rank)
         self.hA = I.uniform(2, (n, n), rng)
         self.hB = I.uniform(2, (n, n), rng)
         self.A = torch.from_numpy(self.hA).cuda()
@@ -363,7 +377,7 @@ class Batched(Workload):
 
     def __init__(self, torch, mm, I, rank, count=512):
         self.torch, self.mm = torch, mm
-        rng = np.random.Generator(np.random.PCG64(I.SEED_BASE + 3 + 1000 * rank))
+        rng = replica_rng(3, rank)
         self.shapes = I.batch_shapes(count, rng)
         self.plans = {}
         self.keep = []
@@ -413,7 +427,7 @@ class Autograd(Workload):
     def __init__(self, torch, mm, I, rank, n=2048):
         from paper_2101_06584_gb300.autograd import dd_matmul
         self.torch, self.mm, self.n, self.f = torch, mm, n, dd_matmul
-        rng = np.random.Generator(np.random.PCG64(I.SEED_BASE + 4 + 1000 * rank))
+        rng = replica_rng(4, rank)
         self.A = torch.from_numpy(I.uniform(2, (n, n), rng)).cuda().requires_grad_(True)
         self.B = torch.from_numpy(I.uniform(2, (n, n), rng)).cuda().requires_grad_(True)
         self.W = torch.from_numpy(I.uniform(2, (n, n), rng)).cuda()
@@ -508,7 +522,7 @@ def run_ours(args):
     kw = {} if args.size is None else {"n": args.size}
     w = WORKLOADS[args.workload](torch, mm, I, rank, **kw)
     total_ms, launch_ms, clocks, wall = measure(torch, w, args.steps, args.warmup, world, local, flush)
-    value = world * w.mads * args.steps / (total_ms * 1e-3)
+    value = aggregate_value(world, w.mads, args.steps, total_ms)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
