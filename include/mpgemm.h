@@ -135,8 +135,8 @@ typedef struct mpgemm_opts {
                        add in a fixed tree order (not bit-identical to k-sequential;
                        within the same error bound) */
     int slices;     /* INT8_OZAKI: slices per operand, 0 = default */
-    int tile;       /* FP64_EFT: tile configuration id 1..mpgemm_num_tiles(P); 0 or -1 =
-                       library choice */
+    int tile;       /* FP64_EFT: tile configuration id 1..mpgemm_num_tiles(P);
+                       INT8_OZAKI: slice-product tiling 1..5; 0 or -1 = library choice */
     void *workspace;          /* device scratch for algorithms that need it */
     size_t workspace_bytes;
 } mpgemm_opts;
@@ -160,8 +160,8 @@ int mpgemm_ex(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k,
  * The result is deterministic and bit-identical to those steps evaluated
  * anywhere; its error against the exact product shrinks by ~2^-7 per slice.
  * Needs opts->workspace: 256-byte aligned, mpgemm_workspace_size() bytes, not
- * overlapping A, B or C.  Layout (mp, np, kp = m, n, k rounded up to 64,
- * padding zero; each region starts on a 256-byte boundary):
+ * overlapping A, B or C.  Layout (mp, np = m, n rounded up to 64, kp = k
+ * rounded up to 128, padding zero; each region starts on a 256-byte boundary):
  *   int8  [S][mp][kp]  slices of op(A);   int8 [S][np][kp] slices of op(B)^T;
  *   int32 [mp] sigma;                     int32 [np] tau.
  * The workspace holds these values after the call. */

@@ -196,7 +196,9 @@ int ozaki_call<2>(const GemmArgs<2>& g, const mpgemm_opts* o)
             overlap(rw, plane_range(g.C[c], g.m, g.n, g.ldc)))
             return fail(MPG_EWORKSPACE, "workspace overlaps an operand");
     }
-    cudaError_t e = launch_ozaki_dd(g, S, o->workspace, g_stream);
+    const int variant = o->tile > 0 ? o->tile - 1 : 0;
+    if (variant > 4) return fail(MPG_EINVAL, "INT8 tile id %d out of range 1..5", o->tile);
+    cudaError_t e = launch_ozaki_dd(g, S, o->workspace, g_stream, variant);
     return e == cudaSuccess ? MPG_OK : cuda_fail(e, "INT8 slicing gemm launch");
 }
 

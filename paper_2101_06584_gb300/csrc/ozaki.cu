@@ -32,9 +32,8 @@ namespace mpg {
 
 namespace {
 
-constexpr int TILE = 64;         // CTA tile of C and k-step, in elements / bytes
-constexpr int SROW = TILE + 16;  // smem row stride in bytes (bank-conflict-free fragments)
-constexpr int STAGES = 3;
+constexpr int TILE = 64;         // padding granularity of the rows of op(A) and op(B)
+constexpr int KPAD = 128;        // padding granularity of k (the largest k-step)
 
 __device__ __forceinline__ uint64_t abs_bits(double x)
 {
@@ -304,107 +303,116 @@ struct Cursor {
     }
 };
 
-__global__ void __launch_bounds__(128) ozaki_gemm_kernel(const OzakiGemmArgs g)
+// CTA of WM x WN warps; each warp owns MT x NT fragments of 16 x 8 outputs,
+// so the CTA tile is (WM*MT*16) x (WN*NT*8).  Slice tiles of TILE bytes of k
+// are staged through a STG-deep cp.async pipeline.
+template <int MT, int NT, int WM, int WN, int STG, int MINB, int KS>
+__global__ void __launch_bounds__(WM * WN * 32, MINB) ozaki_gemm_kernel(const OzakiGemmArgs g)
 {
-    __shared__ __align__(16) int8_t As[STAGES][TILE * SROW];
-    __shared__ __align__(16) int8_t Bs[STAGES][TILE * SROW];
+    constexpr int NTHR = WM * WN * 32;
+    constexpr int BM = WM * MT * 16;
+    constexpr int BN = WN * NT * 8;
+    constexpr int SROW = KS + 16;     // smem row stride in bytes: conflict-free fragment loads
+    constexpr int CPR = KS / 16;      // 16-byte chunks per row
+    __shared__ __align__(16) int8_t As[STG][BM * SROW];
+    __shared__ __align__(16) int8_t Bs[STG][BN * SROW];
 
     const mp::Rn f = mp::make_rn();
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int gq = lane >> 2, tq = lane & 3;
-    const int wm = warp >> 1, wn = warp & 1;
-    const int64_t m0 = static_cast<int64_t>(blockIdx.y) * TILE;
-    const int64_t n0 = static_cast<int64_t>(blockIdx.x) * TILE;
+    const int wm = warp / WN, wn = warp % WN;
+    const int64_t m0 = static_cast<int64_t>(blockIdx.y) * BM;
+    const int64_t n0 = static_cast<int64_t>(blockIdx.x) * BN;
     const int S = g.S;
-    const int KT = static_cast<int>(g.kp / TILE);
+    const int KT = static_cast<int>(g.kp / KS);
     const int total = (S * (S + 1) / 2) * KT;
 
     // exponents of this thread's rows and columns
-    int sg[2][2], tu[4][2];
+    int sg[MT][2], tu[NT][2];
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
+    for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
-        for (int h = 0; h < 2; ++h) sg[mt][h] = g.sig[m0 + wm * 32 + mt * 16 + gq + h * 8];
+        for (int h = 0; h < 2; ++h) sg[mt][h] = g.sig[m0 + wm * MT * 16 + mt * 16 + gq + h * 8];
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
+    for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
-        for (int h = 0; h < 2; ++h) tu[nt][h] = g.tau[n0 + wn * 32 + nt * 8 + 2 * tq + h];
+        for (int h = 0; h < 2; ++h) tu[nt][h] = g.tau[n0 + wn * NT * 8 + nt * 8 + 2 * tq + h];
 
-    double acc0[2][4][4], acc1[2][4][4];
-    int ci[2][4][4];
+    double acc0[MT][NT][4], acc1[MT][NT][4];
+    int ci[MT][NT][4];
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
+    for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
+        for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
             for (int r = 0; r < 4; ++r) { acc0[mt][nt][r] = 0.0; acc1[mt][nt][r] = 0.0; ci[mt][nt][r] = 0; }
 
     auto load = [&](int stage, const Cursor& c) {
-        const int t = S + 1 - c.w + 0;            // unused helper to keep names clear
-        (void)t;
         const int8_t* a = g.sa + ((static_cast<int64_t>(c.s - 1) * g.mp + m0) * g.kp) +
-                          static_cast<int64_t>(c.kt) * TILE;
+                          static_cast<int64_t>(c.kt) * KS;
         const int8_t* b = g.sb + ((static_cast<int64_t>(c.w - c.s - 1) * g.np + n0) * g.kp) +
-                          static_cast<int64_t>(c.kt) * TILE;
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int chunk = tid + i * 128;      // 256 chunks of 16 B per operand
-            const int row = chunk >> 2, col = (chunk & 3) * 16;
-            cp_async16(&As[stage][row * SROW + col], a + static_cast<int64_t>(row) * g.kp + col);
-            cp_async16(&Bs[stage][row * SROW + col], b + static_cast<int64_t>(row) * g.kp + col);
+                          static_cast<int64_t>(c.kt) * KS;
+        // (BM + BN) rows of KS bytes in 16-byte chunks
+        for (int chunk = tid; chunk < (BM + BN) * CPR; chunk += NTHR) {
+            const int row = chunk / CPR, col = (chunk % CPR) * 16;
+            if (row < BM)
+                cp_async16(&As[stage][row * SROW + col], a + static_cast<int64_t>(row) * g.kp + col);
+            else
+                cp_async16(&Bs[stage][(row - BM) * SROW + col],
+                           b + static_cast<int64_t>(row - BM) * g.kp + col);
         }
     };
 
     Cursor ld{S + 1, 1, 0}, cm{S + 1, 1, 0};
 #pragma unroll
-    for (int st = 0; st < STAGES - 1; ++st) {
+    for (int st = 0; st < STG - 1; ++st) {
         if (st < total) load(st, ld);
         ld.advance(S, KT);
         cp_async_commit();
     }
 
     for (int it = 0; it < total; ++it) {
-        cp_async_wait<STAGES - 2>();
+        cp_async_wait<STG - 2>();
         __syncthreads();
         {
-            const int nxt = it + STAGES - 1;
-            if (nxt < total) load(nxt % STAGES, ld);
+            const int nxt = it + STG - 1;
+            if (nxt < total) load(nxt % STG, ld);
             ld.advance(S, KT);
             cp_async_commit();
         }
-        const int8_t* as = As[it % STAGES];
-        const int8_t* bs = Bs[it % STAGES];
+        const int8_t* as = As[it % STG];
+        const int8_t* bs = Bs[it % STG];
 #pragma unroll
-        for (int kk = 0; kk < TILE; kk += 32) {
-            uint32_t af[2][4], bf[4][2];
+        for (int kk = 0; kk < KS; kk += 32) {
+            uint32_t af[MT][4], bf[NT][2];
 #pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const int r = wm * 32 + mt * 16 + gq;
+            for (int mt = 0; mt < MT; ++mt) {
+                const int r = wm * MT * 16 + mt * 16 + gq;
                 af[mt][0] = *reinterpret_cast<const uint32_t*>(as + r * SROW + kk + 4 * tq);
                 af[mt][1] = *reinterpret_cast<const uint32_t*>(as + (r + 8) * SROW + kk + 4 * tq);
                 af[mt][2] = *reinterpret_cast<const uint32_t*>(as + r * SROW + kk + 16 + 4 * tq);
                 af[mt][3] = *reinterpret_cast<const uint32_t*>(as + (r + 8) * SROW + kk + 16 + 4 * tq);
             }
 #pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-                const int c = wn * 32 + nt * 8 + gq;
+            for (int nt = 0; nt < NT; ++nt) {
+                const int c = wn * NT * 8 + nt * 8 + gq;
                 bf[nt][0] = *reinterpret_cast<const uint32_t*>(bs + c * SROW + kk + 4 * tq);
                 bf[nt][1] = *reinterpret_cast<const uint32_t*>(bs + c * SROW + kk + 16 + 4 * tq);
             }
 #pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
+            for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
-                for (int nt = 0; nt < 4; ++nt) mma_s8(ci[mt][nt], af[mt], bf[nt]);
+                for (int nt = 0; nt < NT; ++nt) mma_s8(ci[mt][nt], af[mt], bf[nt]);
         }
         // end of a weight: fold its exact integer sums into the DD accumulators
         const int w = cm.w;
         cm.advance(S, KT);
         if (cm.w != w || it == total - 1) {
 #pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
+            for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
-                for (int nt = 0; nt < 4; ++nt)
+                for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
                         const int e = sg[mt][r >> 1] + tu[nt][r & 1] - 7 * w;
@@ -421,13 +429,13 @@ __global__ void __launch_bounds__(128) ozaki_gemm_kernel(const OzakiGemmArgs g)
     cp_async_wait<0>();
 
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
+    for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
+        for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                const int64_t row = m0 + wm * 32 + mt * 16 + gq + (r >> 1) * 8;
-                const int64_t col = n0 + wn * 32 + nt * 8 + 2 * tq + (r & 1);
+                const int64_t row = m0 + wm * MT * 16 + mt * 16 + gq + (r >> 1) * 8;
+                const int64_t col = n0 + wn * NT * 8 + nt * 8 + 2 * tq + (r & 1);
                 if (row < g.m && col < g.n) {
                     g.C0[row * g.ldc + col] = acc0[mt][nt][r];
                     g.C1[row * g.ldc + col] = acc1[mt][nt][r];
@@ -478,7 +486,7 @@ OzakiLayout ozaki_layout(int S, int64_t m, int64_t n, int64_t k)
     L.S = S;
     L.mp = round_up(m > 0 ? m : 1, TILE);
     L.np = round_up(n > 0 ? n : 1, TILE);
-    L.kp = round_up(k > 0 ? k : 1, TILE);
+    L.kp = round_up(k > 0 ? k : 1, KPAD);
     L.offA = 0;
     L.offB = round_up(static_cast<int64_t>(S) * L.mp * L.kp, 256);
     L.offSig = L.offB + round_up(static_cast<int64_t>(S) * L.np * L.kp, 256);
@@ -509,7 +517,7 @@ static cudaError_t slice_operand(const double* hi, const double* lo, int64_t cou
     return cudaGetLastError();
 }
 
-cudaError_t launch_ozaki_dd(const GemmArgs<2>& g, int S, void* ws, cudaStream_t s)
+cudaError_t launch_ozaki_dd(const GemmArgs<2>& g, int S, void* ws, cudaStream_t s, int variant)
 {
     const OzakiLayout L = ozaki_layout(S, g.m, g.n, g.k);
     int8_t* base = static_cast<int8_t*>(ws);
@@ -524,8 +532,34 @@ cudaError_t launch_ozaki_dd(const GemmArgs<2>& g, int S, void* ws, cudaStream_t 
     e = slice_operand(g.B[0], g.B[1], g.n, g.k, g.ldb, g.trans_b != 0, S, L.np, L.kp, sb, tau, s);
     if (e != cudaSuccess) return e;
     OzakiGemmArgs a{sa, sb, sig, tau, g.C[0], g.C[1], g.ldc, g.m, g.n, L.mp, L.np, L.kp, S};
-    const dim3 grid(static_cast<unsigned>(L.np / TILE), static_cast<unsigned>(L.mp / TILE));
-    ozaki_gemm_kernel<<<grid, 128, 0, s>>>(a);
+    // measured at DD 4096^3, S = 13 on GB300: 0 -> 88 ms, 1 -> 102, 2 -> 91.5, 3 -> 90, 4 -> 96
+    switch (variant) {
+    case 1: {   // 64 x 64 CTA tile, 4 warps of 32 x 32, 3 stages of 64 bytes
+        const dim3 grid(static_cast<unsigned>(L.np / 64), static_cast<unsigned>(L.mp / 64));
+        ozaki_gemm_kernel<2, 4, 2, 2, 3, 1, 64><<<grid, 128, 0, s>>>(a);
+        break;
+    }
+    case 2: {   // 64 x 32 CTA tile, 4 warps of 32 x 16, 4 stages of 64 bytes
+        const dim3 grid(static_cast<unsigned>(L.np / 32), static_cast<unsigned>(L.mp / 64));
+        ozaki_gemm_kernel<2, 2, 2, 2, 4, 4, 64><<<grid, 128, 0, s>>>(a);
+        break;
+    }
+    case 3: {   // 64 x 32 CTA tile, 4 warps of 16 x 32, 4 stages of 64 bytes
+        const dim3 grid(static_cast<unsigned>(L.np / 32), static_cast<unsigned>(L.mp / 64));
+        ozaki_gemm_kernel<1, 4, 4, 1, 4, 4, 64><<<grid, 128, 0, s>>>(a);
+        break;
+    }
+    case 4: {   // 64 x 64 CTA tile, 8 warps of 32 x 16, 4 stages of 64 bytes
+        const dim3 grid(static_cast<unsigned>(L.np / 64), static_cast<unsigned>(L.mp / 64));
+        ozaki_gemm_kernel<2, 2, 2, 4, 4, 2, 64><<<grid, 256, 0, s>>>(a);
+        break;
+    }
+    default: {  // 64 x 32 CTA tile, 4 warps of 32 x 16, 3 stages of 128 bytes
+        const dim3 grid(static_cast<unsigned>(L.np / 32), static_cast<unsigned>(L.mp / 64));
+        ozaki_gemm_kernel<2, 2, 2, 2, 3, 4, 128><<<grid, 128, 0, s>>>(a);
+        break;
+    }
+    }
     return cudaGetLastError();
 }
 

@@ -33,7 +33,7 @@ def _run(torch, A, B, S, trans_a=False, trans_b=False):
 
 def _layout(S, m, n, k):
     r = lambda x, q: (max(x, 1) + q - 1) // q * q
-    mp, np_, kp = r(m, 64), r(n, 64), r(k, 64)
+    mp, np_, kp = r(m, 64), r(n, 64), r(k, 128)
     offB = r(S * mp * kp, 256)
     offSig = offB + r(S * np_ * kp, 256)
     offTau = offSig + r(mp * 4, 256)
@@ -103,3 +103,20 @@ def test_full_size_sampled(torch):
     assert_bitwise(got, want, "int8 4096 sampled")
     err = X.gemm_error(C, A, B, [(i, j) for i in rows for j in cols])
     assert err["err_abs"] <= n * 2.0 ** -100, err
+
+
+def test_tile_variants_agree(torch):
+    """Both CTA tilings of the slice-product kernel give the same bits."""
+    from paper_2101_06584_gb300 import mpgemm as mm
+    rng = np.random.default_rng(630)
+    m, n, k = 150, 97, 200
+    A, B = I.ill_scaled(2, (m, k), rng), I.uniform(2, (k, n), rng)
+    Ad, Bd = dev(torch, A), dev(torch, B)
+    ws = torch.empty(mm.workspace_size("dd", m, n, k, algo="int8", slices=11), dtype=torch.uint8,
+                     device="cuda")
+    C1 = host(mm.gemm("dd", Ad, Bd, algo="int8", slices=11, workspace=ws, tile=1))
+    for tile in (2, 3, 4, 5):
+        C2 = host(mm.gemm("dd", Ad, Bd, algo="int8", slices=11, workspace=ws, tile=tile))
+        assert_bitwise(C1, C2, "tile variant %d" % tile)
+    want, _, _ = OZ.gemm(A, B, 11)
+    assert_bitwise(C1, want, "int8 vs oracle")
