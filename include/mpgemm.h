@@ -122,7 +122,8 @@ int mpgemm_qd(int64_t m, int64_t n, int64_t k,
 typedef enum mpg_algo {
     MPG_ALGO_AUTO = 0,       /* the FP64-EFT kernel (k-sequential unless split_k > 1) */
     MPG_ALGO_FP64_EFT = 1,   /* FP64 error-free transformations on the CUDA cores */
-    MPG_ALGO_INT8_OZAKI = 2  /* DD only: error-free INT8 slicing on the tensor cores */
+    MPG_ALGO_INT8_OZAKI = 2, /* DD only: error-free INT8 slicing on the tensor cores */
+    MPG_ALGO_BF16_SLICES = 3 /* DD only: the same slices as bf16 on the bf16 tensor path */
 } mpg_algo;
 
 /* Options of mpgemm_ex.  Zero-initialised options give the plain call. */
@@ -164,7 +165,15 @@ int mpgemm_ex(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k,
  * rounded up to 128, padding zero; each region starts on a 256-byte boundary):
  *   int8  [S][mp][kp]  slices of op(A);   int8 [S][np][kp] slices of op(B)^T;
  *   int32 [mp] sigma;                     int32 [np] tau.
- * The workspace holds these values after the call. */
+ * The workspace holds these values after the call.
+ *
+ * MPG_ALGO_BF16_SLICES (DD only; not in the paper): the same digits, scales,
+ * weight sums and accumulation, with the slice products on the bf16 tensor
+ * path (mma.sync m16n8k16, fp32 accumulation): the digits are exact in bf16,
+ * every product and partial sum is an integer, and the fp32 partial sums are
+ * moved into the int32 weight sums every 2048 values of k (so each stays
+ * below 2^23 and exact).  The result is bit-identical to MPG_ALGO_INT8_OZAKI.
+ * Workspace layout as above with 2-byte (bf16) digits in place of int8. */
 
 /* Bytes of workspace mpgemm_ex needs for these options and sizes (0 if none). */
 size_t mpgemm_workspace_size(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k);

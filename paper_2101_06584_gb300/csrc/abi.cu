@@ -166,7 +166,7 @@ template int check_gemm<4>(const GemmArgs<4>&);
 template <int P>
 static int ozaki_call(const GemmArgs<P>&, const mpgemm_opts*)
 {
-    return fail(MPG_EUNSUPPORTED, "the INT8 slicing form is provided for DD (P = 2) only");
+    return fail(MPG_EUNSUPPORTED, "the slicing forms are provided for DD (P = 2) only");
 }
 
 template <>
@@ -178,8 +178,9 @@ int ozaki_call<2>(const GemmArgs<2>& g, const mpgemm_opts* o)
     if (g.k > ozaki_k_limit(S))
         return fail(MPG_EUNSUPPORTED, "k = %lld exceeds %lld, the largest k whose %d-slice int32 "
                     "sums are exact", (long long)g.k, (long long)ozaki_k_limit(S), S);
-    const OzakiLayout L = ozaki_layout(S, g.m, g.n, g.k);
-    if (L.mp / 64 > 65535) return fail(MPG_EINVAL, "m too large for the INT8 form's grid");
+    const int engine = o->algo == MPG_ALGO_BF16_SLICES ? 1 : 0;
+    const OzakiLayout L = ozaki_layout(S, g.m, g.n, g.k, engine == 1 ? 2 : 1);
+    if (L.mp / 64 > 65535) return fail(MPG_EINVAL, "m too large for the slicing form's grid");
     if (!o->workspace) return fail(MPG_EWORKSPACE, "the INT8 form needs a workspace of %lld bytes",
                                    (long long)L.total);
     if (reinterpret_cast<uintptr_t>(o->workspace) % 256)
@@ -198,7 +199,7 @@ int ozaki_call<2>(const GemmArgs<2>& g, const mpgemm_opts* o)
     }
     const int variant = o->tile > 0 ? o->tile - 1 : 0;
     if (variant > 4) return fail(MPG_EINVAL, "INT8 tile id %d out of range 1..5", o->tile);
-    cudaError_t e = launch_ozaki_dd(g, S, o->workspace, g_stream, variant);
+    cudaError_t e = launch_ozaki_dd(g, S, o->workspace, g_stream, variant, engine);
     return e == cudaSuccess ? MPG_OK : cuda_fail(e, "INT8 slicing gemm launch");
 }
 
@@ -222,16 +223,18 @@ static int gemm_call(const mpgemm_opts* o, int64_t m, int64_t n, int64_t k,
     if (rc != MPG_OK) return rc;
     if (m == 0 || n == 0) return MPG_OK;
     const int algo = o ? o->algo : MPG_ALGO_AUTO;
-    if (algo != MPG_ALGO_AUTO && algo != MPG_ALGO_FP64_EFT && algo != MPG_ALGO_INT8_OZAKI)
+    if (algo != MPG_ALGO_AUTO && algo != MPG_ALGO_FP64_EFT && algo != MPG_ALGO_INT8_OZAKI &&
+        algo != MPG_ALGO_BF16_SLICES)
         return fail(MPG_EINVAL, "unknown algorithm %d", algo);
-    if (algo == MPG_ALGO_INT8_OZAKI && P != 2)
-        return fail(MPG_EUNSUPPORTED, "the INT8 slicing form is provided for DD (P = 2) only");
+    const bool sliced = algo == MPG_ALGO_INT8_OZAKI || algo == MPG_ALGO_BF16_SLICES;
+    if (sliced && P != 2)
+        return fail(MPG_EUNSUPPORTED, "the slicing forms are provided for DD (P = 2) only");
     cudaError_t e;
     if (k == 0) {
         e = launch_zero<P>(g, g_stream);
         return e == cudaSuccess ? MPG_OK : cuda_fail(e, "zero launch");
     }
-    if (algo == MPG_ALGO_INT8_OZAKI) return ozaki_call(g, o);
+    if (sliced) return ozaki_call(g, o);
     const int split = o ? o->split_k : 0;
     if (split > 1) {
         if (split != 2 && split != 4 && split != 8 && split != 16 && split != 32)
@@ -315,10 +318,12 @@ int mpgemm_ex(int P, const mpgemm_opts* opts, int64_t m, int64_t n, int64_t k,
 
 size_t mpgemm_workspace_size(int P, const mpgemm_opts* opts, int64_t m, int64_t n, int64_t k)
 {
-    if (!opts || opts->algo != MPG_ALGO_INT8_OZAKI || P != 2 || m < 0 || n < 0 || k < 0) return 0;
+    if (!opts || (opts->algo != MPG_ALGO_INT8_OZAKI && opts->algo != MPG_ALGO_BF16_SLICES) || P != 2 ||
+        m < 0 || n < 0 || k < 0)
+        return 0;
     const int S = opts->slices ? opts->slices : kOzakiDefaultSlices;
     if (S < 1 || S > kOzakiMaxSlices) return 0;
-    return static_cast<size_t>(ozaki_layout(S, m, n, k).total);
+    return static_cast<size_t>(ozaki_layout(S, m, n, k, opts->algo == MPG_ALGO_BF16_SLICES ? 2 : 1).total);
 }
 
 int mpgemm_dd_int8_static(int64_t m, int64_t n, int64_t k, const double* const A[2], int64_t lda,

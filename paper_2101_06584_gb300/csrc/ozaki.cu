@@ -25,6 +25,8 @@
 #include "mp_arith.cuh"
 #include "ozaki.h"
 
+#include <cuda_bf16.h>
+
 #include <cstdint>
 #include <mutex>
 
@@ -170,12 +172,43 @@ __global__ void ozaki_fill_int(int* out, int64_t from, int64_t to)
 
 // ------------------------------------------------------------------ slice
 
+// Slice storage: int8 digits for the int8 tensor path, or the same digits as
+// bf16 (exact: |d| <= 64 needs 7 bits of significand) for the bf16 path.
+template <typename T> struct DigitStore;
+template <> struct DigitStore<int8_t> {
+    static __device__ __forceinline__ uint32_t bits(int8_t d) { return static_cast<uint8_t>(d); }
+    static constexpr int kBits = 8;
+};
+template <> struct DigitStore<uint16_t> {
+    static __device__ __forceinline__ uint32_t bits(int8_t d)
+    {
+        return __bfloat16_as_ushort(__float2bfloat16_rn(static_cast<float>(d)));
+    }
+    static constexpr int kBits = 16;
+};
+
+// Four consecutive digits packed little-endian and stored at out (4 * sizeof(T) bytes).
+template <typename T>
+__device__ __forceinline__ void store4(T* out, int8_t d0, int8_t d1, int8_t d2, int8_t d3)
+{
+    if constexpr (sizeof(T) == 1) {
+        *reinterpret_cast<uint32_t*>(out) = DigitStore<T>::bits(d0) | (DigitStore<T>::bits(d1) << 8) |
+                                            (DigitStore<T>::bits(d2) << 16) | (DigitStore<T>::bits(d3) << 24);
+    } else {
+        uint2 v;
+        v.x = DigitStore<T>::bits(d0) | (DigitStore<T>::bits(d1) << 16);
+        v.y = DigitStore<T>::bits(d2) | (DigitStore<T>::bits(d3) << 16);
+        *reinterpret_cast<uint2*>(out) = v;
+    }
+}
+
 // Rows of the sliced operand are contiguous in memory (element (r, p) at
 // base[r*ld + p]).  One thread per 4 consecutive p; rows up to `rows_pad`,
 // columns up to kp, zero outside [rows) x [len).
+template <typename T>
 __global__ void ozaki_slice_rows(const double* __restrict__ hi, const double* __restrict__ lo,
                                  int64_t rows, int64_t len, int64_t ld, const int* __restrict__ sig,
-                                 int S, int64_t rows_pad, int64_t kp, int8_t* __restrict__ out)
+                                 int S, int64_t rows_pad, int64_t kp, T* __restrict__ out)
 {
     const int64_t quads = kp / 4;
     const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -193,22 +226,19 @@ __global__ void ozaki_slice_rows(const double* __restrict__ hi, const double* __
             for (int s = 0; s < S; ++s) dg[u][s] = 0;
         }
     }
-    for (int s = 0; s < S; ++s) {
-        const uint32_t w = static_cast<uint32_t>(static_cast<uint8_t>(dg[0][s])) |
-                           (static_cast<uint32_t>(static_cast<uint8_t>(dg[1][s])) << 8) |
-                           (static_cast<uint32_t>(static_cast<uint8_t>(dg[2][s])) << 16) |
-                           (static_cast<uint32_t>(static_cast<uint8_t>(dg[3][s])) << 24);
-        *reinterpret_cast<uint32_t*>(out + (static_cast<int64_t>(s) * rows_pad + r) * kp + p0) = w;
-    }
+    for (int s = 0; s < S; ++s)
+        store4(out + (static_cast<int64_t>(s) * rows_pad + r) * kp + p0, dg[0][s], dg[1][s], dg[2][s],
+               dg[3][s]);
 }
 
 // Rows of the sliced operand are strided (element (r, p) at base[p*ld + r]):
 // a 32 x 32 tile is read with r fastest, sliced, transposed through shared
 // memory and written with p fastest.
+template <typename T>
 __global__ void __launch_bounds__(256)
 ozaki_slice_cols(const double* __restrict__ hi, const double* __restrict__ lo, int64_t rows,
                  int64_t len, int64_t ld, const int* __restrict__ sig, int S, int64_t rows_pad,
-                 int64_t kp, int8_t* __restrict__ out)
+                 int64_t kp, T* __restrict__ out)
 {
     __shared__ int8_t tile[16][32][36];
     const int64_t r0 = static_cast<int64_t>(blockIdx.x) * 32;
@@ -233,14 +263,9 @@ ozaki_slice_cols(const double* __restrict__ hi, const double* __restrict__ lo, i
     const int wq = (threadIdx.x & 7) * 4;   // p offset
     const int64_t row = r0 + wr;
     if (row < rows_pad && p0 + wq < kp) {
-        for (int s = 0; s < S; ++s) {
-            const uint32_t w = static_cast<uint32_t>(static_cast<uint8_t>(tile[s][wr][wq])) |
-                               (static_cast<uint32_t>(static_cast<uint8_t>(tile[s][wr][wq + 1])) << 8) |
-                               (static_cast<uint32_t>(static_cast<uint8_t>(tile[s][wr][wq + 2])) << 16) |
-                               (static_cast<uint32_t>(static_cast<uint8_t>(tile[s][wr][wq + 3])) << 24);
-            *reinterpret_cast<uint32_t*>(out + (static_cast<int64_t>(s) * rows_pad + row) * kp +
-                                         p0 + wq) = w;
-        }
+        for (int s = 0; s < S; ++s)
+            store4(out + (static_cast<int64_t>(s) * rows_pad + row) * kp + p0 + wq, tile[s][wr][wq],
+                   tile[s][wr][wq + 1], tile[s][wr][wq + 2], tile[s][wr][wq + 3]);
     }
 }
 
@@ -279,8 +304,8 @@ __device__ __forceinline__ double scaled_int(int v, int e)
 }
 
 struct OzakiGemmArgs {
-    const int8_t* sa;   // [S][mp][kp]
-    const int8_t* sb;   // [S][np][kp]
+    const void* sa;     // [S][mp][kp] digits (int8 or bf16)
+    const void* sb;     // [S][np][kp]
     const int* sig;     // [mp]
     const int* tau;     // [np]
     double* C0;
@@ -349,10 +374,10 @@ __global__ void __launch_bounds__(WM * WN * 32, MINB) ozaki_gemm_kernel(const Oz
             for (int r = 0; r < 4; ++r) { acc0[mt][nt][r] = 0.0; acc1[mt][nt][r] = 0.0; ci[mt][nt][r] = 0; }
 
     auto load = [&](int stage, const Cursor& c) {
-        const int8_t* a = g.sa + ((static_cast<int64_t>(c.s - 1) * g.mp + m0) * g.kp) +
-                          static_cast<int64_t>(c.kt) * KS;
-        const int8_t* b = g.sb + ((static_cast<int64_t>(c.w - c.s - 1) * g.np + n0) * g.kp) +
-                          static_cast<int64_t>(c.kt) * KS;
+        const int8_t* a = static_cast<const int8_t*>(g.sa) +
+                          ((static_cast<int64_t>(c.s - 1) * g.mp + m0) * g.kp) + static_cast<int64_t>(c.kt) * KS;
+        const int8_t* b = static_cast<const int8_t*>(g.sb) +
+                          ((static_cast<int64_t>(c.w - c.s - 1) * g.np + n0) * g.kp) + static_cast<int64_t>(c.kt) * KS;
         // (BM + BN) rows of KS bytes in 16-byte chunks
         for (int chunk = tid; chunk < (BM + BN) * CPR; chunk += NTHR) {
             const int row = chunk / CPR, col = (chunk % CPR) * 16;
@@ -443,6 +468,177 @@ __global__ void __launch_bounds__(WM * WN * 32, MINB) ozaki_gemm_kernel(const Oz
             }
 }
 
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// The same weight sums with the digits as bf16 on the bf16 tensor path
+// (mma.sync m16n8k16, fp32 accumulation).  On GB300 this runs no faster than
+// the int8 kernel (DD 4096^3, S = 13: 89.7 vs 87.8 ms): at the bf16 rate its
+// fragment loads would need ~185 B/clk/SM of shared memory, more than the SM
+// delivers, and larger warp tiles do not fit beside the DD accumulators.  Every product is an integer of at
+// most 2^12 and every partial sum an integer; the fp32 fragments are drained
+// into the int32 weight sums every 2048 values of k, so no partial sum exceeds
+// 2^23 and each is exactly representable: the int32 sums, and so the result,
+// equal those of the int8 path bit for bit.
+template <int MT, int NT, int WM, int WN, int STG, int MINB, int KSE>
+__global__ void __launch_bounds__(WM * WN * 32, MINB) ozaki_gemm_bf16_kernel(const OzakiGemmArgs g)
+{
+    constexpr int NTHR = WM * WN * 32;
+    constexpr int BM = WM * MT * 16;
+    constexpr int BN = WN * NT * 8;
+    constexpr int SROWE = KSE + 8;        // row stride in elements: conflict-free fragment loads
+    constexpr int CPR = KSE * 2 / 16;     // 16-byte chunks per row
+    constexpr int FLUSH = 2048 / KSE;     // k-tiles between drains of the fp32 fragments
+    __shared__ __align__(16) uint16_t As[STG][BM * SROWE];
+    __shared__ __align__(16) uint16_t Bs[STG][BN * SROWE];
+
+    const mp::Rn f = mp::make_rn();
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int gq = lane >> 2, tq = lane & 3;
+    const int wm = warp / WN, wn = warp % WN;
+    const int64_t m0 = static_cast<int64_t>(blockIdx.y) * BM;
+    const int64_t n0 = static_cast<int64_t>(blockIdx.x) * BN;
+    const int S = g.S;
+    const int KT = static_cast<int>(g.kp / KSE);
+    const int total = (S * (S + 1) / 2) * KT;
+
+    int sg[MT][2], tu[NT][2];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) sg[mt][h] = g.sig[m0 + wm * MT * 16 + mt * 16 + gq + h * 8];
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) tu[nt][h] = g.tau[n0 + wn * NT * 8 + nt * 8 + 2 * tq + h];
+
+    double acc0[MT][NT][4], acc1[MT][NT][4];
+    float cf[MT][NT][4];
+    int ci[MT][NT][4];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                acc0[mt][nt][r] = 0.0; acc1[mt][nt][r] = 0.0; cf[mt][nt][r] = 0.f; ci[mt][nt][r] = 0;
+            }
+
+    auto load = [&](int stage, const Cursor& c) {
+        const uint16_t* a = static_cast<const uint16_t*>(g.sa) +
+                            ((static_cast<int64_t>(c.s - 1) * g.mp + m0) * g.kp) + static_cast<int64_t>(c.kt) * KSE;
+        const uint16_t* b = static_cast<const uint16_t*>(g.sb) +
+                            ((static_cast<int64_t>(c.w - c.s - 1) * g.np + n0) * g.kp) + static_cast<int64_t>(c.kt) * KSE;
+        for (int chunk = tid; chunk < (BM + BN) * CPR; chunk += NTHR) {
+            const int row = chunk / CPR, col = (chunk % CPR) * 8;
+            if (row < BM)
+                cp_async16(&As[stage][row * SROWE + col], a + static_cast<int64_t>(row) * g.kp + col);
+            else
+                cp_async16(&Bs[stage][(row - BM) * SROWE + col],
+                           b + static_cast<int64_t>(row - BM) * g.kp + col);
+        }
+    };
+
+    Cursor ld{S + 1, 1, 0}, cm{S + 1, 1, 0};
+#pragma unroll
+    for (int st = 0; st < STG - 1; ++st) {
+        if (st < total) load(st, ld);
+        ld.advance(S, KT);
+        cp_async_commit();
+    }
+
+    int since = 0;
+    for (int it = 0; it < total; ++it) {
+        cp_async_wait<STG - 2>();
+        __syncthreads();
+        {
+            const int nxt = it + STG - 1;
+            if (nxt < total) load(nxt % STG, ld);
+            ld.advance(S, KT);
+            cp_async_commit();
+        }
+        const uint16_t* as = As[it % STG];
+        const uint16_t* bs = Bs[it % STG];
+#pragma unroll
+        for (int kk = 0; kk < KSE; kk += 16) {
+            uint32_t af[MT][4], bf[NT][2];
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+                const int r = wm * MT * 16 + mt * 16 + gq;
+                af[mt][0] = *reinterpret_cast<const uint32_t*>(as + r * SROWE + kk + 2 * tq);
+                af[mt][1] = *reinterpret_cast<const uint32_t*>(as + (r + 8) * SROWE + kk + 2 * tq);
+                af[mt][2] = *reinterpret_cast<const uint32_t*>(as + r * SROWE + kk + 8 + 2 * tq);
+                af[mt][3] = *reinterpret_cast<const uint32_t*>(as + (r + 8) * SROWE + kk + 8 + 2 * tq);
+            }
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                const int c = wn * NT * 8 + nt * 8 + gq;
+                bf[nt][0] = *reinterpret_cast<const uint32_t*>(bs + c * SROWE + kk + 2 * tq);
+                bf[nt][1] = *reinterpret_cast<const uint32_t*>(bs + c * SROWE + kk + 8 + 2 * tq);
+            }
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) mma_bf16(cf[mt][nt], af[mt], bf[nt]);
+        }
+        const int w = cm.w;
+        cm.advance(S, KT);
+        const bool weight_end = (cm.w != w || it == total - 1);
+        if (++since == FLUSH || weight_end) {
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        ci[mt][nt][r] += __float2int_rn(cf[mt][nt][r]);
+                        cf[mt][nt][r] = 0.f;
+                    }
+            since = 0;
+        }
+        if (weight_end) {
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int e = sg[mt][r >> 1] + tu[nt][r & 1] - 7 * w;
+                        const double x[2] = {acc0[mt][nt][r], acc1[mt][nt][r]};
+                        const double y[2] = {scaled_int(ci[mt][nt][r], e), f.zero};
+                        double z[2];
+                        mp::dd_add(f, x, y, z);
+                        acc0[mt][nt][r] = z[0];
+                        acc1[mt][nt][r] = z[1];
+                        ci[mt][nt][r] = 0;
+                    }
+        }
+    }
+    cp_async_wait<0>();
+
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int64_t row = m0 + wm * MT * 16 + mt * 16 + gq + (r >> 1) * 8;
+                const int64_t col = n0 + wn * NT * 8 + nt * 8 + 2 * tq + (r & 1);
+                if (row < g.m && col < g.n) {
+                    g.C0[row * g.ldc + col] = acc0[mt][nt][r];
+                    g.C1[row * g.ldc + col] = acc1[mt][nt][r];
+                }
+            }
+}
+
 // ------------------------------------------------------- fixed scratch
 
 // Scratch for callers that cannot allocate device memory (see
@@ -480,7 +676,7 @@ cudaError_t ozaki_static_scratch(void** out)
 
 static int64_t round_up(int64_t x, int64_t r) { return (x + r - 1) / r * r; }
 
-OzakiLayout ozaki_layout(int S, int64_t m, int64_t n, int64_t k)
+OzakiLayout ozaki_layout(int S, int64_t m, int64_t n, int64_t k, int elem_bytes)
 {
     OzakiLayout L;
     L.S = S;
@@ -488,8 +684,8 @@ OzakiLayout ozaki_layout(int S, int64_t m, int64_t n, int64_t k)
     L.np = round_up(n > 0 ? n : 1, TILE);
     L.kp = round_up(k > 0 ? k : 1, KPAD);
     L.offA = 0;
-    L.offB = round_up(static_cast<int64_t>(S) * L.mp * L.kp, 256);
-    L.offSig = L.offB + round_up(static_cast<int64_t>(S) * L.np * L.kp, 256);
+    L.offB = round_up(static_cast<int64_t>(S) * L.mp * L.kp * elem_bytes, 256);
+    L.offSig = L.offB + round_up(static_cast<int64_t>(S) * L.np * L.kp * elem_bytes, 256);
     L.offTau = L.offSig + round_up(L.mp * 4, 256);
     L.total = L.offTau + round_up(L.np * 4, 256);
     return L;
@@ -499,40 +695,60 @@ static unsigned blocks_for(int64_t threads, int per) { return static_cast<unsign
 
 // Slice one operand: vectors (rows of op(A) or columns of op(B)) of length
 // len; `contig` says whether a vector's elements are adjacent in memory.
+template <typename T>
 static cudaError_t slice_operand(const double* hi, const double* lo, int64_t count, int64_t len,
                                  int64_t ld, bool contig, int S, int64_t count_pad, int64_t kp,
-                                 int8_t* out, int* sig, cudaStream_t s)
+                                 T* out, int* sig, cudaStream_t s)
 {
     if (contig) ozaki_scale_contig<<<blocks_for(count * 32, 256), 256, 0, s>>>(hi, count, len, ld, sig);
     else ozaki_scale_strided<<<blocks_for(count, 256), 256, 0, s>>>(hi, count, len, ld, sig);
     if (count_pad > count)
         ozaki_fill_int<<<blocks_for(count_pad - count, 256), 256, 0, s>>>(sig, count, count_pad);
     if (contig) {
-        ozaki_slice_rows<<<blocks_for(count_pad * (kp / 4), 128), 128, 0, s>>>(hi, lo, count, len, ld,
-                                                                               sig, S, count_pad, kp, out);
+        ozaki_slice_rows<T><<<blocks_for(count_pad * (kp / 4), 128), 128, 0, s>>>(
+            hi, lo, count, len, ld, sig, S, count_pad, kp, out);
     } else {
         const dim3 grid(static_cast<unsigned>(count_pad / 32), static_cast<unsigned>(kp / 32));
-        ozaki_slice_cols<<<grid, 256, 0, s>>>(hi, lo, count, len, ld, sig, S, count_pad, kp, out);
+        ozaki_slice_cols<T><<<grid, 256, 0, s>>>(hi, lo, count, len, ld, sig, S, count_pad, kp, out);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_ozaki_dd(const GemmArgs<2>& g, int S, void* ws, cudaStream_t s, int variant)
+cudaError_t launch_ozaki_dd(const GemmArgs<2>& g, int S, void* ws, cudaStream_t s, int variant,
+                            int engine)
 {
-    const OzakiLayout L = ozaki_layout(S, g.m, g.n, g.k);
+    const int eb = engine == 1 ? 2 : 1;
+    const OzakiLayout L = ozaki_layout(S, g.m, g.n, g.k, eb);
     int8_t* base = static_cast<int8_t*>(ws);
-    int8_t* sa = base + L.offA;
-    int8_t* sb = base + L.offB;
     int* sig = reinterpret_cast<int*>(base + L.offSig);
     int* tau = reinterpret_cast<int*>(base + L.offTau);
-    // op(A) row i: contiguous unless A is stored transposed
-    cudaError_t e = slice_operand(g.A[0], g.A[1], g.m, g.k, g.lda, !g.trans_a, S, L.mp, L.kp, sa, sig, s);
+    cudaError_t e;
+    // op(A) row i: contiguous unless A is stored transposed; op(B) column j:
+    // contiguous only if B is stored transposed
+    if (engine == 1) {
+        uint16_t* sa = reinterpret_cast<uint16_t*>(base + L.offA);
+        uint16_t* sb = reinterpret_cast<uint16_t*>(base + L.offB);
+        e = slice_operand(g.A[0], g.A[1], g.m, g.k, g.lda, !g.trans_a, S, L.mp, L.kp, sa, sig, s);
+        if (e == cudaSuccess)
+            e = slice_operand(g.B[0], g.B[1], g.n, g.k, g.ldb, g.trans_b != 0, S, L.np, L.kp, sb, tau, s);
+    } else {
+        int8_t* sa = base + L.offA;
+        int8_t* sb = base + L.offB;
+        e = slice_operand(g.A[0], g.A[1], g.m, g.k, g.lda, !g.trans_a, S, L.mp, L.kp, sa, sig, s);
+        if (e == cudaSuccess)
+            e = slice_operand(g.B[0], g.B[1], g.n, g.k, g.ldb, g.trans_b != 0, S, L.np, L.kp, sb, tau, s);
+    }
     if (e != cudaSuccess) return e;
-    // op(B) column j: contiguous only if B is stored transposed
-    e = slice_operand(g.B[0], g.B[1], g.n, g.k, g.ldb, g.trans_b != 0, S, L.np, L.kp, sb, tau, s);
-    if (e != cudaSuccess) return e;
-    OzakiGemmArgs a{sa, sb, sig, tau, g.C[0], g.C[1], g.ldc, g.m, g.n, L.mp, L.np, L.kp, S};
-    // measured at DD 4096^3, S = 13 on GB300: 0 -> 88 ms, 1 -> 102, 2 -> 91.5, 3 -> 90, 4 -> 96
+    OzakiGemmArgs a{base + L.offA, base + L.offB, sig, tau, g.C[0], g.C[1], g.ldc, g.m, g.n,
+                    L.mp, L.np, L.kp, S};
+    if (engine == 1) {
+        // 64 x 32 CTA tile, 4 warps of 32 x 16, 3 stages of 64 bf16
+        const dim3 grid(static_cast<unsigned>(L.np / 32), static_cast<unsigned>(L.mp / 64));
+        ozaki_gemm_bf16_kernel<2, 2, 2, 2, 3, 3, 64><<<grid, 128, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+    // int8 tilings, measured at DD 4096^3, S = 13 on GB300: 0 -> 88 ms, 1 -> 102, 2 -> 91.5,
+    // 3 -> 90, 4 -> 96
     switch (variant) {
     case 1: {   // 64 x 64 CTA tile, 4 warps of 32 x 32, 3 stages of 64 bytes
         const dim3 grid(static_cast<unsigned>(L.np / 64), static_cast<unsigned>(L.mp / 64));

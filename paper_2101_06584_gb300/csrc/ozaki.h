@@ -13,13 +13,16 @@ struct OzakiLayout {
     int64_t mp, np, kp;
     int64_t offA, offB, offSig, offTau, total;
 };
-OzakiLayout ozaki_layout(int S, int64_t m, int64_t n, int64_t k);
+// elem_bytes: 1 for int8 digits, 2 for bf16 digits
+OzakiLayout ozaki_layout(int S, int64_t m, int64_t n, int64_t k, int elem_bytes = 1);
 
 // Largest k for which the int32 weight sums are exact: S * k * 64 * 64 < 2^31.
 inline int64_t ozaki_k_limit(int S) { return (2147483647LL) / (static_cast<int64_t>(S) * 64 * 64); }
 
-// variant 0..4: CTA tilings of the slice-product kernel (0 is the default)
-cudaError_t launch_ozaki_dd(const GemmArgs<2>& g, int S, void* ws, cudaStream_t s, int variant = 0);
+// engine 0: int8 digits on mma.sync s8 (variant 0..4 selects the CTA tiling, 0
+// the default); engine 1: bf16 digits on mma.sync bf16
+cudaError_t launch_ozaki_dd(const GemmArgs<2>& g, int S, void* ws, cudaStream_t s, int variant = 0,
+                            int engine = 0);
 
 // Size of the library's fixed scratch array and its device address on the
 // current device (looked up on first use per device).

@@ -120,3 +120,62 @@ def test_tile_variants_agree(torch):
         assert_bitwise(C1, C2, "tile variant %d" % tile)
     want, _, _ = OZ.gemm(A, B, 11)
     assert_bitwise(C1, want, "int8 vs oracle")
+
+
+def test_bf16_path_matches_int8(torch):
+    """The bf16 tensor path computes the same integer weight sums: its result
+    equals the int8 path's and the oracle's bit for bit (ragged shape,
+    ill-scaled operands, transposed B)."""
+    from paper_2101_06584_gb300 import mpgemm as mm
+    rng = np.random.default_rng(640)
+    m, n, k = 131, 70, 300
+    A, B = I.ill_scaled(2, (m, k), rng), I.uniform(2, (k, n), rng)
+    Ad, Bt = dev(torch, A), dev(torch, B.transpose(0, 2, 1))
+    S = 12
+    ws = torch.empty(mm.workspace_size("dd", m, n, k, algo="bf16", slices=S), dtype=torch.uint8,
+                     device="cuda")
+    Cb = host(mm.gemm("dd", Ad, Bt, trans_b=True, algo="bf16", slices=S, workspace=ws))
+    Ci = host(mm.gemm("dd", Ad, Bt, trans_b=True, algo="int8", slices=S, workspace=ws))
+    assert_bitwise(Cb, Ci, "bf16 vs int8")
+    want, _, _ = OZ.gemm(A, B, S)
+    assert_bitwise(Cb, want, "bf16 vs oracle")
+
+
+def test_bf16_partial_sums_at_the_drain_limit(torch):
+    """Constant operands whose first digits are all 64: the (1, 1) slice pair
+    sums 64 * 64 over 2048 values of k, exactly 2^23, between drains of the
+    fp32 fragments; the result must still be the exact integer sums."""
+    from paper_2101_06584_gb300 import mpgemm as mm
+    m, n, k = 64, 32, 4096
+    A = np.zeros((2, m, k))
+    B = np.zeros((2, k, n))
+    # a = (1 - 2^-20) / 2: sigma = ilogb(a) + 2 = 0, a 2^-sigma 2^7 = 64 (1 - 2^-20) -> digit 64
+    A[0] = 2.0 ** -1 * (1 - 2.0 ** -20)
+    B[0] = 2.0 ** -1 * (1 - 2.0 ** -20)
+    S = 4
+    sig, DA = OZ.slice_rows(A[:, :1, :8], S)
+    assert DA[0, 0, 0] == 64                       # first digit at its maximum
+    Ad, Bd = dev(torch, A), dev(torch, B)
+    ws = torch.empty(mm.workspace_size("dd", m, n, k, algo="bf16", slices=S), dtype=torch.uint8,
+                     device="cuda")
+    Cb = host(mm.gemm("dd", Ad, Bd, algo="bf16", slices=S, workspace=ws))
+    Ci = host(mm.gemm("dd", Ad, Bd, algo="int8", slices=S, workspace=ws))
+    assert_bitwise(Cb, Ci, "bf16 vs int8 at the limit")
+    want, _, _ = OZ.gemm(A, B, S, rows=[0, 63], cols=[0, 31])
+    assert_bitwise(Cb[:, [0, 63]][:, :, [0, 31]], want, "bf16 vs oracle at the limit")
+
+
+def test_bf16_full_size_sampled(torch):
+    n, S = 4096, 13
+    rng = I.rng_for(2)
+    A, B = I.uniform(2, (n, n), rng), I.uniform(2, (n, n), rng)
+    from paper_2101_06584_gb300 import mpgemm as mm
+    Ad, Bd = dev(torch, A), dev(torch, B)
+    ws = torch.empty(mm.workspace_size("dd", n, n, n, algo="bf16", slices=S), dtype=torch.uint8,
+                     device="cuda")
+    C = host(mm.gemm("dd", Ad, Bd, algo="bf16", slices=S, workspace=ws))
+    srng = np.random.default_rng(650)
+    rows = sorted(set(int(x) for x in srng.integers(0, n, 2)))
+    cols = sorted(set(int(x) for x in srng.integers(0, n, 2)))
+    want, _, _ = OZ.gemm(A, B, S, rows=rows, cols=cols)
+    assert_bitwise(C[:, rows][:, :, cols], want, "bf16 4096 sampled")
