@@ -10,6 +10,8 @@ Workloads (one "step" = one pass of the workload's kernels over its inputs):
   dd_small  DD GEMM 128^3, uniform inputs
   dd_int8   DD GEMM 4096^3 through the INT8 error-free slicing form (slicing +
             tensor-core slice products + EFT accumulation), S = 13 slices
+  td_qd_int8  the TD and QD GEMMs of td_qd through the INT8 slicing form
+            (S = 22 / 29)
   batched   512 DD and 512 QD problems, m, n, k log-uniform in [16, 512], each
             precision one persistent launch replayed from a CUDA graph
   autograd  DDMatmul forward + backward (3 DD GEMMs), m = n = k = 2048
@@ -87,7 +89,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="td_qd",
-                    choices=["td_qd", "dd_small", "dd_int8", "batched", "autograd"])
+                    choices=["td_qd", "dd_small", "dd_int8", "td_qd_int8", "batched", "autograd"])
     ap.add_argument("--size", type=int, default=None, help="override the workload's m = n = k")
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
@@ -372,6 +374,59 @@ class DdInt8(Workload):
                 "fp64_eft_ms": plain_ms, "speedup_vs_fp64_eft": plain_ms / ms}
 
 
+class TdQdInt8(Workload):
+    name = "td_qd_int8"
+
+    def __init__(self, torch, mm, I, rank, n=1024):
+        self.torch, self.mm, self.n = torch, mm, n
+        self.precs = ("td", "qd")
+        self.S = {"td": 22, "qd": 29}
+        rng = replica_rng(1, rank)
+        self.dev = {}
+        for prec in self.precs:
+            P = I.P_OF[prec]
+            A, B = I.cancelling_pair(P, n, n, n, rng)
+            ws = torch.empty(mm.workspace_size(prec, n, n, n, algo="int8", slices=self.S[prec]),
+                             dtype=torch.uint8, device="cuda")
+            self.dev[prec] = (torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(),
+                              torch.empty((P, n, n), dtype=torch.float64, device="cuda"), ws)
+        self.mads = len(self.precs) * n ** 3
+        self.launches_per_step = 2 * (5 if n % 64 == 0 else 7)
+        self.config = {"workload": "TD GEMM + QD GEMM, m=n=k=%d, INT8 error-free slicing form "
+                                   "(S = %d / %d), inputs of the main workload" % (n, self.S["td"], self.S["qd"]),
+                       "m": n, "n": n, "k": n, "slices": self.S}
+
+    def timed_step(self, stream):
+        evs = {}
+        for prec in self.precs:
+            A, B, C, ws = self.dev[prec]
+            e0, e1 = self.torch.cuda.Event(enable_timing=True), self.torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            self.mm.gemm(prec, A, B, out=C, algo="int8", slices=self.S[prec], workspace=ws)
+            e1.record(stream)
+            evs[prec] = (e0, e1)
+        return evs
+
+    def roofline(self, launch_ms, pk):
+        n = self.n
+        S = self.S["qd"]
+        pairs = S * (S + 1) // 2
+        ms = statistics.mean(launch_ms["qd"])
+        ach = 2.0 * pairs * n ** 3 / (ms * 1e-3)
+        plain = {}
+        for prec in self.precs:
+            A, B, C, _ = self.dev[prec]
+            plain[prec] = _time_call(self.torch, lambda: self.mm.gemm_plain(prec, A, B, out=C), 1)
+        return {"bound": "tensor", "kernel": "ozaki_gemm_kernel<4> (QD, mma.sync s8) incl. slicing",
+                "achieved": ach / 1e12, "peak": pk["mma_s8"] / 1e12, "unit": "Tint8op/s",
+                "frac": ach / pk["mma_s8"], "traffic": None, "ops_per_unit": 2 * pairs,
+                "unit_of_work": "QD multiply-add (%d slice-pair int8 MACs)" % pairs,
+                "units_per_launch": n ** 3,
+                "per_precision_mad_s": {p: n ** 3 / (statistics.mean(launch_ms[p]) * 1e-3)
+                                        for p in self.precs},
+                "speedup_vs_fp64_eft": {p: plain[p] / statistics.mean(launch_ms[p]) for p in self.precs}}
+
+
 class Batched(Workload):
     name = "batched"
 
@@ -455,8 +510,8 @@ class Autograd(Workload):
                 "unit_of_work": "DD multiply-add", "units_per_launch": self.n ** 3}
 
 
-WORKLOADS = {"td_qd": TdQd, "dd_small": DdSmall, "dd_int8": DdInt8, "batched": Batched,
-             "autograd": Autograd}
+WORKLOADS = {"td_qd": TdQd, "dd_small": DdSmall, "dd_int8": DdInt8, "td_qd_int8": TdQdInt8,
+             "batched": Batched, "autograd": Autograd}
 
 
 def _time_call(torch, fn, reps=1):
@@ -560,7 +615,7 @@ def run_ours(args):
 def extras(torch, mm, I, pk, flush):
     """One short measurement of each other workload (rank 0, after the main one)."""
     out = {}
-    for name in ("dd_small", "dd_int8", "batched", "autograd"):
+    for name in ("dd_small", "dd_int8", "td_qd_int8", "batched", "autograd"):
         w = WORKLOADS[name](torch, mm, I, 0)
         steps = 2 if name != "dd_small" else 10
         total_ms, launch_ms, _, _ = measure(torch, w, steps, 1, 1, 0, flush, sample_clocks=False)

@@ -122,7 +122,7 @@ int mpgemm_qd(int64_t m, int64_t n, int64_t k,
 typedef enum mpg_algo {
     MPG_ALGO_AUTO = 0,       /* the FP64-EFT kernel (k-sequential unless split_k > 1) */
     MPG_ALGO_FP64_EFT = 1,   /* FP64 error-free transformations on the CUDA cores */
-    MPG_ALGO_INT8_OZAKI = 2, /* DD only: error-free INT8 slicing on the tensor cores */
+    MPG_ALGO_INT8_OZAKI = 2, /* DD/TD/QD: error-free INT8 slicing on the tensor cores */
     MPG_ALGO_BF16_SLICES = 3 /* DD only: the same slices as bf16 on the bf16 tensor path */
 } mpg_algo;
 
@@ -149,8 +149,8 @@ int mpgemm_ex(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k,
               const double *const *B, int64_t ldb,
               double *const *C, int64_t ldc);
 
-/* MPG_ALGO_INT8_OZAKI (DD only; not in the paper).  C := op(A) op(B) via an
- * error-free splitting whose products run on the tensor cores:
+/* MPG_ALGO_INT8_OZAKI (not in the paper).  C := op(A) op(B) via an
+ * error-free splitting whose products run on the tensor cores.  For DD:
  *   sigma_i = ilogb(max_p |a_ip[0]|) + 2 per row of op(A) (0 for a zero row),
  *   tau_j likewise per column of op(B); S = opts->slices (default 14, 1..16)
  *   balanced base-2^7 digits of a 2^-sigma, each the nearest integer (ties to
@@ -166,6 +166,13 @@ int mpgemm_ex(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k,
  *   int8  [S][mp][kp]  slices of op(A);   int8 [S][np][kp] slices of op(B)^T;
  *   int32 [mp] sigma;                     int32 [np] tau.
  * The workspace holds these values after the call.
+ * For TD and QD (P = 3, 4; S default 22 / 29, 1..40): each component is
+ * first floored to a multiple of 2^(sigma - 7S - 12 - 64) and the digits are
+ * those of the sum of the floored components (computed exactly in 384-bit
+ * integers); the weight sums are combined exactly three at a time from the
+ * least significant weight, V = P_w + 2^7 P_(w-1) + 2^14 P_(w-2) (|V| < 2^46),
+ * and acc = TDaddq / QDadd (Sec. 2.3, Alg. 5) of (V 2^(sigma_i + tau_j - 7w),
+ * 0, ...) with w the group's largest weight.
  *
  * MPG_ALGO_BF16_SLICES (DD only; not in the paper): the same digits, scales,
  * weight sums and accumulation, with the slice products on the bf16 tensor

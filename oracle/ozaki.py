@@ -1,9 +1,9 @@
-"""Oracle for the INT8 error-free slicing form of the DD GEMM -- TEST
-INFRASTRUCTURE ONLY (tests, smoke check and the benchmark's CPU leg).
+"""Oracle for the INT8 error-free slicing forms of the DD/TD/QD GEMM --
+TEST INFRASTRUCTURE ONLY (tests, smoke check and the benchmark's CPU leg).
 
-The paper's DD GEMM (Sec. 3, Eq. 1) computed through an Ozaki-style
-error-free splitting; every step is the plain definition, in Python
-integers, so a reader can check it line by line:
+The paper's GEMM (Sec. 3, Eq. 1) computed through an Ozaki-style error-free
+splitting; every step is the plain definition, in Python integers, so a
+reader can check it line by line.  DD (P = 2):
 
   scale    sigma_i = ilogb(max_p |hi(a_ip)|) + 2 for row i of A (0 for an
            all-zero row); tau_j likewise for column j of B.  Then
@@ -17,6 +17,16 @@ integers, so a reader can check it line by line:
            acc = DDadd(acc, (P_w[i,j] 2^(sigma_i + tau_j - 7w), 0))
            with the oracle's DDadd (Alg. 1).  The scaled value is an exact
            binary64 for the sizes this form accepts.
+
+TD and QD (P = 3, 4) differ in two places:
+  slices   each component is first floored to a multiple of
+           2^(sigma - F - 64), F = 7S + 12 (64 guard bits below the last
+           digit's unit); the digits are those of the sum of the floored
+           components, exactly as above.
+  accumulate  weights are taken in groups of three from the least
+           significant end: V = P_w + 2^7 P_(w-1) + 2^14 P_(w-2) (exact, below
+           2^46); acc = add(acc, (V 2^(sigma + tau - 7w), 0, ...)) with TDaddq
+           (Sec. 2.3) or QDadd (Alg. 5), w the group's largest weight.
 """
 import math
 from fractions import Fraction
@@ -46,10 +56,29 @@ def scale_exponent(hi_values):
     return 0 if mx == 0.0 else ilogb(mx) + 2
 
 
-def digits(components, sigma, S):
+GUARD_BITS = 64
+
+
+def truncated_value(components, sigma, S):
+    """Sum of the components, each floored to a multiple of 2^(sigma - F - 64)
+    with F = 7S + 12 (the TD/QD slicing input), as a Fraction."""
+    q = sigma - (7 * S + 12) - GUARD_BITS
+    tot = 0
+    for c in components:
+        M, E = _exact_int(float(c))
+        sh = E - q
+        tot += (M << sh) if sh >= 0 else (M >> -sh)    # Python >> floors
+    return Fraction(tot) * Fraction(2) ** q
+
+
+def digits(components, sigma, S, truncate=False):
     """The S balanced base-2^7 digits of (sum of components) * 2^-sigma and
-    the exact remainder x_S (a Fraction)."""
-    x = sum((Fraction(float(c)) for c in components), Fraction(0)) * Fraction(2) ** (-sigma)
+    the exact remainder x_S (a Fraction).  With truncate, of the sum of the
+    components floored as in truncated_value (TD/QD)."""
+    if truncate:
+        x = truncated_value(components, sigma, S) * Fraction(2) ** (-sigma)
+    else:
+        x = sum((Fraction(float(c)) for c in components), Fraction(0)) * Fraction(2) ** (-sigma)
     out = []
     for _ in range(S):
         y = x * (1 << BASE_BITS)
@@ -64,12 +93,13 @@ def slice_rows(planes, S, rows=None):
     D[s-1][r][p] the s-th digit of element (rows[r], p)."""
     planes = np.asarray(planes)
     rows = range(planes.shape[1]) if rows is None else rows
+    truncate = planes.shape[0] > 2
     sig, D = [], np.zeros((S, len(rows), planes.shape[2]), dtype=np.int64)
     for r, i in enumerate(rows):
         sg = scale_exponent(planes[0, i, :])
         sig.append(sg)
         for p in range(planes.shape[2]):
-            ds, _ = digits(planes[:, i, p], sg, S)
+            ds, _ = digits(planes[:, i, p], sg, S, truncate)
             D[:, r, p] = ds
     return sig, D
 
@@ -92,26 +122,42 @@ def weight_products(DA, DB, S):
     return out
 
 
+PREC_OF = {2: "dd", 3: "td", 4: "qd"}
+
+
+def weight_groups(S, P):
+    """The weights in accumulation order, grouped: one per group for DD,
+    three for TD/QD, from the least significant (w = S+1) end."""
+    ws = list(range(S + 1, 1, -1))
+    g = 1 if P == 2 else 3
+    return [ws[i:i + g] for i in range(0, len(ws), g)]
+
+
 def gemm(A, B, S, rows=None, cols=None, L=None):
-    """DD C = A B through S-slice error-free splitting, for the selected rows
-    of A and columns of B (all by default).  A (2, m, k), B (2, k, n).
-    Returns C (2, len(rows), len(cols)), sigma, tau."""
+    """C = A B through S-slice error-free splitting, for the selected rows of
+    A and columns of B (all by default).  A (P, m, k), B (P, k, n), P = 2, 3
+    or 4.  Returns C (P, len(rows), len(cols)), sigma, tau."""
     A = np.asarray(A)
     B = np.asarray(B)
+    P = A.shape[0]
+    prec = PREC_OF[P]
     rows = list(range(A.shape[1])) if rows is None else list(rows)
     cols = list(range(B.shape[2])) if cols is None else list(cols)
     sig, DA = slice_rows(A, S, rows)
     tau, DB = slice_cols(B, S, cols)
     Pw = weight_products(DA, DB, S)
-    C = np.zeros((2, len(rows), len(cols)))
+    C = np.zeros((P, len(rows), len(cols)))
     for r in range(len(rows)):
         for c in range(len(cols)):
-            acc = (0.0, 0.0)
-            for w in range(S + 1, 1, -1):
-                v = math.ldexp(float(int(Pw[w][r, c])), sig[r] + tau[c] - BASE_BITS * w)
-                assert Fraction(v) == Fraction(int(Pw[w][r, c])) * Fraction(2) ** (
-                    sig[r] + tau[c] - BASE_BITS * w), "scaled product not exact"
-                acc = _op("dd", "add", acc, (v, 0.0), L)
+            acc = (0.0,) * P
+            for grp in weight_groups(S, P):
+                wmax = grp[0]
+                V = sum(int(Pw[w][r, c]) << (BASE_BITS * (wmax - w)) for w in grp)
+                assert abs(V) < 2 ** 53
+                e = sig[r] + tau[c] - BASE_BITS * wmax
+                v = math.ldexp(float(V), e)
+                assert Fraction(v) == Fraction(V) * Fraction(2) ** e, "scaled group sum not exact"
+                acc = _op(prec, "add", acc, (v,) + (0.0,) * (P - 1), L)
             C[:, r, c] = acc
     return C, sig, tau
 

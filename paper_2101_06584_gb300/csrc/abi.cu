@@ -163,25 +163,25 @@ template int check_gemm<2>(const GemmArgs<2>&);
 template int check_gemm<3>(const GemmArgs<3>&);
 template int check_gemm<4>(const GemmArgs<4>&);
 
-template <int P>
-static int ozaki_call(const GemmArgs<P>&, const mpgemm_opts*)
-{
-    return fail(MPG_EUNSUPPORTED, "the slicing forms are provided for DD (P = 2) only");
-}
+// Slice-count limits and defaults per precision.
+static int ozaki_max_slices(int P) { return P == 2 ? kOzakiMaxSlices : kOzakiMaxSlicesWide; }
+static int ozaki_default_slices(int P) { return P == 2 ? kOzakiDefaultSlices : P == 3 ? 22 : 29; }
 
-template <>
-int ozaki_call<2>(const GemmArgs<2>& g, const mpgemm_opts* o)
+template <int P>
+static int ozaki_call(const GemmArgs<P>& g, const mpgemm_opts* o)
 {
-    const int S = o->slices ? o->slices : kOzakiDefaultSlices;
-    if (S < 1 || S > kOzakiMaxSlices)
-        return fail(MPG_EINVAL, "slices must be in 1..%d (got %d)", kOzakiMaxSlices, S);
+    const int engine = o->algo == MPG_ALGO_BF16_SLICES ? 1 : 0;
+    if (engine == 1 && P != 2)
+        return fail(MPG_EUNSUPPORTED, "the bf16 slicing path is provided for DD (P = 2) only");
+    const int S = o->slices ? o->slices : ozaki_default_slices(P);
+    if (S < 1 || S > ozaki_max_slices(P))
+        return fail(MPG_EINVAL, "slices must be in 1..%d for P = %d (got %d)", ozaki_max_slices(P), P, S);
     if (g.k > ozaki_k_limit(S))
         return fail(MPG_EUNSUPPORTED, "k = %lld exceeds %lld, the largest k whose %d-slice int32 "
                     "sums are exact", (long long)g.k, (long long)ozaki_k_limit(S), S);
-    const int engine = o->algo == MPG_ALGO_BF16_SLICES ? 1 : 0;
     const OzakiLayout L = ozaki_layout(S, g.m, g.n, g.k, engine == 1 ? 2 : 1);
     if (L.mp / 64 > 65535) return fail(MPG_EINVAL, "m too large for the slicing form's grid");
-    if (!o->workspace) return fail(MPG_EWORKSPACE, "the INT8 form needs a workspace of %lld bytes",
+    if (!o->workspace) return fail(MPG_EWORKSPACE, "the slicing form needs a workspace of %lld bytes",
                                    (long long)L.total);
     if (reinterpret_cast<uintptr_t>(o->workspace) % 256)
         return fail(MPG_EWORKSPACE, "workspace must be 256-byte aligned");
@@ -192,15 +192,15 @@ int ozaki_call<2>(const GemmArgs<2>& g, const mpgemm_opts* o)
                    reinterpret_cast<uintptr_t>(o->workspace) + static_cast<uintptr_t>(L.total)};
     const int64_t ar = g.trans_a ? g.k : g.m, ac = g.trans_a ? g.m : g.k;
     const int64_t br = g.trans_b ? g.n : g.k, bc = g.trans_b ? g.k : g.n;
-    for (int c = 0; c < 2; ++c) {
+    for (int c = 0; c < P; ++c) {
         if (overlap(rw, plane_range(g.A[c], ar, ac, g.lda)) || overlap(rw, plane_range(g.B[c], br, bc, g.ldb)) ||
             overlap(rw, plane_range(g.C[c], g.m, g.n, g.ldc)))
             return fail(MPG_EWORKSPACE, "workspace overlaps an operand");
     }
     const int variant = o->tile > 0 ? o->tile - 1 : 0;
     if (variant > 4) return fail(MPG_EINVAL, "INT8 tile id %d out of range 1..5", o->tile);
-    cudaError_t e = launch_ozaki_dd(g, S, o->workspace, g_stream, variant, engine);
-    return e == cudaSuccess ? MPG_OK : cuda_fail(e, "INT8 slicing gemm launch");
+    cudaError_t e = launch_ozaki<P>(g, S, o->workspace, g_stream, variant, engine);
+    return e == cudaSuccess ? MPG_OK : cuda_fail(e, "slicing gemm launch");
 }
 
 template <int P>
@@ -227,8 +227,6 @@ static int gemm_call(const mpgemm_opts* o, int64_t m, int64_t n, int64_t k,
         algo != MPG_ALGO_BF16_SLICES)
         return fail(MPG_EINVAL, "unknown algorithm %d", algo);
     const bool sliced = algo == MPG_ALGO_INT8_OZAKI || algo == MPG_ALGO_BF16_SLICES;
-    if (sliced && P != 2)
-        return fail(MPG_EUNSUPPORTED, "the slicing forms are provided for DD (P = 2) only");
     cudaError_t e;
     if (k == 0) {
         e = launch_zero<P>(g, g_stream);
@@ -318,11 +316,12 @@ int mpgemm_ex(int P, const mpgemm_opts* opts, int64_t m, int64_t n, int64_t k,
 
 size_t mpgemm_workspace_size(int P, const mpgemm_opts* opts, int64_t m, int64_t n, int64_t k)
 {
-    if (!opts || (opts->algo != MPG_ALGO_INT8_OZAKI && opts->algo != MPG_ALGO_BF16_SLICES) || P != 2 ||
-        m < 0 || n < 0 || k < 0)
+    if (!opts || (opts->algo != MPG_ALGO_INT8_OZAKI && opts->algo != MPG_ALGO_BF16_SLICES) || P < 2 ||
+        P > 4 || m < 0 || n < 0 || k < 0)
         return 0;
-    const int S = opts->slices ? opts->slices : kOzakiDefaultSlices;
-    if (S < 1 || S > kOzakiMaxSlices) return 0;
+    if (opts->algo == MPG_ALGO_BF16_SLICES && P != 2) return 0;
+    const int S = opts->slices ? opts->slices : ozaki_default_slices(P);
+    if (S < 1 || S > ozaki_max_slices(P)) return 0;
     return static_cast<size_t>(ozaki_layout(S, m, n, k, opts->algo == MPG_ALGO_BF16_SLICES ? 2 : 1).total);
 }
 
@@ -363,7 +362,7 @@ int mpgemm_dd_int8_static(int64_t m, int64_t n, int64_t k, const double* const A
     void* ws = nullptr;
     e = ozaki_static_scratch(&ws);
     if (e != cudaSuccess) return cuda_fail(e, "looking up the fixed scratch array");
-    e = launch_ozaki_dd(g, S, ws, g_stream);
+    e = launch_ozaki<2>(g, S, ws, g_stream);
     return e == cudaSuccess ? MPG_OK : cuda_fail(e, "INT8 slicing gemm launch");
 }
 

@@ -128,6 +128,103 @@ __device__ __forceinline__ void ozaki_digits(double hi, double lo, int sigma, in
     }
 }
 
+// ------------------------------------------------- wide digits (TD, QD)
+//
+// For P >= 3 components the S digits need up to 7S + 12 bits below the scale
+// plus guard bits, beyond 128.  Each component is floored to a multiple of
+// 2^(sigma - F - 64) (F = 7S + 12) and the floored parts are summed exactly
+// in a 384-bit two's-complement integer (six 64-bit words, word 0 least
+// significant); the digits are those of that sum, ties to even decided
+// exactly.  Nothing of the method's arithmetic is approximated: the floor is
+// part of the definition, 64 bits below the last digit.
+
+constexpr int kWideWords = 6;
+constexpr int kGuardBits = 64;
+
+struct Wide {
+    uint64_t w[kWideWords];
+};
+
+// W += M * 2^sh for a signed |M| < 2^53 and 0 <= sh (fits by construction).
+__device__ __forceinline__ void wide_add_shifted(Wide& W, int64_t M, int sh)
+{
+    const int wi = sh >> 6, bo = sh & 63;
+    const uint64_t ext = M < 0 ? ~0ull : 0ull;
+    uint64_t part[kWideWords];
+#pragma unroll
+    for (int i = 0; i < kWideWords; ++i) part[i] = i < wi ? 0ull : ext;
+    const uint64_t lo = static_cast<uint64_t>(M) << bo;
+    const uint64_t hi = bo == 0 ? ext : static_cast<uint64_t>(M >> (64 - bo));
+#pragma unroll
+    for (int i = 0; i < kWideWords; ++i) {
+        if (i == wi) part[i] = lo;
+        if (i == wi + 1) part[i] = hi;
+    }
+    uint64_t carry = 0;
+#pragma unroll
+    for (int i = 0; i < kWideWords; ++i) {
+        const uint64_t a = W.w[i], b = part[i];
+        const uint64_t s1 = a + b;
+        const uint64_t c1 = s1 < a;
+        const uint64_t s2 = s1 + carry;
+        const uint64_t c2 = s2 < s1;
+        W.w[i] = s2;
+        carry = c1 | c2;
+    }
+}
+
+// W += v for a small signed v at bit 0.
+__device__ __forceinline__ void wide_add_small(Wide& W, int64_t v)
+{
+    wide_add_shifted(W, v, 0);
+}
+
+// The S digits of the sum of the P components, each floored at
+// 2^(sigma - F - 64) (nearest, ties to even).
+template <int P>
+__device__ __forceinline__ void ozaki_digits_wide(const double (&c)[P], int sigma, int S, int8_t* out)
+{
+    const int F = 7 * S + 12;
+    Wide W;
+#pragma unroll
+    for (int i = 0; i < kWideWords; ++i) W.w[i] = 0ull;
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        int64_t M;
+        int e;
+        decompose(c[i], M, e);
+        if (M == 0) continue;
+        const int sh = e - sigma + F + kGuardBits;
+        if (sh >= 0) wide_add_shifted(W, M, sh);
+        else if (sh > -64) wide_add_small(W, M >> (-sh));      // arithmetic shift: floor
+        else wide_add_small(W, M < 0 ? -1 : 0);
+    }
+    for (int s = 1; s <= S; ++s) {
+        const int q = F + kGuardBits - 7 * s;     // bit position of the digit's unit (>= 76)
+        const int wq = q >> 6, bq = q & 63;
+        // t = floor((W + 2^(q-1)) / 2^q) from a copy with the half added
+        Wide H = W;
+        wide_add_shifted(H, 1, q - 1);
+        // bits q .. q+63 as a signed 64-bit value; |t| <= 65, so the bits
+        // above q + 7 are copies of the sign
+        int64_t t;
+        if (wq + 1 < kWideWords) {
+            const uint64_t hi = bq == 0 ? 0ull : (H.w[wq + 1] << (64 - bq));
+            t = static_cast<int64_t>((H.w[wq] >> bq) | hi);
+        } else {
+            t = static_cast<int64_t>(H.w[wq]) >> bq;            // arithmetic: top word
+        }
+        // a tie leaves no bits below q after adding the half
+        bool below_zero = (H.w[wq] & ((bq == 0) ? 0ull : ((1ull << bq) - 1))) == 0;
+#pragma unroll
+        for (int i = 0; i < kWideWords; ++i)
+            if (i < wq) below_zero = below_zero && H.w[i] == 0ull;
+        if (below_zero && (t & 1)) t -= 1;
+        wide_add_shifted(W, -t, q);
+        out[s - 1] = static_cast<int8_t>(t);
+    }
+}
+
 // ------------------------------------------------------------------ scale
 
 // One warp per vector whose elements are contiguous (stride 1, vectors ld apart).
@@ -205,23 +302,43 @@ __device__ __forceinline__ void store4(T* out, int8_t d0, int8_t d1, int8_t d2, 
 // Rows of the sliced operand are contiguous in memory (element (r, p) at
 // base[r*ld + p]).  One thread per 4 consecutive p; rows up to `rows_pad`,
 // columns up to kp, zero outside [rows) x [len).
-template <typename T>
-__global__ void ozaki_slice_rows(const double* __restrict__ hi, const double* __restrict__ lo,
-                                 int64_t rows, int64_t len, int64_t ld, const int* __restrict__ sig,
-                                 int S, int64_t rows_pad, int64_t kp, T* __restrict__ out)
+template <int P>
+struct Planes {
+    const double* c[P];
+};
+
+// The S digits of element `off` of the component planes.
+template <int P>
+__device__ __forceinline__ void element_digits(const Planes<P>& pl, int64_t off, int sigma, int S,
+                                               int8_t* out)
+{
+    if constexpr (P == 2) {
+        ozaki_digits(pl.c[0][off], pl.c[1][off], sigma, S, out);
+    } else {
+        double c[P];
+#pragma unroll
+        for (int i = 0; i < P; ++i) c[i] = pl.c[i][off];
+        ozaki_digits_wide<P>(c, sigma, S, out);
+    }
+}
+
+template <int P, typename T>
+__global__ void ozaki_slice_rows(const Planes<P> pl, int64_t rows, int64_t len, int64_t ld,
+                                 const int* __restrict__ sig, int S, int64_t rows_pad, int64_t kp,
+                                 T* __restrict__ out)
 {
     const int64_t quads = kp / 4;
     const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (t >= rows_pad * quads) return;
     const int64_t r = t / quads;
     const int64_t p0 = (t % quads) * 4;
-    int8_t dg[4][16];
+    int8_t dg[4][kOzakiMaxSlicesWide];
     const int sg = r < rows ? sig[r] : 0;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int64_t p = p0 + u;
         if (r < rows && p < len) {
-            ozaki_digits(hi[r * ld + p], lo[r * ld + p], sg, S, dg[u]);
+            element_digits<P>(pl, r * ld + p, sg, S, dg[u]);
         } else {
             for (int s = 0; s < S; ++s) dg[u][s] = 0;
         }
@@ -234,13 +351,14 @@ __global__ void ozaki_slice_rows(const double* __restrict__ hi, const double* __
 // Rows of the sliced operand are strided (element (r, p) at base[p*ld + r]):
 // a 32 x 32 tile is read with r fastest, sliced, transposed through shared
 // memory and written with p fastest.
-template <typename T>
+template <int P, typename T>
 __global__ void __launch_bounds__(256)
-ozaki_slice_cols(const double* __restrict__ hi, const double* __restrict__ lo, int64_t rows,
-                 int64_t len, int64_t ld, const int* __restrict__ sig, int S, int64_t rows_pad,
-                 int64_t kp, T* __restrict__ out)
+ozaki_slice_cols(const Planes<P> pl, int64_t rows, int64_t len, int64_t ld,
+                 const int* __restrict__ sig, int S, int64_t rows_pad, int64_t kp,
+                 T* __restrict__ out)
 {
-    __shared__ int8_t tile[16][32][36];
+    constexpr int SMAX = P == 2 ? kOzakiMaxSlices : kOzakiMaxSlicesWide;
+    __shared__ int8_t tile[SMAX][32][36];
     const int64_t r0 = static_cast<int64_t>(blockIdx.x) * 32;
     const int64_t p0 = static_cast<int64_t>(blockIdx.y) * 32;
     const int tr = threadIdx.x & 31;        // r within the tile
@@ -249,9 +367,9 @@ ozaki_slice_cols(const double* __restrict__ hi, const double* __restrict__ lo, i
     const int sg = r < rows ? sig[r] : 0;
     for (int pp = tp; pp < 32; pp += 8) {
         const int64_t p = p0 + pp;
-        int8_t dg[16];
+        int8_t dg[SMAX];
         if (r < rows && p < len) {
-            ozaki_digits(hi[p * ld + r], lo[p * ld + r], sg, S, dg);
+            element_digits<P>(pl, p * ld + r, sg, S, dg);
         } else {
             for (int s = 0; s < S; ++s) dg[s] = 0;
         }
@@ -303,13 +421,25 @@ __device__ __forceinline__ double scaled_int(int v, int e)
     return __longlong_as_double(static_cast<long long>(bits));
 }
 
+// v * 2^e as a binary64, exactly (|v| < 2^53, result in the normal range).
+__device__ __forceinline__ double scaled_int64(int64_t v, int e)
+{
+    if (v == 0) return 0.0;
+    const uint64_t u = v < 0 ? 0ull - static_cast<uint64_t>(v) : static_cast<uint64_t>(v);
+    const int lz = __clzll(static_cast<long long>(u));
+    const int ex = 63 - lz + e;
+    const uint64_t mant = (u << (lz - 11)) & ((1ull << 52) - 1);
+    const uint64_t bits = (static_cast<uint64_t>(v < 0) << 63) |
+                          (static_cast<uint64_t>(ex + 1023) << 52) | mant;
+    return __longlong_as_double(static_cast<long long>(bits));
+}
+
 struct OzakiGemmArgs {
     const void* sa;     // [S][mp][kp] digits (int8 or bf16)
     const void* sb;     // [S][np][kp]
     const int* sig;     // [mp]
     const int* tau;     // [np]
-    double* C0;
-    double* C1;
+    double* C[4];       // the P output planes
     int64_t ldc, m, n, mp, np, kp;
     int S;
 };
@@ -329,9 +459,11 @@ struct Cursor {
 };
 
 // CTA of WM x WN warps; each warp owns MT x NT fragments of 16 x 8 outputs,
-// so the CTA tile is (WM*MT*16) x (WN*NT*8).  Slice tiles of TILE bytes of k
-// are staged through a STG-deep cp.async pipeline.
-template <int MT, int NT, int WM, int WN, int STG, int MINB, int KS>
+// so the CTA tile is (WM*MT*16) x (WN*NT*8).  Slice tiles of KS bytes of k
+// are staged through a STG-deep cp.async pipeline.  P output components:
+// DD adds every weight's sum; TD/QD combine three weights exactly in int64
+// first and add the group.
+template <int P, int MT, int NT, int WM, int WN, int STG, int MINB, int KS>
 __global__ void __launch_bounds__(WM * WN * 32, MINB) ozaki_gemm_kernel(const OzakiGemmArgs g)
 {
     constexpr int NTHR = WM * WN * 32;
@@ -364,14 +496,20 @@ __global__ void __launch_bounds__(WM * WN * 32, MINB) ozaki_gemm_kernel(const Oz
 #pragma unroll
         for (int h = 0; h < 2; ++h) tu[nt][h] = g.tau[n0 + wn * NT * 8 + nt * 8 + 2 * tq + h];
 
-    double acc0[MT][NT][4], acc1[MT][NT][4];
+    double acc[MT][NT][4][P];
     int ci[MT][NT][4];
+    int64_t grp[MT][NT][4];
 #pragma unroll
     for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
         for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
-            for (int r = 0; r < 4; ++r) { acc0[mt][nt][r] = 0.0; acc1[mt][nt][r] = 0.0; ci[mt][nt][r] = 0; }
+            for (int r = 0; r < 4; ++r) {
+#pragma unroll
+                for (int c = 0; c < P; ++c) acc[mt][nt][r][c] = 0.0;
+                ci[mt][nt][r] = 0;
+                grp[mt][nt][r] = 0;
+            }
 
     auto load = [&](int stage, const Cursor& c) {
         const int8_t* a = static_cast<const int8_t*>(g.sa) +
@@ -430,24 +568,39 @@ __global__ void __launch_bounds__(WM * WN * 32, MINB) ozaki_gemm_kernel(const Oz
 #pragma unroll
                 for (int nt = 0; nt < NT; ++nt) mma_s8(ci[mt][nt], af[mt], bf[nt]);
         }
-        // end of a weight: fold its exact integer sums into the DD accumulators
+        // end of a weight: fold its exact integer sums into the accumulators
         const int w = cm.w;
         cm.advance(S, KT);
         if (cm.w != w || it == total - 1) {
+            // TD/QD: position of w in its group of three, counted from the
+            // least significant weight S+1; the group ends at its third
+            // weight or at w = 2
+            const int j = (S + 1 - w) % 3;
+            const bool group_end = (P == 2) || j == 2 || w == 2;
+            const int wmax = P == 2 ? w : w + j;
 #pragma unroll
             for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
                 for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
-                        const int e = sg[mt][r >> 1] + tu[nt][r & 1] - 7 * w;
-                        const double x[2] = {acc0[mt][nt][r], acc1[mt][nt][r]};
-                        const double y[2] = {scaled_int(ci[mt][nt][r], e), f.zero};
-                        double z[2];
-                        mp::dd_add(f, x, y, z);
-                        acc0[mt][nt][r] = z[0];
-                        acc1[mt][nt][r] = z[1];
+                        double y[P];
+                        if constexpr (P == 2) {
+                            y[0] = scaled_int(ci[mt][nt][r], sg[mt][r >> 1] + tu[nt][r & 1] - 7 * w);
+                        } else {
+                            grp[mt][nt][r] += static_cast<int64_t>(ci[mt][nt][r]) << (7 * j);
+                            y[0] = scaled_int64(grp[mt][nt][r], sg[mt][r >> 1] + tu[nt][r & 1] - 7 * wmax);
+                        }
                         ci[mt][nt][r] = 0;
+                        if (group_end) {
+#pragma unroll
+                            for (int c = 1; c < P; ++c) y[c] = f.zero;
+                            double z[P];
+                            mp::Ops<P>::add(f, acc[mt][nt][r], y, z);
+#pragma unroll
+                            for (int c = 0; c < P; ++c) acc[mt][nt][r][c] = z[c];
+                            grp[mt][nt][r] = 0;
+                        }
                     }
         }
     }
@@ -462,12 +615,11 @@ __global__ void __launch_bounds__(WM * WN * 32, MINB) ozaki_gemm_kernel(const Oz
                 const int64_t row = m0 + wm * MT * 16 + mt * 16 + gq + (r >> 1) * 8;
                 const int64_t col = n0 + wn * NT * 8 + nt * 8 + 2 * tq + (r & 1);
                 if (row < g.m && col < g.n) {
-                    g.C0[row * g.ldc + col] = acc0[mt][nt][r];
-                    g.C1[row * g.ldc + col] = acc1[mt][nt][r];
+#pragma unroll
+                    for (int c = 0; c < P; ++c) g.C[c][row * g.ldc + col] = acc[mt][nt][r][c];
                 }
             }
 }
-
 
 __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
 {
@@ -633,8 +785,8 @@ __global__ void __launch_bounds__(WM * WN * 32, MINB) ozaki_gemm_bf16_kernel(con
                 const int64_t row = m0 + wm * MT * 16 + mt * 16 + gq + (r >> 1) * 8;
                 const int64_t col = n0 + wn * NT * 8 + nt * 8 + 2 * tq + (r & 1);
                 if (row < g.m && col < g.n) {
-                    g.C0[row * g.ldc + col] = acc0[mt][nt][r];
-                    g.C1[row * g.ldc + col] = acc1[mt][nt][r];
+                    g.C[0][row * g.ldc + col] = acc0[mt][nt][r];
+                    g.C[1][row * g.ldc + col] = acc1[mt][nt][r];
                 }
             }
 }
@@ -695,88 +847,104 @@ static unsigned blocks_for(int64_t threads, int per) { return static_cast<unsign
 
 // Slice one operand: vectors (rows of op(A) or columns of op(B)) of length
 // len; `contig` says whether a vector's elements are adjacent in memory.
-template <typename T>
-static cudaError_t slice_operand(const double* hi, const double* lo, int64_t count, int64_t len,
-                                 int64_t ld, bool contig, int S, int64_t count_pad, int64_t kp,
-                                 T* out, int* sig, cudaStream_t s)
+template <int P, typename T>
+static cudaError_t slice_operand(const Planes<P>& pl, int64_t count, int64_t len, int64_t ld,
+                                 bool contig, int S, int64_t count_pad, int64_t kp, T* out,
+                                 int* sig, cudaStream_t s)
 {
-    if (contig) ozaki_scale_contig<<<blocks_for(count * 32, 256), 256, 0, s>>>(hi, count, len, ld, sig);
-    else ozaki_scale_strided<<<blocks_for(count, 256), 256, 0, s>>>(hi, count, len, ld, sig);
+    const double* lead = pl.c[0];
+    if (contig) ozaki_scale_contig<<<blocks_for(count * 32, 256), 256, 0, s>>>(lead, count, len, ld, sig);
+    else ozaki_scale_strided<<<blocks_for(count, 256), 256, 0, s>>>(lead, count, len, ld, sig);
     if (count_pad > count)
         ozaki_fill_int<<<blocks_for(count_pad - count, 256), 256, 0, s>>>(sig, count, count_pad);
     if (contig) {
-        ozaki_slice_rows<T><<<blocks_for(count_pad * (kp / 4), 128), 128, 0, s>>>(
-            hi, lo, count, len, ld, sig, S, count_pad, kp, out);
+        ozaki_slice_rows<P, T><<<blocks_for(count_pad * (kp / 4), 128), 128, 0, s>>>(
+            pl, count, len, ld, sig, S, count_pad, kp, out);
     } else {
         const dim3 grid(static_cast<unsigned>(count_pad / 32), static_cast<unsigned>(kp / 32));
-        ozaki_slice_cols<T><<<grid, 256, 0, s>>>(hi, lo, count, len, ld, sig, S, count_pad, kp, out);
+        ozaki_slice_cols<P, T><<<grid, 256, 0, s>>>(pl, count, len, ld, sig, S, count_pad, kp, out);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_ozaki_dd(const GemmArgs<2>& g, int S, void* ws, cudaStream_t s, int variant,
-                            int engine)
+template <int P>
+cudaError_t launch_ozaki(const GemmArgs<P>& g, int S, void* ws, cudaStream_t s, int variant, int engine)
 {
     const int eb = engine == 1 ? 2 : 1;
     const OzakiLayout L = ozaki_layout(S, g.m, g.n, g.k, eb);
     int8_t* base = static_cast<int8_t*>(ws);
     int* sig = reinterpret_cast<int*>(base + L.offSig);
     int* tau = reinterpret_cast<int*>(base + L.offTau);
+    Planes<P> pa, pb;
+    for (int c = 0; c < P; ++c) {
+        pa.c[c] = g.A[c];
+        pb.c[c] = g.B[c];
+    }
     cudaError_t e;
     // op(A) row i: contiguous unless A is stored transposed; op(B) column j:
     // contiguous only if B is stored transposed
     if (engine == 1) {
         uint16_t* sa = reinterpret_cast<uint16_t*>(base + L.offA);
         uint16_t* sb = reinterpret_cast<uint16_t*>(base + L.offB);
-        e = slice_operand(g.A[0], g.A[1], g.m, g.k, g.lda, !g.trans_a, S, L.mp, L.kp, sa, sig, s);
-        if (e == cudaSuccess)
-            e = slice_operand(g.B[0], g.B[1], g.n, g.k, g.ldb, g.trans_b != 0, S, L.np, L.kp, sb, tau, s);
+        e = slice_operand(pa, g.m, g.k, g.lda, !g.trans_a, S, L.mp, L.kp, sa, sig, s);
+        if (e == cudaSuccess) e = slice_operand(pb, g.n, g.k, g.ldb, g.trans_b != 0, S, L.np, L.kp, sb, tau, s);
     } else {
         int8_t* sa = base + L.offA;
         int8_t* sb = base + L.offB;
-        e = slice_operand(g.A[0], g.A[1], g.m, g.k, g.lda, !g.trans_a, S, L.mp, L.kp, sa, sig, s);
-        if (e == cudaSuccess)
-            e = slice_operand(g.B[0], g.B[1], g.n, g.k, g.ldb, g.trans_b != 0, S, L.np, L.kp, sb, tau, s);
+        e = slice_operand(pa, g.m, g.k, g.lda, !g.trans_a, S, L.mp, L.kp, sa, sig, s);
+        if (e == cudaSuccess) e = slice_operand(pb, g.n, g.k, g.ldb, g.trans_b != 0, S, L.np, L.kp, sb, tau, s);
     }
     if (e != cudaSuccess) return e;
-    OzakiGemmArgs a{base + L.offA, base + L.offB, sig, tau, g.C[0], g.C[1], g.ldc, g.m, g.n,
-                    L.mp, L.np, L.kp, S};
-    if (engine == 1) {
-        // 64 x 32 CTA tile, 4 warps of 32 x 16, 3 stages of 64 bf16
-        const dim3 grid(static_cast<unsigned>(L.np / 32), static_cast<unsigned>(L.mp / 64));
-        ozaki_gemm_bf16_kernel<2, 2, 2, 2, 3, 3, 64><<<grid, 128, 0, s>>>(a);
-        return cudaGetLastError();
-    }
-    // int8 tilings, measured at DD 4096^3, S = 13 on GB300: 0 -> 88 ms, 1 -> 102, 2 -> 91.5,
-    // 3 -> 90, 4 -> 96
-    switch (variant) {
-    case 1: {   // 64 x 64 CTA tile, 4 warps of 32 x 32, 3 stages of 64 bytes
-        const dim3 grid(static_cast<unsigned>(L.np / 64), static_cast<unsigned>(L.mp / 64));
-        ozaki_gemm_kernel<2, 4, 2, 2, 3, 1, 64><<<grid, 128, 0, s>>>(a);
-        break;
-    }
-    case 2: {   // 64 x 32 CTA tile, 4 warps of 32 x 16, 4 stages of 64 bytes
-        const dim3 grid(static_cast<unsigned>(L.np / 32), static_cast<unsigned>(L.mp / 64));
-        ozaki_gemm_kernel<2, 2, 2, 2, 4, 4, 64><<<grid, 128, 0, s>>>(a);
-        break;
-    }
-    case 3: {   // 64 x 32 CTA tile, 4 warps of 16 x 32, 4 stages of 64 bytes
-        const dim3 grid(static_cast<unsigned>(L.np / 32), static_cast<unsigned>(L.mp / 64));
-        ozaki_gemm_kernel<1, 4, 4, 1, 4, 4, 64><<<grid, 128, 0, s>>>(a);
-        break;
-    }
-    case 4: {   // 64 x 64 CTA tile, 8 warps of 32 x 16, 4 stages of 64 bytes
-        const dim3 grid(static_cast<unsigned>(L.np / 64), static_cast<unsigned>(L.mp / 64));
-        ozaki_gemm_kernel<2, 2, 2, 4, 4, 2, 64><<<grid, 256, 0, s>>>(a);
-        break;
-    }
-    default: {  // 64 x 32 CTA tile, 4 warps of 32 x 16, 3 stages of 128 bytes
-        const dim3 grid(static_cast<unsigned>(L.np / 32), static_cast<unsigned>(L.mp / 64));
-        ozaki_gemm_kernel<2, 2, 2, 2, 3, 4, 128><<<grid, 128, 0, s>>>(a);
-        break;
-    }
+    OzakiGemmArgs a{base + L.offA, base + L.offB, sig, tau, {nullptr, nullptr, nullptr, nullptr},
+                    g.ldc, g.m, g.n, L.mp, L.np, L.kp, S};
+    for (int c = 0; c < P; ++c) a.C[c] = g.C[c];
+    if constexpr (P == 2) {
+        if (engine == 1) {
+            // 64 x 32 CTA tile, 4 warps of 32 x 16, 3 stages of 64 bf16
+            const dim3 grid(static_cast<unsigned>(L.np / 32), static_cast<unsigned>(L.mp / 64));
+            ozaki_gemm_bf16_kernel<2, 2, 2, 2, 3, 3, 64><<<grid, 128, 0, s>>>(a);
+            return cudaGetLastError();
+        }
+        // int8 tilings, measured at DD 4096^3, S = 13 on GB300: 0 -> 88 ms, 1 -> 102,
+        // 2 -> 91.5, 3 -> 90, 4 -> 96
+        switch (variant) {
+        case 1: {   // 64 x 64 CTA tile, 4 warps of 32 x 32, 3 stages of 64 bytes
+            const dim3 grid(static_cast<unsigned>(L.np / 64), static_cast<unsigned>(L.mp / 64));
+            ozaki_gemm_kernel<2, 2, 4, 2, 2, 3, 1, 64><<<grid, 128, 0, s>>>(a);
+            break;
+        }
+        case 2: {   // 64 x 32 CTA tile, 4 warps of 32 x 16, 4 stages of 64 bytes
+            const dim3 grid(static_cast<unsigned>(L.np / 32), static_cast<unsigned>(L.mp / 64));
+            ozaki_gemm_kernel<2, 2, 2, 2, 2, 4, 4, 64><<<grid, 128, 0, s>>>(a);
+            break;
+        }
+        case 3: {   // 64 x 32 CTA tile, 4 warps of 16 x 32, 4 stages of 64 bytes
+            const dim3 grid(static_cast<unsigned>(L.np / 32), static_cast<unsigned>(L.mp / 64));
+            ozaki_gemm_kernel<2, 1, 4, 4, 1, 4, 4, 64><<<grid, 128, 0, s>>>(a);
+            break;
+        }
+        case 4: {   // 64 x 64 CTA tile, 8 warps of 32 x 16, 4 stages of 64 bytes
+            const dim3 grid(static_cast<unsigned>(L.np / 64), static_cast<unsigned>(L.mp / 64));
+            ozaki_gemm_kernel<2, 2, 2, 2, 4, 4, 2, 64><<<grid, 256, 0, s>>>(a);
+            break;
+        }
+        default: {  // 64 x 32 CTA tile, 4 warps of 32 x 16, 3 stages of 128 bytes
+            const dim3 grid(static_cast<unsigned>(L.np / 32), static_cast<unsigned>(L.mp / 64));
+            ozaki_gemm_kernel<2, 2, 2, 2, 2, 3, 4, 128><<<grid, 128, 0, s>>>(a);
+            break;
+        }
+        }
+    } else {
+        // TD/QD: 64 x 16 CTA tile, 4 warps of 16 x 16 (8 outputs each), 3 stages of 128 bytes
+        (void)variant;
+        const dim3 grid(static_cast<unsigned>(L.np / 16), static_cast<unsigned>(L.mp / 64));
+        ozaki_gemm_kernel<P, 1, 2, 4, 1, 3, 3, 128><<<grid, 128, 0, s>>>(a);
     }
     return cudaGetLastError();
 }
+
+template cudaError_t launch_ozaki<2>(const GemmArgs<2>&, int, void*, cudaStream_t, int, int);
+template cudaError_t launch_ozaki<3>(const GemmArgs<3>&, int, void*, cudaStream_t, int, int);
+template cudaError_t launch_ozaki<4>(const GemmArgs<4>&, int, void*, cudaStream_t, int, int);
 
 }  // namespace mpg

@@ -4,7 +4,8 @@
 
 namespace mpg {
 
-constexpr int kOzakiMaxSlices = 16;
+constexpr int kOzakiMaxSlices = 16;       // DD: 128-bit exact fixed point
+constexpr int kOzakiMaxSlicesWide = 40;   // TD, QD: 384-bit floored fixed point
 constexpr int kOzakiDefaultSlices = 14;
 
 // Workspace layout for S slices of an m x n x k product (byte offsets).
@@ -19,10 +20,11 @@ OzakiLayout ozaki_layout(int S, int64_t m, int64_t n, int64_t k, int elem_bytes 
 // Largest k for which the int32 weight sums are exact: S * k * 64 * 64 < 2^31.
 inline int64_t ozaki_k_limit(int S) { return (2147483647LL) / (static_cast<int64_t>(S) * 64 * 64); }
 
-// engine 0: int8 digits on mma.sync s8 (variant 0..4 selects the CTA tiling, 0
-// the default); engine 1: bf16 digits on mma.sync bf16
-cudaError_t launch_ozaki_dd(const GemmArgs<2>& g, int S, void* ws, cudaStream_t s, int variant = 0,
-                            int engine = 0);
+// engine 0: int8 digits on mma.sync s8 (for DD, variant 0..4 selects the CTA
+// tiling, 0 the default); engine 1: bf16 digits on mma.sync bf16 (DD only).
+template <int P>
+cudaError_t launch_ozaki(const GemmArgs<P>& g, int S, void* ws, cudaStream_t s, int variant = 0,
+                         int engine = 0);
 
 // Size of the library's fixed scratch array and its device address on the
 // current device (looked up on first use per device).

@@ -82,7 +82,10 @@ def test_workspace_errors(torch):
     assert e.value.code == -3
     Q = torch.zeros((4, 8, 8), dtype=torch.float64, device="cuda")
     with pytest.raises(mm.MPGError) as e:
-        mm.gemm("qd", Q, Q, algo="int8")
+        mm.gemm("qd", Q, Q, algo="int8")                  # supported, but needs a workspace
+    assert e.value.code == -3
+    with pytest.raises(mm.MPGError) as e:
+        mm.gemm("qd", Q, Q, algo="bf16")                  # the bf16 path is DD only
     assert e.value.code == -4
 
 
@@ -179,3 +182,48 @@ def test_bf16_full_size_sampled(torch):
     cols = sorted(set(int(x) for x in srng.integers(0, n, 2)))
     want, _, _ = OZ.gemm(A, B, S, rows=rows, cols=cols)
     assert_bitwise(C[:, rows][:, :, cols], want, "bf16 4096 sampled")
+
+
+@pytest.mark.parametrize("prec,S", [("td", 1), ("td", 22), ("td", 40), ("qd", 5), ("qd", 29), ("qd", 40)])
+def test_td_qd_bitwise(torch, prec, S):
+    """TD/QD slicing forms: the result is bit-identical to the oracle's steps
+    (ragged shape, ill-scaled A, transposed B), and the workspace slices match
+    the oracle's digits."""
+    from paper_2101_06584_gb300 import mpgemm as mm
+    P = I.P_OF[prec]
+    rng = np.random.default_rng(660 + P + S)
+    m, n, k = 37, 21, 150
+    A, B = I.ill_scaled(P, (m, k), rng), I.uniform(P, (k, n), rng)
+    Ad, Bt = dev(torch, A), dev(torch, B.transpose(0, 2, 1))
+    ws = torch.empty(mm.workspace_size(prec, m, n, k, algo="int8", slices=S), dtype=torch.uint8,
+                     device="cuda")
+    C = host(mm.gemm(prec, Ad, Bt, trans_b=True, algo="int8", slices=S, workspace=ws))
+    want, sig, tau = OZ.gemm(A, B, S)
+    assert_bitwise(C, want, "%s int8 S=%d" % (prec, S))
+    w = host(ws)
+    mp, np_, kp, offB, offSig, offTau = _layout(S, m, n, k)
+    _, DA = OZ.slice_rows(A, S)
+    gsa = w[:S * mp * kp].view(np.int8).reshape(S, mp, kp)
+    assert (gsa[:, :m, :k] == DA).all()
+    assert (w[offSig:offSig + 4 * m].view(np.int32) == sig).all()
+
+
+@pytest.mark.parametrize("prec", ["td", "qd"])
+def test_td_qd_full_size_sampled(torch, prec):
+    """TD/QD 1024^3 on the cancelling ill-scaled inputs of the main workload:
+    sampled entries bit-identical to the oracle's steps and within n 2^-p of
+    the exact product at the default slice counts."""
+    from paper_2101_06584_gb300 import mpgemm as mm
+    P = I.P_OF[prec]
+    n = 1024
+    A, B = I.cancelling_pair(P, n, n, n, I.rng_for(1))
+    ws = torch.empty(mm.workspace_size(prec, n, n, n, algo="int8"), dtype=torch.uint8, device="cuda")
+    C = host(mm.gemm(prec, dev(torch, A), dev(torch, B), algo="int8", workspace=ws))
+    S = {"td": 22, "qd": 29}[prec]
+    srng = np.random.default_rng(670 + P)
+    rows = sorted(set(int(x) for x in srng.integers(0, n, 2)))
+    cols = sorted(set(int(x) for x in srng.integers(0, n, 2)))
+    want, _, _ = OZ.gemm(A, B, S, rows=rows, cols=cols)
+    assert_bitwise(C[:, rows][:, :, cols], want, "%s 1024 sampled" % prec)
+    err = X.gemm_error(C, A, B, [(i, j) for i in rows for j in cols])
+    assert err["err_abs"] <= n * 2.0 ** -{"td": 150, "qd": 200}[prec], err

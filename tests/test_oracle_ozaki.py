@@ -113,7 +113,7 @@ def test_matches_plain_definition_of_weights():
 
 MUTANTS = [
     ("ties away from zero", "digits",
-     lambda comps, sigma, S: _digits_mut(comps, sigma, S, tie="away")),
+     lambda comps, sigma, S, truncate=False: _digits_mut(comps, sigma, S, tie="away")),
     ("scale one too small", "scale_exponent",
      lambda hv: (lambda mx: 0 if mx == 0 else OZ.ilogb(mx) + 1)(max(abs(float(v)) for v in hv))),
     ("drops the least significant weight", "weight_products",
@@ -145,3 +145,50 @@ def test_mutant_caught(monkeypatch, name, attr, fn):
         except AssertionError:
             failures += 1
     assert failures, name
+
+
+@pytest.mark.parametrize("P", [3, 4])
+def test_wide_truncation_and_digits(P):
+    """TD/QD slicing input: each component floored at 2^(sigma - F - 64); the
+    truncation is below the value by less than P units of that power, and the
+    digits reconstruct the truncated value exactly."""
+    rng = np.random.default_rng(510 + P)
+    x = I.random_mp(P, 200, rng, spread=40)
+    for t in range(x.shape[1]):
+        comps = [float(c) for c in x[:, t]]
+        for S in (3, 22, 40):
+            sg = OZ.scale_exponent([comps[0]])
+            tv = OZ.truncated_value(comps, sg, S)
+            exact = X.value(comps)
+            unit = Fraction(2) ** (sg - (7 * S + 12) - OZ.GUARD_BITS)
+            assert 0 <= exact - tv < P * unit
+            ds, rem = OZ.digits(comps, sg, S, truncate=True)
+            recon = sum((Fraction(d) * Fraction(2) ** (-7 * (s + 1)) for s, d in enumerate(ds)), Fraction(0))
+            assert (recon + rem * Fraction(2) ** (-7 * S)) * Fraction(2) ** sg == tv
+            assert all(-64 <= d <= 64 for d in ds) and abs(rem) <= Fraction(1, 2)
+
+
+def test_weight_groups():
+    for S in (1, 2, 3, 4, 13, 22, 29, 40):
+        for P in (2, 3, 4):
+            groups = OZ.weight_groups(S, P)
+            flat = [w for g in groups for w in g]
+            assert flat == list(range(S + 1, 1, -1))
+            assert all(len(g) == (1 if P == 2 else min(3, len(g))) for g in groups)
+            assert all(len(g) <= (1 if P == 2 else 3) for g in groups)
+
+
+@pytest.mark.parametrize("P,S", [(3, 22), (4, 29)])
+def test_td_qd_error_meets_bound(P, S):
+    rng = np.random.default_rng(520 + P)
+    m, n, k = 6, 5, 40
+    pbits = {3: 150, 4: 200}[P]
+    for A, B in ((I.uniform(P, (m, k), rng), I.uniform(P, (k, n), rng)),
+                 I.cancelling_pair(P, m, n, k, rng)):
+        C, _, _ = OZ.gemm(A, B, S)
+        err = X.gemm_error(C, A, B, [(i, j) for i in range(m) for j in range(n)])
+        assert err["err_abs"] <= k * 2.0 ** -pbits, err
+        # three fewer slices lose about 2^21
+        C2, _, _ = OZ.gemm(A, B, S - 3)
+        err2 = X.gemm_error(C2, A, B, [(i, j) for i in range(m) for j in range(n)])
+        assert err2["err_abs"] > err["err_abs"] * 2.0 ** 10
