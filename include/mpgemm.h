@@ -123,7 +123,7 @@ typedef enum mpg_algo {
     MPG_ALGO_AUTO = 0,       /* the FP64-EFT kernel (k-sequential unless split_k > 1) */
     MPG_ALGO_FP64_EFT = 1,   /* FP64 error-free transformations on the CUDA cores */
     MPG_ALGO_INT8_OZAKI = 2, /* DD/TD/QD: error-free INT8 slicing on the tensor cores */
-    MPG_ALGO_BF16_SLICES = 3 /* DD only: the same slices as bf16 on the bf16 tensor path */
+    MPG_ALGO_BF16_SLICES = 3 /* DD/TD/QD: the same digits as bf16 on tcgen05 (TMEM accumulators) */
 } mpg_algo;
 
 /* Options of mpgemm_ex.  Zero-initialised options give the plain call. */
@@ -174,13 +174,19 @@ int mpgemm_ex(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k,
  * and acc = TDaddq / QDadd (Sec. 2.3, Alg. 5) of (V 2^(sigma_i + tau_j - 7w),
  * 0, ...) with w the group's largest weight.
  *
- * MPG_ALGO_BF16_SLICES (DD only; not in the paper): the same digits, scales,
- * weight sums and accumulation, with the slice products on the bf16 tensor
- * path (mma.sync m16n8k16, fp32 accumulation): the digits are exact in bf16,
- * every product and partial sum is an integer, and the fp32 partial sums are
- * moved into the int32 weight sums every 2048 values of k (so each stays
- * below 2^23 and exact).  The result is bit-identical to MPG_ALGO_INT8_OZAKI.
- * Workspace layout as above with 2-byte (bf16) digits in place of int8. */
+ * MPG_ALGO_BF16_SLICES (DD/TD/QD; not in the paper): the same digits, scales,
+ * weight sums and accumulation, with the slice products on the 5th-generation
+ * tensor cores: the digits are stored as bf16 (exact: |d| <= 64), loaded by
+ * TMA, multiplied by tcgen05.mma (kind::f16, M = N = 128, fp32 accumulation in
+ * tensor memory), and each accumulator is drained into exact integer sums
+ * after at most 2048 values of k of one weight, so every fp32 partial sum is
+ * an integer below 2^23 and exact.  The result is bit-identical to
+ * MPG_ALGO_INT8_OZAKI.  Workspace: a 256-byte header whose first int32 is 0
+ * after a normal run (a device-side wait that exceeded about a second leaves
+ * the code of the waiting role there), then the digits as bf16 with rows
+ * padded to 128 ([S][mp][kp] for op(A), [S][np][kp] for op(B)^T), then the
+ * int32 exponents; mpgemm_workspace_size gives the total.
+
 
 /* Bytes of workspace mpgemm_ex needs for these options and sizes (0 if none). */
 size_t mpgemm_workspace_size(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k);

@@ -13,20 +13,21 @@ reader can check it line by line.  DD (P = 2):
            Every |d_s| <= 64.  a = 2^sigma (sum_s d_s 2^-7s + 2^-7S x_S).
   products P_w = sum over s + t = w (1 <= s, t <= S) of A^(s) B^(t), for
            w = 2..S+1, computed exactly in integers.
-  accumulate  acc = (0, 0); for w = S+1 down to 2:
-           acc = DDadd(acc, (P_w[i,j] 2^(sigma_i + tau_j - 7w), 0))
-           with the oracle's DDadd (Alg. 1).  The scaled value is an exact
-           binary64 for the sizes this form accepts.
+  accumulate  weights are taken in groups of three from the least
+           significant end (w = S+1, S, S-1; then S-2, ...):
+           V = P_w + 2^7 P_(w-1) + 2^14 P_(w-2), exact and below 2^46;
+           acc = (0, 0); for each group in that order:
+           acc = DDadd(acc, (V 2^(sigma_i + tau_j - 7w), 0)), w the group's
+           largest weight, with the oracle's DDadd (Alg. 1).  The scaled value
+           is an exact binary64 for the sizes this form accepts.
 
 TD and QD (P = 3, 4) differ in two places:
   slices   each component is first floored to a multiple of
            2^(sigma - F - 64), F = 7S + 12 (64 guard bits below the last
            digit's unit); the digits are those of the sum of the floored
            components, exactly as above.
-  accumulate  weights are taken in groups of three from the least
-           significant end: V = P_w + 2^7 P_(w-1) + 2^14 P_(w-2) (exact, below
-           2^46); acc = add(acc, (V 2^(sigma + tau - 7w), 0, ...)) with TDaddq
-           (Sec. 2.3) or QDadd (Alg. 5), w the group's largest weight.
+  accumulate  as for DD with TDaddq (Sec. 2.3) or QDadd (Alg. 5) of
+           (V 2^(sigma + tau - 7w), 0, ...).
 """
 import math
 from fractions import Fraction
@@ -126,11 +127,10 @@ PREC_OF = {2: "dd", 3: "td", 4: "qd"}
 
 
 def weight_groups(S, P):
-    """The weights in accumulation order, grouped: one per group for DD,
-    three for TD/QD, from the least significant (w = S+1) end."""
+    """The weights in accumulation order, three to a group, from the least
+    significant (w = S+1) end (the last group may be shorter)."""
     ws = list(range(S + 1, 1, -1))
-    g = 1 if P == 2 else 3
-    return [ws[i:i + g] for i in range(0, len(ws), g)]
+    return [ws[i:i + 3] for i in range(0, len(ws), 3)]
 
 
 def gemm(A, B, S, rows=None, cols=None, L=None):

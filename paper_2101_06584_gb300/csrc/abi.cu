@@ -171,15 +171,13 @@ template <int P>
 static int ozaki_call(const GemmArgs<P>& g, const mpgemm_opts* o)
 {
     const int engine = o->algo == MPG_ALGO_BF16_SLICES ? 1 : 0;
-    if (engine == 1 && P != 2)
-        return fail(MPG_EUNSUPPORTED, "the bf16 slicing path is provided for DD (P = 2) only");
     const int S = o->slices ? o->slices : ozaki_default_slices(P);
     if (S < 1 || S > ozaki_max_slices(P))
         return fail(MPG_EINVAL, "slices must be in 1..%d for P = %d (got %d)", ozaki_max_slices(P), P, S);
     if (g.k > ozaki_k_limit(S))
         return fail(MPG_EUNSUPPORTED, "k = %lld exceeds %lld, the largest k whose %d-slice int32 "
                     "sums are exact", (long long)g.k, (long long)ozaki_k_limit(S), S);
-    const OzakiLayout L = ozaki_layout(S, g.m, g.n, g.k, engine == 1 ? 2 : 1);
+    const OzakiLayout L = engine == 1 ? ozaki_tc_layout(S, g.m, g.n, g.k) : ozaki_layout(S, g.m, g.n, g.k, 1);
     if (L.mp / 64 > 65535) return fail(MPG_EINVAL, "m too large for the slicing form's grid");
     if (!o->workspace) return fail(MPG_EWORKSPACE, "the slicing form needs a workspace of %lld bytes",
                                    (long long)L.total);
@@ -319,10 +317,10 @@ size_t mpgemm_workspace_size(int P, const mpgemm_opts* opts, int64_t m, int64_t 
     if (!opts || (opts->algo != MPG_ALGO_INT8_OZAKI && opts->algo != MPG_ALGO_BF16_SLICES) || P < 2 ||
         P > 4 || m < 0 || n < 0 || k < 0)
         return 0;
-    if (opts->algo == MPG_ALGO_BF16_SLICES && P != 2) return 0;
     const int S = opts->slices ? opts->slices : ozaki_default_slices(P);
     if (S < 1 || S > ozaki_max_slices(P)) return 0;
-    return static_cast<size_t>(ozaki_layout(S, m, n, k, opts->algo == MPG_ALGO_BF16_SLICES ? 2 : 1).total);
+    if (opts->algo == MPG_ALGO_BF16_SLICES) return static_cast<size_t>(ozaki_tc_layout(S, m, n, k).total);
+    return static_cast<size_t>(ozaki_layout(S, m, n, k, 1).total);
 }
 
 int mpgemm_dd_int8_static(int64_t m, int64_t n, int64_t k, const double* const A[2], int64_t lda,

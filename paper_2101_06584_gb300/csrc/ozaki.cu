@@ -25,6 +25,7 @@
 #include "mp_arith.cuh"
 #include "ozaki.h"
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <cstdint>
@@ -460,9 +461,9 @@ struct Cursor {
 
 // CTA of WM x WN warps; each warp owns MT x NT fragments of 16 x 8 outputs,
 // so the CTA tile is (WM*MT*16) x (WN*NT*8).  Slice tiles of KS bytes of k
-// are staged through a STG-deep cp.async pipeline.  P output components:
-// DD adds every weight's sum; TD/QD combine three weights exactly in int64
-// first and add the group.
+// are staged through a STG-deep cp.async pipeline.  P output components;
+// three weights are combined exactly in int64 and each group is added with
+// the precision's add.
 template <int P, int MT, int NT, int WM, int WN, int STG, int MINB, int KS>
 __global__ void __launch_bounds__(WM * WN * 32, MINB) ozaki_gemm_kernel(const OzakiGemmArgs g)
 {
@@ -572,12 +573,12 @@ __global__ void __launch_bounds__(WM * WN * 32, MINB) ozaki_gemm_kernel(const Oz
         const int w = cm.w;
         cm.advance(S, KT);
         if (cm.w != w || it == total - 1) {
-            // TD/QD: position of w in its group of three, counted from the
-            // least significant weight S+1; the group ends at its third
-            // weight or at w = 2
+            // position of w in its group of three, counted from the least
+            // significant weight S+1; the group ends at its third weight or
+            // at w = 2
             const int j = (S + 1 - w) % 3;
-            const bool group_end = (P == 2) || j == 2 || w == 2;
-            const int wmax = P == 2 ? w : w + j;
+            const bool group_end = j == 2 || w == 2;
+            const int wmax = w + j;
 #pragma unroll
             for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
@@ -585,12 +586,8 @@ __global__ void __launch_bounds__(WM * WN * 32, MINB) ozaki_gemm_kernel(const Oz
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
                         double y[P];
-                        if constexpr (P == 2) {
-                            y[0] = scaled_int(ci[mt][nt][r], sg[mt][r >> 1] + tu[nt][r & 1] - 7 * w);
-                        } else {
-                            grp[mt][nt][r] += static_cast<int64_t>(ci[mt][nt][r]) << (7 * j);
-                            y[0] = scaled_int64(grp[mt][nt][r], sg[mt][r >> 1] + tu[nt][r & 1] - 7 * wmax);
-                        }
+                        grp[mt][nt][r] += static_cast<int64_t>(ci[mt][nt][r]) << (7 * j);
+                        y[0] = scaled_int64(grp[mt][nt][r], sg[mt][r >> 1] + tu[nt][r & 1] - 7 * wmax);
                         ci[mt][nt][r] = 0;
                         if (group_end) {
 #pragma unroll
@@ -621,174 +618,376 @@ __global__ void __launch_bounds__(WM * WN * 32, MINB) ozaki_gemm_kernel(const Oz
             }
 }
 
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
+// ------------------------------------------------------- tcgen05 engine
+//
+// The bf16 digits on the 5th-generation tensor cores.  A persistent CTA per SM
+// owns 128 x 128 tiles of C.  Warp 0 streams 128 x 64 bf16 slice tiles of
+// op(A) and op(B)^T into shared memory with TMA (128-byte swizzle, 4-stage
+// mbarrier ring).  Warp 1 owns 512 TMEM columns and issues
+// tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 128, K = 16, fp32
+// accumulation), filling one of two TMEM accumulators per segment: the k
+// tiles of one weight, at most 2048 values of k, so every fp32 partial sum
+// of integer products of at most 2^12 stays an exact integer below 2^23.
+// Warps 2-5 (one TMEM lane quadrant each, one row of the tile per thread)
+// drain each segment: fp32 -> int, shifted into that thread's int64 group
+// sums held in TMEM columns 256..511; at the end of a group of three
+// weights they add the exact binary64 group value to C with the precision's
+// add.  The integer weight sums equal those of the int8 path, so the result
+// is bit-identical to it.  Every wait is bounded (about 1 s): on a timeout
+// the kernel records an error code in the workspace header, drains what it
+// issued, frees TMEM and returns.
+
+namespace tc {
+constexpr int BM = 128, BN = 128;
+constexpr int KE = 64;                                   // k-step in bf16 elements (128 bytes)
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * KE * 2, B_BYTES = BN * KE * 2;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;           // 32 KB
+constexpr int SEG_TILES = 2048 / KE;                     // k-tiles per fp32 segment
+constexpr int TMEM_COLS = 512;
+constexpr int ACC_COLS = 128;                            // two fp32 accumulators at 0 and 128
+constexpr int GRP_COL = 256;                             // int64 group sums, 2 columns per output
+constexpr unsigned long long TIMEOUT_NS = 1000000000ull;
+}  // namespace tc
+
+struct TcArgs {
+    const int* sig;
+    const int* tau;
+    double* C[4];
+    int64_t ldc, m, n, kp;
+    int S, tiles_m, tiles_n;
+    int* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false after about a second, or once another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, volatile int* abort_flag)
+{
+    const unsigned long long t0 = gtimer();
+    while (!mbar_try(b, parity)) {
+        if (*abort_flag) return false;
+        if (gtimer() - t0 > tc::TIMEOUT_NS) return false;
+    }
+    return true;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar)
 {
     asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
 }
-
-// The same weight sums with the digits as bf16 on the bf16 tensor path
-// (mma.sync m16n8k16, fp32 accumulation).  On GB300 this runs no faster than
-// the int8 kernel (DD 4096^3, S = 13: 89.7 vs 87.8 ms): at the bf16 rate its
-// fragment loads would need ~185 B/clk/SM of shared memory, more than the SM
-// delivers, and larger warp tiles do not fit beside the DD accumulators.  Every product is an integer of at
-// most 2^12 and every partial sum an integer; the fp32 fragments are drained
-// into the int32 weight sums every 2048 values of k, so no partial sum exceeds
-// 2^23 and each is exactly representable: the int32 sums, and so the result,
-// equal those of the int8 path bit for bit.
-template <int MT, int NT, int WM, int WN, int STG, int MINB, int KSE>
-__global__ void __launch_bounds__(WM * WN * 32, MINB) ozaki_gemm_bf16_kernel(const OzakiGemmArgs g)
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr)
 {
-    constexpr int NTHR = WM * WN * 32;
-    constexpr int BM = WM * MT * 16;
-    constexpr int BN = WN * NT * 8;
-    constexpr int SROWE = KSE + 8;        // row stride in elements: conflict-free fragment loads
-    constexpr int CPR = KSE * 2 / 16;     // 16-byte chunks per row
-    constexpr int FLUSH = 2048 / KSE;     // k-tiles between drains of the fp32 fragments
-    __shared__ __align__(16) uint16_t As[STG][BM * SROWE];
-    __shared__ __align__(16) uint16_t Bs[STG][BN * SROWE];
+    return static_cast<uint64_t>((saddr & 0x3FFFF) >> 4) | (1ull << 16) |
+           (static_cast<uint64_t>(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
+// Instruction descriptor: kind::f16, bf16 A and B (K-major), fp32 D, M = 128, N = 128.
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 
-    const mp::Rn f = mp::make_rn();
-    const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
-    const int gq = lane >> 2, tq = lane & 3;
-    const int wm = warp / WN, wn = warp % WN;
-    const int64_t m0 = static_cast<int64_t>(blockIdx.y) * BM;
-    const int64_t n0 = static_cast<int64_t>(blockIdx.x) * BN;
-    const int S = g.S;
-    const int KT = static_cast<int>(g.kp / KSE);
-    const int total = (S * (S + 1) / 2) * KT;
+__device__ __forceinline__ void umma(uint32_t d, uint64_t da, uint64_t db, uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(d), "l"(da), "l"(db), "r"(kTcIdesc), "r"(acc));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_u32(bar)) : "memory");
+}
+#define MPG_R32(r) "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), \
+    "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), \
+    "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), \
+    "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+#define MPG_W32(r) "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), \
+    "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), \
+    "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), \
+    "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+// 32 consecutive 32-bit TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : MPG_R32(r)
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
+        ::"r"(taddr), MPG_W32(r)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
-    int sg[MT][2], tu[NT][2];
-#pragma unroll
-    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) sg[mt][h] = g.sig[m0 + wm * MT * 16 + mt * 16 + gq + h * 8];
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) tu[nt][h] = g.tau[n0 + wn * NT * 8 + nt * 8 + 2 * tq + h];
+template <int P>
+__global__ void __launch_bounds__(192, 1)
+ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                const TcArgs g)
+{
+    extern __shared__ uint8_t dsm[];
+    __shared__ __align__(8) uint64_t full[tc::STAGES], empty[tc::STAGES], accf[2], acce[2], fin;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    __shared__ int s_tau[tc::BN];
 
-    double acc0[MT][NT][4], acc1[MT][NT][4];
-    float cf[MT][NT][4];
-    int ci[MT][NT][4];
-#pragma unroll
-    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                acc0[mt][nt][r] = 0.0; acc1[mt][nt][r] = 0.0; cf[mt][nt][r] = 0.f; ci[mt][nt][r] = 0;
-            }
+    const uint32_t raw = smem_u32(dsm);
+    uint8_t* stage0 = dsm + (((raw + 1023u) & ~1023u) - raw);   // 1024-aligned for the swizzle
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int* abortp = &abort_flag;
 
-    auto load = [&](int stage, const Cursor& c) {
-        const uint16_t* a = static_cast<const uint16_t*>(g.sa) +
-                            ((static_cast<int64_t>(c.s - 1) * g.mp + m0) * g.kp) + static_cast<int64_t>(c.kt) * KSE;
-        const uint16_t* b = static_cast<const uint16_t*>(g.sb) +
-                            ((static_cast<int64_t>(c.w - c.s - 1) * g.np + n0) * g.kp) + static_cast<int64_t>(c.kt) * KSE;
-        for (int chunk = tid; chunk < (BM + BN) * CPR; chunk += NTHR) {
-            const int row = chunk / CPR, col = (chunk % CPR) * 8;
-            if (row < BM)
-                cp_async16(&As[stage][row * SROWE + col], a + static_cast<int64_t>(row) * g.kp + col);
-            else
-                cp_async16(&Bs[stage][(row - BM) * SROWE + col],
-                           b + static_cast<int64_t>(row - BM) * g.kp + col);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < tc::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
         }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 128);
+        }
+        mbar_init(&fin, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&tmem_base)), "r"(tc::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    const int S = g.S;
+    const int KT = static_cast<int>(g.kp / tc::KE);
+    const int per_tile = (S * (S + 1) / 2) * KT;
+    const int ntiles = g.tiles_m * g.tiles_n;
+    auto fail = [&](int code) {
+        *abortp = 1;
+        atomicCAS(g.err, 0, code);
     };
 
-    Cursor ld{S + 1, 1, 0}, cm{S + 1, 1, 0};
-#pragma unroll
-    for (int st = 0; st < STG - 1; ++st) {
-        if (st < total) load(st, ld);
-        ld.advance(S, KT);
-        cp_async_commit();
-    }
-
-    int since = 0;
-    for (int it = 0; it < total; ++it) {
-        cp_async_wait<STG - 2>();
-        __syncthreads();
-        {
-            const int nxt = it + STG - 1;
-            if (nxt < total) load(nxt % STG, ld);
-            ld.advance(S, KT);
-            cp_async_commit();
-        }
-        const uint16_t* as = As[it % STG];
-        const uint16_t* bs = Bs[it % STG];
-#pragma unroll
-        for (int kk = 0; kk < KSE; kk += 16) {
-            uint32_t af[MT][4], bf[NT][2];
-#pragma unroll
-            for (int mt = 0; mt < MT; ++mt) {
-                const int r = wm * MT * 16 + mt * 16 + gq;
-                af[mt][0] = *reinterpret_cast<const uint32_t*>(as + r * SROWE + kk + 2 * tq);
-                af[mt][1] = *reinterpret_cast<const uint32_t*>(as + (r + 8) * SROWE + kk + 2 * tq);
-                af[mt][2] = *reinterpret_cast<const uint32_t*>(as + r * SROWE + kk + 8 + 2 * tq);
-                af[mt][3] = *reinterpret_cast<const uint32_t*>(as + (r + 8) * SROWE + kk + 8 + 2 * tq);
-            }
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt) {
-                const int c = wn * NT * 8 + nt * 8 + gq;
-                bf[nt][0] = *reinterpret_cast<const uint32_t*>(bs + c * SROWE + kk + 2 * tq);
-                bf[nt][1] = *reinterpret_cast<const uint32_t*>(bs + c * SROWE + kk + 8 + 2 * tq);
-            }
-#pragma unroll
-            for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < NT; ++nt) mma_bf16(cf[mt][nt], af[mt], bf[nt]);
-        }
-        const int w = cm.w;
-        cm.advance(S, KT);
-        const bool weight_end = (cm.w != w || it == total - 1);
-        if (++since == FLUSH || weight_end) {
-#pragma unroll
-            for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        ci[mt][nt][r] += __float2int_rn(cf[mt][nt][r]);
-                        cf[mt][nt][r] = 0.f;
-                    }
-            since = 0;
-        }
-        if (weight_end) {
-#pragma unroll
-            for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        const int e = sg[mt][r >> 1] + tu[nt][r & 1] - 7 * w;
-                        const double x[2] = {acc0[mt][nt][r], acc1[mt][nt][r]};
-                        const double y[2] = {scaled_int(ci[mt][nt][r], e), f.zero};
-                        double z[2];
-                        mp::dd_add(f, x, y, z);
-                        acc0[mt][nt][r] = z[0];
-                        acc1[mt][nt][r] = z[1];
-                        ci[mt][nt][r] = 0;
-                    }
-        }
-    }
-    cp_async_wait<0>();
-
-#pragma unroll
-    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int64_t row = m0 + wm * MT * 16 + mt * 16 + gq + (r >> 1) * 8;
-                const int64_t col = n0 + wn * NT * 8 + nt * 8 + 2 * tq + (r & 1);
-                if (row < g.m && col < g.n) {
-                    g.C[0][row * g.ldc + col] = acc0[mt][nt][r];
-                    g.C[1][row * g.ldc + col] = acc1[mt][nt][r];
+    if (warp == 0) {
+        // ---------------------------------------------------------- producer
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                const int m0 = (tile % g.tiles_m) * tc::BM, n0 = (tile / g.tiles_m) * tc::BN;
+                Cursor c{S + 1, 1, 0};
+                for (int i = 0; i < per_tile; ++i, ++it) {
+                    const uint32_t st = it % tc::STAGES, ph = (it / tc::STAGES) & 1u;
+                    if (!mbar_wait(&empty[st], ph ^ 1u, abortp)) { fail(1); ok = false; break; }
+                    uint8_t* sa = stage0 + st * tc::STAGE_BYTES;
+                    mbar_expect_tx(&full[st], tc::STAGE_BYTES);
+                    tma_load_3d(sa, &tmA, c.kt * tc::KE, m0, c.s - 1, &full[st]);
+                    tma_load_3d(sa + tc::A_BYTES, &tmB, c.kt * tc::KE, n0, c.w - c.s - 1, &full[st]);
+                    c.advance(S, KT);
                 }
             }
+            // the last loads issued must have landed before the CTA exits
+            for (uint32_t j = 0; j < tc::STAGES && j < it; ++j) {
+                const uint32_t k = it - 1 - j;
+                const unsigned long long t0 = gtimer();
+                while (!mbar_try(&full[k % tc::STAGES], (k / tc::STAGES) & 1u) && gtimer() - t0 < tc::TIMEOUT_NS) {
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // --------------------------------------------------------------- MMA
+        if (lane == 0) {
+            uint32_t it = 0, seg = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                Cursor c{S + 1, 1, 0};
+                int seg_tiles = 0;
+                uint32_t b = 0;
+                for (int i = 0; i < per_tile; ++i, ++it) {
+                    if (seg_tiles == 0) {
+                        b = seg & 1u;
+                        if (!mbar_wait(&acce[b], ((seg >> 1) & 1u) ^ 1u, abortp)) { fail(2); ok = false; break; }
+                    }
+                    const uint32_t st = it % tc::STAGES, ph = (it / tc::STAGES) & 1u;
+                    if (!mbar_wait(&full[st], ph, abortp)) { fail(3); ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(stage0 + st * tc::STAGE_BYTES);
+                    const uint64_t da = umma_desc(sa), db = umma_desc(sa + tc::A_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < tc::KE / 16; ++kk)
+                        umma(tmem + b * tc::ACC_COLS, da + 2ull * kk, db + 2ull * kk,
+                             (seg_tiles > 0 || kk > 0) ? 1u : 0u);
+                    umma_commit(&empty[st]);
+                    ++seg_tiles;
+                    const int w = c.w;
+                    c.advance(S, KT);
+                    if (c.w != w || seg_tiles == tc::SEG_TILES) {
+                        umma_commit(&accf[b]);
+                        ++seg;
+                        seg_tiles = 0;
+                    }
+                }
+            }
+            // every MMA issued has completed before TMEM is released
+            umma_commit(&fin);
+            const unsigned long long t0 = gtimer();
+            while (!mbar_try(&fin, 0u) && gtimer() - t0 < tc::TIMEOUT_NS) {
+            }
+        }
+    } else {
+        // ---------------------------------------------------------- epilogue
+        const mp::Rn f = mp::make_rn();
+        const int q = warp & 3;                          // TMEM lane quadrant of this warp
+        const int r = 32 * q + lane;                     // row of the tile
+        const uint32_t lane_off = static_cast<uint32_t>(32 * q) << 16;
+        uint32_t seg = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            const int m0 = (tile % g.tiles_m) * tc::BM, n0 = (tile / g.tiles_m) * tc::BN;
+            const int64_t row = m0 + r;
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            s_tau[r] = g.tau[n0 + r];
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            const int sg = g.sig[row];
+            uint32_t z[32];
+#pragma unroll
+            for (int t = 0; t < 32; ++t) z[t] = 0u;
+#pragma unroll
+            for (int c0 = 0; c0 < 2 * tc::BN; c0 += 32) tmem_st32(tmem + lane_off + tc::GRP_COL + c0, z);
+            tmem_wait_st();
+            Cursor c{S + 1, 1, 0};
+            int seg_tiles = 0;
+            bool first_group = true;
+            for (int i = 0; i < per_tile; ++i) {
+                ++seg_tiles;
+                const int w = c.w;
+                c.advance(S, KT);
+                const bool weight_end = c.w != w;
+                if (!weight_end && seg_tiles != tc::SEG_TILES) continue;
+                seg_tiles = 0;
+                const uint32_t b = seg & 1u;
+                // the decision must be warp-uniform: the TMEM loads below are .sync.aligned
+                if (!__all_sync(0xffffffffu, mbar_wait(&accf[b], (seg >> 1) & 1u, abortp))) {
+                    fail(4);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const int j = (S + 1 - w) % 3;
+                for (int c0 = 0; c0 < tc::BN; c0 += 32) {
+                    uint32_t fv[32], g0[32], g1[32];
+                    tmem_ld32(tmem + lane_off + b * tc::ACC_COLS + c0, fv);
+                    tmem_ld32(tmem + lane_off + tc::GRP_COL + 2 * c0, g0);
+                    tmem_ld32(tmem + lane_off + tc::GRP_COL + 2 * c0 + 32, g1);
+                    tmem_wait_ld();
+                    // columns c0..c0+15 live in g0, c0+16..c0+31 in g1 (lo, hi words)
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) {
+                        int64_t V = static_cast<int64_t>((static_cast<uint64_t>(g0[2 * t + 1]) << 32) | g0[2 * t]);
+                        V += static_cast<int64_t>(__float2int_rn(__uint_as_float(fv[t]))) << (7 * j);
+                        g0[2 * t] = static_cast<uint32_t>(static_cast<uint64_t>(V));
+                        g0[2 * t + 1] = static_cast<uint32_t>(static_cast<uint64_t>(V) >> 32);
+                    }
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) {
+                        int64_t V = static_cast<int64_t>((static_cast<uint64_t>(g1[2 * t + 1]) << 32) | g1[2 * t]);
+                        V += static_cast<int64_t>(__float2int_rn(__uint_as_float(fv[16 + t]))) << (7 * j);
+                        g1[2 * t] = static_cast<uint32_t>(static_cast<uint64_t>(V));
+                        g1[2 * t + 1] = static_cast<uint32_t>(static_cast<uint64_t>(V) >> 32);
+                    }
+                    tmem_st32(tmem + lane_off + tc::GRP_COL + 2 * c0, g0);
+                    tmem_st32(tmem + lane_off + tc::GRP_COL + 2 * c0 + 32, g1);
+                    tmem_wait_st();
+                }
+                tc_fence_before();
+                mbar_arrive(&acce[b]);
+                ++seg;
+                if (!(weight_end && (j == 2 || w == 2))) continue;
+                // end of a group: add its exact value to C
+                const int wmax = w + j;
+                for (int c0 = 0; c0 < tc::BN; c0 += 32) {
+                    uint32_t g0[32], g1[32];
+                    tmem_ld32(tmem + lane_off + tc::GRP_COL + 2 * c0, g0);
+                    tmem_ld32(tmem + lane_off + tc::GRP_COL + 2 * c0 + 32, g1);
+                    tmem_wait_ld();
+                    int64_t Vs[32];
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) {
+                        Vs[t] = static_cast<int64_t>((static_cast<uint64_t>(g0[2 * t + 1]) << 32) | g0[2 * t]);
+                        Vs[16 + t] = static_cast<int64_t>((static_cast<uint64_t>(g1[2 * t + 1]) << 32) | g1[2 * t]);
+                    }
+#pragma unroll
+                    for (int t = 0; t < 32; ++t) {
+                        const int64_t col = n0 + c0 + t;
+                        if (row >= g.m || col >= g.n) continue;
+                        const int64_t V = Vs[t];
+                        double y[P], acc[P], zz[P];
+                        y[0] = scaled_int64(V, sg + s_tau[c0 + t] - 7 * wmax);
+#pragma unroll
+                        for (int cc = 1; cc < P; ++cc) y[cc] = f.zero;
+#pragma unroll
+                        for (int cc = 0; cc < P; ++cc)
+                            acc[cc] = first_group ? 0.0 : g.C[cc][row * g.ldc + col];
+                        mp::Ops<P>::add(f, acc, y, zz);
+#pragma unroll
+                        for (int cc = 0; cc < P; ++cc) g.C[cc][row * g.ldc + col] = zz[cc];
+                    }
+                    tmem_st32(tmem + lane_off + tc::GRP_COL + 2 * c0, z);
+                    tmem_st32(tmem + lane_off + tc::GRP_COL + 2 * c0 + 32, z);
+                    tmem_wait_st();
+                }
+                first_group = false;
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tc::TMEM_COLS));
+    }
 }
 
 // ------------------------------------------------------- fixed scratch
@@ -867,11 +1066,97 @@ static cudaError_t slice_operand(const Planes<P>& pl, int64_t count, int64_t len
     return cudaGetLastError();
 }
 
+// ----------------------------------------------------- tcgen05 host side
+
+OzakiLayout ozaki_tc_layout(int S, int64_t m, int64_t n, int64_t k)
+{
+    OzakiLayout L;
+    L.S = S;
+    L.mp = round_up(m > 0 ? m : 1, tc::BM);
+    L.np = round_up(n > 0 ? n : 1, tc::BN);
+    L.kp = round_up(k > 0 ? k : 1, KPAD);
+    L.offA = 256;                                     // bytes 0..255: header (error code)
+    L.offB = L.offA + round_up(static_cast<int64_t>(S) * L.mp * L.kp * 2, 256);
+    L.offSig = L.offB + round_up(static_cast<int64_t>(S) * L.np * L.kp * 2, 256);
+    L.offTau = L.offSig + round_up(L.mp * 4, 256);
+    L.total = L.offTau + round_up(L.np * 4, 256);
+    return L;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
+{
+    static std::mutex mu;
+    static EncodeTiledFn fn = nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// A [S][rows][kp] bf16 slice array as a 3-D TMA tensor; boxes of 64 x 128 x 1,
+// 128-byte swizzle (the UMMA K-major layout).
+static bool slice_map(CUtensorMap* map, void* base, int S, int64_t rows, int64_t kp)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {static_cast<cuuint64_t>(kp), static_cast<cuuint64_t>(rows),
+                                static_cast<cuuint64_t>(S)};
+    const cuuint64_t strides[2] = {static_cast<cuuint64_t>(kp) * 2, static_cast<cuuint64_t>(rows * kp) * 2};
+    const cuuint32_t box[3] = {tc::KE, 128, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int P>
+static cudaError_t launch_ozaki_tc(const GemmArgs<P>& g, int S, void* ws, cudaStream_t s)
+{
+    const OzakiLayout L = ozaki_tc_layout(S, g.m, g.n, g.k);
+    int8_t* base = static_cast<int8_t*>(ws);
+    int* err = reinterpret_cast<int*>(base);
+    uint16_t* sa = reinterpret_cast<uint16_t*>(base + L.offA);
+    uint16_t* sb = reinterpret_cast<uint16_t*>(base + L.offB);
+    int* sig = reinterpret_cast<int*>(base + L.offSig);
+    int* tau = reinterpret_cast<int*>(base + L.offTau);
+    Planes<P> pa, pb;
+    for (int c = 0; c < P; ++c) {
+        pa.c[c] = g.A[c];
+        pb.c[c] = g.B[c];
+    }
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = slice_operand(pa, g.m, g.k, g.lda, !g.trans_a, S, L.mp, L.kp, sa, sig, s);
+    if (e == cudaSuccess) e = slice_operand(pb, g.n, g.k, g.ldb, g.trans_b != 0, S, L.np, L.kp, sb, tau, s);
+    if (e != cudaSuccess) return e;
+    CUtensorMap ma, mb;
+    if (!slice_map(&ma, sa, S, L.mp, L.kp) || !slice_map(&mb, sb, S, L.np, L.kp)) return cudaErrorInvalidValue;
+    TcArgs a{sig, tau, {nullptr, nullptr, nullptr, nullptr}, g.ldc, g.m, g.n, L.kp, S,
+             static_cast<int>(L.mp / tc::BM), static_cast<int>(L.np / tc::BN), err};
+    for (int c = 0; c < P; ++c) a.C[c] = g.C[c];
+    const int smem = tc::STAGES * tc::STAGE_BYTES + 1024;
+    e = cudaFuncSetAttribute(ozaki_tc_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int tiles = a.tiles_m * a.tiles_n;
+    const int grid = tiles < num_sms() ? tiles : num_sms();
+    ozaki_tc_kernel<P><<<grid, 192, smem, s>>>(ma, mb, a);
+    return cudaGetLastError();
+}
+
 template <int P>
 cudaError_t launch_ozaki(const GemmArgs<P>& g, int S, void* ws, cudaStream_t s, int variant, int engine)
 {
-    const int eb = engine == 1 ? 2 : 1;
-    const OzakiLayout L = ozaki_layout(S, g.m, g.n, g.k, eb);
+    if (engine == 1) return launch_ozaki_tc<P>(g, S, ws, s);
+    const OzakiLayout L = ozaki_layout(S, g.m, g.n, g.k, 1);
     int8_t* base = static_cast<int8_t*>(ws);
     int* sig = reinterpret_cast<int*>(base + L.offSig);
     int* tau = reinterpret_cast<int*>(base + L.offTau);
@@ -880,31 +1165,17 @@ cudaError_t launch_ozaki(const GemmArgs<P>& g, int S, void* ws, cudaStream_t s, 
         pa.c[c] = g.A[c];
         pb.c[c] = g.B[c];
     }
-    cudaError_t e;
     // op(A) row i: contiguous unless A is stored transposed; op(B) column j:
     // contiguous only if B is stored transposed
-    if (engine == 1) {
-        uint16_t* sa = reinterpret_cast<uint16_t*>(base + L.offA);
-        uint16_t* sb = reinterpret_cast<uint16_t*>(base + L.offB);
-        e = slice_operand(pa, g.m, g.k, g.lda, !g.trans_a, S, L.mp, L.kp, sa, sig, s);
-        if (e == cudaSuccess) e = slice_operand(pb, g.n, g.k, g.ldb, g.trans_b != 0, S, L.np, L.kp, sb, tau, s);
-    } else {
-        int8_t* sa = base + L.offA;
-        int8_t* sb = base + L.offB;
-        e = slice_operand(pa, g.m, g.k, g.lda, !g.trans_a, S, L.mp, L.kp, sa, sig, s);
-        if (e == cudaSuccess) e = slice_operand(pb, g.n, g.k, g.ldb, g.trans_b != 0, S, L.np, L.kp, sb, tau, s);
-    }
+    int8_t* sa = base + L.offA;
+    int8_t* sb = base + L.offB;
+    cudaError_t e = slice_operand(pa, g.m, g.k, g.lda, !g.trans_a, S, L.mp, L.kp, sa, sig, s);
+    if (e == cudaSuccess) e = slice_operand(pb, g.n, g.k, g.ldb, g.trans_b != 0, S, L.np, L.kp, sb, tau, s);
     if (e != cudaSuccess) return e;
     OzakiGemmArgs a{base + L.offA, base + L.offB, sig, tau, {nullptr, nullptr, nullptr, nullptr},
                     g.ldc, g.m, g.n, L.mp, L.np, L.kp, S};
     for (int c = 0; c < P; ++c) a.C[c] = g.C[c];
     if constexpr (P == 2) {
-        if (engine == 1) {
-            // 64 x 32 CTA tile, 4 warps of 32 x 16, 3 stages of 64 bf16
-            const dim3 grid(static_cast<unsigned>(L.np / 32), static_cast<unsigned>(L.mp / 64));
-            ozaki_gemm_bf16_kernel<2, 2, 2, 2, 3, 3, 64><<<grid, 128, 0, s>>>(a);
-            return cudaGetLastError();
-        }
         // int8 tilings, measured at DD 4096^3, S = 13 on GB300: 0 -> 88 ms, 1 -> 102,
         // 2 -> 91.5, 3 -> 90, 4 -> 96
         switch (variant) {

@@ -16,12 +16,16 @@ struct OzakiLayout {
 };
 // elem_bytes: 1 for int8 digits, 2 for bf16 digits
 OzakiLayout ozaki_layout(int S, int64_t m, int64_t n, int64_t k, int elem_bytes = 1);
+// Workspace of the tcgen05 engine: a 256-byte header (int32 error code of the
+// last call: 0, or the role whose bounded wait expired), bf16 slices with rows
+// padded to 128, exponents.
+OzakiLayout ozaki_tc_layout(int S, int64_t m, int64_t n, int64_t k);
 
 // Largest k for which the int32 weight sums are exact: S * k * 64 * 64 < 2^31.
 inline int64_t ozaki_k_limit(int S) { return (2147483647LL) / (static_cast<int64_t>(S) * 64 * 64); }
 
 // engine 0: int8 digits on mma.sync s8 (for DD, variant 0..4 selects the CTA
-// tiling, 0 the default); engine 1: bf16 digits on mma.sync bf16 (DD only).
+// tiling, 0 the default); engine 1: bf16 digits on tcgen05 (TMEM accumulators).
 template <int P>
 cudaError_t launch_ozaki(const GemmArgs<P>& g, int S, void* ws, cudaStream_t s, int variant = 0,
                          int engine = 0);

@@ -85,8 +85,8 @@ def test_workspace_errors(torch):
         mm.gemm("qd", Q, Q, algo="int8")                  # supported, but needs a workspace
     assert e.value.code == -3
     with pytest.raises(mm.MPGError) as e:
-        mm.gemm("qd", Q, Q, algo="bf16")                  # the bf16 path is DD only
-    assert e.value.code == -4
+        mm.gemm("qd", Q, Q, algo="bf16")                  # the tcgen05 path needs one too
+    assert e.value.code == -3
 
 
 def test_full_size_sampled(torch):
@@ -126,9 +126,9 @@ def test_tile_variants_agree(torch):
 
 
 def test_bf16_path_matches_int8(torch):
-    """The bf16 tensor path computes the same integer weight sums: its result
-    equals the int8 path's and the oracle's bit for bit (ragged shape,
-    ill-scaled operands, transposed B)."""
+    """The bf16 digits on tcgen05 (TMEM accumulators) compute the same integer
+    weight sums: the result equals the int8 path's and the oracle's bit for
+    bit (ragged shape, ill-scaled operands, transposed B)."""
     from paper_2101_06584_gb300 import mpgemm as mm
     rng = np.random.default_rng(640)
     m, n, k = 131, 70, 300
@@ -138,7 +138,10 @@ def test_bf16_path_matches_int8(torch):
     ws = torch.empty(mm.workspace_size("dd", m, n, k, algo="bf16", slices=S), dtype=torch.uint8,
                      device="cuda")
     Cb = host(mm.gemm("dd", Ad, Bt, trans_b=True, algo="bf16", slices=S, workspace=ws))
-    Ci = host(mm.gemm("dd", Ad, Bt, trans_b=True, algo="int8", slices=S, workspace=ws))
+    assert host(ws[:4]).view(np.int32)[0] == 0, "tcgen05 kernel reported a timeout"
+    ws8 = torch.empty(mm.workspace_size("dd", m, n, k, algo="int8", slices=S), dtype=torch.uint8,
+                      device="cuda")
+    Ci = host(mm.gemm("dd", Ad, Bt, trans_b=True, algo="int8", slices=S, workspace=ws8))
     assert_bitwise(Cb, Ci, "bf16 vs int8")
     want, _, _ = OZ.gemm(A, B, S)
     assert_bitwise(Cb, want, "bf16 vs oracle")
@@ -162,7 +165,10 @@ def test_bf16_partial_sums_at_the_drain_limit(torch):
     ws = torch.empty(mm.workspace_size("dd", m, n, k, algo="bf16", slices=S), dtype=torch.uint8,
                      device="cuda")
     Cb = host(mm.gemm("dd", Ad, Bd, algo="bf16", slices=S, workspace=ws))
-    Ci = host(mm.gemm("dd", Ad, Bd, algo="int8", slices=S, workspace=ws))
+    assert host(ws[:4]).view(np.int32)[0] == 0, "tcgen05 kernel reported a timeout"
+    ws8 = torch.empty(mm.workspace_size("dd", m, n, k, algo="int8", slices=S), dtype=torch.uint8,
+                      device="cuda")
+    Ci = host(mm.gemm("dd", Ad, Bd, algo="int8", slices=S, workspace=ws8))
     assert_bitwise(Cb, Ci, "bf16 vs int8 at the limit")
     want, _, _ = OZ.gemm(A, B, S, rows=[0, 63], cols=[0, 31])
     assert_bitwise(Cb[:, [0, 63]][:, :, [0, 31]], want, "bf16 vs oracle at the limit")
@@ -177,6 +183,7 @@ def test_bf16_full_size_sampled(torch):
     ws = torch.empty(mm.workspace_size("dd", n, n, n, algo="bf16", slices=S), dtype=torch.uint8,
                      device="cuda")
     C = host(mm.gemm("dd", Ad, Bd, algo="bf16", slices=S, workspace=ws))
+    assert host(ws[:4]).view(np.int32)[0] == 0, "tcgen05 kernel reported a timeout"
     srng = np.random.default_rng(650)
     rows = sorted(set(int(x) for x in srng.integers(0, n, 2)))
     cols = sorted(set(int(x) for x in srng.integers(0, n, 2)))
@@ -227,3 +234,26 @@ def test_td_qd_full_size_sampled(torch, prec):
     assert_bitwise(C[:, rows][:, :, cols], want, "%s 1024 sampled" % prec)
     err = X.gemm_error(C, A, B, [(i, j) for i in rows for j in cols])
     assert err["err_abs"] <= n * 2.0 ** -{"td": 150, "qd": 200}[prec], err
+
+
+@pytest.mark.parametrize("prec,S", [("td", 22), ("qd", 29), ("dd", 3)])
+def test_tc_engine_matches_int8(torch, prec, S):
+    """TD/QD (and a 3-slice DD) on the tcgen05 engine equal the int8 engine and
+    the oracle bit for bit; several 128 x 128 tiles, ragged edges, both
+    transposes."""
+    from paper_2101_06584_gb300 import mpgemm as mm
+    P = I.P_OF[prec]
+    rng = np.random.default_rng(680 + P)
+    m, n, k = 200, 150, 190
+    A, B = I.ill_scaled(P, (m, k), rng), I.uniform(P, (k, n), rng)
+    At, Bt = dev(torch, A.transpose(0, 2, 1)), dev(torch, B.transpose(0, 2, 1))
+    wsb = torch.empty(mm.workspace_size(prec, m, n, k, algo="bf16", slices=S), dtype=torch.uint8,
+                      device="cuda")
+    wsi = torch.empty(mm.workspace_size(prec, m, n, k, algo="int8", slices=S), dtype=torch.uint8,
+                      device="cuda")
+    Cb = host(mm.gemm(prec, At, Bt, trans_a=True, trans_b=True, algo="bf16", slices=S, workspace=wsb))
+    assert host(wsb[:4]).view(np.int32)[0] == 0, "tcgen05 kernel reported a timeout"
+    Ci = host(mm.gemm(prec, At, Bt, trans_a=True, trans_b=True, algo="int8", slices=S, workspace=wsi))
+    assert_bitwise(Cb, Ci, "%s tcgen05 vs int8" % prec)
+    want, _, _ = OZ.gemm(A, B, S, rows=[0, 127, 128, 199], cols=[0, 127, 128, 149])
+    assert_bitwise(Cb[:, [0, 127, 128, 199]][:, :, [0, 127, 128, 149]], want, "%s tcgen05 vs oracle" % prec)

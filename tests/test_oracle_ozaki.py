@@ -118,9 +118,12 @@ MUTANTS = [
      lambda hv: (lambda mx: 0 if mx == 0 else OZ.ilogb(mx) + 1)(max(abs(float(v)) for v in hv))),
     ("drops the least significant weight", "weight_products",
      lambda DA, DB, S: {w: (v if w < S + 1 else v * 0) for w, v in _orig_wp(DA, DB, S).items()}),
+    ("groups shifted the wrong way", "weight_groups",
+     lambda S, P: [list(reversed(g)) for g in _orig_groups(S, P)]),
 ]
 _orig_digits = OZ.digits
 _orig_wp = OZ.weight_products
+_orig_groups = OZ.weight_groups
 
 
 def _digits_mut(comps, sigma, S, tie):
@@ -142,7 +145,7 @@ def test_mutant_caught(monkeypatch, name, attr, fn):
               lambda: test_error_shrinks_per_slice_and_meets_bound("uniform")):
         try:
             t()
-        except AssertionError:
+        except (AssertionError, ValueError):     # a crash inside the definition also exposes it
             failures += 1
     assert failures, name
 
@@ -174,8 +177,7 @@ def test_weight_groups():
             groups = OZ.weight_groups(S, P)
             flat = [w for g in groups for w in g]
             assert flat == list(range(S + 1, 1, -1))
-            assert all(len(g) == (1 if P == 2 else min(3, len(g))) for g in groups)
-            assert all(len(g) <= (1 if P == 2 else 3) for g in groups)
+            assert all(len(g) == 3 for g in groups[:-1]) and 1 <= len(groups[-1]) <= 3
 
 
 @pytest.mark.parametrize("P,S", [(3, 22), (4, 29)])
