@@ -156,8 +156,11 @@ int mpgemm_ex(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k,
  *   balanced base-2^7 digits of a 2^-sigma, each the nearest integer (ties to
  *   even) of the exact scaled remainder; for w = S+1 down to 2 the int32 sum
  *   P_w of the slice products with s + t = w (exact: requires
- *   S * k * 4096 < 2^31, else MPG_EUNSUPPORTED); acc = DDadd(acc,
- *   (P_w 2^(sigma_i + tau_j - 7w), 0)) (Alg. 1) from acc = 0.
+ *   S * k * 4096 < 2^31, else MPG_EUNSUPPORTED); the weight sums combined
+ *   exactly three at a time from the least significant weight,
+ *   V = P_w + 2^7 P_(w-1) + 2^14 P_(w-2) (|V| < 2^46), and from acc = 0,
+ *   acc = DDadd(acc, (V 2^(sigma_i + tau_j - 7w), 0)) (Alg. 1), w the
+ *   group's largest weight.
  * The result is deterministic and bit-identical to those steps evaluated
  * anywhere; its error against the exact product shrinks by ~2^-7 per slice.
  * Needs opts->workspace: 256-byte aligned, mpgemm_workspace_size() bytes, not
@@ -169,10 +172,8 @@ int mpgemm_ex(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k,
  * For TD and QD (P = 3, 4; S default 22 / 29, 1..40): each component is
  * first floored to a multiple of 2^(sigma - 7S - 12 - 64) and the digits are
  * those of the sum of the floored components (computed exactly in 384-bit
- * integers); the weight sums are combined exactly three at a time from the
- * least significant weight, V = P_w + 2^7 P_(w-1) + 2^14 P_(w-2) (|V| < 2^46),
- * and acc = TDaddq / QDadd (Sec. 2.3, Alg. 5) of (V 2^(sigma_i + tau_j - 7w),
- * 0, ...) with w the group's largest weight.
+ * integers); the groups are added with TDaddq / QDadd (Sec. 2.3, Alg. 5) of
+ * (V 2^(sigma_i + tau_j - 7w), 0, ...).
  *
  * MPG_ALGO_BF16_SLICES (DD/TD/QD; not in the paper): the same digits, scales,
  * weight sums and accumulation, with the slice products on the 5th-generation
@@ -185,8 +186,7 @@ int mpgemm_ex(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k,
  * after a normal run (a device-side wait that exceeded about a second leaves
  * the code of the waiting role there), then the digits as bf16 with rows
  * padded to 128 ([S][mp][kp] for op(A), [S][np][kp] for op(B)^T), then the
- * int32 exponents; mpgemm_workspace_size gives the total.
-
+ * int32 exponents; mpgemm_workspace_size gives the total. */
 
 /* Bytes of workspace mpgemm_ex needs for these options and sizes (0 if none). */
 size_t mpgemm_workspace_size(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k);
