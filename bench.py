@@ -10,8 +10,10 @@ Workloads (one "step" = one pass of the workload's kernels over its inputs):
   dd_small  DD GEMM 128^3, uniform inputs
   dd_int8   DD GEMM 4096^3 through the INT8 error-free slicing form (slicing +
             tensor-core slice products + EFT accumulation), S = 13 slices
-  td_qd_int8  the TD and QD GEMMs of td_qd through the INT8 slicing form
-            (S = 22 / 29)
+  dd_tc     the dd_int8 product with the digits as bf16 on tcgen05 (TMEM
+            accumulators, TMA staging)
+  td_qd_int8, td_qd_tc  the TD and QD GEMMs of td_qd through the slicing form
+            (S = 22 / 29) on either engine
   batched   512 DD and 512 QD problems, m, n, k log-uniform in [16, 512], each
             precision one persistent launch replayed from a CUDA graph
   autograd  DDMatmul forward + backward (3 DD GEMMs), m = n = k = 2048
@@ -48,6 +50,20 @@ FP64_OPS_PER_MAD = {"dd": 20, "td": 128, "qd": 210}
 L2_FLUSH_BYTES = 256 << 20          # larger than the 129 MB L2
 INT8_SLICES = 13
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def bf16_peak():
+    """Dense bf16 tensor peak (FLOP/s) for a kernel timed alone: the measured
+    burst figure of MEASURED_PEAKS.json, else the profiling recipe's fallback."""
+    try:
+        with open(PEAKS_FILE) as f:
+            v = json.load(f).get("bf16_tflops")
+        if v:
+            return float(v) * 1e12, "measured (MEASURED_PEAKS.json bf16_tflops, cuBLAS burst)"
+    except (OSError, ValueError):
+        pass
+    return 1.9e15, "fallback 1.9 PFLOP/s"
 
 
 # the sources each recorded kernel is compiled from
@@ -89,7 +105,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="td_qd",
-                    choices=["td_qd", "dd_small", "dd_int8", "td_qd_int8", "batched", "autograd"])
+                    choices=["td_qd", "dd_small", "dd_int8", "dd_tc", "td_qd_int8", "td_qd_tc",
+                             "batched", "autograd"])
     ap.add_argument("--size", type=int, default=None, help="override the workload's m = n = k")
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
@@ -331,54 +348,67 @@ class DdSmall(Workload):
 
 
 class DdInt8(Workload):
+    """DD GEMM through the slicing form; engine "int8" (mma.sync s8) or "tc"
+    (the same digits as bf16 on tcgen05)."""
     name = "dd_int8"
 
-    def __init__(self, torch, mm, I, rank, n=4096, S=INT8_SLICES):
-        self.torch, self.mm, self.n, self.S = torch, mm, n, S
+    def __init__(self, torch, mm, I, rank, n=4096, S=INT8_SLICES, engine="int8"):
+        self.torch, self.mm, self.n, self.S, self.engine = torch, mm, n, S, engine
+        self.algo = "int8" if engine == "int8" else "bf16"
         rng = replica_rng(2, rank)
-        self.hA = I.uniform(2, (n, n), rng)
-        self.hB = I.uniform(2, (n, n), rng)
-        self.A = torch.from_numpy(self.hA).cuda()
-        self.B = torch.from_numpy(self.hB).cuda()
+        self.A = torch.from_numpy(I.uniform(2, (n, n), rng)).cuda()
+        self.B = torch.from_numpy(I.uniform(2, (n, n), rng)).cuda()
         self.C = torch.empty((2, n, n), dtype=torch.float64, device="cuda")
-        self.ws = torch.empty(mm.workspace_size("dd", n, n, n, algo="int8", slices=S),
+        self.ws = torch.empty(mm.workspace_size("dd", n, n, n, algo=self.algo, slices=S),
                               dtype=torch.uint8, device="cuda")
         self.mads = n ** 3
-        # scale + slice for each operand (+ exponent padding when n % 64 != 0) and the product
-        self.launches_per_step = 5 if n % 64 == 0 else 7
-        self.config = {"workload": "DD GEMM m=n=k=%d, INT8 error-free slicing form, S=%d" % (n, S),
-                       "m": n, "n": n, "k": n, "slices": S}
+        # scale + slice for each operand (+ exponent padding when n is not a tile multiple) and the product
+        self.launches_per_step = 5 if n % 128 == 0 else 7
+        if engine != "int8":
+            self.launches_per_step += 1          # the workspace-header clear
+        eng = ("mma.sync s8 engine" if engine == "int8"
+               else "tcgen05 engine (digits as bf16, TMEM accumulators)")
+        self.config = {"workload": "DD GEMM m=n=k=%d, INT8 error-free slicing form, S=%d, %s" % (n, S, eng),
+                       "m": n, "n": n, "k": n, "slices": S, "engine": engine}
 
     def timed_step(self, stream):
         e0, e1 = self.torch.cuda.Event(enable_timing=True), self.torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        self.mm.gemm("dd", self.A, self.B, out=self.C, algo="int8", slices=self.S, workspace=self.ws)
+        self.mm.gemm("dd", self.A, self.B, out=self.C, algo=self.algo, slices=self.S, workspace=self.ws)
         e1.record(stream)
-        return {"int8": (e0, e1)}
+        return {"call": (e0, e1)}
 
     def roofline(self, launch_ms, pk):
         S, n = self.S, self.n
         pairs = S * (S + 1) // 2
         ops = 2.0 * pairs * n ** 3
-        ms = statistics.mean(launch_ms["int8"])
+        ms = statistics.mean(launch_ms["call"])
         ach = ops / (ms * 1e-3)
         plain_ms = _time_call(self.torch, lambda: self.mm.gemm_plain("dd", self.A, self.B), 1)
-        return {"bound": "tensor", "kernel": "ozaki_gemm_kernel (mma.sync m16n8k32 s8) incl. slicing",
-                "achieved": ach / 1e12, "peak": pk["mma_s8"] / 1e12, "unit": "Tint8op/s",
-                "frac": ach / pk["mma_s8"], "traffic": recorded_traffic("dd_int8_%d_s%d:call" % (n, S)),
+        if self.engine == "int8":
+            peak, src, unit, kern = (pk["mma_s8"], "measured mma.sync s8 probe at this run's clocks "
+                                     "(tcgen05 has no int8 kind on sm_103a)", "Tint8op/s",
+                                     "ozaki_gemm_kernel (mma.sync m16n8k32 s8) incl. slicing")
+            key = "dd_int8_%d_s%d:call" % (n, S)
+        else:
+            peak, src = bf16_peak()
+            unit, kern = "TFLOP/s", "ozaki_tc_kernel (tcgen05.mma kind::f16) incl. slicing"
+            key = "dd_tc_%d_s%d:call" % (n, S)
+        return {"bound": "tensor", "kernel": kern, "achieved": ach / 1e12, "peak": peak / 1e12,
+                "unit": unit, "frac": ach / peak, "traffic": recorded_traffic(key),
                 "ops_per_unit": 2 * pairs,
-                "unit_of_work": "DD multiply-add (%d slice-pair int8 MACs)" % pairs,
-                "units_per_launch": n ** 3,
-                "peak_source": "measured mma.sync s8 probe at this run's clocks "
-                               "(tcgen05 has no int8 kind on sm_103a)",
+                "unit_of_work": "DD multiply-add (%d slice-pair MACs)" % pairs,
+                "units_per_launch": n ** 3, "peak_source": src,
                 "fp64_eft_ms": plain_ms, "speedup_vs_fp64_eft": plain_ms / ms}
 
 
 class TdQdInt8(Workload):
+    """The TD and QD GEMMs of td_qd through the slicing form (engine "int8" or "tc")."""
     name = "td_qd_int8"
 
-    def __init__(self, torch, mm, I, rank, n=1024):
-        self.torch, self.mm, self.n = torch, mm, n
+    def __init__(self, torch, mm, I, rank, n=1024, engine="int8"):
+        self.torch, self.mm, self.n, self.engine = torch, mm, n, engine
+        self.algo = "int8" if engine == "int8" else "bf16"
         self.precs = ("td", "qd")
         self.S = {"td": 22, "qd": 29}
         rng = replica_rng(1, rank)
@@ -386,15 +416,17 @@ class TdQdInt8(Workload):
         for prec in self.precs:
             P = I.P_OF[prec]
             A, B = I.cancelling_pair(P, n, n, n, rng)
-            ws = torch.empty(mm.workspace_size(prec, n, n, n, algo="int8", slices=self.S[prec]),
+            ws = torch.empty(mm.workspace_size(prec, n, n, n, algo=self.algo, slices=self.S[prec]),
                              dtype=torch.uint8, device="cuda")
             self.dev[prec] = (torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(),
                               torch.empty((P, n, n), dtype=torch.float64, device="cuda"), ws)
         self.mads = len(self.precs) * n ** 3
-        self.launches_per_step = 2 * (5 if n % 64 == 0 else 7)
+        self.launches_per_step = 2 * (5 if n % 128 == 0 else 7) + (0 if engine == "int8" else 2)
+        eng = "mma.sync s8 engine" if engine == "int8" else "tcgen05 engine"
         self.config = {"workload": "TD GEMM + QD GEMM, m=n=k=%d, INT8 error-free slicing form "
-                                   "(S = %d / %d), inputs of the main workload" % (n, self.S["td"], self.S["qd"]),
-                       "m": n, "n": n, "k": n, "slices": self.S}
+                                   "(S = %d / %d), %s, inputs of the main workload"
+                                   % (n, self.S["td"], self.S["qd"], eng),
+                       "m": n, "n": n, "k": n, "slices": self.S, "engine": engine}
 
     def timed_step(self, stream):
         evs = {}
@@ -402,7 +434,7 @@ class TdQdInt8(Workload):
             A, B, C, ws = self.dev[prec]
             e0, e1 = self.torch.cuda.Event(enable_timing=True), self.torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            self.mm.gemm(prec, A, B, out=C, algo="int8", slices=self.S[prec], workspace=ws)
+            self.mm.gemm(prec, A, B, out=C, algo=self.algo, slices=self.S[prec], workspace=ws)
             e1.record(stream)
             evs[prec] = (e0, e1)
         return evs
@@ -417,14 +449,35 @@ class TdQdInt8(Workload):
         for prec in self.precs:
             A, B, C, _ = self.dev[prec]
             plain[prec] = _time_call(self.torch, lambda: self.mm.gemm_plain(prec, A, B, out=C), 1)
-        return {"bound": "tensor", "kernel": "ozaki_gemm_kernel<4> (QD, mma.sync s8) incl. slicing",
-                "achieved": ach / 1e12, "peak": pk["mma_s8"] / 1e12, "unit": "Tint8op/s",
-                "frac": ach / pk["mma_s8"], "traffic": None, "ops_per_unit": 2 * pairs,
-                "unit_of_work": "QD multiply-add (%d slice-pair int8 MACs)" % pairs,
+        if self.engine == "int8":
+            peak, src, unit = pk["mma_s8"], "measured mma.sync s8 probe", "Tint8op/s"
+        else:
+            (peak, src), unit = bf16_peak(), "TFLOP/s"
+        # the QD call spends most of its time in the FP64 group additions
+        fp64_ops = (n * n) * ((S + 2) // 3) * FP64_OPS_PER_MAD["qd"] * 87 // 210
+        return {"bound": "tensor", "kernel": "QD slicing form (%s) incl. slicing" % self.engine,
+                "achieved": ach / 1e12, "peak": peak / 1e12, "unit": unit, "peak_source": src,
+                "frac": ach / peak, "traffic": None, "ops_per_unit": 2 * pairs,
+                "unit_of_work": "QD multiply-add (%d slice-pair MACs)" % pairs,
                 "units_per_launch": n ** 3,
+                "fp64_epilogue_ops_per_call": fp64_ops,
                 "per_precision_mad_s": {p: n ** 3 / (statistics.mean(launch_ms[p]) * 1e-3)
                                         for p in self.precs},
                 "speedup_vs_fp64_eft": {p: plain[p] / statistics.mean(launch_ms[p]) for p in self.precs}}
+
+
+class DdTc(DdInt8):
+    name = "dd_tc"
+
+    def __init__(self, torch, mm, I, rank, n=4096):
+        super().__init__(torch, mm, I, rank, n=n, engine="tc")
+
+
+class TdQdTc(TdQdInt8):
+    name = "td_qd_tc"
+
+    def __init__(self, torch, mm, I, rank, n=1024):
+        super().__init__(torch, mm, I, rank, n=n, engine="tc")
 
 
 class Batched(Workload):
@@ -510,8 +563,8 @@ class Autograd(Workload):
                 "unit_of_work": "DD multiply-add", "units_per_launch": self.n ** 3}
 
 
-WORKLOADS = {"td_qd": TdQd, "dd_small": DdSmall, "dd_int8": DdInt8, "td_qd_int8": TdQdInt8,
-             "batched": Batched, "autograd": Autograd}
+WORKLOADS = {"td_qd": TdQd, "dd_small": DdSmall, "dd_int8": DdInt8, "dd_tc": DdTc,
+             "td_qd_int8": TdQdInt8, "td_qd_tc": TdQdTc, "batched": Batched, "autograd": Autograd}
 
 
 def _time_call(torch, fn, reps=1):
@@ -615,7 +668,7 @@ def run_ours(args):
 def extras(torch, mm, I, pk, flush):
     """One short measurement of each other workload (rank 0, after the main one)."""
     out = {}
-    for name in ("dd_small", "dd_int8", "td_qd_int8", "batched", "autograd"):
+    for name in ("dd_small", "dd_int8", "dd_tc", "td_qd_int8", "td_qd_tc", "batched", "autograd"):
         w = WORKLOADS[name](torch, mm, I, 0)
         steps = 2 if name != "dd_small" else 10
         total_ms, launch_ms, _, _ = measure(torch, w, steps, 1, 1, 0, flush, sample_clocks=False)
