@@ -137,7 +137,7 @@ typedef struct mpgemm_opts {
                        within the same error bound) */
     int slices;     /* INT8_OZAKI: slices per operand, 0 = default */
     int tile;       /* FP64_EFT: tile configuration id 1..mpgemm_num_tiles(P);
-                       INT8_OZAKI: slice-product tiling 1..5; 0 or -1 = library choice */
+                       INT8_OZAKI: slice-product tiling 1..3; 0 or -1 = library choice */
     void *workspace;          /* device scratch for algorithms that need it */
     size_t workspace_bytes;
 } mpgemm_opts;
@@ -157,10 +157,12 @@ int mpgemm_ex(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k,
  *   even) of the exact scaled remainder; for w = S+1 down to 2 the int32 sum
  *   P_w of the slice products with s + t = w (exact: requires
  *   S * k * 4096 < 2^31, else MPG_EUNSUPPORTED); the weight sums combined
- *   exactly three at a time from the least significant weight,
- *   V = P_w + 2^7 P_(w-1) + 2^14 P_(w-2) (|V| < 2^46), and from acc = 0,
- *   acc = DDadd(acc, (V 2^(sigma_i + tau_j - 7w), 0)) (Alg. 1), w the
- *   group's largest weight.
+ *   exactly G = 5 at a time from the least significant weight (w = S+1,
+ *   ..., S-3, then S-4, ...; the last group may be shorter),
+ *   V = P_w + 2^7 P_(w-1) + ... + 2^28 P_(w-4) (|V| < 2^60), V split exactly
+ *   into hi = RN(V) (ties to even) and lo = V - hi, and from acc = 0,
+ *   acc = DDadd(acc, (hi 2^e, lo 2^e)), e = sigma_i + tau_j - 7w (Alg. 1),
+ *   w the group's largest weight.
  * The result is deterministic and bit-identical to those steps evaluated
  * anywhere; its error against the exact product shrinks by ~2^-7 per slice.
  * Needs opts->workspace: 256-byte aligned, mpgemm_workspace_size() bytes, not
@@ -172,20 +174,21 @@ int mpgemm_ex(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k,
  * For TD and QD (P = 3, 4; S default 22 / 29, 1..40): each component is
  * first floored to a multiple of 2^(sigma - 7S - 12 - 64) and the digits are
  * those of the sum of the floored components (computed exactly in 384-bit
- * integers); the groups are added with TDaddq / QDadd (Sec. 2.3, Alg. 5) of
- * (V 2^(sigma_i + tau_j - 7w), 0, ...).
+ * integers); the groups hold G = 10 weights (|V| < 2^95) and are added with
+ * TDaddq / QDadd (Sec. 2.3, Alg. 5) of (hi 2^e, lo 2^e, 0, ...).
  *
  * MPG_ALGO_BF16_SLICES (DD/TD/QD; not in the paper): the same digits, scales,
  * weight sums and accumulation, with the slice products on the 5th-generation
  * tensor cores: the digits are stored as bf16 (exact: |d| <= 64), loaded by
- * TMA, multiplied by tcgen05.mma (kind::f16, M = N = 128, fp32 accumulation in
+ * TMA, multiplied by tcgen05.mma (kind::f16, M = 128, N = 128 for DD and 64
+ * for TD/QD, fp32 accumulation in
  * tensor memory), and each accumulator is drained into exact integer sums
  * after at most 2048 values of k of one weight, so every fp32 partial sum is
  * an integer below 2^23 and exact.  The result is bit-identical to
  * MPG_ALGO_INT8_OZAKI.  Workspace: a 256-byte header whose first int32 is 0
  * after a normal run (a device-side wait that exceeded about a second leaves
  * the code of the waiting role there), then the digits as bf16 with rows
- * padded to 128 ([S][mp][kp] for op(A), [S][np][kp] for op(B)^T), then the
+ * padded to 128 ([S][mp][kp] for op(A)) and to N ([S][np][kp] for op(B)^T), then the
  * int32 exponents; mpgemm_workspace_size gives the total. */
 
 /* Bytes of workspace mpgemm_ex needs for these options and sizes (0 if none). */

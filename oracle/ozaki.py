@@ -13,21 +13,22 @@ reader can check it line by line.  DD (P = 2):
            Every |d_s| <= 64.  a = 2^sigma (sum_s d_s 2^-7s + 2^-7S x_S).
   products P_w = sum over s + t = w (1 <= s, t <= S) of A^(s) B^(t), for
            w = 2..S+1, computed exactly in integers.
-  accumulate  weights are taken in groups of three from the least
-           significant end (w = S+1, S, S-1; then S-2, ...):
-           V = P_w + 2^7 P_(w-1) + 2^14 P_(w-2), exact and below 2^46;
+  accumulate  weights are taken in groups of G = 5 from the least
+           significant end (w = S+1, ..., S-3; then S-4, ...):
+           V = sum_j P_(w-j) 2^(7j), an exact integer below 2^60; V is split
+           exactly into hi = RN(V) (ties to even) and lo = V - hi;
            acc = (0, 0); for each group in that order:
-           acc = DDadd(acc, (V 2^(sigma_i + tau_j - 7w), 0)), w the group's
-           largest weight, with the oracle's DDadd (Alg. 1).  The scaled value
-           is an exact binary64 for the sizes this form accepts.
+           acc = DDadd(acc, (hi 2^e, lo 2^e)), e = sigma_i + tau_j - 7w, w
+           the group's largest weight, with the oracle's DDadd (Alg. 1).  The
+           scaled values are exact binary64 for the sizes this form accepts.
 
 TD and QD (P = 3, 4) differ in two places:
   slices   each component is first floored to a multiple of
            2^(sigma - F - 64), F = 7S + 12 (64 guard bits below the last
            digit's unit); the digits are those of the sum of the floored
            components, exactly as above.
-  accumulate  as for DD with TDaddq (Sec. 2.3) or QDadd (Alg. 5) of
-           (V 2^(sigma + tau - 7w), 0, ...).
+  accumulate  as for DD with groups of G = 10 (V below 2^95) and TDaddq
+           (Sec. 2.3) or QDadd (Alg. 5) of (hi 2^e, lo 2^e, 0, ...).
 """
 import math
 from fractions import Fraction
@@ -126,11 +127,26 @@ def weight_products(DA, DB, S):
 PREC_OF = {2: "dd", 3: "td", 4: "qd"}
 
 
+def group_size(P):
+    """Weights combined exactly per add: 5 for DD (64-bit sums), 10 for TD/QD (128-bit)."""
+    return 5 if P == 2 else 10
+
+
 def weight_groups(S, P):
-    """The weights in accumulation order, three to a group, from the least
-    significant (w = S+1) end (the last group may be shorter)."""
+    """The weights in accumulation order, group_size(P) to a group, from the
+    least significant (w = S+1) end (the last group may be shorter)."""
     ws = list(range(S + 1, 1, -1))
-    return [ws[i:i + 3] for i in range(0, len(ws), 3)]
+    G = group_size(P)
+    return [ws[i:i + G] for i in range(0, len(ws), G)]
+
+
+def split_exact(V):
+    """(hi, lo) with hi = RN(V) (ties to even) and lo = V - hi, both exact
+    binary64 values, for an integer |V| < 2^106."""
+    hi = float(V)                      # Python rounds int -> float to nearest, ties to even
+    lo = V - int(hi)
+    assert abs(lo) < 2 ** 53 and float(lo) == lo
+    return hi, float(lo)
 
 
 def gemm(A, B, S, rows=None, cols=None, L=None):
@@ -153,11 +169,12 @@ def gemm(A, B, S, rows=None, cols=None, L=None):
             for grp in weight_groups(S, P):
                 wmax = grp[0]
                 V = sum(int(Pw[w][r, c]) << (BASE_BITS * (wmax - w)) for w in grp)
-                assert abs(V) < 2 ** 53
+                assert abs(V) < (2 ** 60 if P == 2 else 2 ** 95)
+                hi, lo = split_exact(V)
                 e = sig[r] + tau[c] - BASE_BITS * wmax
-                v = math.ldexp(float(V), e)
-                assert Fraction(v) == Fraction(V) * Fraction(2) ** e, "scaled group sum not exact"
-                acc = _op(prec, "add", acc, (v,) + (0.0,) * (P - 1), L)
+                vh, vl = math.ldexp(hi, e), math.ldexp(lo, e)
+                assert Fraction(vh) + Fraction(vl) == Fraction(V) * Fraction(2) ** e, "scaled group sum not exact"
+                acc = _op(prec, "add", acc, (vh, vl) + (0.0,) * (P - 2), L)
             C[:, r, c] = acc
     return C, sig, tau
 

@@ -177,7 +177,7 @@ static int ozaki_call(const GemmArgs<P>& g, const mpgemm_opts* o)
     if (g.k > ozaki_k_limit(S))
         return fail(MPG_EUNSUPPORTED, "k = %lld exceeds %lld, the largest k whose %d-slice int32 "
                     "sums are exact", (long long)g.k, (long long)ozaki_k_limit(S), S);
-    const OzakiLayout L = engine == 1 ? ozaki_tc_layout(S, g.m, g.n, g.k) : ozaki_layout(S, g.m, g.n, g.k, 1);
+    const OzakiLayout L = engine == 1 ? ozaki_tc_layout(P, S, g.m, g.n, g.k) : ozaki_layout(S, g.m, g.n, g.k, 1);
     if (L.mp / 64 > 65535) return fail(MPG_EINVAL, "m too large for the slicing form's grid");
     if (!o->workspace) return fail(MPG_EWORKSPACE, "the slicing form needs a workspace of %lld bytes",
                                    (long long)L.total);
@@ -196,7 +196,7 @@ static int ozaki_call(const GemmArgs<P>& g, const mpgemm_opts* o)
             return fail(MPG_EWORKSPACE, "workspace overlaps an operand");
     }
     const int variant = o->tile > 0 ? o->tile - 1 : 0;
-    if (variant > 4) return fail(MPG_EINVAL, "INT8 tile id %d out of range 1..5", o->tile);
+    if (variant > 2) return fail(MPG_EINVAL, "INT8 tile id %d out of range 1..3", o->tile);
     cudaError_t e = launch_ozaki<P>(g, S, o->workspace, g_stream, variant, engine);
     return e == cudaSuccess ? MPG_OK : cuda_fail(e, "slicing gemm launch");
 }
@@ -319,7 +319,7 @@ size_t mpgemm_workspace_size(int P, const mpgemm_opts* opts, int64_t m, int64_t 
         return 0;
     const int S = opts->slices ? opts->slices : ozaki_default_slices(P);
     if (S < 1 || S > ozaki_max_slices(P)) return 0;
-    if (opts->algo == MPG_ALGO_BF16_SLICES) return static_cast<size_t>(ozaki_tc_layout(S, m, n, k).total);
+    if (opts->algo == MPG_ALGO_BF16_SLICES) return static_cast<size_t>(ozaki_tc_layout(P, S, m, n, k).total);
     return static_cast<size_t>(ozaki_layout(S, m, n, k, 1).total);
 }
 

@@ -435,6 +435,60 @@ __device__ __forceinline__ double scaled_int64(int64_t v, int e)
     return __longlong_as_double(static_cast<long long>(bits));
 }
 
+// x * 2^k for a finite x whose result is normal: the exponent field moves by k.
+__device__ __forceinline__ double scale_pow2(double x, int k)
+{
+    if (!mp::nonzero(x)) return x;
+    return __longlong_as_double(__double_as_longlong(x) + (static_cast<long long>(k) << 52));
+}
+
+// The exact split of a group sum v times 2^e: hi = RN(v) 2^e (ties to even),
+// lo = (v - RN(v)) 2^e, both exact binary64 for the exponents the slicing forms
+// accept; a zero lo is +0.
+__device__ __forceinline__ void split_exact(long long v, int e, double& hi, double& lo)
+{
+    const double h = __ll2double_rn(v);                       // |v| < 2^60: RN(v) fits in 64 bits
+    const long long rest = v - static_cast<long long>(h);     // |rest| <= 2^6, exact
+    hi = scale_pow2(h, e);
+    lo = scale_pow2(static_cast<double>(rest), e);
+}
+__device__ __forceinline__ void split_exact(__int128 v, int e, double& hi, double& lo)
+{
+    if (v == 0) {
+        hi = 0.0;
+        lo = 0.0;
+        return;
+    }
+    const bool neg = v < 0;
+    const unsigned __int128 u = neg ? static_cast<unsigned __int128>(-v) : static_cast<unsigned __int128>(v);
+    const uint64_t uh = static_cast<uint64_t>(u >> 64), ul = static_cast<uint64_t>(u);
+    const int nb = uh ? 128 - __clzll(static_cast<long long>(uh)) : 64 - __clzll(static_cast<long long>(ul));
+    uint64_t q;
+    int sh = 0;
+    int64_t rest = 0;                       // u - q 2^sh, |rest| <= 2^(sh-1)
+    if (nb <= 53) {
+        q = ul;
+    } else {
+        sh = nb - 53;
+        q = static_cast<uint64_t>(u >> sh);
+        const uint64_t rem = static_cast<uint64_t>(u - (static_cast<unsigned __int128>(q) << sh));
+        const uint64_t half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (q & 1ull))) {
+            q += 1;
+            rest = static_cast<int64_t>(rem) - static_cast<int64_t>(1ull << sh);
+        } else {
+            rest = static_cast<int64_t>(rem);
+        }
+    }
+    const double h = scale_pow2(static_cast<double>(q), sh + e);         // q <= 2^53: exact
+    hi = neg ? -h : h;
+    lo = scale_pow2(static_cast<double>(neg ? -rest : rest), e);         // |rest| < 2^53: exact
+}
+
+// The exact group sums of precision P: 64-bit integers for DD, 128-bit for TD and QD.
+template <int P> struct GroupSum { using T = __int128; };
+template <> struct GroupSum<2> { using T = long long; };
+
 struct OzakiGemmArgs {
     const void* sa;     // [S][mp][kp] digits (int8 or bf16)
     const void* sb;     // [S][np][kp]
@@ -462,8 +516,8 @@ struct Cursor {
 // CTA of WM x WN warps; each warp owns MT x NT fragments of 16 x 8 outputs,
 // so the CTA tile is (WM*MT*16) x (WN*NT*8).  Slice tiles of KS bytes of k
 // are staged through a STG-deep cp.async pipeline.  P output components;
-// three weights are combined exactly in int64 and each group is added with
-// the precision's add.
+// ozaki_group(P) weights are combined exactly in integers and each group is
+// added, split exactly into two binary64, with the precision's add.
 template <int P, int MT, int NT, int WM, int WN, int STG, int MINB, int KS>
 __global__ void __launch_bounds__(WM * WN * 32, MINB) ozaki_gemm_kernel(const OzakiGemmArgs g)
 {
@@ -499,7 +553,9 @@ __global__ void __launch_bounds__(WM * WN * 32, MINB) ozaki_gemm_kernel(const Oz
 
     double acc[MT][NT][4][P];
     int ci[MT][NT][4];
-    int64_t grp[MT][NT][4];
+    using G = typename GroupSum<P>::T;
+    constexpr int kGroup = ozaki_group(P);
+    G grp[MT][NT][4];
 #pragma unroll
     for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
@@ -573,11 +629,10 @@ __global__ void __launch_bounds__(WM * WN * 32, MINB) ozaki_gemm_kernel(const Oz
         const int w = cm.w;
         cm.advance(S, KT);
         if (cm.w != w || it == total - 1) {
-            // position of w in its group of three, counted from the least
-            // significant weight S+1; the group ends at its third weight or
-            // at w = 2
-            const int j = (S + 1 - w) % 3;
-            const bool group_end = j == 2 || w == 2;
+            // position of w in its group, counted from the least significant
+            // weight S+1; the group ends at its last weight or at w = 2
+            const int j = (S + 1 - w) % kGroup;
+            const bool group_end = j == kGroup - 1 || w == 2;
             const int wmax = w + j;
 #pragma unroll
             for (int mt = 0; mt < MT; ++mt)
@@ -585,13 +640,13 @@ __global__ void __launch_bounds__(WM * WN * 32, MINB) ozaki_gemm_kernel(const Oz
                 for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
-                        double y[P];
-                        grp[mt][nt][r] += static_cast<int64_t>(ci[mt][nt][r]) << (7 * j);
-                        y[0] = scaled_int64(grp[mt][nt][r], sg[mt][r >> 1] + tu[nt][r & 1] - 7 * wmax);
+                        grp[mt][nt][r] += static_cast<G>(ci[mt][nt][r]) << (7 * j);
                         ci[mt][nt][r] = 0;
                         if (group_end) {
+                            double y[P];
+                            split_exact(grp[mt][nt][r], sg[mt][r >> 1] + tu[nt][r & 1] - 7 * wmax, y[0], y[1]);
 #pragma unroll
-                            for (int c = 1; c < P; ++c) y[c] = f.zero;
+                            for (int c = 2; c < P; ++c) y[c] = f.zero;
                             double z[P];
                             mp::Ops<P>::add(f, acc[mt][nt][r], y, z);
 #pragma unroll
@@ -621,33 +676,46 @@ __global__ void __launch_bounds__(WM * WN * 32, MINB) ozaki_gemm_kernel(const Oz
 // ------------------------------------------------------- tcgen05 engine
 //
 // The bf16 digits on the 5th-generation tensor cores.  A persistent CTA per SM
-// owns 128 x 128 tiles of C.  Warp 0 streams 128 x 64 bf16 slice tiles of
-// op(A) and op(B)^T into shared memory with TMA (128-byte swizzle, 4-stage
-// mbarrier ring).  Warp 1 owns 512 TMEM columns and issues
-// tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 128, K = 16, fp32
-// accumulation), filling one of two TMEM accumulators per segment: the k
-// tiles of one weight, at most 2048 values of k, so every fp32 partial sum
-// of integer products of at most 2^12 stays an exact integer below 2^23.
-// Warps 2-5 (one TMEM lane quadrant each, one row of the tile per thread)
-// drain each segment: fp32 -> int, shifted into that thread's int64 group
-// sums held in TMEM columns 256..511; at the end of a group of three
-// weights they add the exact binary64 group value to C with the precision's
-// add.  The integer weight sums equal those of the int8 path, so the result
-// is bit-identical to it.  Every wait is bounded (about 1 s): on a timeout
-// the kernel records an error code in the workspace header, drains what it
-// issued, frees TMEM and returns.
+// owns 128 x BN tiles of C (BN = 128 for DD, 64 for TD and QD).  Warp 0
+// streams 128 x 64 (A) and BN x 64 (B) bf16 slice tiles of op(A) and op(B)^T
+// into shared memory with TMA (128-byte swizzle, 6-stage mbarrier ring).
+// Warp 1 owns 512 TMEM columns and issues tcgen05.mma.cta_group::1.kind::f16
+// (M = 128, N = BN, K = 16, fp32 accumulation), filling one of two TMEM
+// accumulators per segment: the k tiles of one weight, at most 2048 values of
+// k, so every fp32 partial sum of integer products of at most 2^12 stays an
+// exact integer below 2^23.  Warps 2-5 (one TMEM lane quadrant each, one row
+// of the tile per thread) drain each segment: fp32 -> int, shifted into that
+// thread's exact group sums held in TMEM after the accumulators (DD: 64-bit,
+// 2 columns per output; TD/QD: 128-bit, 4 columns); at the end of a group
+// they split the group value exactly into two binary64 and add it to C with
+// the precision's add.  The integer weight sums equal those of the int8 path,
+// so the result is bit-identical to it.  Every wait is bounded (about 1 s): on
+// a timeout the kernel records an error code in the workspace header, drains
+// what it issued, frees TMEM and returns.
 
 namespace tc {
-constexpr int BM = 128, BN = 128;
+constexpr int BM = 128;
 constexpr int KE = 64;                                   // k-step in bf16 elements (128 bytes)
-constexpr int STAGES = 4;
-constexpr int A_BYTES = BM * KE * 2, B_BYTES = BN * KE * 2;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;           // 32 KB
+constexpr int STAGES = 6;
+constexpr int A_BYTES = BM * KE * 2;
 constexpr int SEG_TILES = 2048 / KE;                     // k-tiles per fp32 segment
 constexpr int TMEM_COLS = 512;
-constexpr int ACC_COLS = 128;                            // two fp32 accumulators at 0 and 128
-constexpr int GRP_COL = 256;                             // int64 group sums, 2 columns per output
 constexpr unsigned long long TIMEOUT_NS = 1000000000ull;
+
+// Per-precision tile: TMEM holds two BN-column fp32 accumulators and BN
+// group sums of GW 32-bit words each (2 BN + GW BN <= 512).
+template <int P> struct Cfg {
+    static constexpr int BN = P == 2 ? 128 : 64;
+    static constexpr int GW = P == 2 ? 2 : 4;
+    static constexpr int B_BYTES = BN * KE * 2;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;   // 32 KB (DD), 24 KB
+    static constexpr int ACC_COLS = BN;                      // accumulators at columns 0 and BN
+    static constexpr int GRP_COL = 2 * BN;
+    static_assert(GRP_COL + GW * BN <= TMEM_COLS, "TMEM columns");
+    // instruction descriptor: kind::f16, bf16 A and B (K-major), fp32 D, M = 128, N = BN
+    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
+                                      ((static_cast<uint32_t>(BN) >> 3) << 17) | ((128u >> 4) << 24);
+};
 }  // namespace tc
 
 struct TcArgs {
@@ -717,15 +785,12 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr)
     return static_cast<uint64_t>((saddr & 0x3FFFF) >> 4) | (1ull << 16) |
            (static_cast<uint64_t>(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
 }
-// Instruction descriptor: kind::f16, bf16 A and B (K-major), fp32 D, M = 128, N = 128.
-constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
-
-__device__ __forceinline__ void umma(uint32_t d, uint64_t da, uint64_t db, uint32_t acc)
+__device__ __forceinline__ void umma(uint32_t d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc)
 {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-        ::"r"(d), "l"(da), "l"(db), "r"(kTcIdesc), "r"(acc));
+        ::"r"(d), "l"(da), "l"(db), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void umma_commit(uint64_t* bar)
 {
@@ -762,6 +827,22 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
+// A group sum as GW little-endian 32-bit TMEM words.
+template <typename T, int GW>
+__device__ __forceinline__ T group_load(const uint32_t* w)
+{
+    unsigned __int128 u = 0;
+#pragma unroll
+    for (int i = GW - 1; i >= 0; --i) u = (u << 32) | w[i];
+    return static_cast<T>(u);
+}
+template <typename T, int GW>
+__device__ __forceinline__ void group_store(uint32_t* w, T v)
+{
+#pragma unroll
+    for (int i = 0; i < GW; ++i) w[i] = static_cast<uint32_t>(v >> (32 * i));
+}
+
 template <int P>
 __global__ void __launch_bounds__(192, 1)
 ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -771,7 +852,11 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     __shared__ __align__(8) uint64_t full[tc::STAGES], empty[tc::STAGES], accf[2], acce[2], fin;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
-    __shared__ int s_tau[tc::BN];
+    using Cf = tc::Cfg<P>;
+    using G = typename GroupSum<P>::T;
+    constexpr int BN = Cf::BN, GW = Cf::GW, OPW = 32 / GW;   // outputs per 32 group columns
+    constexpr int kGroup = ozaki_group(P);
+    __shared__ int s_tau[BN];
 
     const uint32_t raw = smem_u32(dsm);
     uint8_t* stage0 = dsm + (((raw + 1023u) & ~1023u) - raw);   // 1024-aligned for the swizzle
@@ -815,13 +900,13 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             uint32_t it = 0;
             bool ok = true;
             for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-                const int m0 = (tile % g.tiles_m) * tc::BM, n0 = (tile / g.tiles_m) * tc::BN;
+                const int m0 = (tile % g.tiles_m) * tc::BM, n0 = (tile / g.tiles_m) * BN;
                 Cursor c{S + 1, 1, 0};
                 for (int i = 0; i < per_tile; ++i, ++it) {
                     const uint32_t st = it % tc::STAGES, ph = (it / tc::STAGES) & 1u;
                     if (!mbar_wait(&empty[st], ph ^ 1u, abortp)) { fail(1); ok = false; break; }
-                    uint8_t* sa = stage0 + st * tc::STAGE_BYTES;
-                    mbar_expect_tx(&full[st], tc::STAGE_BYTES);
+                    uint8_t* sa = stage0 + st * Cf::STAGE_BYTES;
+                    mbar_expect_tx(&full[st], Cf::STAGE_BYTES);
                     tma_load_3d(sa, &tmA, c.kt * tc::KE, m0, c.s - 1, &full[st]);
                     tma_load_3d(sa + tc::A_BYTES, &tmB, c.kt * tc::KE, n0, c.w - c.s - 1, &full[st]);
                     c.advance(S, KT);
@@ -852,11 +937,11 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                     const uint32_t st = it % tc::STAGES, ph = (it / tc::STAGES) & 1u;
                     if (!mbar_wait(&full[st], ph, abortp)) { fail(3); ok = false; break; }
                     tc_fence_after();
-                    const uint32_t sa = smem_u32(stage0 + st * tc::STAGE_BYTES);
+                    const uint32_t sa = smem_u32(stage0 + st * Cf::STAGE_BYTES);
                     const uint64_t da = umma_desc(sa), db = umma_desc(sa + tc::A_BYTES);
 #pragma unroll
                     for (int kk = 0; kk < tc::KE / 16; ++kk)
-                        umma(tmem + b * tc::ACC_COLS, da + 2ull * kk, db + 2ull * kk,
+                        umma(tmem + b * Cf::ACC_COLS, da + 2ull * kk, db + 2ull * kk, Cf::IDESC,
                              (seg_tiles > 0 || kk > 0) ? 1u : 0u);
                     umma_commit(&empty[st]);
                     ++seg_tiles;
@@ -881,20 +966,21 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         const int q = warp & 3;                          // TMEM lane quadrant of this warp
         const int r = 32 * q + lane;                     // row of the tile
         const uint32_t lane_off = static_cast<uint32_t>(32 * q) << 16;
+        const uint32_t grp = tmem + lane_off + Cf::GRP_COL;
+        uint32_t zero32[32];
+#pragma unroll
+        for (int t = 0; t < 32; ++t) zero32[t] = 0u;
         uint32_t seg = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-            const int m0 = (tile % g.tiles_m) * tc::BM, n0 = (tile / g.tiles_m) * tc::BN;
+            const int m0 = (tile % g.tiles_m) * tc::BM, n0 = (tile / g.tiles_m) * BN;
             const int64_t row = m0 + r;
             asm volatile("bar.sync 1, 128;" ::: "memory");
-            s_tau[r] = g.tau[n0 + r];
+            if (r < BN) s_tau[r] = g.tau[n0 + r];
             asm volatile("bar.sync 1, 128;" ::: "memory");
             const int sg = g.sig[row];
-            uint32_t z[32];
 #pragma unroll
-            for (int t = 0; t < 32; ++t) z[t] = 0u;
-#pragma unroll
-            for (int c0 = 0; c0 < 2 * tc::BN; c0 += 32) tmem_st32(tmem + lane_off + tc::GRP_COL + c0, z);
+            for (int c0 = 0; c0 < GW * BN; c0 += 32) tmem_st32(grp + c0, zero32);
             tmem_wait_st();
             Cursor c{S + 1, 1, 0};
             int seg_tiles = 0;
@@ -914,58 +1000,45 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                     break;
                 }
                 tc_fence_after();
-                const int j = (S + 1 - w) % 3;
-                for (int c0 = 0; c0 < tc::BN; c0 += 32) {
-                    uint32_t fv[32], g0[32], g1[32];
-                    tmem_ld32(tmem + lane_off + b * tc::ACC_COLS + c0, fv);
-                    tmem_ld32(tmem + lane_off + tc::GRP_COL + 2 * c0, g0);
-                    tmem_ld32(tmem + lane_off + tc::GRP_COL + 2 * c0 + 32, g1);
+                const int j = (S + 1 - w) % kGroup;
+                // OPW outputs per 32 TMEM columns of group sums
+                for (int c0 = 0; c0 < BN; c0 += 32) {
+                    uint32_t fv[32];
+                    tmem_ld32(tmem + lane_off + b * Cf::ACC_COLS + c0, fv);
                     tmem_wait_ld();
-                    // columns c0..c0+15 live in g0, c0+16..c0+31 in g1 (lo, hi words)
 #pragma unroll
-                    for (int t = 0; t < 16; ++t) {
-                        int64_t V = static_cast<int64_t>((static_cast<uint64_t>(g0[2 * t + 1]) << 32) | g0[2 * t]);
-                        V += static_cast<int64_t>(__float2int_rn(__uint_as_float(fv[t]))) << (7 * j);
-                        g0[2 * t] = static_cast<uint32_t>(static_cast<uint64_t>(V));
-                        g0[2 * t + 1] = static_cast<uint32_t>(static_cast<uint64_t>(V) >> 32);
-                    }
+                    for (int h = 0; h < GW; ++h) {
+                        uint32_t gw[32];
+                        tmem_ld32(grp + GW * c0 + 32 * h, gw);
+                        tmem_wait_ld();
 #pragma unroll
-                    for (int t = 0; t < 16; ++t) {
-                        int64_t V = static_cast<int64_t>((static_cast<uint64_t>(g1[2 * t + 1]) << 32) | g1[2 * t]);
-                        V += static_cast<int64_t>(__float2int_rn(__uint_as_float(fv[16 + t]))) << (7 * j);
-                        g1[2 * t] = static_cast<uint32_t>(static_cast<uint64_t>(V));
-                        g1[2 * t + 1] = static_cast<uint32_t>(static_cast<uint64_t>(V) >> 32);
+                        for (int t = 0; t < OPW; ++t) {
+                            const int add = __float2int_rn(__uint_as_float(fv[OPW * h + t]));
+                            const G V = group_load<G, GW>(gw + GW * t) + (static_cast<G>(add) << (7 * j));
+                            group_store<G, GW>(gw + GW * t, V);
+                        }
+                        tmem_st32(grp + GW * c0 + 32 * h, gw);
                     }
-                    tmem_st32(tmem + lane_off + tc::GRP_COL + 2 * c0, g0);
-                    tmem_st32(tmem + lane_off + tc::GRP_COL + 2 * c0 + 32, g1);
                     tmem_wait_st();
                 }
                 tc_fence_before();
                 mbar_arrive(&acce[b]);
                 ++seg;
-                if (!(weight_end && (j == 2 || w == 2))) continue;
+                if (!(weight_end && (j == kGroup - 1 || w == 2))) continue;
                 // end of a group: add its exact value to C
                 const int wmax = w + j;
-                for (int c0 = 0; c0 < tc::BN; c0 += 32) {
-                    uint32_t g0[32], g1[32];
-                    tmem_ld32(tmem + lane_off + tc::GRP_COL + 2 * c0, g0);
-                    tmem_ld32(tmem + lane_off + tc::GRP_COL + 2 * c0 + 32, g1);
+                for (int c0 = 0; c0 < GW * BN; c0 += 32) {
+                    uint32_t gw[32];
+                    tmem_ld32(grp + c0, gw);
                     tmem_wait_ld();
-                    int64_t Vs[32];
 #pragma unroll
-                    for (int t = 0; t < 16; ++t) {
-                        Vs[t] = static_cast<int64_t>((static_cast<uint64_t>(g0[2 * t + 1]) << 32) | g0[2 * t]);
-                        Vs[16 + t] = static_cast<int64_t>((static_cast<uint64_t>(g1[2 * t + 1]) << 32) | g1[2 * t]);
-                    }
-#pragma unroll
-                    for (int t = 0; t < 32; ++t) {
-                        const int64_t col = n0 + c0 + t;
+                    for (int t = 0; t < OPW; ++t) {
+                        const int64_t col = n0 + c0 / GW + t;
                         if (row >= g.m || col >= g.n) continue;
-                        const int64_t V = Vs[t];
                         double y[P], acc[P], zz[P];
-                        y[0] = scaled_int64(V, sg + s_tau[c0 + t] - 7 * wmax);
+                        split_exact(group_load<G, GW>(gw + GW * t), sg + s_tau[c0 / GW + t] - 7 * wmax, y[0], y[1]);
 #pragma unroll
-                        for (int cc = 1; cc < P; ++cc) y[cc] = f.zero;
+                        for (int cc = 2; cc < P; ++cc) y[cc] = f.zero;
 #pragma unroll
                         for (int cc = 0; cc < P; ++cc)
                             acc[cc] = first_group ? 0.0 : g.C[cc][row * g.ldc + col];
@@ -973,10 +1046,9 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 #pragma unroll
                         for (int cc = 0; cc < P; ++cc) g.C[cc][row * g.ldc + col] = zz[cc];
                     }
-                    tmem_st32(tmem + lane_off + tc::GRP_COL + 2 * c0, z);
-                    tmem_st32(tmem + lane_off + tc::GRP_COL + 2 * c0 + 32, z);
-                    tmem_wait_st();
+                    tmem_st32(grp + c0, zero32);
                 }
+                tmem_wait_st();
                 first_group = false;
             }
         }
@@ -1068,12 +1140,12 @@ static cudaError_t slice_operand(const Planes<P>& pl, int64_t count, int64_t len
 
 // ----------------------------------------------------- tcgen05 host side
 
-OzakiLayout ozaki_tc_layout(int S, int64_t m, int64_t n, int64_t k)
+OzakiLayout ozaki_tc_layout(int P, int S, int64_t m, int64_t n, int64_t k)
 {
     OzakiLayout L;
     L.S = S;
     L.mp = round_up(m > 0 ? m : 1, tc::BM);
-    L.np = round_up(n > 0 ? n : 1, tc::BN);
+    L.np = round_up(n > 0 ? n : 1, P == 2 ? tc::Cfg<2>::BN : tc::Cfg<4>::BN);
     L.kp = round_up(k > 0 ? k : 1, KPAD);
     L.offA = 256;                                     // bytes 0..255: header (error code)
     L.offB = L.offA + round_up(static_cast<int64_t>(S) * L.mp * L.kp * 2, 256);
@@ -1103,16 +1175,16 @@ static EncodeTiledFn encode_fn()
     return fn;
 }
 
-// A [S][rows][kp] bf16 slice array as a 3-D TMA tensor; boxes of 64 x 128 x 1,
-// 128-byte swizzle (the UMMA K-major layout).
-static bool slice_map(CUtensorMap* map, void* base, int S, int64_t rows, int64_t kp)
+// A [S][rows][kp] bf16 slice array as a 3-D TMA tensor; boxes of 64 (k) x
+// box_rows x 1, 128-byte swizzle (the UMMA K-major layout).
+static bool slice_map(CUtensorMap* map, void* base, int S, int64_t rows, int64_t kp, int box_rows)
 {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return false;
     const cuuint64_t dims[3] = {static_cast<cuuint64_t>(kp), static_cast<cuuint64_t>(rows),
                                 static_cast<cuuint64_t>(S)};
     const cuuint64_t strides[2] = {static_cast<cuuint64_t>(kp) * 2, static_cast<cuuint64_t>(rows * kp) * 2};
-    const cuuint32_t box[3] = {tc::KE, 128, 1};
+    const cuuint32_t box[3] = {tc::KE, static_cast<cuuint32_t>(box_rows), 1};
     const cuuint32_t es[3] = {1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -1122,7 +1194,8 @@ static bool slice_map(CUtensorMap* map, void* base, int S, int64_t rows, int64_t
 template <int P>
 static cudaError_t launch_ozaki_tc(const GemmArgs<P>& g, int S, void* ws, cudaStream_t s)
 {
-    const OzakiLayout L = ozaki_tc_layout(S, g.m, g.n, g.k);
+    using Cf = tc::Cfg<P>;
+    const OzakiLayout L = ozaki_tc_layout(P, S, g.m, g.n, g.k);
     int8_t* base = static_cast<int8_t*>(ws);
     int* err = reinterpret_cast<int*>(base);
     uint16_t* sa = reinterpret_cast<uint16_t*>(base + L.offA);
@@ -1139,11 +1212,12 @@ static cudaError_t launch_ozaki_tc(const GemmArgs<P>& g, int S, void* ws, cudaSt
     if (e == cudaSuccess) e = slice_operand(pb, g.n, g.k, g.ldb, g.trans_b != 0, S, L.np, L.kp, sb, tau, s);
     if (e != cudaSuccess) return e;
     CUtensorMap ma, mb;
-    if (!slice_map(&ma, sa, S, L.mp, L.kp) || !slice_map(&mb, sb, S, L.np, L.kp)) return cudaErrorInvalidValue;
+    if (!slice_map(&ma, sa, S, L.mp, L.kp, tc::BM) || !slice_map(&mb, sb, S, L.np, L.kp, Cf::BN))
+        return cudaErrorInvalidValue;
     TcArgs a{sig, tau, {nullptr, nullptr, nullptr, nullptr}, g.ldc, g.m, g.n, L.kp, S,
-             static_cast<int>(L.mp / tc::BM), static_cast<int>(L.np / tc::BN), err};
+             static_cast<int>(L.mp / tc::BM), static_cast<int>(L.np / Cf::BN), err};
     for (int c = 0; c < P; ++c) a.C[c] = g.C[c];
-    const int smem = tc::STAGES * tc::STAGE_BYTES + 1024;
+    const int smem = tc::STAGES * Cf::STAGE_BYTES + 1024;
     e = cudaFuncSetAttribute(ozaki_tc_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int tiles = a.tiles_m * a.tiles_n;
@@ -1176,32 +1250,23 @@ cudaError_t launch_ozaki(const GemmArgs<P>& g, int S, void* ws, cudaStream_t s, 
                     g.ldc, g.m, g.n, L.mp, L.np, L.kp, S};
     for (int c = 0; c < P; ++c) a.C[c] = g.C[c];
     if constexpr (P == 2) {
-        // int8 tilings, measured at DD 4096^3, S = 13 on GB300: 0 -> 88 ms, 1 -> 102,
-        // 2 -> 91.5, 3 -> 90, 4 -> 96
+        // int8 tilings (DD 4096^3, S = 13 on GB300, 3-weight groups: 0 -> 88 ms,
+        // 1 -> 91.5, 2 -> 90; the 64 x 64 tilings cannot hold 32 outputs'
+        // 128-bit group sums in registers)
         switch (variant) {
-        case 1: {   // 64 x 64 CTA tile, 4 warps of 32 x 32, 3 stages of 64 bytes
-            const dim3 grid(static_cast<unsigned>(L.np / 64), static_cast<unsigned>(L.mp / 64));
-            ozaki_gemm_kernel<2, 2, 4, 2, 2, 3, 1, 64><<<grid, 128, 0, s>>>(a);
-            break;
-        }
-        case 2: {   // 64 x 32 CTA tile, 4 warps of 32 x 16, 4 stages of 64 bytes
+        case 1: {   // 64 x 32 CTA tile, 4 warps of 32 x 16, 4 stages of 64 bytes
             const dim3 grid(static_cast<unsigned>(L.np / 32), static_cast<unsigned>(L.mp / 64));
-            ozaki_gemm_kernel<2, 2, 2, 2, 2, 4, 4, 64><<<grid, 128, 0, s>>>(a);
+            ozaki_gemm_kernel<2, 2, 2, 2, 2, 4, 3, 64><<<grid, 128, 0, s>>>(a);
             break;
         }
-        case 3: {   // 64 x 32 CTA tile, 4 warps of 16 x 32, 4 stages of 64 bytes
+        case 2: {   // 64 x 32 CTA tile, 4 warps of 16 x 32, 4 stages of 64 bytes
             const dim3 grid(static_cast<unsigned>(L.np / 32), static_cast<unsigned>(L.mp / 64));
-            ozaki_gemm_kernel<2, 1, 4, 4, 1, 4, 4, 64><<<grid, 128, 0, s>>>(a);
-            break;
-        }
-        case 4: {   // 64 x 64 CTA tile, 8 warps of 32 x 16, 4 stages of 64 bytes
-            const dim3 grid(static_cast<unsigned>(L.np / 64), static_cast<unsigned>(L.mp / 64));
-            ozaki_gemm_kernel<2, 2, 2, 2, 4, 4, 2, 64><<<grid, 256, 0, s>>>(a);
+            ozaki_gemm_kernel<2, 1, 4, 4, 1, 4, 3, 64><<<grid, 128, 0, s>>>(a);
             break;
         }
         default: {  // 64 x 32 CTA tile, 4 warps of 32 x 16, 3 stages of 128 bytes
             const dim3 grid(static_cast<unsigned>(L.np / 32), static_cast<unsigned>(L.mp / 64));
-            ozaki_gemm_kernel<2, 2, 2, 2, 2, 3, 4, 128><<<grid, 128, 0, s>>>(a);
+            ozaki_gemm_kernel<2, 2, 2, 2, 2, 3, 3, 128><<<grid, 128, 0, s>>>(a);
             break;
         }
         }

@@ -7,6 +7,9 @@ namespace mpg {
 constexpr int kOzakiMaxSlices = 16;       // DD: 128-bit exact fixed point
 constexpr int kOzakiMaxSlicesWide = 40;   // TD, QD: 384-bit floored fixed point
 constexpr int kOzakiDefaultSlices = 14;
+// Weights combined exactly per add: DD 5 (sums below 2^60, 64-bit integers),
+// TD and QD 10 (below 2^95, 128-bit integers).
+constexpr int ozaki_group(int P) { return P == 2 ? 5 : 10; }
 
 // Workspace layout for S slices of an m x n x k product (byte offsets).
 struct OzakiLayout {
@@ -18,13 +21,14 @@ struct OzakiLayout {
 OzakiLayout ozaki_layout(int S, int64_t m, int64_t n, int64_t k, int elem_bytes = 1);
 // Workspace of the tcgen05 engine: a 256-byte header (int32 error code of the
 // last call: 0, or the role whose bounded wait expired), bf16 slices with rows
-// padded to 128, exponents.
-OzakiLayout ozaki_tc_layout(int S, int64_t m, int64_t n, int64_t k);
+// of op(A) padded to 128 and columns of op(B) to the tile width of precision P
+// (DD 128, TD/QD 64), exponents.
+OzakiLayout ozaki_tc_layout(int P, int S, int64_t m, int64_t n, int64_t k);
 
 // Largest k for which the int32 weight sums are exact: S * k * 64 * 64 < 2^31.
 inline int64_t ozaki_k_limit(int S) { return (2147483647LL) / (static_cast<int64_t>(S) * 64 * 64); }
 
-// engine 0: int8 digits on mma.sync s8 (for DD, variant 0..4 selects the CTA
+// engine 0: int8 digits on mma.sync s8 (for DD, variant 0..2 selects the CTA
 // tiling, 0 the default); engine 1: bf16 digits on tcgen05 (TMEM accumulators).
 template <int P>
 cudaError_t launch_ozaki(const GemmArgs<P>& g, int S, void* ws, cudaStream_t s, int variant = 0,

@@ -118,7 +118,7 @@ def test_tile_variants_agree(torch):
     ws = torch.empty(mm.workspace_size("dd", m, n, k, algo="int8", slices=11), dtype=torch.uint8,
                      device="cuda")
     C1 = host(mm.gemm("dd", Ad, Bd, algo="int8", slices=11, workspace=ws, tile=1))
-    for tile in (2, 3, 4, 5):
+    for tile in (2, 3):
         C2 = host(mm.gemm("dd", Ad, Bd, algo="int8", slices=11, workspace=ws, tile=tile))
         assert_bitwise(C1, C2, "tile variant %d" % tile)
     want, _, _ = OZ.gemm(A, B, 11)
@@ -239,7 +239,7 @@ def test_td_qd_full_size_sampled(torch, prec):
 @pytest.mark.parametrize("prec,S", [("td", 22), ("qd", 29), ("dd", 3)])
 def test_tc_engine_matches_int8(torch, prec, S):
     """TD/QD (and a 3-slice DD) on the tcgen05 engine equal the int8 engine and
-    the oracle bit for bit; several 128 x 128 tiles, ragged edges, both
+    the oracle bit for bit; several output tiles, ragged edges, both
     transposes."""
     from paper_2101_06584_gb300 import mpgemm as mm
     P = I.P_OF[prec]

@@ -171,13 +171,24 @@ def test_wide_truncation_and_digits(P):
             assert all(-64 <= d <= 64 for d in ds) and abs(rem) <= Fraction(1, 2)
 
 
+def test_split_exact():
+    """hi = RN(V) with ties to even, lo = V - hi exactly."""
+    for V in (0, 1, -1, 2 ** 53 + 1, 2 ** 53 + 3, -(2 ** 60) - 2 ** 7 - 1, 2 ** 93 - 1, 3 * 2 ** 52 + 1):
+        hi, lo = OZ.split_exact(V)
+        assert Fraction(hi) + Fraction(lo) == V
+        assert abs(Fraction(lo)) <= X.ulp(hi) / 2 if hi else lo == 0
+    assert OZ.split_exact(2 ** 53 + 1) == (2.0 ** 53, 1.0)        # tie -> even
+    assert OZ.split_exact(2 ** 53 + 3) == (2.0 ** 53 + 4, -1.0)   # tie -> even (up)
+
+
 def test_weight_groups():
     for S in (1, 2, 3, 4, 13, 22, 29, 40):
         for P in (2, 3, 4):
             groups = OZ.weight_groups(S, P)
             flat = [w for g in groups for w in g]
             assert flat == list(range(S + 1, 1, -1))
-            assert all(len(g) == 3 for g in groups[:-1]) and 1 <= len(groups[-1]) <= 3
+            G = OZ.group_size(P)
+            assert all(len(g) == G for g in groups[:-1]) and 1 <= len(groups[-1]) <= G
 
 
 @pytest.mark.parametrize("P,S", [(3, 22), (4, 29)])
