@@ -675,18 +675,18 @@ __global__ void __launch_bounds__(WM * WN * 32, MINB) ozaki_gemm_kernel(const Oz
 
 // ------------------------------------------------------- tcgen05 engine
 //
-// The bf16 digits on the 5th-generation tensor cores.  A persistent CTA per SM
-// owns 128 x BN tiles of C (BN = 128 for DD, 64 for TD and QD).  Warp 0
-// streams 128 x 64 (A) and BN x 64 (B) bf16 slice tiles of op(A) and op(B)^T
+// The bf16 digits on the 5th-generation tensor cores, TD and QD (DD runs on
+// CTA pairs, below).  A persistent CTA per SM owns 128 x 64 tiles of C.  Warp 0
+// streams 128 x 64 (A) and 64 x 64 (B) bf16 slice tiles of op(A) and op(B)^T
 // into shared memory with TMA (128-byte swizzle, 6-stage mbarrier ring).
 // Warp 1 owns 512 TMEM columns and issues tcgen05.mma.cta_group::1.kind::f16
-// (M = 128, N = BN, K = 16, fp32 accumulation), filling one of two TMEM
+// (M = 128, N = 64, K = 16, fp32 accumulation), filling one of two TMEM
 // accumulators per segment: the k tiles of one weight, at most 2048 values of
 // k, so every fp32 partial sum of integer products of at most 2^12 stays an
 // exact integer below 2^23.  Warps 2-5 (one TMEM lane quadrant each, one row
 // of the tile per thread) drain each segment: fp32 -> int, shifted into that
-// thread's exact group sums held in TMEM after the accumulators (DD: 64-bit,
-// 2 columns per output; TD/QD: 128-bit, 4 columns); at the end of a group
+// thread's exact 128-bit group sums held in TMEM after the accumulators (4
+// columns per output); at the end of a group
 // they split the group value exactly into two binary64 and add it to C with
 // the precision's add.  The integer weight sums equal those of the int8 path,
 // so the result is bit-identical to it.  Every wait is bounded (about 1 s): on
@@ -702,13 +702,14 @@ constexpr int SEG_TILES = 2048 / KE;                     // k-tiles per fp32 seg
 constexpr int TMEM_COLS = 512;
 constexpr unsigned long long TIMEOUT_NS = 1000000000ull;
 
-// Per-precision tile: TMEM holds two BN-column fp32 accumulators and BN
-// group sums of GW 32-bit words each (2 BN + GW BN <= 512).
+// Tile of TD and QD: TMEM holds two BN-column fp32 accumulators and BN group
+// sums of GW 32-bit words each (2 BN + GW BN <= 512).
 template <int P> struct Cfg {
-    static constexpr int BN = P == 2 ? 128 : 64;
-    static constexpr int GW = P == 2 ? 2 : 4;
+    static_assert(P == 3 || P == 4, "DD runs on CTA pairs");
+    static constexpr int BN = 64;
+    static constexpr int GW = 4;
     static constexpr int B_BYTES = BN * KE * 2;
-    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;   // 32 KB (DD), 24 KB
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;   // 24 KB
     static constexpr int ACC_COLS = BN;                      // accumulators at columns 0 and BN
     static constexpr int GRP_COL = 2 * BN;
     static_assert(GRP_COL + GW * BN <= TMEM_COLS, "TMEM columns");
@@ -1062,6 +1063,374 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     }
 }
 
+// ------------------------------------------------- tcgen05 engine, CTA pairs
+//
+// DD on pairs of SMs (a cluster of two CTAs, tcgen05 .cta_group::2).  The pair
+// owns a 256 x 128 tile of C; each CTA holds 128 rows of it in its own TMEM
+// (two 128-column fp32 accumulators and the 64-bit group sums, exactly as in
+// the single-CTA engine, so the epilogue and the result are the same).  Each
+// CTA's TMA loads its 128 rows of the op(A) slice tile and its half (64 rows)
+// of the op(B)^T slice tile, 128 values of k per stage (two 64-wide boxes
+// each), and signals the leader CTA's barrier; the leader's MMA thread issues
+// tcgen05.mma.cta_group::2 with M = 256, N = 128, which reads A from both CTAs
+// and B halves from both, and releases a stage in both CTAs with one
+// multicast commit.  Compared with a 128 x 128 tile per SM this loads a
+// quarter fewer bytes per product and waits once per eight MMAs instead of
+// four.  Epilogue warps of both CTAs signal the leader when an accumulator
+// has been drained.  Every wait is bounded; a role that gives up sets the
+// abort flag of both CTAs.
+
+namespace tc2 {
+constexpr int BM = 128;                                  // rows per CTA (the pair covers 256)
+constexpr int BN = 128;                                  // columns of the pair's tile
+constexpr int KE = 64;                                   // box width in bf16 (128 bytes)
+constexpr int KB = 2;                                    // boxes per stage: 128 values of k
+constexpr int STAGES = 4;
+constexpr int A_BOX = BM * KE * 2;                       // 16 KB
+constexpr int B_BOX = (BN / 2) * KE * 2;                 // 8 KB
+constexpr int STAGE_BYTES = KB * (A_BOX + B_BOX);        // 48 KB per CTA
+constexpr int SEG_STAGES = 2048 / (KE * KB);             // stages per fp32 segment
+constexpr int GW = 2;                                    // 64-bit group sums
+constexpr int ACC_COLS = BN;
+constexpr int GRP_COL = 2 * BN;
+constexpr int TMEM_COLS = 512;
+constexpr int EPI_ARRIVALS = 8;                          // 4 epilogue warps in each CTA
+static_assert(GRP_COL + GW * BN <= TMEM_COLS, "TMEM columns");
+static_assert(2048 % (KE * KB) == 0 && KPAD % (KE * KB) == 0, "stage k");
+// kind::f16, bf16 A and B (K-major), fp32 D, M = 256, N = 128
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((static_cast<uint32_t>(BN) >> 3) << 17) |
+                           ((256u >> 4) << 24);
+}  // namespace tc2
+
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_index()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_count()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+// The shared::cluster address of the same variable in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_cl(uint64_t* b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_cl(uint64_t* b, unsigned parity, volatile int* abort_flag)
+{
+    const unsigned long long t0 = gtimer();
+    while (!mbar_try_cl(b, parity)) {
+        if (*abort_flag) return false;
+        if (gtimer() - t0 > tc::TIMEOUT_NS) return false;
+    }
+    return true;
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t caddr)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
+}
+__device__ __forceinline__ void st_cluster(uint32_t caddr, int v)
+{
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(caddr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void tma_load_3d_pair(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                                 uint32_t bar_caddr)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar_caddr)
+        : "memory");
+}
+__device__ __forceinline__ void umma_pair(uint32_t d, uint64_t da, uint64_t db, uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(d), "l"(da), "l"(db), "r"(tc2::IDESC), "r"(acc));
+}
+// Arrive on the barrier at this address in both CTAs once the MMAs issued so far complete.
+__device__ __forceinline__ void umma_commit_both(uint64_t* bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+        ::"r"(smem_u32(bar)), "h"(static_cast<uint16_t>(3)) : "memory");
+}
+__device__ __forceinline__ void umma_commit_pair_local(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <int P>
+__global__ void __launch_bounds__(192, 1)
+ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     const TcArgs g)
+{
+    static_assert(P == 2, "the CTA-pair engine keeps 64-bit group sums (DD)");
+    using G = typename GroupSum<P>::T;
+    constexpr int BN = tc2::BN, GW = tc2::GW, OPW = 32 / GW;
+    constexpr int kGroup = ozaki_group(P);
+    extern __shared__ uint8_t dsm[];
+    __shared__ __align__(8) uint64_t full[tc2::STAGES], empty[tc2::STAGES], accf[2], acce[2], fin;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    __shared__ int s_tau[BN];
+
+    const uint32_t raw = smem_u32(dsm);
+    uint8_t* stage0 = dsm + (((raw + 1023u) & ~1023u) - raw);   // 1024-aligned for the swizzle
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    volatile int* abortp = &abort_flag;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < tc2::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], tc2::EPI_ARRIVALS);
+        }
+        mbar_init(&fin, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        // both CTAs of the pair allocate together
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&tmem_base)), "r"(tc2::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    __syncwarp();
+    cluster_sync_all();        // barriers of both CTAs initialised before any remote arrival
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    const int S = g.S;
+    const int KT = static_cast<int>(g.kp / (tc2::KE * tc2::KB));
+    const int per_tile = (S * (S + 1) / 2) * KT;
+    const int ntiles = g.tiles_m * g.tiles_n;
+    const int cid = static_cast<int>(cluster_index()), ncl = static_cast<int>(cluster_count());
+    const uint32_t peer_abort = cluster_addr(&abort_flag, rank ^ 1u);
+    auto fail = [&](int code) {
+        *abortp = 1;
+        st_cluster(peer_abort, 1);
+        atomicCAS(g.err, 0, code);
+    };
+
+    if (warp == 0) {
+        // ---------------------------------------------------------- producer
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int tile = cid; tile < ntiles && ok; tile += ncl) {
+                const int ma = (tile % g.tiles_m) * 2 * tc2::BM + static_cast<int>(rank) * tc2::BM;
+                const int nb = (tile / g.tiles_m) * BN + static_cast<int>(rank) * (BN / 2);
+                Cursor c{S + 1, 1, 0};
+                for (int i = 0; i < per_tile; ++i, ++it) {
+                    const uint32_t st = it % tc2::STAGES, ph = (it / tc2::STAGES) & 1u;
+                    if (!mbar_wait_cl(&empty[st], ph ^ 1u, abortp)) { fail(1); ok = false; break; }
+                    uint8_t* sa = stage0 + st * tc2::STAGE_BYTES;
+                    const uint32_t bar = cluster_addr(&full[st], 0);
+                    if (rank == 0) mbar_expect_tx(&full[st], 2 * tc2::STAGE_BYTES);
+#pragma unroll
+                    for (int q = 0; q < tc2::KB; ++q) {
+                        const int x = (c.kt * tc2::KB + q) * tc2::KE;
+                        tma_load_3d_pair(sa + q * tc2::A_BOX, &tmA, x, ma, c.s - 1, bar);
+                        tma_load_3d_pair(sa + tc2::KB * tc2::A_BOX + q * tc2::B_BOX, &tmB, x, nb, c.w - c.s - 1, bar);
+                    }
+                    c.advance(S, KT);
+                }
+            }
+            // every stage's last release has arrived (the leader's MMAs have
+            // read this CTA's loads) before the CTA may exit
+            for (uint32_t j = 0; j < tc2::STAGES && j < it; ++j) {
+                const uint32_t k = it - 1 - j;
+                const unsigned long long t0 = gtimer();
+                while (!mbar_try_cl(&empty[k % tc2::STAGES], (k / tc2::STAGES) & 1u) &&
+                       gtimer() - t0 < tc::TIMEOUT_NS) {
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA (leader only)
+        if (lane == 0 && rank == 0) {
+            uint32_t it = 0, seg = 0;
+            bool ok = true;
+            for (int tile = cid; tile < ntiles && ok; tile += ncl) {
+                Cursor c{S + 1, 1, 0};
+                int seg_stages = 0;
+                uint32_t b = 0;
+                for (int i = 0; i < per_tile; ++i, ++it) {
+                    if (seg_stages == 0) {
+                        b = seg & 1u;
+                        if (!mbar_wait_cl(&acce[b], ((seg >> 1) & 1u) ^ 1u, abortp)) { fail(2); ok = false; break; }
+                    }
+                    const uint32_t st = it % tc2::STAGES, ph = (it / tc2::STAGES) & 1u;
+                    if (!mbar_wait_cl(&full[st], ph, abortp)) { fail(3); ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(stage0 + st * tc2::STAGE_BYTES);
+#pragma unroll
+                    for (int q = 0; q < tc2::KB; ++q) {
+                        const uint64_t da = umma_desc(sa + q * tc2::A_BOX);
+                        const uint64_t db = umma_desc(sa + tc2::KB * tc2::A_BOX + q * tc2::B_BOX);
+#pragma unroll
+                        for (int kk = 0; kk < tc2::KE / 16; ++kk)
+                            umma_pair(tmem + b * tc2::ACC_COLS, da + 2ull * kk, db + 2ull * kk,
+                                      (seg_stages > 0 || q > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    umma_commit_both(&empty[st]);
+                    ++seg_stages;
+                    const int w = c.w;
+                    c.advance(S, KT);
+                    if (c.w != w || seg_stages == tc2::SEG_STAGES) {
+                        umma_commit_both(&accf[b]);
+                        ++seg;
+                        seg_stages = 0;
+                    }
+                }
+            }
+            // every MMA issued has completed before TMEM is released
+            umma_commit_pair_local(&fin);
+            const unsigned long long t0 = gtimer();
+            while (!mbar_try_cl(&fin, 0u) && gtimer() - t0 < tc::TIMEOUT_NS) {
+            }
+        }
+    } else {
+        // ---------------------------------------------------------- epilogue
+        const mp::Rn f = mp::make_rn();
+        const int q = warp & 3;                          // TMEM lane quadrant of this warp
+        const int r = 32 * q + lane;                     // row of this CTA's half of the tile
+        const uint32_t lane_off = static_cast<uint32_t>(32 * q) << 16;
+        const uint32_t grp = tmem + lane_off + tc2::GRP_COL;
+        const uint32_t lead_acce0 = cluster_addr(&acce[0], 0), lead_acce1 = cluster_addr(&acce[1], 0);
+        uint32_t zero32[32];
+#pragma unroll
+        for (int t = 0; t < 32; ++t) zero32[t] = 0u;
+        uint32_t seg = 0;
+        bool ok = true;
+        for (int tile = cid; tile < ntiles && ok; tile += ncl) {
+            const int m0 = (tile % g.tiles_m) * 2 * tc2::BM + static_cast<int>(rank) * tc2::BM;
+            const int n0 = (tile / g.tiles_m) * BN;
+            const int64_t row = m0 + r;
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (r < BN) s_tau[r] = g.tau[n0 + r];
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            const int sg = g.sig[row];
+#pragma unroll
+            for (int c0 = 0; c0 < GW * BN; c0 += 32) tmem_st32(grp + c0, zero32);
+            tmem_wait_st();
+            Cursor c{S + 1, 1, 0};
+            int seg_stages = 0;
+            bool first_group = true;
+            for (int i = 0; i < per_tile; ++i) {
+                ++seg_stages;
+                const int w = c.w;
+                c.advance(S, KT);
+                const bool weight_end = c.w != w;
+                if (!weight_end && seg_stages != tc2::SEG_STAGES) continue;
+                seg_stages = 0;
+                const uint32_t b = seg & 1u;
+                // the decision must be warp-uniform: the TMEM loads below are .sync.aligned
+                if (!__all_sync(0xffffffffu, mbar_wait_cl(&accf[b], (seg >> 1) & 1u, abortp))) {
+                    fail(4);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const int j = (S + 1 - w) % kGroup;
+                for (int c0 = 0; c0 < BN; c0 += 32) {
+                    uint32_t fv[32];
+                    tmem_ld32(tmem + lane_off + b * tc2::ACC_COLS + c0, fv);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int h = 0; h < GW; ++h) {
+                        uint32_t gw[32];
+                        tmem_ld32(grp + GW * c0 + 32 * h, gw);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int t = 0; t < OPW; ++t) {
+                            const int add = __float2int_rn(__uint_as_float(fv[OPW * h + t]));
+                            const G V = group_load<G, GW>(gw + GW * t) + (static_cast<G>(add) << (7 * j));
+                            group_store<G, GW>(gw + GW * t, V);
+                        }
+                        tmem_st32(grp + GW * c0 + 32 * h, gw);
+                    }
+                    tmem_wait_st();
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(b ? lead_acce1 : lead_acce0);
+                ++seg;
+                if (!(weight_end && (j == kGroup - 1 || w == 2))) continue;
+                // end of a group: add its exact value to C
+                const int wmax = w + j;
+                for (int c0 = 0; c0 < GW * BN; c0 += 32) {
+                    uint32_t gw[32];
+                    tmem_ld32(grp + c0, gw);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int t = 0; t < OPW; ++t) {
+                        const int64_t col = n0 + c0 / GW + t;
+                        if (row >= g.m || col >= g.n) continue;
+                        double y[P], acc[P], zz[P];
+                        split_exact(group_load<G, GW>(gw + GW * t), sg + s_tau[c0 / GW + t] - 7 * wmax, y[0], y[1]);
+#pragma unroll
+                        for (int cc = 2; cc < P; ++cc) y[cc] = f.zero;
+#pragma unroll
+                        for (int cc = 0; cc < P; ++cc)
+                            acc[cc] = first_group ? 0.0 : g.C[cc][row * g.ldc + col];
+                        mp::Ops<P>::add(f, acc, y, zz);
+#pragma unroll
+                        for (int cc = 0; cc < P; ++cc) g.C[cc][row * g.ldc + col] = zz[cc];
+                    }
+                    tmem_st32(grp + c0, zero32);
+                }
+                tmem_wait_st();
+                first_group = false;
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    __syncwarp();
+    cluster_sync_all();        // no remote arrival or TMA into this CTA is outstanding
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tc2::TMEM_COLS));
+    }
+}
+
 // ------------------------------------------------------- fixed scratch
 
 // Scratch for callers that cannot allocate device memory (see
@@ -1144,8 +1513,9 @@ OzakiLayout ozaki_tc_layout(int P, int S, int64_t m, int64_t n, int64_t k)
 {
     OzakiLayout L;
     L.S = S;
-    L.mp = round_up(m > 0 ? m : 1, tc::BM);
-    L.np = round_up(n > 0 ? n : 1, P == 2 ? tc::Cfg<2>::BN : tc::Cfg<4>::BN);
+    // DD runs on CTA pairs (256 x 128 tiles), TD/QD on single CTAs (128 x 64)
+    L.mp = round_up(m > 0 ? m : 1, P == 2 ? 2 * tc2::BM : tc::BM);
+    L.np = round_up(n > 0 ? n : 1, P == 2 ? tc2::BN : tc::Cfg<4>::BN);
     L.kp = round_up(k > 0 ? k : 1, KPAD);
     L.offA = 256;                                     // bytes 0..255: header (error code)
     L.offB = L.offA + round_up(static_cast<int64_t>(S) * L.mp * L.kp * 2, 256);
@@ -1191,6 +1561,41 @@ static bool slice_map(CUtensorMap* map, void* base, int S, int64_t rows, int64_t
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Clusters of two CTAs of the pair kernel that fit on the device at once.
+static cudaError_t pair_clusters(int* out)
+{
+    static std::mutex mu;
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!cached[dev]) {
+        const int smem = tc2::STAGES * tc2::STAGE_BYTES + 1024;
+        e = cudaFuncSetAttribute(ozaki_tc_pair_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(2);
+        cfg.blockDim = dim3(192);
+        cfg.dynamicSmemBytes = smem;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        e = cudaOccupancyMaxActiveClusters(&n, ozaki_tc_pair_kernel<2>, &cfg);
+        if (e != cudaSuccess) return e;
+        if (n < 1) return cudaErrorInvalidConfiguration;
+        cached[dev] = n;
+    }
+    *out = cached[dev];
+    return cudaSuccess;
+}
+
 template <int P>
 static cudaError_t launch_ozaki_tc(const GemmArgs<P>& g, int S, void* ws, cudaStream_t s)
 {
@@ -1212,18 +1617,44 @@ static cudaError_t launch_ozaki_tc(const GemmArgs<P>& g, int S, void* ws, cudaSt
     if (e == cudaSuccess) e = slice_operand(pb, g.n, g.k, g.ldb, g.trans_b != 0, S, L.np, L.kp, sb, tau, s);
     if (e != cudaSuccess) return e;
     CUtensorMap ma, mb;
-    if (!slice_map(&ma, sa, S, L.mp, L.kp, tc::BM) || !slice_map(&mb, sb, S, L.np, L.kp, Cf::BN))
-        return cudaErrorInvalidValue;
-    TcArgs a{sig, tau, {nullptr, nullptr, nullptr, nullptr}, g.ldc, g.m, g.n, L.kp, S,
-             static_cast<int>(L.mp / tc::BM), static_cast<int>(L.np / Cf::BN), err};
-    for (int c = 0; c < P; ++c) a.C[c] = g.C[c];
-    const int smem = tc::STAGES * Cf::STAGE_BYTES + 1024;
-    e = cudaFuncSetAttribute(ozaki_tc_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    const int tiles = a.tiles_m * a.tiles_n;
-    const int grid = tiles < num_sms() ? tiles : num_sms();
-    ozaki_tc_kernel<P><<<grid, 192, smem, s>>>(ma, mb, a);
-    return cudaGetLastError();
+    if constexpr (P == 2) {
+        if (!slice_map(&ma, sa, S, L.mp, L.kp, tc2::BM) || !slice_map(&mb, sb, S, L.np, L.kp, tc2::BN / 2))
+            return cudaErrorInvalidValue;
+        TcArgs a{sig, tau, {g.C[0], g.C[1], nullptr, nullptr}, g.ldc, g.m, g.n, L.kp, S,
+                 static_cast<int>(L.mp / (2 * tc2::BM)), static_cast<int>(L.np / tc2::BN), err};
+        int clusters = 0;
+        e = pair_clusters(&clusters);
+        if (e != cudaSuccess) return e;
+        const int tiles = a.tiles_m * a.tiles_n;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(2 * static_cast<unsigned>(tiles < clusters ? tiles : clusters));
+        cfg.blockDim = dim3(192);
+        cfg.dynamicSmemBytes = tc2::STAGES * tc2::STAGE_BYTES + 1024;
+        cfg.stream = s;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, ozaki_tc_pair_kernel<2>, ma, mb, a);
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+    } else {
+        if (!slice_map(&ma, sa, S, L.mp, L.kp, tc::BM) || !slice_map(&mb, sb, S, L.np, L.kp, Cf::BN))
+            return cudaErrorInvalidValue;
+        TcArgs a{sig, tau, {nullptr, nullptr, nullptr, nullptr}, g.ldc, g.m, g.n, L.kp, S,
+                 static_cast<int>(L.mp / tc::BM), static_cast<int>(L.np / Cf::BN), err};
+        for (int c = 0; c < P; ++c) a.C[c] = g.C[c];
+        const int smem = tc::STAGES * Cf::STAGE_BYTES + 1024;
+        e = cudaFuncSetAttribute(ozaki_tc_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        const int tiles = a.tiles_m * a.tiles_n;
+        const int grid = tiles < num_sms() ? tiles : num_sms();
+        ozaki_tc_kernel<P><<<grid, 192, smem, s>>>(ma, mb, a);
+        return cudaGetLastError();
+    }
 }
 
 template <int P>
