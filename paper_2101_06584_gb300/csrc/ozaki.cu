@@ -112,21 +112,35 @@ __device__ __forceinline__ __int128 fixed_point(double hi, double lo, int sigma,
 
 }  // namespace
 
-// The S digits of (hi + lo) 2^-sigma (nearest, ties to even).
-__device__ __forceinline__ void ozaki_digits(double hi, double lo, int sigma, int S, int8_t* out)
+// Digits of a fixed-point value held with the current digit's unit at bit
+// 120 of a 128-bit two's-complement integer (hi, lo): |value| < 2^126.  Each
+// step takes the nearest integer of value / 2^120 (ties to even unless
+// `sticky` says the true value lies above the held one), subtracts it, and
+// moves the next digit's unit up by the 7 bits of the base.
+struct DigitCursor {
+    uint64_t hi, lo;
+    bool sticky;
+    __device__ __forceinline__ int next()
+    {
+        const int64_t t = static_cast<int64_t>(hi + (1ull << 55)) >> 56;          // nearest, ties up
+        const bool tie = lo == 0 && (hi & ((1ull << 56) - 1)) == (1ull << 55);
+        const int64_t d = (tie && !sticky && (t & 1)) ? t - 1 : t;                // ties to even
+        hi -= static_cast<uint64_t>(d) << 56;                                      // |value| <= 2^119
+        hi = (hi << 7) | (lo >> 57);
+        lo <<= 7;
+        return static_cast<int>(d);
+    }
+};
+
+// The digit cursor of (hi + lo) 2^-sigma with S digits: R = floor((hi + lo)
+// 2^(F - sigma)), F = 7S + 12, |R| < 2^(F-1), shifted left by 115 - 7S so that
+// the first digit's unit 2^(F-7) sits at bit 120.
+__device__ __forceinline__ DigitCursor ozaki_cursor(double hi, double lo, int sigma, int S)
 {
     const int F = 7 * S + 12;
     bool sticky;
-    __int128 R = fixed_point(hi, lo, sigma, F, sticky);
-    for (int s = 1; s <= S; ++s) {
-        const int q = F - 7 * s;
-        const __int128 U = static_cast<__int128>(1) << q;
-        const __int128 half = U >> 1;
-        __int128 dd = (R + half) >> q;                       // nearest, ties up
-        if (!sticky && (R & (U - 1)) == half && (dd & 1)) dd -= 1;   // ties to even
-        R -= dd << q;
-        out[s - 1] = static_cast<int8_t>(static_cast<int>(dd));
-    }
+    const unsigned __int128 R = static_cast<unsigned __int128>(fixed_point(hi, lo, sigma, F, sticky)) << (115 - 7 * S);
+    return DigitCursor{static_cast<uint64_t>(R >> 64), static_cast<uint64_t>(R), sticky};
 }
 
 // ------------------------------------------------- wide digits (TD, QD)
@@ -180,10 +194,30 @@ __device__ __forceinline__ void wide_add_small(Wide& W, int64_t v)
     wide_add_shifted(W, v, 0);
 }
 
-// The S digits of the sum of the P components, each floored at
-// 2^(sigma - F - 64) (nearest, ties to even).
+// Digits of a 384-bit fixed-point value with the current digit's unit at bit
+// 376 (|value| < 2^382); as DigitCursor, with every tie exact.
+struct WideCursor {
+    uint64_t w[kWideWords];
+    __device__ __forceinline__ int next()
+    {
+        const int64_t t = static_cast<int64_t>(w[5] + (1ull << 55)) >> 56;        // nearest, ties up
+        bool tie = (w[5] & ((1ull << 56) - 1)) == (1ull << 55);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) tie = tie && w[i] == 0;
+        const int64_t d = (tie && (t & 1)) ? t - 1 : t;                           // ties to even
+        w[5] -= static_cast<uint64_t>(d) << 56;
+#pragma unroll
+        for (int i = 5; i > 0; --i) w[i] = (w[i] << 7) | (w[i - 1] >> 57);
+        w[0] <<= 7;
+        return static_cast<int>(d);
+    }
+};
+
+// The digit cursor of the sum of the P components, each floored at
+// 2^(sigma - F - 64), F = 7S + 12: the floored sum W (|W| < 2^(F+63)) shifted
+// left by 307 - 7S so that the first digit's unit 2^(F+57) sits at bit 376.
 template <int P>
-__device__ __forceinline__ void ozaki_digits_wide(const double (&c)[P], int sigma, int S, int8_t* out)
+__device__ __forceinline__ WideCursor ozaki_cursor_wide(const double (&c)[P], int sigma, int S)
 {
     const int F = 7 * S + 12;
     Wide W;
@@ -200,30 +234,22 @@ __device__ __forceinline__ void ozaki_digits_wide(const double (&c)[P], int sigm
         else if (sh > -64) wide_add_small(W, M >> (-sh));      // arithmetic shift: floor
         else wide_add_small(W, M < 0 ? -1 : 0);
     }
-    for (int s = 1; s <= S; ++s) {
-        const int q = F + kGuardBits - 7 * s;     // bit position of the digit's unit (>= 76)
-        const int wq = q >> 6, bq = q & 63;
-        // t = floor((W + 2^(q-1)) / 2^q) from a copy with the half added
-        Wide H = W;
-        wide_add_shifted(H, 1, q - 1);
-        // bits q .. q+63 as a signed 64-bit value; |t| <= 65, so the bits
-        // above q + 7 are copies of the sign
-        int64_t t;
-        if (wq + 1 < kWideWords) {
-            const uint64_t hi = bq == 0 ? 0ull : (H.w[wq + 1] << (64 - bq));
-            t = static_cast<int64_t>((H.w[wq] >> bq) | hi);
-        } else {
-            t = static_cast<int64_t>(H.w[wq]) >> bq;            // arithmetic: top word
-        }
-        // a tie leaves no bits below q after adding the half
-        bool below_zero = (H.w[wq] & ((bq == 0) ? 0ull : ((1ull << bq) - 1))) == 0;
+    // shift left by L = 307 - 7S (27 <= L <= 300): whole words first, with
+    // unrolled selects so that W stays in registers, then the bits
+    const int L = 307 - 7 * S, ws = L >> 6, bs = L & 63;
 #pragma unroll
-        for (int i = 0; i < kWideWords; ++i)
-            if (i < wq) below_zero = below_zero && H.w[i] == 0ull;
-        if (below_zero && (t & 1)) t -= 1;
-        wide_add_shifted(W, -t, q);
-        out[s - 1] = static_cast<int8_t>(t);
+    for (int k = 0; k < 4; ++k) {
+        if (k < ws) {
+#pragma unroll
+            for (int i = kWideWords - 1; i > 0; --i) W.w[i] = W.w[i - 1];
+            W.w[0] = 0ull;
+        }
     }
+    WideCursor cur;
+#pragma unroll
+    for (int i = kWideWords - 1; i > 0; --i) cur.w[i] = bs ? (W.w[i] << bs) | (W.w[i - 1] >> (64 - bs)) : W.w[i];
+    cur.w[0] = W.w[0] << bs;
+    return cur;
 }
 
 // ------------------------------------------------------------------ scale
@@ -247,18 +273,31 @@ __global__ void ozaki_scale_contig(const double* __restrict__ hi, int64_t count,
     if (lane == 0) out[v] = mx ? ilogb_bits(mx) + 2 : 0;
 }
 
-// One thread per vector whose elements are ld apart (vectors adjacent).
-__global__ void ozaki_scale_strided(const double* __restrict__ hi, int64_t count, int64_t len,
-                                    int64_t ld, int* __restrict__ out)
+// Vectors whose elements are ld apart (vectors adjacent): a block of 32 x 32
+// threads covers 32 vectors, each column of threads a 32-way split of the
+// elements (coalesced rows of 32 vectors), reduced in shared memory.
+__global__ void __launch_bounds__(1024) ozaki_scale_strided(const double* __restrict__ hi, int64_t count,
+                                                           int64_t len, int64_t ld, int* __restrict__ out)
 {
-    const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (v >= count) return;
+    __shared__ unsigned long long smax[32];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t v = static_cast<int64_t>(blockIdx.x) * 32 + tx;
+    if (ty == 0) smax[tx] = 0;
+    __syncthreads();
     uint64_t mx = 0;
-    for (int64_t p = 0; p < len; ++p) {
-        const uint64_t b = abs_bits(hi[p * ld + v]);
-        mx = b > mx ? b : mx;
+    if (v < count) {
+#pragma unroll 4
+        for (int64_t p = ty; p < len; p += 32) {
+            const uint64_t b = abs_bits(hi[p * ld + v]);
+            mx = b > mx ? b : mx;
+        }
     }
-    out[v] = mx ? ilogb_bits(mx) + 2 : 0;
+    atomicMax(&smax[tx], static_cast<unsigned long long>(mx));
+    __syncthreads();
+    if (ty == 0 && v < count) {
+        const uint64_t m = smax[tx];
+        out[v] = m ? ilogb_bits(m) + 2 : 0;
+    }
 }
 
 // Zero the exponent padding [count, padded).
@@ -308,19 +347,36 @@ struct Planes {
     const double* c[P];
 };
 
-// The S digits of element `off` of the component planes.
+// The digit cursor of element `off` of the component planes.
+template <int P> struct CursorOf { using T = WideCursor; };
+template <> struct CursorOf<2> { using T = DigitCursor; };
+
 template <int P>
-__device__ __forceinline__ void element_digits(const Planes<P>& pl, int64_t off, int sigma, int S,
-                                               int8_t* out)
+__device__ __forceinline__ typename CursorOf<P>::T element_cursor(const Planes<P>& pl, int64_t off, int sigma, int S)
 {
     if constexpr (P == 2) {
-        ozaki_digits(pl.c[0][off], pl.c[1][off], sigma, S, out);
+        return ozaki_cursor(pl.c[0][off], pl.c[1][off], sigma, S);
     } else {
         double c[P];
 #pragma unroll
         for (int i = 0; i < P; ++i) c[i] = pl.c[i][off];
-        ozaki_digits_wide<P>(c, sigma, S, out);
+        return ozaki_cursor_wide<P>(c, sigma, S);
     }
+}
+// A cursor whose digits are all zero (padding).
+template <int P>
+__device__ __forceinline__ typename CursorOf<P>::T zero_cursor()
+{
+    typename CursorOf<P>::T c;
+    if constexpr (P == 2) {
+        c.hi = 0;
+        c.lo = 0;
+        c.sticky = false;
+    } else {
+#pragma unroll
+        for (int i = 0; i < kWideWords; ++i) c.w[i] = 0;
+    }
+    return c;
 }
 
 template <int P, typename T>
@@ -333,20 +389,19 @@ __global__ void ozaki_slice_rows(const Planes<P> pl, int64_t rows, int64_t len, 
     if (t >= rows_pad * quads) return;
     const int64_t r = t / quads;
     const int64_t p0 = (t % quads) * 4;
-    int8_t dg[4][kOzakiMaxSlicesWide];
     const int sg = r < rows ? sig[r] : 0;
+    typename CursorOf<P>::T cur[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int64_t p = p0 + u;
-        if (r < rows && p < len) {
-            element_digits<P>(pl, r * ld + p, sg, S, dg[u]);
-        } else {
-            for (int s = 0; s < S; ++s) dg[u][s] = 0;
-        }
+        cur[u] = (r < rows && p < len) ? element_cursor<P>(pl, r * ld + p, sg, S) : zero_cursor<P>();
     }
-    for (int s = 0; s < S; ++s)
-        store4(out + (static_cast<int64_t>(s) * rows_pad + r) * kp + p0, dg[0][s], dg[1][s], dg[2][s],
-               dg[3][s]);
+    T* o = out + r * kp + p0;
+    const int64_t plane = rows_pad * kp;
+    for (int s = 0; s < S; ++s, o += plane) {
+        const int d0 = cur[0].next(), d1 = cur[1].next(), d2 = cur[2].next(), d3 = cur[3].next();
+        store4(o, static_cast<int8_t>(d0), static_cast<int8_t>(d1), static_cast<int8_t>(d2), static_cast<int8_t>(d3));
+    }
 }
 
 // Rows of the sliced operand are strided (element (r, p) at base[p*ld + r]):
@@ -363,18 +418,18 @@ ozaki_slice_cols(const Planes<P> pl, int64_t rows, int64_t len, int64_t ld,
     const int64_t r0 = static_cast<int64_t>(blockIdx.x) * 32;
     const int64_t p0 = static_cast<int64_t>(blockIdx.y) * 32;
     const int tr = threadIdx.x & 31;        // r within the tile
-    const int tp = threadIdx.x >> 5;        // 0..7
+    const int tp = threadIdx.x >> 5;        // 0..7: p = tp, tp + 8, tp + 16, tp + 24
     const int64_t r = r0 + tr;
     const int sg = r < rows ? sig[r] : 0;
-    for (int pp = tp; pp < 32; pp += 8) {
-        const int64_t p = p0 + pp;
-        int8_t dg[SMAX];
-        if (r < rows && p < len) {
-            element_digits<P>(pl, p * ld + r, sg, S, dg);
-        } else {
-            for (int s = 0; s < S; ++s) dg[s] = 0;
-        }
-        for (int s = 0; s < S; ++s) tile[s][tr][pp] = dg[s];
+    typename CursorOf<P>::T cur[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int64_t p = p0 + tp + 8 * u;
+        cur[u] = (r < rows && p < len) ? element_cursor<P>(pl, p * ld + r, sg, S) : zero_cursor<P>();
+    }
+    for (int s = 0; s < S; ++s) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) tile[s][tr][tp + 8 * u] = static_cast<int8_t>(cur[u].next());
     }
     __syncthreads();
     // write: each thread writes 4 consecutive p of one row r
@@ -765,6 +820,7 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, unsigned parity)
 // Bounded wait: false after about a second, or once another role aborted.
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, volatile int* abort_flag)
 {
+    if (mbar_try(b, parity)) return true;      // the common case reads no clock
     const unsigned long long t0 = gtimer();
     while (!mbar_try(b, parity)) {
         if (*abort_flag) return false;
@@ -925,6 +981,7 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         // --------------------------------------------------------------- MMA
         if (lane == 0) {
             uint32_t it = 0, seg = 0;
+            int pend = -1;          // accumulator whose commit waits for the next stage
             bool ok = true;
             for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
                 Cursor c{S + 1, 1, 0};
@@ -938,6 +995,10 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                     const uint32_t st = it % tc::STAGES, ph = (it / tc::STAGES) & 1u;
                     if (!mbar_wait(&full[st], ph, abortp)) { fail(3); ok = false; break; }
                     tc_fence_after();
+                    if (pend >= 0) {
+                        umma_commit(&accf[pend]);
+                        pend = -1;
+                    }
                     const uint32_t sa = smem_u32(stage0 + st * Cf::STAGE_BYTES);
                     const uint64_t da = umma_desc(sa), db = umma_desc(sa + tc::A_BYTES);
 #pragma unroll
@@ -949,12 +1010,13 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                     const int w = c.w;
                     c.advance(S, KT);
                     if (c.w != w || seg_tiles == tc::SEG_TILES) {
-                        umma_commit(&accf[b]);
+                        pend = static_cast<int>(b);
                         ++seg;
                         seg_tiles = 0;
                     }
                 }
             }
+            if (pend >= 0) umma_commit(&accf[pend]);
             // every MMA issued has completed before TMEM is released
             umma_commit(&fin);
             const unsigned long long t0 = gtimer();
@@ -1074,7 +1136,9 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 // each), and signals the leader CTA's barrier; the leader's MMA thread issues
 // tcgen05.mma.cta_group::2 with M = 256, N = 128, which reads A from both CTAs
 // and B halves from both, and releases a stage in both CTAs with one
-// multicast commit.  Compared with a 128 x 128 tile per SM this loads a
+// multicast commit.  A finished accumulator is committed after the next
+// stage's barrier wait, not right behind the stage's own commit: two commits
+// in a row stall the issuing thread.  Compared with a 128 x 128 tile per SM this loads a
 // quarter fewer bytes per product and waits once per eight MMAs instead of
 // four.  Epilogue warps of both CTAs signal the leader when an accumulator
 // has been drained.  Every wait is bounded; a role that gives up sets the
@@ -1144,6 +1208,7 @@ __device__ __forceinline__ bool mbar_try_cl(uint64_t* b, unsigned parity)
 }
 __device__ __forceinline__ bool mbar_wait_cl(uint64_t* b, unsigned parity, volatile int* abort_flag)
 {
+    if (mbar_try_cl(b, parity)) return true;
     const unsigned long long t0 = gtimer();
     while (!mbar_try_cl(b, parity)) {
         if (*abort_flag) return false;
@@ -1285,6 +1350,7 @@ ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
         // ------------------------------------------------ MMA (leader only)
         if (lane == 0 && rank == 0) {
             uint32_t it = 0, seg = 0;
+            int pend = -1;          // accumulator whose commit waits for the next stage
             bool ok = true;
             for (int tile = cid; tile < ntiles && ok; tile += ncl) {
                 Cursor c{S + 1, 1, 0};
@@ -1298,6 +1364,10 @@ ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                     const uint32_t st = it % tc2::STAGES, ph = (it / tc2::STAGES) & 1u;
                     if (!mbar_wait_cl(&full[st], ph, abortp)) { fail(3); ok = false; break; }
                     tc_fence_after();
+                    if (pend >= 0) {
+                        umma_commit_both(&accf[pend]);
+                        pend = -1;
+                    }
                     const uint32_t sa = smem_u32(stage0 + st * tc2::STAGE_BYTES);
 #pragma unroll
                     for (int q = 0; q < tc2::KB; ++q) {
@@ -1313,12 +1383,13 @@ ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                     const int w = c.w;
                     c.advance(S, KT);
                     if (c.w != w || seg_stages == tc2::SEG_STAGES) {
-                        umma_commit_both(&accf[b]);
+                        pend = static_cast<int>(b);
                         ++seg;
                         seg_stages = 0;
                     }
                 }
             }
+            if (pend >= 0) umma_commit_both(&accf[pend]);
             // every MMA issued has completed before TMEM is released
             umma_commit_pair_local(&fin);
             const unsigned long long t0 = gtimer();
@@ -1494,7 +1565,7 @@ static cudaError_t slice_operand(const Planes<P>& pl, int64_t count, int64_t len
 {
     const double* lead = pl.c[0];
     if (contig) ozaki_scale_contig<<<blocks_for(count * 32, 256), 256, 0, s>>>(lead, count, len, ld, sig);
-    else ozaki_scale_strided<<<blocks_for(count, 256), 256, 0, s>>>(lead, count, len, ld, sig);
+    else ozaki_scale_strided<<<blocks_for(count, 32), 1024, 0, s>>>(lead, count, len, ld, sig);
     if (count_pad > count)
         ozaki_fill_int<<<blocks_for(count_pad - count, 256), 256, 0, s>>>(sig, count, count_pad);
     if (contig) {
