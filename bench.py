@@ -392,7 +392,8 @@ class DdInt8(Workload):
             key = "dd_int8_%d_s%d:call" % (n, S)
         else:
             peak, src = bf16_peak()
-            unit, kern = "TFLOP/s", "ozaki_tc_kernel (tcgen05.mma kind::f16) incl. slicing"
+            unit, kern = "TFLOP/s", ("ozaki_tc_pair_kernel (tcgen05.mma.cta_group::2 kind::f16, CTA pairs) "
+                                     "incl. slicing")
             key = "dd_tc_%d_s%d:call" % (n, S)
         return {"bound": "tensor", "kernel": kern, "achieved": ach / 1e12, "peak": peak / 1e12,
                 "unit": unit, "frac": ach / peak, "traffic": recorded_traffic(key),
@@ -453,8 +454,9 @@ class TdQdInt8(Workload):
             peak, src, unit = pk["mma_s8"], "measured mma.sync s8 probe", "Tint8op/s"
         else:
             (peak, src), unit = bf16_peak(), "TFLOP/s"
-        # the QD call spends most of its time in the FP64 group additions
-        fp64_ops = (n * n) * ((S + 2) // 3) * FP64_OPS_PER_MAD["qd"] * 87 // 210
+        # FP64 work of the QD call: one QDadd (87 of the 210 operations of a QD
+        # multiply-add) per output per group of ten weights (S weights)
+        fp64_ops = (n * n) * (-(-S // 10)) * FP64_OPS_PER_MAD["qd"] * 87 // 210
         return {"bound": "tensor", "kernel": "QD slicing form (%s) incl. slicing" % self.engine,
                 "achieved": ach / 1e12, "peak": peak / 1e12, "unit": unit, "peak_source": src,
                 "frac": ach / peak, "traffic": None, "ops_per_unit": 2 * pairs,
