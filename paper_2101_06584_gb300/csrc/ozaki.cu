@@ -463,49 +463,73 @@ __device__ __forceinline__ void mma_s8(int (&c)[4], const uint32_t (&a)[4], cons
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// v * 2^e as a binary64, exactly (v an int32, result in the normal range),
-// built with integer operations.
-__device__ __forceinline__ double scaled_int(int v, int e)
+// u 2^E as binary64 (0 < u <= 2^53), assembled from its bits with integer
+// operations only: the group-end splits run next to the FP64 additions, and
+// integer <-> binary64 conversions would share the FP64 pipe with them.  The
+// result must be a normal binary64, as for every value this form produces.
+__device__ __forceinline__ double pow2_scaled(bool neg, uint64_t u, int E)
 {
-    if (v == 0) return 0.0;
-    const unsigned u = v < 0 ? 0u - static_cast<unsigned>(v) : static_cast<unsigned>(v);
-    const int lz = __clz(static_cast<int>(u));
-    const int ex = 31 - lz + e;
-    const uint64_t mant = (static_cast<uint64_t>(u) << (21 + lz)) & ((1ull << 52) - 1);
-    const uint64_t bits = (static_cast<uint64_t>(v < 0) << 63) |
-                          (static_cast<uint64_t>(ex + 1023) << 52) | mant;
-    return __longlong_as_double(static_cast<long long>(bits));
+    const int msb = 63 - __clzll(static_cast<long long>(u));
+    const uint64_t mant = msb <= 52 ? (u << (52 - msb)) & ((1ull << 52) - 1) : 0ull;   // u = 2^53: 0
+    return __longlong_as_double(static_cast<long long>((static_cast<uint64_t>(neg) << 63) |
+                                                       (static_cast<uint64_t>(msb + E + 1023) << 52) | mant));
 }
 
-// v * 2^e as a binary64, exactly (|v| < 2^53, result in the normal range).
-__device__ __forceinline__ double scaled_int64(int64_t v, int e)
+// The split of the magnitude u (< 2^128) of a group sum: q 2^sh = RN(u) with
+// q <= 2^53 (ties to even), rest = u - q 2^sh (|rest| <= 2^(sh-1)).
+__device__ __forceinline__ void round53(unsigned __int128 u, uint64_t& q, int& sh, int64_t& rest)
 {
-    if (v == 0) return 0.0;
-    const uint64_t u = v < 0 ? 0ull - static_cast<uint64_t>(v) : static_cast<uint64_t>(v);
-    const int lz = __clzll(static_cast<long long>(u));
-    const int ex = 63 - lz + e;
-    const uint64_t mant = (u << (lz - 11)) & ((1ull << 52) - 1);
-    const uint64_t bits = (static_cast<uint64_t>(v < 0) << 63) |
-                          (static_cast<uint64_t>(ex + 1023) << 52) | mant;
-    return __longlong_as_double(static_cast<long long>(bits));
-}
-
-// x * 2^k for a finite x whose result is normal: the exponent field moves by k.
-__device__ __forceinline__ double scale_pow2(double x, int k)
-{
-    if (!mp::nonzero(x)) return x;
-    return __longlong_as_double(__double_as_longlong(x) + (static_cast<long long>(k) << 52));
+    const uint64_t uh = static_cast<uint64_t>(u >> 64), ul = static_cast<uint64_t>(u);
+    const int nb = uh ? 128 - __clzll(static_cast<long long>(uh)) : 64 - __clzll(static_cast<long long>(ul));
+    sh = 0;
+    rest = 0;
+    if (nb <= 53) {
+        q = ul;
+        return;
+    }
+    sh = nb - 53;
+    q = static_cast<uint64_t>(u >> sh);
+    const uint64_t rem = static_cast<uint64_t>(u - (static_cast<unsigned __int128>(q) << sh));
+    const uint64_t half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (q & 1ull))) {
+        q += 1;
+        rest = static_cast<int64_t>(rem) - static_cast<int64_t>(1ull << sh);
+    } else {
+        rest = static_cast<int64_t>(rem);
+    }
 }
 
 // The exact split of a group sum v times 2^e: hi = RN(v) 2^e (ties to even),
 // lo = (v - RN(v)) 2^e, both exact binary64 for the exponents the slicing forms
-// accept; a zero lo is +0.
+// accept; a zero part is +0.
+__device__ __forceinline__ void split_parts(bool neg, uint64_t q, int sh, int64_t rest, int e, double& hi, double& lo)
+{
+    hi = pow2_scaled(neg, q, sh + e);
+    lo = rest == 0 ? 0.0 : pow2_scaled(neg != (rest < 0), static_cast<uint64_t>(rest < 0 ? -rest : rest), e);
+}
 __device__ __forceinline__ void split_exact(long long v, int e, double& hi, double& lo)
 {
-    const double h = __ll2double_rn(v);                       // |v| < 2^60: RN(v) fits in 64 bits
-    const long long rest = v - static_cast<long long>(h);     // |rest| <= 2^6, exact
-    hi = scale_pow2(h, e);
-    lo = scale_pow2(static_cast<double>(rest), e);
+    if (v == 0) {
+        hi = 0.0;
+        lo = 0.0;
+        return;
+    }
+    const bool neg = v < 0;
+    const uint64_t u = neg ? 0ull - static_cast<uint64_t>(v) : static_cast<uint64_t>(v);
+    const int nb = 64 - __clzll(static_cast<long long>(u));
+    const int sh = nb > 53 ? nb - 53 : 0;
+    uint64_t q = u >> sh;
+    int64_t rest = 0;
+    if (sh) {
+        const uint64_t rem = u & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (q & 1ull))) {
+            q += 1;
+            rest = static_cast<int64_t>(rem) - static_cast<int64_t>(1ull << sh);
+        } else {
+            rest = static_cast<int64_t>(rem);
+        }
+    }
+    split_parts(neg, q, sh, rest, e, hi, lo);
 }
 __device__ __forceinline__ void split_exact(__int128 v, int e, double& hi, double& lo)
 {
@@ -516,28 +540,11 @@ __device__ __forceinline__ void split_exact(__int128 v, int e, double& hi, doubl
     }
     const bool neg = v < 0;
     const unsigned __int128 u = neg ? static_cast<unsigned __int128>(-v) : static_cast<unsigned __int128>(v);
-    const uint64_t uh = static_cast<uint64_t>(u >> 64), ul = static_cast<uint64_t>(u);
-    const int nb = uh ? 128 - __clzll(static_cast<long long>(uh)) : 64 - __clzll(static_cast<long long>(ul));
     uint64_t q;
-    int sh = 0;
-    int64_t rest = 0;                       // u - q 2^sh, |rest| <= 2^(sh-1)
-    if (nb <= 53) {
-        q = ul;
-    } else {
-        sh = nb - 53;
-        q = static_cast<uint64_t>(u >> sh);
-        const uint64_t rem = static_cast<uint64_t>(u - (static_cast<unsigned __int128>(q) << sh));
-        const uint64_t half = 1ull << (sh - 1);
-        if (rem > half || (rem == half && (q & 1ull))) {
-            q += 1;
-            rest = static_cast<int64_t>(rem) - static_cast<int64_t>(1ull << sh);
-        } else {
-            rest = static_cast<int64_t>(rem);
-        }
-    }
-    const double h = scale_pow2(static_cast<double>(q), sh + e);         // q <= 2^53: exact
-    hi = neg ? -h : h;
-    lo = scale_pow2(static_cast<double>(neg ? -rest : rest), e);         // |rest| < 2^53: exact
+    int sh;
+    int64_t rest;
+    round53(u, q, sh, rest);
+    split_parts(neg, q, sh, rest, e, hi, lo);
 }
 
 // The exact group sums of precision P: 64-bit integers for DD, 128-bit for TD and QD.
@@ -1475,11 +1482,15 @@ ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                         if (row >= g.m || col >= g.n) continue;
                         double y[P], acc[P], zz[P];
                         split_exact(group_load<G, GW>(gw + GW * t), sg + s_tau[c0 / GW + t] - 7 * wmax, y[0], y[1]);
+                        if (first_group) {
+                            // DDadd((0, 0), y) is y exactly: y is an exact split
+                            // with hi = RN(hi + lo) and no negative zero
+                            g.C[0][row * g.ldc + col] = y[0];
+                            g.C[1][row * g.ldc + col] = y[1];
+                            continue;
+                        }
 #pragma unroll
-                        for (int cc = 2; cc < P; ++cc) y[cc] = f.zero;
-#pragma unroll
-                        for (int cc = 0; cc < P; ++cc)
-                            acc[cc] = first_group ? 0.0 : g.C[cc][row * g.ldc + col];
+                        for (int cc = 0; cc < P; ++cc) acc[cc] = g.C[cc][row * g.ldc + col];
                         mp::Ops<P>::add(f, acc, y, zz);
 #pragma unroll
                         for (int cc = 0; cc < P; ++cc) g.C[cc][row * g.ldc + col] = zz[cc];

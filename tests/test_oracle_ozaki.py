@@ -181,6 +181,24 @@ def test_split_exact():
     assert OZ.split_exact(2 ** 53 + 3) == (2.0 ** 53 + 4, -1.0)   # tie -> even (up)
 
 
+def test_dd_first_group_add_is_the_identity():
+    """DDadd (Alg. 1) of (0, 0) and an exact split (hi 2^e, lo 2^e) returns the
+    split bit for bit: the DD kernels store the first group of a tile without
+    the addition, and this is why that changes no result."""
+    rng = np.random.default_rng(77)
+    Vs = [0, 1, -1, 2 ** 53 + 1, 2 ** 53 + 3, -(2 ** 54) - 2, 2 ** 59 - 1, -(2 ** 59) + 1, 2 ** 52, 2 ** 53 - 1]
+    Vs += [int(v) for v in rng.integers(-(2 ** 62), 2 ** 62, 4000)]
+    Vs += [int(rng.integers(1, 2 ** 20)) << int(rng.integers(0, 40)) for _ in range(1000)]
+    # ties and near-ties on both sides of a power of two
+    Vs += [(1 << b) + (1 << (b - 54)) * t for b in range(55, 60) for t in (1, -1, 2, -2, 3, -3)]
+    for V in Vs:
+        hi, lo = OZ.split_exact(V)
+        for e in (-300, -60, 0, 17):
+            y = (math.ldexp(hi, e), math.ldexp(lo, e))
+            got = oracle.op("dd", "add", (0.0, 0.0), y)
+            assert [math.copysign(1, g) for g in got] == [math.copysign(1, v) for v in y] and got == y, (V, e, got, y)
+
+
 def test_weight_groups():
     for S in (1, 2, 3, 4, 13, 22, 29, 40):
         for P in (2, 3, 4):
