@@ -739,8 +739,9 @@ __global__ void __launch_bounds__(WM * WN * 32, MINB) ozaki_gemm_kernel(const Oz
 //
 // The bf16 digits on the 5th-generation tensor cores, TD and QD (DD runs on
 // CTA pairs, below).  A persistent CTA per SM owns 128 x 64 tiles of C.  Warp 0
-// streams 128 x 64 (A) and 64 x 64 (B) bf16 slice tiles of op(A) and op(B)^T
-// into shared memory with TMA (128-byte swizzle, 6-stage mbarrier ring).
+// streams 128 x 128 (A) and 64 x 128 (B) bf16 slice tiles of op(A) and
+// op(B)^T, two 64-wide boxes each, into shared memory with TMA (128-byte
+// swizzle, 4-stage mbarrier ring: eight MMAs per barrier wait).
 // Warp 1 owns 512 TMEM columns and issues tcgen05.mma.cta_group::1.kind::f16
 // (M = 128, N = 64, K = 16, fp32 accumulation), filling one of two TMEM
 // accumulators per segment: the k tiles of one weight, at most 2048 values of
@@ -757,10 +758,12 @@ __global__ void __launch_bounds__(WM * WN * 32, MINB) ozaki_gemm_kernel(const Oz
 
 namespace tc {
 constexpr int BM = 128;
-constexpr int KE = 64;                                   // k-step in bf16 elements (128 bytes)
-constexpr int STAGES = 6;
-constexpr int A_BYTES = BM * KE * 2;
-constexpr int SEG_TILES = 2048 / KE;                     // k-tiles per fp32 segment
+constexpr int KE = 64;                                   // box width in bf16 elements (128 bytes)
+constexpr int KB = 2;                                    // boxes per stage: 128 values of k
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * KE * 2;                     // one A box, 16 KB
+constexpr int SEG_STAGES = 2048 / (KE * KB);             // stages per fp32 segment
+static_assert(KPAD % (KE * KB) == 0, "stage k");
 constexpr int TMEM_COLS = 512;
 constexpr unsigned long long TIMEOUT_NS = 1000000000ull;
 
@@ -770,8 +773,8 @@ template <int P> struct Cfg {
     static_assert(P == 3 || P == 4, "DD runs on CTA pairs");
     static constexpr int BN = 64;
     static constexpr int GW = 4;
-    static constexpr int B_BYTES = BN * KE * 2;
-    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;   // 24 KB
+    static constexpr int B_BYTES = BN * KE * 2;                   // one B box, 8 KB
+    static constexpr int STAGE_BYTES = KB * (A_BYTES + B_BYTES);   // 48 KB
     static constexpr int ACC_COLS = BN;                      // accumulators at columns 0 and BN
     static constexpr int GRP_COL = 2 * BN;
     static_assert(GRP_COL + GW * BN <= TMEM_COLS, "TMEM columns");
@@ -950,7 +953,7 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     const uint32_t tmem = tmem_base;
 
     const int S = g.S;
-    const int KT = static_cast<int>(g.kp / tc::KE);
+    const int KT = static_cast<int>(g.kp / (tc::KE * tc::KB));
     const int per_tile = (S * (S + 1) / 2) * KT;
     const int ntiles = g.tiles_m * g.tiles_n;
     auto fail = [&](int code) {
@@ -971,8 +974,12 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                     if (!mbar_wait(&empty[st], ph ^ 1u, abortp)) { fail(1); ok = false; break; }
                     uint8_t* sa = stage0 + st * Cf::STAGE_BYTES;
                     mbar_expect_tx(&full[st], Cf::STAGE_BYTES);
-                    tma_load_3d(sa, &tmA, c.kt * tc::KE, m0, c.s - 1, &full[st]);
-                    tma_load_3d(sa + tc::A_BYTES, &tmB, c.kt * tc::KE, n0, c.w - c.s - 1, &full[st]);
+#pragma unroll
+                    for (int q = 0; q < tc::KB; ++q) {
+                        const int x = (c.kt * tc::KB + q) * tc::KE;
+                        tma_load_3d(sa + q * tc::A_BYTES, &tmA, x, m0, c.s - 1, &full[st]);
+                        tma_load_3d(sa + tc::KB * tc::A_BYTES + q * Cf::B_BYTES, &tmB, x, n0, c.w - c.s - 1, &full[st]);
+                    }
                     c.advance(S, KT);
                 }
             }
@@ -992,10 +999,10 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             bool ok = true;
             for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
                 Cursor c{S + 1, 1, 0};
-                int seg_tiles = 0;
+                int seg_stages = 0;
                 uint32_t b = 0;
                 for (int i = 0; i < per_tile; ++i, ++it) {
-                    if (seg_tiles == 0) {
+                    if (seg_stages == 0) {
                         b = seg & 1u;
                         if (!mbar_wait(&acce[b], ((seg >> 1) & 1u) ^ 1u, abortp)) { fail(2); ok = false; break; }
                     }
@@ -1007,19 +1014,23 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                         pend = -1;
                     }
                     const uint32_t sa = smem_u32(stage0 + st * Cf::STAGE_BYTES);
-                    const uint64_t da = umma_desc(sa), db = umma_desc(sa + tc::A_BYTES);
 #pragma unroll
-                    for (int kk = 0; kk < tc::KE / 16; ++kk)
-                        umma(tmem + b * Cf::ACC_COLS, da + 2ull * kk, db + 2ull * kk, Cf::IDESC,
-                             (seg_tiles > 0 || kk > 0) ? 1u : 0u);
+                    for (int q = 0; q < tc::KB; ++q) {
+                        const uint64_t da = umma_desc(sa + q * tc::A_BYTES);
+                        const uint64_t db = umma_desc(sa + tc::KB * tc::A_BYTES + q * Cf::B_BYTES);
+#pragma unroll
+                        for (int kk = 0; kk < tc::KE / 16; ++kk)
+                            umma(tmem + b * Cf::ACC_COLS, da + 2ull * kk, db + 2ull * kk, Cf::IDESC,
+                                 (seg_stages > 0 || q > 0 || kk > 0) ? 1u : 0u);
+                    }
                     umma_commit(&empty[st]);
-                    ++seg_tiles;
+                    ++seg_stages;
                     const int w = c.w;
                     c.advance(S, KT);
-                    if (c.w != w || seg_tiles == tc::SEG_TILES) {
+                    if (c.w != w || seg_stages == tc::SEG_STAGES) {
                         pend = static_cast<int>(b);
                         ++seg;
-                        seg_tiles = 0;
+                        seg_stages = 0;
                     }
                 }
             }
@@ -1053,15 +1064,15 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             for (int c0 = 0; c0 < GW * BN; c0 += 32) tmem_st32(grp + c0, zero32);
             tmem_wait_st();
             Cursor c{S + 1, 1, 0};
-            int seg_tiles = 0;
+            int seg_stages = 0;
             bool first_group = true;
             for (int i = 0; i < per_tile; ++i) {
-                ++seg_tiles;
+                ++seg_stages;
                 const int w = c.w;
                 c.advance(S, KT);
                 const bool weight_end = c.w != w;
-                if (!weight_end && seg_tiles != tc::SEG_TILES) continue;
-                seg_tiles = 0;
+                if (!weight_end && seg_stages != tc::SEG_STAGES) continue;
+                seg_stages = 0;
                 const uint32_t b = seg & 1u;
                 // the decision must be warp-uniform: the TMEM loads below are .sync.aligned
                 if (!__all_sync(0xffffffffu, mbar_wait(&accf[b], (seg >> 1) & 1u, abortp))) {
@@ -1109,9 +1120,15 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                         split_exact(group_load<G, GW>(gw + GW * t), sg + s_tau[c0 / GW + t] - 7 * wmax, y[0], y[1]);
 #pragma unroll
                         for (int cc = 2; cc < P; ++cc) y[cc] = f.zero;
+                        if (first_group) {
+                            // TDaddq / QDadd of zero and an exact split (no
+                            // negative zero) is the split itself
 #pragma unroll
-                        for (int cc = 0; cc < P; ++cc)
-                            acc[cc] = first_group ? 0.0 : g.C[cc][row * g.ldc + col];
+                            for (int cc = 0; cc < P; ++cc) g.C[cc][row * g.ldc + col] = y[cc];
+                            continue;
+                        }
+#pragma unroll
+                        for (int cc = 0; cc < P; ++cc) acc[cc] = g.C[cc][row * g.ldc + col];
                         mp::Ops<P>::add(f, acc, y, zz);
 #pragma unroll
                         for (int cc = 0; cc < P; ++cc) g.C[cc][row * g.ldc + col] = zz[cc];

@@ -181,10 +181,13 @@ def test_split_exact():
     assert OZ.split_exact(2 ** 53 + 3) == (2.0 ** 53 + 4, -1.0)   # tie -> even (up)
 
 
-def test_dd_first_group_add_is_the_identity():
-    """DDadd (Alg. 1) of (0, 0) and an exact split (hi 2^e, lo 2^e) returns the
-    split bit for bit: the DD kernels store the first group of a tile without
-    the addition, and this is why that changes no result."""
+@pytest.mark.parametrize("prec", ["dd", "td", "qd"])
+def test_first_group_add_is_the_identity(prec):
+    """DDadd (Alg. 1), TDaddq (Sec. 2.3) and QDadd (Alg. 5) of zero and an exact
+    split (hi 2^e, lo 2^e, 0, ...) return the split bit for bit: the tcgen05
+    kernels store the first group of a tile without the addition, and this is
+    why that changes no result."""
+    P = {"dd": 2, "td": 3, "qd": 4}[prec]
     rng = np.random.default_rng(77)
     Vs = [0, 1, -1, 2 ** 53 + 1, 2 ** 53 + 3, -(2 ** 54) - 2, 2 ** 59 - 1, -(2 ** 59) + 1, 2 ** 52, 2 ** 53 - 1]
     Vs += [int(v) for v in rng.integers(-(2 ** 62), 2 ** 62, 4000)]
@@ -194,8 +197,8 @@ def test_dd_first_group_add_is_the_identity():
     for V in Vs:
         hi, lo = OZ.split_exact(V)
         for e in (-300, -60, 0, 17):
-            y = (math.ldexp(hi, e), math.ldexp(lo, e))
-            got = oracle.op("dd", "add", (0.0, 0.0), y)
+            y = (math.ldexp(hi, e), math.ldexp(lo, e)) + (0.0,) * (P - 2)
+            got = oracle.op(prec, "add", (0.0,) * P, y)
             assert [math.copysign(1, g) for g in got] == [math.copysign(1, v) for v in y] and got == y, (V, e, got, y)
 
 
