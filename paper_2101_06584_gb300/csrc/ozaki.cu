@@ -827,12 +827,29 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, unsigned parity)
         : "memory");
     return ok != 0;
 }
+// try_wait with a suspend-time hint in ns.  Measured on GB300 in the MMA
+// thread: any hint, against none, frees about 100 cycles per stage.
+template <unsigned HINT>
+__device__ __forceinline__ bool mbar_try_hint(uint64_t* b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity), "r"(HINT)
+        : "memory");
+    return ok != 0;
+}
+constexpr unsigned kHintIssue = 20;        // waits of the MMA-issuing thread
+constexpr unsigned kHintIdle = 10000;      // waits of the producer and the epilogue
 // Bounded wait: false after about a second, or once another role aborted.
+template <unsigned HINT>
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, volatile int* abort_flag)
 {
-    if (mbar_try(b, parity)) return true;      // the common case reads no clock
+    if (mbar_try_hint<HINT>(b, parity)) return true;      // the common case reads no clock
     const unsigned long long t0 = gtimer();
-    while (!mbar_try(b, parity)) {
+    while (!mbar_try_hint<HINT>(b, parity)) {
         if (*abort_flag) return false;
         if (gtimer() - t0 > tc::TIMEOUT_NS) return false;
     }
@@ -971,7 +988,7 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 Cursor c{S + 1, 1, 0};
                 for (int i = 0; i < per_tile; ++i, ++it) {
                     const uint32_t st = it % tc::STAGES, ph = (it / tc::STAGES) & 1u;
-                    if (!mbar_wait(&empty[st], ph ^ 1u, abortp)) { fail(1); ok = false; break; }
+                    if (!mbar_wait<kHintIdle>(&empty[st], ph ^ 1u, abortp)) { fail(1); ok = false; break; }
                     uint8_t* sa = stage0 + st * Cf::STAGE_BYTES;
                     mbar_expect_tx(&full[st], Cf::STAGE_BYTES);
 #pragma unroll
@@ -1004,10 +1021,10 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 for (int i = 0; i < per_tile; ++i, ++it) {
                     if (seg_stages == 0) {
                         b = seg & 1u;
-                        if (!mbar_wait(&acce[b], ((seg >> 1) & 1u) ^ 1u, abortp)) { fail(2); ok = false; break; }
+                        if (!mbar_wait<kHintIssue>(&acce[b], ((seg >> 1) & 1u) ^ 1u, abortp)) { fail(2); ok = false; break; }
                     }
                     const uint32_t st = it % tc::STAGES, ph = (it / tc::STAGES) & 1u;
-                    if (!mbar_wait(&full[st], ph, abortp)) { fail(3); ok = false; break; }
+                    if (!mbar_wait<kHintIssue>(&full[st], ph, abortp)) { fail(3); ok = false; break; }
                     tc_fence_after();
                     if (pend >= 0) {
                         umma_commit(&accf[pend]);
@@ -1075,7 +1092,7 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 seg_stages = 0;
                 const uint32_t b = seg & 1u;
                 // the decision must be warp-uniform: the TMEM loads below are .sync.aligned
-                if (!__all_sync(0xffffffffu, mbar_wait(&accf[b], (seg >> 1) & 1u, abortp))) {
+                if (!__all_sync(0xffffffffu, mbar_wait<kHintIdle>(&accf[b], (seg >> 1) & 1u, abortp))) {
                     fail(4);
                     ok = false;
                     break;
@@ -1230,11 +1247,24 @@ __device__ __forceinline__ bool mbar_try_cl(uint64_t* b, unsigned parity)
         : "memory");
     return ok != 0;
 }
+template <unsigned HINT>
+__device__ __forceinline__ bool mbar_try_cl_hint(uint64_t* b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity), "r"(HINT)
+        : "memory");
+    return ok != 0;
+}
+template <unsigned HINT>
 __device__ __forceinline__ bool mbar_wait_cl(uint64_t* b, unsigned parity, volatile int* abort_flag)
 {
-    if (mbar_try_cl(b, parity)) return true;
+    if (mbar_try_cl_hint<HINT>(b, parity)) return true;
     const unsigned long long t0 = gtimer();
-    while (!mbar_try_cl(b, parity)) {
+    while (!mbar_try_cl_hint<HINT>(b, parity)) {
         if (*abort_flag) return false;
         if (gtimer() - t0 > tc::TIMEOUT_NS) return false;
     }
@@ -1347,7 +1377,7 @@ ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                 Cursor c{S + 1, 1, 0};
                 for (int i = 0; i < per_tile; ++i, ++it) {
                     const uint32_t st = it % tc2::STAGES, ph = (it / tc2::STAGES) & 1u;
-                    if (!mbar_wait_cl(&empty[st], ph ^ 1u, abortp)) { fail(1); ok = false; break; }
+                    if (!mbar_wait_cl<kHintIdle>(&empty[st], ph ^ 1u, abortp)) { fail(1); ok = false; break; }
                     uint8_t* sa = stage0 + st * tc2::STAGE_BYTES;
                     const uint32_t bar = cluster_addr(&full[st], 0);
                     if (rank == 0) mbar_expect_tx(&full[st], 2 * tc2::STAGE_BYTES);
@@ -1383,10 +1413,10 @@ ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                 for (int i = 0; i < per_tile; ++i, ++it) {
                     if (seg_stages == 0) {
                         b = seg & 1u;
-                        if (!mbar_wait_cl(&acce[b], ((seg >> 1) & 1u) ^ 1u, abortp)) { fail(2); ok = false; break; }
+                        if (!mbar_wait_cl<kHintIssue>(&acce[b], ((seg >> 1) & 1u) ^ 1u, abortp)) { fail(2); ok = false; break; }
                     }
                     const uint32_t st = it % tc2::STAGES, ph = (it / tc2::STAGES) & 1u;
-                    if (!mbar_wait_cl(&full[st], ph, abortp)) { fail(3); ok = false; break; }
+                    if (!mbar_wait_cl<kHintIssue>(&full[st], ph, abortp)) { fail(3); ok = false; break; }
                     tc_fence_after();
                     if (pend >= 0) {
                         umma_commit_both(&accf[pend]);
@@ -1456,7 +1486,7 @@ ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                 seg_stages = 0;
                 const uint32_t b = seg & 1u;
                 // the decision must be warp-uniform: the TMEM loads below are .sync.aligned
-                if (!__all_sync(0xffffffffu, mbar_wait_cl(&accf[b], (seg >> 1) & 1u, abortp))) {
+                if (!__all_sync(0xffffffffu, mbar_wait_cl<kHintIdle>(&accf[b], (seg >> 1) & 1u, abortp))) {
                     fail(4);
                     ok = false;
                     break;
