@@ -106,7 +106,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="td_qd",
                     choices=["td_qd", "dd_small", "dd_int8", "dd_tc", "td_qd_int8", "td_qd_tc",
-                             "batched", "autograd"])
+                             "batched", "autograd", "elementwise"])
     ap.add_argument("--size", type=int, default=None, help="override the workload's m = n = k")
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
@@ -482,6 +482,56 @@ class TdQdTc(TdQdInt8):
         super().__init__(torch, mm, I, rank, n=n, engine="tc")
 
 
+class Elementwise(Workload):
+    """The paper's elementwise benchmarks (Sec. 4, Figs. 2-4): DDadd/DDmul,
+    TDaddq, merge TDadd (Alg. 3), TDmul, QDadd/QDmul over SoA vectors of n
+    elements, every op on its own buffers (inputs far larger than L2)."""
+    name = "elementwise"
+    # (precision, op, FP64 operations per element of the implemented sequence)
+    OPS = (("dd", "add", 11), ("dd", "mul", 9), ("td", "add", 81), ("td", "addm", 45), ("td", "mul", 47),
+           ("qd", "add", 87), ("qd", "mul", 123))
+
+    def __init__(self, torch, mm, I, rank, n=1 << 24):
+        self.torch, self.mm, self.n = torch, mm, n
+        rng = replica_rng(0, rank)
+        self.dev = {}
+        for prec in ("dd", "td", "qd"):
+            P = I.P_OF[prec]
+            x, y = I.random_mp(P, n, rng), I.random_mp(P, n, rng)
+            self.dev[prec] = (torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(),
+                              torch.empty((P, n), dtype=torch.float64, device="cuda"))
+        self.mads = len(self.OPS) * n          # elements processed per step
+        self.launches_per_step = len(self.OPS)
+        self.config = {"workload": "elementwise DD/TD/QD add and mul, n=%d elements per op" % n, "n": n}
+
+    def timed_step(self, stream):
+        evs = {}
+        for prec, op, _ in self.OPS:
+            x, y, r = self.dev[prec]
+            e0, e1 = self.torch.cuda.Event(enable_timing=True), self.torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            self.mm.vec(prec, op, x, y, out=r)
+            e1.record(stream)
+            evs[prec + "_" + op] = (e0, e1)
+        return evs
+
+    def roofline(self, launch_ms, pk):
+        per_op = {}
+        for prec, op, ops in self.OPS:
+            P = {"dd": 2, "td": 3, "qd": 4}[prec]
+            ms = statistics.mean(launch_ms[prec + "_" + op])
+            el_s = self.n / (ms * 1e-3)
+            per_op[prec + "_" + op] = {"elements_s": el_s, "fp64_ops_per_element": ops,
+                                       "frac_fp64": el_s * ops / pk["dfma"],
+                                       "hbm_gb_s": el_s * 3 * P * 8 / 1e9}
+        # the slowest op in FP64 throughput
+        worst = min(per_op.items(), key=lambda kv: kv[1]["frac_fp64"])
+        return {"bound": "alu", "kernel": "elementwise ops (one launch each)", "unit": "TFP64op/s",
+                "achieved": worst[1]["elements_s"] * worst[1]["fp64_ops_per_element"] / 1e12,
+                "peak": pk["dfma"] / 1e12, "frac": worst[1]["frac_fp64"], "frac_of": worst[0],
+                "traffic": None, "per_op": per_op}
+
+
 class Batched(Workload):
     name = "batched"
 
@@ -566,7 +616,8 @@ class Autograd(Workload):
 
 
 WORKLOADS = {"td_qd": TdQd, "dd_small": DdSmall, "dd_int8": DdInt8, "dd_tc": DdTc,
-             "td_qd_int8": TdQdInt8, "td_qd_tc": TdQdTc, "batched": Batched, "autograd": Autograd}
+             "td_qd_int8": TdQdInt8, "td_qd_tc": TdQdTc, "batched": Batched, "autograd": Autograd,
+             "elementwise": Elementwise}
 
 
 def _time_call(torch, fn, reps=1):
@@ -670,11 +721,12 @@ def run_ours(args):
 def extras(torch, mm, I, pk, flush):
     """One short measurement of each other workload (rank 0, after the main one)."""
     out = {}
-    for name in ("dd_small", "dd_int8", "dd_tc", "td_qd_int8", "td_qd_tc", "batched", "autograd"):
+    for name in ("dd_small", "dd_int8", "dd_tc", "td_qd_int8", "td_qd_tc", "batched", "autograd", "elementwise"):
         w = WORKLOADS[name](torch, mm, I, 0)
-        steps = 2 if name != "dd_small" else 10
+        steps = 2 if name not in ("dd_small", "elementwise") else 10
         total_ms, launch_ms, _, _ = measure(torch, w, steps, 1, 1, 0, flush, sample_clocks=False)
-        out[name] = {"config": w.config, "mad_s": w.mads * steps / (total_ms * 1e-3),
+        rate_key = "elements_s" if name == "elementwise" else "mad_s"
+        out[name] = {"config": w.config, rate_key: w.mads * steps / (total_ms * 1e-3),
                      "ms_per_step": total_ms / steps, "roofline": w.roofline(launch_ms, pk)}
         del w
         torch.cuda.empty_cache()
