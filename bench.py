@@ -106,7 +106,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="td_qd",
                     choices=["td_qd", "dd_small", "dd_int8", "dd_tc", "td_qd_int8", "td_qd_tc",
-                             "batched", "autograd", "elementwise"])
+                             "batched", "autograd", "elementwise", "strassen"])
     ap.add_argument("--size", type=int, default=None, help="override the workload's m = n = k")
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
@@ -532,6 +532,67 @@ class Elementwise(Workload):
                 "traffic": None, "per_op": per_op}
 
 
+class Strassen(Workload):
+    """The Strassen form (Sec. 3) beside the block algorithm: DD 4096^3 (the
+    slicing forms' inputs) and QD 1024^3 (the main workload's inputs), one and
+    two levels over the k-sequential kernel."""
+    name = "strassen"
+    CASES = (("dd", 1), ("dd", 2), ("qd", 1), ("qd", 2))
+
+    def __init__(self, torch, mm, I, rank, n_dd=4096, n_qd=1024):
+        self.torch, self.mm = torch, mm
+        self.n = {"dd": n_dd, "qd": n_qd}
+        self.dev, self.ws = {}, {}
+        rng = replica_rng(2, rank)
+        A, B = I.uniform(2, (n_dd, n_dd), rng), I.uniform(2, (n_dd, n_dd), rng)
+        self.dev["dd"] = (torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(),
+                          torch.empty((2, n_dd, n_dd), dtype=torch.float64, device="cuda"))
+        A, B = I.cancelling_pair(4, n_qd, n_qd, n_qd, replica_rng(1, rank))
+        self.dev["qd"] = (torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(),
+                          torch.empty((4, n_qd, n_qd), dtype=torch.float64, device="cuda"))
+        for prec, L in self.CASES:
+            n = self.n[prec]
+            self.ws[(prec, L)] = torch.empty(mm.workspace_size(prec, n, n, n, strassen=L), dtype=torch.uint8,
+                                             device="cuda")
+        self.mads = sum(self.n[p] ** 3 for p, _ in self.CASES)
+        # per level: 18 block additions and 7 products, recursively; the leaves are one launch each
+        self.launches_per_step = sum(18 * (7 ** L - 1) // 6 + 7 ** L for _, L in self.CASES)
+        self.config = {"workload": "Strassen form: DD m=n=k=%d and QD m=n=k=%d, 1 and 2 levels" % (n_dd, n_qd),
+                       "cases": ["%s L=%d" % c for c in self.CASES]}
+
+    def timed_step(self, stream):
+        evs = {}
+        for prec, L in self.CASES:
+            A, B, C = self.dev[prec]
+            e0, e1 = self.torch.cuda.Event(enable_timing=True), self.torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            self.mm.gemm(prec, A, B, out=C, strassen=L, workspace=self.ws[(prec, L)])
+            e1.record(stream)
+            evs["%s_L%d" % (prec, L)] = (e0, e1)
+        return evs
+
+    def roofline(self, launch_ms, pk):
+        ops = {"dd": FP64_OPS_PER_MAD["dd"], "qd": FP64_OPS_PER_MAD["qd"]}
+        plain = {}
+        for prec in ("dd", "qd"):
+            A, B, C = self.dev[prec]
+            plain[prec] = _time_call(self.torch, lambda: self.mm.gemm_plain(prec, A, B, out=C), 1)
+        cases = {}
+        for prec, L in self.CASES:
+            n = self.n[prec]
+            ms = statistics.mean(launch_ms["%s_L%d" % (prec, L)])
+            # FP64 work actually done: 7^L leaf products of (n/2^L)^3 mads
+            leaf_mads = 7 ** L * (n // 2 ** L) ** 3
+            cases["%s_L%d" % (prec, L)] = {"ms": ms, "nominal_mad_s": n ** 3 / (ms * 1e-3),
+                                           "speedup_vs_block": plain[prec] / ms,
+                                           "frac_fp64_of_leaf_work": leaf_mads * ops[prec] / (ms * 1e-3) / pk["dfma"]}
+        worst = min(cases.items(), key=lambda kv: kv[1]["frac_fp64_of_leaf_work"])
+        return {"bound": "alu", "kernel": "gemm_kseq_kernel leaves + mat_addsub_kernel", "unit": "TFP64op/s",
+                "achieved": worst[1]["frac_fp64_of_leaf_work"] * pk["dfma"] / 1e12, "peak": pk["dfma"] / 1e12,
+                "frac": worst[1]["frac_fp64_of_leaf_work"], "frac_of": worst[0], "traffic": None,
+                "block_ms": plain, "cases": cases}
+
+
 class Batched(Workload):
     name = "batched"
 
@@ -617,7 +678,7 @@ class Autograd(Workload):
 
 WORKLOADS = {"td_qd": TdQd, "dd_small": DdSmall, "dd_int8": DdInt8, "dd_tc": DdTc,
              "td_qd_int8": TdQdInt8, "td_qd_tc": TdQdTc, "batched": Batched, "autograd": Autograd,
-             "elementwise": Elementwise}
+             "elementwise": Elementwise, "strassen": Strassen}
 
 
 def _time_call(torch, fn, reps=1):
@@ -721,9 +782,10 @@ def run_ours(args):
 def extras(torch, mm, I, pk, flush):
     """One short measurement of each other workload (rank 0, after the main one)."""
     out = {}
-    for name in ("dd_small", "dd_int8", "dd_tc", "td_qd_int8", "td_qd_tc", "batched", "autograd", "elementwise"):
+    for name in ("dd_small", "dd_int8", "dd_tc", "td_qd_int8", "td_qd_tc", "batched", "autograd", "elementwise",
+                 "strassen"):
         w = WORKLOADS[name](torch, mm, I, 0)
-        steps = 2 if name not in ("dd_small", "elementwise") else 10
+        steps = {"dd_small": 10, "elementwise": 10, "strassen": 1}.get(name, 2)
         total_ms, launch_ms, _, _ = measure(torch, w, steps, 1, 1, 0, flush, sample_clocks=False)
         rate_key = "elements_s" if name == "elementwise" else "mad_s"
         out[name] = {"config": w.config, rate_key: w.mads * steps / (total_ms * 1e-3),

@@ -140,6 +140,8 @@ typedef struct mpgemm_opts {
                        INT8_OZAKI: slice-product tiling 1..3; 0 or -1 = library choice */
     void *workspace;          /* device scratch for algorithms that need it */
     size_t workspace_bytes;
+    int strassen;   /* FP64_EFT / AUTO: levels of Strassen's algorithm (0..8, 0 = none;
+                       untransposed operands, split_k 0 or 1): see below */
 } mpgemm_opts;
 
 /* C := op(A) op(B) with the options above; P in {2, 3, 4}; lda/ldb must
@@ -190,6 +192,24 @@ int mpgemm_ex(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k,
  * the code of the waiting role there), then the digits as bf16 with rows
  * padded to 128 ([S][mp][kp] for op(A)) and to N ([S][np][kp] for op(B)^T), then the
  * int32 exponents; mpgemm_workspace_size gives the total. */
+
+/* The Strassen form (Sec. 3: the paper's divide-and-conquer alternative to
+ * the block algorithm).  With opts->strassen = L > 0, C := A B is computed
+ * from Strassen's seven products of half-size blocks,
+ *   M1 = (A11 + A22)(B11 + B22)   M2 = (A21 + A22) B11   M3 = A11 (B12 - B22)
+ *   M4 = A22 (B21 - B11)          M5 = (A11 + A12) B22   M6 = (A21 - A11)(B11 + B12)
+ *   M7 = (A12 - A22)(B21 + B22)
+ *   C11 = ((M1 + M4) - M5) + M7   C12 = M3 + M5   C21 = M2 + M4
+ *   C22 = ((M1 - M2) + M3) + M6,
+ * applied L times while m, n and k are even (an odd or zero dimension ends the
+ * recursion); the leaf products are the k-sequential GEMM of mpgemm_dd/td/qd.
+ * "+" is the precision's addition (DDadd Alg. 1, TDaddq Sec. 2.3, QDadd
+ * Alg. 5) elementwise, x - y is x + (-y) with every component of y negated,
+ * and each sum is evaluated left to right.  The result is deterministic and
+ * bit-identical to those steps evaluated anywhere; it is not bit-identical to
+ * the block algorithm, and its error bound grows with L.  Workspace:
+ * mpgemm_workspace_size bytes (256-byte aligned, not overlapping A, B or C):
+ * per level P (m/2 k/2 + k/2 n/2 + 7 m/2 n/2) binary64 values. */
 
 /* Bytes of workspace mpgemm_ex needs for these options and sizes (0 if none). */
 size_t mpgemm_workspace_size(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k);

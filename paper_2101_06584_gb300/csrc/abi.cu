@@ -163,6 +163,8 @@ template int check_gemm<2>(const GemmArgs<2>&);
 template int check_gemm<3>(const GemmArgs<3>&);
 template int check_gemm<4>(const GemmArgs<4>&);
 
+constexpr int kMaxStrassenLevels = 8;
+
 // Slice-count limits and defaults per precision.
 static int ozaki_max_slices(int P) { return P == 2 ? kOzakiMaxSlices : kOzakiMaxSlicesWide; }
 static int ozaki_default_slices(int P) { return P == 2 ? kOzakiDefaultSlices : P == 3 ? 22 : 29; }
@@ -230,8 +232,37 @@ static int gemm_call(const mpgemm_opts* o, int64_t m, int64_t n, int64_t k,
         e = launch_zero<P>(g, g_stream);
         return e == cudaSuccess ? MPG_OK : cuda_fail(e, "zero launch");
     }
-    if (sliced) return ozaki_call(g, o);
+    if (sliced) {
+        if (o->strassen) return fail(MPG_EINVAL, "strassen applies to the FP64-EFT algorithm only");
+        return ozaki_call(g, o);
+    }
     const int split = o ? o->split_k : 0;
+    const int levels = o ? o->strassen : 0;
+    if (levels < 0 || levels > kMaxStrassenLevels)
+        return fail(MPG_EINVAL, "strassen must be in 0..%d (got %d)", kMaxStrassenLevels, levels);
+    if (levels > 0) {
+        if (g.trans_a || g.trans_b) return fail(MPG_EUNSUPPORTED, "the Strassen form takes untransposed operands");
+        if (split > 1) return fail(MPG_EINVAL, "split_k and strassen cannot be combined");
+        const int64_t bytes = strassen_workspace_elems(P, m, n, k, levels) * 8;
+        if (bytes > 0) {
+            if (!o->workspace) return fail(MPG_EWORKSPACE, "the Strassen form needs a workspace of %lld bytes",
+                                           (long long)bytes);
+            if (reinterpret_cast<uintptr_t>(o->workspace) % 256)
+                return fail(MPG_EWORKSPACE, "workspace must be 256-byte aligned");
+            if (o->workspace_bytes < static_cast<size_t>(bytes))
+                return fail(MPG_EWORKSPACE, "workspace of %zu bytes is smaller than the %lld needed",
+                            o->workspace_bytes, (long long)bytes);
+            const Range rw{reinterpret_cast<uintptr_t>(o->workspace),
+                           reinterpret_cast<uintptr_t>(o->workspace) + static_cast<uintptr_t>(bytes)};
+            for (int c = 0; c < P; ++c) {
+                if (overlap(rw, plane_range(g.A[c], m, k, g.lda)) || overlap(rw, plane_range(g.B[c], k, n, g.ldb)) ||
+                    overlap(rw, plane_range(g.C[c], m, n, g.ldc)))
+                    return fail(MPG_EWORKSPACE, "workspace overlaps an operand");
+            }
+        }
+        e = launch_strassen<P>(g, levels, static_cast<double*>(o->workspace), g_stream);
+        return e == cudaSuccess ? MPG_OK : cuda_fail(e, "strassen launch");
+    }
     if (split > 1) {
         if (split != 2 && split != 4 && split != 8 && split != 16 && split != 32)
             return fail(MPG_EINVAL, "split_k must be 0, 1, 2, 4, 8, 16 or 32 (got %d)", split);
@@ -314,9 +345,11 @@ int mpgemm_ex(int P, const mpgemm_opts* opts, int64_t m, int64_t n, int64_t k,
 
 size_t mpgemm_workspace_size(int P, const mpgemm_opts* opts, int64_t m, int64_t n, int64_t k)
 {
-    if (!opts || (opts->algo != MPG_ALGO_INT8_OZAKI && opts->algo != MPG_ALGO_BF16_SLICES) || P < 2 ||
-        P > 4 || m < 0 || n < 0 || k < 0)
-        return 0;
+    if (!opts || P < 2 || P > 4 || m < 0 || n < 0 || k < 0) return 0;
+    if ((opts->algo == MPG_ALGO_AUTO || opts->algo == MPG_ALGO_FP64_EFT) && opts->strassen > 0 &&
+        opts->strassen <= kMaxStrassenLevels)
+        return static_cast<size_t>(strassen_workspace_elems(P, m, n, k, opts->strassen) * 8);
+    if (opts->algo != MPG_ALGO_INT8_OZAKI && opts->algo != MPG_ALGO_BF16_SLICES) return 0;
     const int S = opts->slices ? opts->slices : ozaki_default_slices(P);
     if (S < 1 || S > ozaki_max_slices(P)) return 0;
     if (opts->algo == MPG_ALGO_BF16_SLICES) return static_cast<size_t>(ozaki_tc_layout(P, S, m, n, k).total);

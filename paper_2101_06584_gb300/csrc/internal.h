@@ -41,6 +41,12 @@ cudaError_t launch_gemm_splitk(const GemmArgs<P>& g, int split, cudaStream_t s);
 template <int P>
 int check_gemm(const GemmArgs<P>& g);
 
+// Strassen form: `levels` levels of Strassen's seven products over the
+// k-sequential kernel (untransposed operands); workspace in doubles.
+int64_t strassen_workspace_elems(int P, int64_t m, int64_t n, int64_t k, int levels);
+template <int P>
+cudaError_t launch_strassen(const GemmArgs<P>& g, int levels, double* ws, cudaStream_t s);
+
 // C := 0 (all planes), for k == 0.
 template <int P>
 cudaError_t launch_zero(const GemmArgs<P>& g, cudaStream_t s);

@@ -29,7 +29,8 @@ class MPGError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("trans_a", ctypes.c_int), ("trans_b", ctypes.c_int), ("algo", ctypes.c_int),
                 ("split_k", ctypes.c_int), ("slices", ctypes.c_int), ("tile", ctypes.c_int),
-                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
+                ("strassen", ctypes.c_int)]
 
 
 class Problem(ctypes.Structure):
@@ -118,7 +119,7 @@ def _ld(t):
 
 
 def gemm(prec, A, B, out=None, trans_a=False, trans_b=False, algo="auto", split_k=0, tile=0,
-         slices=0, workspace=None):
+         slices=0, workspace=None, strassen=0):
     """C = op(A) op(B) for (P, rows, cols) planes; op = transpose when trans_*.
 
     A is (P, m, k) or, with trans_a, (P, k, m); B is (P, k, n) or, with
@@ -136,7 +137,7 @@ def gemm(prec, A, B, out=None, trans_a=False, trans_b=False, algo="auto", split_
     if tuple(out.shape[1:]) != (m, n):
         raise ValueError("out must be (P, %d, %d)" % (m, n))
     o = Opts(int(trans_a), int(trans_b), ALGO[algo], int(split_k), int(slices), int(tile),
-             None, 0)
+             None, 0, int(strassen))
     if workspace is not None:
         _require_ws(workspace)
         o.workspace = workspace.data_ptr()
@@ -152,8 +153,9 @@ def _require_ws(w):
         raise ValueError("workspace must be a contiguous CUDA tensor")
 
 
-def workspace_size(prec, m, n, k, algo="auto", slices=0, split_k=0, trans_a=False, trans_b=False):
-    o = Opts(int(trans_a), int(trans_b), ALGO[algo], int(split_k), int(slices), 0, None, 0)
+def workspace_size(prec, m, n, k, algo="auto", slices=0, split_k=0, trans_a=False, trans_b=False,
+                   strassen=0):
+    o = Opts(int(trans_a), int(trans_b), ALGO[algo], int(split_k), int(slices), 0, None, 0, int(strassen))
     return int(lib().mpgemm_workspace_size(P_OF[prec], ctypes.byref(o), m, n, k))
 
 

@@ -114,6 +114,36 @@ def test_ex_rejects_bad_options(L):
     assert "lda" in err(L)
 
 
+def test_strassen_options(L):
+    """Workspace of the Strassen form and the argument errors it reports
+    before any launch."""
+    from paper_2101_06584_gb300.mpgemm import Opts
+    size = L.mpgemm_workspace_size
+    size.restype = ctypes.c_size_t
+    o = Opts(0, 0, 0, 0, 0, 0, None, 0, 1)
+    # one level: P (m/2 k/2 + k/2 n/2 + 7 m/2 n/2) doubles
+    assert size(2, ctypes.byref(o), 8, 6, 4) == 2 * (4 * 2 + 2 * 3 + 7 * 4 * 3) * 8
+    o = Opts(0, 0, 0, 0, 0, 0, None, 0, 2)
+    # two levels: the outer level's blocks plus the inner level's, once
+    assert size(4, ctypes.byref(o), 8, 8, 8) == 4 * ((16 + 16 + 7 * 16) + (4 + 4 + 7 * 4)) * 8
+    assert size(2, ctypes.byref(o), 7, 8, 8) == 0              # odd m: the plain GEMM
+    o = Opts(0, 0, 0, 0, 0, 0, None, 0, 0)
+    assert size(2, ctypes.byref(o), 8, 8, 8) == 0
+    A, B, C = planes(FAKE, 2), planes(2 * FAKE, 2), planes(3 * FAKE, 2)
+    o = Opts(0, 0, 0, 0, 0, 0, None, 0, -1)
+    assert L.mpgemm_ex(2, ctypes.byref(o), 8, 8, 8, A, 8, B, 8, C, 8) == -1
+    assert "strassen" in err(L)
+    o = Opts(1, 0, 0, 0, 0, 0, None, 0, 1)
+    assert L.mpgemm_ex(2, ctypes.byref(o), 8, 8, 8, A, 8, B, 8, C, 8) == -4
+    o = Opts(0, 0, 0, 2, 0, 0, None, 0, 1)
+    assert L.mpgemm_ex(2, ctypes.byref(o), 8, 8, 8, A, 8, B, 8, C, 8) == -1
+    o = Opts(0, 0, 0, 0, 0, 0, None, 0, 1)
+    assert L.mpgemm_ex(2, ctypes.byref(o), 8, 8, 8, A, 8, B, 8, C, 8) == -3
+    assert "workspace" in err(L)
+    o = Opts(0, 0, 2, 0, 0, 0, None, 0, 1)                  # with a slicing form
+    assert L.mpgemm_ex(2, ctypes.byref(o), 8, 8, 8, A, 8, B, 8, C, 8) == -1
+
+
 def test_vector_validation(L):
     x, y, r = planes(FAKE, 2), planes(2 * FAKE, 2), planes(3 * FAKE, 2)
     assert L.mp_dd_add(-5, x, y, r) == -1
