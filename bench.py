@@ -455,7 +455,8 @@ class TdQdInt8(Workload):
         else:
             (peak, src), unit = bf16_peak(), "TFLOP/s"
         # FP64 work of the QD call: one QDadd (87 of the 210 operations of a QD
-        # multiply-add) per output per group of ten weights (S weights)
+        # multiply-add) per output per group of ten weights (S weights; the
+        # first group of a tile needs none on the tcgen05 engine)
         fp64_ops = (n * n) * (-(-S // 10)) * FP64_OPS_PER_MAD["qd"] * 87 // 210
         return {"bound": "tensor", "kernel": "QD slicing form (%s) incl. slicing" % self.engine,
                 "achieved": ach / 1e12, "peak": peak / 1e12, "unit": unit, "peak_source": src,

@@ -176,7 +176,8 @@ int mpgemm_ex(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k,
  * For TD and QD (P = 3, 4; S default 22 / 29, 1..40): each component is
  * first floored to a multiple of 2^(sigma - 7S - 12 - 64) and the digits are
  * those of the sum of the floored components (computed exactly in 384-bit
- * integers); the groups hold G = 10 weights (|V| < 2^95) and are added with
+ * integers); the groups hold G = 11 (TD, |V| < 2^102) or 10 (QD, |V| < 2^95)
+ * weights and are added with
  * TDaddq / QDadd (Sec. 2.3, Alg. 5) of (hi 2^e, lo 2^e, 0, ...).
  *
  * MPG_ALGO_BF16_SLICES (DD/TD/QD; not in the paper): the same digits, scales,

@@ -27,8 +27,9 @@ TD and QD (P = 3, 4) differ in two places:
            2^(sigma - F - 64), F = 7S + 12 (64 guard bits below the last
            digit's unit); the digits are those of the sum of the floored
            components, exactly as above.
-  accumulate  as for DD with groups of G = 10 (V below 2^95) and TDaddq
-           (Sec. 2.3) or QDadd (Alg. 5) of (hi 2^e, lo 2^e, 0, ...).
+  accumulate  as for DD with groups of G = 11 (TD; V below 2^102) or
+           G = 10 (QD; V below 2^95) and TDaddq (Sec. 2.3) or QDadd (Alg. 5)
+           of (hi 2^e, lo 2^e, 0, ...).
 """
 import math
 from fractions import Fraction
@@ -128,8 +129,9 @@ PREC_OF = {2: "dd", 3: "td", 4: "qd"}
 
 
 def group_size(P):
-    """Weights combined exactly per add: 5 for DD (64-bit sums), 10 for TD/QD (128-bit)."""
-    return 5 if P == 2 else 10
+    """Weights combined exactly per add: 5 for DD (64-bit sums), 11 for TD and
+    10 for QD (128-bit sums; 11 TD weights make the default 22 two groups)."""
+    return {2: 5, 3: 11, 4: 10}[P]
 
 
 def weight_groups(S, P):
@@ -169,7 +171,7 @@ def gemm(A, B, S, rows=None, cols=None, L=None):
             for grp in weight_groups(S, P):
                 wmax = grp[0]
                 V = sum(int(Pw[w][r, c]) << (BASE_BITS * (wmax - w)) for w in grp)
-                assert abs(V) < (2 ** 60 if P == 2 else 2 ** 95)
+                assert abs(V) < {2: 2 ** 60, 3: 2 ** 102, 4: 2 ** 95}[P]
                 hi, lo = split_exact(V)
                 e = sig[r] + tau[c] - BASE_BITS * wmax
                 vh, vl = math.ldexp(hi, e), math.ldexp(lo, e)

@@ -8,8 +8,9 @@ constexpr int kOzakiMaxSlices = 16;       // DD: 128-bit exact fixed point
 constexpr int kOzakiMaxSlicesWide = 40;   // TD, QD: 384-bit floored fixed point
 constexpr int kOzakiDefaultSlices = 14;
 // Weights combined exactly per add: DD 5 (sums below 2^60, 64-bit integers),
-// TD and QD 10 (below 2^95, 128-bit integers).
-constexpr int ozaki_group(int P) { return P == 2 ? 5 : 10; }
+// TD 11 (below 2^102) and QD 10 (below 2^95) in 128-bit integers.  Eleven TD
+// weights make the default 22 slices two groups.
+constexpr int ozaki_group(int P) { return P == 2 ? 5 : P == 3 ? 11 : 10; }
 
 // Workspace layout for S slices of an m x n x k product (byte offsets).
 struct OzakiLayout {
