@@ -106,7 +106,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="td_qd",
                     choices=["td_qd", "dd_small", "dd_int8", "dd_tc", "td_qd_int8", "td_qd_tc",
-                             "batched", "autograd", "elementwise", "strassen"])
+                             "batched", "autograd", "elementwise", "strassen", "autograd_tc"])
     ap.add_argument("--size", type=int, default=None, help="override the workload's m = n = k")
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
@@ -677,9 +677,33 @@ class Autograd(Workload):
                 "unit_of_work": "DD multiply-add", "units_per_launch": self.n ** 3}
 
 
+class AutogradTc(Autograd):
+    """DDMatmul forward + backward on the tcgen05 slicing form (default slices)."""
+    name = "autograd_tc"
+
+    def __init__(self, torch, mm, I, rank, n=2048):
+        super().__init__(torch, mm, I, rank, n=n)
+        from paper_2101_06584_gb300.autograd import dd_matmul
+        self.f = lambda A, B: dd_matmul(A, B, algo="bf16")
+        # per product: header clear, scale and slice of both operands, the product kernel
+        self.launches_per_step = 3 * 6
+        self.config = dict(self.config, workload=self.config["workload"] + ", tcgen05 slicing form", engine="tc")
+
+    def roofline(self, launch_ms, pk):
+        S = 14
+        pairs = S * (S + 1) // 2
+        ms = statistics.mean(launch_ms["fwd"])
+        ach = 2.0 * pairs * self.n ** 3 / (ms * 1e-3)
+        peak, src = bf16_peak()
+        return {"bound": "tensor", "kernel": "ozaki_tc_pair_kernel (forward call incl. slicing)",
+                "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": ach / peak,
+                "peak_source": src, "traffic": None, "ops_per_unit": 2 * pairs,
+                "unit_of_work": "DD multiply-add (%d slice-pair MACs)" % pairs, "units_per_launch": self.n ** 3}
+
+
 WORKLOADS = {"td_qd": TdQd, "dd_small": DdSmall, "dd_int8": DdInt8, "dd_tc": DdTc,
              "td_qd_int8": TdQdInt8, "td_qd_tc": TdQdTc, "batched": Batched, "autograd": Autograd,
-             "elementwise": Elementwise, "strassen": Strassen}
+             "elementwise": Elementwise, "strassen": Strassen, "autograd_tc": AutogradTc}
 
 
 def _time_call(torch, fn, reps=1):
@@ -783,8 +807,8 @@ def run_ours(args):
 def extras(torch, mm, I, pk, flush):
     """One short measurement of each other workload (rank 0, after the main one)."""
     out = {}
-    for name in ("dd_small", "dd_int8", "dd_tc", "td_qd_int8", "td_qd_tc", "batched", "autograd", "elementwise",
-                 "strassen"):
+    for name in ("dd_small", "dd_int8", "dd_tc", "td_qd_int8", "td_qd_tc", "batched", "autograd", "autograd_tc",
+                 "elementwise", "strassen"):
         w = WORKLOADS[name](torch, mm, I, 0)
         steps = {"dd_small": 10, "elementwise": 10, "strassen": 1}.get(name, 2)
         total_ms, launch_ms, _, _ = measure(torch, w, steps, 1, 1, 0, flush, sample_clocks=False)

@@ -8,20 +8,36 @@ operands (no transpose copies):
     dA = dC B^T   (mpgemm_ex with trans_b; mul(x = dC entry, y = B entry))
     dB = A^T dC   (mpgemm_ex with trans_a; mul(x = A entry, y = dC entry))
 
-Each is the k-sequential DD product of Sec. 3, Eq. 1, so the gradients are
-bit-identical to that product evaluated anywhere.  The incoming gradient is
-itself a DD plane pair: for loss = sum(W * C), call C.backward(W).
+By default each is the k-sequential DD product of Sec. 3, Eq. 1, so the
+gradients are bit-identical to that product evaluated anywhere.  With
+algo="bf16" (or "int8") the forward product and both gradients run the
+error-free slicing form on the tensor cores instead (the form defined in
+include/mpgemm.h): each is bit-identical to that form's steps on the same
+operands and within its DD error bound of the exact product.  The incoming
+gradient is itself a DD plane pair: for loss = sum(W * C), call C.backward(W).
 """
 import torch
 
 from . import mpgemm
 
 
+def _product(A, B, algo, slices, trans_a=False, trans_b=False):
+    if algo in ("auto", "fp64"):
+        return mpgemm.gemm("dd", A, B, trans_a=trans_a, trans_b=trans_b, algo=algo)
+    m = A.shape[2] if trans_a else A.shape[1]
+    k = A.shape[1] if trans_a else A.shape[2]
+    n = B.shape[1] if trans_b else B.shape[2]
+    ws = torch.empty(mpgemm.workspace_size("dd", m, n, k, algo=algo, slices=slices), dtype=torch.uint8,
+                     device=A.device)
+    return mpgemm.gemm("dd", A, B, trans_a=trans_a, trans_b=trans_b, algo=algo, slices=slices, workspace=ws)
+
+
 class DDMatmul(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, A, B):
+    def forward(ctx, A, B, algo="auto", slices=0):
         ctx.save_for_backward(A, B)
-        return mpgemm.gemm("dd", A, B)
+        ctx.algo, ctx.slices = algo, slices
+        return _product(A, B, algo, slices)
 
     @staticmethod
     def backward(ctx, dC):
@@ -29,15 +45,17 @@ class DDMatmul(torch.autograd.Function):
         dC = dC.contiguous()
         dA = dB = None
         if ctx.needs_input_grad[0]:
-            dA = mpgemm.gemm("dd", dC, B, trans_b=True)
+            dA = _product(dC, B, ctx.algo, ctx.slices, trans_b=True)
         if ctx.needs_input_grad[1]:
-            dB = mpgemm.gemm("dd", A, dC, trans_a=True)
-        return dA, dB
+            dB = _product(A, dC, ctx.algo, ctx.slices, trans_a=True)
+        return dA, dB, None, None
 
 
-def dd_matmul(A, B):
-    """C = A B in DD with gradients through the DD kernels."""
-    return DDMatmul.apply(A, B)
+def dd_matmul(A, B, algo="auto", slices=0):
+    """C = A B in DD with gradients through the DD kernels (algo "auto" /
+    "fp64") or the slicing form on the tensor cores ("bf16", "int8"; slices
+    0 = the library's default)."""
+    return DDMatmul.apply(A, B, algo, slices)
 
 
 def dd_weighted_sum(W, C, split_k=32):

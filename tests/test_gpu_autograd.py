@@ -40,6 +40,25 @@ def test_small_gradients_bitwise(torch):
     assert_bitwise(host(Bd.grad), oracle.gemm("dd", np.ascontiguousarray(A.transpose(0, 2, 1)), W), "dB")
 
 
+def test_small_gradients_slicing_form_bitwise(torch):
+    """With the tcgen05 slicing form, the forward product and both gradients
+    equal the slicing oracle on the same operands bit for bit."""
+    from oracle import ozaki as OZ
+    from paper_2101_06584_gb300.autograd import dd_matmul
+    rng = np.random.default_rng(820)
+    S = 12
+    A, B, W = I.uniform(2, (70, 90), rng), I.uniform(2, (90, 50), rng), I.uniform(2, (70, 50), rng)
+    Ad = dev(torch, A).requires_grad_(True)
+    Bd = dev(torch, B).requires_grad_(True)
+    C = dd_matmul(Ad, Bd, algo="bf16", slices=S)
+    C.backward(dev(torch, W))
+    Bt = np.ascontiguousarray(B.transpose(0, 2, 1))
+    At = np.ascontiguousarray(A.transpose(0, 2, 1))
+    assert_bitwise(host(C.detach()), OZ.gemm(A, B, S)[0], "forward")
+    assert_bitwise(host(Ad.grad), OZ.gemm(W, Bt, S)[0], "dA")
+    assert_bitwise(host(Bd.grad), OZ.gemm(At, W, S)[0], "dB")
+
+
 def _fd_rows(A, B, W, samples):
     """QD central differences of loss(A) = sum(W * (A B)) wrt A[p, q]: only
     row p of C changes, so each needs a 1 x k by k x n QD product and a QD dot
@@ -64,11 +83,46 @@ def _fd_rows(A, B, W, samples):
     return out
 
 
-def test_full_size_against_fd_and_oracle(torch):
-    from paper_2101_06584_gb300.autograd import dd_matmul
+@pytest.fixture(scope="module")
+def full_size():
     n = 2048
     rng = I.rng_for(4)
-    A, B, W = I.uniform(2, (n, n), rng), I.uniform(2, (n, n), rng), I.uniform(2, (n, n), rng)
+    return n, I.uniform(2, (n, n), rng), I.uniform(2, (n, n), rng), I.uniform(2, (n, n), rng)
+
+
+def _check_fd(A, B, W, dA, dB, n, srng):
+    """dA and dB within n 2^-100 of QD central differences on 64 entries each."""
+    Bt = np.ascontiguousarray(B.transpose(0, 2, 1))
+    At = np.ascontiguousarray(A.transpose(0, 2, 1))
+    samples = [(int(srng.integers(n)), int(srng.integers(n))) for _ in range(64)]
+    fd = _fd_rows(A, B, W, samples)
+    absWB = X.ExactRows(np.abs(W), np.abs(Bt))
+    for (p, q), g in zip(samples, fd):
+        bound = n * Fraction(2) ** -100 * absWB.dot(p, q)
+        assert abs(X.value(dA[:, p, q]) - g) <= bound, ("dA", p, q)
+    Wt = np.ascontiguousarray(W.transpose(0, 2, 1))
+    fdb = _fd_rows(Bt, At, Wt, samples)
+    absWA = X.ExactRows(np.abs(Wt), np.abs(A))
+    for (p, q), g in zip(samples, fdb):
+        bound = n * Fraction(2) ** -100 * absWA.dot(p, q)
+        assert abs(X.value(dB[:, q, p]) - g) <= bound, ("dB", q, p)
+
+
+def test_full_size_slicing_form_against_fd(torch, full_size):
+    """The tcgen05 slicing form (default 14 slices) at 2048^3: both gradients
+    within n 2^-100 of QD central differences, like the k-sequential ones."""
+    from paper_2101_06584_gb300.autograd import dd_matmul
+    n, A, B, W = full_size
+    Ad = dev(torch, A).requires_grad_(True)
+    Bd = dev(torch, B).requires_grad_(True)
+    C = dd_matmul(Ad, Bd, algo="bf16")
+    C.backward(dev(torch, W))
+    _check_fd(A, B, W, host(Ad.grad), host(Bd.grad), n, np.random.default_rng(830))
+
+
+def test_full_size_against_fd_and_oracle(torch, full_size):
+    from paper_2101_06584_gb300.autograd import dd_matmul
+    n, A, B, W = full_size
     Ad = dev(torch, A).requires_grad_(True)
     Bd = dev(torch, B).requires_grad_(True)
     C = dd_matmul(Ad, Bd)
