@@ -70,6 +70,7 @@ def bf16_peak():
 TRAFFIC_SOURCES = {
     "td_qd": ["mp_arith.cuh", "gemm_kernel.cuh", "gemm_qd.cu", "internal.h"],
     "dd_int8": ["mp_arith.cuh", "ozaki.cu", "ozaki.h", "internal.h"],
+    "dd_tc": ["mp_arith.cuh", "ozaki.cu", "ozaki.h", "internal.h"],
 }
 
 
