@@ -191,8 +191,10 @@ int mpgemm_ex(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k,
  * MPG_ALGO_INT8_OZAKI.  Workspace: a 256-byte header whose first int32 is 0
  * after a normal run (a device-side wait that exceeded about a second leaves
  * the code of the waiting role there), then the digits as bf16 with rows
- * padded to 128 ([S][mp][kp] for op(A)) and to N ([S][np][kp] for op(B)^T), then the
- * int32 exponents; mpgemm_workspace_size gives the total. */
+ * padded to 128 ([S][mp][kp] for op(A); 256 for DD) and to N ([S][np][kp] for
+ * op(B)^T), then the int32 exponents, then for DD 256 KB per SM in which
+ * finished groups wait for their additions to C; mpgemm_workspace_size gives
+ * the total. */
 
 /* The Strassen form (Sec. 3: the paper's divide-and-conquer alternative to
  * the block algorithm).  With opts->strassen = L > 0, C := A B is computed

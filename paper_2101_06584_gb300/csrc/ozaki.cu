@@ -791,6 +791,7 @@ struct TcArgs {
     int64_t ldc, m, n, kp;
     int S, tiles_m, tiles_n;
     int* err;
+    long long* scratch;     // CTA-pair engine: per CTA, two [BN][BM] buffers of finished group sums
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -1179,7 +1180,10 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 // and B halves from both, and releases a stage in both CTAs with one
 // multicast commit.  A finished accumulator is committed after the next
 // stage's barrier wait, not right behind the stage's own commit: two commits
-// in a row stall the issuing thread.  Compared with a 128 x 128 tile per SM this loads a
+// in a row stall the issuing thread.  The FP64 work of a finished group is
+// done by four adder warps (warps 6-9): a drain warp copies its rows' 64-bit
+// group sums to a per-CTA buffer in global memory and goes on draining, and
+// the adder of its lane quadrant splits them and adds them to C in order.  Compared with a 128 x 128 tile per SM this loads a
 // quarter fewer bytes per product and waits once per eight MMAs instead of
 // four.  Epilogue warps of both CTAs signal the leader when an accumulator
 // has been drained.  Every wait is bounded; a role that gives up sets the
@@ -1199,7 +1203,9 @@ constexpr int GW = 2;                                    // 64-bit group sums
 constexpr int ACC_COLS = BN;
 constexpr int GRP_COL = 2 * BN;
 constexpr int TMEM_COLS = 512;
-constexpr int EPI_ARRIVALS = 8;                          // 4 epilogue warps in each CTA
+constexpr int EPI_ARRIVALS = 8;                          // 4 drain warps in each CTA
+constexpr int THREADS = 320;                             // producer, MMA, 4 drain, 4 adder warps
+constexpr int SCRATCH_BYTES = 2 * BN * BM * 8;           // per CTA: two buffers of 64-bit group sums
 static_assert(GRP_COL + GW * BN <= TMEM_COLS, "TMEM columns");
 static_assert(2048 % (KE * KB) == 0 && KPAD % (KE * KB) == 0, "stage k");
 // kind::f16, bf16 A and B (K-major), fp32 D, M = 256, N = 128
@@ -1307,8 +1313,22 @@ __device__ __forceinline__ void umma_commit_pair_local(uint64_t* bar)
                  ::"r"(smem_u32(bar)) : "memory");
 }
 
+// Bounded wait until the shared counter reaches `target` (false after about a
+// second or once another role aborted).
+__device__ __forceinline__ bool wait_count(const volatile int* f, int target, volatile int* abort_flag)
+{
+    if (*f >= target) return true;
+    const unsigned long long t0 = gtimer();
+    while (*f < target) {
+        if (*abort_flag) return false;
+        if (gtimer() - t0 > tc::TIMEOUT_NS) return false;
+        __nanosleep(128);
+    }
+    return true;
+}
+
 template <int P>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(tc2::THREADS, 1)
 ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const TcArgs g)
 {
@@ -1321,6 +1341,10 @@ ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     __shared__ int s_tau[BN];
+    // drain -> adder hand-over, per TMEM lane quadrant: buffers filled and
+    // released so far, a finish flag, and each buffer's tile and weight
+    __shared__ int ready_gen[4], done_gen[4], fin_flag[4];
+    __shared__ int meta[4][2][3];
 
     const uint32_t raw = smem_u32(dsm);
     uint8_t* stage0 = dsm + (((raw + 1023u) & ~1023u) - raw);   // 1024-aligned for the swizzle
@@ -1339,6 +1363,7 @@ ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
         }
         mbar_init(&fin, 1);
         abort_flag = 0;
+        for (int i = 0; i < 4; ++i) ready_gen[i] = done_gen[i] = fin_flag[i] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -1450,7 +1475,7 @@ ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
             while (!mbar_try_cl(&fin, 0u) && gtimer() - t0 < tc::TIMEOUT_NS) {
             }
         }
-    } else {
+    } else if (warp < 6) {
         // ---------------------------------------------------------- epilogue
         const mp::Rn f = mp::make_rn();
         const int q = warp & 3;                          // TMEM lane quadrant of this warp
@@ -1461,6 +1486,8 @@ ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
         uint32_t zero32[32];
 #pragma unroll
         for (int t = 0; t < 32; ++t) zero32[t] = 0u;
+        long long* const scr = g.scratch + static_cast<int64_t>(blockIdx.x) * 2 * BN * tc2::BM;
+        int issued = 0;                                  // groups handed to the adder warp
         uint32_t seg = 0;
         bool ok = true;
         for (int tile = cid; tile < ntiles && ok; tile += ncl) {
@@ -1517,36 +1544,113 @@ ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                 if (lane == 0) mbar_arrive_cluster(b ? lead_acce1 : lead_acce0);
                 ++seg;
                 if (!(weight_end && (j == kGroup - 1 || w == 2))) continue;
-                // end of a group: add its exact value to C
+                // end of a group: the first of a tile goes to C as it is
+                // (DDadd((0, 0), y) is y exactly: an exact split with no
+                // negative zero); a later one is handed to this quadrant's
+                // adder warp, which adds it to C while the drains go on
                 const int wmax = w + j;
+                const int bi = issued & 1;
+                long long* const buf = scr + static_cast<int64_t>(bi) * BN * tc2::BM;
+                if (!first_group && issued >= 2 &&
+                    !__all_sync(0xffffffffu, wait_count(&done_gen[q], issued - 1, abortp))) {
+                    fail(6);
+                    ok = false;
+                    break;
+                }
                 for (int c0 = 0; c0 < GW * BN; c0 += 32) {
                     uint32_t gw[32];
                     tmem_ld32(grp + c0, gw);
                     tmem_wait_ld();
 #pragma unroll
                     for (int t = 0; t < OPW; ++t) {
-                        const int64_t col = n0 + c0 / GW + t;
-                        if (row >= g.m || col >= g.n) continue;
-                        double y[P], acc[P], zz[P];
-                        split_exact(group_load<G, GW>(gw + GW * t), sg + s_tau[c0 / GW + t] - 7 * wmax, y[0], y[1]);
+                        const int cc = c0 / GW + t;
+                        const G V = group_load<G, GW>(gw + GW * t);
                         if (first_group) {
-                            // DDadd((0, 0), y) is y exactly: y is an exact split
-                            // with hi = RN(hi + lo) and no negative zero
-                            g.C[0][row * g.ldc + col] = y[0];
-                            g.C[1][row * g.ldc + col] = y[1];
-                            continue;
+                            const int64_t col = n0 + cc;
+                            if (row < g.m && col < g.n) {
+                                double y[2];
+                                split_exact(V, sg + s_tau[cc] - 7 * wmax, y[0], y[1]);
+                                g.C[0][row * g.ldc + col] = y[0];
+                                g.C[1][row * g.ldc + col] = y[1];
+                            }
+                        } else {
+                            buf[static_cast<int64_t>(cc) * tc2::BM + r] = V;      // coalesced over the warp
                         }
-#pragma unroll
-                        for (int cc = 0; cc < P; ++cc) acc[cc] = g.C[cc][row * g.ldc + col];
-                        mp::Ops<P>::add(f, acc, y, zz);
-#pragma unroll
-                        for (int cc = 0; cc < P; ++cc) g.C[cc][row * g.ldc + col] = zz[cc];
                     }
                     tmem_st32(grp + c0, zero32);
                 }
                 tmem_wait_st();
+                if (!first_group) {
+                    if (lane == 0) {
+                        meta[q][bi][0] = m0;
+                        meta[q][bi][1] = n0;
+                        meta[q][bi][2] = wmax;
+                    }
+                    __threadfence_block();
+                    __syncwarp();
+                    if (lane == 0) *static_cast<volatile int*>(&ready_gen[q]) = issued + 1;
+                    ++issued;
+                }
                 first_group = false;
             }
+        }
+        __threadfence_block();
+        __syncwarp();
+        if (lane == 0) *static_cast<volatile int*>(&fin_flag[q]) = 1;
+    } else {
+        // ------------------------------------------------------------ adder
+        // Finished groups of this quadrant's 32 rows: split each group sum
+        // exactly and add it to C with DDadd, in the order the groups ended.
+        const mp::Rn f = mp::make_rn();
+        const int q = warp & 3;
+        const int r = 32 * q + lane;
+        const long long* const scr = g.scratch + static_cast<int64_t>(blockIdx.x) * 2 * BN * tc2::BM;
+        const volatile int* const rdy = &ready_gen[q];
+        const volatile int* const fin_q = &fin_flag[q];
+        int processed = 0;
+        for (;;) {
+            // next group, or the end of the drains
+            const unsigned long long t0 = gtimer();
+            bool have = *rdy > processed;
+            while (!have) {
+                if (*fin_q) {
+                    __threadfence_block();           // the drain warp raised fin after its last hand-over
+                    have = *rdy > processed;
+                    break;
+                }
+                if (*abortp || gtimer() - t0 > tc::TIMEOUT_NS) break;
+                __nanosleep(256);
+                have = *rdy > processed;
+            }
+            if (!__all_sync(0xffffffffu, have)) {
+                if (!*fin_q && !*abortp) fail(5);
+                break;
+            }
+            __threadfence_block();
+            const int bi = processed & 1;
+            const int m0 = meta[q][bi][0], n0 = meta[q][bi][1], wmax = meta[q][bi][2];
+            const long long* const buf = scr + static_cast<int64_t>(bi) * BN * tc2::BM;
+            const int64_t row = m0 + r;
+            if (row < g.m) {
+                const int sg = g.sig[row];
+#pragma unroll 4
+                for (int cc = 0; cc < BN; ++cc) {
+                    const int64_t col = n0 + cc;
+                    if (col >= g.n) break;
+                    double y[P], acc[P], zz[P];
+                    split_exact(static_cast<long long>(buf[static_cast<int64_t>(cc) * tc2::BM + r]),
+                                sg + g.tau[col] - 7 * wmax, y[0], y[1]);
+#pragma unroll
+                    for (int h = 0; h < P; ++h) acc[h] = g.C[h][row * g.ldc + col];
+                    mp::Ops<P>::add(f, acc, y, zz);
+#pragma unroll
+                    for (int h = 0; h < P; ++h) g.C[h][row * g.ldc + col] = zz[h];
+                }
+            }
+            __threadfence_block();
+            __syncwarp();
+            ++processed;
+            if (lane == 0) *static_cast<volatile int*>(&done_gen[q]) = processed;
         }
     }
 
@@ -1609,6 +1713,7 @@ OzakiLayout ozaki_layout(int S, int64_t m, int64_t n, int64_t k, int elem_bytes)
     L.offSig = L.offB + round_up(static_cast<int64_t>(S) * L.np * L.kp * elem_bytes, 256);
     L.offTau = L.offSig + round_up(L.mp * 4, 256);
     L.total = L.offTau + round_up(L.np * 4, 256);
+    L.offScr = L.total;
     return L;
 }
 
@@ -1650,7 +1755,10 @@ OzakiLayout ozaki_tc_layout(int P, int S, int64_t m, int64_t n, int64_t k)
     L.offB = L.offA + round_up(static_cast<int64_t>(S) * L.mp * L.kp * 2, 256);
     L.offSig = L.offB + round_up(static_cast<int64_t>(S) * L.np * L.kp * 2, 256);
     L.offTau = L.offSig + round_up(L.mp * 4, 256);
-    L.total = L.offTau + round_up(L.np * 4, 256);
+    L.offScr = L.offTau + round_up(L.np * 4, 256);
+    // DD: the pair kernel's hand-over buffers, one area per CTA (at most one
+    // CTA per SM)
+    L.total = L.offScr + (P == 2 ? static_cast<int64_t>(num_sms()) * tc2::SCRATCH_BYTES : 0);
     return L;
 }
 
@@ -1711,7 +1819,7 @@ static cudaError_t pair_clusters(int* out)
         at[0].val.clusterDim.y = 1;
         at[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3(2);
-        cfg.blockDim = dim3(192);
+        cfg.blockDim = dim3(tc2::THREADS);
         cfg.dynamicSmemBytes = smem;
         cfg.attrs = at;
         cfg.numAttrs = 1;
@@ -1750,7 +1858,8 @@ static cudaError_t launch_ozaki_tc(const GemmArgs<P>& g, int S, void* ws, cudaSt
         if (!slice_map(&ma, sa, S, L.mp, L.kp, tc2::BM) || !slice_map(&mb, sb, S, L.np, L.kp, tc2::BN / 2))
             return cudaErrorInvalidValue;
         TcArgs a{sig, tau, {g.C[0], g.C[1], nullptr, nullptr}, g.ldc, g.m, g.n, L.kp, S,
-                 static_cast<int>(L.mp / (2 * tc2::BM)), static_cast<int>(L.np / tc2::BN), err};
+                 static_cast<int>(L.mp / (2 * tc2::BM)), static_cast<int>(L.np / tc2::BN), err,
+                 reinterpret_cast<long long*>(base + L.offScr)};
         int clusters = 0;
         e = pair_clusters(&clusters);
         if (e != cudaSuccess) return e;
@@ -1762,7 +1871,7 @@ static cudaError_t launch_ozaki_tc(const GemmArgs<P>& g, int S, void* ws, cudaSt
         at[0].val.clusterDim.y = 1;
         at[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3(2 * static_cast<unsigned>(tiles < clusters ? tiles : clusters));
-        cfg.blockDim = dim3(192);
+        cfg.blockDim = dim3(tc2::THREADS);
         cfg.dynamicSmemBytes = tc2::STAGES * tc2::STAGE_BYTES + 1024;
         cfg.stream = s;
         cfg.attrs = at;
@@ -1774,7 +1883,7 @@ static cudaError_t launch_ozaki_tc(const GemmArgs<P>& g, int S, void* ws, cudaSt
         if (!slice_map(&ma, sa, S, L.mp, L.kp, tc::BM) || !slice_map(&mb, sb, S, L.np, L.kp, Cf::BN))
             return cudaErrorInvalidValue;
         TcArgs a{sig, tau, {nullptr, nullptr, nullptr, nullptr}, g.ldc, g.m, g.n, L.kp, S,
-                 static_cast<int>(L.mp / tc::BM), static_cast<int>(L.np / Cf::BN), err};
+                 static_cast<int>(L.mp / tc::BM), static_cast<int>(L.np / Cf::BN), err, nullptr};
         for (int c = 0; c < P; ++c) a.C[c] = g.C[c];
         const int smem = tc::STAGES * Cf::STAGE_BYTES + 1024;
         e = cudaFuncSetAttribute(ozaki_tc_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

@@ -16,14 +16,14 @@ constexpr int ozaki_group(int P) { return P == 2 ? 5 : P == 3 ? 11 : 10; }
 struct OzakiLayout {
     int S;
     int64_t mp, np, kp;
-    int64_t offA, offB, offSig, offTau, total;
+    int64_t offA, offB, offSig, offTau, offScr, total;
 };
 // elem_bytes: 1 for int8 digits, 2 for bf16 digits
 OzakiLayout ozaki_layout(int S, int64_t m, int64_t n, int64_t k, int elem_bytes = 1);
 // Workspace of the tcgen05 engine: a 256-byte header (int32 error code of the
 // last call: 0, or the role whose bounded wait expired), bf16 slices with rows
-// of op(A) padded to 128 and columns of op(B) to the tile width of precision P
-// (DD 128, TD/QD 64), exponents.
+// of op(A) padded to 256 (DD) or 128 and columns of op(B) to 128 (DD) or 64,
+// exponents, and for DD two 128 x 128 buffers of 64-bit group sums per SM.
 OzakiLayout ozaki_tc_layout(int P, int S, int64_t m, int64_t n, int64_t k);
 
 // Largest k for which the int32 weight sums are exact: S * k * 64 * 64 < 2^31.
