@@ -174,6 +174,27 @@ def test_bf16_partial_sums_at_the_drain_limit(torch):
     assert_bitwise(Cb[:, [0, 63]][:, :, [0, 31]], want, "bf16 vs oracle at the limit")
 
 
+def test_bf16_long_ragged_k(torch):
+    """k = 2500 (segments of 2048 and of the rest for each pair, zero-padded
+    last stage), three weight groups (S = 12), ragged m and n on the CTA-pair
+    engine: equal to the int8 engine everywhere and to the oracle on sampled
+    entries."""
+    from paper_2101_06584_gb300 import mpgemm as mm
+    rng = np.random.default_rng(660)
+    m, n, k, S = 300, 200, 2500, 12
+    A, B = I.ill_scaled(2, (m, k), rng), I.uniform(2, (k, n), rng)
+    Ad, Bd = dev(torch, A), dev(torch, B)
+    wsb = torch.empty(mm.workspace_size("dd", m, n, k, algo="bf16", slices=S), dtype=torch.uint8, device="cuda")
+    Cb = host(mm.gemm("dd", Ad, Bd, algo="bf16", slices=S, workspace=wsb))
+    assert host(wsb[:4]).view(np.int32)[0] == 0, "tcgen05 kernel reported a timeout"
+    ws8 = torch.empty(mm.workspace_size("dd", m, n, k, algo="int8", slices=S), dtype=torch.uint8, device="cuda")
+    Ci = host(mm.gemm("dd", Ad, Bd, algo="int8", slices=S, workspace=ws8))
+    assert_bitwise(Cb, Ci, "bf16 vs int8, long k")
+    rows, cols = [0, 131, 299], [0, 127, 128, 199]
+    want, _, _ = OZ.gemm(A, B, S, rows=rows, cols=cols)
+    assert_bitwise(Cb[:, rows][:, :, cols], want, "bf16 vs oracle, long k")
+
+
 def test_bf16_full_size_sampled(torch):
     n, S = 4096, 13
     rng = I.rng_for(2)
