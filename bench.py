@@ -340,12 +340,12 @@ class DdSmall(Workload):
         ach = self.mads * 20 / (statistics.mean(launch_ms["dd"]) * 1e-3)
         # the split-K variant for reference (not bit-identical, within bound)
         ms = _time_call(self.torch, lambda: self.mm.gemm("dd", self.A, self.B, out=self.C, split_k=8), 20)
-        return {"bound": "alu", "kernel": "gemm_kseq_kernel<2,32,32,16,2,2> (DD)",
+        return {"bound": "alu", "kernel": "gemm_kseq_kernel<2,8,8,16,1,1> (DD, one entry per thread)",
                 "achieved": ach / 1e12, "peak": pk["dfma"] / 1e12, "unit": "TFP64op/s",
                 "frac": ach / pk["dfma"], "traffic": None, "ops_per_unit": 20,
                 "unit_of_work": "DD multiply-add", "units_per_launch": self.mads,
-                "note": "16 CTAs for 152 SMs: latency-bound; warp split-K 8 runs at %.3g mad/s" % (
-                    self.mads / (ms * 1e-3))}
+                "note": "256 CTAs of 64 threads (16K entries, about one warp per SM sub-partition); "
+                        "warp split-K 8 runs at %.3g mad/s" % (self.mads / (ms * 1e-3))}
 
 
 class DdInt8(Workload):

@@ -10,6 +10,7 @@ const TileInfo kTiles[] = {
     {32, 16, 16, 2, 1, 256},
     {64, 32, 16, 2, 2, 512},
     {64, 64, 16, 4, 4, 256},
+    {8, 8, 16, 1, 1, 64},
 };
 constexpr int kNumTiles = static_cast<int>(sizeof(kTiles) / sizeof(kTiles[0]));
 }  // namespace
@@ -20,8 +21,19 @@ int num_tiles<P>() { return kNumTiles; }
 template <>
 TileInfo tile_info<P>(int t) { return kTiles[t]; }
 
+// 32 x 32 unless that leaves SMs without a CTA; then 16 x 16, then 8 x 8 (one
+// entry per thread; every tile gives the same, k-sequential result).  One warp
+// per SM sub-partition already keeps its FP64 pipe busy, so small tiles trade
+// nothing but staging for the idle SMs they fill.
 template <>
-int default_tile<P>(int64_t, int64_t, int64_t) { return 0; }
+int default_tile<P>(int64_t m, int64_t n, int64_t)
+{
+    const int64_t sms = num_sms();
+    auto ctas = [&](int64_t bm, int64_t bn) { return ((m + bm - 1) / bm) * ((n + bn - 1) / bn); };
+    if (ctas(32, 32) >= sms) return 0;
+    if (ctas(16, 16) >= sms) return 1;
+    return 5;
+}
 
 template <>
 cudaError_t launch_gemm_kseq<P>(const GemmArgs<P>& g, int tile, cudaStream_t s)
@@ -32,6 +44,7 @@ cudaError_t launch_gemm_kseq<P>(const GemmArgs<P>& g, int tile, cudaStream_t s)
     case 2: return launch_kseq_cfg<P, 32, 16, 16, 2, 1>(g, s);
     case 3: return launch_kseq_cfg<P, 64, 32, 16, 2, 2>(g, s);
     case 4: return launch_kseq_cfg<P, 64, 64, 16, 4, 4>(g, s);
+    case 5: return launch_kseq_cfg<P, 8, 8, 16, 1, 1>(g, s);
     default: return cudaErrorInvalidValue;
     }
 }
