@@ -42,7 +42,7 @@ def _load(path):
     L.or_vec_sum.argtypes = [ctypes.c_int, pd, pd]
     L.or_vseb.argtypes = [ctypes.c_int, pd, ctypes.c_int, pd]
     for name in ("or_dd_add", "or_dd_mul", "or_td_add", "or_td_addq", "or_td_mul",
-                 "or_qd_add", "or_qd_mul"):
+                 "or_td_mulq", "or_td_mul_acc", "or_qd_add", "or_qd_mul", "or_qd_add_acc"):
         getattr(L, name).argtypes = [pd, pd, pd]
     vp = ctypes.c_void_p
     L.or_vec_op.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, vp, vp, vp]
@@ -122,11 +122,16 @@ def vseb(e, k, L=None):
 _SCALAR = {("dd", "add"): "or_dd_add", ("dd", "mul"): "or_dd_mul",
            ("td", "add"): "or_td_addq", ("td", "addm"): "or_td_add",
            ("td", "mul"): "or_td_mul",
-           ("qd", "add"): "or_qd_add", ("qd", "mul"): "or_qd_mul"}
+           ("td", "mulq"): "or_td_mulq", ("td", "mula"): "or_td_mul_acc",
+           ("qd", "add"): "or_qd_add", ("qd", "mul"): "or_qd_mul", ("qd", "adda"): "or_qd_add_acc"}
+# elementwise op codes of or_vec_op
+VEC_OPS = {"add": 0, "mul": 1, "addm": 2, "mulq": 3, "mula": 4, "adda": 5}
 
 
 def op(prec, name, x, y, L=None):
-    """Scalar multi-component op; ``name`` in add/mul (``addm`` = merge TDadd)."""
+    """Scalar multi-component op; ``name`` in add/mul, or a variant: ``addm``
+    (TDadd, Alg. 3), ``mulq`` (TDmulq), ``mula`` (accurate TD product),
+    ``adda`` (accurate QD addition)."""
     L = L or lib()
     P = P_OF[prec]
     r = _arr([], P)
@@ -144,7 +149,8 @@ def _planes_ptrs(arr):
 
 
 def vec_op(prec, name, x, y, L=None):
-    """Elementwise r = x (add|mul) y over SoA vectors of shape (P, n)."""
+    """Elementwise r = x op y over SoA vectors of shape (P, n); op names as
+    in ``op``."""
     L = L or lib()
     P = P_OF[prec]
     x = np.ascontiguousarray(x, dtype=np.float64)
@@ -152,7 +158,7 @@ def vec_op(prec, name, x, y, L=None):
     assert x.shape == y.shape and x.shape[0] == P
     r = np.empty_like(x)
     n = x[0].size
-    rc = L.or_vec_op(P, {"add": 0, "mul": 1}[name], n, _planes_ptrs(x), _planes_ptrs(y),
+    rc = L.or_vec_op(P, VEC_OPS[name], n, _planes_ptrs(x), _planes_ptrs(y),
                      _planes_ptrs(r))
     assert rc == 0
     return r

@@ -331,6 +331,129 @@ void or_qd_mul(const double x[4], const double y[4], double r[4])
     or_renorm5(c, r);
 }
 
+/* ------------------------------------------ variants of Sec. 2.3 - 2.4 */
+
+/* Stable sort by decreasing magnitude (insertion sort): equal magnitudes keep
+ * their order, so for operands that are each already in decreasing order the
+ * result is the two-way merge of Alg. 3 with the first operand first on ties. */
+static void sort_by_magnitude(int n, double *z)
+{
+    for (int i = 1; i < n; ++i) {
+        double v = z[i];
+        int j = i;
+        while (j > 0 && fabs(v) > fabs(z[j - 1])) {
+            z[j] = z[j - 1];
+            j = j - 1;
+        }
+        z[j] = v;
+    }
+}
+
+/* TDmulq (Sec. 2.3, the trial TD product): QDmul (Alg. 6) applied to TD
+ * operands padded with a zero fourth component; the fourth component of the
+ * result is dropped. */
+void or_td_mulq(const double x[3], const double y[3], double r[3])
+{
+    double x4[4] = {x[0], x[1], x[2], 0.0};
+    double y4[4] = {y[0], y[1], y[2], 0.0};
+    double r4[4];
+    or_qd_mul(x4, y4, r4);
+    r[0] = r4[0];
+    r[1] = r4[1];
+    r[2] = r4[2];
+}
+
+/* The normalisation of the accurate variants, after the IEEE-style QD
+ * addition of Hida, Li and Bailey: n >= 2 terms, sorted by decreasing
+ * magnitude, are added one by one into a two-term accumulator (u, v).  A term
+ * t gives (s1, e1) = TwoSum(v, t) and (s, e2) = TwoSum(u, s1), so that
+ * u + v + t = s + e2 + e1 exactly; when both errors are nonzero, s is final
+ * and is emitted as the next component and the accumulator becomes (e2, e1);
+ * otherwise the accumulator becomes s and the nonzero error.  Renorm turns
+ * the components and the rest into four.  Readings: once four components are
+ * out, the accumulator and the terms not yet added are summed into a fifth
+ * term with plain additions, in order; if the terms run out first, the
+ * accumulator's two terms follow the emitted components. */
+static void accumulate_sorted(int n, const double *z, double r[4])
+{
+    double u, v;
+    or_quick_two_sum(z[0], z[1], &u, &v);
+    double c[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    int k = 0, i = 2;
+    while (i < n && k < 4) {
+        double s1, e1, s, e2;
+        or_two_sum(v, z[i], &s1, &e1);
+        or_two_sum(u, s1, &s, &e2);
+        i = i + 1;
+        if (e2 != 0.0 && e1 != 0.0) {
+            c[k] = s;
+            k = k + 1;
+            u = e2;
+            v = e1;
+        } else if (e1 == 0.0) {
+            u = s;
+            v = e2;
+        } else {
+            u = s;
+            v = e1;
+        }
+    }
+    if (k < 4) {
+        c[k] = u;
+        c[k + 1] = v;
+    } else {
+        double t = u + v;
+        for (; i < n; ++i)
+            t = t + z[i];
+        c[4] = t;
+    }
+    or_renorm5(c, r);
+}
+
+/* Accurate TD product (Sec. 2.3 names the "accurate" triple-word product of
+ * Fabiano, Muller and Picot without giving its steps).  Reading: every
+ * partial product x_i y_j with i + j <= 2 is split exactly by TwoProd; the
+ * terms of order three (the errors of the order-two products, then x2 y1 and
+ * x1 y2 by fma) are summed with one rounding each; x2 y2 is dropped.  The ten
+ * terms, sorted by decreasing magnitude, go through the accurate
+ * normalisation above; as in TDaddq and TDmulq, the fourth component is
+ * dropped. */
+void or_td_mul_acc(const double x[3], const double y[3], double r[3])
+{
+    double p00, q00, p01, q01, p10, q10, p02, q02, p11, q11, p20, q20;
+    or_two_prod(x[0], y[0], &p00, &q00);
+    or_two_prod(x[0], y[1], &p01, &q01);
+    or_two_prod(x[1], y[0], &p10, &q10);
+    or_two_prod(x[0], y[2], &p02, &q02);
+    or_two_prod(x[1], y[1], &p11, &q11);
+    or_two_prod(x[2], y[0], &p20, &q20);
+    double t3 = (q02 + q11) + q20;
+    t3 = fma(x[2], y[1], t3);
+    t3 = fma(x[1], y[2], t3);
+
+    double z[10] = {p00, q00, p01, p10, q01, q10, p02, p11, p20, t3};
+    double r4[4];
+    sort_by_magnitude(10, z);
+    accumulate_sorted(10, z, r4);
+    r[0] = r4[0];
+    r[1] = r4[1];
+    r[2] = r4[2];
+}
+
+/* Accurate QD addition (the IEEE-style addition of Hida, Li and Bailey): the
+ * eight components sorted by decreasing magnitude (x first on ties), then
+ * the accurate normalisation above. */
+void or_qd_add_acc(const double x[4], const double y[4], double r[4])
+{
+    double z[8];
+    for (int c = 0; c < 4; ++c) {
+        z[c] = x[c];
+        z[4 + c] = y[c];
+    }
+    sort_by_magnitude(8, z);
+    accumulate_sorted(8, z, r);
+}
+
 /* --------------------------------------------------------- dispatch */
 
 static void mp_add(int P, const double *x, const double *y, double *r)
@@ -353,11 +476,15 @@ static void mp_mul(int P, const double *x, const double *y, double *r)
         or_qd_mul(x, y, r);
 }
 
-/* Elementwise add/mul of SoA vectors (Sec. 2.5). */
+/* Elementwise ops of SoA vectors (Sec. 2.5).  op: 0 add, 1 mul (the GEMM's
+ * pair for P); 2 TDadd (Alg. 3), 3 TDmulq, 4 accurate TD product (P = 3);
+ * 5 accurate QD addition (P = 4). */
 int or_vec_op(int P, int op, int64_t n, const double *const *x,
               const double *const *y, double *const *r)
 {
-    if (P < 2 || P > 4 || op < 0 || op > 1 || n < 0)
+    if (P < 2 || P > 4 || op < 0 || op > 5 || n < 0)
+        return -1;
+    if ((op >= 2 && op <= 4 && P != 3) || (op == 5 && P != 4))
         return -1;
     for (int64_t i = 0; i < n; ++i) {
         double xv[4], yv[4], rv[4];
@@ -367,8 +494,16 @@ int or_vec_op(int P, int op, int64_t n, const double *const *x,
         }
         if (op == 0)
             mp_add(P, xv, yv, rv);
-        else
+        else if (op == 1)
             mp_mul(P, xv, yv, rv);
+        else if (op == 2)
+            or_td_add(xv, yv, rv);
+        else if (op == 3)
+            or_td_mulq(xv, yv, rv);
+        else if (op == 4)
+            or_td_mul_acc(xv, yv, rv);
+        else
+            or_qd_add_acc(xv, yv, rv);
         for (int c = 0; c < P; ++c)
             r[c][i] = rv[c];
     }

@@ -42,6 +42,9 @@ void or_td_addq(const double x[3], const double y[3], double r[3]);  /* Sec. 2.3
 void or_td_mul(const double x[3], const double y[3], double r[3]);   /* Alg. 4 */
 void or_qd_add(const double x[4], const double y[4], double r[4]);   /* Alg. 5 */
 void or_qd_mul(const double x[4], const double y[4], double r[4]);   /* Alg. 6 */
+void or_td_mulq(const double x[3], const double y[3], double r[3]);  /* Sec. 2.3, TDmulq */
+void or_td_mul_acc(const double x[3], const double y[3], double r[3]); /* Sec. 2.3, accurate TD product */
+void or_qd_add_acc(const double x[4], const double y[4], double r[4]); /* accurate QD addition */
 
 /* elementwise over SoA planes, Sec. 2.5: r_i = x_i (op) y_i, op 0 = add, 1 = mul.
  * P in {2,3,4}; the TD add is TDaddq (the paper's default TD addition). */

@@ -26,9 +26,20 @@ U = Fraction(1, 2 ** 53)
 # normalised operands (DD add 2^-105.5, DD mul 2^-104.5, TD addq 2^-161,
 # TD mul 2^-158, merge TDadd 2^-159, QD add 2^-215, QD mul 2^-210); a dropped
 # or misplaced term moves the error by many binades.
+# The variants: TDmulq and the accurate TD product 2^-161 (both), the
+# accurate QD addition 2^-215.
 BOUND = {("dd", "add"): 2.0 ** -103, ("dd", "mul"): 2.0 ** -103,
          ("td", "add"): 2.0 ** -157, ("td", "addm"): 2.0 ** -155, ("td", "mul"): 2.0 ** -155,
-         ("qd", "add"): 2.0 ** -211, ("qd", "mul"): 2.0 ** -207}
+         ("td", "mulq"): 2.0 ** -158, ("td", "mula"): 2.0 ** -158,
+         ("qd", "add"): 2.0 ** -211, ("qd", "mul"): 2.0 ** -207, ("qd", "adda"): 2.0 ** -211}
+# the ops of each precision that the op pins cover
+OP_NAMES = {"dd": ("add", "mul"), "td": ("add", "mul", "addm", "mulq", "mula"),
+            "qd": ("add", "mul", "adda")}
+# bounds relative to the exact RESULT |x + y| under cancellation, for the
+# additions that claim one (worst seen over 20000 near-negations with gapped
+# components: TDaddq 2^-161, TDadd 2^-159.6, accurate QD add 2^-215; the
+# sloppy QD add reaches 2^-163 there)
+RESULT_BOUND = {("td", "add"): 2.0 ** -157, ("td", "addm"): 2.0 ** -156, ("qd", "adda"): 2.0 ** -211}
 GEMM_P = {"dd": 100, "td": 150, "qd": 200}
 
 
@@ -162,7 +173,7 @@ def pin_renorm(L, n=1000):
 def _check_bound(prec, name, x, y, r, L):
     P = oracle.P_OF[prec]
     xv, yv, rv = X.value(x), X.value(y), X.value(r)
-    if name == "mul":
+    if name.startswith("mul"):
         exact, scale = xv * yv, abs(xv * yv)
     else:
         exact, scale = xv + yv, abs(xv) + abs(yv)
@@ -178,12 +189,11 @@ def pin_op_bounds(L, n=1500, precs=("dd", "td", "qd")):
     rng = np.random.default_rng(18)
     for prec in precs:
         P = oracle.P_OF[prec]
-        names = ("add", "mul", "addm") if prec == "td" else ("add", "mul")
-        for name in names:
+        for name in OP_NAMES[prec]:
             xs = I.random_mp(P, n, rng, spread=6)
             ys = I.random_mp(P, n, rng, spread=6)
             # a third of the additions nearly cancel in the leading component
-            if name != "mul":
+            if name.startswith("add"):
                 cut = n // 3
                 ys[:, :cut] = I.expand(-xs[0, :cut] * (1 + 2.0 ** -40), P, rng)
             for t in range(n):
@@ -200,13 +210,93 @@ def pin_op_special(L, n=400):
         for prec in ("dd", "td", "qd"):
             P = oracle.P_OF[prec]
             z = [0.0] * (P - 1)
-            names = ("add", "addm") if prec == "td" else ("add",)
-            for name in names:
+            for name in OP_NAMES[prec]:
                 r = oracle.op(prec, name, [a] + z, [b] + z, L)
-                assert list(r) == [s, e] + [0.0] * (P - 2), (prec, name, a, b, r, s, e)
-            r = oracle.op(prec, "mul", [a] + z, [b] + z, L)
-            if abs(p) > 2.0 ** -900 or p == 0:
-                assert list(r) == [p, q] + [0.0] * (P - 2), (prec, "mul", a, b, r, p, q)
+                if name.startswith("add"):
+                    assert list(r) == [s, e] + [0.0] * (P - 2), (prec, name, a, b, r, s, e)
+                elif abs(p) > 2.0 ** -900 or p == 0:
+                    assert list(r) == [p, q] + [0.0] * (P - 2), (prec, name, a, b, r, p, q)
+
+
+def _gapped(P, rng):
+    """A normalised value whose components sit 0-30 bits further apart than
+    adjacent binades, so that it spans more bits than P components hold."""
+    x = [math.ldexp(rng.uniform(-1, 1), int(rng.integers(-6, 7)))]
+    for _ in range(P - 1):
+        x.append(float(rng.uniform(-1, 1)) * X.ulp(x[-1]) / 2 * 2.0 ** -int(rng.integers(0, 30)))
+    return x
+
+
+def _greedy(V, P):
+    """P components of the rational V, each the nearest double to what is left."""
+    out = []
+    for _ in range(P):
+        c = float(V)
+        out.append(c)
+        V -= F(c)
+    return out
+
+
+def _near_negations(P, n, rng):
+    """Pairs (x, y) with y the P-component rounding of -(x + delta), |delta|
+    2^-d |x| for d up to 53 (P - 1): the sum cancels across components that do
+    not line up, and its exact value needs more bits than P components hold."""
+    out = []
+    for _ in range(n):
+        x = _gapped(P, rng)
+        d = int(rng.integers(1, 53 * (P - 1)))
+        delta = X.value(_gapped(P, rng)) * Fraction(2) ** -d * abs(F(x[0]))
+        out.append((x, _greedy(-X.value(x) - delta, P)))
+    return out
+
+
+def pin_accurate_cancellation(L, n=600):
+    """The additions that claim a result-relative bound keep it under
+    cancellation across components, where the sloppy QD addition (Alg. 5),
+    accurate only relative to |x| + |y|, does not: on the same set it misses
+    the accurate one's bound by many binades."""
+    rng = np.random.default_rng(23)
+    for prec in ("td", "qd"):
+        P = oracle.P_OF[prec]
+        pairs = _near_negations(P, n, rng)
+        worst_sloppy = Fraction(0)
+        for x, y in pairs:
+            exact = X.value(x) + X.value(y)
+            for (pr, name), bound in RESULT_BOUND.items():
+                if pr != prec:
+                    continue
+                r = oracle.op(prec, name, x, y, L)
+                assert abs(X.value(r) - exact) <= Fraction(bound) * abs(exact), (prec, name, x, y, r)
+            if prec == "qd" and exact:
+                r = oracle.op(prec, "add", x, y, L)
+                worst_sloppy = max(worst_sloppy, abs(X.value(r) - exact) / abs(exact))
+        if prec == "qd":
+            assert worst_sloppy > Fraction(2) ** -190, float(worst_sloppy)
+
+
+def pin_accurate_products(L, n=800):
+    """TDmulq and the accurate TD product on operands with gapped components:
+    within 2^-158 of the exact product (the fast TDmul of Alg. 4 is held to
+    2^-155 only), and exact where the product fits in three components."""
+    rng = np.random.default_rng(24)
+    for _ in range(n):
+        x, y = _gapped(3, rng), _gapped(3, rng)
+        exact = X.value(x) * X.value(y)
+        for name in ("mulq", "mula"):
+            r = oracle.op("td", name, x, y, L)
+            assert abs(X.value(r) - exact) <= Fraction(BOUND[("td", name)]) * abs(exact), (name, x, y, r)
+    # (a0 + a1)(b0 + b1), a0, b0 integers below 2^20 and a1, b1 integers
+    # below 2^20 scaled by 2^-80 (normalised: below ulp(a0)/2): the product is
+    # a0 b0 + (a0 b1 + a1 b0) + a1 b1, three parts of at most 41 bits each,
+    # which three components hold exactly
+    for _ in range(n // 4):
+        a0, b0 = (float(rng.integers(1, 1 << 20)) * (1 if rng.uniform() < .5 else -1) for _ in range(2))
+        a1, b1 = (float(rng.integers(1, 1 << 20)) * 2.0 ** -80 for _ in range(2))
+        x, y = [a0, a1, 0.0], [b0, b1, 0.0]
+        exact = X.value(x) * X.value(y)
+        for name in ("mulq", "mula"):
+            r = oracle.op("td", name, x, y, L)
+            assert X.value(r) == exact, (name, x, y, r)
 
 
 def _golden_lines():
@@ -311,4 +401,5 @@ def pin_gemm_paper(L, n=17):
 
 ALL_PINS = [pin_two_sum, pin_quick_two_sum, pin_two_prod, pin_three_sums, pin_vec_sum,
             pin_vseb, pin_renorm, pin_worked, pin_op_special, pin_op_bounds,
+            pin_accurate_cancellation, pin_accurate_products,
             pin_gemm_integer, pin_gemm_bound, pin_gemm_structure, pin_gemm_paper]

@@ -43,7 +43,24 @@ MUTANTS = [
     ("qd_mul dropped q5", "s1 = s1 + q5;", ""),
     ("qd_mul wrong three_sum operand", "or_three_sum(&p2, &q1, &q2);", "or_three_sum(&p2, &q1, &q1);"),
     ("qd_mul transposed operand", "or_two_prod(x[1], y[0], &p2, &q2);", "or_two_prod(x[0], y[1], &p2, &q2);"),
-    ("td_addq drops a component", "r[2] = r4[2];", "r[2] = 0.0;"),
+    ("td_addq drops a component", "or_qd_add(x4, y4, r4);\n    r[0] = r4[0];\n    r[1] = r4[1];\n    r[2] = r4[2];",
+     "or_qd_add(x4, y4, r4);\n    r[0] = r4[0];\n    r[1] = r4[1];\n    r[2] = 0.0;"),
+    ("td_mulq drops a component", "or_qd_mul(x4, y4, r4);\n    r[0] = r4[0];\n    r[1] = r4[1];\n    r[2] = r4[2];",
+     "or_qd_mul(x4, y4, r4);\n    r[0] = r4[0];\n    r[1] = r4[1];\n    r[2] = 0.0;"),
+    ("td_mulq pads with a nonzero", "double x4[4] = {x[0], x[1], x[2], 0.0};\n    double y4[4] = {y[0], y[1], y[2], 0.0};\n    double r4[4];\n    or_qd_mul",
+     "double x4[4] = {x[0], x[1], x[2], x[2]};\n    double y4[4] = {y[0], y[1], y[2], 0.0};\n    double r4[4];\n    or_qd_mul"),
+    ("accurate sort ascending", "while (j > 0 && fabs(v) > fabs(z[j - 1])) {", "while (j > 0 && fabs(v) < fabs(z[j - 1])) {"),
+    ("accurate sort by value", "while (j > 0 && fabs(v) > fabs(z[j - 1])) {", "while (j > 0 && v > z[j - 1]) {"),
+    ("accumulate emits the error", "c[k] = s;\n            k = k + 1;\n            u = e2;", "c[k] = e2;\n            k = k + 1;\n            u = s;"),
+    ("accumulate emits on one error", "if (e2 != 0.0 && e1 != 0.0) {", "if (e2 != 0.0 || e1 != 0.0) {"),
+    ("accumulate keeps the wrong error", "u = s;\n            v = e1;", "u = s;\n            v = e2;"),
+    ("accumulate drops the accumulator", "c[k] = u;\n        c[k + 1] = v;", "c[k] = u;"),
+    ("accumulate drops the tail", "double t = u + v;", "double t = 0.0;"),
+    ("accurate td mul dropped p11", "p02, p11, p20, t3}", "p02, 0.0, p20, t3}"),
+    ("accurate td mul wrong index", "or_two_prod(x[1], y[1], &p11, &q11);", "or_two_prod(x[1], y[0], &p11, &q11);"),
+    ("accurate td mul dropped q01", "q01, q10, p02", "0.0, q10, p02"),
+    ("accurate td mul dropped x1 y2", "t3 = fma(x[1], y[2], t3);", ""),
+    ("accurate qd add drops a y component", "z[4 + c] = y[c];", "z[4 + c] = c < 3 ? y[c] : 0.0;"),
     ("gemm transposed B", "b[c] = B[c][p * ldb + j];", "b[c] = B[c][j * ldb + p];"),
     ("gemm swapped mul operands", "mp_mul(P, a, b, prod);", "mp_mul(P, b, a, prod);"),
     ("gemm skips the first term", "for (int64_t p = 0; p < k; ++p) {", "for (int64_t p = 1; p < k; ++p) {"),
