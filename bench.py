@@ -486,12 +486,15 @@ class TdQdTc(TdQdInt8):
 
 class Elementwise(Workload):
     """The paper's elementwise benchmarks (Sec. 4, Figs. 2-4): DDadd/DDmul,
-    TDaddq, merge TDadd (Alg. 3), TDmul, QDadd/QDmul over SoA vectors of n
+    TDaddq, merge TDadd (Alg. 3), TDmul, QDadd/QDmul, and the variants TDmulq,
+    accurate TD product and accurate QD addition, over SoA vectors of n
     elements, every op on its own buffers (inputs far larger than L2)."""
     name = "elementwise"
-    # (precision, op, FP64 operations per element of the implemented sequence)
+    # (precision, op, FP64 operations per element of the implemented sequence;
+    # for the accurate variants both predicated sides of each accumulator step)
     OPS = (("dd", "add", 11), ("dd", "mul", 9), ("td", "add", 81), ("td", "addm", 45), ("td", "mul", 47),
-           ("qd", "add", 87), ("qd", "mul", 123))
+           ("td", "mulq", 123), ("td", "mula", 155), ("qd", "add", 87), ("qd", "mul", 123),
+           ("qd", "adda", 111))
 
     def __init__(self, torch, mm, I, rank, n=1 << 24):
         self.torch, self.mm, self.n = torch, mm, n
@@ -504,7 +507,8 @@ class Elementwise(Workload):
                               torch.empty((P, n), dtype=torch.float64, device="cuda"))
         self.mads = len(self.OPS) * n          # elements processed per step
         self.launches_per_step = len(self.OPS)
-        self.config = {"workload": "elementwise DD/TD/QD add and mul, n=%d elements per op" % n, "n": n}
+        self.config = {"workload": "elementwise DD/TD/QD add and mul and the TD/QD variants, n=%d elements per op"
+                                   % n, "n": n}
 
     def timed_step(self, stream):
         evs = {}

@@ -92,6 +92,41 @@ int mp_qd_add(int64_t n, const double *const x[4], const double *const y[4], dou
 int mp_qd_mul(int64_t n, const double *const x[4], const double *const y[4], double *const r[4]);
 
 /* ---------------------------------------------------------------------
+ * Variants of the TD/QD operations (Sec. 2.3-2.4), same arguments and rules
+ * as the calls above:
+ *   mp_td_mul_q  TDmulq, the trial TD product of Sec. 2.3: QDmul (Alg. 6) on
+ *                operands padded with a zero fourth component, the fourth
+ *                result component dropped.
+ *   mp_td_mul_accurate  the accurate TD product (Sec. 2.3 names it; its steps
+ *                are this library's): each x_i y_j with i + j <= 2 split
+ *                exactly by TwoProd, the order-three terms summed with one
+ *                rounding each -- (q02 + q11) + q20, then fma(x2, y1, .), then
+ *                fma(x1, y2, .) -- and x2 y2 dropped.  The ten terms
+ *                (p00, q00, p01, p10, q01, q10, p02, p11, p20, t3), stably
+ *                sorted by decreasing magnitude, go through the accurate
+ *                normalisation below; the fourth component is dropped.
+ *                Within 2^-158 of the exact product, relative to it.
+ *   mp_qd_add_accurate  the accurate (IEEE-style) QD addition of Hida, Li and
+ *                Bailey: the eight components (x0..x3, y0..y3) stably sorted
+ *                by decreasing magnitude, then the accurate normalisation.
+ *                Within 2^-211 of the exact sum relative to |x + y|, also
+ *                under cancellation (the sloppy mp_qd_add is bounded only
+ *                relative to |x| + |y|).
+ * The accurate normalisation: the sorted terms are added one by one into a
+ * two-term accumulator (u, v); a term t gives (s1, e1) = TwoSum(v, t) and
+ * (s, e2) = TwoSum(u, s1); if both errors are nonzero s is emitted as the
+ * next component and (u, v) = (e2, e1), else u = s and v is the nonzero
+ * error (e2 when both are zero).  After four components the accumulator and
+ * the remaining terms are summed, in order, into a fifth term; if the terms
+ * run out first, u and v follow the components.  Renorm (Sec. 2.4) of the
+ * five terms gives the result.  Every result is bit-identical to these steps
+ * in binary64 with round-to-nearest-even.
+ * ------------------------------------------------------------------- */
+int mp_td_mul_q(int64_t n, const double *const x[3], const double *const y[3], double *const r[3]);
+int mp_td_mul_accurate(int64_t n, const double *const x[3], const double *const y[3], double *const r[3]);
+int mp_qd_add_accurate(int64_t n, const double *const x[4], const double *const y[4], double *const r[4]);
+
+/* ---------------------------------------------------------------------
  * GEMM, Sec. 3, Eq. 1: C := A B with A m x k, B k x n, C m x n, each a set
  * of P row-major device planes.  C is overwritten (there is no alpha/beta,
  * as in the paper).  Requirements: m, n, k >= 0; lda >= max(1, k),

@@ -320,6 +320,12 @@ int mp_qd_add(int64_t n, const double* const x[4], const double* const y[4], dou
 { return vec_call<4>(0, n, x, y, r); }
 int mp_qd_mul(int64_t n, const double* const x[4], const double* const y[4], double* const r[4])
 { return vec_call<4>(1, n, x, y, r); }
+int mp_td_mul_q(int64_t n, const double* const x[3], const double* const y[3], double* const r[3])
+{ return vec_call<3>(3, n, x, y, r); }
+int mp_td_mul_accurate(int64_t n, const double* const x[3], const double* const y[3], double* const r[3])
+{ return vec_call<3>(4, n, x, y, r); }
+int mp_qd_add_accurate(int64_t n, const double* const x[4], const double* const y[4], double* const r[4])
+{ return vec_call<4>(5, n, x, y, r); }
 
 int mpgemm_dd(int64_t m, int64_t n, int64_t k, const double* const A[2], int64_t lda,
               const double* const B[2], int64_t ldb, double* const C[2], int64_t ldc)

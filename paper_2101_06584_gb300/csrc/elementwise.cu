@@ -1,5 +1,5 @@
 // elementwise.cu -- elementwise EFTs and DD/TD/QD add/mul over SoA vectors
-// (Sec. 2.1-2.5).  Each element is independent; a grid-stride loop with one
+// (Sec. 2.1-2.5), with the TD/QD variants of Sec. 2.3-2.4.  Each element is independent; a grid-stride loop with one
 // element per thread per iteration keeps loads coalesced per plane.  Every
 // kernel here is FP64-bound on GB300 (e.g. a DD add is 11 FP64 operations for
 // 48 bytes of traffic), so there is no staging.
@@ -33,9 +33,18 @@ __global__ void __launch_bounds__(256) vec_kernel(const VecArgs<P> a)
             mp::Ops<P>::add(f, x, y, r);
         } else if constexpr (OP == 1) {
             mp::Ops<P>::mul(f, x, y, r);
-        } else {
+        } else if constexpr (OP == 2) {
             static_assert(P == 3, "merge-based add is the TD addition of Alg. 3");
             mp::td_add_merge(f, x, y, r);
+        } else if constexpr (OP == 3) {
+            static_assert(P == 3, "TDmulq is a TD product");
+            mp::td_mulq(f, x, y, r);
+        } else if constexpr (OP == 4) {
+            static_assert(P == 3, "the accurate product is a TD product");
+            mp::td_mul_acc(f, x, y, r);
+        } else {
+            static_assert(P == 4, "the accurate addition is a QD addition");
+            mp::qd_add_acc(f, x, y, r);
         }
 #pragma unroll
         for (int c = 0; c < P; ++c) a.r[c][i] = r[c];
@@ -81,10 +90,21 @@ cudaError_t launch_vec(int op, int64_t n, const double* const* x, const double* 
     }
     a.n = n;
     const unsigned grid = grid_for(n);
+    // op codes: 0 add, 1 mul (the GEMM's pair for P); 2 TDadd (Alg. 3),
+    // 3 TDmulq, 4 accurate TD product; 5 accurate QD addition
     if (op == 0) vec_kernel<P, 0><<<grid, 256, 0, s>>>(a);
     else if (op == 1) vec_kernel<P, 1><<<grid, 256, 0, s>>>(a);
-    else if constexpr (P == 3) vec_kernel<P, 2><<<grid, 256, 0, s>>>(a);
-    else return cudaErrorInvalidValue;
+    else if constexpr (P == 3) {
+        if (op == 2) vec_kernel<P, 2><<<grid, 256, 0, s>>>(a);
+        else if (op == 3) vec_kernel<P, 3><<<grid, 256, 0, s>>>(a);
+        else if (op == 4) vec_kernel<P, 4><<<grid, 256, 0, s>>>(a);
+        else return cudaErrorInvalidValue;
+    } else if constexpr (P == 4) {
+        if (op == 5) vec_kernel<P, 5><<<grid, 256, 0, s>>>(a);
+        else return cudaErrorInvalidValue;
+    } else {
+        return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

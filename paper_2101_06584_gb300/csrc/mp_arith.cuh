@@ -390,6 +390,126 @@ __device__ __forceinline__ void qd_mul(const Rn& f, const double x[4], const dou
     renorm5(f, p0, p1, s0, s1, s2, r[0], r[1], r[2], r[3]);
 }
 
+// ------------------------------------------ variants of Sec. 2.3 - 2.4
+
+// TDmulq (Sec. 2.3, the trial TD product): QDmul on operands padded with a
+// zero fourth component, the fourth result component dropped.  The padding is
+// the register zero, so every operation on it runs as written and the signs
+// of zero results agree with the same steps on the host.
+__device__ __forceinline__ void td_mulq(const Rn& f, const double x[3], const double y[3], double r[3])
+{
+    const double x4[4] = {x[0], x[1], x[2], f.zero};
+    const double y4[4] = {y[0], y[1], y[2], f.zero};
+    double r4[4];
+    qd_mul(f, x4, y4, r4);
+    r[0] = r4[0];
+    r[1] = r4[1];
+    r[2] = r4[2];
+}
+
+// Stable sort of N values by decreasing magnitude: the insertion sort
+// unrolled into adjacent compare-exchanges that swap only when the later
+// entry is strictly larger in magnitude.  Once an inserted value stops, the
+// exchanges below it meet a sorted prefix and do nothing, so the network
+// gives exactly the insertion sort's order, equal magnitudes unmoved.
+template <int N>
+__device__ __forceinline__ void sort_by_magnitude(double z[N])
+{
+#pragma unroll
+    for (int i = 1; i < N; ++i) {
+#pragma unroll
+        for (int j = i; j > 0; --j) {
+            const bool sw = !abs_ge(z[j - 1], z[j]);
+            const double a = z[j - 1], b = z[j];
+            z[j - 1] = sw ? b : a;
+            z[j] = sw ? a : b;
+        }
+    }
+}
+
+// The normalisation of the accurate variants (after the IEEE-style QD
+// addition of Hida, Li and Bailey): N sorted terms are added one by one into
+// a two-term accumulator (u, v).  A term t gives (s1, e1) = TwoSum(v, t) and
+// (s, e2) = TwoSum(u, s1); with both errors nonzero s is emitted as the next
+// component and the accumulator becomes (e2, e1), otherwise s and the nonzero
+// error.  After four components the accumulator and the remaining terms are
+// summed into a fifth term with plain additions; if the terms run out first
+// the accumulator's two terms follow the components.  Renorm ends it.  The
+// emission count k selects the slot, so nothing is indexed dynamically.
+template <int N>
+__device__ __forceinline__ void accumulate_sorted(const Rn& f, const double z[N], double r[4])
+{
+    double u, v;
+    quick_two_sum(f, z[0], z[1], u, v);
+    double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0, tail = 0.0;
+    int k = 0;
+#pragma unroll
+    for (int i = 2; i < N; ++i) {
+        const bool live = k < 4;
+        double s1, e1, s, e2;
+        two_sum(f, v, z[i], s1, e1);
+        two_sum(f, u, s1, s, e2);
+        const bool nz1 = nonzero(e1);
+        const bool emit = live && nz1 && nonzero(e2);
+        c0 = (emit && k == 0) ? s : c0;
+        c1 = (emit && k == 1) ? s : c1;
+        c2 = (emit && k == 2) ? s : c2;
+        c3 = (emit && k == 3) ? s : c3;
+        const double nu = emit ? e2 : s;
+        const double nv = (emit || nz1) ? e1 : e2;
+        // the term joins the tail once four components are out
+        tail = live ? tail : f.add(tail, z[i]);
+        u = live ? nu : u;
+        v = live ? nv : v;
+        k += emit ? 1 : 0;
+        // the fourth emission starts the tail with the accumulator
+        tail = (emit && k == 4) ? f.add(u, v) : tail;
+    }
+    const bool left = k < 4;
+    const double c4 = left ? ((k == 3) ? v : 0.0) : tail;
+    c3 = (left && k == 3) ? u : (left && k == 2) ? v : c3;
+    c2 = (left && k == 2) ? u : (left && k == 1) ? v : c2;
+    c1 = (left && k == 1) ? u : (left && k == 0) ? v : c1;
+    c0 = (left && k == 0) ? u : c0;
+    renorm5(f, c0, c1, c2, c3, c4, r[0], r[1], r[2], r[3]);
+}
+
+// Accurate TD product: every x_i y_j with i + j <= 2 split exactly by
+// TwoProd; the order-three terms (the order-two products' errors, then x2 y1
+// and x1 y2 by fma) summed with one rounding each; x2 y2 dropped.  The ten
+// terms, stably sorted by decreasing magnitude, go through the accurate
+// normalisation; the fourth component is dropped.
+__device__ __forceinline__ void td_mul_acc(const Rn& f, const double x[3], const double y[3], double r[3])
+{
+    double z[10];
+    double q02, q11, q20;
+    two_prod(f, x[0], y[0], z[0], z[1]);
+    two_prod(f, x[0], y[1], z[2], z[4]);
+    two_prod(f, x[1], y[0], z[3], z[5]);
+    two_prod(f, x[0], y[2], z[6], q02);
+    two_prod(f, x[1], y[1], z[7], q11);
+    two_prod(f, x[2], y[0], z[8], q20);
+    double t3 = f.add(f.add(q02, q11), q20);
+    t3 = f.fma(x[2], y[1], t3);
+    z[9] = f.fma(x[1], y[2], t3);
+    sort_by_magnitude<10>(z);
+    double r4[4];
+    accumulate_sorted<10>(f, z, r4);
+    r[0] = r4[0];
+    r[1] = r4[1];
+    r[2] = r4[2];
+}
+
+// Accurate QD addition (the IEEE-style addition of Hida, Li and Bailey): the
+// eight components stably sorted by decreasing magnitude, x first on ties,
+// then the accurate normalisation.
+__device__ __forceinline__ void qd_add_acc(const Rn& f, const double x[4], const double y[4], double r[4])
+{
+    double z[8] = {x[0], x[1], x[2], x[3], y[0], y[1], y[2], y[3]};
+    sort_by_magnitude<8>(z);
+    accumulate_sorted<8>(f, z, r);
+}
+
 // ------------------------------------------------ generic by component count
 
 template <int P> struct Ops;

@@ -58,8 +58,8 @@ def _declare(L):
     L.mpgemm_get_stream.restype = vp
     for f in ("mp_quick_two_sum", "mp_two_sum", "mp_two_prod"):
         getattr(L, f).argtypes = [i64, vp, vp, vp, vp]
-    for f in ("mp_dd_add", "mp_dd_mul", "mp_td_add", "mp_td_add_merge", "mp_td_mul",
-              "mp_qd_add", "mp_qd_mul"):
+    for f in ("mp_dd_add", "mp_dd_mul", "mp_td_add", "mp_td_add_merge", "mp_td_mul", "mp_td_mul_q",
+              "mp_td_mul_accurate", "mp_qd_add", "mp_qd_mul", "mp_qd_add_accurate"):
         getattr(L, f).argtypes = [i64, vp, vp, vp]
     for f in ("mpgemm_dd", "mpgemm_td", "mpgemm_qd"):
         getattr(L, f).argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64]
@@ -179,11 +179,14 @@ def gemm_plain(prec, A, B, out=None):
 
 _VEC = {("dd", "add"): "mp_dd_add", ("dd", "mul"): "mp_dd_mul", ("td", "add"): "mp_td_add",
         ("td", "addm"): "mp_td_add_merge", ("td", "mul"): "mp_td_mul",
-        ("qd", "add"): "mp_qd_add", ("qd", "mul"): "mp_qd_mul"}
+        ("td", "mulq"): "mp_td_mul_q", ("td", "mula"): "mp_td_mul_accurate",
+        ("qd", "add"): "mp_qd_add", ("qd", "mul"): "mp_qd_mul", ("qd", "adda"): "mp_qd_add_accurate"}
 
 
 def vec(prec, op, x, y, out=None):
-    """Elementwise r = x (add|mul) y over (P, n) SoA vectors (``addm``: Alg. 3 TD add)."""
+    """Elementwise r = x op y over (P, n) SoA vectors: ``add``, ``mul``, or a
+    variant -- ``addm`` (TDadd, Alg. 3), ``mulq`` (TDmulq), ``mula`` (accurate
+    TD product), ``adda`` (accurate QD addition)."""
     P = P_OF[prec]
     _require(x, "x", P, 2)
     _require(y, "y", P, 2)

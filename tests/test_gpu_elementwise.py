@@ -1,5 +1,7 @@
-"""Elementwise EFTs and DD/TD/QD add/mul on the GPU are bit-identical to the
-oracle (Sec. 2.1-2.5) on a million seeded elements plus edge cases."""
+"""Elementwise EFTs, DD/TD/QD add/mul and the TD/QD variants (TDadd of
+Alg. 3, TDmulq, the accurate TD product and QD addition) on the GPU are
+bit-identical to the oracle (Sec. 2.1-2.5) on a million seeded elements,
+gapped and cancelling operands, and edge cases."""
 import numpy as np
 import pytest
 
@@ -34,7 +36,7 @@ def test_eft_bitwise(torch, which):
 
 
 OPS = [("dd", "add"), ("dd", "mul"), ("td", "add"), ("td", "addm"), ("td", "mul"),
-       ("qd", "add"), ("qd", "mul")]
+       ("td", "mulq"), ("td", "mula"), ("qd", "add"), ("qd", "mul"), ("qd", "adda")]
 
 
 @pytest.mark.parametrize("prec,op", OPS)
@@ -44,19 +46,49 @@ def test_vec_bitwise_random(torch, prec, op):
     rng = np.random.default_rng(200 + P)
     x = I.random_mp(P, N, rng, spread=30)
     y = I.random_mp(P, N, rng, spread=30)
-    if op != "mul":                                # a third nearly cancel
+    if op.startswith("add"):                       # a third nearly cancel
         cut = N // 3
         y[:, :cut] = I.expand(-x[0, :cut] * (1 + np.ldexp(1.0, -45)), P, rng)
     r = mpgemm.vec(prec, op, dev(torch, x), dev(torch, y))
-    assert_bitwise(host(r), oracle.vec_op(prec, "add" if op == "addm" else op, x, y)
-                   if op != "addm" else _addm(x, y), "%s %s" % (prec, op))
+    assert_bitwise(host(r), oracle.vec_op(prec, op, x, y), "%s %s" % (prec, op))
 
 
-def _addm(x, y):
-    out = np.empty_like(x)
-    for t in range(x.shape[1]):
-        out[:, t] = oracle.op("td", "addm", x[:, t], y[:, t])
+def _gapped(P, n, rng):
+    """Normalised values whose components sit 0-30 bits further apart than
+    adjacent binades (more bits than P components hold)."""
+    out = np.empty((P, n))
+    out[0] = np.ldexp(rng.uniform(-1, 1, n), rng.integers(-6, 7, n))
+    for c in range(1, P):
+        half_ulp = np.ldexp(np.spacing(np.abs(out[c - 1])), -1)
+        out[c] = rng.uniform(-1, 1, n) * half_ulp * np.ldexp(1.0, -rng.integers(0, 30, n))
     return out
+
+
+@pytest.mark.parametrize("prec,op", [("td", "add"), ("td", "addm"), ("qd", "add"), ("qd", "adda"),
+                                     ("td", "mul"), ("td", "mulq"), ("td", "mula")])
+def test_vec_bitwise_gapped_and_cancelling(torch, prec, op):
+    """Operands with gapped components, and for the additions y = -x with
+    one component scaled by 1 + d, |d| in 2^-52 .. 2^-1, and a quarter of the
+    last components replaced, so that the sum cancels across components that
+    do not line up: the sort, the accumulator's emissions and the tail all
+    take data-dependent paths here."""
+    from paper_2101_06584_gb300 import mpgemm
+    P = I.P_OF[prec]
+    n = 200_003
+    rng = np.random.default_rng(400 + P)
+    x = _gapped(P, n, rng)
+    y = _gapped(P, n, rng)
+    if op.startswith("add"):
+        y = -x.copy()
+        j = rng.integers(0, P, n)
+        for c in range(P):
+            sel = j == c
+            y[c, sel] *= 1 + np.ldexp(rng.uniform(-1, 1, sel.sum()), -rng.integers(1, 53, sel.sum()))
+        # and a quarter with one component replaced by fresh gapped values
+        q = rng.integers(0, n, n // 4)
+        y[P - 1, q] = _gapped(P, q.size, rng)[P - 1]
+    r = mpgemm.vec(prec, op, dev(torch, x), dev(torch, y))
+    assert_bitwise(host(r), oracle.vec_op(prec, op, x, y), "%s %s gapped" % (prec, op))
 
 
 @pytest.mark.parametrize("prec,op", OPS)
@@ -68,11 +100,7 @@ def test_vec_bitwise_edges(torch, prec, op):
     x2 = np.concatenate([x, y], axis=1)
     y2 = np.concatenate([y, x], axis=1)
     r = mpgemm.vec(prec, op, dev(torch, x2), dev(torch, y2))
-    if op == "addm":
-        want = _addm(x2, y2)
-    else:
-        want = oracle.vec_op(prec, op, x2, y2)
-    assert_bitwise(host(r), want, "%s %s edges" % (prec, op))
+    assert_bitwise(host(r), oracle.vec_op(prec, op, x2, y2), "%s %s edges" % (prec, op))
 
 
 def test_vec_in_place(torch):
