@@ -491,10 +491,13 @@ class Elementwise(Workload):
     elements, every op on its own buffers (inputs far larger than L2)."""
     name = "elementwise"
     # (precision, op, FP64 operations per element of the implemented sequence;
-    # for the accurate variants both predicated sides of each accumulator step)
+    # for the accurate variants: two TwoSums per accumulator step, plus the
+    # tail additions where four components can be out -- four emissions need
+    # the steps of terms 2-5, so the tail starts at the sixth term at the
+    # earliest and grows from the seventh; the FP64-pipe counters agree)
     OPS = (("dd", "add", 11), ("dd", "mul", 9), ("td", "add", 81), ("td", "addm", 45), ("td", "mul", 47),
-           ("td", "mulq", 123), ("td", "mula", 155), ("qd", "add", 87), ("qd", "mul", 123),
-           ("qd", "adda", 111))
+           ("td", "mulq", 123), ("td", "mula", 148), ("qd", "add", 87), ("qd", "mul", 123),
+           ("qd", "adda", 104))
 
     def __init__(self, torch, mm, I, rank, n=1 << 24):
         self.torch, self.mm, self.n = torch, mm, n
