@@ -56,11 +56,12 @@ __device__ __forceinline__ Rn make_rn()
     return Rn{p[lane], p[32 + lane], p[64 + lane]};
 }
 
-// The bit tests below work on the two 32-bit words of a double.  On GB300 the
-// 64-bit integer shift and compare of a one-word form issue to the FP64 pipe,
-// which every kernel built on these helpers keeps saturated (measured: QDadd
-// 93 FP64-pipe instructions per element with the 64-bit forms, 87 -- its
-// arithmetic alone -- with these); 32-bit integer work stays on the ALU.
+// The bit tests below work on the two 32-bit words of a double.  Written on
+// the whole 64-bit pattern they cost FP64-pipe instructions, which every
+// kernel built on these helpers keeps saturated (measured on GB300: QDadd 93
+// FP64-pipe instructions per element that way, 87 -- its arithmetic alone --
+// with these); 64-bit integer shifts and compares by themselves stay off that
+// pipe, so the one-word tests evidently become floating-point comparisons.
 
 // x != 0 (true for every value but +0 and -0), tested on the bit pattern.
 __device__ __forceinline__ bool nonzero(double x)
