@@ -172,7 +172,10 @@ typedef struct mpgemm_opts {
                        within the same error bound) */
     int slices;     /* INT8_OZAKI: slices per operand, 0 = default */
     int tile;       /* FP64_EFT: tile configuration id 1..mpgemm_num_tiles(P);
-                       INT8_OZAKI: slice-product tiling 1..3; 0 or -1 = library choice */
+                       INT8_OZAKI: slice-product tiling 1..3; 0 or -1 = library choice
+                       (FP64_EFT: the largest of a few tiles whose CTAs keep at least
+                       90% of the SMs busy in the last wave; every tile gives the
+                       same result) */
     void *workspace;          /* device scratch for algorithms that need it */
     size_t workspace_bytes;
     int strassen;   /* FP64_EFT / AUTO: levels of Strassen's algorithm (0..8, 0 = none;

@@ -21,18 +21,13 @@ int num_tiles<P>() { return kNumTiles; }
 template <>
 TileInfo tile_info<P>(int t) { return kTiles[t]; }
 
-// 32 x 32 unless that leaves SMs without a CTA; then 16 x 16, then 8 x 8 (one
-// entry per thread; every tile gives the same, k-sequential result).  One warp
-// per SM sub-partition already keeps its FP64 pipe busy, so small tiles trade
-// nothing but staging for the idle SMs they fill.
+// 32 x 32, 16 x 16 or 8 x 8 (one entry per thread), by the last wave's
+// occupancy.  One warp per SM sub-partition already keeps its FP64 pipe busy,
+// so small tiles trade nothing but staging for the idle SMs they fill.
 template <>
 int default_tile<P>(int64_t m, int64_t n, int64_t)
 {
-    const int64_t sms = num_sms();
-    auto ctas = [&](int64_t bm, int64_t bn) { return ((m + bm - 1) / bm) * ((n + bn - 1) / bn); };
-    if (ctas(32, 32) >= sms) return 0;
-    if (ctas(16, 16) >= sms) return 1;
-    return 5;
+    return pick_tile<P>(m, n, {0, 1, 5});
 }
 
 template <>

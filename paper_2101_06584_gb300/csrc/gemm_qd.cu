@@ -8,6 +8,7 @@ const TileInfo kTiles[] = {
     {16, 16, 16, 1, 1, 256},
     {32, 16, 16, 2, 1, 256},
     {32, 32, 16, 2, 2, 256},
+    {8, 8, 16, 1, 1, 64},
 };
 constexpr int kNumTiles = static_cast<int>(sizeof(kTiles) / sizeof(kTiles[0]));
 }  // namespace
@@ -18,8 +19,13 @@ int num_tiles<P>() { return kNumTiles; }
 template <>
 TileInfo tile_info<P>(int t) { return kTiles[t]; }
 
+// 16 x 16, or 8 x 8 where 16 x 16 leaves much of the last wave's SMs idle
+// (one entry per thread either way).
 template <>
-int default_tile<P>(int64_t, int64_t, int64_t) { return 0; }
+int default_tile<P>(int64_t m, int64_t n, int64_t)
+{
+    return pick_tile<P>(m, n, {0, 3});
+}
 
 template <>
 cudaError_t launch_gemm_kseq<P>(const GemmArgs<P>& g, int tile, cudaStream_t s)
@@ -28,6 +34,7 @@ cudaError_t launch_gemm_kseq<P>(const GemmArgs<P>& g, int tile, cudaStream_t s)
     case 0: return launch_kseq_cfg<P, 16, 16, 16, 1, 1>(g, s);
     case 1: return launch_kseq_cfg<P, 32, 16, 16, 2, 1>(g, s);
     case 2: return launch_kseq_cfg<P, 32, 32, 16, 2, 2>(g, s);
+    case 3: return launch_kseq_cfg<P, 8, 8, 16, 1, 1>(g, s);
     default: return cudaErrorInvalidValue;
     }
 }

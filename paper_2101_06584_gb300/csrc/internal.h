@@ -2,6 +2,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <initializer_list>
 #include <cuda_runtime.h>
 
 namespace mpg {
@@ -51,7 +52,9 @@ cudaError_t launch_strassen(const GemmArgs<P>& g, int levels, double* ws, cudaSt
 template <int P>
 cudaError_t launch_zero(const GemmArgs<P>& g, cudaStream_t s);
 
-// Elementwise kernels.  op: 0 add, 1 mul, 2 merge-based add (P == 3 only).
+// Elementwise kernels.  op: 0 add, 1 mul (the GEMM's pair for P); 2 TDadd
+// (Alg. 3), 3 TDmulq, 4 accurate TD product (P == 3); 5 accurate QD addition
+// (P == 4).
 template <int P>
 cudaError_t launch_vec(int op, int64_t n, const double* const* x, const double* const* y,
                        double* const* r, cudaStream_t s);
@@ -60,6 +63,32 @@ cudaError_t launch_eft(int which, int64_t n, const double* a, const double* b, d
                        double* e, cudaStream_t st);
 
 int num_sms();
+
+// The default tile among `cands` (tile ids, largest tile first): the first
+// whose CTAs, dealt round-robin to the SMs, keep at least 90% of the SMs'
+// time busy -- ctas / (sms * ceil(ctas / sms)) -- else the one that comes
+// closest.  Every tile gives the same, k-sequential result, so this only
+// trades staging per output against idle SMs in the last wave.
+template <int P>
+int pick_tile(int64_t m, int64_t n, std::initializer_list<int> cands)
+{
+    const int64_t sms = num_sms();
+    int best = *cands.begin();
+    double best_eff = -1.0;
+    for (const int t : cands) {
+        const TileInfo ti = tile_info<P>(t);
+        const int64_t ctas = ((m + ti.bm - 1) / ti.bm) * ((n + ti.bn - 1) / ti.bn);
+        const int64_t per_sm = (ctas + sms - 1) / sms;
+        const double eff = per_sm > 0 ? static_cast<double>(ctas) / static_cast<double>(sms * per_sm) : 0.0;
+        if (eff >= 0.9) return t;
+        if (eff > best_eff) {
+            best_eff = eff;
+            best = t;
+        }
+    }
+    return best;
+}
+
 cudaStream_t current_stream();
 void clear_error();
 int set_error(int code, const char* msg);
