@@ -334,6 +334,14 @@ int mpgemm_dd_int8_static(int64_t m, int64_t n, int64_t k,
 int mpgemm_num_tiles(int P);
 int mpgemm_tile_info(int P, int id, int info[6]);
 
+/* The FP64-EFT tile id (1-based) that mpgemm_ex uses for an m x n x k product
+ * when opts->tile is 0: of the candidates (DD: 32x32, 16x16, 8x8; TD/QD:
+ * 16x16, 8x8), the first whose CTAs, dealt round-robin to the device's SMs,
+ * keep at least 90% of them busy -- ctas / (sms * ceil(ctas / sms)) -- else
+ * the closest.  Uses the current device's SM count (152 when there is no
+ * device).  MPG_EINVAL for an unknown P or a negative dimension. */
+int mpgemm_default_tile(int P, int64_t m, int64_t n, int64_t k);
+
 /* ---------------------------------------------------------------------
  * Measurement aid (no counterpart in the paper): pipe throughput probes used
  * as roofline denominators.  Launches `blocks` CTAs of 256 threads and writes

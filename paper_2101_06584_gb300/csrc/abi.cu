@@ -413,6 +413,20 @@ int mpgemm_num_tiles(int P)
     }
 }
 
+int mpgemm_default_tile(int P, int64_t m, int64_t n, int64_t k)
+{
+    clear_error();
+    if (m < 0 || n < 0 || k < 0)
+        return fail(MPG_EINVAL, "m, n, k must be >= 0 (got %lld, %lld, %lld)", (long long)m, (long long)n,
+                    (long long)k);
+    switch (P) {
+    case 2: return default_tile<2>(m, n, k) + 1;
+    case 3: return default_tile<3>(m, n, k) + 1;
+    case 4: return default_tile<4>(m, n, k) + 1;
+    default: return fail(MPG_EINVAL, "P must be 2, 3 or 4 (got %d)", P);
+    }
+}
+
 int mpgemm_tile_info(int P, int id, int info[6])
 {
     clear_error();

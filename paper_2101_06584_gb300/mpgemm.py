@@ -77,6 +77,7 @@ def _declare(L):
     L.mpgemm_batch_autotune.argtypes = [i, i, PP, vp, ctypes.c_size_t, i, ctypes.POINTER(i),
                                         ctypes.POINTER(ctypes.c_float)]
     L.mpgemm_num_tiles.argtypes = [i]
+    L.mpgemm_default_tile.argtypes = [i, i64, i64, i64]
     L.mpgemm_tile_info.argtypes = [i, i, ctypes.POINTER(ctypes.c_int * 6)]
     return L
 
@@ -215,6 +216,13 @@ def eft(which, a, b):
 
 def num_tiles(prec):
     return lib().mpgemm_num_tiles(P_OF[prec])
+
+
+def default_tile(prec, m, n, k):
+    """The tile id (1-based) the library picks for an m x n x k FP64-EFT GEMM."""
+    t = lib().mpgemm_default_tile(P_OF[prec], m, n, k)
+    check(t if t < 0 else 0)
+    return t
 
 
 def tile_info(prec, tile):

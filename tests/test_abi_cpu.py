@@ -167,6 +167,31 @@ def test_tile_table(L):
         assert L.mpgemm_tile_info(P, nt + 1, ctypes.byref(info)) == -1
 
 
+def _tile(L, P, t):
+    info = (ctypes.c_int * 6)()
+    assert L.mpgemm_tile_info(P, t, ctypes.byref(info)) == 0
+    return tuple(info)[:2]
+
+
+def test_default_tile_rule(L):
+    """Without a device the library assumes 152 SMs: the largest candidate
+    tile whose CTAs keep >= 90% of the SMs busy in the last wave, else the
+    closest."""
+    def pick(P, m, n):
+        return _tile(L, P, L.mpgemm_default_tile(P, m, n, 64))
+    assert pick(4, 1024, 1024) == (16, 16)          # 4096 CTAs: 27 per SM, 99.8%
+    assert pick(3, 1024, 1024) == (16, 16)
+    assert pick(4, 256, 256) == (8, 8)              # 16x16: 256 CTAs, 84%; 8x8: 1024 CTAs, 96%
+    assert pick(2, 4096, 4096) == (32, 32)
+    assert pick(2, 2048, 2048) == (32, 32)
+    assert pick(2, 256, 256) == (8, 8)              # 32x32: 42%, 16x16: 84%, 8x8: 96%
+    assert pick(2, 128, 128) == (8, 8)              # none reaches 90%; 8x8 comes closest (84%)
+    assert pick(2, 608, 256) == (32, 32)            # 19 x 8 = 152 CTAs: one per SM
+    assert pick(2, 640, 256) == (8, 8)              # 32x32: 160 CTAs, 53%; 16x16: 84%; 8x8: 99%
+    assert L.mpgemm_default_tile(5, 8, 8, 8) == -1 and "P must be" in err(L)
+    assert L.mpgemm_default_tile(2, -1, 8, 8) == -1
+
+
 def test_batch_plan_rejects_bad_problem(L):
     from paper_2101_06584_gb300.mpgemm import Problem
     probs = (Problem * 2)()
