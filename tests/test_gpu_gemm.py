@@ -2,8 +2,10 @@
 
 The k-sequential FP64-EFT kernel is bit-identical to the oracle's Eq. 1 loop
 for every tile configuration, both transposes, ragged shapes spanning several
-tiles, the cancelling ill-scaled inputs and the paper's Sec. 3 matrices.  The
-split-K kernel is within the normwise bound k 2^-p of the exact product."""
+tiles, the cancelling ill-scaled inputs and the paper's Sec. 3 matrices, and
+on sampled rows at the full sizes of the TD/QD 1024^3 and DD 4096^3 workloads
+in the launch configuration the benchmark times.  The split-K kernel is within
+the normwise bound k 2^-p of the exact product."""
 import numpy as np
 import pytest
 
@@ -115,3 +117,40 @@ def test_splitk_within_bound(torch, prec, split):
         ent = [(i, j) for i in range(m) for j in range(n)]
         err = X.gemm_error(C1, A, B, ent)
         assert err["err_abs"] <= k * 2.0 ** -PBITS[prec], err
+
+
+def test_full_size_main_workload_sampled(torch):
+    """The main workload at its full size and launch configuration: TD then QD
+    at m = n = k = 1024 on the cancelling ill-scaled inputs of its seed (the
+    same generator, in the same order, as the benchmark), through the plain
+    entry points with the library's default tile (16 x 16).  Eight sampled
+    rows of each product, all 1024 columns, are bit-identical to the oracle's
+    Eq. 1 loop."""
+    mm = _mm()
+    n = 1024
+    rng = I.rng_for(1)
+    srng = np.random.default_rng(450)
+    for prec in ("td", "qd"):
+        P = I.P_OF[prec]
+        A, B = I.cancelling_pair(P, n, n, n, rng)
+        ti = mm.tile_info(prec, mm.default_tile(prec, n, n, n))
+        assert (ti["bm"], ti["bn"]) == (16, 16)
+        C = host(mm.gemm_plain(prec, dev(torch, A), dev(torch, B)))
+        rows = sorted({0, n - 1} | set(int(r) for r in srng.integers(0, n, 6)))
+        want = oracle.gemm(prec, np.ascontiguousarray(A[:, rows, :]), B, nthreads=8)
+        assert_bitwise(C[:, rows, :], want, "%s %d sampled rows" % (prec, n))
+
+
+def test_full_size_dd_4096_sampled(torch):
+    """DD at m = n = k = 4096 on the uniform inputs of that workload's seed (the
+    plain product the benchmark times beside the slicing forms): three sampled
+    rows, all 4096 columns, bit-identical to the oracle."""
+    mm = _mm()
+    n = 4096
+    rng = I.rng_for(2)
+    A = I.uniform(2, (n, n), rng)
+    B = I.uniform(2, (n, n), rng)
+    C = host(mm.gemm_plain("dd", dev(torch, A), dev(torch, B)))
+    rows = [0, 2047, n - 1]
+    want = oracle.gemm("dd", np.ascontiguousarray(A[:, rows, :]), B, nthreads=8)
+    assert_bitwise(C[:, rows, :], want, "dd 4096 sampled rows")
