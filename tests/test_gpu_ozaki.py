@@ -237,22 +237,26 @@ def test_td_qd_bitwise(torch, prec, S):
 
 
 @pytest.mark.parametrize("prec", ["td", "qd"])
-def test_td_qd_full_size_sampled(torch, prec):
-    """TD/QD 1024^3 on the cancelling ill-scaled inputs of the main workload:
-    sampled entries bit-identical to the oracle's steps and within n 2^-p of
-    the exact product at the default slice counts."""
+@pytest.mark.parametrize("algo", ["int8", "bf16"])
+def test_td_qd_full_size_sampled(torch, prec, algo):
+    """TD/QD 1024^3 on the cancelling ill-scaled inputs of the main workload,
+    both engines (the tcgen05 one on 64 CTA-pair tiles): sampled entries
+    bit-identical to the oracle's steps and within n 2^-p of the exact product
+    at the default slice counts."""
     from paper_2101_06584_gb300 import mpgemm as mm
     P = I.P_OF[prec]
     n = 1024
     A, B = I.cancelling_pair(P, n, n, n, I.rng_for(1))
-    ws = torch.empty(mm.workspace_size(prec, n, n, n, algo="int8"), dtype=torch.uint8, device="cuda")
-    C = host(mm.gemm(prec, dev(torch, A), dev(torch, B), algo="int8", workspace=ws))
+    ws = torch.empty(mm.workspace_size(prec, n, n, n, algo=algo), dtype=torch.uint8, device="cuda")
+    C = host(mm.gemm(prec, dev(torch, A), dev(torch, B), algo=algo, workspace=ws))
+    if algo == "bf16":
+        assert host(ws[:4]).view(np.int32)[0] == 0, "tcgen05 kernel reported a timeout"
     S = {"td": 22, "qd": 29}[prec]
     srng = np.random.default_rng(670 + P)
     rows = sorted(set(int(x) for x in srng.integers(0, n, 2)))
     cols = sorted(set(int(x) for x in srng.integers(0, n, 2)))
     want, _, _ = OZ.gemm(A, B, S, rows=rows, cols=cols)
-    assert_bitwise(C[:, rows][:, :, cols], want, "%s 1024 sampled" % prec)
+    assert_bitwise(C[:, rows][:, :, cols], want, "%s %s 1024 sampled" % (prec, algo))
     err = X.gemm_error(C, A, B, [(i, j) for i in rows for j in cols])
     assert err["err_abs"] <= n * 2.0 ** -{"td": 150, "qd": 200}[prec], err
 
