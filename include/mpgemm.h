@@ -45,7 +45,7 @@ typedef enum mpg_status {
     MPG_EINVAL = -1,       /* invalid argument; nothing was launched */
     MPG_ECUDA = -2,        /* a CUDA call or launch failed */
     MPG_EWORKSPACE = -3,   /* workspace missing, too small or misaligned */
-    MPG_EUNSUPPORTED = -4  /* valid request this build does not provide */
+    MPG_EUNSUPPORTED = -4  /* valid request the library does not support */
 } mpg_status;
 
 /* Message describing the calling thread's most recent failure ("" if none). */
