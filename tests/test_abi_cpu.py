@@ -144,6 +144,39 @@ def test_strassen_options(L):
     assert L.mpgemm_ex(2, ctypes.byref(o), 8, 8, 8, A, 8, B, 8, C, 8) == -1
 
 
+def test_slicing_options(L):
+    """Host-side limits of the slicing forms, each reported before any launch:
+    the slice count, k beyond the exact int32 weight sums (S k 4096 < 2^31),
+    the workspace (missing, misaligned, too small, overlapping an operand),
+    the int8 tiling id and the grid's row limit."""
+    from paper_2101_06584_gb300.mpgemm import Opts
+    A, B, C = planes(FAKE, 4), planes(2 * FAKE, 4), planes(3 * FAKE, 4)
+    W = 4 * FAKE                                        # 256-byte aligned, far from the operands
+    big = 1 << 40
+    for algo in (2, 3):                                 # int8, bf16
+        o = Opts(0, 0, algo, 0, 17, 0, W, big)
+        assert L.mpgemm_ex(2, ctypes.byref(o), 8, 8, 8, A, 8, B, 8, C, 8) == -1 and "slices" in err(L)
+        o = Opts(0, 0, algo, 0, 41, 0, W, big)
+        assert L.mpgemm_ex(4, ctypes.byref(o), 8, 8, 8, A, 8, B, 8, C, 8) == -1 and "slices" in err(L)
+        # S = 14: k <= (2^31 - 1) // (14 * 4096) = 37449
+        k = (2 ** 31 - 1) // (14 * 4096)
+        o = Opts(0, 0, algo, 0, 14, 0, None, 0)
+        assert L.mpgemm_ex(2, ctypes.byref(o), 8, 8, k + 1, A, k + 1, B, 8, C, 8) == -4
+        assert "exceeds" in err(L)
+        assert L.mpgemm_ex(2, ctypes.byref(o), 8, 8, k, A, k, B, 8, C, 8) == -3   # no workspace
+        o = Opts(0, 0, algo, 0, 0, 0, W + 8, big)
+        assert L.mpgemm_ex(2, ctypes.byref(o), 8, 8, 8, A, 8, B, 8, C, 8) == -3 and "aligned" in err(L)
+        o = Opts(0, 0, algo, 0, 0, 0, W, 1024)
+        assert L.mpgemm_ex(2, ctypes.byref(o), 8, 8, 8, A, 8, B, 8, C, 8) == -3 and "smaller" in err(L)
+        o = Opts(0, 0, algo, 0, 0, 0, FAKE, big)        # on top of A
+        assert L.mpgemm_ex(2, ctypes.byref(o), 8, 8, 8, A, 8, B, 8, C, 8) == -3 and "overlaps" in err(L)
+    o = Opts(0, 0, 2, 0, 0, 4, W, big)                  # int8 tilings are 1..3
+    assert L.mpgemm_ex(2, ctypes.byref(o), 8, 8, 8, A, 8, B, 8, C, 8) == -1 and "tile" in err(L)
+    m = 64 * 65536                                      # 65536 row blocks of 64
+    o = Opts(0, 0, 2, 0, 0, 0, W, big)
+    assert L.mpgemm_ex(2, ctypes.byref(o), m, 8, 8, A, 8, B, 8, C, 8) == -1 and "too large" in err(L)
+
+
 def test_vector_validation(L):
     x, y, r = planes(FAKE, 2), planes(2 * FAKE, 2), planes(3 * FAKE, 2)
     assert L.mp_dd_add(-5, x, y, r) == -1
