@@ -282,3 +282,34 @@ def test_tc_engine_matches_int8(torch, prec, S):
     assert_bitwise(Cb, Ci, "%s tcgen05 vs int8" % prec)
     want, _, _ = OZ.gemm(A, B, S, rows=[0, 127, 128, 199], cols=[0, 127, 128, 149])
     assert_bitwise(Cb[:, [0, 127, 128, 199]][:, :, [0, 127, 128, 149]], want, "%s tcgen05 vs oracle" % prec)
+
+
+def test_largest_exact_k(torch):
+    """DD at the largest k the slicing form accepts with 14 slices,
+    (2^31 - 1) // (14 * 4096) = 37449 (every int32 weight sum exact): both
+    engines agree on all 64 x 64 entries, and four sampled entries are
+    bit-identical to the oracle's steps; k + 1 is refused."""
+    from paper_2101_06584_gb300 import mpgemm as mm
+    S = 14
+    k = OZ.k_limit(S)
+    assert k == (2 ** 31 - 1) // (S * 4096)
+    m = n = 64
+    rng = np.random.default_rng(690)
+    A, B = I.uniform(2, (m, k), rng), I.uniform(2, (k, n), rng)
+    Ad, Bd = dev(torch, A), dev(torch, B)
+    out = {}
+    for algo in ("int8", "bf16"):
+        ws = torch.empty(mm.workspace_size("dd", m, n, k, algo=algo, slices=S), dtype=torch.uint8,
+                         device="cuda")
+        out[algo] = host(mm.gemm("dd", Ad, Bd, algo=algo, slices=S, workspace=ws))
+        if algo == "bf16":
+            assert host(ws[:4]).view(np.int32)[0] == 0, "tcgen05 kernel reported a timeout"
+    assert_bitwise(out["bf16"], out["int8"], "bf16 vs int8 at the largest k")
+    rows, cols = [0, 40], [31, 63]
+    want, _, _ = OZ.gemm(A, B, S, rows=rows, cols=cols)
+    assert_bitwise(out["int8"][:, rows][:, :, cols], want, "largest k sampled")
+    A1 = np.concatenate([A, np.zeros((2, m, 1))], axis=2)
+    B1 = np.concatenate([B, np.zeros((2, 1, n))], axis=1)
+    with pytest.raises(mm.MPGError):
+        mm.gemm("dd", dev(torch, A1), dev(torch, B1), algo="int8", slices=S,
+                workspace=torch.empty(1 << 20, dtype=torch.uint8, device="cuda"))
