@@ -1741,6 +1741,64 @@ static cudaError_t slice_operand(const Planes<P>& pl, int64_t count, int64_t len
     return cudaGetLastError();
 }
 
+// A second stream for slicing op(B) while op(A) is sliced on the caller's
+// stream (the two are independent and neither fills the GPU alone), with the
+// events that fork it from and join it back to the caller's stream, so the
+// call stays ordered on that stream and can be captured into a CUDA graph.
+// One set per host thread and device: concurrent callers never share events.
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    ~SideStream()
+    {
+        // at thread exit; errors (e.g. a runtime already unloaded) are moot
+        if (join) cudaEventDestroy(join);
+        if (fork) cudaEventDestroy(fork);
+        if (s) cudaStreamDestroy(s);
+    }
+};
+
+static cudaError_t side_stream(SideStream** out)
+{
+    thread_local SideStream per_dev[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    SideStream& ss = per_dev[dev];
+    if (!ss.s) {
+        e = cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+    }
+    *out = &ss;
+    return cudaSuccess;
+}
+
+// Slices op(A) on stream s and op(B) on the side stream, joined back to s.
+template <int P, typename T>
+static cudaError_t slice_both(const GemmArgs<P>& g, int S, const OzakiLayout& L, T* sa, T* sb, int* sig,
+                              int* tau, cudaStream_t s)
+{
+    Planes<P> pa, pb;
+    for (int c = 0; c < P; ++c) {
+        pa.c[c] = g.A[c];
+        pb.c[c] = g.B[c];
+    }
+    SideStream* ss = nullptr;
+    cudaError_t e = side_stream(&ss);
+    if (e == cudaSuccess) e = cudaEventRecord(ss->fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ss->s, ss->fork, 0);
+    // op(A) row i: contiguous unless A is stored transposed; op(B) column j:
+    // contiguous only if B is stored transposed
+    if (e == cudaSuccess) e = slice_operand(pb, g.n, g.k, g.ldb, g.trans_b != 0, S, L.np, L.kp, sb, tau, ss->s);
+    if (e == cudaSuccess) e = cudaEventRecord(ss->join, ss->s);
+    if (e == cudaSuccess) e = slice_operand(pa, g.m, g.k, g.lda, !g.trans_a, S, L.mp, L.kp, sa, sig, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ss->join, 0);
+    return e;
+}
+
 // ----------------------------------------------------- tcgen05 host side
 
 OzakiLayout ozaki_tc_layout(int P, int S, int64_t m, int64_t n, int64_t k)
@@ -1844,14 +1902,8 @@ static cudaError_t launch_ozaki_tc(const GemmArgs<P>& g, int S, void* ws, cudaSt
     uint16_t* sb = reinterpret_cast<uint16_t*>(base + L.offB);
     int* sig = reinterpret_cast<int*>(base + L.offSig);
     int* tau = reinterpret_cast<int*>(base + L.offTau);
-    Planes<P> pa, pb;
-    for (int c = 0; c < P; ++c) {
-        pa.c[c] = g.A[c];
-        pb.c[c] = g.B[c];
-    }
     cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = slice_operand(pa, g.m, g.k, g.lda, !g.trans_a, S, L.mp, L.kp, sa, sig, s);
-    if (e == cudaSuccess) e = slice_operand(pb, g.n, g.k, g.ldb, g.trans_b != 0, S, L.np, L.kp, sb, tau, s);
+    if (e == cudaSuccess) e = slice_both<P>(g, S, L, sa, sb, sig, tau, s);
     if (e != cudaSuccess) return e;
     CUtensorMap ma, mb;
     if constexpr (P == 2) {
@@ -1903,17 +1955,9 @@ cudaError_t launch_ozaki(const GemmArgs<P>& g, int S, void* ws, cudaStream_t s, 
     int8_t* base = static_cast<int8_t*>(ws);
     int* sig = reinterpret_cast<int*>(base + L.offSig);
     int* tau = reinterpret_cast<int*>(base + L.offTau);
-    Planes<P> pa, pb;
-    for (int c = 0; c < P; ++c) {
-        pa.c[c] = g.A[c];
-        pb.c[c] = g.B[c];
-    }
-    // op(A) row i: contiguous unless A is stored transposed; op(B) column j:
-    // contiguous only if B is stored transposed
     int8_t* sa = base + L.offA;
     int8_t* sb = base + L.offB;
-    cudaError_t e = slice_operand(pa, g.m, g.k, g.lda, !g.trans_a, S, L.mp, L.kp, sa, sig, s);
-    if (e == cudaSuccess) e = slice_operand(pb, g.n, g.k, g.ldb, g.trans_b != 0, S, L.np, L.kp, sb, tau, s);
+    cudaError_t e = slice_both<P>(g, S, L, sa, sb, sig, tau, s);
     if (e != cudaSuccess) return e;
     OzakiGemmArgs a{base + L.offA, base + L.offB, sig, tau, {nullptr, nullptr, nullptr, nullptr},
                     g.ldc, g.m, g.n, L.mp, L.np, L.kp, S};

@@ -313,3 +313,31 @@ def test_largest_exact_k(torch):
     with pytest.raises(mm.MPGError):
         mm.gemm("dd", dev(torch, A1), dev(torch, B1), algo="int8", slices=S,
                 workspace=torch.empty(1 << 20, dtype=torch.uint8, device="cuda"))
+
+
+@pytest.mark.parametrize("algo", ["int8", "bf16"])
+def test_slicing_form_in_a_cuda_graph(torch, algo):
+    """A slicing-form call captured into a CUDA graph replays to the same bits
+    as a direct call: the op(B) slicing runs on a second stream forked from
+    the capturing stream and joined back to it, so it is captured too."""
+    from paper_2101_06584_gb300 import mpgemm as mm
+    rng = np.random.default_rng(695)
+    m, n, k = 300, 200, 260
+    A, B = I.uniform(2, (m, k), rng), I.uniform(2, (k, n), rng)
+    Ad, Bd = dev(torch, A), dev(torch, B)
+    ws = torch.empty(mm.workspace_size("dd", m, n, k, algo=algo), dtype=torch.uint8, device="cuda")
+    want = host(mm.gemm("dd", Ad, Bd, algo=algo, workspace=ws))
+    out = torch.empty((2, m, n), dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):                       # a warm-up call on a side stream, outside the capture
+        mm.gemm("dd", Ad, Bd, out=out, algo=algo, workspace=ws)
+    torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        mm.gemm("dd", Ad, Bd, out=out, algo=algo, workspace=ws)
+    for _ in range(2):
+        out.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert_bitwise(host(out), want, "%s graph replay" % algo)
