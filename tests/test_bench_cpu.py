@@ -1,0 +1,86 @@
+"""Host-side logic of the benchmark on CPU: DRAM traffic recorded from an ncu
+CSV is stored with a hash of the kernel's sources and reported only while
+those sources are unchanged; the committed records are well formed; the
+per-kernel byte sums and per-call averages of a capture."""
+import csv
+import json
+import os
+
+import pytest
+
+import bench
+
+
+def test_committed_records_are_well_formed():
+    """Each record names its capture command (with ncu's clocks left alone),
+    its launches and a source hash; while the hash matches the sources the
+    record is what the benchmark reports (a stale one is reported as null)."""
+    with open(bench.TRAFFIC_FILE) as f:
+        rec = json.load(f)
+    assert rec
+    for key, ent in rec.items():
+        assert key.split("_")[0] + "_" + key.split("_")[1] in bench.TRAFFIC_SOURCES, key
+        assert ent["bytes_per_launch"] > 0 and ent["launches"] >= ent["per_call"] >= 1, key
+        assert ent["command"].startswith("ncu ") and "--clock-control none" in ent["command"], key
+        assert len(ent["source_sha256"]) == 64 and int(ent["source_sha256"], 16) >= 0, key
+        fresh = ent["source_sha256"] == bench.kernel_source_hash(key)
+        assert bench.recorded_traffic(key) == (ent["bytes_per_launch"] if fresh else None), key
+
+
+def _fake_csv(path, launches):
+    """An ncu --csv log: per launch (id, kernel, read, write) three metric rows."""
+    with open(path, "w", newline="") as f:
+        w = csv.writer(f)
+        w.writerow(["==PROF== a line before the table"])
+        w.writerow(["ID", "Kernel Name", "Metric Name", "Metric Unit", "Metric Value"])
+        for i, name, rd, wr in launches:
+            w.writerow([i, name, "dram__bytes_read.sum", "byte", "{:,}".format(rd)])
+            w.writerow([i, name, "dram__bytes_write.sum", "byte", "{:,}".format(wr)])
+            w.writerow([i, name, "gpu__time_duration.sum", "ns", "1000"])
+
+
+def test_record_and_stale_hash(tmp_path, monkeypatch):
+    traffic = tmp_path / "traffic.json"
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(traffic))
+    log = tmp_path / "log.csv"
+    # two calls of two kernels each; only the matching kernels count
+    _fake_csv(log, [(0, "ozaki_slice(x)", 100, 50), (1, "ozaki_tc_pair_kernel<2>(y)", 1000, 10),
+                    (2, "other_kernel(z)", 7, 7),
+                    (3, "ozaki_slice(x)", 120, 30), (4, "ozaki_tc_pair_kernel<2>(y)", 1100, 20)])
+
+    class Args:
+        record_traffic = str(log)
+        kernel_regex = "ozaki_"
+        per_call = 2
+        traffic_key = "dd_tc_4096_s13:call"
+        command = "ncu ..."
+
+    bench.record_traffic(Args)
+    ent = json.load(open(traffic))["dd_tc_4096_s13:call"]
+    # (150 + 1010 + 150 + 1120) bytes over 4 launches / 2 per call = 2 calls
+    assert ent["bytes_per_launch"] == pytest.approx((150 + 1010 + 150 + 1120) / 2)
+    assert ent["launches"] == 4 and ent["per_call"] == 2
+    assert bench.recorded_traffic("dd_tc_4096_s13:call") == ent["bytes_per_launch"]
+    # a record taken from other sources is not reported
+    ent["source_sha256"] = "0" * 64
+    json.dump({"dd_tc_4096_s13:call": ent}, open(traffic, "w"))
+    assert bench.recorded_traffic("dd_tc_4096_s13:call") is None
+    assert bench.recorded_traffic("td_qd_1024:qd") is None          # no record at all
+
+
+def test_source_hash_follows_the_sources(tmp_path, monkeypatch):
+    """The hash covers every listed source: changing one byte of one changes it."""
+    src = os.path.join(bench.ROOT, "paper_2101_06584_gb300", "csrc")
+    fake = tmp_path / "paper_2101_06584_gb300" / "csrc"
+    fake.mkdir(parents=True)
+    for name in bench.TRAFFIC_SOURCES["td_qd"]:
+        (fake / name).write_bytes(open(os.path.join(src, name), "rb").read())
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_source_hash("td_qd_1024:qd")
+    for name in bench.TRAFFIC_SOURCES["td_qd"]:
+        p = fake / name
+        data = p.read_bytes()
+        p.write_bytes(data + b" ")
+        assert bench.kernel_source_hash("td_qd_1024:qd") != h0, name
+        p.write_bytes(data)
+    assert bench.kernel_source_hash("td_qd_1024:qd") == h0
