@@ -202,7 +202,10 @@ int mpgemm_ex(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k,
  *   V = P_w + 2^7 P_(w-1) + ... + 2^28 P_(w-4) (|V| < 2^60), V split exactly
  *   into hi = RN(V) (ties to even) and lo = V - hi, and from acc = 0,
  *   acc = DDadd(acc, (hi 2^e, lo 2^e)), e = sigma_i + tau_j - 7w (Alg. 1),
- *   w the group's largest weight.
+ *   w the group's largest weight.  hi 2^e and lo 2^e are scaled as C's
+ *   ldexp: exact in the normal binary64 range (every product but the
+ *   tiniest and the largest); below it rounded to the nearest multiple of
+ *   2^-1074, ties to even, a zero keeping its sign; above it +-inf.
  * The result is deterministic and bit-identical to those steps evaluated
  * anywhere; its error against the exact product shrinks by ~2^-7 per slice.
  * Needs opts->workspace: 256-byte aligned, mpgemm_workspace_size() bytes, not

@@ -20,7 +20,9 @@ reader can check it line by line.  DD (P = 2):
            acc = (0, 0); for each group in that order:
            acc = DDadd(acc, (hi 2^e, lo 2^e)), e = sigma_i + tau_j - 7w, w
            the group's largest weight, with the oracle's DDadd (Alg. 1).  The
-           scaled values are exact binary64 for the sizes this form accepts.
+           scaled parts are C's ldexp of hi and lo: exact while they stay in
+           the normal binary64 range (as for all but the tiniest or largest
+           products), rounded to nearest (ties to even) below it, +-inf above.
 
 TD and QD (P = 3, 4) differ in two places:
   slices   each component is first floored to a multiple of
@@ -151,6 +153,20 @@ def split_exact(V):
     return hi, float(lo)
 
 
+def scale2(x, e):
+    """x 2^e as binary64, as C's ldexp: exact in the normal range; below it
+    the nearest multiple of 2^-1074 (ties to even; a zero keeps the sign of
+    x); above it +-inf."""
+    try:
+        return math.ldexp(x, e)
+    except OverflowError:
+        return math.copysign(math.inf, x)
+
+
+def _in_normal_range(x, v):
+    return x == 0 or 2.0 ** -1022 <= abs(v) < math.inf
+
+
 def gemm(A, B, S, rows=None, cols=None, L=None):
     """C = A B through S-slice error-free splitting, for the selected rows of
     A and columns of B (all by default).  A (P, m, k), B (P, k, n), P = 2, 3
@@ -174,8 +190,9 @@ def gemm(A, B, S, rows=None, cols=None, L=None):
                 assert abs(V) < {2: 2 ** 60, 3: 2 ** 102, 4: 2 ** 95}[P]
                 hi, lo = split_exact(V)
                 e = sig[r] + tau[c] - BASE_BITS * wmax
-                vh, vl = math.ldexp(hi, e), math.ldexp(lo, e)
-                assert Fraction(vh) + Fraction(vl) == Fraction(V) * Fraction(2) ** e, "scaled group sum not exact"
+                vh, vl = scale2(hi, e), scale2(lo, e)
+                if _in_normal_range(hi, vh) and _in_normal_range(lo, vl):
+                    assert Fraction(vh) + Fraction(vl) == Fraction(V) * Fraction(2) ** e, "scaled group sum not exact"
                 acc = _op(prec, "add", acc, (vh, vl) + (0.0,) * (P - 2), L)
             C[:, r, c] = acc
     return C, sig, tau

@@ -465,14 +465,40 @@ __device__ __forceinline__ void mma_s8(int (&c)[4], const uint32_t (&a)[4], cons
 
 // u 2^E as binary64 (0 < u <= 2^53), assembled from its bits with integer
 // operations only: the group-end splits run next to the FP64 additions, and
-// integer <-> binary64 conversions would share the FP64 pipe with them.  The
-// result must be a normal binary64, as for every value this form produces.
-__device__ __forceinline__ double pow2_scaled(bool neg, uint64_t u, int E)
+// integer <-> binary64 conversions would share the FP64 pipe with them.  As
+// ldexp of the binary64 u by E: exact in the normal range; below it rounded
+// to the nearest multiple of 2^-1074, ties to even (gradual underflow; a part
+// that rounds to zero keeps its sign); above it +-inf.  `exact` is cleared
+// when the result is not u 2^E exactly.
+__device__ __forceinline__ double pow2_scaled(bool neg, uint64_t u, int E, bool& exact)
 {
     const int msb = 63 - __clzll(static_cast<long long>(u));
-    const uint64_t mant = msb <= 52 ? (u << (52 - msb)) & ((1ull << 52) - 1) : 0ull;   // u = 2^53: 0
-    return __longlong_as_double(static_cast<long long>((static_cast<uint64_t>(neg) << 63) |
-                                                       (static_cast<uint64_t>(msb + E + 1023) << 52) | mant));
+    const int ef = msb + E + 1023;                    // biased exponent of the leading bit
+    const uint64_t sign = static_cast<uint64_t>(neg) << 63;
+    if (ef >= 2047) {
+        exact = false;
+        return __longlong_as_double(static_cast<long long>(sign | 0x7ff0000000000000ull));
+    }
+    if (ef >= 1) {
+        const uint64_t mant = msb <= 52 ? (u << (52 - msb)) & ((1ull << 52) - 1) : 0ull;   // u = 2^53: 0
+        return __longlong_as_double(static_cast<long long>(sign | (static_cast<uint64_t>(ef) << 52) | mant));
+    }
+    // below the normal range: in units of 2^-1074 the value is u 2^t, and
+    // msb + t <= 51, so a left shift stays below 2^52
+    const int t = E + 1074;
+    uint64_t m;
+    if (t >= 0) {
+        m = u << t;
+    } else if (t <= -64) {
+        m = 0;                                        // u <= 2^53: below half a unit
+        exact = false;
+    } else {
+        const int sr = -t;
+        const uint64_t q = u >> sr, rem = u & ((1ull << sr) - 1), half = 1ull << (sr - 1);
+        m = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+        if (rem) exact = false;
+    }
+    return __longlong_as_double(static_cast<long long>(sign | m));   // m = 2^52 is the least normal
 }
 
 // The split of the magnitude u (< 2^128) of a group sum: q 2^sh = RN(u) with
@@ -499,20 +525,24 @@ __device__ __forceinline__ void round53(unsigned __int128 u, uint64_t& q, int& s
     }
 }
 
-// The exact split of a group sum v times 2^e: hi = RN(v) 2^e (ties to even),
-// lo = (v - RN(v)) 2^e, both exact binary64 for the exponents the slicing forms
-// accept; a zero part is +0.
-__device__ __forceinline__ void split_parts(bool neg, uint64_t q, int sh, int64_t rest, int e, double& hi, double& lo)
+// The split of a group sum v times 2^e: hi = RN(v) 2^e (ties to even), lo =
+// (v - RN(v)) 2^e, each scaled as pow2_scaled does; a zero remainder is +0.
+// Returns whether both parts are exact (always, unless a part leaves the
+// normal binary64 range).
+__device__ __forceinline__ bool split_parts(bool neg, uint64_t q, int sh, int64_t rest, int e, double& hi, double& lo)
 {
-    hi = pow2_scaled(neg, q, sh + e);
-    lo = rest == 0 ? 0.0 : pow2_scaled(neg != (rest < 0), static_cast<uint64_t>(rest < 0 ? -rest : rest), e);
+    bool exact = true;
+    hi = pow2_scaled(neg, q, sh + e, exact);
+    lo = rest == 0 ? 0.0
+                   : pow2_scaled(neg != (rest < 0), static_cast<uint64_t>(rest < 0 ? -rest : rest), e, exact);
+    return exact;
 }
-__device__ __forceinline__ void split_exact(long long v, int e, double& hi, double& lo)
+__device__ __forceinline__ bool split_exact(long long v, int e, double& hi, double& lo)
 {
     if (v == 0) {
         hi = 0.0;
         lo = 0.0;
-        return;
+        return true;
     }
     const bool neg = v < 0;
     const uint64_t u = neg ? 0ull - static_cast<uint64_t>(v) : static_cast<uint64_t>(v);
@@ -529,14 +559,14 @@ __device__ __forceinline__ void split_exact(long long v, int e, double& hi, doub
             rest = static_cast<int64_t>(rem);
         }
     }
-    split_parts(neg, q, sh, rest, e, hi, lo);
+    return split_parts(neg, q, sh, rest, e, hi, lo);
 }
-__device__ __forceinline__ void split_exact(__int128 v, int e, double& hi, double& lo)
+__device__ __forceinline__ bool split_exact(__int128 v, int e, double& hi, double& lo)
 {
     if (v == 0) {
         hi = 0.0;
         lo = 0.0;
-        return;
+        return true;
     }
     const bool neg = v < 0;
     const unsigned __int128 u = neg ? static_cast<unsigned __int128>(-v) : static_cast<unsigned __int128>(v);
@@ -544,7 +574,7 @@ __device__ __forceinline__ void split_exact(__int128 v, int e, double& hi, doubl
     int sh;
     int64_t rest;
     round53(u, q, sh, rest);
-    split_parts(neg, q, sh, rest, e, hi, lo);
+    return split_parts(neg, q, sh, rest, e, hi, lo);
 }
 
 // The exact group sums of precision P: 64-bit integers for DD, 128-bit for TD and QD.
@@ -1135,18 +1165,21 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                         const int64_t col = n0 + c0 / GW + t;
                         if (row >= g.m || col >= g.n) continue;
                         double y[P], acc[P], zz[P];
-                        split_exact(group_load<G, GW>(gw + GW * t), sg + s_tau[c0 / GW + t] - 7 * wmax, y[0], y[1]);
+                        const bool exact = split_exact(group_load<G, GW>(gw + GW * t),
+                                                       sg + s_tau[c0 / GW + t] - 7 * wmax, y[0], y[1]);
 #pragma unroll
                         for (int cc = 2; cc < P; ++cc) y[cc] = f.zero;
-                        if (first_group) {
+                        if (first_group && exact) {
                             // TDaddq / QDadd of zero and an exact split (no
                             // negative zero) is the split itself
 #pragma unroll
                             for (int cc = 0; cc < P; ++cc) g.C[cc][row * g.ldc + col] = y[cc];
                             continue;
                         }
+                        // a first group whose split left the normal range is
+                        // added to zero as written
 #pragma unroll
-                        for (int cc = 0; cc < P; ++cc) acc[cc] = g.C[cc][row * g.ldc + col];
+                        for (int cc = 0; cc < P; ++cc) acc[cc] = first_group ? f.zero : g.C[cc][row * g.ldc + col];
                         mp::Ops<P>::add(f, acc, y, zz);
 #pragma unroll
                         for (int cc = 0; cc < P; ++cc) g.C[cc][row * g.ldc + col] = zz[cc];
@@ -1569,7 +1602,14 @@ ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                             const int64_t col = n0 + cc;
                             if (row < g.m && col < g.n) {
                                 double y[2];
-                                split_exact(V, sg + s_tau[cc] - 7 * wmax, y[0], y[1]);
+                                if (!split_exact(V, sg + s_tau[cc] - 7 * wmax, y[0], y[1])) {
+                                    // a part left the normal range: DDadd to zero as written
+                                    const double z[2] = {f.zero, f.zero};
+                                    double r2[2];
+                                    mp::Ops<2>::add(f, z, y, r2);
+                                    y[0] = r2[0];
+                                    y[1] = r2[1];
+                                }
                                 g.C[0][row * g.ldc + col] = y[0];
                                 g.C[1][row * g.ldc + col] = y[1];
                             }

@@ -226,3 +226,67 @@ def test_td_qd_error_meets_bound(P, S):
         C2, _, _ = OZ.gemm(A, B, S - 3)
         err2 = X.gemm_error(C2, A, B, [(i, j) for i in range(m) for j in range(n)])
         assert err2["err_abs"] > err["err_abs"] * 2.0 ** 10
+
+
+def _rne_binary64(v):
+    """The rational v rounded to binary64 by exact arithmetic: the nearest
+    multiple of the spacing at |v| (2^-1074 below the normal range), ties to
+    even, +-inf beyond the largest finite value; v = 0 gives +0."""
+    if v == 0:
+        return 0.0
+    a = abs(v)
+    ex = a.numerator.bit_length() - a.denominator.bit_length()
+    if Fraction(2) ** ex > a:
+        ex -= 1                                         # 2^ex <= a < 2^(ex+1)
+    sp = Fraction(2) ** max(ex - 52, -1074)
+    q = a // sp
+    r = a - q * sp
+    if r > sp / 2 or (r == sp / 2 and q % 2 == 1):
+        q += 1
+    x = q * sp
+    sign = -1.0 if v < 0 else 1.0
+    if x > Fraction(float.fromhex("0x1.fffffffffffffp+1023")):
+        return sign * math.inf
+    return sign * float(x)
+
+
+def test_scale2_rounds_like_ieee():
+    """The group parts are scaled as ldexp: exact in the normal range, rounded
+    to the nearest multiple of 2^-1074 (ties to even, signed zeros) below it,
+    +-inf above it -- checked against exact rational rounding."""
+    rng = np.random.default_rng(506)
+    cases = [(1.0, -1074), (1.0, -1075), (3.0, -1076), (-3.0, -1076), (1.5, -1075), (2.5, -1075),
+             (-1.0, -1076), (float(2 ** 53), -1127), (float(2 ** 53 - 1), -1126), (1.0, 1023),
+             (1.0, 1024), (-float(2 ** 52 + 1), 972), (float(2 ** 52 + 1), 971)]
+    for _ in range(3000):
+        q = float(int(rng.integers(1, 2 ** 53)) * (1 if rng.uniform() < .5 else -1))
+        e = int(rng.integers(-1180, -1000)) if rng.uniform() < .8 else int(rng.integers(900, 1000))
+        cases.append((q, e))
+    for x, e in cases:
+        got = OZ.scale2(x, e)
+        want = _rne_binary64(Fraction(x) * Fraction(2) ** e)
+        if want == 0:
+            want = math.copysign(0.0, x)                # a part that rounds to zero keeps its sign
+        assert got == want and math.copysign(1, got) == math.copysign(1, want), (x, e, got, want)
+
+
+def test_tiny_products_round_in_the_subnormal_range():
+    """Rows of A and columns of B scaled by 2^-530: products of two such are
+    about 2^-1060, so the group parts fall below the normal range and are
+    rounded there; every entry stays within the slicing form's relative bound
+    plus a few units of 2^-1074 per group of the exact product."""
+    rng = np.random.default_rng(507)
+    m, n, k, S = 6, 5, 24, 14
+    A, B = I.uniform(2, (m, k), rng), I.uniform(2, (k, n), rng)
+    A[:, :3] *= 2.0 ** -530
+    B[:, :, :2] *= 2.0 ** -530
+    C, sig, tau = OZ.gemm(A, B, S)
+    ex = X.ExactRows(A, B)
+    groups = len(OZ.weight_groups(S, 2))
+    tiny = 0
+    for i in range(m):
+        for j in range(n):
+            err = abs(X.value(C[:, i, j]) - ex.dot(i, j))
+            assert err <= k * Fraction(2) ** -100 * ex.absdot(i, j) + 4 * groups * Fraction(2) ** -1074, (i, j)
+            tiny += abs(C[0, i, j]) < 2.0 ** -1022
+    assert tiny >= 6                                    # the two-tiny-factor entries are subnormal
