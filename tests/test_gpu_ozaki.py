@@ -346,17 +346,19 @@ def test_slicing_form_in_a_cuda_graph(torch, algo):
 @pytest.mark.parametrize("prec,S", [("dd", 14), ("qd", 29)])
 @pytest.mark.parametrize("algo", ["int8", "bf16"])
 def test_products_below_the_normal_range(torch, prec, S, algo):
-    """Rows of A and columns of B scaled by 1, 2^-500 or 2^-530: outputs of
-    two tiny factors are near 2^-1000 .. 2^-1060, where the group parts fall
-    below the normal binary64 range and are rounded there (and the first
-    group is added to zero instead of being stored as it is).  Both engines
-    are bit-identical to the oracle's steps on every entry."""
+    """Rows of A scaled by 1, 2^-500, 2^-530 or 2^-1060 (a subnormal leading
+    component) and columns of B by 1, 2^-500 or 2^-530: outputs range from
+    normal through 2^-1000 .. 2^-1060, where the group parts fall below the
+    normal binary64 range and are rounded there (the first group then being
+    added to zero instead of stored as it is), down to products that round
+    to signed zeros.  Both engines are bit-identical to the oracle's steps on
+    every entry."""
     from paper_2101_06584_gb300 import mpgemm as mm
     P = I.P_OF[prec]
     rng = np.random.default_rng(700 + P)
     m, n, k = 48, 40, 64
     A, B = I.uniform(P, (m, k), rng), I.uniform(P, (k, n), rng)
-    rs = np.array([1.0, 2.0 ** -500, 2.0 ** -530])[np.arange(m) % 3]
+    rs = np.array([1.0, 2.0 ** -500, 2.0 ** -530, 2.0 ** -1060])[np.arange(m) % 4]
     cs = np.array([1.0, 2.0 ** -500, 2.0 ** -530])[(np.arange(n) // 2) % 3]
     A *= rs[None, :, None]
     B *= cs[None, None, :]

@@ -271,14 +271,16 @@ def test_scale2_rounds_like_ieee():
 
 
 def test_tiny_products_round_in_the_subnormal_range():
-    """Rows of A and columns of B scaled by 2^-530: products of two such are
-    about 2^-1060, so the group parts fall below the normal range and are
-    rounded there; every entry stays within the slicing form's relative bound
-    plus a few units of 2^-1074 per group of the exact product."""
+    """Rows of A and columns of B scaled by 2^-530 (and two rows of A by
+    2^-1060, subnormal): products of two tiny factors fall below the normal
+    range, so the group parts are rounded there; every entry stays within the
+    slicing form's relative bound plus a few units of 2^-1074 per group of
+    the exact product."""
     rng = np.random.default_rng(507)
     m, n, k, S = 6, 5, 24, 14
     A, B = I.uniform(2, (m, k), rng), I.uniform(2, (k, n), rng)
     A[:, :3] *= 2.0 ** -530
+    A[:, 3:5] *= 2.0 ** -1060                           # subnormal leading components
     B[:, :, :2] *= 2.0 ** -530
     C, sig, tau = OZ.gemm(A, B, S)
     ex = X.ExactRows(A, B)
