@@ -128,8 +128,9 @@ def random_mp(P, n, rng, spread=30):
 
 def edge_mp(P):
     """Hand-picked operand pairs (x, y), each (P, count): zeros of both signs,
-    exact cancellation, equal magnitudes, far exponents, ties, powers of two and
-    values near the bottom of the normal range."""
+    exact cancellation, equal magnitudes, far exponents, ties, powers of two,
+    values near the bottom of the normal range, subnormal values and products
+    that fall into or below the subnormal range."""
     rows_x, rows_y = [], []
     tiny = 2.0 ** -900
     lead_pairs = [
@@ -138,6 +139,9 @@ def edge_mp(P):
         (2.0 ** 500, 2.0 ** -500), (3.0, 1.0 / 3.0), (0.1, 0.2), (-0.7, 0.7 + 2.0 ** -53),
         (tiny, tiny), (tiny, -tiny * 0.75), (2.0 ** 30, -2.0 ** 30 + 1.0),
         (1.5, 1.5), (math.pi, math.e), (-math.pi, 1e-30), (2.0 ** -60, 2.0 ** 60),
+        (2.0 ** -1060, 2.0 ** -1062), (2.0 ** -1074, -2.0 ** -1074), (3 * 2.0 ** -1074, 2.0 ** -1073),
+        (2.0 ** -540 * 1.25, -2.0 ** -540 * 1.75), (2.0 ** -1000, -2.0 ** -1001 * 1.5),
+        (2.0 ** -600, 2.0 ** -600), (-2.0 ** -1022, 2.0 ** -1023),
     ]
     for (a, b) in lead_pairs:
         xa = [a] + [0.0] * (P - 1)

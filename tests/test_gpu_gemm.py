@@ -154,3 +154,22 @@ def test_full_size_dd_4096_sampled(torch):
     rows = [0, 2047, n - 1]
     want = oracle.gemm("dd", np.ascontiguousarray(A[:, rows, :]), B, nthreads=8)
     assert_bitwise(C[:, rows, :], want, "dd 4096 sampled rows")
+
+
+@pytest.mark.parametrize("prec", ["dd", "td", "qd"])
+def test_kseq_subnormal_products(torch, prec):
+    """Rows of A and columns of B scaled so that products and partial sums
+    fall into and below the subnormal range (IEEE gradual underflow on both
+    sides): bit-identical to the oracle for every tile."""
+    mm = _mm()
+    P = I.P_OF[prec]
+    rng = np.random.default_rng(460 + P)
+    m, n, k = 24, 20, 40
+    A, B = I.uniform(P, (m, k), rng), I.uniform(P, (k, n), rng)
+    A *= np.array([1.0, 2.0 ** -530, 2.0 ** -560, 2.0 ** -1060])[np.arange(m) % 4][None, :, None]
+    B *= np.array([1.0, 2.0 ** -520])[np.arange(n) % 2][None, None, :]
+    want = oracle.gemm(prec, A, B, nthreads=4)
+    assert ((np.abs(want[0]) < 2.0 ** -1022) & (want[0] != 0)).any()
+    Ad, Bd = dev(torch, A), dev(torch, B)
+    for tile in range(1, mm.num_tiles(prec) + 1):
+        assert_bitwise(host(mm.gemm(prec, Ad, Bd, tile=tile)), want, "%s subnormal tile %d" % (prec, tile))
