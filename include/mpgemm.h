@@ -237,6 +237,18 @@ int mpgemm_ex(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k,
  * finished groups wait for their additions to C; mpgemm_workspace_size gives
  * the total. */
 
+/* After an MPG_ALGO_BF16_SLICES call with this workspace: synchronises the
+ * calling thread's stream and returns the code in the workspace header.  0
+ * after a normal run.  A positive code names the role whose bounded wait
+ * (about a second) gave up, the kernel having then stopped every role and
+ * released its resources: 1 the producer (a stage to refill), 2 the MMA
+ * issuer (a free accumulator), 3 the MMA issuer (a loaded stage), 4 a drain
+ * warp (a finished accumulator), 5 an adder warp (a finished group), 6 a
+ * drain warp (a free hand-over buffer); C is then incomplete, and
+ * mpgemm_last_error() says which.  MPG_EINVAL for a NULL workspace,
+ * MPG_ECUDA if the header cannot be read. */
+int mpgemm_tc_status(const void *workspace);
+
 /* The Strassen form (Sec. 3: the paper's divide-and-conquer alternative to
  * the block algorithm).  With opts->strassen = L > 0, C := A B is computed
  * from Strassen's seven products of half-size blocks,

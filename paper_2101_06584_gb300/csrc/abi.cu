@@ -427,6 +427,24 @@ int mpgemm_default_tile(int P, int64_t m, int64_t n, int64_t k)
     }
 }
 
+int mpgemm_tc_status(const void* workspace)
+{
+    clear_error();
+    if (!workspace) return fail(MPG_EINVAL, "workspace is NULL");
+    cudaError_t e = cudaStreamSynchronize(g_stream);
+    int code = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&code, workspace, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the workspace header");
+    if (code != 0) {
+        static const char* const kRole[] = {"", "the producer (a stage to refill)", "the MMA issuer (a free accumulator)",
+                                            "the MMA issuer (a loaded stage)", "a drain warp (a finished accumulator)",
+                                            "an adder warp (a finished group)", "a drain warp (a free hand-over buffer)"};
+        fail(MPG_OK, "a bounded wait gave up: %s; C is incomplete",
+             code > 0 && code < 7 ? kRole[code] : "unknown role");
+    }
+    return code;
+}
+
 int mpgemm_tile_info(int P, int id, int info[6])
 {
     clear_error();

@@ -78,6 +78,7 @@ def _declare(L):
                                         ctypes.POINTER(ctypes.c_float)]
     L.mpgemm_num_tiles.argtypes = [i]
     L.mpgemm_default_tile.argtypes = [i, i64, i64, i64]
+    L.mpgemm_tc_status.argtypes = [vp]
     L.mpgemm_tile_info.argtypes = [i, i, ctypes.POINTER(ctypes.c_int * 6)]
     return L
 
@@ -216,6 +217,16 @@ def eft(which, a, b):
 
 def num_tiles(prec):
     return lib().mpgemm_num_tiles(P_OF[prec])
+
+
+def tc_status(workspace):
+    """The tcgen05 engine's status after a call with ``workspace`` (waits for
+    the stream): 0, or the code of the role whose bounded wait gave up."""
+    _require_ws(workspace)
+    _bind_stream()
+    code = lib().mpgemm_tc_status(ctypes.c_void_p(workspace.data_ptr()))
+    check(code if code < 0 else 0)
+    return code
 
 
 def default_tile(prec, m, n, k):

@@ -177,6 +177,10 @@ def test_slicing_options(L):
     assert L.mpgemm_ex(2, ctypes.byref(o), m, 8, 8, A, 8, B, 8, C, 8) == -1 and "too large" in err(L)
 
 
+def test_tc_status_validation(L):
+    assert L.mpgemm_tc_status(None) == -1 and "NULL" in err(L)
+
+
 def test_vector_validation(L):
     x, y, r = planes(FAKE, 2), planes(2 * FAKE, 2), planes(3 * FAKE, 2)
     assert L.mp_dd_add(-5, x, y, r) == -1

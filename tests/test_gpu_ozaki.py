@@ -369,3 +369,20 @@ def test_products_below_the_normal_range(torch, prec, S, algo):
     want, _, _ = OZ.gemm(A, B, S)
     assert (np.abs(want[0]) < 2.0 ** -1022).sum() > 0 and np.isfinite(want).all()
     assert_bitwise(C, want, "%s %s tiny products" % (prec, algo))
+
+
+def test_tc_status(torch):
+    """The tcgen05 engine's status read through the C ABI: 0 after a normal
+    call; a code planted in the workspace header on the host (the device-side
+    timeout is not provoked) is returned with the role it names."""
+    from paper_2101_06584_gb300 import mpgemm as mm
+    rng = np.random.default_rng(710)
+    A, B = I.uniform(2, (70, 90), rng), I.uniform(2, (90, 50), rng)
+    ws = torch.empty(mm.workspace_size("dd", 70, 50, 90, algo="bf16"), dtype=torch.uint8, device="cuda")
+    mm.gemm("dd", dev(torch, A), dev(torch, B), algo="bf16", workspace=ws)
+    assert mm.tc_status(ws) == 0
+    ws[:4].view(torch.int32).fill_(3)
+    assert mm.tc_status(ws) == 3
+    assert "loaded stage" in mm.lib().mpgemm_last_error().decode()
+    mm.gemm("dd", dev(torch, A), dev(torch, B), algo="bf16", workspace=ws)
+    assert mm.tc_status(ws) == 0                       # every call clears the header first
