@@ -56,7 +56,8 @@ const char *mpgemm_last_error(void);
 int mpgemm_set_stream(void *stream);
 void *mpgemm_get_stream(void);
 
-/* Library ABI version (major * 100 + minor). */
+/* Library ABI version (major * 100 + minor): 101 adds the TD/QD variants,
+ * mpgemm_default_tile and mpgemm_tc_status to 100. */
 int mpgemm_version(void);
 
 /* ---------------------------------------------------------------------

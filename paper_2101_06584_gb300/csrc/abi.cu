@@ -297,7 +297,7 @@ int mpgemm_set_stream(void* stream)
 
 void* mpgemm_get_stream(void) { return static_cast<void*>(g_stream); }
 
-int mpgemm_version(void) { return 100; }
+int mpgemm_version(void) { return 101; }
 
 int mp_quick_two_sum(int64_t n, const double* a, const double* b, double* s, double* e)
 { return eft_call(0, n, a, b, s, e); }

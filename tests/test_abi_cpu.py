@@ -177,6 +177,10 @@ def test_slicing_options(L):
     assert L.mpgemm_ex(2, ctypes.byref(o), m, 8, 8, A, 8, B, 8, C, 8) == -1 and "too large" in err(L)
 
 
+def test_version(L):
+    assert L.mpgemm_version() == 101
+
+
 def test_tc_status_validation(L):
     assert L.mpgemm_tc_status(None) == -1 and "NULL" in err(L)
 
