@@ -32,6 +32,8 @@ MUTANTS = [
     ("dd_add dropped trailing sum", "e = e + w;", "e = e;"),
     ("dd_mul dropped cross product", "w3 = w1 + w2;", "w3 = w1;"),
     ("dd_mul wrong index", "w2 = x[1] * y[0];", "w2 = x[1] * y[1];"),
+    ("dd_mul cross term fused (contracted)", "w1 = x[0] * y[1];\n    w2 = x[1] * y[0];\n    w3 = w1 + w2;",
+     "w1 = 0.0;\n    w2 = x[1] * y[0];\n    w3 = fma(x[0], y[1], w2);"),
     ("td_mul wrong fma index", "double c = fma(x[1], y[1], b[2]);", "double c = fma(x[1], y[0], b[2]);"),
     ("td_mul dropped z32", "double z3 = z31 + z32;", "double z3 = z31;"),
     ("td_mul vseb off by one", "or_vseb(3, &e[1], 2, &r[1]);", "or_vseb(3, &e[0], 2, &r[1]);"),
