@@ -57,7 +57,9 @@ int mpgemm_set_stream(void *stream);
 void *mpgemm_get_stream(void);
 
 /* Library ABI version (major * 100 + minor): 101 adds the TD/QD variants,
- * mpgemm_default_tile and mpgemm_tc_status to 100. */
+ * mpgemm_default_tile and mpgemm_tc_status to 100; 102 adds mpgemm_d and
+ * P = 1 in mpgemm_ex, mpgemm_num_tiles, mpgemm_tile_info and
+ * mpgemm_default_tile. */
 int mpgemm_version(void);
 
 /* ---------------------------------------------------------------------
@@ -154,6 +156,22 @@ int mpgemm_qd(int64_t m, int64_t n, int64_t k,
               const double *const B[4], int64_t ldb,
               double *const C[4], int64_t ldc);
 
+/* The binary64-only product: C := A B of Sec. 3, Eq. 1 evaluated in plain
+ * binary64, the arithmetic the multi-component formats extend (Sec. 1) and
+ * against which Sec. 3 counts the decimal digits a product loses.  A, B, C
+ * are single row-major device planes (m x k, k x n, m x n) with the
+ * requirements of mpgemm_dd.  Every c_ij is accumulated by one thread as
+ * acc = fma(a_ip, b_pj, acc) for p = 0, 1, ..., k-1 from acc = +0, so the
+ * result is bit-identical to that sequence evaluated anywhere else and within
+ * k * 2^-53 (|A| |B|)_ij of the exact product.  Given the leading planes of
+ * DD/TD/QD operands it is the FP64-only GEMM that the multi-component
+ * results are compared with.  mpgemm_ex with P = 1 takes the same product
+ * with transposes and a tile choice (no slicing, split_k or strassen). */
+int mpgemm_d(int64_t m, int64_t n, int64_t k,
+             const double *A, int64_t lda,
+             const double *B, int64_t ldb,
+             double *C, int64_t ldc);
+
 /* Algorithms selectable through mpgemm_ex. */
 typedef enum mpg_algo {
     MPG_ALGO_AUTO = 0,       /* the FP64-EFT kernel (k-sequential unless split_k > 1) */
@@ -183,8 +201,9 @@ typedef struct mpgemm_opts {
                        untransposed operands, split_k 0 or 1): see below */
 } mpgemm_opts;
 
-/* C := op(A) op(B) with the options above; P in {2, 3, 4}; lda/ldb must
- * cover the stored (possibly transposed) shapes. */
+/* C := op(A) op(B) with the options above; P in {2, 3, 4} (or 1, the
+ * binary64-only product of mpgemm_d); lda/ldb must cover the stored
+ * (possibly transposed) shapes. */
 int mpgemm_ex(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k,
               const double *const *A, int64_t lda,
               const double *const *B, int64_t ldb,
@@ -344,15 +363,15 @@ int mpgemm_dd_int8_static(int64_t m, int64_t n, int64_t k,
                           const double *const B[2], int64_t ldb,
                           double *const C[2], int64_t ldc, int slices);
 
-/* Number of FP64-EFT tile configurations for precision P, and a description
+/* Number of FP64-EFT tile configurations for precision P (1..4), and a description
  * of configuration id (BM, BN, BK, TM, TN, threads); returns MPG_EINVAL for
  * an unknown id. */
 int mpgemm_num_tiles(int P);
 int mpgemm_tile_info(int P, int id, int info[6]);
 
 /* The FP64-EFT tile id (1-based) that mpgemm_ex uses for an m x n x k product
- * when opts->tile is 0: of the candidates (DD: 32x32, 16x16, 8x8; TD/QD:
- * 16x16, 8x8), the first whose CTAs, dealt round-robin to the device's SMs,
+ * when opts->tile is 0: of the candidates (binary64-only: 64x64, 32x32,
+ * 16x16, 8x8; DD: 32x32, 16x16, 8x8; TD/QD: 16x16, 8x8), the first whose CTAs, dealt round-robin to the device's SMs,
  * keep at least 90% of them busy -- ctas / (sms * ceil(ctas / sms)) -- else
  * the closest.  Uses the current device's SM count (152 when there is no
  * device).  MPG_EINVAL for an unknown P or a negative dimension. */

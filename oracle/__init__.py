@@ -53,6 +53,10 @@ def _load(path):
                           vp, ctypes.c_int64, vp, ctypes.c_int64, vp, ctypes.c_int64,
                           ctypes.c_int]
     L.or_gemm.restype = ctypes.c_int
+    L.or_dgemm.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                           vp, ctypes.c_int64, vp, ctypes.c_int64, vp, ctypes.c_int64,
+                           ctypes.c_int]
+    L.or_dgemm.restype = ctypes.c_int
     return L
 
 
@@ -187,6 +191,21 @@ def gemm(prec, A, B, nthreads=1, L=None):
     C = np.zeros((P, m, n), dtype=np.float64)
     rc = L.or_gemm(P, m, n, k, _planes_ptrs(A), k, _planes_ptrs(B), n, _planes_ptrs(C), n,
                    int(nthreads))
+    assert rc == 0
+    return C
+
+
+def dgemm(A, B, nthreads=1, L=None):
+    """C = A B in plain binary64 (Eq. 1, k-sequential, one fma per term) for
+    single planes A (m, k) and B (k, n)."""
+    L = L or lib()
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    assert A.ndim == 2 and B.ndim == 2 and A.shape[1] == B.shape[0]
+    m, k = A.shape
+    n = B.shape[1]
+    C = np.zeros((m, n), dtype=np.float64)
+    rc = L.or_dgemm(m, n, k, A.ctypes.data, k, B.ctypes.data, n, C.ctypes.data, n, int(nthreads))
     assert rc == 0
     return C
 

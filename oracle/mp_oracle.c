@@ -560,3 +560,29 @@ int or_gemm(int P, int64_t m, int64_t n, int64_t k,
     }
     return 0;
 }
+
+/* Eq. 1 in plain binary64 (Sec. 1: the 53-bit format the multi-component
+ * numbers extend; Sec. 3 counts the digits a product loses): c_ij = sum_k
+ * a_ik b_kj with one fused multiply-add per term, acc = fma(a_ik, b_kj, acc),
+ * k increasing from acc = +0.  The FP64-only GEMM the DD/TD/QD products are
+ * compared with. */
+int or_dgemm(int64_t m, int64_t n, int64_t k,
+             const double *A, int64_t lda,
+             const double *B, int64_t ldb,
+             double *C, int64_t ldc, int nthreads)
+{
+    if (m < 0 || n < 0 || k < 0)
+        return -1;
+    if (nthreads < 1)
+        nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+    for (int64_t i = 0; i < m; ++i) {
+        for (int64_t j = 0; j < n; ++j) {
+            double acc = 0.0;
+            for (int64_t p = 0; p < k; ++p)
+                acc = fma(A[i * lda + p], B[p * ldb + j], acc);
+            C[i * ldc + j] = acc;
+        }
+    }
+    return 0;
+}

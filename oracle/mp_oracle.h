@@ -63,6 +63,13 @@ int or_gemm(int P, int64_t m, int64_t n, int64_t k,
             const double *const *B, int64_t ldb,
             double *const *C, int64_t ldc, int nthreads);
 
+/* The binary64-only product: C := A B (Eq. 1) with acc = fma(a_ip, b_pj, acc)
+ * for p = 0..k-1 in order from acc = +0; single row-major planes. */
+int or_dgemm(int64_t m, int64_t n, int64_t k,
+             const double *A, int64_t lda,
+             const double *B, int64_t ldb,
+             double *C, int64_t ldc, int nthreads);
+
 #ifdef __cplusplus
 }
 #endif

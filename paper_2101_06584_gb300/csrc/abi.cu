@@ -159,6 +159,7 @@ int check_gemm(const GemmArgs<P>& g)
     return MPG_OK;
 }
 
+template int check_gemm<1>(const GemmArgs<1>&);
 template int check_gemm<2>(const GemmArgs<2>&);
 template int check_gemm<3>(const GemmArgs<3>&);
 template int check_gemm<4>(const GemmArgs<4>&);
@@ -227,47 +228,51 @@ static int gemm_call(const mpgemm_opts* o, int64_t m, int64_t n, int64_t k,
         algo != MPG_ALGO_BF16_SLICES)
         return fail(MPG_EINVAL, "unknown algorithm %d", algo);
     const bool sliced = algo == MPG_ALGO_INT8_OZAKI || algo == MPG_ALGO_BF16_SLICES;
+    const int split = o ? o->split_k : 0;
+    const int levels = o ? o->strassen : 0;
+    if (P == 1 && (sliced || split > 1 || levels != 0))
+        return fail(MPG_EINVAL, "the binary64-only product (P = 1) takes no slicing, split_k or strassen option");
     cudaError_t e;
     if (k == 0) {
         e = launch_zero<P>(g, g_stream);
         return e == cudaSuccess ? MPG_OK : cuda_fail(e, "zero launch");
     }
-    if (sliced) {
-        if (o->strassen) return fail(MPG_EINVAL, "strassen applies to the FP64-EFT algorithm only");
-        return ozaki_call(g, o);
-    }
-    const int split = o ? o->split_k : 0;
-    const int levels = o ? o->strassen : 0;
-    if (levels < 0 || levels > kMaxStrassenLevels)
-        return fail(MPG_EINVAL, "strassen must be in 0..%d (got %d)", kMaxStrassenLevels, levels);
-    if (levels > 0) {
-        if (g.trans_a || g.trans_b) return fail(MPG_EUNSUPPORTED, "the Strassen form takes untransposed operands");
-        if (split > 1) return fail(MPG_EINVAL, "split_k and strassen cannot be combined");
-        const int64_t bytes = strassen_workspace_elems(P, m, n, k, levels) * 8;
-        if (bytes > 0) {
-            if (!o->workspace) return fail(MPG_EWORKSPACE, "the Strassen form needs a workspace of %lld bytes",
-                                           (long long)bytes);
-            if (reinterpret_cast<uintptr_t>(o->workspace) % 256)
-                return fail(MPG_EWORKSPACE, "workspace must be 256-byte aligned");
-            if (o->workspace_bytes < static_cast<size_t>(bytes))
-                return fail(MPG_EWORKSPACE, "workspace of %zu bytes is smaller than the %lld needed",
-                            o->workspace_bytes, (long long)bytes);
-            const Range rw{reinterpret_cast<uintptr_t>(o->workspace),
-                           reinterpret_cast<uintptr_t>(o->workspace) + static_cast<uintptr_t>(bytes)};
-            for (int c = 0; c < P; ++c) {
-                if (overlap(rw, plane_range(g.A[c], m, k, g.lda)) || overlap(rw, plane_range(g.B[c], k, n, g.ldb)) ||
-                    overlap(rw, plane_range(g.C[c], m, n, g.ldc)))
-                    return fail(MPG_EWORKSPACE, "workspace overlaps an operand");
-            }
+    if constexpr (P >= 2) {
+        if (sliced) {
+            if (o->strassen) return fail(MPG_EINVAL, "strassen applies to the FP64-EFT algorithm only");
+            return ozaki_call(g, o);
         }
-        e = launch_strassen<P>(g, levels, static_cast<double*>(o->workspace), g_stream);
-        return e == cudaSuccess ? MPG_OK : cuda_fail(e, "strassen launch");
-    }
-    if (split > 1) {
-        if (split != 2 && split != 4 && split != 8 && split != 16 && split != 32)
-            return fail(MPG_EINVAL, "split_k must be 0, 1, 2, 4, 8, 16 or 32 (got %d)", split);
-        e = launch_gemm_splitk<P>(g, split, g_stream);
-        return e == cudaSuccess ? MPG_OK : cuda_fail(e, "split-k gemm launch");
+        if (levels < 0 || levels > kMaxStrassenLevels)
+            return fail(MPG_EINVAL, "strassen must be in 0..%d (got %d)", kMaxStrassenLevels, levels);
+        if (levels > 0) {
+            if (g.trans_a || g.trans_b) return fail(MPG_EUNSUPPORTED, "the Strassen form takes untransposed operands");
+            if (split > 1) return fail(MPG_EINVAL, "split_k and strassen cannot be combined");
+            const int64_t bytes = strassen_workspace_elems(P, m, n, k, levels) * 8;
+            if (bytes > 0) {
+                if (!o->workspace) return fail(MPG_EWORKSPACE, "the Strassen form needs a workspace of %lld bytes",
+                                               (long long)bytes);
+                if (reinterpret_cast<uintptr_t>(o->workspace) % 256)
+                    return fail(MPG_EWORKSPACE, "workspace must be 256-byte aligned");
+                if (o->workspace_bytes < static_cast<size_t>(bytes))
+                    return fail(MPG_EWORKSPACE, "workspace of %zu bytes is smaller than the %lld needed",
+                                o->workspace_bytes, (long long)bytes);
+                const Range rw{reinterpret_cast<uintptr_t>(o->workspace),
+                               reinterpret_cast<uintptr_t>(o->workspace) + static_cast<uintptr_t>(bytes)};
+                for (int c = 0; c < P; ++c) {
+                    if (overlap(rw, plane_range(g.A[c], m, k, g.lda)) || overlap(rw, plane_range(g.B[c], k, n, g.ldb)) ||
+                        overlap(rw, plane_range(g.C[c], m, n, g.ldc)))
+                        return fail(MPG_EWORKSPACE, "workspace overlaps an operand");
+                }
+            }
+            e = launch_strassen<P>(g, levels, static_cast<double*>(o->workspace), g_stream);
+            return e == cudaSuccess ? MPG_OK : cuda_fail(e, "strassen launch");
+        }
+        if (split > 1) {
+            if (split != 2 && split != 4 && split != 8 && split != 16 && split != 32)
+                return fail(MPG_EINVAL, "split_k must be 0, 1, 2, 4, 8, 16 or 32 (got %d)", split);
+            e = launch_gemm_splitk<P>(g, split, g_stream);
+            return e == cudaSuccess ? MPG_OK : cuda_fail(e, "split-k gemm launch");
+        }
     }
     if (split < 0) return fail(MPG_EINVAL, "split_k must be >= 0 (got %d)", split);
     int tile = o ? o->tile : 0;
@@ -297,7 +302,7 @@ int mpgemm_set_stream(void* stream)
 
 void* mpgemm_get_stream(void) { return static_cast<void*>(g_stream); }
 
-int mpgemm_version(void) { return 101; }
+int mpgemm_version(void) { return 102; }
 
 int mp_quick_two_sum(int64_t n, const double* a, const double* b, double* s, double* e)
 { return eft_call(0, n, a, b, s, e); }
@@ -337,15 +342,25 @@ int mpgemm_qd(int64_t m, int64_t n, int64_t k, const double* const A[4], int64_t
               const double* const B[4], int64_t ldb, double* const C[4], int64_t ldc)
 { return gemm_call<4>(nullptr, m, n, k, A, lda, B, ldb, C, ldc); }
 
+int mpgemm_d(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
+             double* C, int64_t ldc)
+{
+    const double* const a[1] = {A};
+    const double* const b[1] = {B};
+    double* const c[1] = {C};
+    return gemm_call<1>(nullptr, m, n, k, a, lda, b, ldb, c, ldc);
+}
+
 int mpgemm_ex(int P, const mpgemm_opts* opts, int64_t m, int64_t n, int64_t k,
               const double* const* A, int64_t lda, const double* const* B, int64_t ldb,
               double* const* C, int64_t ldc)
 {
     switch (P) {
+    case 1: return gemm_call<1>(opts, m, n, k, A, lda, B, ldb, C, ldc);
     case 2: return gemm_call<2>(opts, m, n, k, A, lda, B, ldb, C, ldc);
     case 3: return gemm_call<3>(opts, m, n, k, A, lda, B, ldb, C, ldc);
     case 4: return gemm_call<4>(opts, m, n, k, A, lda, B, ldb, C, ldc);
-    default: clear_error(); return fail(MPG_EINVAL, "P must be 2, 3 or 4 (got %d)", P);
+    default: clear_error(); return fail(MPG_EINVAL, "P must be 1, 2, 3 or 4 (got %d)", P);
     }
 }
 
@@ -406,6 +421,7 @@ int mpgemm_dd_int8_static(int64_t m, int64_t n, int64_t k, const double* const A
 int mpgemm_num_tiles(int P)
 {
     switch (P) {
+    case 1: return num_tiles<1>();
     case 2: return num_tiles<2>();
     case 3: return num_tiles<3>();
     case 4: return num_tiles<4>();
@@ -420,10 +436,11 @@ int mpgemm_default_tile(int P, int64_t m, int64_t n, int64_t k)
         return fail(MPG_EINVAL, "m, n, k must be >= 0 (got %lld, %lld, %lld)", (long long)m, (long long)n,
                     (long long)k);
     switch (P) {
+    case 1: return default_tile<1>(m, n, k) + 1;
     case 2: return default_tile<2>(m, n, k) + 1;
     case 3: return default_tile<3>(m, n, k) + 1;
     case 4: return default_tile<4>(m, n, k) + 1;
-    default: return fail(MPG_EINVAL, "P must be 2, 3 or 4 (got %d)", P);
+    default: return fail(MPG_EINVAL, "P must be 1, 2, 3 or 4 (got %d)", P);
     }
 }
 
@@ -450,7 +467,8 @@ int mpgemm_tile_info(int P, int id, int info[6])
     clear_error();
     const int nt = mpgemm_num_tiles(P);
     if (nt == 0 || id < 1 || id > nt || !info) return fail(MPG_EINVAL, "unknown tile %d for P = %d", id, P);
-    TileInfo t = P == 2 ? tile_info<2>(id - 1) : P == 3 ? tile_info<3>(id - 1) : tile_info<4>(id - 1);
+    TileInfo t = P == 1 ? tile_info<1>(id - 1) : P == 2 ? tile_info<2>(id - 1)
+                 : P == 3 ? tile_info<3>(id - 1) : tile_info<4>(id - 1);
     info[0] = t.bm; info[1] = t.bn; info[2] = t.bk; info[3] = t.tm; info[4] = t.tn; info[5] = t.threads;
     return MPG_OK;
 }

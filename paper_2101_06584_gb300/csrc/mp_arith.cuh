@@ -547,4 +547,12 @@ __device__ __forceinline__ void mad(const Rn& f, double* acc, const double* a, c
     for (int c = 0; c < P; ++c) acc[c] = sum[c];
 }
 
+// The binary64-only product (P = 1): acc = fma(a, b, acc), one rounding per
+// term -- the plain FP64 GEMM the multi-component forms are compared with.
+template <>
+__device__ __forceinline__ void mad<1>(const Rn& f, double* acc, const double* a, const double* b)
+{
+    acc[0] = f.fma(a[0], b[0], acc[0]);
+}
+
 }  // namespace mp

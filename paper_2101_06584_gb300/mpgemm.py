@@ -14,7 +14,7 @@ import torch
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libmpgemm.so")
-P_OF = {"dd": 2, "td": 3, "qd": 4}
+P_OF = {"d": 1, "dd": 2, "td": 3, "qd": 4}   # "d": the binary64-only product
 ALGO = {"auto": 0, "fp64": 1, "int8": 2, "bf16": 3}
 
 _lib = None
@@ -61,7 +61,7 @@ def _declare(L):
     for f in ("mp_dd_add", "mp_dd_mul", "mp_td_add", "mp_td_add_merge", "mp_td_mul", "mp_td_mul_q",
               "mp_td_mul_accurate", "mp_qd_add", "mp_qd_mul", "mp_qd_add_accurate"):
         getattr(L, f).argtypes = [i64, vp, vp, vp]
-    for f in ("mpgemm_dd", "mpgemm_td", "mpgemm_qd"):
+    for f in ("mpgemm_d", "mpgemm_dd", "mpgemm_td", "mpgemm_qd"):
         getattr(L, f).argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64]
     L.mpgemm_ex.argtypes = [i, ctypes.POINTER(Opts), i64, i64, i64, vp, i64, vp, i64, vp, i64]
     L.mpgemm_workspace_size.argtypes = [i, ctypes.POINTER(Opts), i64, i64, i64]
@@ -176,6 +176,41 @@ def gemm_plain(prec, A, B, out=None):
     _bind_stream()
     fn = getattr(lib(), "mpgemm_" + prec)
     check(fn(m, n, k, planes(A), _ld(A), planes(B), _ld(B), planes(out), _ld(out)))
+    return out
+
+
+def _ld2(t):
+    """Leading dimension of a 2-D row-major plane."""
+    if t.numel() == 0 or t.shape[0] <= 1:
+        return max(t.shape[1], 1)
+    return t.stride(0)
+
+
+def gemm_fp64(A, B, out=None, trans_a=False, trans_b=False, tile=0):
+    """The binary64-only product C = op(A) op(B) of single planes (2-D float64
+    CUDA tensors, e.g. the leading plane A[0] of a DD/TD/QD operand): one fma
+    per term, k-sequential (mpgemm_d, or mpgemm_ex with P = 1 for transposes
+    and a tile choice).  Returns C (m, n)."""
+    for t, name in ((A, "A"), (B, "B")):
+        _require(t, name, None, 2)
+    m, k = (A.shape[1], A.shape[0]) if trans_a else (A.shape[0], A.shape[1])
+    kb, n = (B.shape[1], B.shape[0]) if trans_b else (B.shape[0], B.shape[1])
+    if kb != k:
+        raise ValueError("inner dimensions differ: %d vs %d" % (k, kb))
+    if out is None:
+        out = torch.empty((m, n), dtype=torch.float64, device=A.device)
+    _require(out, "out", None, 2)
+    if tuple(out.shape) != (m, n):
+        raise ValueError("out must be (%d, %d)" % (m, n))
+    _bind_stream()
+    if not trans_a and not trans_b and not tile:
+        check(lib().mpgemm_d(m, n, k, A.data_ptr(), _ld2(A), B.data_ptr(), _ld2(B),
+                             out.data_ptr(), _ld2(out)))
+    else:
+        o = Opts(int(trans_a), int(trans_b), ALGO["auto"], 0, 0, int(tile), None, 0, 0)
+        one = lambda t: (ctypes.c_void_p * 1)(t.data_ptr())
+        check(lib().mpgemm_ex(1, ctypes.byref(o), m, n, k, one(A), _ld2(A), one(B), _ld2(B),
+                              one(out), _ld2(out)))
     return out
 
 

@@ -399,7 +399,42 @@ def pin_gemm_paper(L, n=17):
         assert X.gemm_error(C, A, B, ent)["err_abs"] <= n * 2.0 ** -p
 
 
+def pin_dgemm(L, size=23):
+    """The binary64-only product (Eq. 1 in binary64, one fma per term, k
+    increasing from +0):
+    - integer matrices with |a|, |b| < 2^20 and k <= 2^10 are exact;
+    - k = 1 gives RN(a b) entry by entry;
+    - two hand-derived results.  With a = 1 + 2^-30, a^2 = 1 + 2^-29 + 2^-60:
+      [a, a] . [a, -a] = RN(a^2) then RN(RN(a^2) - a^2) = 1 + 2^-29, then
+      -2^-60 exactly; a separate multiply and add would give 0, the reversed
+      order +2^-60.  [1, 2^-53, 2^-53] . [1, 1, 1]: 1 + 2^-53 is a tie that
+      rounds to 1, twice, so 1; the reversed order gives 1 + 2^-52;
+    - random products: |c_hat - c| <= k 2^-53 (|A||B|)_ij per entry, exactly."""
+    rng = np.random.default_rng(24)
+    m, n, k = size, size + 2, size + 5
+    A = rng.integers(-(1 << 19), 1 << 19, size=(m, k)).astype(np.float64)
+    B = rng.integers(-(1 << 19), 1 << 19, size=(k, n)).astype(np.float64)
+    C = oracle.dgemm(A, B, L=L)
+    want = A.astype(object).dot(B.astype(object))
+    assert (C == want.astype(np.float64)).all(), "integer product"
+    a = rng.uniform(-1, 1, size=(m, 1))
+    b = rng.uniform(-1, 1, size=(1, n))
+    assert (oracle.dgemm(a, b, L=L) == a * b).all(), "k = 1 is one rounded product"
+    x = 1.0 + 2.0 ** -30
+    C = oracle.dgemm(np.array([[x, x]]), np.array([[x], [-x]]), L=L)
+    assert C[0, 0] == -(2.0 ** -60), ("fused accumulation in increasing k", C[0, 0])
+    C = oracle.dgemm(np.array([[1.0, 2.0 ** -53, 2.0 ** -53]]), np.ones((3, 1)), L=L)
+    assert C[0, 0] == 1.0, ("increasing k", C[0, 0])
+    A = rng.uniform(-1, 1, size=(m, k)) * np.ldexp(1.0, rng.integers(-8, 8, size=(m, k)))
+    B = rng.uniform(-1, 1, size=(k, n))
+    C = oracle.dgemm(A, B, L=L)
+    ex = X.ExactRows(A[None], B[None])
+    for i in range(m):
+        for j in range(n):
+            assert abs(Fraction(float(C[i, j])) - ex.dot(i, j)) <= k * U * ex.absdot(i, j), (i, j)
+
+
 ALL_PINS = [pin_two_sum, pin_quick_two_sum, pin_two_prod, pin_three_sums, pin_vec_sum,
             pin_vseb, pin_renorm, pin_worked, pin_op_special, pin_op_bounds,
             pin_accurate_cancellation, pin_accurate_products,
-            pin_gemm_integer, pin_gemm_bound, pin_gemm_structure, pin_gemm_paper]
+            pin_gemm_integer, pin_gemm_bound, pin_gemm_structure, pin_gemm_paper, pin_dgemm]

@@ -178,7 +178,7 @@ def test_slicing_options(L):
 
 
 def test_version(L):
-    assert L.mpgemm_version() == 101
+    assert L.mpgemm_version() == 102
 
 
 def test_tc_status_validation(L):
@@ -252,3 +252,26 @@ def test_batch_plan_rejects_bad_problem(L):
     rc = L.mpgemm_batch_plan_create(2, 2, probs, 0, ctypes.c_void_p(4 * FAKE + 8), 1 << 20, ctypes.byref(h))
     assert rc == -3
     assert L.mpgemm_batch_workspace_size(2, 2, probs) > 256
+
+
+def test_binary64_product_validation(L):
+    """mpgemm_d (and mpgemm_ex with P = 1) check their arguments like the
+    multi-component calls and take no slicing, split-K or Strassen option."""
+    from paper_2101_06584_gb300.mpgemm import Opts
+    A, B, C = FAKE, 2 * FAKE, 3 * FAKE
+    assert L.mpgemm_d(-1, 4, 4, A, 4, B, 4, C, 4) == -1
+    assert "m, n, k" in err(L)
+    assert L.mpgemm_d(8, 9, 10, A, 9, B, 9, C, 9) == -1
+    assert "lda" in err(L)
+    assert L.mpgemm_d(8, 8, 8, FAKE, 8, B, 8, FAKE + 64, 8) == -1
+    assert "overlaps A" in err(L)
+    assert L.mpgemm_d(0, 8, 8, A, 8, B, 8, C, 8) == 0
+    one = lambda a: ptrs(a)
+    for opts in (Opts(0, 0, 2, 0, 0, 0, None, 0), Opts(0, 0, 0, 4, 0, 0, None, 0),
+                 Opts(0, 0, 0, 0, 0, 0, None, 0, 1)):
+        assert L.mpgemm_ex(1, ctypes.byref(opts), 8, 8, 8, one(A), 8, one(B), 8, one(C), 8) == -1
+        assert "P = 1" in err(L)
+    assert L.mpgemm_num_tiles(1) == 4
+    info = (ctypes.c_int * 6)()
+    assert L.mpgemm_tile_info(1, 1, ctypes.byref(info)) == 0 and list(info)[:2] == [64, 64]
+    assert L.mpgemm_version() >= 102

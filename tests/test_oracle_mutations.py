@@ -66,6 +66,12 @@ MUTANTS = [
     ("gemm transposed B", "b[c] = B[c][p * ldb + j];", "b[c] = B[c][j * ldb + p];"),
     ("gemm swapped mul operands", "mp_mul(P, a, b, prod);", "mp_mul(P, b, a, prod);"),
     ("gemm skips the first term", "for (int64_t p = 0; p < k; ++p) {", "for (int64_t p = 1; p < k; ++p) {"),
+    ("dgemm multiply and add rounded separately", "acc = fma(A[i * lda + p], B[p * ldb + j], acc);",
+     "acc = acc + A[i * lda + p] * B[p * ldb + j];"),
+    ("dgemm decreasing k", "for (int64_t p = 0; p < k; ++p)\n                acc = fma(",
+     "for (int64_t p = k - 1; p >= 0; --p)\n                acc = fma("),
+    ("dgemm skips the last term", "for (int64_t p = 0; p < k; ++p)\n                acc = fma(",
+     "for (int64_t p = 0; p + 1 < k; ++p)\n                acc = fma("),
 ]
 
 # a lighter pass of every pin (fewer random cases) for each mutant
