@@ -9,7 +9,8 @@ Workloads (one "step" = one pass of the workload's kernels over its inputs):
             (bit-identical to the oracle)
   dd_small  DD GEMM 128^3, uniform inputs
   dd_int8   DD GEMM 4096^3 through the INT8 error-free slicing form (slicing +
-            tensor-core slice products + EFT accumulation), S = 13 slices
+            tensor-core slice products + EFT accumulation), S the smallest
+            slice count whose product meets n 2^-100 on sampled entries
   dd_tc     the dd_int8 product with the digits as bf16 on tcgen05 (TMEM
             accumulators, TMA staging)
   td_qd_int8, td_qd_tc  the TD and QD GEMMs of td_qd through the slicing form
@@ -27,6 +28,7 @@ other workload.  Under torchrun each rank runs its own independent problem
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -48,7 +50,6 @@ UNIT = "mad/s"
 # QD = QDmul 123 + QDadd 87.
 FP64_OPS_PER_MAD = {"dd": 20, "td": 128, "qd": 210}
 L2_FLUSH_BYTES = 256 << 20          # larger than the 129 MB L2
-INT8_SLICES = 13
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
@@ -111,6 +112,8 @@ def parse_args():
     ap.add_argument("--size", type=int, default=None, help="override the workload's m = n = k")
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the error figures (the slicing forms then take fixed slice counts)")
     ap.add_argument("--record-traffic", metavar="NCU_CSV",
                     help="record DRAM bytes per launch from an ncu --csv log (dram__bytes_read.sum, "
                          "dram__bytes_write.sum) into profiles/traffic.json and exit")
@@ -232,6 +235,209 @@ def peaks(torch, mm):
     return res
 
 
+# ---------------------------------------------------------------- accuracy
+#
+# The error of a computed product against the exact one, on sampled entries
+# (a seeded set of random entries plus whole rows).  Each exact entry
+# c_ij = sum_p sum_{c,d} a_ip[c] b_pj[d] is a sum of binary64 products; every
+# product is split exactly into two binary64 (Veltkamp's splitting and
+# Dekker's product, exact while nothing overflows or underflows -- checked),
+# and math.fsum, which returns the correctly rounded value of the exact sum of
+# its arguments, peels the exact sum into a non-overlapping expansion
+# s0 + s1 + ... (s_t the rounded remainder of the terms after s0..s_{t-1}).
+# The residual of any candidate c_hat is then fsum(s + (-c_hat)), rounded
+# once.  This is independent of the library (plain Python floats).
+
+SPLIT = 134217729.0                 # 2**27 + 1
+
+
+def _exact_products(a, b):
+    """(p, e) with a*b = p + e exactly, elementwise (Dekker's product on
+    Veltkamp's halves)."""
+    p = a * b
+    t = SPLIT * a
+    ah = t - (t - a)
+    al = a - ah
+    t = SPLIT * b
+    bh = t - (t - b)
+    bl = b - bh
+    e = ((ah * bh - p) + ah * bl + al * bh) + al * bl
+    return p, e
+
+
+def _expansion(terms, cap):
+    """Non-overlapping expansion (list of binary64) of the exact sum of terms,
+    stopped after ``cap`` components (the part left is then below about
+    2^(-53 cap) of the sum's magnitude)."""
+    out = []
+    rest = list(terms)
+    for _ in range(cap):
+        s = math.fsum(rest)
+        if s == 0.0:
+            break
+        out.append(s)
+        rest.append(-s)
+    return out
+
+
+def exact_entries_task(args):
+    """Exact expansions and sum_p |a_ip| |b_pj| for the pairs (A row r, B column
+    c): A_rows (P, R, k), B_cols (P, k, Cn), pairs [(r, c)].  Returns a list of
+    (expansion, absdot)."""
+    A_rows, B_cols, pairs = args
+    P = A_rows.shape[0]
+    ri = np.array([r for r, _ in pairs])
+    ci = np.array([c for _, c in pairs])
+    a = A_rows[:, ri, :]                              # (P, npairs, k)
+    b = np.transpose(B_cols[:, :, ci], (0, 2, 1))      # (P, npairs, k)
+    nz_a, nz_b = np.abs(a[a != 0]), np.abs(b[b != 0])
+    if nz_a.size and nz_b.size:
+        lo = nz_a.min() * nz_b.min()
+        hi = nz_a.max() * nz_b.max()
+        if lo < 2.0 ** -900 or hi > 2.0 ** 900:
+            raise ValueError("entries outside the range in which the exact products are exact")
+    parts = []
+    for c in range(P):
+        for d in range(P):
+            p, e = _exact_products(a[c], b[d])
+            parts.append(p)
+            parts.append(e)
+    terms = np.concatenate(parts, axis=1)             # (npairs, 2 P^2 k)
+    absdot = np.einsum("ik,ik->i", np.abs(a.sum(axis=0)), np.abs(b.sum(axis=0)))
+    return [(_expansion(terms[t].tolist(), P + 3), float(absdot[t])) for t in range(len(pairs))]
+
+
+def sample_entries(m, n, count, rng, full_rows=2):
+    """Seeded sample: ``count`` random (i, j) plus ``full_rows`` whole rows."""
+    ent = set()
+    for _ in range(count):
+        ent.add((int(rng.integers(m)), int(rng.integers(n))))
+    for r in rng.choice(m, size=min(full_rows, m), replace=False):
+        ent.update((int(r), j) for j in range(n))
+    return sorted(ent)
+
+
+class ExactReference:
+    """Exact values of sampled entries of A B (planes (P, m, k), (P, k, n)),
+    computed once on the host cores by a spawned process pool."""
+
+    def __init__(self, A, B, entries, pool=None):
+        self.entries = list(entries)
+        A = np.asarray(A, dtype=np.float64)
+        B = np.asarray(B, dtype=np.float64)
+        tasks = []
+        by_row = {}
+        for (i, j) in self.entries:
+            by_row.setdefault(i, []).append(j)
+        singles = []
+        for i, js in sorted(by_row.items()):
+            if len(js) >= 64:                          # a whole (or long) row: chunks of 128 columns
+                for s in range(0, len(js), 128):
+                    cols = js[s:s + 128]
+                    tasks.append((A[:, [i], :], B[:, :, cols], [(0, t) for t in range(len(cols))]))
+            else:
+                singles.extend((i, j) for j in js)
+        for s in range(0, len(singles), 16):
+            chunk = singles[s:s + 16]
+            tasks.append((A[:, [i for i, _ in chunk], :], B[:, :, [j for _, j in chunk]],
+                          [(t, t) for t in range(len(chunk))]))
+        res = pool.map(exact_entries_task, tasks) if pool is not None else map(exact_entries_task, tasks)
+        flat = [x for part in res for x in part]
+        order = [(i, j) for i, js in sorted(by_row.items()) if len(js) >= 64 for j in js] + singles
+        got = dict(zip(order, flat))
+        self.exp = [got[e][0] for e in self.entries]
+        self.absdot = np.array([got[e][1] for e in self.entries])
+        self.value = np.array([x[0] if x else 0.0 for x in self.exp])
+
+    def errors(self, C):
+        """err_abs = ||C_hat - C||_F / || |A||B| ||_F, err_rel = ||C_hat - C||_F /
+        ||C||_F and the worst entry's |c_hat - c| / (|A||B|)_ij over the
+        sample, for C_hat given as planes (Pc, m, n) (or one plane (m, n))
+        whose sampled entries are read here."""
+        ii = np.array([i for i, _ in self.entries])
+        jj = np.array([j for _, j in self.entries])
+        if isinstance(C, np.ndarray):
+            chat = (C if C.ndim == 3 else C[None])[:, ii, jj]      # (Pc, entries)
+        else:                                           # a torch tensor: gather on its device
+            import torch
+            Ct = C if C.dim() == 3 else C[None]
+            chat = Ct[:, torch.as_tensor(ii, device=Ct.device),
+                      torch.as_tensor(jj, device=Ct.device)].cpu().numpy()
+        res = np.array([math.fsum(s + [-float(x) for x in chat[:, t]])
+                        for t, s in enumerate(self.exp)])
+        num = math.sqrt(math.fsum(res * res))
+        den_abs = math.sqrt(math.fsum(self.absdot * self.absdot))
+        den_c = math.sqrt(math.fsum(self.value * self.value))
+        with np.errstate(divide="ignore", invalid="ignore"):
+            worst = np.where(self.absdot > 0, np.abs(res) / self.absdot, 0.0)
+        return {"err_abs": num / den_abs if den_abs else 0.0,
+                "err_rel": num / den_c if den_c else (0.0 if num == 0 else math.inf),
+                "max_abs": float(worst.max()) if worst.size else 0.0}
+
+
+# precision p of the normwise bound n 2^-p each product is checked against
+# (the binary64-only product: its bound is k 2^-53)
+GEMM_PBITS = {"d": 53, "dd": 100, "td": 150, "qd": 200}
+# "enabled": accuracy figures and slice-count selection run (rank 0 of a
+# single-rank run); otherwise the slicing workloads take FIXED_SLICES
+_ACC = {"pool": None, "refs": {}, "enabled": False}
+FIXED_SLICES = {"dd": 13, "td": 22, "qd": 29}
+
+
+def exact_reference(key, A, B, entries):
+    """The ExactReference of sampled entries of A B, computed once per key."""
+    if key not in _ACC["refs"]:
+        _ACC["refs"][key] = ExactReference(A, B, entries, pool=_ACC["pool"])
+    return _ACC["refs"][key]
+
+
+def accuracy_of(ref, C, prec, k, bound_factor=1.0):
+    """Errors of C against the exact product with the pass/fail bound
+    bound_factor * k 2^-p of its precision."""
+    e = ref.errors(C)
+    bound = bound_factor * k * 2.0 ** -GEMM_PBITS[prec]
+    return dict(e, bound=bound, meets_bound=bool(e["err_abs"] <= bound))
+
+
+def fp64_only_accuracy(mm, ref, A, B, k):
+    """Errors of the binary64-only product of the leading planes."""
+    return accuracy_of(ref, mm.gemm_fp64(A[0], B[0]), "d", k)
+
+
+def choose_slices(run, ref, bound, start, smax):
+    """The smallest slice count whose product meets ``bound`` (normwise, on
+    the sampled entries): from ``start`` downward while the bound holds, or
+    upward to ``smax`` when it does not hold at ``start``.  ``run(S)`` returns
+    the product.  Returns (S or None, {S: err_abs} of every count tried)."""
+    tried = {}
+
+    def err(S):
+        if S not in tried:
+            tried[S] = ref.errors(run(S))["err_abs"]
+        return tried[S]
+    S = start
+    if err(S) <= bound:
+        while S > 1 and err(S - 1) <= bound:
+            S -= 1
+        return S, tried
+    while S < smax:
+        S += 1
+        if err(S) <= bound:
+            return S, tried
+    return None, tried
+
+
+def error_pool():
+    """A spawn-started process pool over the host cores (safe after CUDA
+    initialisation, unlike fork)."""
+    import multiprocessing as mp
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    return mp.get_context("spawn").Pool(max(1, min(cores, 32)))
+
+
 # --------------------------------------------------------------- workloads
 
 class Workload:
@@ -290,6 +496,21 @@ class TdQd(Workload):
                 "per_precision_mad_s": {p: n ** 3 / (statistics.mean(launch_ms[p]) * 1e-3)
                                         for p in self.precs}}
 
+    def accuracy(self):
+        """Errors of the TD and QD products and of the binary64-only product of
+        their leading planes, on 256 sampled entries plus 2 whole rows."""
+        out = {}
+        n = self.n
+        for prec in self.precs:
+            A, B = self.host[prec]
+            ref = exact_reference(("cfg1", prec, n), A, B,
+                                  sample_entries(n, n, 256, np.random.default_rng(11 + len(prec))))
+            Ad, Bd, C = self.dev[prec]
+            self.mm.gemm_plain(prec, Ad, Bd, out=C)
+            out[prec] = dict(accuracy_of(ref, C, prec, n), fp64_only=fp64_only_accuracy(self.mm, ref, Ad, Bd, n),
+                             entries=len(ref.entries))
+        return out
+
     def e2e(self, steps, world):
         torch = self.torch
         pinned = {p: tuple(torch.from_numpy(x).pin_memory() for x in self.host[p]) for p in self.precs}
@@ -327,7 +548,16 @@ class DdSmall(Workload):
         self.B = torch.from_numpy(I.uniform(2, (n, n), rng)).cuda()
         self.C = torch.empty((2, n, n), dtype=torch.float64, device="cuda")
         self.mads = n ** 3
+        self.host = (host_of(self.A), host_of(self.B))
         self.config = {"workload": "DD GEMM m=n=k=%d, k-sequential FP64-EFT" % n, "m": n, "n": n, "k": n}
+
+    def accuracy(self):
+        """Errors of the DD product and of the binary64-only product over every entry."""
+        n = self.n
+        ref = exact_reference(("cfg0", n), *self.host, [(i, j) for i in range(n) for j in range(n)])
+        self.mm.gemm_plain("dd", self.A, self.B, out=self.C)
+        return {"dd": dict(accuracy_of(ref, self.C, "dd", n),
+                           fp64_only=fp64_only_accuracy(self.mm, ref, self.A, self.B, n), entries=n * n)}
 
     def timed_step(self, stream):
         e0, e1 = self.torch.cuda.Event(enable_timing=True), self.torch.cuda.Event(enable_timing=True)
@@ -350,16 +580,23 @@ class DdSmall(Workload):
 
 class DdInt8(Workload):
     """DD GEMM through the slicing form; engine "int8" (mma.sync s8) or "tc"
-    (the same digits as bf16 on tcgen05)."""
+    (the same digits as bf16 on tcgen05).  With S = None the slice count is
+    the smallest that meets the DD bound n 2^-100 on the sampled entries."""
     name = "dd_int8"
 
-    def __init__(self, torch, mm, I, rank, n=4096, S=INT8_SLICES, engine="int8"):
-        self.torch, self.mm, self.n, self.S, self.engine = torch, mm, n, S, engine
+    def __init__(self, torch, mm, I, rank, n=4096, S=None, engine="int8"):
+        self.torch, self.mm, self.n, self.engine = torch, mm, n, engine
         self.algo = "int8" if engine == "int8" else "bf16"
         rng = replica_rng(2, rank)
-        self.A = torch.from_numpy(I.uniform(2, (n, n), rng)).cuda()
-        self.B = torch.from_numpy(I.uniform(2, (n, n), rng)).cuda()
+        A, B = I.uniform(2, (n, n), rng), I.uniform(2, (n, n), rng)
+        self.host = (A, B)
+        self.A = torch.from_numpy(A).cuda()
+        self.B = torch.from_numpy(B).cuda()
         self.C = torch.empty((2, n, n), dtype=torch.float64, device="cuda")
+        self.search = None
+        if S is None:
+            S, self.search = self._choose(n) if _ACC["enabled"] else (FIXED_SLICES["dd"], None)
+        self.S = S
         self.ws = torch.empty(mm.workspace_size("dd", n, n, n, algo=self.algo, slices=S),
                               dtype=torch.uint8, device="cuda")
         self.mads = n ** 3
@@ -370,7 +607,25 @@ class DdInt8(Workload):
         eng = ("mma.sync s8 engine" if engine == "int8"
                else "tcgen05 engine (digits as bf16, TMEM accumulators)")
         self.config = {"workload": "DD GEMM m=n=k=%d, INT8 error-free slicing form, S=%d, %s" % (n, S, eng),
-                       "m": n, "n": n, "k": n, "slices": S, "engine": engine}
+                       "m": n, "n": n, "k": n, "slices": S, "engine": engine,
+                       "slices_rule": "smallest S meeting n 2^-100 on the sampled entries"
+                       if self.search is not None else "given"}
+
+    def reference(self):
+        n = self.n
+        return exact_reference(("cfg2", n), *self.host, sample_entries(n, n, 256, np.random.default_rng(12)))
+
+    def _choose(self, n):
+        ref = self.reference()
+
+        def run(S):
+            ws = self.torch.empty(self.mm.workspace_size("dd", n, n, n, algo=self.algo, slices=S),
+                                  dtype=self.torch.uint8, device="cuda")
+            return self.mm.gemm("dd", self.A, self.B, out=self.C, algo=self.algo, slices=S, workspace=ws)
+        S, tried = choose_slices(run, ref, n * 2.0 ** -100, 14, 16)
+        if S is None:
+            raise RuntimeError("no slice count up to 16 meets n 2^-100: %r" % tried)
+        return S, {str(k): v for k, v in sorted(tried.items())}
 
     def timed_step(self, stream):
         e0, e1 = self.torch.cuda.Event(enable_timing=True), self.torch.cuda.Event(enable_timing=True)
@@ -379,13 +634,29 @@ class DdInt8(Workload):
         e1.record(stream)
         return {"call": (e0, e1)}
 
+    def accuracy(self):
+        """Errors of the sliced product (at the chosen S), of the FP64-EFT
+        product of the same inputs and of the binary64-only product."""
+        n = self.n
+        ref = self.reference()
+        self.mm.gemm("dd", self.A, self.B, out=self.C, algo=self.algo, slices=self.S, workspace=self.ws)
+        out = {"dd": dict(accuracy_of(ref, self.C, "dd", n), slices=self.S, entries=len(ref.entries))}
+        if self.search is not None:
+            out["dd"]["err_abs_by_slices"] = self.search
+        if getattr(self, "plain_C", None) is None:
+            self.plain_C = self.mm.gemm_plain("dd", self.A, self.B)
+        out["dd"]["fp64_eft"] = accuracy_of(ref, self.plain_C, "dd", n)
+        out["dd"]["fp64_only"] = fp64_only_accuracy(self.mm, ref, self.A, self.B, n)
+        return out
+
     def roofline(self, launch_ms, pk):
         S, n = self.S, self.n
         pairs = S * (S + 1) // 2
         ops = 2.0 * pairs * n ** 3
         ms = statistics.mean(launch_ms["call"])
         ach = ops / (ms * 1e-3)
-        plain_ms = _time_call(self.torch, lambda: self.mm.gemm_plain("dd", self.A, self.B), 1)
+        self.plain_C = self.torch.empty_like(self.C)
+        plain_ms = _time_call(self.torch, lambda: self.mm.gemm_plain("dd", self.A, self.B, out=self.plain_C), 1)
         if self.engine == "int8":
             peak, src, unit, kern = (pk["mma_s8"], "measured mma.sync s8 probe at this run's clocks "
                                      "(tcgen05 has no int8 kind on sm_103a)", "Tint8op/s",
@@ -408,27 +679,69 @@ class TdQdInt8(Workload):
     """The TD and QD GEMMs of td_qd through the slicing form (engine "int8" or "tc")."""
     name = "td_qd_int8"
 
-    def __init__(self, torch, mm, I, rank, n=1024, engine="int8"):
+    def __init__(self, torch, mm, I, rank, n=1024, engine="int8", S=None):
         self.torch, self.mm, self.n, self.engine = torch, mm, n, engine
         self.algo = "int8" if engine == "int8" else "bf16"
         self.precs = ("td", "qd")
-        self.S = {"td": 22, "qd": 29}
         rng = replica_rng(1, rank)
-        self.dev = {}
+        self.dev, self.host, self.search = {}, {}, {}
         for prec in self.precs:
             P = I.P_OF[prec]
             A, B = I.cancelling_pair(P, n, n, n, rng)
-            ws = torch.empty(mm.workspace_size(prec, n, n, n, algo=self.algo, slices=self.S[prec]),
-                             dtype=torch.uint8, device="cuda")
-            self.dev[prec] = (torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(),
-                              torch.empty((P, n, n), dtype=torch.float64, device="cuda"), ws)
+            self.host[prec] = (A, B)
+            self.dev[prec] = [torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(),
+                              torch.empty((P, n, n), dtype=torch.float64, device="cuda"), None]
+        if S is None and not _ACC["enabled"]:
+            S = {p: FIXED_SLICES[p] for p in self.precs}
+        if S is None:
+            # the smallest slice count meeting n 2^-150 (TD) / n 2^-200 (QD) on the
+            # sampled entries, searched from the library's defaults 22 / 29
+            S = {}
+            for prec, start in (("td", 22), ("qd", 29)):
+                S[prec], self.search[prec] = self._choose(prec, start)
+        self.S = S
+        for prec in self.precs:
+            self.dev[prec][3] = torch.empty(mm.workspace_size(prec, n, n, n, algo=self.algo, slices=S[prec]),
+                                            dtype=torch.uint8, device="cuda")
         self.mads = len(self.precs) * n ** 3
         self.launches_per_step = 2 * (5 if n % 128 == 0 else 7) + (0 if engine == "int8" else 2)
         eng = "mma.sync s8 engine" if engine == "int8" else "tcgen05 engine"
         self.config = {"workload": "TD GEMM + QD GEMM, m=n=k=%d, INT8 error-free slicing form "
                                    "(S = %d / %d), %s, inputs of the main workload"
                                    % (n, self.S["td"], self.S["qd"], eng),
-                       "m": n, "n": n, "k": n, "slices": self.S, "engine": engine}
+                       "m": n, "n": n, "k": n, "slices": self.S, "engine": engine,
+                       "slices_rule": "smallest S meeting n 2^-150 (TD) / n 2^-200 (QD) on the sampled "
+                                      "entries" if self.search else "given"}
+
+    def reference(self, prec):
+        n = self.n
+        return exact_reference(("cfg1", prec, n), *self.host[prec],
+                               sample_entries(n, n, 256, np.random.default_rng(11 + len(prec))))
+
+    def _choose(self, prec, start):
+        n = self.n
+        A, B, C, _ = self.dev[prec]
+
+        def run(S):
+            ws = self.torch.empty(self.mm.workspace_size(prec, n, n, n, algo=self.algo, slices=S),
+                                  dtype=self.torch.uint8, device="cuda")
+            return self.mm.gemm(prec, A, B, out=C, algo=self.algo, slices=S, workspace=ws)
+        S, tried = choose_slices(run, self.reference(prec), n * 2.0 ** -GEMM_PBITS[prec], start, 40)
+        if S is None:
+            raise RuntimeError("no slice count up to 40 meets the %s bound: %r" % (prec, tried))
+        return S, {str(k): v for k, v in sorted(tried.items())}
+
+    def accuracy(self):
+        """Errors of the sliced TD and QD products at the chosen slice counts."""
+        out = {}
+        for prec in self.precs:
+            A, B, C, ws = self.dev[prec]
+            ref = self.reference(prec)
+            self.mm.gemm(prec, A, B, out=C, algo=self.algo, slices=self.S[prec], workspace=ws)
+            out[prec] = dict(accuracy_of(ref, C, prec, self.n), slices=self.S[prec], entries=len(ref.entries))
+            if self.search:
+                out[prec]["err_abs_by_slices"] = self.search[prec]
+        return out
 
     def timed_step(self, stream):
         evs = {}
@@ -580,6 +893,20 @@ class Strassen(Workload):
             evs["%s_L%d" % (prec, L)] = (e0, e1)
         return evs
 
+    def accuracy(self):
+        """Errors of the DD Strassen products (the DD 4096^3 workload's inputs)
+        against the bound 4^L n 2^-100."""
+        n = self.n["dd"]
+        A, B, C = self.dev["dd"]
+        ref = exact_reference(("cfg2", n), host_of(A), host_of(B),
+                              sample_entries(n, n, 256, np.random.default_rng(12)))
+        out = {}
+        for prec, L in self.CASES:
+            if prec == "dd":
+                self.mm.gemm(prec, A, B, out=C, strassen=L, workspace=self.ws[(prec, L)])
+                out["dd_L%d" % L] = accuracy_of(ref, C, "dd", n, bound_factor=4.0 ** L)
+        return out
+
     def roofline(self, launch_ms, pk):
         ops = {"dd": FP64_OPS_PER_MAD["dd"], "qd": FP64_OPS_PER_MAD["qd"]}
         plain = {}
@@ -714,6 +1041,10 @@ WORKLOADS = {"td_qd": TdQd, "dd_small": DdSmall, "dd_int8": DdInt8, "dd_tc": DdT
              "elementwise": Elementwise, "strassen": Strassen, "autograd_tc": AutogradTc}
 
 
+def host_of(t):
+    return t.detach().cpu().numpy()
+
+
 def _time_call(torch, fn, reps=1):
     fn()
     torch.cuda.synchronize()
@@ -773,6 +1104,9 @@ def run_ours(args):
     from paper_2101_06584_gb300 import mpgemm as mm
 
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    _ACC["enabled"] = rank == 0 and world == 1 and not args.no_accuracy
+    if _ACC["enabled"]:
+        _ACC["pool"] = error_pool()
     pk = peaks(torch, mm)
     kw = {} if args.size is None else {"n": args.size}
     w = WORKLOADS[args.workload](torch, mm, I, rank, **kw)
@@ -796,20 +1130,52 @@ def run_ours(args):
         line["e2e"] = w.e2e(args.steps, world)
     else:
         line["e2e"] = None
+    if hasattr(w, "accuracy") and _ACC["enabled"]:
+        line["accuracy"] = w.accuracy()
     if not args.no_extras and rank == 0 and args.workload == "td_qd":
         line["configs"] = extras(torch, mm, I, pk, flush)
+        line["sliced_vs_plain"] = sliced_summary(line["configs"])
+    if _ACC["pool"] is not None:
+        _ACC["pool"].close()
+        _ACC["pool"] = None
     if rank == 0 and world == 1 and not args.no_cpu and args.workload == "td_qd":
         import oracle
         rows = max(oracle.num_cpus(), w.n // 16)
         rate, cores, secs = cpu_sample_rate(w.precs, w.n, rows=rows)
+        rate1, _, secs1 = cpu_sample_rate(w.precs, w.n, rows=4, threads=1)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": "first %d rows of C for TD and QD at m=n=k=%d "
-                                          "(%.1f s on %d threads)" % (rows, w.n, secs, cores)}
+                                          "(%.1f s on %d threads)" % (rows, w.n, secs, cores),
+                                "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                                                  "sample": "first 4 rows of C for TD and QD at m=n=k=%d "
+                                                            "(%.1f s on 1 thread)" % (w.n, secs1)},
+                                "extrapolation": "rates are mads of the sampled rows over their time; "
+                                                 "the whole product takes m / rows times as long"}
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def sliced_summary(configs):
+    """The slicing form against the plain FP64-EFT kernel on the DD 4096^3
+    workload, at the slice count chosen to meet the same bound n 2^-100 that
+    the plain product meets, with the binary64-only product's error beside."""
+    out = {}
+    for name in ("dd_tc", "dd_int8"):
+        c = configs.get(name)
+        if not c:
+            continue
+        acc = c.get("accuracy", {}).get("dd", {})
+        out[name] = {"slices": c["config"]["slices"], "ms": c["ms_per_step"],
+                     "fp64_eft_ms": c["roofline"]["fp64_eft_ms"],
+                     "speedup_vs_fp64_eft": c["roofline"]["speedup_vs_fp64_eft"],
+                     "bound": acc.get("bound"), "err_abs": acc.get("err_abs"),
+                     "err_abs_fp64_eft": acc.get("fp64_eft", {}).get("err_abs"),
+                     "err_abs_fp64_only": acc.get("fp64_only", {}).get("err_abs"),
+                     "both_meet_bound": bool(acc.get("meets_bound") and acc.get("fp64_eft", {}).get("meets_bound"))}
+    return out
 
 
 def extras(torch, mm, I, pk, flush):
@@ -823,6 +1189,8 @@ def extras(torch, mm, I, pk, flush):
         rate_key = "elements_s" if name == "elementwise" else "mad_s"
         out[name] = {"config": w.config, rate_key: w.mads * steps / (total_ms * 1e-3),
                      "ms_per_step": total_ms / steps, "roofline": w.roofline(launch_ms, pk)}
+        if hasattr(w, "accuracy") and _ACC["enabled"]:
+            out[name]["accuracy"] = w.accuracy()
         del w
         torch.cuda.empty_cache()
     return out
@@ -830,12 +1198,12 @@ def extras(torch, mm, I, pk, flush):
 
 # ------------------------------------------------------------ CPU baseline
 
-def cpu_sample_rate(prec_list, size, rows, cfg=1):
-    """Oracle (as it stands) on all host cores: mad/s over the first ``rows``
-    rows of C for each precision, same inputs as the GPU workload."""
+def cpu_sample_rate(prec_list, size, rows, cfg=1, threads=None):
+    """Oracle (as it stands) on all host cores (or ``threads``): mad/s over the
+    first ``rows`` rows of C for each precision, same inputs as the GPU workload."""
     import oracle
     from paper_2101_06584_gb300 import inputs as I
-    cores = oracle.num_cpus()
+    cores = threads or oracle.num_cpus()
     mads, secs = 0, 0.0
     for prec in prec_list:
         P = I.P_OF[prec]

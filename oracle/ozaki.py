@@ -116,13 +116,19 @@ def slice_cols(planes, S, cols=None):
 
 
 def weight_products(DA, DB, S):
-    """P_w for w = 2..S+1: dict w -> integer matrix (rows of DA x rows of DB)."""
+    """P_w for w = 2..S+1: dict w -> integer matrix (rows of DA x rows of DB).
+    Exact in int64: every |digit| <= 64, so |P_w| <= S k 2^12, far below 2^63
+    for any k the slicing form accepts."""
+    k = DA.shape[2]
+    assert S * k * 64 * 64 < 2 ** 62
+    DA = DA.astype(np.int64)
+    DB = DB.astype(np.int64)
     out = {}
     for w in range(2, S + 2):
-        acc = np.zeros((DA.shape[1], DB.shape[1]), dtype=object)
+        acc = np.zeros((DA.shape[1], DB.shape[1]), dtype=np.int64)
         for s in range(max(1, w - S), min(S, w - 1) + 1):
             t = w - s
-            acc = acc + DA[s - 1].astype(object).dot(DB[t - 1].astype(object).T)
+            acc = acc + DA[s - 1].dot(DB[t - 1].T)
         out[w] = acc
     return out
 

@@ -84,3 +84,40 @@ def test_source_hash_follows_the_sources(tmp_path, monkeypatch):
         assert bench.kernel_source_hash("td_qd_1024:qd") != h0, name
         p.write_bytes(data)
     assert bench.kernel_source_hash("td_qd_1024:qd") == h0
+
+
+@pytest.mark.parametrize("prec", ["dd", "td", "qd"])
+def test_bench_errors_match_exact_arithmetic(prec):
+    """The benchmark's error figures (exact products split into binary64 and
+    peeled by math.fsum) agree with the oracle's rational arithmetic on the
+    same entries, for the oracle's product, a perturbed copy of it and the
+    leading plane alone (the FP64-only figure), on ordinary and cancelling
+    inputs; whole rows and scattered entries both take their paths."""
+    import numpy as np
+    import oracle
+    from oracle import exact as X
+    from paper_2101_06584_gb300 import inputs as I
+    P = I.P_OF[prec]
+    rng = np.random.default_rng(700 + P)
+    m, n, k = 70, 90, 37
+    for A, B in ((I.uniform(P, (m, k), rng), I.uniform(P, (k, n), rng)),
+                 I.cancelling_pair(P, m, n, k, rng)):
+        ent = bench.sample_entries(m, n, 40, np.random.default_rng(5), full_rows=1)
+        ref = bench.ExactReference(A, B, ent)
+        C = oracle.gemm(prec, A, B, nthreads=2)
+        bumped = C.copy()
+        bumped[-1] *= 1.0 + 2.0 ** -20
+        for cand in (C, bumped, C[:1], oracle.dgemm(A[0], B[0])):
+            got = ref.errors(cand)
+            want = X.gemm_error(cand if cand.ndim == 3 else cand[None], A, B, ent)
+            for key in ("err_abs", "err_rel", "max_abs"):
+                assert got[key] == pytest.approx(want[key], rel=1e-9, abs=1e-300), (key, got, want)
+
+
+def test_bench_exact_products_refuse_extreme_ranges():
+    """Products outside the range where the split products are exact raise."""
+    import numpy as np
+    A = np.full((1, 2, 3), 2.0 ** -500)
+    B = np.full((1, 3, 2), 2.0 ** -500)
+    with pytest.raises(ValueError):
+        bench.ExactReference(A, B, [(0, 0)])

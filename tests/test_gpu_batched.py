@@ -75,3 +75,30 @@ def test_autotune_and_large_batch(torch):
         want = oracle.gemm("dd", np.ascontiguousarray(A[:, rows, :]), B, nthreads=8)
         assert_bitwise(C[:, rows, :], want, "batch problem %d %s" % (i, shapes[i]))
     plan.close()
+
+
+def test_qd_512_problem_batch_of_the_benchmark(torch):
+    """The QD half of the benchmark's batch: the same generator in the same
+    order (the 512 shapes, the DD inputs, then the QD inputs), tuned plan as
+    the benchmark builds it.  Ten sampled problems and the one with the most
+    work are bit-identical to the oracle (every row of the smaller ones,
+    sampled rows of the others)."""
+    from paper_2101_06584_gb300 import mpgemm as mm
+    rng = I.rng_for(3)
+    shapes = I.batch_shapes(512, rng)
+    dd_triples, _ = _make(torch, "dd", shapes, rng)            # drawn first, as in the benchmark
+    del dd_triples
+    triples, host_in = _make(torch, "qd", shapes, rng)
+    plan = mm.BatchPlan("qd", triples, policy=None, reps=1)
+    plan.run()
+    torch.cuda.synchronize()
+    srng = np.random.default_rng(720)
+    work = [m * n * k for (m, n, k) in shapes]
+    picks = set(int(i) for i in srng.choice(len(shapes), 10, replace=False)) | {int(np.argmax(work))}
+    for i in sorted(picks):
+        A, B = host_in[i]
+        C = host(triples[i][2])
+        rows = np.arange(A.shape[1]) if A.shape[1] <= 48 else np.sort(srng.choice(A.shape[1], 12, replace=False))
+        want = oracle.gemm("qd", np.ascontiguousarray(A[:, rows, :]), B, nthreads=8)
+        assert_bitwise(C[:, rows, :], want, "qd batch problem %d %s" % (i, shapes[i]))
+    plan.close()

@@ -89,25 +89,6 @@ def test_workspace_errors(torch):
     assert e.value.code == -3
 
 
-def test_full_size_sampled(torch):
-    """DD 4096^3 (uniform inputs, seed of the 4096 workload): sampled entries
-    bit-identical to the oracle's steps and within n 2^-100 of the exact
-    product, at the slice count the benchmark uses."""
-    n = 4096
-    S = 13
-    rng = I.rng_for(2)
-    A, B = I.uniform(2, (n, n), rng), I.uniform(2, (n, n), rng)
-    C, _ = _run(torch, A, B, S)
-    srng = np.random.default_rng(620)
-    rows = sorted(set(int(x) for x in srng.integers(0, n, 3)))
-    cols = sorted(set(int(x) for x in srng.integers(0, n, 3)))
-    want, _, _ = OZ.gemm(A, B, S, rows=rows, cols=cols)
-    got = C[:, rows][:, :, cols]
-    assert_bitwise(got, want, "int8 4096 sampled")
-    err = X.gemm_error(C, A, B, [(i, j) for i in rows for j in cols])
-    assert err["err_abs"] <= n * 2.0 ** -100, err
-
-
 def test_tile_variants_agree(torch):
     """Both CTA tilings of the slice-product kernel give the same bits."""
     from paper_2101_06584_gb300 import mpgemm as mm
@@ -195,23 +176,6 @@ def test_bf16_long_ragged_k(torch):
     assert_bitwise(Cb[:, rows][:, :, cols], want, "bf16 vs oracle, long k")
 
 
-def test_bf16_full_size_sampled(torch):
-    n, S = 4096, 13
-    rng = I.rng_for(2)
-    A, B = I.uniform(2, (n, n), rng), I.uniform(2, (n, n), rng)
-    from paper_2101_06584_gb300 import mpgemm as mm
-    Ad, Bd = dev(torch, A), dev(torch, B)
-    ws = torch.empty(mm.workspace_size("dd", n, n, n, algo="bf16", slices=S), dtype=torch.uint8,
-                     device="cuda")
-    C = host(mm.gemm("dd", Ad, Bd, algo="bf16", slices=S, workspace=ws))
-    assert host(ws[:4]).view(np.int32)[0] == 0, "tcgen05 kernel reported a timeout"
-    srng = np.random.default_rng(650)
-    rows = sorted(set(int(x) for x in srng.integers(0, n, 2)))
-    cols = sorted(set(int(x) for x in srng.integers(0, n, 2)))
-    want, _, _ = OZ.gemm(A, B, S, rows=rows, cols=cols)
-    assert_bitwise(C[:, rows][:, :, cols], want, "bf16 4096 sampled")
-
-
 @pytest.mark.parametrize("prec,S", [("td", 1), ("td", 22), ("td", 40), ("qd", 5), ("qd", 29), ("qd", 40)])
 def test_td_qd_bitwise(torch, prec, S):
     """TD/QD slicing forms: the result is bit-identical to the oracle's steps
@@ -234,31 +198,6 @@ def test_td_qd_bitwise(torch, prec, S):
     gsa = w[:S * mp * kp].view(np.int8).reshape(S, mp, kp)
     assert (gsa[:, :m, :k] == DA).all()
     assert (w[offSig:offSig + 4 * m].view(np.int32) == sig).all()
-
-
-@pytest.mark.parametrize("prec", ["td", "qd"])
-@pytest.mark.parametrize("algo", ["int8", "bf16"])
-def test_td_qd_full_size_sampled(torch, prec, algo):
-    """TD/QD 1024^3 on the cancelling ill-scaled inputs of the main workload,
-    both engines (the tcgen05 one on 64 CTA-pair tiles): sampled entries
-    bit-identical to the oracle's steps and within n 2^-p of the exact product
-    at the default slice counts."""
-    from paper_2101_06584_gb300 import mpgemm as mm
-    P = I.P_OF[prec]
-    n = 1024
-    A, B = I.cancelling_pair(P, n, n, n, I.rng_for(1))
-    ws = torch.empty(mm.workspace_size(prec, n, n, n, algo=algo), dtype=torch.uint8, device="cuda")
-    C = host(mm.gemm(prec, dev(torch, A), dev(torch, B), algo=algo, workspace=ws))
-    if algo == "bf16":
-        assert host(ws[:4]).view(np.int32)[0] == 0, "tcgen05 kernel reported a timeout"
-    S = {"td": 22, "qd": 29}[prec]
-    srng = np.random.default_rng(670 + P)
-    rows = sorted(set(int(x) for x in srng.integers(0, n, 2)))
-    cols = sorted(set(int(x) for x in srng.integers(0, n, 2)))
-    want, _, _ = OZ.gemm(A, B, S, rows=rows, cols=cols)
-    assert_bitwise(C[:, rows][:, :, cols], want, "%s %s 1024 sampled" % (prec, algo))
-    err = X.gemm_error(C, A, B, [(i, j) for i in rows for j in cols])
-    assert err["err_abs"] <= n * 2.0 ** -{"td": 150, "qd": 200}[prec], err
 
 
 @pytest.mark.parametrize("prec,S", [("td", 22), ("qd", 29), ("dd", 3)])
@@ -386,3 +325,48 @@ def test_tc_status(torch):
     assert "loaded stage" in mm.lib().mpgemm_last_error().decode()
     mm.gemm("dd", dev(torch, A), dev(torch, B), algo="bf16", workspace=ws)
     assert mm.tc_status(ws) == 0                       # every call clears the header first
+
+
+def _workload_inputs(prec, n):
+    """The benchmark's inputs: DD from the 4096 workload's seed (uniform A
+    then B); TD and QD from the main workload's seed, TD drawn first."""
+    if prec == "dd":
+        rng = I.rng_for(2)
+        return I.uniform(2, (n, n), rng), I.uniform(2, (n, n), rng)
+    rng = I.rng_for(1)
+    pair = I.cancelling_pair(3, n, n, n, rng)
+    return pair if prec == "td" else I.cancelling_pair(4, n, n, n, rng)
+
+
+@pytest.mark.parametrize("prec,n,S", [("dd", 4096, 13), ("td", 1024, 22), ("qd", 1024, 29)])
+def test_full_size_both_engines(torch, prec, n, S):
+    """The slicing form at the benchmark's full sizes and inputs, in its launch
+    configuration, on both engines:
+    - the tcgen05 engine (CTA pairs for DD) equals the int8 engine on every
+      one of the n^2 entries, compared on the device;
+    - a 16 x 16 grid of random rows and columns (256 entries) is bit-identical
+      to the oracle's steps;
+    - two whole rows and the grid are within n 2^-p of the exact product."""
+    from paper_2101_06584_gb300 import mpgemm as mm
+    P = I.P_OF[prec]
+    A, B = _workload_inputs(prec, n)
+    Ad, Bd = dev(torch, A), dev(torch, B)
+    out = {}
+    for algo in ("int8", "bf16"):
+        ws = torch.empty(mm.workspace_size(prec, n, n, n, algo=algo, slices=S), dtype=torch.uint8, device="cuda")
+        out[algo] = mm.gemm(prec, Ad, Bd, algo=algo, slices=S, workspace=ws)
+        if algo == "bf16":
+            assert mm.tc_status(ws) == 0, "tcgen05 kernel reported a timeout"
+        del ws
+    diff = int((out["int8"].view(torch.int64) != out["bf16"].view(torch.int64)).sum())
+    assert diff == 0, "%d of %d values differ between the engines" % (diff, P * n * n)
+    C = host(out["bf16"])
+    srng = np.random.default_rng(620 + P)
+    rows = sorted(int(x) for x in srng.choice(n, 16, replace=False))
+    cols = sorted(int(x) for x in srng.choice(n, 16, replace=False))
+    want, _, _ = OZ.gemm(A, B, S, rows=rows, cols=cols)
+    assert_bitwise(C[:, rows][:, :, cols], want, "%s %d grid of 256 entries" % (prec, n))
+    full = sorted(int(x) for x in srng.choice(n, 2, replace=False))
+    ent = sorted({(i, j) for i in full for j in range(n)} | {(i, j) for i in rows for j in cols})
+    err = X.gemm_error(C, A, B, ent)
+    assert err["err_abs"] <= n * 2.0 ** -{"dd": 100, "td": 150, "qd": 200}[prec], err
