@@ -570,12 +570,16 @@ class DdSmall(Workload):
         ach = self.mads * 20 / (statistics.mean(launch_ms["dd"]) * 1e-3)
         # the split-K variant for reference (not bit-identical, within bound)
         ms = _time_call(self.torch, lambda: self.mm.gemm("dd", self.A, self.B, out=self.C, split_k=8), 20)
-        return {"bound": "alu", "kernel": "gemm_kseq_kernel<2,8,8,16,1,1> (DD, one entry per thread)",
+        ti = self.mm.tile_info("dd", self.mm.default_tile("dd", self.n, self.n, self.n))
+        kern = ("gemm_flat_kernel<2> (one output per thread, warps of outputs dealt to one CTA per SM)"
+                if ti["bk"] == 0 else "gemm_kseq_kernel<2,%d,%d,%d,%d,%d>" % (ti["bm"], ti["bn"], ti["bk"],
+                                                                               ti["tm"], ti["tn"]))
+        return {"bound": "alu", "kernel": kern,
                 "achieved": ach / 1e12, "peak": pk["dfma"] / 1e12, "unit": "TFP64op/s",
                 "frac": ach / pk["dfma"], "traffic": None, "ops_per_unit": 20,
                 "unit_of_work": "DD multiply-add", "units_per_launch": self.mads,
-                "note": "256 CTAs of 64 threads (16K entries, about one warp per SM sub-partition); "
-                        "warp split-K 8 runs at %.3g mad/s" % (self.mads / (ms * 1e-3))}
+                "note": "16K entries = 512 warps, at most 4 per SM; "
+                        "warp split-K 8 (not k-sequential) runs at %.3g mad/s" % (self.mads / (ms * 1e-3))}
 
 
 class DdInt8(Workload):

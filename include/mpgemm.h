@@ -345,15 +345,22 @@ int mpgemm_batch_autotune(int P, int count, const mpgemm_problem *problems, void
  * allocate device memory -- code running inside a host framework that owns
  * all device memory through its own pool and forbids raw allocations, or a
  * latency-critical loop that cannot afford cudaMalloc's implicit
- * synchronisation -- so it allocates nothing and calls no allocating routine.
+ * synchronisation -- so it allocates no device memory and calls no cudaMalloc,
+ * cudaFree or allocating library routine.
  * Its scratch is a fixed 32 MiB array inside the library, present on every
  * device that loads it until the process exits.  Products whose scratch
  * (mpgemm_workspace_size with algo MPG_ALGO_INT8_OZAKI) exceeds 32 MiB are
  * rejected with MPG_EWORKSPACE before anything is launched; e.g. DD
  * 1024 x 1024 x 1024 with 14 slices fits.  slices = 0 means 14.
- * The first call on a device looks up the array's device address once
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call uses the same array and each call
+ * First-call work: the first call in a device's context looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current), and the
+ * first call of each host thread on a device creates the stream on which op(B)
+ * is sliced and its two fork/join events (driver resources, not device
+ * memory).  Make those first calls before any stream capture and outside
+ * latency-critical loops.  A device reset (cudaDeviceReset) ends the context
+ * the address and the stream belong to; the library notices the new context
+ * (by its id) and repeats that first-call work on the next call, which should
+ * then also come before any capture.  Every call uses the same array and each call
  * writes every scratch byte it reads, so a call never depends on what an
  * earlier one left there; but calls whose execution overlaps on the GPU
  * (different streams, or different host threads without ordering) race on
@@ -365,13 +372,17 @@ int mpgemm_dd_int8_static(int64_t m, int64_t n, int64_t k,
 
 /* Number of FP64-EFT tile configurations for precision P (1..4), and a description
  * of configuration id (BM, BN, BK, TM, TN, threads); returns MPG_EINVAL for
- * an unknown id. */
+ * an unknown id.  The last id of every precision is the flat kernel, described
+ * as (1, 1, 0, 1, 1, 0): one thread per output, the outputs dealt in warps of 32
+ * to one CTA per SM, operands read from L1/L2 without staging. */
 int mpgemm_num_tiles(int P);
 int mpgemm_tile_info(int P, int id, int info[6]);
 
 /* The FP64-EFT tile id (1-based) that mpgemm_ex uses for an m x n x k product
- * when opts->tile is 0: of the candidates (binary64-only: 64x64, 32x32,
- * 16x16, 8x8; DD: 32x32, 16x16, 8x8; TD/QD: 16x16, 8x8), the first whose CTAs, dealt round-robin to the device's SMs,
+ * when opts->tile is 0: the flat kernel when dealing the ceil(m n / 32) warps
+ * of outputs to the device's SMs gives each at most 8; otherwise, of the
+ * candidates (binary64-only: 64x64, 32x32, 16x16, 8x8; DD: 32x32, 16x16, 8x8;
+ * TD/QD: 16x16, 8x8), the first whose CTAs, dealt round-robin to the device's SMs,
  * keep at least 90% of them busy -- ctas / (sms * ceil(ctas / sms)) -- else
  * the closest.  Uses the current device's SM count (152 when there is no
  * device).  MPG_EINVAL for an unknown P or a negative dimension. */

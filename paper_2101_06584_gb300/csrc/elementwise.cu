@@ -51,6 +51,50 @@ __global__ void __launch_bounds__(256) vec_kernel(const VecArgs<P> a)
     }
 }
 
+// DD add / mul with two adjacent elements per thread and iteration: the four
+// operand planes are read as double2 (16-byte loads, 512 contiguous bytes per
+// warp and plane) and both elements' loads are issued before either result is
+// stored, so each thread keeps twice the bytes in flight.  A DD operation is
+// only 9-11 FP64 operations per 48 bytes, the least work per byte of all the
+// elementwise operations, and one element per thread leaves the FP64 pipe
+// waiting on memory.  Requires 16-byte aligned planes (checked by the host);
+// an odd last element is done by one thread with scalar loads.
+template <int OP>
+__global__ void __launch_bounds__(256) vec_dd_x2_kernel(const VecArgs<2> a)
+{
+    const mp::Rn f = mp::make_rn();
+    const int64_t pairs = a.n >> 1;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    const double2* x0 = reinterpret_cast<const double2*>(a.x[0]);
+    const double2* x1 = reinterpret_cast<const double2*>(a.x[1]);
+    const double2* y0 = reinterpret_cast<const double2*>(a.y[0]);
+    const double2* y1 = reinterpret_cast<const double2*>(a.y[1]);
+    double2* r0 = reinterpret_cast<double2*>(a.r[0]);
+    double2* r1 = reinterpret_cast<double2*>(a.r[1]);
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < pairs; i += stride) {
+        const double2 u0 = x0[i], u1 = x1[i], v0 = y0[i], v1 = y1[i];
+        double xa[2] = {u0.x, u1.x}, ya[2] = {v0.x, v1.x}, ra[2];
+        double xb[2] = {u0.y, u1.y}, yb[2] = {v0.y, v1.y}, rb[2];
+        if constexpr (OP == 0) {
+            mp::dd_add(f, xa, ya, ra);
+            mp::dd_add(f, xb, yb, rb);
+        } else {
+            mp::dd_mul(f, xa, ya, ra);
+            mp::dd_mul(f, xb, yb, rb);
+        }
+        r0[i] = make_double2(ra[0], rb[0]);
+        r1[i] = make_double2(ra[1], rb[1]);
+    }
+    if ((a.n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        const int64_t t = a.n - 1;
+        double x[2] = {a.x[0][t], a.x[1][t]}, y[2] = {a.y[0][t], a.y[1][t]}, r[2];
+        if constexpr (OP == 0) mp::dd_add(f, x, y, r);
+        else mp::dd_mul(f, x, y, r);
+        a.r[0][t] = r[0];
+        a.r[1][t] = r[1];
+    }
+}
+
 template <int W>
 __global__ void __launch_bounds__(256)
 eft_kernel(int64_t n, const double* a, const double* b, double* s,
@@ -89,6 +133,18 @@ cudaError_t launch_vec(int op, int64_t n, const double* const* x, const double* 
         a.r[c] = r[c];
     }
     a.n = n;
+    if constexpr (P == 2) {
+        bool aligned = true;
+        for (int c = 0; c < P; ++c)
+            aligned = aligned && (reinterpret_cast<uintptr_t>(x[c]) | reinterpret_cast<uintptr_t>(y[c]) |
+                                  reinterpret_cast<uintptr_t>(r[c])) % 16 == 0;
+        if (aligned && (op == 0 || op == 1)) {
+            const unsigned grid2 = grid_for(n / 2 > 0 ? n / 2 : 1);
+            if (op == 0) vec_dd_x2_kernel<0><<<grid2, 256, 0, s>>>(a);
+            else vec_dd_x2_kernel<1><<<grid2, 256, 0, s>>>(a);
+            return cudaGetLastError();
+        }
+    }
     const unsigned grid = grid_for(n);
     // op codes: 0 add, 1 mul (the GEMM's pair for P); 2 TDadd (Alg. 3),
     // 3 TDmulq, 4 accurate TD product; 5 accurate QD addition

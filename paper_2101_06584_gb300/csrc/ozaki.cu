@@ -1716,7 +1716,38 @@ static __device__ __align__(256) unsigned char g_static_scratch[kOzakiStaticScra
 namespace {
 std::mutex g_static_mu;
 void* g_static_ptr[64] = {nullptr};
+unsigned long long g_static_ctx[64] = {0};
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
 }  // namespace
+
+// Unique id of the calling thread's current CUDA context, 0 if there is none
+// or the driver cannot say.  A device reset ends the primary context; the
+// next one gets a new id, which is how the caches below notice that the
+// handles and addresses they hold belong to a context that is gone.
+static unsigned long long current_context_id()
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+    });
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    unsigned long long id = 0;
+    return get_id(ctx, &id) == CUDA_SUCCESS ? id : 0;
+}
 
 cudaError_t ozaki_static_scratch(void** out)
 {
@@ -1725,13 +1756,17 @@ cudaError_t ozaki_static_scratch(void** out)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_ptr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_static_ptr[dev] || ctx == 0 || ctx != g_static_ctx[dev]) {
         // In host code the array's name is only a stand-in: the kernels need
-        // the device address, looked up once per device with it current.
+        // the device address, looked up with the device current -- once per
+        // context (again after a device reset replaced the context, and on
+        // every call if the context's id cannot be read).
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) return e;
         g_static_ptr[dev] = p;
+        g_static_ctx[dev] = current_context_id();
     }
     *out = g_static_ptr[dev];
     return cudaSuccess;
@@ -1789,6 +1824,7 @@ static cudaError_t slice_operand(const Planes<P>& pl, int64_t count, int64_t len
 struct SideStream {
     cudaStream_t s = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
+    unsigned long long ctx = 0;     // the context they were created in
     ~SideStream()
     {
         // at thread exit; errors (e.g. a runtime already unloaded) are moot
@@ -1806,11 +1842,19 @@ static cudaError_t side_stream(SideStream** out)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     SideStream& ss = per_dev[dev];
+    const unsigned long long ctx = current_context_id();
+    if (ss.s && ctx != 0 && ctx != ss.ctx) {
+        // created in a context that a device reset has ended: the handles
+        // went with it, so they are dropped, not destroyed
+        ss.s = nullptr;
+        ss.fork = ss.join = nullptr;
+    }
     if (!ss.s) {
         e = cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming);
         if (e != cudaSuccess) return e;
+        ss.ctx = current_context_id();
     }
     *out = &ss;
     return cudaSuccess;

@@ -119,3 +119,33 @@ def test_empty_vector(torch):
     z = torch.empty((2, 0), dtype=torch.float64, device="cuda")
     r = mpgemm.vec("dd", "add", z, z)
     assert r.shape == (2, 0)
+
+
+@pytest.mark.parametrize("op", ["add", "mul"])
+@pytest.mark.parametrize("n", [1, 2, 3, 64, 1_000_003, 1_000_004])
+def test_dd_paired_path(torch, op, n):
+    """DD add and mul on 16-byte aligned planes take the two-elements-per-
+    thread kernel (double2 loads; an odd last element on its own), also in
+    place and with unaligned planes (the one-element kernel): bit-identical
+    to the oracle in every case."""
+    from paper_2101_06584_gb300 import mpgemm
+    rng = np.random.default_rng(250 + n % 97)
+    x = I.random_mp(2, n, rng, spread=30)
+    y = I.random_mp(2, n, rng, spread=30)
+    y[:, : n // 3] = I.expand(-x[0, : n // 3] * (1 + np.ldexp(1.0, -45)), 2, rng)
+    want = oracle.vec_op("dd", op, x, y)
+    pad = n + (n % 2)                                 # an even plane stride keeps both planes aligned
+    X = torch.zeros((2, pad), dtype=torch.float64, device="cuda")
+    Y = torch.zeros((2, pad), dtype=torch.float64, device="cuda")
+    X[:, :n] = dev(torch, x)
+    Y[:, :n] = dev(torch, y)
+    out = torch.full((2, pad), 7.0, dtype=torch.float64, device="cuda")
+    mpgemm.vec("dd", op, X[:, :n], Y[:, :n], out=out[:, :n])
+    assert_bitwise(host(out[:, :n]), want, "dd %s aligned n=%d" % (op, n))
+    assert (host(out[:, n:]) == 7.0).all()
+    mpgemm.vec("dd", op, X[:, :n], Y[:, :n], out=X[:, :n])          # in place
+    assert_bitwise(host(X[:, :n]), want, "dd %s in place n=%d" % (op, n))
+    Xu = torch.zeros((2, pad + 1), dtype=torch.float64, device="cuda")
+    Xu[:, 1:n + 1] = dev(torch, x)                    # planes on an 8-byte boundary
+    mpgemm.vec("dd", op, Xu[:, 1:n + 1], Y[:, :n], out=out[:, :n])
+    assert_bitwise(host(out[:, :n]), want, "dd %s unaligned n=%d" % (op, n))

@@ -68,3 +68,33 @@ def test_oversized_product_is_refused(torch):
     rc = L.mpgemm_dd_int8_static(n, n, n, mm.planes(A), n, mm.planes(A), n, mm.planes(C), n, 14)
     assert rc == -3
     assert b"fixed array" in L.mpgemm_last_error()
+
+
+def test_back_to_back_calls_on_one_stream(torch):
+    """Two different products issued back to back on one stream, with a single
+    synchronisation at the end: the second call reuses the array while the
+    first may still be queued, so they are ordered only by the stream (op(B)
+    of each is sliced on a side stream forked from and joined back to it).
+    Both results equal the workspace entry's bit for bit."""
+    from paper_2101_06584_gb300 import mpgemm as mm
+    rng = np.random.default_rng(910)
+    shapes = ((300, 260, 250, 14), (130, 190, 170, 9))
+    ops = []
+    for (m, n, k, S) in shapes:
+        A = I.ill_scaled(2, (m, k), rng)
+        B = I.uniform(2, (k, n), rng)
+        ops.append((dev(torch, A), dev(torch, B), S))
+    wants = [host(_with_workspace(torch, Ad, Bd, S)) for Ad, Bd, S in ops]
+    torch.cuda.synchronize()
+    L = mm.lib()
+    mm._bind_stream()
+    outs = []
+    for Ad, Bd, S in ops:
+        m, k = Ad.shape[1], Ad.shape[2]
+        n = Bd.shape[2]
+        C = torch.full((2, m, n), float("nan"), dtype=torch.float64, device="cuda")
+        mm.check(L.mpgemm_dd_int8_static(m, n, k, mm.planes(Ad), k, mm.planes(Bd), n, mm.planes(C), n, S))
+        outs.append(C)
+    torch.cuda.synchronize()
+    for (m, n, k, S), C, want in zip(shapes, outs, wants):
+        assert_bitwise(host(C), want, "back to back %s" % ((m, n, k, S),))
