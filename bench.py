@@ -571,9 +571,7 @@ class DdSmall(Workload):
         # the split-K variant for reference (not bit-identical, within bound)
         ms = _time_call(self.torch, lambda: self.mm.gemm("dd", self.A, self.B, out=self.C, split_k=8), 20)
         ti = self.mm.tile_info("dd", self.mm.default_tile("dd", self.n, self.n, self.n))
-        kern = ("gemm_flat_kernel<2> (one output per thread, warps of outputs dealt to one CTA per SM)"
-                if ti["bk"] == 0 else "gemm_kseq_kernel<2,%d,%d,%d,%d,%d>" % (ti["bm"], ti["bn"], ti["bk"],
-                                                                               ti["tm"], ti["tn"]))
+        kern = "gemm_kseq_kernel<2,%d,%d,%d,%d,%d>" % (ti["bm"], ti["bn"], ti["bk"], ti["tm"], ti["tn"])
         return {"bound": "alu", "kernel": kern,
                 "achieved": ach / 1e12, "peak": pk["dfma"] / 1e12, "unit": "TFP64op/s",
                 "frac": ach / pk["dfma"], "traffic": None, "ops_per_unit": 20,

@@ -372,17 +372,13 @@ int mpgemm_dd_int8_static(int64_t m, int64_t n, int64_t k,
 
 /* Number of FP64-EFT tile configurations for precision P (1..4), and a description
  * of configuration id (BM, BN, BK, TM, TN, threads); returns MPG_EINVAL for
- * an unknown id.  The last id of every precision is the flat kernel, described
- * as (1, 1, 0, 1, 1, 0): one thread per output, the outputs dealt in warps of 32
- * to one CTA per SM, operands read from L1/L2 without staging. */
+ * an unknown id. */
 int mpgemm_num_tiles(int P);
 int mpgemm_tile_info(int P, int id, int info[6]);
 
 /* The FP64-EFT tile id (1-based) that mpgemm_ex uses for an m x n x k product
- * when opts->tile is 0: the flat kernel when dealing the ceil(m n / 32) warps
- * of outputs to the device's SMs gives each at most 8; otherwise, of the
- * candidates (binary64-only: 64x64, 32x32, 16x16, 8x8; DD: 32x32, 16x16, 8x8;
- * TD/QD: 16x16, 8x8), the first whose CTAs, dealt round-robin to the device's SMs,
+ * when opts->tile is 0: of the candidates (binary64-only: 64x64, 32x32,
+ * 16x16, 8x8; DD: 32x32, 16x16, 8x8; TD/QD: 16x16, 8x8), the first whose CTAs, dealt round-robin to the device's SMs,
  * keep at least 90% of them busy -- ctas / (sms * ceil(ctas / sms)) -- else
  * the closest.  Uses the current device's SM count (152 when there is no
  * device).  MPG_EINVAL for an unknown P or a negative dimension. */

@@ -280,7 +280,7 @@ static int gemm_call(const mpgemm_opts* o, int64_t m, int64_t n, int64_t k,
     else tile -= 1;
     if (tile >= num_tiles<P>()) return fail(MPG_EINVAL, "tile id %d out of range", tile + 1);
     const TileInfo ti = tile_info<P>(tile);
-    if (ti.bk > 0 && ((n + ti.bn - 1) / ti.bn > 2147483647LL || (m + ti.bm - 1) / ti.bm > 65535LL))
+    if ((n + ti.bn - 1) / ti.bn > 2147483647LL || (m + ti.bm - 1) / ti.bm > 65535LL)
         return fail(MPG_EINVAL, "matrix too large for the grid of tile %d", tile + 1);
     e = launch_gemm_kseq<P>(g, tile, g_stream);
     return e == cudaSuccess ? MPG_OK : cuda_fail(e, "gemm launch");

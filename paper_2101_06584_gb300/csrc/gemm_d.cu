@@ -14,7 +14,6 @@ const TileInfo kTiles[] = {
     {32, 32, 16, 2, 2, 256},
     {16, 16, 16, 1, 1, 256},
     {8, 8, 16, 1, 1, 64},
-    kFlatTile,
 };
 constexpr int kNumTiles = static_cast<int>(sizeof(kTiles) / sizeof(kTiles[0]));
 }  // namespace
@@ -30,7 +29,6 @@ TileInfo tile_info<P>(int t) { return kTiles[t]; }
 template <>
 int default_tile<P>(int64_t m, int64_t n, int64_t)
 {
-    if (flat_is_default(m, n)) return 4;
     return pick_tile<P>(m, n, {0, 1, 2, 3});
 }
 
@@ -42,7 +40,6 @@ cudaError_t launch_gemm_kseq<P>(const GemmArgs<P>& g, int tile, cudaStream_t s)
     case 1: return launch_kseq_cfg<P, 32, 32, 16, 2, 2>(g, s);
     case 2: return launch_kseq_cfg<P, 16, 16, 16, 1, 1>(g, s);
     case 3: return launch_kseq_cfg<P, 8, 8, 16, 1, 1>(g, s);
-    case 4: return launch_flat_cfg<P>(g, s);
     default: return cudaErrorInvalidValue;
     }
 }

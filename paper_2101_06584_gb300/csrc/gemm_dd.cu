@@ -11,7 +11,6 @@ const TileInfo kTiles[] = {
     {64, 32, 16, 2, 2, 512},
     {64, 64, 16, 4, 4, 256},
     {8, 8, 16, 1, 1, 64},
-    kFlatTile,
 };
 constexpr int kNumTiles = static_cast<int>(sizeof(kTiles) / sizeof(kTiles[0]));
 }  // namespace
@@ -28,7 +27,6 @@ TileInfo tile_info<P>(int t) { return kTiles[t]; }
 template <>
 int default_tile<P>(int64_t m, int64_t n, int64_t)
 {
-    if (flat_is_default(m, n)) return 6;
     return pick_tile<P>(m, n, {0, 1, 5});
 }
 
@@ -42,7 +40,6 @@ cudaError_t launch_gemm_kseq<P>(const GemmArgs<P>& g, int tile, cudaStream_t s)
     case 3: return launch_kseq_cfg<P, 64, 32, 16, 2, 2>(g, s);
     case 4: return launch_kseq_cfg<P, 64, 64, 16, 4, 4>(g, s);
     case 5: return launch_kseq_cfg<P, 8, 8, 16, 1, 1>(g, s);
-    case 6: return launch_flat_cfg<P>(g, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -181,72 +181,6 @@ gemm_splitk_warp_kernel(const GemmArgs<P> g)
     }
 }
 
-// Flat k-sequential kernel for products whose m*n outputs leave the tiled
-// kernels' CTAs unevenly spread over the SMs: the outputs are cut into warps
-// of 32 consecutive entries (row-major), the warps are dealt out in equal
-// contiguous runs to the CTAs (one CTA per SM), and every thread accumulates
-// its entry over p = 0..k-1 in order reading its operands straight from
-// L1/L2 -- a warp shares a_ip (broadcast) and reads consecutive b_pj, so there
-// is no staging and no barrier.  Same result bits as every other tile.
-template <int P>
-__global__ void __launch_bounds__(256) gemm_flat_kernel(const GemmArgs<P> g)
-{
-    const mp::Rn f = mp::make_rn();
-    const int64_t total = g.m * g.n;
-    const int64_t warps = (total + 31) / 32;
-    const int64_t per = (warps + gridDim.x - 1) / gridDim.x;
-    const int64_t w0 = static_cast<int64_t>(blockIdx.x) * per;
-    const int64_t w1 = w0 + per < warps ? w0 + per : warps;
-    const int lane = threadIdx.x & 31;
-    for (int64_t w = w0 + (threadIdx.x >> 5); w < w1; w += blockDim.x >> 5) {
-        const int64_t o = w * 32 + lane;
-        if (o >= total) continue;
-        const int64_t i = o / g.n, j = o % g.n;
-        double acc[P];
-#pragma unroll
-        for (int c = 0; c < P; ++c) acc[c] = 0.0;
-#pragma unroll 4
-        for (int64_t p = 0; p < g.k; ++p) {
-            const int64_t offa = g.trans_a ? p * g.lda + i : i * g.lda + p;
-            const int64_t offb = g.trans_b ? j * g.ldb + p : p * g.ldb + j;
-            double a[P], b[P];
-#pragma unroll
-            for (int c = 0; c < P; ++c) {
-                a[c] = __ldg(g.A[c] + offa);
-                b[c] = __ldg(g.B[c] + offb);
-            }
-            mp::mad<P>(f, acc, a, b);
-        }
-#pragma unroll
-        for (int c = 0; c < P; ++c) g.C[c][i * g.ldc + j] = acc[c];
-    }
-}
-
-template <int P>
-cudaError_t launch_flat_cfg(const GemmArgs<P>& g, cudaStream_t s)
-{
-    const int64_t warps = (g.m * g.n + 31) / 32;
-    const int64_t sms = num_sms();
-    const int64_t grid = warps < sms ? warps : sms;
-    const int64_t per = (warps + grid - 1) / grid;
-    const int threads = static_cast<int>(32 * (per < 8 ? per : 8));
-    gemm_flat_kernel<P><<<static_cast<unsigned>(grid), threads, 0, s>>>(g);
-    return cudaGetLastError();
-}
-
-// The flat kernel's tile entry: bk = 0 marks it.
-constexpr TileInfo kFlatTile = {1, 1, 0, 1, 1, 0};
-
-// Whether the flat kernel is the default for an m x n product: when dealing
-// its warps of outputs to the SMs gives each at most eight (one CTA of at most
-// 256 threads per SM) -- too few outputs for the tiled kernels' staging to pay.
-inline bool flat_is_default(int64_t m, int64_t n)
-{
-    const int64_t warps = (m * n + 31) / 32;
-    const int64_t sms = num_sms();
-    return warps > 0 && (warps + sms - 1) / sms <= 8;
-}
-
 template <int P>
 __global__ void zero_kernel(const GemmArgs<P> g)
 {

@@ -790,23 +790,27 @@ namespace tc {
 constexpr int BM = 128;
 constexpr int KE = 64;                                   // box width in bf16 elements (128 bytes)
 constexpr int KB = 2;                                    // boxes per stage: 128 values of k
-constexpr int STAGES = 4;
+constexpr int STAGES = 3;
 constexpr int A_BYTES = BM * KE * 2;                     // one A box, 16 KB
 constexpr int SEG_STAGES = 2048 / (KE * KB);             // stages per fp32 segment
 static_assert(KPAD % (KE * KB) == 0, "stage k");
 constexpr int TMEM_COLS = 512;
 constexpr unsigned long long TIMEOUT_NS = 1000000000ull;
 
-// Tile of TD and QD: TMEM holds two BN-column fp32 accumulators and BN group
-// sums of GW 32-bit words each (2 BN + GW BN <= 512).
+// Tile of TD and QD: TMEM holds two sets of two BN-column fp32 accumulators
+// (one per weight of a block) and BN group sums of GW 32-bit words each
+// (4 BN + GW BN <= 512).  A stage holds one A slice tile and the B slice tiles
+// of the block's (at most) two weights.
 template <int P> struct Cfg {
     static_assert(P == 3 || P == 4, "DD runs on CTA pairs");
     static constexpr int BN = 64;
     static constexpr int GW = 4;
     static constexpr int B_BYTES = BN * KE * 2;                   // one B box, 8 KB
-    static constexpr int STAGE_BYTES = KB * (A_BYTES + B_BYTES);   // 48 KB
-    static constexpr int ACC_COLS = BN;                      // accumulators at columns 0 and BN
-    static constexpr int GRP_COL = 2 * BN;
+    static constexpr int A_STAGE = KB * A_BYTES;                  // 32 KB
+    static constexpr int B_STAGE = KB * B_BYTES;                  // 16 KB per weight
+    static constexpr int STAGE_BYTES = A_STAGE + 2 * B_STAGE;     // 64 KB
+    static constexpr int SET_COLS = 2 * BN;                  // accumulator sets at columns 0 and 2 BN
+    static constexpr int GRP_COL = 4 * BN;
     static_assert(GRP_COL + GW * BN <= TMEM_COLS, "TMEM columns");
     // instruction descriptor: kind::f16, bf16 A and B (K-major), fp32 D, M = 128, N = BN
     static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
@@ -958,6 +962,57 @@ __device__ __forceinline__ void group_store(uint32_t* w, T v)
     for (int i = 0; i < GW; ++i) w[i] = static_cast<uint32_t>(v >> (32 * i));
 }
 
+// Iteration over the stages of one TD/QD tile on the tcgen05 engine.  The
+// weights S+1, S, ..., 2 are cut into the accumulation groups of G weights
+// (from the least significant end), and each group into blocks of two
+// consecutive weights (w, w - 1), a lone last weight forming a block of its
+// own, so no block spans two groups.  A block's stages run over the pair
+// index s = 1 .. w - 1 and, for each s, the k tiles: the stage multiplies the
+// A slice s by the B slices w - s and (while s <= w - 2) w - 1 - s, so one A
+// tile feeds both weights' accumulators.  The integer group sums do not depend
+// on the order in which their weights' products arrive, so the result is that
+// of the weight-by-weight order.
+struct BlockCursor {
+    int wh;     // the block's larger weight
+    int two;    // 1 when the block also holds wh - 1
+    int s, kt;
+    __device__ __forceinline__ void begin(int S, int G, int w)
+    {
+        wh = w;
+        const int j = (S + 1 - w) % G;
+        two = (j + 1 < G && w - 1 >= 2) ? 1 : 0;
+        s = 1;
+        kt = 0;
+    }
+    // whether the current stage carries the pair of weight wh - 1
+    __device__ __forceinline__ bool lo() const { return two && s <= wh - 2; }
+    // the next stage; returns true when that starts a new block
+    __device__ __forceinline__ bool advance(int S, int G, int KT)
+    {
+        if (++kt < KT) return false;
+        kt = 0;
+        if (++s <= wh - 1) return false;
+        begin(S, G, wh - 1 - two);
+        return true;
+    }
+    // index of weight w within its group, and whether it closes the group
+    static __device__ __forceinline__ int index(int S, int G, int w) { return (S + 1 - w) % G; }
+    static __device__ __forceinline__ bool closes(int S, int G, int w) { return index(S, G, w) == G - 1 || w == 2; }
+};
+
+// Stages of one tile: sum over the blocks of (wh - 1) KT.
+__device__ __forceinline__ int tile_stages(int S, int G, int KT)
+{
+    int n = 0;
+    for (int w = S + 1; w >= 2;) {
+        const int j = (S + 1 - w) % G;
+        const int two = (j + 1 < G && w - 1 >= 2) ? 1 : 0;
+        n += (w - 1) * KT;
+        w -= 1 + two;
+    }
+    return n;
+}
+
 template <int P>
 __global__ void __launch_bounds__(192, 1)
 ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -1002,7 +1057,7 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 
     const int S = g.S;
     const int KT = static_cast<int>(g.kp / (tc::KE * tc::KB));
-    const int per_tile = (S * (S + 1) / 2) * KT;
+    const int per_tile = tile_stages(S, kGroup, KT);
     const int ntiles = g.tiles_m * g.tiles_n;
     auto fail = [&](int code) {
         *abortp = 1;
@@ -1016,19 +1071,24 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             bool ok = true;
             for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
                 const int m0 = (tile % g.tiles_m) * tc::BM, n0 = (tile / g.tiles_m) * BN;
-                Cursor c{S + 1, 1, 0};
+                BlockCursor c;
+                c.begin(S, kGroup, S + 1);
                 for (int i = 0; i < per_tile; ++i, ++it) {
                     const uint32_t st = it % tc::STAGES, ph = (it / tc::STAGES) & 1u;
                     if (!mbar_wait<kHintIdle>(&empty[st], ph ^ 1u, abortp)) { fail(1); ok = false; break; }
                     uint8_t* sa = stage0 + st * Cf::STAGE_BYTES;
-                    mbar_expect_tx(&full[st], Cf::STAGE_BYTES);
+                    const bool lo = c.lo();
+                    mbar_expect_tx(&full[st], Cf::A_STAGE + (lo ? 2 : 1) * Cf::B_STAGE);
 #pragma unroll
                     for (int q = 0; q < tc::KB; ++q) {
                         const int x = (c.kt * tc::KB + q) * tc::KE;
                         tma_load_3d(sa + q * tc::A_BYTES, &tmA, x, m0, c.s - 1, &full[st]);
-                        tma_load_3d(sa + tc::KB * tc::A_BYTES + q * Cf::B_BYTES, &tmB, x, n0, c.w - c.s - 1, &full[st]);
+                        tma_load_3d(sa + Cf::A_STAGE + q * Cf::B_BYTES, &tmB, x, n0, c.wh - c.s - 1, &full[st]);
+                        if (lo)
+                            tma_load_3d(sa + Cf::A_STAGE + Cf::B_STAGE + q * Cf::B_BYTES, &tmB, x, n0,
+                                        c.wh - 1 - c.s - 1, &full[st]);
                     }
-                    c.advance(S, KT);
+                    c.advance(S, kGroup, KT);
                 }
             }
             // the last loads issued must have landed before the CTA exits
@@ -1043,15 +1103,18 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         // --------------------------------------------------------------- MMA
         if (lane == 0) {
             uint32_t it = 0, seg = 0;
-            int pend = -1;          // accumulator whose commit waits for the next stage
+            int pend = -1;          // accumulator set whose commit waits for the next stage
             bool ok = true;
             for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-                Cursor c{S + 1, 1, 0};
+                BlockCursor c;
+                c.begin(S, kGroup, S + 1);
                 int seg_stages = 0;
+                bool lo_started = false;
                 uint32_t b = 0;
                 for (int i = 0; i < per_tile; ++i, ++it) {
                     if (seg_stages == 0) {
                         b = seg & 1u;
+                        lo_started = false;
                         if (!mbar_wait<kHintIssue>(&acce[b], ((seg >> 1) & 1u) ^ 1u, abortp)) { fail(2); ok = false; break; }
                     }
                     const uint32_t st = it % tc::STAGES, ph = (it / tc::STAGES) & 1u;
@@ -1061,21 +1124,26 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                         umma_commit(&accf[pend]);
                         pend = -1;
                     }
+                    const bool lo = c.lo();
                     const uint32_t sa = smem_u32(stage0 + st * Cf::STAGE_BYTES);
+                    const uint32_t d_hi = tmem + b * Cf::SET_COLS, d_lo = d_hi + BN;
 #pragma unroll
                     for (int q = 0; q < tc::KB; ++q) {
                         const uint64_t da = umma_desc(sa + q * tc::A_BYTES);
-                        const uint64_t db = umma_desc(sa + tc::KB * tc::A_BYTES + q * Cf::B_BYTES);
+                        const uint64_t dh = umma_desc(sa + Cf::A_STAGE + q * Cf::B_BYTES);
+                        const uint64_t dl = umma_desc(sa + Cf::A_STAGE + Cf::B_STAGE + q * Cf::B_BYTES);
 #pragma unroll
-                        for (int kk = 0; kk < tc::KE / 16; ++kk)
-                            umma(tmem + b * Cf::ACC_COLS, da + 2ull * kk, db + 2ull * kk, Cf::IDESC,
-                                 (seg_stages > 0 || q > 0 || kk > 0) ? 1u : 0u);
+                        for (int kk = 0; kk < tc::KE / 16; ++kk) {
+                            const uint32_t more = (q > 0 || kk > 0) ? 1u : 0u;
+                            umma(d_hi, da + 2ull * kk, dh + 2ull * kk, Cf::IDESC, (seg_stages > 0 || more) ? 1u : 0u);
+                            if (lo) umma(d_lo, da + 2ull * kk, dl + 2ull * kk, Cf::IDESC, (lo_started || more) ? 1u : 0u);
+                        }
                     }
                     umma_commit(&empty[st]);
+                    lo_started = lo_started || lo;
                     ++seg_stages;
-                    const int w = c.w;
-                    c.advance(S, KT);
-                    if (c.w != w || seg_stages == tc::SEG_STAGES) {
+                    const bool block_end = c.advance(S, kGroup, KT);
+                    if (block_end || seg_stages == tc::SEG_STAGES) {
                         pend = static_cast<int>(b);
                         ++seg;
                         seg_stages = 0;
@@ -1111,16 +1179,20 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 #pragma unroll
             for (int c0 = 0; c0 < GW * BN; c0 += 32) tmem_st32(grp + c0, zero32);
             tmem_wait_st();
-            Cursor c{S + 1, 1, 0};
+            BlockCursor c;
+            c.begin(S, kGroup, S + 1);
             int seg_stages = 0;
+            bool lo_used = false;
             bool first_group = true;
             for (int i = 0; i < per_tile; ++i) {
                 ++seg_stages;
-                const int w = c.w;
-                c.advance(S, KT);
-                const bool weight_end = c.w != w;
-                if (!weight_end && seg_stages != tc::SEG_STAGES) continue;
+                lo_used = lo_used || c.lo();
+                const int wh = c.wh, two = c.two;
+                const bool block_end = c.advance(S, kGroup, KT);
+                if (!block_end && seg_stages != tc::SEG_STAGES) continue;
                 seg_stages = 0;
+                const bool use_lo = lo_used;
+                lo_used = false;
                 const uint32_t b = seg & 1u;
                 // the decision must be warp-uniform: the TMEM loads below are .sync.aligned
                 if (!__all_sync(0xffffffffu, mbar_wait<kHintIdle>(&accf[b], (seg >> 1) & 1u, abortp))) {
@@ -1129,11 +1201,12 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                     break;
                 }
                 tc_fence_after();
-                const int j = (S + 1 - w) % kGroup;
-                // OPW outputs per 32 TMEM columns of group sums
+                const int jh = BlockCursor::index(S, kGroup, wh);     // the lower weight is jh + 1
+                const uint32_t acc = tmem + lane_off + b * Cf::SET_COLS;
                 for (int c0 = 0; c0 < BN; c0 += 32) {
-                    uint32_t fv[32];
-                    tmem_ld32(tmem + lane_off + b * Cf::ACC_COLS + c0, fv);
+                    uint32_t fh[32], fl[32];
+                    tmem_ld32(acc + c0, fh);
+                    if (use_lo) tmem_ld32(acc + BN + c0, fl);
                     tmem_wait_ld();
 #pragma unroll
                     for (int h = 0; h < GW; ++h) {
@@ -1142,9 +1215,10 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                         tmem_wait_ld();
 #pragma unroll
                         for (int t = 0; t < OPW; ++t) {
-                            const int add = __float2int_rn(__uint_as_float(fv[OPW * h + t]));
-                            const G V = group_load<G, GW>(gw + GW * t) + (static_cast<G>(add) << (7 * j));
-                            group_store<G, GW>(gw + GW * t, V);
+                            G add = static_cast<G>(__float2int_rn(__uint_as_float(fh[OPW * h + t]))) << (7 * jh);
+                            if (use_lo)
+                                add += static_cast<G>(__float2int_rn(__uint_as_float(fl[OPW * h + t]))) << (7 * (jh + 1));
+                            group_store<G, GW>(gw + GW * t, group_load<G, GW>(gw + GW * t) + add);
                         }
                         tmem_st32(grp + GW * c0 + 32 * h, gw);
                     }
@@ -1153,9 +1227,10 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 tc_fence_before();
                 mbar_arrive(&acce[b]);
                 ++seg;
-                if (!(weight_end && (j == kGroup - 1 || w == 2))) continue;
+                const int wl = wh - two;
+                if (!(block_end && BlockCursor::closes(S, kGroup, wl))) continue;
                 // end of a group: add its exact value to C
-                const int wmax = w + j;
+                const int wmax = wl + BlockCursor::index(S, kGroup, wl);
                 for (int c0 = 0; c0 < GW * BN; c0 += 32) {
                     uint32_t gw[32];
                     tmem_ld32(grp + c0, gw);
@@ -1164,7 +1239,7 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                     for (int t = 0; t < OPW; ++t) {
                         const int64_t col = n0 + c0 / GW + t;
                         if (row >= g.m || col >= g.n) continue;
-                        double y[P], acc[P], zz[P];
+                        double y[P], accv[P], zz[P];
                         const bool exact = split_exact(group_load<G, GW>(gw + GW * t),
                                                        sg + s_tau[c0 / GW + t] - 7 * wmax, y[0], y[1]);
 #pragma unroll
@@ -1179,8 +1254,8 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                         // a first group whose split left the normal range is
                         // added to zero as written
 #pragma unroll
-                        for (int cc = 0; cc < P; ++cc) acc[cc] = first_group ? f.zero : g.C[cc][row * g.ldc + col];
-                        mp::Ops<P>::add(f, acc, y, zz);
+                        for (int cc = 0; cc < P; ++cc) accv[cc] = first_group ? f.zero : g.C[cc][row * g.ldc + col];
+                        mp::Ops<P>::add(f, accv, y, zz);
 #pragma unroll
                         for (int cc = 0; cc < P; ++cc) g.C[cc][row * g.ldc + col] = zz[cc];
                     }
