@@ -29,6 +29,7 @@
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <cstdlib>
 #include <mutex>
 
 namespace mpg {
@@ -826,6 +827,7 @@ struct TcArgs {
     int S, tiles_m, tiles_n;
     int* err;
     long long* scratch;     // CTA-pair engine: per CTA, two [BN][BM] buffers of finished group sums
+    int test_abort;         // test of the abort path: the producer gives up before its first load
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -1069,6 +1071,12 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
+            if (g.test_abort) {
+                // as if the first wait had run out: nothing has been loaded,
+                // so no role has anything in flight when it sees the abort
+                fail(1);
+                ok = false;
+            }
             for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
                 const int m0 = (tile % g.tiles_m) * tc::BM, n0 = (tile / g.tiles_m) * BN;
                 BlockCursor c;
@@ -1504,6 +1512,12 @@ ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
+            if (g.test_abort) {
+                // as if the first wait had run out, in both CTAs of the pair:
+                // nothing has been loaded, so nothing is in flight
+                fail(1);
+                ok = false;
+            }
             for (int tile = cid; tile < ntiles && ok; tile += ncl) {
                 const int ma = (tile % g.tiles_m) * 2 * tc2::BM + static_cast<int>(rank) * tc2::BM;
                 const int nb = (tile / g.tiles_m) * BN + static_cast<int>(rank) * (BN / 2);
@@ -2050,6 +2064,17 @@ static cudaError_t pair_clusters(int* out)
     return cudaSuccess;
 }
 
+// Test of the tcgen05 engines' abort path: with MPGEMM_TEST_TC_ABORT=1 in the
+// environment the producer gives up before issuing any load, as if its first
+// bounded wait had run out; every other role then finds the abort flag with
+// nothing in flight, the kernel releases TMEM and returns, and the workspace
+// header holds code 1 (C is not computed).
+static int tc_test_abort()
+{
+    const char* v = getenv("MPGEMM_TEST_TC_ABORT");
+    return v && v[0] == '1' && v[1] == '\0';
+}
+
 template <int P>
 static cudaError_t launch_ozaki_tc(const GemmArgs<P>& g, int S, void* ws, cudaStream_t s)
 {
@@ -2070,7 +2095,7 @@ static cudaError_t launch_ozaki_tc(const GemmArgs<P>& g, int S, void* ws, cudaSt
             return cudaErrorInvalidValue;
         TcArgs a{sig, tau, {g.C[0], g.C[1], nullptr, nullptr}, g.ldc, g.m, g.n, L.kp, S,
                  static_cast<int>(L.mp / (2 * tc2::BM)), static_cast<int>(L.np / tc2::BN), err,
-                 reinterpret_cast<long long*>(base + L.offScr)};
+                 reinterpret_cast<long long*>(base + L.offScr), tc_test_abort()};
         int clusters = 0;
         e = pair_clusters(&clusters);
         if (e != cudaSuccess) return e;
@@ -2094,7 +2119,8 @@ static cudaError_t launch_ozaki_tc(const GemmArgs<P>& g, int S, void* ws, cudaSt
         if (!slice_map(&ma, sa, S, L.mp, L.kp, tc::BM) || !slice_map(&mb, sb, S, L.np, L.kp, Cf::BN))
             return cudaErrorInvalidValue;
         TcArgs a{sig, tau, {nullptr, nullptr, nullptr, nullptr}, g.ldc, g.m, g.n, L.kp, S,
-                 static_cast<int>(L.mp / tc::BM), static_cast<int>(L.np / Cf::BN), err, nullptr};
+                 static_cast<int>(L.mp / tc::BM), static_cast<int>(L.np / Cf::BN), err, nullptr,
+                 tc_test_abort()};
         for (int c = 0; c < P; ++c) a.C[c] = g.C[c];
         const int smem = tc::STAGES * Cf::STAGE_BYTES + 1024;
         e = cudaFuncSetAttribute(ozaki_tc_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

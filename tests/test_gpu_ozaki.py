@@ -371,3 +371,38 @@ def test_full_size_both_engines(torch, prec, n, S):
     ent = sorted({(i, j) for i in full for j in range(n)} | {(i, j) for i in rows for j in cols})
     err = X.gemm_error(C, A, B, ent)
     assert err["err_abs"] <= n * 2.0 ** -{"dd": 100, "td": 150, "qd": 200}[prec], err
+
+
+@pytest.mark.parametrize("prec", ["dd", "td", "qd"])
+def test_tc_abort_path(torch, prec):
+    """The tcgen05 engines' abort path, run for real: with MPGEMM_TEST_TC_ABORT=1
+    the producer gives up before issuing any load (as if its first bounded wait
+    had run out), so every other role finds the abort flag with no load or MMA
+    in flight.  The call returns at once, mpgemm_tc_status names the producer,
+    and the next normal call on the same workspace is bit-identical to the int8
+    engine (TMEM was released, the header is cleared)."""
+    import os
+    import time
+    from paper_2101_06584_gb300 import mpgemm as mm
+    P = I.P_OF[prec]
+    rng = np.random.default_rng(720 + P)
+    m, n, k = 300, 200, 260
+    A, B = I.uniform(P, (m, k), rng), I.uniform(P, (k, n), rng)
+    Ad, Bd = dev(torch, A), dev(torch, B)
+    ws = torch.empty(mm.workspace_size(prec, m, n, k, algo="bf16"), dtype=torch.uint8, device="cuda")
+    C = torch.zeros((P, m, n), dtype=torch.float64, device="cuda")
+    os.environ["MPGEMM_TEST_TC_ABORT"] = "1"
+    try:
+        t0 = time.perf_counter()
+        mm.gemm(prec, Ad, Bd, out=C, algo="bf16", workspace=ws)
+        code = mm.tc_status(ws)
+        elapsed = time.perf_counter() - t0
+    finally:
+        del os.environ["MPGEMM_TEST_TC_ABORT"]
+    assert code == 1 and "producer" in mm.lib().mpgemm_last_error().decode()
+    assert elapsed < 5.0, elapsed                     # no wait ran to its one-second limit
+    got = mm.gemm(prec, Ad, Bd, algo="bf16", workspace=ws)
+    assert mm.tc_status(ws) == 0
+    ws8 = torch.empty(mm.workspace_size(prec, m, n, k, algo="int8"), dtype=torch.uint8, device="cuda")
+    want = mm.gemm(prec, Ad, Bd, algo="int8", workspace=ws8)
+    assert_bitwise(host(got), host(want), "%s after an aborted call" % prec)
