@@ -1,0 +1,155 @@
+"""Oracle for the CRT form of the DD/TD/QD GEMM (Ozaki scheme II) -- TEST
+INFRASTRUCTURE ONLY (tests, smoke check and the benchmark's CPU leg).
+
+Not in the paper: the product of Sec. 3 (Eq. 1) computed with the scaled
+operands turned into integers, the integer product recovered exactly from its
+residues modulo N small pairwise coprime moduli (Chinese remainder theorem),
+each residue product running on the tensor cores.  Every step is the plain
+definition in Python integers:
+
+  scale    sigma_i = ilogb(max_p |a_ip[0]|) + 2 for row i of A (0 for an
+           all-zero row), tau_j likewise for column j of B, so that
+           |a_ip| 2^-sigma_i < 1/2.
+  integers A'_ip = the nearest integer (ties to even) of the exact value of
+           a_ip (the sum of its components) times 2^(beta - sigma_i);
+           |A'| <= 2^(beta - 1).  B' likewise with tau_j.
+  moduli   m_1, ..., m_N: the first N of MODULI, pairwise coprime integers
+           <= 256 taken greedily from 256 downward; M = m_1 ... m_N.
+  bits     beta = the largest integer with k 2^(2 beta - 1) < M, so that
+           |A' B'| <= k 2^(2 beta - 2) < M / 2 (beta >= 1 is required).
+  residues r(x, m) = the representative of x mod m in [-floor(m/2),
+           ceil(m/2) - 1]; |r| <= 128, exact in int8 and in bf16.
+  products Q_i = r(A', m_i) r(B', m_i)^T, exact integers
+           (|Q_i| <= k 2^14 < 2^31 for k < 2^17).
+  recover  C' = the integer in [-M/2, M/2) with C' = Q_i mod m_i for every
+           i (C' = A'B' exactly).
+  output   v = C' 2^(sigma_i + tau_j - 2 beta); the P components are
+           c_0 = RN(v), c_1 = RN(v - c_0), ..., each the nearest binary64
+           (ties to even) of the exact remainder.
+
+The result is deterministic; its error against the exact product comes from
+rounding the scaled entries to integers (about 2^-beta relative to the row
+and column scales) and from the final rounding to P components.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+
+
+def _coprime_moduli(limit=256, count=64):
+    out = []
+    m = limit
+    while m > 1 and len(out) < count:
+        if all(math.gcd(m, x) == 1 for x in out):
+            out.append(m)
+        m -= 1
+    return out
+
+
+MODULI = _coprime_moduli()
+RES_BITS = 14            # |r(a) r(b)| <= 128 * 128 = 2^14
+
+
+def k_limit():
+    """Largest k whose residue products sum exactly in int32."""
+    return (2 ** 31 - 1) // (1 << RES_BITS)
+
+
+def modulus_product(N):
+    return math.prod(MODULI[:N])
+
+
+def beta_bits(N, k):
+    """The largest beta with k 2^(2 beta - 1) < M (0 if none)."""
+    M = modulus_product(N)
+    b = 0
+    while max(k, 1) * 2 ** (2 * (b + 1) - 1) < M:
+        b += 1
+    return b
+
+
+def sym_mod(x, m):
+    """Representative of x mod m in [-floor(m/2), ceil(m/2) - 1]."""
+    r = x % m
+    return r - m if r >= (m + 1) // 2 else r
+
+
+def ilogb(x):
+    return math.frexp(abs(x))[1] - 1
+
+
+def scale_exponent(hi_values):
+    mx = max((abs(float(v)) for v in hi_values), default=0.0)
+    return 0 if mx == 0.0 else ilogb(mx) + 2
+
+
+def scaled_integer(components, shift):
+    """Nearest integer (ties to even) of (sum of components) * 2^shift."""
+    v = sum((Fraction(float(c)) for c in components), Fraction(0)) * Fraction(2) ** shift
+    return round(v)          # Fraction.__round__: nearest, ties to even
+
+
+def integer_rows(planes, beta):
+    """planes (P, r, k): exponents (list) and the integers A' (list of lists)."""
+    planes = np.asarray(planes)
+    sig, rows = [], []
+    for i in range(planes.shape[1]):
+        s = scale_exponent(planes[0, i, :])
+        sig.append(s)
+        rows.append([scaled_integer(planes[:, i, p], beta - s) for p in range(planes.shape[2])])
+    return sig, rows
+
+
+def nearest_expansion(v, P):
+    """The P components c_t = RN(v - c_0 - ... - c_(t-1)) of an exact rational v."""
+    out = []
+    rest = Fraction(v)
+    for _ in range(P):
+        try:
+            c = float(rest)                    # correctly rounded, ties to even
+        except OverflowError:
+            c = math.copysign(math.inf, rest)
+        out.append(c)
+        if not math.isfinite(c):
+            rest = Fraction(0)
+        else:
+            rest -= Fraction(c)
+    return out
+
+
+def crt_recover(residues, N):
+    """The integer in [-M/2, M/2) congruent to residues[i] mod MODULI[i]."""
+    M = modulus_product(N)
+    x = 0
+    for i in range(N):
+        m = MODULI[i]
+        Mi = M // m
+        x += residues[i] * Mi * pow(Mi, -1, m)
+    x %= M
+    return x - M if x >= (M + 1) // 2 else x
+
+
+def gemm(A, B, N, rows=None, cols=None):
+    """C = A B through the CRT form with N moduli, for the selected rows of A
+    and columns of B (all by default).  A (P, m, k), B (P, k, n).  Returns
+    C (P, len(rows), len(cols)), sigma, tau and beta."""
+    A = np.asarray(A)
+    B = np.asarray(B)
+    P = A.shape[0]
+    k = A.shape[2]
+    rows = list(range(A.shape[1])) if rows is None else list(rows)
+    cols = list(range(B.shape[2])) if cols is None else list(cols)
+    beta = beta_bits(N, k)
+    assert beta >= 1, "too few moduli for this k"
+    sig, Ai = integer_rows(A[:, rows, :], beta)
+    tau, Bi = integer_rows(np.ascontiguousarray(B[:, :, cols].transpose(0, 2, 1)), beta)
+    C = np.zeros((P, len(rows), len(cols)))
+    for r in range(len(rows)):
+        ra = [[sym_mod(a, MODULI[i]) for a in Ai[r]] for i in range(N)]
+        for c in range(len(cols)):
+            Q = [sum(x * sym_mod(b, MODULI[i]) for x, b in zip(ra[i], Bi[c])) for i in range(N)]
+            Cp = crt_recover([q % MODULI[i] for i, q in enumerate(Q)], N)
+            v = Fraction(Cp) * Fraction(2) ** (sig[r] + tau[c] - 2 * beta)
+            C[:, r, c] = nearest_expansion(v, P)
+    return C, sig, tau, beta
