@@ -59,7 +59,7 @@ void *mpgemm_get_stream(void);
 /* Library ABI version (major * 100 + minor): 101 adds the TD/QD variants,
  * mpgemm_default_tile and mpgemm_tc_status to 100; 102 adds mpgemm_d and
  * P = 1 in mpgemm_ex, mpgemm_num_tiles, mpgemm_tile_info and
- * mpgemm_default_tile. */
+ * mpgemm_default_tile; 103 adds MPG_ALGO_INT8_CRT and mpgemm_crt_beta. */
 int mpgemm_version(void);
 
 /* ---------------------------------------------------------------------
@@ -177,7 +177,8 @@ typedef enum mpg_algo {
     MPG_ALGO_AUTO = 0,       /* the FP64-EFT kernel (k-sequential unless split_k > 1) */
     MPG_ALGO_FP64_EFT = 1,   /* FP64 error-free transformations on the CUDA cores */
     MPG_ALGO_INT8_OZAKI = 2, /* DD/TD/QD: error-free INT8 slicing on the tensor cores */
-    MPG_ALGO_BF16_SLICES = 3 /* DD/TD/QD: the same digits as bf16 on tcgen05 (TMEM accumulators) */
+    MPG_ALGO_BF16_SLICES = 3, /* DD/TD/QD: the same digits as bf16 on tcgen05 (TMEM accumulators) */
+    MPG_ALGO_INT8_CRT = 4     /* DD/TD/QD: residues modulo small coprime moduli on the tensor cores */
 } mpg_algo;
 
 /* Options of mpgemm_ex.  Zero-initialised options give the plain call. */
@@ -256,6 +257,41 @@ int mpgemm_ex(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k,
  * op(B)^T), then the int32 exponents, then for DD 256 KB per SM in which
  * finished groups wait for their additions to C; mpgemm_workspace_size gives
  * the total. */
+
+/* MPG_ALGO_INT8_CRT (not in the paper; the Chinese-remainder form, also
+ * called Ozaki scheme II).  C := op(A) op(B) for P = 2, 3, 4 with N =
+ * opts->slices moduli (default 28 for DD, 44 for TD, 49 for QD; 1..49):
+ *   moduli  m_0 = 256, m_1 = 255, 253, 251, 247, ...: the pairwise coprime
+ *           integers <= 256 taken greedily from 256 downward (49 of them);
+ *           M = m_0 ... m_(N-1).
+ *   bits    beta = mpgemm_crt_beta(N, k), the largest beta with
+ *           k 2^(2 beta - 1) < M (MPG_EUNSUPPORTED if there is none).
+ *   scale   sigma_i, tau_j as for MPG_ALGO_INT8_OZAKI.
+ *   integers A'_ip = the nearest integer (ties to even) of the sum of the
+ *           components of a_ip, each first floored to a multiple of
+ *           2^(sigma_i - beta - 64), in units of 2^(sigma_i - beta);
+ *           |A'| <= 2^(beta - 1); B' likewise with tau_j.
+ *   residues r(x, m) in [-floor(m/2), ceil(m/2) - 1] (|r| <= 128, int8).
+ *   products Q_i = r(A', m_i) r(B', m_i)^T on mma.sync m16n8k32 s8, exact in
+ *           int32 (k <= 131071, else MPG_EUNSUPPORTED).
+ *   recover C' = the integer in [-M/2, M/2) congruent to Q_i mod m_i for
+ *           every i, which is A'B' exactly.
+ *   output  the P components of C' 2^(sigma_i + tau_j - 2 beta), each the
+ *           nearest binary64 (ties to even; gradual underflow, +-inf above
+ *           the range) of the exact remainder of the previous ones.
+ * The result is deterministic and bit-identical to these steps evaluated
+ * anywhere; its error against the exact product is about 2^-beta relative to
+ * the row and column scales (beta is about 170 at most, so QD results carry
+ * fewer bits than the QD format).  Workspace (mpgemm_workspace_size, 256-byte
+ * aligned, not overlapping A, B or C), with mp, np, kp = m, n, k rounded up
+ * to 128 and each region on a 256-byte boundary: int8 [N][mp][kp] residues
+ * of op(A), int8 [N][np][kp] of op(B)^T, int32 [mp] sigma, int32 [np] tau,
+ * int8 [N][mp][np] residues of the products. */
+
+/* beta of the CRT form for N moduli and inner dimension k (>= 1 when the
+ * form applies, 0 when the moduli's product is too small); MPG_EINVAL for N
+ * outside 1..49 or k < 0. */
+int mpgemm_crt_beta(int moduli, int64_t k);
 
 /* After an MPG_ALGO_BF16_SLICES call with this workspace: synchronises the
  * calling thread's stream and returns the code in the workspace header.  0

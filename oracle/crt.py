@@ -10,9 +10,12 @@ definition in Python integers:
   scale    sigma_i = ilogb(max_p |a_ip[0]|) + 2 for row i of A (0 for an
            all-zero row), tau_j likewise for column j of B, so that
            |a_ip| 2^-sigma_i < 1/2.
-  integers A'_ip = the nearest integer (ties to even) of the exact value of
-           a_ip (the sum of its components) times 2^(beta - sigma_i);
-           |A'| <= 2^(beta - 1).  B' likewise with tau_j.
+  integers A'_ip = the nearest integer (ties to even) of the sum of the
+           components of a_ip, each first floored to a multiple of
+           2^(sigma_i - beta - 64), in units of 2^(sigma_i - beta)
+           (the floor, 64 bits below the unit, is part of the definition and
+           moves A' only when the exact value lies within about 2^-62 units
+           of a half); |A'| <= 2^(beta - 1).  B' likewise with tau_j.
   moduli   m_1, ..., m_N: the first N of MODULI, pairwise coprime integers
            <= 256 taken greedily from 256 downward; M = m_1 ... m_N.
   bits     beta = the largest integer with k 2^(2 beta - 1) < M, so that
@@ -84,10 +87,15 @@ def scale_exponent(hi_values):
     return 0 if mx == 0.0 else ilogb(mx) + 2
 
 
+GUARD = 64
+
+
 def scaled_integer(components, shift):
-    """Nearest integer (ties to even) of (sum of components) * 2^shift."""
-    v = sum((Fraction(float(c)) for c in components), Fraction(0)) * Fraction(2) ** shift
-    return round(v)          # Fraction.__round__: nearest, ties to even
+    """Nearest integer (ties to even) of the sum of the components times
+    2^shift, each component first floored to a multiple of 2^-64 in those
+    units."""
+    W = sum(math.floor(Fraction(float(c)) * Fraction(2) ** (shift + GUARD)) for c in components)
+    return round(Fraction(W, 2 ** GUARD))          # Fraction.__round__: nearest, ties to even
 
 
 def integer_rows(planes, beta):
@@ -130,6 +138,13 @@ def crt_recover(residues, N):
     return x - M if x >= (M + 1) // 2 else x
 
 
+def residues(planes, N, beta):
+    """planes (P, r, k): exponents and the residues [N][r][k] of the integers."""
+    sig, rows = integer_rows(planes, beta)
+    return sig, np.array([[[sym_mod(a, MODULI[i]) for a in row] for row in rows] for i in range(N)],
+                         dtype=np.int64).reshape(N, len(rows), np.asarray(planes).shape[2])
+
+
 def gemm(A, B, N, rows=None, cols=None):
     """C = A B through the CRT form with N moduli, for the selected rows of A
     and columns of B (all by default).  A (P, m, k), B (P, k, n).  Returns
@@ -144,12 +159,17 @@ def gemm(A, B, N, rows=None, cols=None):
     assert beta >= 1, "too few moduli for this k"
     sig, Ai = integer_rows(A[:, rows, :], beta)
     tau, Bi = integer_rows(np.ascontiguousarray(B[:, :, cols].transpose(0, 2, 1)), beta)
+    # residues as int64 arrays [N][rows][k] and [N][cols][k]; the products are
+    # exact in int64 (|Q_i| <= k 2^14)
+    RA = np.array([[[sym_mod(a, MODULI[i]) for a in Ai[r]] for r in range(len(rows))] for i in range(N)],
+                  dtype=np.int64).reshape(N, len(rows), k)
+    RB = np.array([[[sym_mod(b, MODULI[i]) for b in Bi[c]] for c in range(len(cols))] for i in range(N)],
+                  dtype=np.int64).reshape(N, len(cols), k)
+    Q = np.einsum("irk,ick->irc", RA, RB)
     C = np.zeros((P, len(rows), len(cols)))
     for r in range(len(rows)):
-        ra = [[sym_mod(a, MODULI[i]) for a in Ai[r]] for i in range(N)]
         for c in range(len(cols)):
-            Q = [sum(x * sym_mod(b, MODULI[i]) for x, b in zip(ra[i], Bi[c])) for i in range(N)]
-            Cp = crt_recover([q % MODULI[i] for i, q in enumerate(Q)], N)
+            Cp = crt_recover([int(Q[i, r, c]) % MODULI[i] for i in range(N)], N)
             v = Fraction(Cp) * Fraction(2) ** (sig[r] + tau[c] - 2 * beta)
             C[:, r, c] = nearest_expansion(v, P)
     return C, sig, tau, beta

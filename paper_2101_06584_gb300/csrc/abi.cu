@@ -204,6 +204,43 @@ static int ozaki_call(const GemmArgs<P>& g, const mpgemm_opts* o)
     return e == cudaSuccess ? MPG_OK : cuda_fail(e, "slicing gemm launch");
 }
 
+static int crt_default_moduli(int P) { return P == 2 ? 28 : P == 3 ? 44 : kCrtMaxModuli; }
+
+template <int P>
+static int crt_call(const GemmArgs<P>& g, const mpgemm_opts* o)
+{
+    const int N = o->slices ? o->slices : crt_default_moduli(P);
+    if (N < 1 || N > kCrtMaxModuli)
+        return fail(MPG_EINVAL, "the CRT form takes 1..%d moduli (got %d)", kCrtMaxModuli, N);
+    if (g.k > crt_k_limit())
+        return fail(MPG_EUNSUPPORTED, "k = %lld exceeds %lld, the largest k whose residue products sum "
+                    "exactly in int32", (long long)g.k, (long long)crt_k_limit());
+    const int beta = crt_beta(N, g.k);
+    if (beta < 1)
+        return fail(MPG_EUNSUPPORTED, "%d moduli leave no bits for k = %lld (their product must exceed 2k)", N,
+                    (long long)g.k);
+    const OzakiLayout L = crt_layout(N, g.m, g.n, g.k);
+    if (L.mp / 128 > 65535) return fail(MPG_EINVAL, "m too large for the CRT form's grid");
+    if (!o->workspace) return fail(MPG_EWORKSPACE, "the CRT form needs a workspace of %lld bytes",
+                                   (long long)L.total);
+    if (reinterpret_cast<uintptr_t>(o->workspace) % 256)
+        return fail(MPG_EWORKSPACE, "workspace must be 256-byte aligned");
+    if (o->workspace_bytes < static_cast<size_t>(L.total))
+        return fail(MPG_EWORKSPACE, "workspace of %zu bytes is smaller than the %lld needed",
+                    o->workspace_bytes, (long long)L.total);
+    const Range rw{reinterpret_cast<uintptr_t>(o->workspace),
+                   reinterpret_cast<uintptr_t>(o->workspace) + static_cast<uintptr_t>(L.total)};
+    const int64_t ar = g.trans_a ? g.k : g.m, ac = g.trans_a ? g.m : g.k;
+    const int64_t br = g.trans_b ? g.n : g.k, bc = g.trans_b ? g.k : g.n;
+    for (int c = 0; c < P; ++c) {
+        if (overlap(rw, plane_range(g.A[c], ar, ac, g.lda)) || overlap(rw, plane_range(g.B[c], br, bc, g.ldb)) ||
+            overlap(rw, plane_range(g.C[c], g.m, g.n, g.ldc)))
+            return fail(MPG_EWORKSPACE, "workspace overlaps an operand");
+    }
+    cudaError_t e = launch_crt<P>(g, N, o->workspace, g_stream);
+    return e == cudaSuccess ? MPG_OK : cuda_fail(e, "CRT gemm launch");
+}
+
 template <int P>
 static int gemm_call(const mpgemm_opts* o, int64_t m, int64_t n, int64_t k,
                      const double* const* A, int64_t lda, const double* const* B, int64_t ldb,
@@ -225,9 +262,10 @@ static int gemm_call(const mpgemm_opts* o, int64_t m, int64_t n, int64_t k,
     if (m == 0 || n == 0) return MPG_OK;
     const int algo = o ? o->algo : MPG_ALGO_AUTO;
     if (algo != MPG_ALGO_AUTO && algo != MPG_ALGO_FP64_EFT && algo != MPG_ALGO_INT8_OZAKI &&
-        algo != MPG_ALGO_BF16_SLICES)
+        algo != MPG_ALGO_BF16_SLICES && algo != MPG_ALGO_INT8_CRT)
         return fail(MPG_EINVAL, "unknown algorithm %d", algo);
-    const bool sliced = algo == MPG_ALGO_INT8_OZAKI || algo == MPG_ALGO_BF16_SLICES;
+    const bool crt = algo == MPG_ALGO_INT8_CRT;
+    const bool sliced = algo == MPG_ALGO_INT8_OZAKI || algo == MPG_ALGO_BF16_SLICES || crt;
     const int split = o ? o->split_k : 0;
     const int levels = o ? o->strassen : 0;
     if (P == 1 && (sliced || split > 1 || levels != 0))
@@ -240,7 +278,7 @@ static int gemm_call(const mpgemm_opts* o, int64_t m, int64_t n, int64_t k,
     if constexpr (P >= 2) {
         if (sliced) {
             if (o->strassen) return fail(MPG_EINVAL, "strassen applies to the FP64-EFT algorithm only");
-            return ozaki_call(g, o);
+            return crt ? crt_call(g, o) : ozaki_call(g, o);
         }
         if (levels < 0 || levels > kMaxStrassenLevels)
             return fail(MPG_EINVAL, "strassen must be in 0..%d (got %d)", kMaxStrassenLevels, levels);
@@ -302,7 +340,7 @@ int mpgemm_set_stream(void* stream)
 
 void* mpgemm_get_stream(void) { return static_cast<void*>(g_stream); }
 
-int mpgemm_version(void) { return 102; }
+int mpgemm_version(void) { return 103; }
 
 int mp_quick_two_sum(int64_t n, const double* a, const double* b, double* s, double* e)
 { return eft_call(0, n, a, b, s, e); }
@@ -370,6 +408,11 @@ size_t mpgemm_workspace_size(int P, const mpgemm_opts* opts, int64_t m, int64_t 
     if ((opts->algo == MPG_ALGO_AUTO || opts->algo == MPG_ALGO_FP64_EFT) && opts->strassen > 0 &&
         opts->strassen <= kMaxStrassenLevels)
         return static_cast<size_t>(strassen_workspace_elems(P, m, n, k, opts->strassen) * 8);
+    if (opts->algo == MPG_ALGO_INT8_CRT) {
+        const int N = opts->slices ? opts->slices : crt_default_moduli(P);
+        if (N < 1 || N > kCrtMaxModuli) return 0;
+        return static_cast<size_t>(crt_layout(N, m, n, k).total);
+    }
     if (opts->algo != MPG_ALGO_INT8_OZAKI && opts->algo != MPG_ALGO_BF16_SLICES) return 0;
     const int S = opts->slices ? opts->slices : ozaki_default_slices(P);
     if (S < 1 || S > ozaki_max_slices(P)) return 0;
@@ -416,6 +459,15 @@ int mpgemm_dd_int8_static(int64_t m, int64_t n, int64_t k, const double* const A
     if (e != cudaSuccess) return cuda_fail(e, "looking up the fixed scratch array");
     e = launch_ozaki<2>(g, S, ws, g_stream);
     return e == cudaSuccess ? MPG_OK : cuda_fail(e, "INT8 slicing gemm launch");
+}
+
+int mpgemm_crt_beta(int moduli, int64_t k)
+{
+    clear_error();
+    if (moduli < 1 || moduli > kCrtMaxModuli || k < 0)
+        return fail(MPG_EINVAL, "moduli must be in 1..%d and k >= 0 (got %d, %lld)", kCrtMaxModuli, moduli,
+                    (long long)k);
+    return crt_beta(moduli, k);
 }
 
 int mpgemm_num_tiles(int P)

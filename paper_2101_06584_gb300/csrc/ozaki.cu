@@ -253,6 +253,157 @@ __device__ __forceinline__ WideCursor ozaki_cursor_wide(const double (&c)[P], in
     return cur;
 }
 
+// ------------------------------------------------------- CRT residues
+//
+// The CRT form (Ozaki scheme II; not in the paper): each scaled entry of
+// op(A) and op(B) becomes an integer A' (the nearest integer, ties to even,
+// of the sum of its components each floored to a multiple of
+// 2^(sigma - beta - 64), in units of 2^(sigma - beta)), whose residues modulo
+// N pairwise coprime moduli m_i <= 256 -- symmetric representatives, so
+// |r| <= 128, exact in int8 and in bf16 -- replace the digits of the slicing
+// form.  The product of each residue pair is exact on the tensor cores; the
+// integer product A'B' is recovered from its residues (Garner's mixed radix)
+// and rounded to P binary64 components.
+
+namespace crt {
+constexpr int kMaxModuli = 49;
+constexpr int kLimbs = 12;                        // |A'| < 2^192 in 16-bit limbs
+
+struct Tables {
+    int count;
+    int m[kMaxModuli];                            // 256, 255, 253, 251, 247, ...
+    uint32_t magic[kMaxModuli];                   // floor(2^32 / m) + 1
+    uint32_t pw16[kMaxModuli][kLimbs];            // 2^(16 j) mod m_i
+    uint32_t pm[kMaxModuli][kMaxModuli];          // (m_0 ... m_(j-1)) mod m_i, j < i
+    uint32_t inv[kMaxModuli];                     // (m_0 ... m_(i-1))^-1 mod m_i
+};
+
+constexpr int gcd_c(int a, int b)
+{
+    while (b) {
+        const int t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// The moduli: pairwise coprime integers taken greedily from 256 downward.
+constexpr Tables make_tables()
+{
+    Tables t{};
+    int n = 0;
+    for (int m = 256; m > 1 && n < kMaxModuli; --m) {
+        bool ok = true;
+        for (int i = 0; i < n; ++i) ok = ok && gcd_c(m, t.m[i]) == 1;
+        if (ok) t.m[n++] = m;
+    }
+    t.count = n;
+    for (int i = 0; i < n; ++i) {
+        const uint32_t m = static_cast<uint32_t>(t.m[i]);
+        t.magic[i] = static_cast<uint32_t>((1ull << 32) / m + 1);
+        uint32_t p = 1;
+        for (int j = 0; j < kLimbs; ++j) {
+            t.pw16[i][j] = p;
+            p = static_cast<uint32_t>((static_cast<uint64_t>(p) << 16) % m);
+        }
+        uint32_t q = 1 % m;
+        for (int j = 0; j < i; ++j) {
+            t.pm[i][j] = q;
+            q = static_cast<uint32_t>((static_cast<uint64_t>(q) * static_cast<uint32_t>(t.m[j])) % m);
+        }
+        uint32_t inv = 0;
+        for (uint32_t x = 1; x < m; ++x)
+            if ((static_cast<uint64_t>(q) * x) % m == 1) { inv = x; break; }
+        t.inv[i] = i == 0 ? 1 % m : inv;
+    }
+    return t;
+}
+
+constexpr Tables kHost = make_tables();
+static_assert(kHost.count == kMaxModuli, "49 pairwise coprime moduli up to 256");
+__constant__ Tables kDev = kHost;
+
+// x mod m_i for x < 2^32 (one Barrett step: the estimate is the quotient or
+// one more).
+__device__ __forceinline__ uint32_t mod_small(uint32_t x, int i)
+{
+    const uint32_t m = static_cast<uint32_t>(kDev.m[i]);
+    const uint32_t q = __umulhi(x, kDev.magic[i]);
+    const int r = static_cast<int>(x - q * m);
+    return static_cast<uint32_t>(r < 0 ? r + static_cast<int>(m) : r);
+}
+}  // namespace crt
+
+// Residues of one scaled entry, one modulus per next(): the symmetric
+// representative of A' mod m_i, i = 0, 1, ...
+struct ResidueCursor {
+    uint32_t limb[crt::kLimbs];       // |A'| in 16-bit limbs, least significant first
+    bool neg;
+    int idx;
+    __device__ __forceinline__ int next()
+    {
+        const int i = idx++;
+        uint32_t s = 0;
+#pragma unroll
+        for (int j = 0; j < crt::kLimbs; ++j) s += limb[j] * crt::kDev.pw16[i][j];
+        const int m = crt::kDev.m[i];
+        int r = static_cast<int>(crt::mod_small(s, i));
+        if (neg && r) r = m - r;
+        return r >= (m + 1) / 2 ? r - m : r;
+    }
+};
+
+// A' of the P components: each floored at 2^(sigma - beta - 64), summed
+// exactly in 384 bits, rounded to the nearest integer (ties to even) in units
+// of 2^(sigma - beta).
+template <int P>
+__device__ __forceinline__ ResidueCursor residue_cursor(const double (&c)[P], int sigma, int beta)
+{
+    Wide W;
+#pragma unroll
+    for (int i = 0; i < kWideWords; ++i) W.w[i] = 0ull;
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        int64_t M;
+        int e;
+        decompose(c[i], M, e);
+        if (M == 0) continue;
+        const int sh = e - sigma + beta + kGuardBits;
+        if (sh >= 0) wide_add_shifted(W, M, sh);
+        else if (sh > -64) wide_add_small(W, M >> (-sh));      // arithmetic shift: floor
+        else wide_add_small(W, M < 0 ? -1 : 0);
+    }
+    // integer part (words 1..5, floor) and the fraction in word 0
+    const uint64_t f = W.w[0];
+    const bool up = f > (1ull << 63) || (f == (1ull << 63) && (W.w[1] & 1ull));
+    uint64_t I[kWideWords - 1];
+#pragma unroll
+    for (int i = 0; i < kWideWords - 1; ++i) I[i] = W.w[i + 1];
+    uint64_t carry = up ? 1ull : 0ull;
+#pragma unroll
+    for (int i = 0; i < kWideWords - 1; ++i) {
+        const uint64_t s = I[i] + carry;
+        carry = (carry && s == 0) ? 1ull : 0ull;
+        I[i] = s;
+    }
+    ResidueCursor cur;
+    cur.neg = (I[kWideWords - 2] >> 63) != 0;
+    if (cur.neg) {                                   // magnitude: two's complement negation
+        uint64_t cc = 1;
+#pragma unroll
+        for (int i = 0; i < kWideWords - 1; ++i) {
+            const uint64_t s = ~I[i] + cc;
+            cc = (cc && s == 0) ? 1ull : 0ull;
+            I[i] = s;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < crt::kLimbs; ++j) cur.limb[j] = static_cast<uint32_t>(I[j / 4] >> (16 * (j % 4))) & 0xffffu;
+    cur.idx = 0;
+    return cur;
+}
+
 // ------------------------------------------------------------------ scale
 
 // One warp per vector whose elements are contiguous (stride 1, vectors ld apart).
@@ -380,10 +531,29 @@ __device__ __forceinline__ typename CursorOf<P>::T zero_cursor()
     return c;
 }
 
-template <int P, typename T>
+// KIND 0: the slicing form's digits (S of them); KIND 1: the CRT form's
+// residues (S moduli, beta bits per scaled entry).
+template <int P, int KIND> struct KindCursor { using T = typename CursorOf<P>::T; };
+template <int P> struct KindCursor<P, 1> { using T = ResidueCursor; };
+
+template <int P, int KIND>
+__device__ __forceinline__ typename KindCursor<P, KIND>::T make_cursor(const Planes<P>& pl, int64_t off, bool valid,
+                                                                      int sigma, int S, int beta)
+{
+    if constexpr (KIND == 0) {
+        return valid ? element_cursor<P>(pl, off, sigma, S) : zero_cursor<P>();
+    } else {
+        double c[P];
+#pragma unroll
+        for (int i = 0; i < P; ++i) c[i] = valid ? pl.c[i][off] : 0.0;
+        return residue_cursor<P>(c, sigma, beta);
+    }
+}
+
+template <int P, typename T, int KIND = 0>
 __global__ void ozaki_slice_rows(const Planes<P> pl, int64_t rows, int64_t len, int64_t ld,
                                  const int* __restrict__ sig, int S, int64_t rows_pad, int64_t kp,
-                                 T* __restrict__ out)
+                                 T* __restrict__ out, int beta = 0)
 {
     const int64_t quads = kp / 4;
     const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -391,11 +561,11 @@ __global__ void ozaki_slice_rows(const Planes<P> pl, int64_t rows, int64_t len, 
     const int64_t r = t / quads;
     const int64_t p0 = (t % quads) * 4;
     const int sg = r < rows ? sig[r] : 0;
-    typename CursorOf<P>::T cur[4];
+    typename KindCursor<P, KIND>::T cur[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int64_t p = p0 + u;
-        cur[u] = (r < rows && p < len) ? element_cursor<P>(pl, r * ld + p, sg, S) : zero_cursor<P>();
+        cur[u] = make_cursor<P, KIND>(pl, r * ld + p, r < rows && p < len, sg, S, beta);
     }
     T* o = out + r * kp + p0;
     const int64_t plane = rows_pad * kp;
@@ -408,39 +578,43 @@ __global__ void ozaki_slice_rows(const Planes<P> pl, int64_t rows, int64_t len, 
 // Rows of the sliced operand are strided (element (r, p) at base[p*ld + r]):
 // a 32 x 32 tile is read with r fastest, sliced, transposed through shared
 // memory and written with p fastest.
-template <int P, typename T>
+template <int P, typename T, int KIND = 0>
 __global__ void __launch_bounds__(256)
 ozaki_slice_cols(const Planes<P> pl, int64_t rows, int64_t len, int64_t ld,
                  const int* __restrict__ sig, int S, int64_t rows_pad, int64_t kp,
-                 T* __restrict__ out)
+                 T* __restrict__ out, int beta = 0)
 {
-    constexpr int SMAX = P == 2 ? kOzakiMaxSlices : kOzakiMaxSlicesWide;
-    __shared__ int8_t tile[SMAX][32][36];
+    constexpr int CHUNK = 16;               // digits (residues) staged per pass
+    __shared__ int8_t tile[CHUNK][32][36];
     const int64_t r0 = static_cast<int64_t>(blockIdx.x) * 32;
     const int64_t p0 = static_cast<int64_t>(blockIdx.y) * 32;
     const int tr = threadIdx.x & 31;        // r within the tile
     const int tp = threadIdx.x >> 5;        // 0..7: p = tp, tp + 8, tp + 16, tp + 24
     const int64_t r = r0 + tr;
     const int sg = r < rows ? sig[r] : 0;
-    typename CursorOf<P>::T cur[4];
+    typename KindCursor<P, KIND>::T cur[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int64_t p = p0 + tp + 8 * u;
-        cur[u] = (r < rows && p < len) ? element_cursor<P>(pl, p * ld + r, sg, S) : zero_cursor<P>();
+        cur[u] = make_cursor<P, KIND>(pl, p * ld + r, r < rows && p < len, sg, S, beta);
     }
-    for (int s = 0; s < S; ++s) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) tile[s][tr][tp + 8 * u] = static_cast<int8_t>(cur[u].next());
-    }
-    __syncthreads();
     // write: each thread writes 4 consecutive p of one row r
     const int wr = threadIdx.x >> 3;        // 0..31 row within tile
     const int wq = (threadIdx.x & 7) * 4;   // p offset
     const int64_t row = r0 + wr;
-    if (row < rows_pad && p0 + wq < kp) {
-        for (int s = 0; s < S; ++s)
-            store4(out + (static_cast<int64_t>(s) * rows_pad + row) * kp + p0 + wq, tile[s][wr][wq],
-                   tile[s][wr][wq + 1], tile[s][wr][wq + 2], tile[s][wr][wq + 3]);
+    for (int s0 = 0; s0 < S; s0 += CHUNK) {
+        const int cnt = S - s0 < CHUNK ? S - s0 : CHUNK;
+        for (int s = 0; s < cnt; ++s) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) tile[s][tr][tp + 8 * u] = static_cast<int8_t>(cur[u].next());
+        }
+        __syncthreads();
+        if (row < rows_pad && p0 + wq < kp) {
+            for (int s = 0; s < cnt; ++s)
+                store4(out + (static_cast<int64_t>(s0 + s) * rows_pad + row) * kp + p0 + wq, tile[s][wr][wq],
+                       tile[s][wr][wq + 1], tile[s][wr][wq + 2], tile[s][wr][wq + 3]);
+        }
+        __syncthreads();
     }
 }
 
@@ -764,6 +938,311 @@ __global__ void __launch_bounds__(WM * WN * 32, MINB) ozaki_gemm_kernel(const Oz
                     for (int c = 0; c < P; ++c) g.C[c][row * g.ldc + col] = acc[mt][nt][r][c];
                 }
             }
+}
+
+// ------------------------------------------------------- CRT products
+//
+// One modulus per grid z: Q_i = R_A,i R_B,i^T on mma.sync m16n8k32 s8 (exact
+// int32: |Q_i| <= k 2^14 < 2^31), reduced to its symmetric residue mod m_i
+// and stored as int8 [N][mp][np].  CTA of WM x WN warps, MT x NT fragments
+// of 16 x 8 per warp, KS bytes of k per cp.async stage (STG stages).
+
+struct CrtGemmArgs {
+    const int8_t* ra;       // [N][mp][kp] residues of op(A)
+    const int8_t* rb;       // [N][np][kp] residues of op(B)^T
+    int8_t* out;            // [N][mp][np] residues of the products
+    int64_t mp, np, kp;
+};
+
+template <int MT, int NT, int WM, int WN, int STG, int KS>
+__global__ void __launch_bounds__(WM * WN * 32) crt_gemm_kernel(const CrtGemmArgs g)
+{
+    constexpr int NTHR = WM * WN * 32;
+    constexpr int BM = WM * MT * 16;
+    constexpr int BN = WN * NT * 8;
+    constexpr int SROW = KS + 16;     // smem row stride in bytes: conflict-free fragment loads
+    constexpr int CPR = KS / 16;      // 16-byte chunks per row
+    extern __shared__ __align__(16) int8_t csm[];
+    int8_t* As = csm;                              // [STG][BM * SROW]
+    int8_t* Bs = csm + STG * BM * SROW;            // [STG][BN * SROW]
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int gq = lane >> 2, tq = lane & 3;
+    const int wm = warp / WN, wn = warp % WN;
+    const int64_t m0 = static_cast<int64_t>(blockIdx.y) * BM;
+    const int64_t n0 = static_cast<int64_t>(blockIdx.x) * BN;
+    const int mi = blockIdx.z;
+    const int KT = static_cast<int>(g.kp / KS);
+    const int8_t* a = g.ra + (static_cast<int64_t>(mi) * g.mp + m0) * g.kp;
+    const int8_t* b = g.rb + (static_cast<int64_t>(mi) * g.np + n0) * g.kp;
+
+    int ci[MT][NT][4];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) ci[mt][nt][r] = 0;
+
+    auto load = [&](int stage, int kt) {
+        for (int chunk = tid; chunk < (BM + BN) * CPR; chunk += NTHR) {
+            const int row = chunk / CPR, col = (chunk % CPR) * 16;
+            if (row < BM)
+                cp_async16(As + stage * BM * SROW + row * SROW + col,
+                           a + static_cast<int64_t>(row) * g.kp + static_cast<int64_t>(kt) * KS + col);
+            else
+                cp_async16(Bs + stage * BN * SROW + (row - BM) * SROW + col,
+                           b + static_cast<int64_t>(row - BM) * g.kp + static_cast<int64_t>(kt) * KS + col);
+        }
+    };
+#pragma unroll
+    for (int st = 0; st < STG - 1; ++st) {
+        if (st < KT) load(st, st);
+        cp_async_commit();
+    }
+    for (int it = 0; it < KT; ++it) {
+        cp_async_wait<STG - 2>();
+        __syncthreads();
+        if (it + STG - 1 < KT) load((it + STG - 1) % STG, it + STG - 1);
+        cp_async_commit();
+        const int8_t* as = As + (it % STG) * BM * SROW;
+        const int8_t* bs = Bs + (it % STG) * BN * SROW;
+#pragma unroll
+        for (int kk = 0; kk < KS; kk += 32) {
+            uint32_t af[MT][4], bf[NT][2];
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+                const int r = wm * MT * 16 + mt * 16 + gq;
+                af[mt][0] = *reinterpret_cast<const uint32_t*>(as + r * SROW + kk + 4 * tq);
+                af[mt][1] = *reinterpret_cast<const uint32_t*>(as + (r + 8) * SROW + kk + 4 * tq);
+                af[mt][2] = *reinterpret_cast<const uint32_t*>(as + r * SROW + kk + 16 + 4 * tq);
+                af[mt][3] = *reinterpret_cast<const uint32_t*>(as + (r + 8) * SROW + kk + 16 + 4 * tq);
+            }
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                const int c = wn * NT * 8 + nt * 8 + gq;
+                bf[nt][0] = *reinterpret_cast<const uint32_t*>(bs + c * SROW + kk + 4 * tq);
+                bf[nt][1] = *reinterpret_cast<const uint32_t*>(bs + c * SROW + kk + 16 + 4 * tq);
+            }
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) mma_s8(ci[mt][nt], af[mt], bf[nt]);
+        }
+    }
+    cp_async_wait<0>();
+
+    const int m = crt::kDev.m[mi];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t row = m0 + wm * MT * 16 + mt * 16 + gq + h * 8;
+                const int64_t col = n0 + wn * NT * 8 + nt * 8 + 2 * tq;
+                int8_t rr[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int v = ci[mt][nt][2 * h + u];
+                    const uint32_t mag = static_cast<uint32_t>(v < 0 ? -v : v);
+                    int r = static_cast<int>(crt::mod_small(mag, mi));
+                    if (v < 0 && r) r = m - r;
+                    rr[u] = static_cast<int8_t>(r >= (m + 1) / 2 ? r - m : r);
+                }
+                char2 pk;
+                pk.x = rr[0];
+                pk.y = rr[1];
+                *reinterpret_cast<char2*>(g.out + (static_cast<int64_t>(mi) * g.mp + row) * g.np + col) = pk;
+            }
+}
+
+// ------------------------------------------------------- CRT recovery
+//
+// Per output: the residues of Q_i give the mixed-radix digits of A'B' (Garner:
+// v_i = (r_i - (v_0 + v_1 m_0 + ... ) mod m_i) (m_0 ... m_(i-1))^-1 mod m_i,
+// all in small integers), Horner's rule turns them into the integer X in
+// [0, M) (11 32-bit limbs), X >= ceil(M/2) is taken as X - M, and the P
+// components of X 2^(sigma_i + tau_j - 2 beta) are rounded to nearest (ties
+// to even) one after another, each from the exact remainder of the previous
+// ones, with integer operations only.
+
+namespace crt {
+constexpr int kRecLimbs = 11;                     // M < 2^352
+}
+
+struct CrtRecArgs {
+    const int8_t* res;      // [N][mp][np] residues of the products
+    const int* sig;
+    const int* tau;
+    double* C[4];
+    int64_t ldc, m, n, mp, np;
+    int N, beta;
+    uint32_t M[crt::kRecLimbs];          // the product of the moduli
+    uint32_t H[crt::kRecLimbs];          // ceil(M / 2)
+};
+
+using Limbs = uint32_t[crt::kRecLimbs];
+
+// Word w of u (0 beyond the top), with a static loop so u stays in registers.
+__device__ __forceinline__ uint32_t limb_at(const Limbs& u, int w)
+{
+    uint32_t r = 0;
+#pragma unroll
+    for (int k = 0; k < crt::kRecLimbs; ++k) r = (k == w) ? u[k] : r;
+    return r;
+}
+
+__device__ __forceinline__ int bit_length(const Limbs& u)
+{
+    int bl = 0;
+#pragma unroll
+    for (int k = 0; k < crt::kRecLimbs; ++k)
+        if (u[k]) bl = 32 * k + (32 - __clz(static_cast<int>(u[k])));
+    return bl;
+}
+
+// Bits [pos, pos + 53) of u, pos >= 0.
+__device__ __forceinline__ uint64_t bits53(const Limbs& u, int pos)
+{
+    const int w = pos >> 5, off = pos & 31;
+    const unsigned __int128 x = static_cast<unsigned __int128>(limb_at(u, w)) |
+                                (static_cast<unsigned __int128>(limb_at(u, w + 1)) << 32) |
+                                (static_cast<unsigned __int128>(limb_at(u, w + 2)) << 64);
+    return static_cast<uint64_t>(x >> off) & ((1ull << 53) - 1);
+}
+
+// Whether any bit of u below position pos is set.
+__device__ __forceinline__ bool any_below(const Limbs& u, int pos)
+{
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < crt::kRecLimbs; ++k) {
+        const int lo = 32 * k;
+        const uint32_t mask = pos >= lo + 32 ? 0xffffffffu : (pos <= lo ? 0u : ((1u << (pos - lo)) - 1u));
+        any = any || (u[k] & mask) != 0u;
+    }
+    return any;
+}
+
+// u = u mod 2^s (s >= 1), then, when `complement`, u = 2^s - u (u != 0).
+__device__ __forceinline__ void low_bits(Limbs& u, int s, bool complement)
+{
+#pragma unroll
+    for (int k = 0; k < crt::kRecLimbs; ++k) {
+        const int lo = 32 * k;
+        const uint32_t mask = s >= lo + 32 ? 0xffffffffu : (s <= lo ? 0u : ((1u << (s - lo)) - 1u));
+        u[k] &= mask;
+    }
+    if (!complement) return;
+    uint32_t carry = 1;
+#pragma unroll
+    for (int k = 0; k < crt::kRecLimbs; ++k) {
+        const int lo = 32 * k;
+        const uint32_t mask = s >= lo + 32 ? 0xffffffffu : (s <= lo ? 0u : ((1u << (s - lo)) - 1u));
+        const uint64_t t = static_cast<uint64_t>(~u[k]) + carry;
+        u[k] = static_cast<uint32_t>(t) & mask;
+        carry = static_cast<uint32_t>(t >> 32);
+    }
+}
+
+// RN((-1)^neg u 2^e) as binary64 (ties to even; gradual underflow; +-inf
+// above the range); u and neg become the exact remainder (magnitude, sign).
+__device__ __forceinline__ double rn_component(Limbs& u, bool& neg, int e)
+{
+    const int bl = bit_length(u);
+    if (bl == 0) return 0.0;
+    const uint64_t sign = neg ? (1ull << 63) : 0ull;
+    const int E = bl - 1 + e;
+    int qx = E >= -1022 ? E - 52 : -1074;
+    const int s = qx - e;
+    uint64_t q;
+    if (s <= 0) {                                     // exactly representable
+        q = bits53(u, 0) << (-s);
+#pragma unroll
+        for (int k = 0; k < crt::kRecLimbs; ++k) u[k] = 0u;
+    } else {
+        q = bits53(u, s);
+        const bool half = (limb_at(u, (s - 1) >> 5) >> ((s - 1) & 31)) & 1u;
+        const bool up = half && ((q & 1ull) || any_below(u, s - 1));
+        low_bits(u, s, up);
+        if (up) {
+            ++q;
+            neg = !neg;
+        }
+        if (q == (1ull << 53)) {
+            q = 1ull << 52;
+            ++qx;
+        }
+    }
+    if (q == 0) return __longlong_as_double(static_cast<long long>(sign));     // a signed zero
+    if (q >= (1ull << 52) && qx + 52 > 1023) {                                  // beyond the range
+#pragma unroll
+        for (int k = 0; k < crt::kRecLimbs; ++k) u[k] = 0u;
+        return __longlong_as_double(static_cast<long long>(sign | 0x7ff0000000000000ull));
+    }
+    const uint64_t bits = q >= (1ull << 52)
+                              ? (static_cast<uint64_t>(qx + 52 + 1023) << 52) | (q - (1ull << 52))
+                              : q;                    // subnormal: qx = -1074
+    return __longlong_as_double(static_cast<long long>(sign | bits));
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) crt_recover_kernel(const CrtRecArgs g)
+{
+    const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= g.m * g.n) return;
+    const int64_t row = t / g.n, col = t % g.n;
+    uint32_t v[crt::kMaxModuli];
+    const int N = g.N;
+    for (int i = 0; i < N; ++i) {
+        const int mi = crt::kDev.m[i];
+        int r = g.res[(static_cast<int64_t>(i) * g.mp + row) * g.np + col];
+        if (r < 0) r += mi;
+        uint32_t ts = 0;
+        for (int j = 0; j < i; ++j) ts += v[j] * crt::kDev.pm[i][j];
+        const uint32_t d = static_cast<uint32_t>(r) + static_cast<uint32_t>(mi) - crt::mod_small(ts, i);
+        v[i] = crt::mod_small(d * crt::kDev.inv[i], i);
+    }
+    Limbs X;
+#pragma unroll
+    for (int k = 0; k < crt::kRecLimbs; ++k) X[k] = 0u;
+    X[0] = v[N - 1];
+    for (int i = N - 2; i >= 0; --i) {
+        const uint64_t mi = static_cast<uint64_t>(crt::kDev.m[i]);
+        uint64_t carry = v[i];
+#pragma unroll
+        for (int k = 0; k < crt::kRecLimbs; ++k) {
+            const uint64_t p = static_cast<uint64_t>(X[k]) * mi + carry;
+            X[k] = static_cast<uint32_t>(p);
+            carry = p >> 32;
+        }
+    }
+    // X >= ceil(M/2): the value is X - M < 0, magnitude M - X
+    bool ge = true;
+#pragma unroll
+    for (int k = crt::kRecLimbs - 1; k >= 0; --k) {
+        // compare from the top: the first differing word decides
+        if (X[k] != g.H[k]) {
+            ge = X[k] > g.H[k];
+            break;
+        }
+    }
+    bool neg = false;
+    if (ge) {
+        uint64_t borrow = 0;
+#pragma unroll
+        for (int k = 0; k < crt::kRecLimbs; ++k) {
+            const uint64_t d = static_cast<uint64_t>(g.M[k]) - X[k] - borrow;
+            X[k] = static_cast<uint32_t>(d);
+            borrow = (d >> 63) & 1ull;
+        }
+        neg = true;
+    }
+    const int e = g.sig[row] + g.tau[col] - 2 * g.beta;
+#pragma unroll
+    for (int c = 0; c < P; ++c) g.C[c][row * g.ldc + col] = rn_component(X, neg, e);
 }
 
 // ------------------------------------------------------- tcgen05 engine
@@ -1885,10 +2364,10 @@ static unsigned blocks_for(int64_t threads, int per) { return static_cast<unsign
 
 // Slice one operand: vectors (rows of op(A) or columns of op(B)) of length
 // len; `contig` says whether a vector's elements are adjacent in memory.
-template <int P, typename T>
+template <int P, typename T, int KIND = 0>
 static cudaError_t slice_operand(const Planes<P>& pl, int64_t count, int64_t len, int64_t ld,
                                  bool contig, int S, int64_t count_pad, int64_t kp, T* out,
-                                 int* sig, cudaStream_t s)
+                                 int* sig, cudaStream_t s, int beta = 0)
 {
     const double* lead = pl.c[0];
     if (contig) ozaki_scale_contig<<<blocks_for(count * 32, 256), 256, 0, s>>>(lead, count, len, ld, sig);
@@ -1896,11 +2375,11 @@ static cudaError_t slice_operand(const Planes<P>& pl, int64_t count, int64_t len
     if (count_pad > count)
         ozaki_fill_int<<<blocks_for(count_pad - count, 256), 256, 0, s>>>(sig, count, count_pad);
     if (contig) {
-        ozaki_slice_rows<P, T><<<blocks_for(count_pad * (kp / 4), 128), 128, 0, s>>>(
-            pl, count, len, ld, sig, S, count_pad, kp, out);
+        ozaki_slice_rows<P, T, KIND><<<blocks_for(count_pad * (kp / 4), 128), 128, 0, s>>>(
+            pl, count, len, ld, sig, S, count_pad, kp, out, beta);
     } else {
         const dim3 grid(static_cast<unsigned>(count_pad / 32), static_cast<unsigned>(kp / 32));
-        ozaki_slice_cols<P, T><<<grid, 256, 0, s>>>(pl, count, len, ld, sig, S, count_pad, kp, out);
+        ozaki_slice_cols<P, T, KIND><<<grid, 256, 0, s>>>(pl, count, len, ld, sig, S, count_pad, kp, out, beta);
     }
     return cudaGetLastError();
 }
@@ -1950,9 +2429,9 @@ static cudaError_t side_stream(SideStream** out)
 }
 
 // Slices op(A) on stream s and op(B) on the side stream, joined back to s.
-template <int P, typename T>
+template <int P, typename T, int KIND = 0>
 static cudaError_t slice_both(const GemmArgs<P>& g, int S, const OzakiLayout& L, T* sa, T* sb, int* sig,
-                              int* tau, cudaStream_t s)
+                              int* tau, cudaStream_t s, int beta = 0)
 {
     Planes<P> pa, pb;
     for (int c = 0; c < P; ++c) {
@@ -1965,9 +2444,11 @@ static cudaError_t slice_both(const GemmArgs<P>& g, int S, const OzakiLayout& L,
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ss->s, ss->fork, 0);
     // op(A) row i: contiguous unless A is stored transposed; op(B) column j:
     // contiguous only if B is stored transposed
-    if (e == cudaSuccess) e = slice_operand(pb, g.n, g.k, g.ldb, g.trans_b != 0, S, L.np, L.kp, sb, tau, ss->s);
+    if (e == cudaSuccess)
+        e = slice_operand<P, T, KIND>(pb, g.n, g.k, g.ldb, g.trans_b != 0, S, L.np, L.kp, sb, tau, ss->s, beta);
     if (e == cudaSuccess) e = cudaEventRecord(ss->join, ss->s);
-    if (e == cudaSuccess) e = slice_operand(pa, g.m, g.k, g.lda, !g.trans_a, S, L.mp, L.kp, sa, sig, s);
+    if (e == cudaSuccess)
+        e = slice_operand<P, T, KIND>(pa, g.m, g.k, g.lda, !g.trans_a, S, L.mp, L.kp, sa, sig, s, beta);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ss->join, 0);
     return e;
 }
@@ -2180,5 +2661,106 @@ cudaError_t launch_ozaki(const GemmArgs<P>& g, int S, void* ws, cudaStream_t s, 
 template cudaError_t launch_ozaki<2>(const GemmArgs<2>&, int, void*, cudaStream_t, int, int);
 template cudaError_t launch_ozaki<3>(const GemmArgs<3>&, int, void*, cudaStream_t, int, int);
 template cudaError_t launch_ozaki<4>(const GemmArgs<4>&, int, void*, cudaStream_t, int, int);
+
+
+// ----------------------------------------------------- CRT form, host side
+
+OzakiLayout crt_layout(int N, int64_t m, int64_t n, int64_t k, int elem_bytes)
+{
+    OzakiLayout L;
+    L.S = N;
+    L.mp = round_up(m > 0 ? m : 1, 128);
+    L.np = round_up(n > 0 ? n : 1, 128);
+    L.kp = round_up(k > 0 ? k : 1, KPAD);
+    L.offA = 0;
+    L.offB = round_up(static_cast<int64_t>(N) * L.mp * L.kp * elem_bytes, 256);
+    L.offSig = L.offB + round_up(static_cast<int64_t>(N) * L.np * L.kp * elem_bytes, 256);
+    L.offTau = L.offSig + round_up(L.mp * 4, 256);
+    L.offScr = L.offTau + round_up(L.np * 4, 256);      // [N][mp][np] int8 residues of the products
+    L.total = L.offScr + round_up(static_cast<int64_t>(N) * L.mp * L.np, 256);
+    return L;
+}
+
+// M = m_0 ... m_(N-1) in 32-bit limbs.
+static void crt_modulus(int N, uint32_t (&M)[crt::kRecLimbs])
+{
+    for (int k = 0; k < crt::kRecLimbs; ++k) M[k] = 0;
+    M[0] = 1;
+    for (int i = 0; i < N; ++i) {
+        uint64_t carry = 0;
+        for (int k = 0; k < crt::kRecLimbs; ++k) {
+            const uint64_t p = static_cast<uint64_t>(M[k]) * static_cast<uint32_t>(crt::kHost.m[i]) + carry;
+            M[k] = static_cast<uint32_t>(p);
+            carry = p >> 32;
+        }
+    }
+}
+
+int crt_beta(int N, int64_t k)
+{
+    if (N < 1 || N > crt::kMaxModuli || k < 0) return -1;
+    uint32_t T[crt::kRecLimbs];
+    crt_modulus(N, T);
+    // T = floor((M - 1) / k): the largest beta with k 2^(2 beta - 1) < M is
+    // floor(bitlength(T) / 2)
+    for (int w = 0; w < crt::kRecLimbs; ++w) {
+        if (T[w]--) break;                 // M - 1 (M >= 2)
+    }
+    const uint64_t d = static_cast<uint64_t>(k > 0 ? k : 1);
+    uint64_t rem = 0;
+    for (int w = crt::kRecLimbs - 1; w >= 0; --w) {
+        const uint64_t cur = (rem << 32) | T[w];
+        T[w] = static_cast<uint32_t>(cur / d);
+        rem = cur % d;
+    }
+    int bl = 0;
+    for (int w = 0; w < crt::kRecLimbs; ++w)
+        if (T[w]) bl = 32 * w + (32 - __builtin_clz(T[w]));
+    return bl / 2;
+}
+
+template <int P>
+cudaError_t launch_crt(const GemmArgs<P>& g, int N, void* ws, cudaStream_t s)
+{
+    const int beta = crt_beta(N, g.k);
+    if (beta < 1) return cudaErrorInvalidValue;
+    const OzakiLayout L = crt_layout(N, g.m, g.n, g.k, 1);
+    int8_t* base = static_cast<int8_t*>(ws);
+    int* sig = reinterpret_cast<int*>(base + L.offSig);
+    int* tau = reinterpret_cast<int*>(base + L.offTau);
+    int8_t* ra = base + L.offA;
+    int8_t* rb = base + L.offB;
+    int8_t* rq = base + L.offScr;
+    cudaError_t e = slice_both<P, int8_t, 1>(g, N, L, ra, rb, sig, tau, s, beta);
+    if (e != cudaSuccess) return e;
+    // 128 x 128 CTA tile, 8 warps of 64 x 32, 4 stages of 64 bytes of k
+    constexpr int MT = 4, NT = 4, WM = 2, WN = 4, STG = 4, KS = 64;
+    constexpr int smem = STG * (WM * MT * 16 + WN * NT * 8) * (KS + 16);
+    e = cudaFuncSetAttribute(crt_gemm_kernel<MT, NT, WM, WN, STG, KS>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const CrtGemmArgs ga{ra, rb, rq, L.mp, L.np, L.kp};
+    const dim3 grid(static_cast<unsigned>(L.np / 128), static_cast<unsigned>(L.mp / 128), static_cast<unsigned>(N));
+    crt_gemm_kernel<MT, NT, WM, WN, STG, KS><<<grid, WM * WN * 32, smem, s>>>(ga);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    CrtRecArgs ra_{rq, sig, tau, {nullptr, nullptr, nullptr, nullptr}, g.ldc, g.m, g.n, L.mp, L.np, N, beta, {}, {}};
+    for (int c = 0; c < P; ++c) ra_.C[c] = g.C[c];
+    crt_modulus(N, ra_.M);
+    // H = ceil(M / 2) = (M + 1) >> 1
+    uint32_t M1[crt::kRecLimbs];
+    for (int k = 0; k < crt::kRecLimbs; ++k) M1[k] = ra_.M[k];
+    for (int k = 0; k < crt::kRecLimbs; ++k)
+        if (++M1[k]) break;
+    for (int k = 0; k < crt::kRecLimbs; ++k)
+        ra_.H[k] = (M1[k] >> 1) | (k + 1 < crt::kRecLimbs ? (M1[k + 1] << 31) : 0u);
+    const int64_t outs = g.m * g.n;
+    crt_recover_kernel<P><<<blocks_for(outs, 256), 256, 0, s>>>(ra_);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_crt<2>(const GemmArgs<2>&, int, void*, cudaStream_t);
+template cudaError_t launch_crt<3>(const GemmArgs<3>&, int, void*, cudaStream_t);
+template cudaError_t launch_crt<4>(const GemmArgs<4>&, int, void*, cudaStream_t);
 
 }  // namespace mpg

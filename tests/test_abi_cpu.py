@@ -178,7 +178,7 @@ def test_slicing_options(L):
 
 
 def test_version(L):
-    assert L.mpgemm_version() == 102
+    assert L.mpgemm_version() == 103
 
 
 def test_tc_status_validation(L):
@@ -275,3 +275,32 @@ def test_binary64_product_validation(L):
     info = (ctypes.c_int * 6)()
     assert L.mpgemm_tile_info(1, 1, ctypes.byref(info)) == 0 and list(info)[:2] == [64, 64]
     assert L.mpgemm_version() >= 102
+
+
+def test_crt_form_host_checks(L):
+    """The CRT form's bit count agrees with the oracle's definition for every
+    moduli count and several k (which checks the library's moduli and their
+    product), its workspace follows the stated layout, and bad requests are
+    refused before any launch."""
+    from oracle import crt as R
+    from paper_2101_06584_gb300.mpgemm import Opts
+    for N in range(1, 50):
+        for k in (1, 2, 127, 1024, 4096, 37449, 131071):
+            assert L.mpgemm_crt_beta(N, k) == R.beta_bits(N, k), (N, k)
+    assert L.mpgemm_crt_beta(0, 8) == -1 and L.mpgemm_crt_beta(50, 8) == -1
+    r = lambda x: (x + 127) // 128 * 128
+    r256 = lambda x: (x + 255) // 256 * 256
+    for (m, n, k, N) in ((100, 70, 300, 28), (4096, 4096, 4096, 26), (1, 1, 1, 49)):
+        o = Opts(0, 0, 4, 0, N, 0, None, 0)
+        want = (r256(N * r(m) * r(k)) + r256(N * r(n) * r(k)) + r256(4 * r(m)) + r256(4 * r(n)) +
+                r256(N * r(m) * r(n)))
+        assert L.mpgemm_workspace_size(2, ctypes.byref(o), m, n, k) == want
+    A, B, C = planes(FAKE, 2), planes(2 * FAKE, 2), planes(3 * FAKE, 2)
+    for N, k, code, text in ((50, 8, -1, "moduli"), (1, 200, -4, "no bits"), (28, 8, -3, "workspace")):
+        o = Opts(0, 0, 4, 0, N, 0, None, 0)
+        assert L.mpgemm_ex(2, ctypes.byref(o), 8, 8, k, A, k, B, 8, C, 8) == code
+        assert text in err(L)
+    o = Opts(0, 0, 4, 0, 28, 0, None, 0)
+    big = 131072
+    assert L.mpgemm_ex(2, ctypes.byref(o), 8, 8, big, A, big, B, 8, C, 8) == -4
+    assert "int32" in err(L)

@@ -1,0 +1,132 @@
+"""The CRT form (MPG_ALGO_INT8_CRT) on the GPU against its oracle
+(oracle/crt.py): the residues in the workspace equal the oracle's for every
+modulus; the results are bit-identical to the oracle's steps for DD, TD and
+QD, ragged shapes spanning several tiles, both transposes, cancelling inputs,
+outputs down to the subnormal range, one modulus and all 49, and at the
+largest k the form accepts; at the DD 4096^3 workload's full size a 16 x 16
+grid of entries is bit-identical and two whole rows are within n 2^-100 of
+the exact product."""
+import numpy as np
+import pytest
+
+from gpu_util import assert_bitwise, dev, host, torch_cuda
+from oracle import crt as R
+from oracle import exact as X
+from paper_2101_06584_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return torch_cuda()
+
+
+def _run(torch, prec, A, B, N, trans_a=False, trans_b=False):
+    from paper_2101_06584_gb300 import mpgemm as mm
+    Ad = dev(torch, A.transpose(0, 2, 1) if trans_a else A)
+    Bd = dev(torch, B.transpose(0, 2, 1) if trans_b else B)
+    m, k = A.shape[1], A.shape[2]
+    n = B.shape[2]
+    ws = torch.empty(mm.workspace_size(prec, m, n, k, algo="crt", slices=N), dtype=torch.uint8, device="cuda")
+    C = mm.gemm(prec, Ad, Bd, trans_a=trans_a, trans_b=trans_b, algo="crt", slices=N, workspace=ws)
+    return host(C), host(ws)
+
+
+def _layout(N, m, n, k):
+    r = lambda x, q: (max(x, 1) + q - 1) // q * q
+    mp, np_, kp = r(m, 128), r(n, 128), r(k, 128)
+    offB = r(N * mp * kp, 256)
+    offSig = offB + r(N * np_ * kp, 256)
+    offTau = offSig + r(mp * 4, 256)
+    return mp, np_, kp, offB, offSig, offTau
+
+
+@pytest.mark.parametrize("prec,N", [("dd", 1), ("dd", 28), ("td", 44), ("qd", 49)])
+def test_residues_and_result_bitwise(torch, prec, N):
+    P = I.P_OF[prec]
+    rng = np.random.default_rng(800 + P + N)
+    m, n, k = 37, 45, 53 if N > 1 else 3
+    A, B = I.uniform(P, (m, k), rng), I.ill_scaled(P, (k, n), rng)
+    C, ws = _run(torch, prec, A, B, N)
+    beta = R.beta_bits(N, k)
+    mp, np_, kp, offB, offSig, offTau = _layout(N, m, n, k)
+    sig, RA = R.residues(A, N, beta)
+    tau, RB = R.residues(np.ascontiguousarray(B.transpose(0, 2, 1)), N, beta)
+    ga = ws[:N * mp * kp].view(np.int8).reshape(N, mp, kp)
+    gb = ws[offB:offB + N * np_ * kp].view(np.int8).reshape(N, np_, kp)
+    assert (ws[offSig:offSig + 4 * m].view(np.int32) == sig).all()
+    assert (ws[offTau:offTau + 4 * n].view(np.int32) == tau).all()
+    assert (ga[:, :m, :k] == RA).all() and not ga[:, m:, :].any() and not ga[:, :, k:].any()
+    assert (gb[:, :n, :k] == RB).all() and not gb[:, n:, :].any() and not gb[:, :, k:].any()
+    want, _, _, _ = R.gemm(A, B, N)
+    assert_bitwise(C, want, "%s crt N=%d" % (prec, N))
+
+
+@pytest.mark.parametrize("prec", ["dd", "td"])
+def test_transposes_tiles_and_cancellation(torch, prec):
+    """Several 128 x 128 tiles with ragged edges, every transpose, cancelling
+    ill-scaled operands."""
+    P = I.P_OF[prec]
+    rng = np.random.default_rng(810 + P)
+    A, B = I.cancelling_pair(P, 150, 270, 140, rng)
+    N = 28 if prec == "dd" else 44
+    want, _, _, _ = R.gemm(A, B, N)
+    for ta, tb in ((False, False), (True, False), (False, True), (True, True)):
+        C, _ = _run(torch, prec, A, B, N, trans_a=ta, trans_b=tb)
+        assert_bitwise(C, want, "%s crt trans %s %s" % (prec, ta, tb))
+
+
+@pytest.mark.parametrize("prec", ["dd", "qd"])
+def test_products_below_the_normal_range(torch, prec):
+    """Rows of A scaled by 1 .. 2^-1060 and columns of B by 1 .. 2^-530: the
+    components of the recovered products run through the subnormal range and
+    down to signed zeros; every entry bit-identical to the oracle."""
+    P = I.P_OF[prec]
+    rng = np.random.default_rng(820 + P)
+    m, n, k = 40, 36, 64
+    A, B = I.uniform(P, (m, k), rng), I.uniform(P, (k, n), rng)
+    A *= np.array([1.0, 2.0 ** -500, 2.0 ** -530, 2.0 ** -1060])[np.arange(m) % 4][None, :, None]
+    B *= np.array([1.0, 2.0 ** -500, 2.0 ** -530])[(np.arange(n) // 2) % 3][None, None, :]
+    C, _ = _run(torch, prec, A, B, 30)
+    want, _, _, _ = R.gemm(A, B, 30)
+    assert ((np.abs(want) < 2.0 ** -1022) & (want != 0)).any() and np.isfinite(want).all()
+    assert_bitwise(C, want, "%s crt tiny products" % prec)
+
+
+def test_largest_k_and_refusal(torch):
+    """k = 131071, the largest whose residue products sum exactly in int32:
+    sampled entries bit-identical to the oracle; k + 1 is refused."""
+    from paper_2101_06584_gb300 import mpgemm as mm
+    k = R.k_limit()
+    m = n = 16
+    rng = np.random.default_rng(830)
+    A, B = I.uniform(2, (m, k), rng), I.uniform(2, (k, n), rng)
+    C, _ = _run(torch, "dd", A, B, 40)
+    want, _, _, _ = R.gemm(A, B, 40, rows=[0, 15], cols=[3, 9])
+    assert_bitwise(C[:, [0, 15]][:, :, [3, 9]], want, "crt at the largest k")
+    A1 = np.concatenate([A, np.zeros((2, m, 1))], axis=2)
+    B1 = np.concatenate([B, np.zeros((2, 1, n))], axis=1)
+    with pytest.raises(mm.MPGError) as e:
+        mm.gemm("dd", dev(torch, A1), dev(torch, B1), algo="crt", slices=40,
+                workspace=torch.empty(1 << 20, dtype=torch.uint8, device="cuda"))
+    assert e.value.code == -4
+
+
+def test_full_size_dd(torch):
+    """DD 4096^3 on the uniform inputs of that workload's seed, 28 moduli:
+    a 16 x 16 grid of random rows and columns bit-identical to the oracle,
+    and two whole rows with the grid within n 2^-100 of the exact product."""
+    n = 4096
+    rng = I.rng_for(2)
+    A, B = I.uniform(2, (n, n), rng), I.uniform(2, (n, n), rng)
+    C, _ = _run(torch, "dd", A, B, 28)
+    srng = np.random.default_rng(840)
+    rows = sorted(int(x) for x in srng.choice(n, 16, replace=False))
+    cols = sorted(int(x) for x in srng.choice(n, 16, replace=False))
+    want, _, _, _ = R.gemm(A, B, 28, rows=rows, cols=cols)
+    assert_bitwise(C[:, rows][:, :, cols], want, "crt 4096 grid")
+    full = sorted(int(x) for x in srng.choice(n, 2, replace=False))
+    ent = sorted({(i, j) for i in full for j in range(n)} | {(i, j) for i in rows for j in cols})
+    err = X.gemm_error(C, A, B, ent)
+    assert err["err_abs"] <= n * 2.0 ** -100, err
