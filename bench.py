@@ -72,6 +72,8 @@ TRAFFIC_SOURCES = {
     "td_qd": ["mp_arith.cuh", "gemm_kernel.cuh", "gemm_qd.cu", "internal.h"],
     "dd_int8": ["mp_arith.cuh", "ozaki.cu", "ozaki.h", "internal.h"],
     "dd_tc": ["mp_arith.cuh", "ozaki.cu", "ozaki.h", "internal.h"],
+    "dd_crtint8": ["ozaki.cu", "ozaki.h", "internal.h"],
+    "dd_crttc": ["ozaki.cu", "ozaki.h", "internal.h"],
 }
 
 
@@ -107,7 +109,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="td_qd",
-                    choices=["td_qd", "dd_small", "dd_int8", "dd_tc", "td_qd_int8", "td_qd_tc",
+                    choices=["td_qd", "dd_small", "dd_int8", "dd_tc", "dd_crt", "dd_crt_int8", "td_qd_int8", "td_qd_tc",
                              "batched", "autograd", "elementwise", "strassen", "autograd_tc"])
     ap.add_argument("--size", type=int, default=None, help="override the workload's m = n = k")
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads")
@@ -605,9 +607,14 @@ class DdInt8(Workload):
     the smallest that meets the DD bound n 2^-100 on the sampled entries."""
     name = "dd_int8"
 
+    # (algo, first slice count tried, largest allowed, fixed count without the search)
+    FORMS = {"int8": ("int8", 14, 16, FIXED_SLICES["dd"]), "tc": ("bf16", 14, 16, FIXED_SLICES["dd"]),
+             "crt_int8": ("crt", 28, 49, 28), "crt_tc": ("crt_bf16", 28, 49, 28)}
+
     def __init__(self, torch, mm, I, rank, n=4096, S=None, engine="int8"):
         self.torch, self.mm, self.n, self.engine = torch, mm, n, engine
-        self.algo = "int8" if engine == "int8" else "bf16"
+        self.algo, self.s_start, self.s_max, s_fixed = self.FORMS[engine]
+        self.crt = self.algo.startswith("crt")
         rng = replica_rng(2, rank)
         A, B = I.uniform(2, (n, n), rng), I.uniform(2, (n, n), rng)
         self.host = (A, B)
@@ -616,7 +623,7 @@ class DdInt8(Workload):
         self.C = torch.empty((2, n, n), dtype=torch.float64, device="cuda")
         self.search = None
         if S is None:
-            S, self.search = self._choose(n) if _ACC["enabled"] else (FIXED_SLICES["dd"], None)
+            S, self.search = self._choose(n) if _ACC["enabled"] else (s_fixed, None)
         self.S = S
         self.ws = torch.empty(mm.workspace_size("dd", n, n, n, algo=self.algo, slices=S),
                               dtype=torch.uint8, device="cuda")
@@ -625,12 +632,17 @@ class DdInt8(Workload):
         self.launches_per_step = 5 if n % 128 == 0 else 7
         if engine != "int8":
             self.launches_per_step += 1          # the workspace-header clear
-        eng = ("mma.sync s8 engine" if engine == "int8"
-               else "tcgen05 engine (digits as bf16, TMEM accumulators)")
-        self.config = {"workload": "DD GEMM m=n=k=%d, INT8 error-free slicing form, S=%d, %s" % (n, S, eng),
+        eng = ("mma.sync s8 engine" if engine in ("int8", "crt_int8")
+               else "tcgen05 engine (bf16 operands, TMEM accumulators)")
+        if self.crt:
+            form = "CRT form (Ozaki scheme II), N=%d moduli, beta=%d bits" % (S, mm.crt_beta(S, n))
+            self.launches_per_step = 6 + (1 if engine == "crt_tc" else 0)
+        else:
+            form = "INT8 error-free slicing form, S=%d" % S
+        self.config = {"workload": "DD GEMM m=n=k=%d, %s, %s" % (n, form, eng),
                        "m": n, "n": n, "k": n, "slices": S, "engine": engine,
-                       "slices_rule": "smallest S meeting n 2^-100 on the sampled entries"
-                       if self.search is not None else "given"}
+                       "slices_rule": ("smallest %s meeting n 2^-100 on the sampled entries" %
+                                       ("N" if self.crt else "S")) if self.search is not None else "given"}
 
     def reference(self):
         n = self.n
@@ -643,9 +655,9 @@ class DdInt8(Workload):
             ws = self.torch.empty(self.mm.workspace_size("dd", n, n, n, algo=self.algo, slices=S),
                                   dtype=self.torch.uint8, device="cuda")
             return self.mm.gemm("dd", self.A, self.B, out=self.C, algo=self.algo, slices=S, workspace=ws)
-        S, tried = choose_slices(run, ref, n * 2.0 ** -100, 14, 16)
+        S, tried = choose_slices(run, ref, n * 2.0 ** -100, self.s_start, self.s_max)
         if S is None:
-            raise RuntimeError("no slice count up to 16 meets n 2^-100: %r" % tried)
+            raise RuntimeError("no count up to %d meets n 2^-100: %r" % (self.s_max, tried))
         return S, {str(k): v for k, v in sorted(tried.items())}
 
     def timed_step(self, stream):
@@ -672,13 +684,21 @@ class DdInt8(Workload):
 
     def roofline(self, launch_ms, pk):
         S, n = self.S, self.n
-        pairs = S * (S + 1) // 2
+        pairs = S if self.crt else S * (S + 1) // 2
         ops = 2.0 * pairs * n ** 3
         ms = statistics.mean(launch_ms["call"])
         ach = ops / (ms * 1e-3)
         self.plain_C = self.torch.empty_like(self.C)
         plain_ms = _time_call(self.torch, lambda: self.mm.gemm_plain("dd", self.A, self.B, out=self.plain_C), 1)
-        if self.engine == "int8":
+        if self.engine == "crt_int8":
+            peak, src, unit, kern = (pk["mma_s8"], "measured mma.sync s8 probe at this run's clocks",
+                                     "Tint8op/s", "crt_gemm_kernel (mma.sync m16n8k32 s8) incl. residues and recovery")
+            key = "dd_crtint8_%d_s%d:call" % (n, S)
+        elif self.engine == "crt_tc":
+            peak, src = bf16_peak()
+            unit, kern = "TFLOP/s", "crt_tc_kernel (tcgen05.mma kind::f16, 128 x 128) incl. residues and recovery"
+            key = "dd_crttc_%d_s%d:call" % (n, S)
+        elif self.engine == "int8":
             peak, src, unit, kern = (pk["mma_s8"], "measured mma.sync s8 probe at this run's clocks "
                                      "(tcgen05 has no int8 kind on sm_103a)", "Tint8op/s",
                                      "ozaki_gemm_kernel (mma.sync m16n8k32 s8) incl. slicing")
@@ -691,9 +711,23 @@ class DdInt8(Workload):
         return {"bound": "tensor", "kernel": kern, "achieved": ach / 1e12, "peak": peak / 1e12,
                 "unit": unit, "frac": ach / peak, "traffic": recorded_traffic(key),
                 "ops_per_unit": 2 * pairs,
-                "unit_of_work": "DD multiply-add (%d slice-pair MACs)" % pairs,
+                "unit_of_work": "DD multiply-add (%d %s MACs)" % (pairs, "residue" if self.crt else "slice-pair"),
                 "units_per_launch": n ** 3, "peak_source": src,
                 "fp64_eft_ms": plain_ms, "speedup_vs_fp64_eft": plain_ms / ms}
+
+
+class DdCrt(DdInt8):
+    name = "dd_crt"
+
+    def __init__(self, torch, mm, I, rank, n=4096):
+        super().__init__(torch, mm, I, rank, n=n, engine="crt_tc")
+
+
+class DdCrtInt8(DdInt8):
+    name = "dd_crt_int8"
+
+    def __init__(self, torch, mm, I, rank, n=4096):
+        super().__init__(torch, mm, I, rank, n=n, engine="crt_int8")
 
 
 class TdQdInt8(Workload):
@@ -1057,7 +1091,8 @@ class AutogradTc(Autograd):
                 "unit_of_work": "DD multiply-add (%d slice-pair MACs)" % pairs, "units_per_launch": self.n ** 3}
 
 
-WORKLOADS = {"td_qd": TdQd, "dd_small": DdSmall, "dd_int8": DdInt8, "dd_tc": DdTc,
+WORKLOADS = {"td_qd": TdQd, "dd_small": DdSmall, "dd_int8": DdInt8, "dd_tc": DdTc, "dd_crt": DdCrt,
+             "dd_crt_int8": DdCrtInt8,
              "td_qd_int8": TdQdInt8, "td_qd_tc": TdQdTc, "batched": Batched, "autograd": Autograd,
              "elementwise": Elementwise, "strassen": Strassen, "autograd_tc": AutogradTc}
 
@@ -1184,7 +1219,7 @@ def sliced_summary(configs):
     workload, at the slice count chosen to meet the same bound n 2^-100 that
     the plain product meets, with the binary64-only product's error beside."""
     out = {}
-    for name in ("dd_tc", "dd_int8"):
+    for name in ("dd_crt", "dd_tc", "dd_crt_int8", "dd_int8"):
         c = configs.get(name)
         if not c:
             continue
@@ -1202,8 +1237,8 @@ def sliced_summary(configs):
 def extras(torch, mm, I, pk, flush):
     """One short measurement of each other workload (rank 0, after the main one)."""
     out = {}
-    for name in ("dd_small", "dd_int8", "dd_tc", "td_qd_int8", "td_qd_tc", "batched", "autograd", "autograd_tc",
-                 "elementwise", "strassen"):
+    for name in ("dd_small", "dd_int8", "dd_tc", "dd_crt", "dd_crt_int8", "td_qd_int8", "td_qd_tc", "batched",
+                 "autograd", "autograd_tc", "elementwise", "strassen"):
         w = WORKLOADS[name](torch, mm, I, 0)
         steps = {"dd_small": 10, "elementwise": 10, "strassen": 1}.get(name, 2)
         total_ms, launch_ms, _, _ = measure(torch, w, steps, 1, 1, 0, flush, sample_clocks=False)

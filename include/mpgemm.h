@@ -59,7 +59,8 @@ void *mpgemm_get_stream(void);
 /* Library ABI version (major * 100 + minor): 101 adds the TD/QD variants,
  * mpgemm_default_tile and mpgemm_tc_status to 100; 102 adds mpgemm_d and
  * P = 1 in mpgemm_ex, mpgemm_num_tiles, mpgemm_tile_info and
- * mpgemm_default_tile; 103 adds MPG_ALGO_INT8_CRT and mpgemm_crt_beta. */
+ * mpgemm_default_tile; 103 adds MPG_ALGO_INT8_CRT, MPG_ALGO_BF16_CRT and
+ * mpgemm_crt_beta. */
 int mpgemm_version(void);
 
 /* ---------------------------------------------------------------------
@@ -178,7 +179,8 @@ typedef enum mpg_algo {
     MPG_ALGO_FP64_EFT = 1,   /* FP64 error-free transformations on the CUDA cores */
     MPG_ALGO_INT8_OZAKI = 2, /* DD/TD/QD: error-free INT8 slicing on the tensor cores */
     MPG_ALGO_BF16_SLICES = 3, /* DD/TD/QD: the same digits as bf16 on tcgen05 (TMEM accumulators) */
-    MPG_ALGO_INT8_CRT = 4     /* DD/TD/QD: residues modulo small coprime moduli on the tensor cores */
+    MPG_ALGO_INT8_CRT = 4,    /* DD/TD/QD: residues modulo small coprime moduli on the tensor cores */
+    MPG_ALGO_BF16_CRT = 5     /* DD/TD/QD: the same residues as bf16 on tcgen05 (TMEM accumulators) */
 } mpg_algo;
 
 /* Options of mpgemm_ex.  Zero-initialised options give the plain call. */
@@ -286,7 +288,17 @@ int mpgemm_ex(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k,
  * aligned, not overlapping A, B or C), with mp, np, kp = m, n, k rounded up
  * to 128 and each region on a 256-byte boundary: int8 [N][mp][kp] residues
  * of op(A), int8 [N][np][kp] of op(B)^T, int32 [mp] sigma, int32 [np] tau,
- * int8 [N][mp][np] residues of the products. */
+ * int8 [N][mp][np] residues of the products.
+ *
+ * MPG_ALGO_BF16_CRT: the same residues, products and result (bit-identical
+ * to MPG_ALGO_INT8_CRT), with the residues stored as bf16 (exact: |r| <= 128),
+ * loaded by TMA and multiplied by tcgen05.mma (kind::f16, M = N = 128, fp32
+ * accumulation in tensor memory); each accumulator is drained into an exact
+ * int32 sum after at most 1024 values of k, so every fp32 partial sum is an
+ * integer below 2^24.  Workspace: a 256-byte header whose first int32 is 0
+ * after a normal run (else the code of the role whose bounded wait gave up,
+ * read by mpgemm_tc_status), then the regions above with the residues of
+ * op(A) and op(B)^T as bf16 (2 bytes each). */
 
 /* beta of the CRT form for N moduli and inner dimension k (>= 1 when the
  * form applies, 0 when the moduli's product is too small); MPG_EINVAL for N

@@ -219,7 +219,8 @@ static int crt_call(const GemmArgs<P>& g, const mpgemm_opts* o)
     if (beta < 1)
         return fail(MPG_EUNSUPPORTED, "%d moduli leave no bits for k = %lld (their product must exceed 2k)", N,
                     (long long)g.k);
-    const OzakiLayout L = crt_layout(N, g.m, g.n, g.k);
+    const int engine = o->algo == MPG_ALGO_BF16_CRT ? 1 : 0;
+    const OzakiLayout L = crt_layout(N, g.m, g.n, g.k, engine);
     if (L.mp / 128 > 65535) return fail(MPG_EINVAL, "m too large for the CRT form's grid");
     if (!o->workspace) return fail(MPG_EWORKSPACE, "the CRT form needs a workspace of %lld bytes",
                                    (long long)L.total);
@@ -237,7 +238,7 @@ static int crt_call(const GemmArgs<P>& g, const mpgemm_opts* o)
             overlap(rw, plane_range(g.C[c], g.m, g.n, g.ldc)))
             return fail(MPG_EWORKSPACE, "workspace overlaps an operand");
     }
-    cudaError_t e = launch_crt<P>(g, N, o->workspace, g_stream);
+    cudaError_t e = launch_crt<P>(g, N, o->workspace, g_stream, engine);
     return e == cudaSuccess ? MPG_OK : cuda_fail(e, "CRT gemm launch");
 }
 
@@ -262,9 +263,9 @@ static int gemm_call(const mpgemm_opts* o, int64_t m, int64_t n, int64_t k,
     if (m == 0 || n == 0) return MPG_OK;
     const int algo = o ? o->algo : MPG_ALGO_AUTO;
     if (algo != MPG_ALGO_AUTO && algo != MPG_ALGO_FP64_EFT && algo != MPG_ALGO_INT8_OZAKI &&
-        algo != MPG_ALGO_BF16_SLICES && algo != MPG_ALGO_INT8_CRT)
+        algo != MPG_ALGO_BF16_SLICES && algo != MPG_ALGO_INT8_CRT && algo != MPG_ALGO_BF16_CRT)
         return fail(MPG_EINVAL, "unknown algorithm %d", algo);
-    const bool crt = algo == MPG_ALGO_INT8_CRT;
+    const bool crt = algo == MPG_ALGO_INT8_CRT || algo == MPG_ALGO_BF16_CRT;
     const bool sliced = algo == MPG_ALGO_INT8_OZAKI || algo == MPG_ALGO_BF16_SLICES || crt;
     const int split = o ? o->split_k : 0;
     const int levels = o ? o->strassen : 0;
@@ -408,10 +409,10 @@ size_t mpgemm_workspace_size(int P, const mpgemm_opts* opts, int64_t m, int64_t 
     if ((opts->algo == MPG_ALGO_AUTO || opts->algo == MPG_ALGO_FP64_EFT) && opts->strassen > 0 &&
         opts->strassen <= kMaxStrassenLevels)
         return static_cast<size_t>(strassen_workspace_elems(P, m, n, k, opts->strassen) * 8);
-    if (opts->algo == MPG_ALGO_INT8_CRT) {
+    if (opts->algo == MPG_ALGO_INT8_CRT || opts->algo == MPG_ALGO_BF16_CRT) {
         const int N = opts->slices ? opts->slices : crt_default_moduli(P);
         if (N < 1 || N > kCrtMaxModuli) return 0;
-        return static_cast<size_t>(crt_layout(N, m, n, k).total);
+        return static_cast<size_t>(crt_layout(N, m, n, k, opts->algo == MPG_ALGO_BF16_CRT ? 1 : 0).total);
     }
     if (opts->algo != MPG_ALGO_INT8_OZAKI && opts->algo != MPG_ALGO_BF16_SLICES) return 0;
     const int S = opts->slices ? opts->slices : ozaki_default_slices(P);

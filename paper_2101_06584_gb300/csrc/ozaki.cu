@@ -1762,6 +1762,236 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     }
 }
 
+// ----------------------------------------------- CRT form on tcgen05
+//
+// The residue products on the 5th-generation tensor cores: residues as bf16
+// (exact: |r| <= 128), TMA-loaded 128 x 128 tiles of op(A) and op(B)^T,
+// tcgen05.mma kind::f16 with M = N = 128 and fp32 accumulation in tensor
+// memory.  A product of two residues is at most 2^14, so an accumulator is
+// drained after at most 1024 values of k (8 stages) while every partial sum
+// is an integer below 2^24, exact in fp32; the drains add it to an exact
+// int32 sum per output kept in tensor memory, and at the end of a modulus the
+// sum's symmetric residue is stored as int8.  Warp roles, barriers, bounded
+// waits and the abort protocol are those of the slicing engine.
+
+namespace tcc {
+constexpr int BM = 128;
+constexpr int BN = 128;
+constexpr int KE = 64;
+constexpr int KB = 2;                                     // 128 values of k per stage
+constexpr int STAGES = 3;
+constexpr int BOX = BM * KE * 2;                          // one 128 x 64 bf16 box, 16 KB
+constexpr int STAGE_BYTES = 2 * KB * BOX;                 // A and B, 64 KB
+constexpr int SEG_STAGES = 1024 / (KE * KB);              // fp32 exact: 1024 k per drain
+constexpr int SUM_COL = 2 * BN;                           // int32 sums after two accumulators
+constexpr int TMEM_COLS = 512;
+static_assert(SUM_COL + BN <= TMEM_COLS, "TMEM columns");
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((static_cast<uint32_t>(BN) >> 3) << 17) |
+                           ((128u >> 4) << 24);
+}  // namespace tcc
+
+struct CrtTcArgs {
+    int8_t* out;            // [N][mp][np] residues of the products
+    int64_t mp, np, kp;
+    int N, tiles_m, tiles_n;
+    int* err;
+    int test_abort;
+};
+
+__global__ void __launch_bounds__(192, 1)
+crt_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const CrtTcArgs g)
+{
+    extern __shared__ uint8_t dsm[];
+    __shared__ __align__(8) uint64_t full[tcc::STAGES], empty[tcc::STAGES], accf[2], acce[2], fin;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    const uint32_t raw = smem_u32(dsm);
+    uint8_t* stage0 = dsm + (((raw + 1023u) & ~1023u) - raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int* abortp = &abort_flag;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < tcc::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 128);
+        }
+        mbar_init(&fin, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&tmem_base)), "r"(tcc::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const int KT = static_cast<int>(g.kp / (tcc::KE * tcc::KB));
+    const int per_tile = g.N * KT;
+    const int ntiles = g.tiles_m * g.tiles_n;
+    auto fail = [&](int code) {
+        *abortp = 1;
+        atomicCAS(g.err, 0, code);
+    };
+    // a segment ends after SEG_STAGES stages or at the end of a modulus
+    auto seg_end = [&](int kt, int seg_stages) { return kt == KT - 1 || seg_stages == tcc::SEG_STAGES; };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            if (g.test_abort) {
+                fail(1);
+                ok = false;
+            }
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                const int m0 = (tile % g.tiles_m) * tcc::BM, n0 = (tile / g.tiles_m) * tcc::BN;
+                for (int i = 0; i < per_tile; ++i, ++it) {
+                    const int mi = i / KT, kt = i % KT;
+                    const uint32_t st = it % tcc::STAGES, ph = (it / tcc::STAGES) & 1u;
+                    if (!mbar_wait<kHintIdle>(&empty[st], ph ^ 1u, abortp)) { fail(1); ok = false; break; }
+                    uint8_t* sa = stage0 + st * tcc::STAGE_BYTES;
+                    mbar_expect_tx(&full[st], tcc::STAGE_BYTES);
+#pragma unroll
+                    for (int q = 0; q < tcc::KB; ++q) {
+                        const int x = (kt * tcc::KB + q) * tcc::KE;
+                        tma_load_3d(sa + q * tcc::BOX, &tmA, x, m0, mi, &full[st]);
+                        tma_load_3d(sa + (tcc::KB + q) * tcc::BOX, &tmB, x, n0, mi, &full[st]);
+                    }
+                }
+            }
+            for (uint32_t j = 0; j < tcc::STAGES && j < it; ++j) {
+                const uint32_t k = it - 1 - j;
+                const unsigned long long t0 = gtimer();
+                while (!mbar_try(&full[k % tcc::STAGES], (k / tcc::STAGES) & 1u) && gtimer() - t0 < tc::TIMEOUT_NS) {
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            uint32_t it = 0, seg = 0;
+            int pend = -1;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                int seg_stages = 0;
+                uint32_t b = 0;
+                for (int i = 0; i < per_tile; ++i, ++it) {
+                    const int kt = i % KT;
+                    if (seg_stages == 0) {
+                        b = seg & 1u;
+                        if (!mbar_wait<kHintIssue>(&acce[b], ((seg >> 1) & 1u) ^ 1u, abortp)) { fail(2); ok = false; break; }
+                    }
+                    const uint32_t st = it % tcc::STAGES, ph = (it / tcc::STAGES) & 1u;
+                    if (!mbar_wait<kHintIssue>(&full[st], ph, abortp)) { fail(3); ok = false; break; }
+                    tc_fence_after();
+                    if (pend >= 0) {
+                        umma_commit(&accf[pend]);
+                        pend = -1;
+                    }
+                    const uint32_t sa = smem_u32(stage0 + st * tcc::STAGE_BYTES);
+#pragma unroll
+                    for (int q = 0; q < tcc::KB; ++q) {
+                        const uint64_t da = umma_desc(sa + q * tcc::BOX);
+                        const uint64_t db = umma_desc(sa + (tcc::KB + q) * tcc::BOX);
+#pragma unroll
+                        for (int kk = 0; kk < tcc::KE / 16; ++kk)
+                            umma(tmem + b * tcc::BN, da + 2ull * kk, db + 2ull * kk, tcc::IDESC,
+                                 (seg_stages > 0 || q > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    umma_commit(&empty[st]);
+                    ++seg_stages;
+                    if (seg_end(kt, seg_stages)) {
+                        pend = static_cast<int>(b);
+                        ++seg;
+                        seg_stages = 0;
+                    }
+                }
+            }
+            if (pend >= 0) umma_commit(&accf[pend]);
+            umma_commit(&fin);
+            const unsigned long long t0 = gtimer();
+            while (!mbar_try(&fin, 0u) && gtimer() - t0 < tc::TIMEOUT_NS) {
+            }
+        }
+    } else {
+        const int q = warp & 3;
+        const int r = 32 * q + lane;
+        const uint32_t lane_off = static_cast<uint32_t>(32 * q) << 16;
+        const uint32_t sums = tmem + lane_off + tcc::SUM_COL;
+        uint32_t seg = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            const int m0 = (tile % g.tiles_m) * tcc::BM, n0 = (tile / g.tiles_m) * tcc::BN;
+            int seg_stages = 0;
+            bool first = true;                            // first segment of a modulus
+            for (int i = 0; i < per_tile; ++i) {
+                const int mi = i / KT, kt = i % KT;
+                ++seg_stages;
+                if (!seg_end(kt, seg_stages)) continue;
+                seg_stages = 0;
+                const uint32_t b = seg & 1u;
+                if (!__all_sync(0xffffffffu, mbar_wait<kHintIdle>(&accf[b], (seg >> 1) & 1u, abortp))) {
+                    fail(4);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const bool last = kt == KT - 1;
+                const int m = crt::kDev.m[mi];
+                for (int c0 = 0; c0 < tcc::BN; c0 += 32) {
+                    uint32_t fv[32], sv[32];
+                    tmem_ld32(tmem + lane_off + b * tcc::BN + c0, fv);
+                    if (!first) tmem_ld32(sums + c0, sv);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int t = 0; t < 32; ++t) {
+                        const int add = __float2int_rn(__uint_as_float(fv[t]));
+                        sv[t] = first ? static_cast<uint32_t>(add) : sv[t] + static_cast<uint32_t>(add);
+                    }
+                    if (!last) {
+                        tmem_st32(sums + c0, sv);
+                    } else {
+                        // symmetric residue of each exact sum, 32 consecutive bytes of this row
+                        uint32_t pk[8];
+#pragma unroll
+                        for (int w = 0; w < 8; ++w) pk[w] = 0u;
+#pragma unroll
+                        for (int t = 0; t < 32; ++t) {
+                            const int v = static_cast<int>(sv[t]);
+                            const uint32_t mag = static_cast<uint32_t>(v < 0 ? -v : v);
+                            int rr = static_cast<int>(crt::mod_small(mag, mi));
+                            if (v < 0 && rr) rr = m - rr;
+                            rr = rr >= (m + 1) / 2 ? rr - m : rr;
+                            pk[t >> 2] |= (static_cast<uint32_t>(rr) & 0xffu) << (8 * (t & 3));
+                        }
+                        uint4* dst = reinterpret_cast<uint4*>(g.out + (static_cast<int64_t>(mi) * g.mp + m0 + r) * g.np +
+                                                              n0 + c0);
+                        dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                    }
+                }
+                tmem_wait_st();
+                tc_fence_before();
+                mbar_arrive(&acce[b]);
+                ++seg;
+                first = last;
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcc::TMEM_COLS));
+    }
+}
+
 // ------------------------------------------------- tcgen05 engine, CTA pairs
 //
 // DD on pairs of SMs (a cluster of two CTAs, tcgen05 .cta_group::2).  The pair
@@ -2665,14 +2895,15 @@ template cudaError_t launch_ozaki<4>(const GemmArgs<4>&, int, void*, cudaStream_
 
 // ----------------------------------------------------- CRT form, host side
 
-OzakiLayout crt_layout(int N, int64_t m, int64_t n, int64_t k, int elem_bytes)
+OzakiLayout crt_layout(int N, int64_t m, int64_t n, int64_t k, int engine)
 {
     OzakiLayout L;
+    const int elem_bytes = engine == 1 ? 2 : 1;
     L.S = N;
     L.mp = round_up(m > 0 ? m : 1, 128);
     L.np = round_up(n > 0 ? n : 1, 128);
     L.kp = round_up(k > 0 ? k : 1, KPAD);
-    L.offA = 0;
+    L.offA = engine == 1 ? 256 : 0;                    // tcgen05: a 256-byte header (error code)
     L.offB = round_up(static_cast<int64_t>(N) * L.mp * L.kp * elem_bytes, 256);
     L.offSig = L.offB + round_up(static_cast<int64_t>(N) * L.np * L.kp * elem_bytes, 256);
     L.offTau = L.offSig + round_up(L.mp * 4, 256);
@@ -2720,18 +2951,45 @@ int crt_beta(int N, int64_t k)
 }
 
 template <int P>
-cudaError_t launch_crt(const GemmArgs<P>& g, int N, void* ws, cudaStream_t s)
+static cudaError_t crt_recover(const GemmArgs<P>& g, int N, int beta, const OzakiLayout& L, const int* sig,
+                               const int* tau, const int8_t* rq, cudaStream_t s);
+
+template <int P>
+cudaError_t launch_crt(const GemmArgs<P>& g, int N, void* ws, cudaStream_t s, int engine)
 {
     const int beta = crt_beta(N, g.k);
     if (beta < 1) return cudaErrorInvalidValue;
-    const OzakiLayout L = crt_layout(N, g.m, g.n, g.k, 1);
+    const OzakiLayout L = crt_layout(N, g.m, g.n, g.k, engine);
     int8_t* base = static_cast<int8_t*>(ws);
     int* sig = reinterpret_cast<int*>(base + L.offSig);
     int* tau = reinterpret_cast<int*>(base + L.offTau);
+    int8_t* rq = base + L.offScr;
+    cudaError_t e;
+    if (engine == 1) {
+        int* err = reinterpret_cast<int*>(base);
+        uint16_t* sa = reinterpret_cast<uint16_t*>(base + L.offA);
+        uint16_t* sb = reinterpret_cast<uint16_t*>(base + L.offB);
+        e = cudaMemsetAsync(err, 0, sizeof(int), s);
+        if (e == cudaSuccess) e = slice_both<P, uint16_t, 1>(g, N, L, sa, sb, sig, tau, s, beta);
+        if (e != cudaSuccess) return e;
+        CUtensorMap ma, mb;
+        if (!slice_map(&ma, sa, N, L.mp, L.kp, tcc::BM) || !slice_map(&mb, sb, N, L.np, L.kp, tcc::BN))
+            return cudaErrorInvalidValue;
+        const CrtTcArgs a{rq, L.mp, L.np, L.kp, N, static_cast<int>(L.mp / tcc::BM),
+                          static_cast<int>(L.np / tcc::BN), err, tc_test_abort()};
+        const int smem = tcc::STAGES * tcc::STAGE_BYTES + 1024;
+        e = cudaFuncSetAttribute(crt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        const int tiles = a.tiles_m * a.tiles_n;
+        const int grid = tiles < num_sms() ? tiles : num_sms();
+        crt_tc_kernel<<<grid, 192, smem, s>>>(ma, mb, a);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        return crt_recover<P>(g, N, beta, L, sig, tau, rq, s);
+    }
     int8_t* ra = base + L.offA;
     int8_t* rb = base + L.offB;
-    int8_t* rq = base + L.offScr;
-    cudaError_t e = slice_both<P, int8_t, 1>(g, N, L, ra, rb, sig, tau, s, beta);
+    e = slice_both<P, int8_t, 1>(g, N, L, ra, rb, sig, tau, s, beta);
     if (e != cudaSuccess) return e;
     // 128 x 128 CTA tile, 8 warps of 64 x 32, 4 stages of 64 bytes of k
     constexpr int MT = 4, NT = 4, WM = 2, WN = 4, STG = 4, KS = 64;
@@ -2744,6 +3002,14 @@ cudaError_t launch_crt(const GemmArgs<P>& g, int N, void* ws, cudaStream_t s)
     crt_gemm_kernel<MT, NT, WM, WN, STG, KS><<<grid, WM * WN * 32, smem, s>>>(ga);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    return crt_recover<P>(g, N, beta, L, sig, tau, rq, s);
+}
+
+// The recovery kernel over the products' residues rq.
+template <int P>
+static cudaError_t crt_recover(const GemmArgs<P>& g, int N, int beta, const OzakiLayout& L, const int* sig,
+                               const int* tau, const int8_t* rq, cudaStream_t s)
+{
     CrtRecArgs ra_{rq, sig, tau, {nullptr, nullptr, nullptr, nullptr}, g.ldc, g.m, g.n, L.mp, L.np, N, beta, {}, {}};
     for (int c = 0; c < P; ++c) ra_.C[c] = g.C[c];
     crt_modulus(N, ra_.M);
@@ -2759,8 +3025,8 @@ cudaError_t launch_crt(const GemmArgs<P>& g, int N, void* ws, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template cudaError_t launch_crt<2>(const GemmArgs<2>&, int, void*, cudaStream_t);
-template cudaError_t launch_crt<3>(const GemmArgs<3>&, int, void*, cudaStream_t);
-template cudaError_t launch_crt<4>(const GemmArgs<4>&, int, void*, cudaStream_t);
+template cudaError_t launch_crt<2>(const GemmArgs<2>&, int, void*, cudaStream_t, int);
+template cudaError_t launch_crt<3>(const GemmArgs<3>&, int, void*, cudaStream_t, int);
+template cudaError_t launch_crt<4>(const GemmArgs<4>&, int, void*, cudaStream_t, int);
 
 }  // namespace mpg

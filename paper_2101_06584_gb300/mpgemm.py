@@ -15,7 +15,7 @@ import torch
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libmpgemm.so")
 P_OF = {"d": 1, "dd": 2, "td": 3, "qd": 4}   # "d": the binary64-only product
-ALGO = {"auto": 0, "fp64": 1, "int8": 2, "bf16": 3, "crt": 4}
+ALGO = {"auto": 0, "fp64": 1, "int8": 2, "bf16": 3, "crt": 4, "crt_bf16": 5}
 
 _lib = None
 

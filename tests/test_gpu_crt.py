@@ -1,4 +1,5 @@
-"""The CRT form (MPG_ALGO_INT8_CRT) on the GPU against its oracle
+"""The CRT form (MPG_ALGO_INT8_CRT, and MPG_ALGO_BF16_CRT on tcgen05) on the
+GPU against its oracle
 (oracle/crt.py): the residues in the workspace equal the oracle's for every
 modulus; the results are bit-identical to the oracle's steps for DD, TD and
 QD, ragged shapes spanning several tiles, both transposes, cancelling inputs,
@@ -22,14 +23,19 @@ def torch():
     return torch_cuda()
 
 
-def _run(torch, prec, A, B, N, trans_a=False, trans_b=False):
+ENGINES = ["crt", "crt_bf16"]
+
+
+def _run(torch, prec, A, B, N, trans_a=False, trans_b=False, algo="crt"):
     from paper_2101_06584_gb300 import mpgemm as mm
     Ad = dev(torch, A.transpose(0, 2, 1) if trans_a else A)
     Bd = dev(torch, B.transpose(0, 2, 1) if trans_b else B)
     m, k = A.shape[1], A.shape[2]
     n = B.shape[2]
-    ws = torch.empty(mm.workspace_size(prec, m, n, k, algo="crt", slices=N), dtype=torch.uint8, device="cuda")
-    C = mm.gemm(prec, Ad, Bd, trans_a=trans_a, trans_b=trans_b, algo="crt", slices=N, workspace=ws)
+    ws = torch.empty(mm.workspace_size(prec, m, n, k, algo=algo, slices=N), dtype=torch.uint8, device="cuda")
+    C = mm.gemm(prec, Ad, Bd, trans_a=trans_a, trans_b=trans_b, algo=algo, slices=N, workspace=ws)
+    if algo == "crt_bf16":
+        assert mm.tc_status(ws) == 0, "tcgen05 kernel reported a timeout"
     return host(C), host(ws)
 
 
@@ -61,24 +67,34 @@ def test_residues_and_result_bitwise(torch, prec, N):
     assert (gb[:, :n, :k] == RB).all() and not gb[:, n:, :].any() and not gb[:, :, k:].any()
     want, _, _, _ = R.gemm(A, B, N)
     assert_bitwise(C, want, "%s crt N=%d" % (prec, N))
+    Ct, _ = _run(torch, prec, A, B, N, algo="crt_bf16")
+    assert_bitwise(Ct, want, "%s crt on tcgen05 N=%d" % (prec, N))
 
 
+@pytest.mark.parametrize("algo", ENGINES)
 @pytest.mark.parametrize("prec", ["dd", "td"])
-def test_transposes_tiles_and_cancellation(torch, prec):
+def test_transposes_tiles_and_cancellation(torch, prec, algo):
     """Several 128 x 128 tiles with ragged edges, every transpose, cancelling
-    ill-scaled operands."""
+    ill-scaled operands, k over several 1024-wide drains of the tcgen05
+    engine's accumulators."""
     P = I.P_OF[prec]
     rng = np.random.default_rng(810 + P)
-    A, B = I.cancelling_pair(P, 150, 270, 140, rng)
+    A, B = I.cancelling_pair(P, 150, 270, 2300, rng)
     N = 28 if prec == "dd" else 44
-    want, _, _, _ = R.gemm(A, B, N)
+    rows, cols = [0, 77, 127, 128, 149], [0, 100, 127, 128, 255, 256, 269]
+    want, _, _, _ = R.gemm(A, B, N, rows=rows, cols=cols)
+    first = None
     for ta, tb in ((False, False), (True, False), (False, True), (True, True)):
-        C, _ = _run(torch, prec, A, B, N, trans_a=ta, trans_b=tb)
-        assert_bitwise(C, want, "%s crt trans %s %s" % (prec, ta, tb))
+        C, _ = _run(torch, prec, A, B, N, trans_a=ta, trans_b=tb, algo=algo)
+        assert_bitwise(C[:, rows][:, :, cols], want, "%s %s trans %s %s" % (prec, algo, ta, tb))
+        if first is None:
+            first = C
+        assert_bitwise(C, first, "%s %s transposes agree" % (prec, algo))
 
 
+@pytest.mark.parametrize("algo", ENGINES)
 @pytest.mark.parametrize("prec", ["dd", "qd"])
-def test_products_below_the_normal_range(torch, prec):
+def test_products_below_the_normal_range(torch, prec, algo):
     """Rows of A scaled by 1 .. 2^-1060 and columns of B by 1 .. 2^-530: the
     components of the recovered products run through the subnormal range and
     down to signed zeros; every entry bit-identical to the oracle."""
@@ -88,7 +104,7 @@ def test_products_below_the_normal_range(torch, prec):
     A, B = I.uniform(P, (m, k), rng), I.uniform(P, (k, n), rng)
     A *= np.array([1.0, 2.0 ** -500, 2.0 ** -530, 2.0 ** -1060])[np.arange(m) % 4][None, :, None]
     B *= np.array([1.0, 2.0 ** -500, 2.0 ** -530])[(np.arange(n) // 2) % 3][None, None, :]
-    C, _ = _run(torch, prec, A, B, 30)
+    C, _ = _run(torch, prec, A, B, 30, algo=algo)
     want, _, _, _ = R.gemm(A, B, 30)
     assert ((np.abs(want) < 2.0 ** -1022) & (want != 0)).any() and np.isfinite(want).all()
     assert_bitwise(C, want, "%s crt tiny products" % prec)
@@ -105,6 +121,8 @@ def test_largest_k_and_refusal(torch):
     C, _ = _run(torch, "dd", A, B, 40)
     want, _, _, _ = R.gemm(A, B, 40, rows=[0, 15], cols=[3, 9])
     assert_bitwise(C[:, [0, 15]][:, :, [3, 9]], want, "crt at the largest k")
+    Ct, _ = _run(torch, "dd", A, B, 40, algo="crt_bf16")
+    assert_bitwise(Ct, C, "both engines at the largest k")
     A1 = np.concatenate([A, np.zeros((2, m, 1))], axis=2)
     B1 = np.concatenate([B, np.zeros((2, 1, n))], axis=1)
     with pytest.raises(mm.MPGError) as e:
@@ -113,20 +131,59 @@ def test_largest_k_and_refusal(torch):
     assert e.value.code == -4
 
 
-def test_full_size_dd(torch):
-    """DD 4096^3 on the uniform inputs of that workload's seed, 28 moduli:
-    a 16 x 16 grid of random rows and columns bit-identical to the oracle,
-    and two whole rows with the grid within n 2^-100 of the exact product."""
+@pytest.mark.parametrize("N", [26, 28])
+def test_full_size_dd(torch, N):
+    """DD 4096^3 on the uniform inputs of that workload's seed: the tcgen05
+    engine equals the int8 engine on every entry (compared on the device), a
+    16 x 16 grid of random rows and columns is bit-identical to the oracle,
+    and two whole rows with the grid are within n 2^-100 of the exact
+    product."""
+    from paper_2101_06584_gb300 import mpgemm as mm
     n = 4096
     rng = I.rng_for(2)
     A, B = I.uniform(2, (n, n), rng), I.uniform(2, (n, n), rng)
-    C, _ = _run(torch, "dd", A, B, 28)
+    Ad, Bd = dev(torch, A), dev(torch, B)
+    out = {}
+    for algo in ENGINES:
+        ws = torch.empty(mm.workspace_size("dd", n, n, n, algo=algo, slices=N), dtype=torch.uint8, device="cuda")
+        out[algo] = mm.gemm("dd", Ad, Bd, algo=algo, slices=N, workspace=ws)
+        if algo == "crt_bf16":
+            assert mm.tc_status(ws) == 0
+        del ws
+    diff = int((out["crt"].view(torch.int64) != out["crt_bf16"].view(torch.int64)).sum())
+    assert diff == 0, "%d values differ between the engines" % diff
+    C = host(out["crt_bf16"])
+    del out
     srng = np.random.default_rng(840)
     rows = sorted(int(x) for x in srng.choice(n, 16, replace=False))
     cols = sorted(int(x) for x in srng.choice(n, 16, replace=False))
-    want, _, _, _ = R.gemm(A, B, 28, rows=rows, cols=cols)
+    want, _, _, _ = R.gemm(A, B, N, rows=rows, cols=cols)
     assert_bitwise(C[:, rows][:, :, cols], want, "crt 4096 grid")
     full = sorted(int(x) for x in srng.choice(n, 2, replace=False))
     ent = sorted({(i, j) for i in full for j in range(n)} | {(i, j) for i in rows for j in cols})
     err = X.gemm_error(C, A, B, ent)
     assert err["err_abs"] <= n * 2.0 ** -100, err
+
+
+def test_tcgen05_abort_path(torch):
+    """The abort path of the tcgen05 CRT kernel: with MPGEMM_TEST_TC_ABORT=1 the
+    producer gives up before any load; the call returns, the status names the
+    producer, and the next call is bit-identical to the int8 engine."""
+    import os
+    from paper_2101_06584_gb300 import mpgemm as mm
+    rng = np.random.default_rng(850)
+    A, B = I.uniform(2, (200, 300), rng), I.uniform(2, (300, 150), rng)
+    Ad, Bd = dev(torch, A), dev(torch, B)
+    ws = torch.empty(mm.workspace_size("dd", 200, 150, 300, algo="crt_bf16", slices=28), dtype=torch.uint8,
+                     device="cuda")
+    os.environ["MPGEMM_TEST_TC_ABORT"] = "1"
+    try:
+        mm.gemm("dd", Ad, Bd, algo="crt_bf16", slices=28, workspace=ws)
+        code = mm.tc_status(ws)
+    finally:
+        del os.environ["MPGEMM_TEST_TC_ABORT"]
+    assert code == 1 and "producer" in mm.lib().mpgemm_last_error().decode()
+    got = host(mm.gemm("dd", Ad, Bd, algo="crt_bf16", slices=28, workspace=ws))
+    assert mm.tc_status(ws) == 0
+    want, _ = _run(torch, "dd", A, B, 28)
+    assert_bitwise(got, want, "after an aborted call")
