@@ -2904,7 +2904,7 @@ OzakiLayout crt_layout(int N, int64_t m, int64_t n, int64_t k, int engine)
     L.np = round_up(n > 0 ? n : 1, 128);
     L.kp = round_up(k > 0 ? k : 1, KPAD);
     L.offA = engine == 1 ? 256 : 0;                    // tcgen05: a 256-byte header (error code)
-    L.offB = round_up(static_cast<int64_t>(N) * L.mp * L.kp * elem_bytes, 256);
+    L.offB = L.offA + round_up(static_cast<int64_t>(N) * L.mp * L.kp * elem_bytes, 256);
     L.offSig = L.offB + round_up(static_cast<int64_t>(N) * L.np * L.kp * elem_bytes, 256);
     L.offTau = L.offSig + round_up(L.mp * 4, 256);
     L.offScr = L.offTau + round_up(L.np * 4, 256);      // [N][mp][np] int8 residues of the products

@@ -291,10 +291,11 @@ def test_crt_form_host_checks(L):
     r = lambda x: (x + 127) // 128 * 128
     r256 = lambda x: (x + 255) // 256 * 256
     for (m, n, k, N) in ((100, 70, 300, 28), (4096, 4096, 4096, 26), (1, 1, 1, 49)):
-        o = Opts(0, 0, 4, 0, N, 0, None, 0)
-        want = (r256(N * r(m) * r(k)) + r256(N * r(n) * r(k)) + r256(4 * r(m)) + r256(4 * r(n)) +
-                r256(N * r(m) * r(n)))
-        assert L.mpgemm_workspace_size(2, ctypes.byref(o), m, n, k) == want
+        for algo, head, eb in ((4, 0, 1), (5, 256, 2)):           # int8; tcgen05: header, bf16 residues
+            o = Opts(0, 0, algo, 0, N, 0, None, 0)
+            want = (head + r256(N * r(m) * r(k) * eb) + r256(N * r(n) * r(k) * eb) + r256(4 * r(m)) +
+                    r256(4 * r(n)) + r256(N * r(m) * r(n)))
+            assert L.mpgemm_workspace_size(2, ctypes.byref(o), m, n, k) == want, (algo, m, n, k, N)
     A, B, C = planes(FAKE, 2), planes(2 * FAKE, 2), planes(3 * FAKE, 2)
     for N, k, code, text in ((50, 8, -1, "moduli"), (1, 200, -4, "no bits"), (28, 8, -3, "workspace")):
         o = Opts(0, 0, 4, 0, N, 0, None, 0)
