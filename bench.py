@@ -112,6 +112,8 @@ def parse_args():
                     choices=["td_qd", "dd_small", "dd_int8", "dd_tc", "dd_crt", "dd_crt_int8", "td_qd_int8", "td_qd_tc",
                              "batched", "autograd", "elementwise", "strassen", "autograd_tc"])
     ap.add_argument("--size", type=int, default=None, help="override the workload's m = n = k")
+    ap.add_argument("--slices", type=int, default=None,
+                    help="slice (or moduli) count of the DD slicing/CRT workloads instead of the search")
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--no-accuracy", action="store_true",
@@ -719,15 +721,15 @@ class DdInt8(Workload):
 class DdCrt(DdInt8):
     name = "dd_crt"
 
-    def __init__(self, torch, mm, I, rank, n=4096):
-        super().__init__(torch, mm, I, rank, n=n, engine="crt_tc")
+    def __init__(self, torch, mm, I, rank, n=4096, S=None):
+        super().__init__(torch, mm, I, rank, n=n, S=S, engine="crt_tc")
 
 
 class DdCrtInt8(DdInt8):
     name = "dd_crt_int8"
 
-    def __init__(self, torch, mm, I, rank, n=4096):
-        super().__init__(torch, mm, I, rank, n=n, engine="crt_int8")
+    def __init__(self, torch, mm, I, rank, n=4096, S=None):
+        super().__init__(torch, mm, I, rank, n=n, S=S, engine="crt_int8")
 
 
 class TdQdInt8(Workload):
@@ -841,8 +843,8 @@ class TdQdInt8(Workload):
 class DdTc(DdInt8):
     name = "dd_tc"
 
-    def __init__(self, torch, mm, I, rank, n=4096):
-        super().__init__(torch, mm, I, rank, n=n, engine="tc")
+    def __init__(self, torch, mm, I, rank, n=4096, S=None):
+        super().__init__(torch, mm, I, rank, n=n, S=S, engine="tc")
 
 
 class TdQdTc(TdQdInt8):
@@ -1165,6 +1167,8 @@ def run_ours(args):
         _ACC["pool"] = error_pool()
     pk = peaks(torch, mm)
     kw = {} if args.size is None else {"n": args.size}
+    if args.slices is not None and args.workload in ("dd_int8", "dd_tc", "dd_crt", "dd_crt_int8"):
+        kw["S"] = args.slices
     w = WORKLOADS[args.workload](torch, mm, I, rank, **kw)
     total_ms, launch_ms, clocks, wall = measure(torch, w, args.steps, args.warmup, world, local, flush)
     value = aggregate_value(world, w.mads, args.steps, total_ms)

@@ -131,7 +131,7 @@ def test_largest_k_and_refusal(torch):
     assert e.value.code == -4
 
 
-@pytest.mark.parametrize("N", [26, 28])
+@pytest.mark.parametrize("N", [23, 28])          # 23: the count the benchmark chooses
 def test_full_size_dd(torch, N):
     """DD 4096^3 on the uniform inputs of that workload's seed: the tcgen05
     engine equals the int8 engine on every entry (compared on the device), a
