@@ -109,7 +109,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="td_qd",
-                    choices=["td_qd", "dd_small", "dd_int8", "dd_tc", "dd_crt", "dd_crt_int8", "td_qd_int8", "td_qd_tc",
+                    choices=["td_qd", "dd_small", "dd_int8", "dd_tc", "dd_crt", "dd_crt_int8", "td_crt",
+                             "td_qd_int8", "td_qd_tc",
                              "batched", "autograd", "elementwise", "strassen", "autograd_tc"])
     ap.add_argument("--size", type=int, default=None, help="override the workload's m = n = k")
     ap.add_argument("--slices", type=int, default=None,
@@ -736,46 +737,64 @@ class TdQdInt8(Workload):
     """The TD and QD GEMMs of td_qd through the slicing form (engine "int8" or "tc")."""
     name = "td_qd_int8"
 
+    ALGO = {"int8": "int8", "tc": "bf16", "crt_tc": "crt_bf16"}
+    # first count tried (the library's defaults) and the largest, per precision
+    START = {"td": (22, 40), "qd": (29, 40)}
+    START_CRT = {"td": (44, 49)}
+
     def __init__(self, torch, mm, I, rank, n=1024, engine="int8", S=None):
         self.torch, self.mm, self.n, self.engine = torch, mm, n, engine
-        self.algo = "int8" if engine == "int8" else "bf16"
-        self.precs = ("td", "qd")
+        self.algo = self.ALGO[engine]
+        self.crt = self.algo.startswith("crt")
+        self.precs = ("td",) if self.crt else ("td", "qd")
         rng = replica_rng(1, rank)
         self.dev, self.host, self.search = {}, {}, {}
-        for prec in self.precs:
+        for prec in ("td", "qd"):                 # drawn in this order whichever precisions run
             P = I.P_OF[prec]
             A, B = I.cancelling_pair(P, n, n, n, rng)
+            if prec not in self.precs:
+                continue
             self.host[prec] = (A, B)
             self.dev[prec] = [torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(),
                               torch.empty((P, n, n), dtype=torch.float64, device="cuda"), None]
+        starts = self.START_CRT if self.crt else self.START
         if S is None and not _ACC["enabled"]:
-            S = {p: FIXED_SLICES[p] for p in self.precs}
+            S = {p: starts[p][0] if self.crt else FIXED_SLICES[p] for p in self.precs}
         if S is None:
-            # the smallest slice count meeting n 2^-150 (TD) / n 2^-200 (QD) on the
-            # sampled entries, searched from the library's defaults 22 / 29
+            # the smallest count meeting n 2^-150 (TD) / n 2^-200 (QD) on the
+            # sampled entries, searched from the library's defaults
             S = {}
-            for prec, start in (("td", 22), ("qd", 29)):
-                S[prec], self.search[prec] = self._choose(prec, start)
+            for prec in self.precs:
+                S[prec], self.search[prec] = self._choose(prec, *starts[prec])
         self.S = S
         for prec in self.precs:
             self.dev[prec][3] = torch.empty(mm.workspace_size(prec, n, n, n, algo=self.algo, slices=S[prec]),
                                             dtype=torch.uint8, device="cuda")
         self.mads = len(self.precs) * n ** 3
-        self.launches_per_step = 2 * (5 if n % 128 == 0 else 7) + (0 if engine == "int8" else 2)
         eng = "mma.sync s8 engine" if engine == "int8" else "tcgen05 engine"
-        self.config = {"workload": "TD GEMM + QD GEMM, m=n=k=%d, INT8 error-free slicing form "
-                                   "(S = %d / %d), %s, inputs of the main workload"
-                                   % (n, self.S["td"], self.S["qd"], eng),
-                       "m": n, "n": n, "k": n, "slices": self.S, "engine": engine,
-                       "slices_rule": "smallest S meeting n 2^-150 (TD) / n 2^-200 (QD) on the sampled "
-                                      "entries" if self.search else "given"}
+        if self.crt:
+            self.launches_per_step = 7
+            self.config = {"workload": "TD GEMM, m=n=k=%d, CRT form (N = %d moduli, beta = %d bits), %s, "
+                                       "inputs of the main workload" % (n, self.S["td"], mm.crt_beta(self.S["td"], n),
+                                                                         eng),
+                           "m": n, "n": n, "k": n, "slices": self.S, "engine": engine,
+                           "slices_rule": "smallest N meeting n 2^-150 on the sampled entries"
+                           if self.search else "given"}
+        else:
+            self.launches_per_step = 2 * (5 if n % 128 == 0 else 7) + (0 if engine == "int8" else 2)
+            self.config = {"workload": "TD GEMM + QD GEMM, m=n=k=%d, INT8 error-free slicing form "
+                                       "(S = %d / %d), %s, inputs of the main workload"
+                                       % (n, self.S["td"], self.S["qd"], eng),
+                           "m": n, "n": n, "k": n, "slices": self.S, "engine": engine,
+                           "slices_rule": "smallest S meeting n 2^-150 (TD) / n 2^-200 (QD) on the sampled "
+                                          "entries" if self.search else "given"}
 
     def reference(self, prec):
         n = self.n
         return exact_reference(("cfg1", prec, n), *self.host[prec],
                                sample_entries(n, n, 256, np.random.default_rng(11 + len(prec))))
 
-    def _choose(self, prec, start):
+    def _choose(self, prec, start, smax):
         n = self.n
         A, B, C, _ = self.dev[prec]
 
@@ -783,9 +802,9 @@ class TdQdInt8(Workload):
             ws = self.torch.empty(self.mm.workspace_size(prec, n, n, n, algo=self.algo, slices=S),
                                   dtype=self.torch.uint8, device="cuda")
             return self.mm.gemm(prec, A, B, out=C, algo=self.algo, slices=S, workspace=ws)
-        S, tried = choose_slices(run, self.reference(prec), n * 2.0 ** -GEMM_PBITS[prec], start, 40)
+        S, tried = choose_slices(run, self.reference(prec), n * 2.0 ** -GEMM_PBITS[prec], start, smax)
         if S is None:
-            raise RuntimeError("no slice count up to 40 meets the %s bound: %r" % (prec, tried))
+            raise RuntimeError("no count up to %d meets the %s bound: %r" % (smax, prec, tried))
         return S, {str(k): v for k, v in sorted(tried.items())}
 
     def accuracy(self):
@@ -813,9 +832,10 @@ class TdQdInt8(Workload):
 
     def roofline(self, launch_ms, pk):
         n = self.n
-        S = self.S["qd"]
-        pairs = S * (S + 1) // 2
-        ms = statistics.mean(launch_ms["qd"])
+        dom = self.precs[-1]
+        S = self.S[dom]
+        pairs = S if self.crt else S * (S + 1) // 2
+        ms = statistics.mean(launch_ms[dom])
         ach = 2.0 * pairs * n ** 3 / (ms * 1e-3)
         plain = {}
         for prec in self.precs:
@@ -828,11 +848,14 @@ class TdQdInt8(Workload):
         # FP64 work of the QD call: one QDadd (87 of the 210 operations of a QD
         # multiply-add) per output per group of ten weights (S weights; the
         # first group of a tile needs none on the tcgen05 engine)
-        fp64_ops = (n * n) * (-(-S // 10)) * FP64_OPS_PER_MAD["qd"] * 87 // 210
-        return {"bound": "tensor", "kernel": "QD slicing form (%s) incl. slicing" % self.engine,
+        fp64_ops = 0 if self.crt else (n * n) * (-(-S // 10)) * FP64_OPS_PER_MAD["qd"] * 87 // 210
+        kern = ("TD CRT form (crt_tc_kernel) incl. residues and recovery" if self.crt
+                else "QD slicing form (%s) incl. slicing" % self.engine)
+        return {"bound": "tensor", "kernel": kern,
                 "achieved": ach / 1e12, "peak": peak / 1e12, "unit": unit, "peak_source": src,
                 "frac": ach / peak, "traffic": None, "ops_per_unit": 2 * pairs,
-                "unit_of_work": "QD multiply-add (%d slice-pair MACs)" % pairs,
+                "unit_of_work": "%s multiply-add (%d %s MACs)" % (dom.upper(), pairs,
+                                                                  "residue" if self.crt else "slice-pair"),
                 "units_per_launch": n ** 3,
                 "fp64_epilogue_ops_per_call": fp64_ops,
                 "per_precision_mad_s": {p: n ** 3 / (statistics.mean(launch_ms[p]) * 1e-3)
@@ -852,6 +875,15 @@ class TdQdTc(TdQdInt8):
 
     def __init__(self, torch, mm, I, rank, n=1024):
         super().__init__(torch, mm, I, rank, n=n, engine="tc")
+
+
+class TdCrt(TdQdInt8):
+    """The TD GEMM of the main workload through the CRT form on tcgen05 (QD
+    needs more bits than 49 moduli of at most 256 give)."""
+    name = "td_crt"
+
+    def __init__(self, torch, mm, I, rank, n=1024):
+        super().__init__(torch, mm, I, rank, n=n, engine="crt_tc")
 
 
 class Elementwise(Workload):
@@ -1094,7 +1126,7 @@ class AutogradTc(Autograd):
 
 
 WORKLOADS = {"td_qd": TdQd, "dd_small": DdSmall, "dd_int8": DdInt8, "dd_tc": DdTc, "dd_crt": DdCrt,
-             "dd_crt_int8": DdCrtInt8,
+             "dd_crt_int8": DdCrtInt8, "td_crt": TdCrt,
              "td_qd_int8": TdQdInt8, "td_qd_tc": TdQdTc, "batched": Batched, "autograd": Autograd,
              "elementwise": Elementwise, "strassen": Strassen, "autograd_tc": AutogradTc}
 
@@ -1241,8 +1273,8 @@ def sliced_summary(configs):
 def extras(torch, mm, I, pk, flush):
     """One short measurement of each other workload (rank 0, after the main one)."""
     out = {}
-    for name in ("dd_small", "dd_int8", "dd_tc", "dd_crt", "dd_crt_int8", "td_qd_int8", "td_qd_tc", "batched",
-                 "autograd", "autograd_tc", "elementwise", "strassen"):
+    for name in ("dd_small", "dd_int8", "dd_tc", "dd_crt", "dd_crt_int8", "td_qd_int8", "td_qd_tc", "td_crt",
+                 "batched", "autograd", "autograd_tc", "elementwise", "strassen"):
         w = WORKLOADS[name](torch, mm, I, 0)
         steps = {"dd_small": 10, "elementwise": 10, "strassen": 1}.get(name, 2)
         total_ms, launch_ms, _, _ = measure(torch, w, steps, 1, 1, 0, flush, sample_clocks=False)

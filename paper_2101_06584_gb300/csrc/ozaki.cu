@@ -336,9 +336,11 @@ __device__ __forceinline__ uint32_t mod_small(uint32_t x, int i)
 }  // namespace crt
 
 // Residues of one scaled entry, one modulus per next(): the symmetric
-// representative of A' mod m_i, i = 0, 1, ...
+// representative of A' mod m_i, i = 0, 1, ...  NL 16-bit limbs hold |A'|
+// (|A'| <= 2^(beta - 1): NL = 4, 8 or 12 for beta up to 64, 128, 192).
+template <int NL>
 struct ResidueCursor {
-    uint32_t limb[crt::kLimbs];       // |A'| in 16-bit limbs, least significant first
+    uint32_t limb[NL];                // |A'| in 16-bit limbs, least significant first
     bool neg;
     int idx;
     __device__ __forceinline__ int next()
@@ -346,7 +348,7 @@ struct ResidueCursor {
         const int i = idx++;
         uint32_t s = 0;
 #pragma unroll
-        for (int j = 0; j < crt::kLimbs; ++j) s += limb[j] * crt::kDev.pw16[i][j];
+        for (int j = 0; j < NL; ++j) s += limb[j] * crt::kDev.pw16[i][j];
         const int m = crt::kDev.m[i];
         int r = static_cast<int>(crt::mod_small(s, i));
         if (neg && r) r = m - r;
@@ -357,8 +359,8 @@ struct ResidueCursor {
 // A' of the P components: each floored at 2^(sigma - beta - 64), summed
 // exactly in 384 bits, rounded to the nearest integer (ties to even) in units
 // of 2^(sigma - beta).
-template <int P>
-__device__ __forceinline__ ResidueCursor residue_cursor(const double (&c)[P], int sigma, int beta)
+template <int NL, int P>
+__device__ __forceinline__ ResidueCursor<NL> residue_cursor(const double (&c)[P], int sigma, int beta)
 {
     Wide W;
 #pragma unroll
@@ -387,7 +389,7 @@ __device__ __forceinline__ ResidueCursor residue_cursor(const double (&c)[P], in
         carry = (carry && s == 0) ? 1ull : 0ull;
         I[i] = s;
     }
-    ResidueCursor cur;
+    ResidueCursor<NL> cur;
     cur.neg = (I[kWideWords - 2] >> 63) != 0;
     if (cur.neg) {                                   // magnitude: two's complement negation
         uint64_t cc = 1;
@@ -399,7 +401,7 @@ __device__ __forceinline__ ResidueCursor residue_cursor(const double (&c)[P], in
         }
     }
 #pragma unroll
-    for (int j = 0; j < crt::kLimbs; ++j) cur.limb[j] = static_cast<uint32_t>(I[j / 4] >> (16 * (j % 4))) & 0xffffu;
+    for (int j = 0; j < NL; ++j) cur.limb[j] = static_cast<uint32_t>(I[j / 4] >> (16 * (j % 4))) & 0xffffu;
     cur.idx = 0;
     return cur;
 }
@@ -533,8 +535,12 @@ __device__ __forceinline__ typename CursorOf<P>::T zero_cursor()
 
 // KIND 0: the slicing form's digits (S of them); KIND 1: the CRT form's
 // residues (S moduli, beta bits per scaled entry).
+// KIND 1, 2, 3: residues with 12, 8 or 4 limbs (beta up to 192, 128, 64 bits).
 template <int P, int KIND> struct KindCursor { using T = typename CursorOf<P>::T; };
-template <int P> struct KindCursor<P, 1> { using T = ResidueCursor; };
+template <int P> struct KindCursor<P, 1> { using T = ResidueCursor<12>; };
+template <int P> struct KindCursor<P, 2> { using T = ResidueCursor<8>; };
+template <int P> struct KindCursor<P, 3> { using T = ResidueCursor<4>; };
+constexpr int residue_kind(int beta) { return beta <= 64 ? 3 : beta <= 128 ? 2 : 1; }
 
 template <int P, int KIND>
 __device__ __forceinline__ typename KindCursor<P, KIND>::T make_cursor(const Planes<P>& pl, int64_t off, bool valid,
@@ -546,7 +552,7 @@ __device__ __forceinline__ typename KindCursor<P, KIND>::T make_cursor(const Pla
         double c[P];
 #pragma unroll
         for (int i = 0; i < P; ++i) c[i] = valid ? pl.c[i][off] : 0.0;
-        return residue_cursor<P>(c, sigma, beta);
+        return residue_cursor<KIND == 1 ? 12 : KIND == 2 ? 8 : 4, P>(c, sigma, beta);
     }
 }
 
@@ -1083,75 +1089,75 @@ struct CrtRecArgs {
     uint32_t H[crt::kRecLimbs];          // ceil(M / 2)
 };
 
-using Limbs = uint32_t[crt::kRecLimbs];
-
-// Word w of u (0 beyond the top), with a static loop so u stays in registers.
-__device__ __forceinline__ uint32_t limb_at(const Limbs& u, int w)
+// Big unsigned integers of L 32-bit limbs, least significant first, kept in
+// registers: every index below is a compile-time constant after unrolling.
+template <int L>
+__device__ __forceinline__ uint32_t limb_at(const uint32_t (&u)[L], int w)
 {
     uint32_t r = 0;
 #pragma unroll
-    for (int k = 0; k < crt::kRecLimbs; ++k) r = (k == w) ? u[k] : r;
+    for (int k = 0; k < L; ++k) r = (k == w) ? u[k] : r;
     return r;
 }
 
-__device__ __forceinline__ int bit_length(const Limbs& u)
+template <int L>
+__device__ __forceinline__ int bit_length(const uint32_t (&u)[L])
 {
     int bl = 0;
 #pragma unroll
-    for (int k = 0; k < crt::kRecLimbs; ++k)
+    for (int k = 0; k < L; ++k)
         if (u[k]) bl = 32 * k + (32 - __clz(static_cast<int>(u[k])));
     return bl;
 }
 
 // Bits [pos, pos + 53) of u, pos >= 0.
-__device__ __forceinline__ uint64_t bits53(const Limbs& u, int pos)
+template <int L>
+__device__ __forceinline__ uint64_t bits53(const uint32_t (&u)[L], int pos)
 {
     const int w = pos >> 5, off = pos & 31;
-    const unsigned __int128 x = static_cast<unsigned __int128>(limb_at(u, w)) |
-                                (static_cast<unsigned __int128>(limb_at(u, w + 1)) << 32) |
-                                (static_cast<unsigned __int128>(limb_at(u, w + 2)) << 64);
+    const unsigned __int128 x = static_cast<unsigned __int128>(limb_at<L>(u, w)) |
+                                (static_cast<unsigned __int128>(limb_at<L>(u, w + 1)) << 32) |
+                                (static_cast<unsigned __int128>(limb_at<L>(u, w + 2)) << 64);
     return static_cast<uint64_t>(x >> off) & ((1ull << 53) - 1);
 }
 
+__device__ __forceinline__ uint32_t low_mask(int s, int lo)
+{
+    return s >= lo + 32 ? 0xffffffffu : (s <= lo ? 0u : ((1u << (s - lo)) - 1u));
+}
+
 // Whether any bit of u below position pos is set.
-__device__ __forceinline__ bool any_below(const Limbs& u, int pos)
+template <int L>
+__device__ __forceinline__ bool any_below(const uint32_t (&u)[L], int pos)
 {
     bool any = false;
 #pragma unroll
-    for (int k = 0; k < crt::kRecLimbs; ++k) {
-        const int lo = 32 * k;
-        const uint32_t mask = pos >= lo + 32 ? 0xffffffffu : (pos <= lo ? 0u : ((1u << (pos - lo)) - 1u));
-        any = any || (u[k] & mask) != 0u;
-    }
+    for (int k = 0; k < L; ++k) any = any || (u[k] & low_mask(pos, 32 * k)) != 0u;
     return any;
 }
 
 // u = u mod 2^s (s >= 1), then, when `complement`, u = 2^s - u (u != 0).
-__device__ __forceinline__ void low_bits(Limbs& u, int s, bool complement)
+template <int L>
+__device__ __forceinline__ void low_bits(uint32_t (&u)[L], int s, bool complement)
 {
 #pragma unroll
-    for (int k = 0; k < crt::kRecLimbs; ++k) {
-        const int lo = 32 * k;
-        const uint32_t mask = s >= lo + 32 ? 0xffffffffu : (s <= lo ? 0u : ((1u << (s - lo)) - 1u));
-        u[k] &= mask;
-    }
+    for (int k = 0; k < L; ++k) u[k] &= low_mask(s, 32 * k);
     if (!complement) return;
     uint32_t carry = 1;
 #pragma unroll
-    for (int k = 0; k < crt::kRecLimbs; ++k) {
-        const int lo = 32 * k;
-        const uint32_t mask = s >= lo + 32 ? 0xffffffffu : (s <= lo ? 0u : ((1u << (s - lo)) - 1u));
+    for (int k = 0; k < L; ++k) {
         const uint64_t t = static_cast<uint64_t>(~u[k]) + carry;
-        u[k] = static_cast<uint32_t>(t) & mask;
+        u[k] = static_cast<uint32_t>(t) & low_mask(s, 32 * k);
         carry = static_cast<uint32_t>(t >> 32);
     }
 }
 
 // RN((-1)^neg u 2^e) as binary64 (ties to even; gradual underflow; +-inf
 // above the range); u and neg become the exact remainder (magnitude, sign).
-__device__ __forceinline__ double rn_component(Limbs& u, bool& neg, int e)
+template <int L>
+__device__ __forceinline__ double rn_component(uint32_t (&u)[L], bool& neg, int e)
 {
-    const int bl = bit_length(u);
+    const int bl = bit_length<L>(u);
     if (bl == 0) return 0.0;
     const uint64_t sign = neg ? (1ull << 63) : 0ull;
     const int E = bl - 1 + e;
@@ -1159,14 +1165,14 @@ __device__ __forceinline__ double rn_component(Limbs& u, bool& neg, int e)
     const int s = qx - e;
     uint64_t q;
     if (s <= 0) {                                     // exactly representable
-        q = bits53(u, 0) << (-s);
+        q = bits53<L>(u, 0) << (-s);
 #pragma unroll
-        for (int k = 0; k < crt::kRecLimbs; ++k) u[k] = 0u;
+        for (int k = 0; k < L; ++k) u[k] = 0u;
     } else {
-        q = bits53(u, s);
-        const bool half = (limb_at(u, (s - 1) >> 5) >> ((s - 1) & 31)) & 1u;
-        const bool up = half && ((q & 1ull) || any_below(u, s - 1));
-        low_bits(u, s, up);
+        q = bits53<L>(u, s);
+        const bool half = (limb_at<L>(u, (s - 1) >> 5) >> ((s - 1) & 31)) & 1u;
+        const bool up = half && ((q & 1ull) || any_below<L>(u, s - 1));
+        low_bits<L>(u, s, up);
         if (up) {
             ++q;
             neg = !neg;
@@ -1179,7 +1185,7 @@ __device__ __forceinline__ double rn_component(Limbs& u, bool& neg, int e)
     if (q == 0) return __longlong_as_double(static_cast<long long>(sign));     // a signed zero
     if (q >= (1ull << 52) && qx + 52 > 1023) {                                  // beyond the range
 #pragma unroll
-        for (int k = 0; k < crt::kRecLimbs; ++k) u[k] = 0u;
+        for (int k = 0; k < L; ++k) u[k] = 0u;
         return __longlong_as_double(static_cast<long long>(sign | 0x7ff0000000000000ull));
     }
     const uint64_t bits = q >= (1ull << 52)
@@ -1188,52 +1194,62 @@ __device__ __forceinline__ double rn_component(Limbs& u, bool& neg, int e)
     return __longlong_as_double(static_cast<long long>(sign | bits));
 }
 
-template <int P>
+// NB: the moduli count rounded up to a multiple of 8 (the loops below are
+// unrolled NB times and skip moduli i >= N, so the digits stay in registers);
+// L = NB / 4 limbs (at most 11) hold the product of NB moduli <= 256.
+template <int P, int NB>
 __global__ void __launch_bounds__(256) crt_recover_kernel(const CrtRecArgs g)
 {
+    constexpr int L = NB / 4 < crt::kRecLimbs ? NB / 4 : crt::kRecLimbs;
     const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (t >= g.m * g.n) return;
     const int64_t row = t / g.n, col = t % g.n;
-    uint32_t v[crt::kMaxModuli];
     const int N = g.N;
-    for (int i = 0; i < N; ++i) {
-        const int mi = crt::kDev.m[i];
-        int r = g.res[(static_cast<int64_t>(i) * g.mp + row) * g.np + col];
-        if (r < 0) r += mi;
-        uint32_t ts = 0;
-        for (int j = 0; j < i; ++j) ts += v[j] * crt::kDev.pm[i][j];
-        const uint32_t d = static_cast<uint32_t>(r) + static_cast<uint32_t>(mi) - crt::mod_small(ts, i);
-        v[i] = crt::mod_small(d * crt::kDev.inv[i], i);
+    uint32_t v[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        v[i] = 0u;
+        if (i < N) {
+            const int mi = crt::kDev.m[i];
+            int r = g.res[(static_cast<int64_t>(i) * g.mp + row) * g.np + col];
+            if (r < 0) r += mi;
+            uint32_t ts = 0;
+#pragma unroll
+            for (int j = 0; j < i; ++j) ts += v[j] * crt::kDev.pm[i][j];
+            const uint32_t d = static_cast<uint32_t>(r) + static_cast<uint32_t>(mi) - crt::mod_small(ts, i);
+            v[i] = crt::mod_small(d * crt::kDev.inv[i], i);
+        }
     }
-    Limbs X;
+    uint32_t X[L];
 #pragma unroll
-    for (int k = 0; k < crt::kRecLimbs; ++k) X[k] = 0u;
-    X[0] = v[N - 1];
-    for (int i = N - 2; i >= 0; --i) {
-        const uint64_t mi = static_cast<uint64_t>(crt::kDev.m[i]);
-        uint64_t carry = v[i];
+    for (int k = 0; k < L; ++k) X[k] = 0u;
 #pragma unroll
-        for (int k = 0; k < crt::kRecLimbs; ++k) {
-            const uint64_t p = static_cast<uint64_t>(X[k]) * mi + carry;
-            X[k] = static_cast<uint32_t>(p);
-            carry = p >> 32;
+    for (int i = NB - 1; i >= 0; --i) {
+        if (i < N) {
+            const uint64_t mi = static_cast<uint64_t>(crt::kDev.m[i]);
+            uint64_t carry = v[i];
+#pragma unroll
+            for (int k = 0; k < L; ++k) {
+                const uint64_t p = static_cast<uint64_t>(X[k]) * mi + carry;
+                X[k] = static_cast<uint32_t>(p);
+                carry = p >> 32;
+            }
         }
     }
     // X >= ceil(M/2): the value is X - M < 0, magnitude M - X
-    bool ge = true;
+    bool ge = true, decided = false;
 #pragma unroll
-    for (int k = crt::kRecLimbs - 1; k >= 0; --k) {
-        // compare from the top: the first differing word decides
-        if (X[k] != g.H[k]) {
+    for (int k = L - 1; k >= 0; --k) {
+        if (!decided && X[k] != g.H[k]) {
             ge = X[k] > g.H[k];
-            break;
+            decided = true;
         }
     }
     bool neg = false;
     if (ge) {
         uint64_t borrow = 0;
 #pragma unroll
-        for (int k = 0; k < crt::kRecLimbs; ++k) {
+        for (int k = 0; k < L; ++k) {
             const uint64_t d = static_cast<uint64_t>(g.M[k]) - X[k] - borrow;
             X[k] = static_cast<uint32_t>(d);
             borrow = (d >> 63) & 1ull;
@@ -1242,7 +1258,7 @@ __global__ void __launch_bounds__(256) crt_recover_kernel(const CrtRecArgs g)
     }
     const int e = g.sig[row] + g.tau[col] - 2 * g.beta;
 #pragma unroll
-    for (int c = 0; c < P; ++c) g.C[c][row * g.ldc + col] = rn_component(X, neg, e);
+    for (int c = 0; c < P; ++c) g.C[c][row * g.ldc + col] = rn_component<L>(X, neg, e);
 }
 
 // ------------------------------------------------------- tcgen05 engine
@@ -2954,6 +2970,18 @@ template <int P>
 static cudaError_t crt_recover(const GemmArgs<P>& g, int N, int beta, const OzakiLayout& L, const int* sig,
                                const int* tau, const int8_t* rq, cudaStream_t s);
 
+// Residues of both operands, with as few 16-bit limbs as beta needs.
+template <int P, typename T>
+static cudaError_t crt_residues(const GemmArgs<P>& g, int N, const OzakiLayout& L, T* ra, T* rb, int* sig,
+                                int* tau, cudaStream_t s, int beta)
+{
+    switch (residue_kind(beta)) {
+    case 3: return slice_both<P, T, 3>(g, N, L, ra, rb, sig, tau, s, beta);
+    case 2: return slice_both<P, T, 2>(g, N, L, ra, rb, sig, tau, s, beta);
+    default: return slice_both<P, T, 1>(g, N, L, ra, rb, sig, tau, s, beta);
+    }
+}
+
 template <int P>
 cudaError_t launch_crt(const GemmArgs<P>& g, int N, void* ws, cudaStream_t s, int engine)
 {
@@ -2970,7 +2998,7 @@ cudaError_t launch_crt(const GemmArgs<P>& g, int N, void* ws, cudaStream_t s, in
         uint16_t* sa = reinterpret_cast<uint16_t*>(base + L.offA);
         uint16_t* sb = reinterpret_cast<uint16_t*>(base + L.offB);
         e = cudaMemsetAsync(err, 0, sizeof(int), s);
-        if (e == cudaSuccess) e = slice_both<P, uint16_t, 1>(g, N, L, sa, sb, sig, tau, s, beta);
+        if (e == cudaSuccess) e = crt_residues<P, uint16_t>(g, N, L, sa, sb, sig, tau, s, beta);
         if (e != cudaSuccess) return e;
         CUtensorMap ma, mb;
         if (!slice_map(&ma, sa, N, L.mp, L.kp, tcc::BM) || !slice_map(&mb, sb, N, L.np, L.kp, tcc::BN))
@@ -2989,7 +3017,7 @@ cudaError_t launch_crt(const GemmArgs<P>& g, int N, void* ws, cudaStream_t s, in
     }
     int8_t* ra = base + L.offA;
     int8_t* rb = base + L.offB;
-    e = slice_both<P, int8_t, 1>(g, N, L, ra, rb, sig, tau, s, beta);
+    e = crt_residues<P, int8_t>(g, N, L, ra, rb, sig, tau, s, beta);
     if (e != cudaSuccess) return e;
     // 128 x 128 CTA tile, 8 warps of 64 x 32, 4 stages of 64 bytes of k
     constexpr int MT = 4, NT = 4, WM = 2, WN = 4, STG = 4, KS = 64;
@@ -3021,7 +3049,16 @@ static cudaError_t crt_recover(const GemmArgs<P>& g, int N, int beta, const Ozak
     for (int k = 0; k < crt::kRecLimbs; ++k)
         ra_.H[k] = (M1[k] >> 1) | (k + 1 < crt::kRecLimbs ? (M1[k + 1] << 31) : 0u);
     const int64_t outs = g.m * g.n;
-    crt_recover_kernel<P><<<blocks_for(outs, 256), 256, 0, s>>>(ra_);
+    const unsigned grid = blocks_for(outs, 256);
+    switch ((N + 7) / 8) {
+    case 1: crt_recover_kernel<P, 8><<<grid, 256, 0, s>>>(ra_); break;
+    case 2: crt_recover_kernel<P, 16><<<grid, 256, 0, s>>>(ra_); break;
+    case 3: crt_recover_kernel<P, 24><<<grid, 256, 0, s>>>(ra_); break;
+    case 4: crt_recover_kernel<P, 32><<<grid, 256, 0, s>>>(ra_); break;
+    case 5: crt_recover_kernel<P, 40><<<grid, 256, 0, s>>>(ra_); break;
+    case 6: crt_recover_kernel<P, 48><<<grid, 256, 0, s>>>(ra_); break;
+    default: crt_recover_kernel<P, 56><<<grid, 256, 0, s>>>(ra_); break;
+    }
     return cudaGetLastError();
 }
 
