@@ -2518,6 +2518,247 @@ ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
     }
 }
 
+// ------------------------------------------- CRT form on tcgen05 CTA pairs
+//
+// The residue products on pairs of SMs (clusters of two CTAs,
+// tcgen05 .cta_group::2), as the slicing form's DD pair engine: the pair owns
+// a 256 x 128 tile of the products' residues; each CTA loads its 128 rows of
+// the op(A) residue tile and its half (64 rows) of the op(B)^T tile, 128
+// values of k per stage, and signals the leader's barrier; the leader issues
+// M = 256, N = 128 MMAs and releases a stage in both CTAs with one multicast
+// commit.  Each CTA drains its own 128 rows exactly as the single-CTA CRT
+// kernel does.  A CTA receives 48 KB per 2.1 M multiply-adds instead of 64 KB
+// per 2.1 M.  Every wait is bounded; a role that gives up sets the abort flag
+// of both CTAs.
+
+namespace tcp {
+constexpr int BM = 128;                                   // rows per CTA (the pair covers 256)
+constexpr int BN = 128;
+constexpr int KE = 64;
+constexpr int KB = 2;
+constexpr int STAGES = 4;
+constexpr int A_BOX = BM * KE * 2;                        // 16 KB
+constexpr int B_BOX = (BN / 2) * KE * 2;                  // 8 KB
+constexpr int STAGE_BYTES = KB * (A_BOX + B_BOX);         // 48 KB per CTA
+constexpr int SEG_STAGES = 1024 / (KE * KB);
+constexpr int SUM_COL = 2 * BN;
+constexpr int TMEM_COLS = 512;
+constexpr int EPI_ARRIVALS = 8;                           // 4 drain warps in each CTA
+static_assert(SUM_COL + BN <= TMEM_COLS, "TMEM columns");
+}  // namespace tcp
+
+__global__ void __launch_bounds__(192, 1)
+crt_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const CrtTcArgs g)
+{
+    extern __shared__ uint8_t dsm[];
+    __shared__ __align__(8) uint64_t full[tcp::STAGES], empty[tcp::STAGES], accf[2], acce[2], fin;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    const uint32_t raw = smem_u32(dsm);
+    uint8_t* stage0 = dsm + (((raw + 1023u) & ~1023u) - raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    volatile int* abortp = &abort_flag;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < tcp::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], tcp::EPI_ARRIVALS);
+        }
+        mbar_init(&fin, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&tmem_base)), "r"(tcp::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    __syncwarp();
+    cluster_sync_all();        // barriers of both CTAs initialised before any remote arrival
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    const int KT = static_cast<int>(g.kp / (tcp::KE * tcp::KB));
+    const int per_tile = g.N * KT;
+    const int ntiles = g.tiles_m * g.tiles_n;           // pair tiles: tiles_m counts 256-row blocks
+    const int cid = static_cast<int>(cluster_index()), ncl = static_cast<int>(cluster_count());
+    const uint32_t peer_abort = cluster_addr(&abort_flag, rank ^ 1u);
+    auto fail = [&](int code) {
+        *abortp = 1;
+        st_cluster(peer_abort, 1);
+        atomicCAS(g.err, 0, code);
+    };
+    auto seg_end = [&](int kt, int seg_stages) { return kt == KT - 1 || seg_stages == tcp::SEG_STAGES; };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            if (g.test_abort) {
+                fail(1);
+                ok = false;
+            }
+            for (int tile = cid; tile < ntiles && ok; tile += ncl) {
+                const int ma = (tile % g.tiles_m) * 2 * tcp::BM + static_cast<int>(rank) * tcp::BM;
+                const int nb = (tile / g.tiles_m) * tcp::BN + static_cast<int>(rank) * (tcp::BN / 2);
+                for (int i = 0; i < per_tile; ++i, ++it) {
+                    const int mi = i / KT, kt = i % KT;
+                    const uint32_t st = it % tcp::STAGES, ph = (it / tcp::STAGES) & 1u;
+                    if (!mbar_wait_cl<kHintIdle>(&empty[st], ph ^ 1u, abortp)) { fail(1); ok = false; break; }
+                    uint8_t* sa = stage0 + st * tcp::STAGE_BYTES;
+                    const uint32_t bar = cluster_addr(&full[st], 0);
+                    if (rank == 0) mbar_expect_tx(&full[st], 2 * tcp::STAGE_BYTES);
+#pragma unroll
+                    for (int q = 0; q < tcp::KB; ++q) {
+                        const int x = (kt * tcp::KB + q) * tcp::KE;
+                        tma_load_3d_pair(sa + q * tcp::A_BOX, &tmA, x, ma, mi, bar);
+                        tma_load_3d_pair(sa + tcp::KB * tcp::A_BOX + q * tcp::B_BOX, &tmB, x, nb, mi, bar);
+                    }
+                }
+            }
+            // every stage's last release has arrived (the leader's MMAs have
+            // read this CTA's loads) before the CTA may exit
+            for (uint32_t j = 0; j < tcp::STAGES && j < it; ++j) {
+                const uint32_t k = it - 1 - j;
+                const unsigned long long t0 = gtimer();
+                while (!mbar_try_cl(&empty[k % tcp::STAGES], (k / tcp::STAGES) & 1u) &&
+                       gtimer() - t0 < tc::TIMEOUT_NS) {
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && rank == 0) {
+            uint32_t it = 0, seg = 0;
+            int pend = -1;
+            bool ok = true;
+            for (int tile = cid; tile < ntiles && ok; tile += ncl) {
+                int seg_stages = 0;
+                uint32_t b = 0;
+                for (int i = 0; i < per_tile; ++i, ++it) {
+                    const int kt = i % KT;
+                    if (seg_stages == 0) {
+                        b = seg & 1u;
+                        if (!mbar_wait_cl<kHintIssue>(&acce[b], ((seg >> 1) & 1u) ^ 1u, abortp)) { fail(2); ok = false; break; }
+                    }
+                    const uint32_t st = it % tcp::STAGES, ph = (it / tcp::STAGES) & 1u;
+                    if (!mbar_wait_cl<kHintIssue>(&full[st], ph, abortp)) { fail(3); ok = false; break; }
+                    tc_fence_after();
+                    if (pend >= 0) {
+                        umma_commit_both(&accf[pend]);
+                        pend = -1;
+                    }
+                    const uint32_t sa = smem_u32(stage0 + st * tcp::STAGE_BYTES);
+#pragma unroll
+                    for (int q = 0; q < tcp::KB; ++q) {
+                        const uint64_t da = umma_desc(sa + q * tcp::A_BOX);
+                        const uint64_t db = umma_desc(sa + tcp::KB * tcp::A_BOX + q * tcp::B_BOX);
+#pragma unroll
+                        for (int kk = 0; kk < tcp::KE / 16; ++kk)
+                            umma_pair(tmem + b * tcp::BN, da + 2ull * kk, db + 2ull * kk,
+                                      (seg_stages > 0 || q > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    umma_commit_both(&empty[st]);
+                    ++seg_stages;
+                    if (seg_end(kt, seg_stages)) {
+                        pend = static_cast<int>(b);
+                        ++seg;
+                        seg_stages = 0;
+                    }
+                }
+            }
+            if (pend >= 0) umma_commit_both(&accf[pend]);
+            // every MMA issued has completed before TMEM is released
+            umma_commit_pair_local(&fin);
+            const unsigned long long t0 = gtimer();
+            while (!mbar_try_cl(&fin, 0u) && gtimer() - t0 < tc::TIMEOUT_NS) {
+            }
+        }
+    } else {
+        const int q = warp & 3;
+        const int r = 32 * q + lane;
+        const uint32_t lane_off = static_cast<uint32_t>(32 * q) << 16;
+        const uint32_t sums = tmem + lane_off + tcp::SUM_COL;
+        const uint32_t lead_acce0 = cluster_addr(&acce[0], 0), lead_acce1 = cluster_addr(&acce[1], 0);
+        uint32_t seg = 0;
+        bool ok = true;
+        for (int tile = cid; tile < ntiles && ok; tile += ncl) {
+            const int m0 = (tile % g.tiles_m) * 2 * tcp::BM + static_cast<int>(rank) * tcp::BM;
+            const int n0 = (tile / g.tiles_m) * tcp::BN;
+            int seg_stages = 0;
+            bool first = true;                            // first segment of a modulus
+            for (int i = 0; i < per_tile; ++i) {
+                const int mi = i / KT, kt = i % KT;
+                ++seg_stages;
+                if (!seg_end(kt, seg_stages)) continue;
+                seg_stages = 0;
+                const uint32_t b = seg & 1u;
+                if (!__all_sync(0xffffffffu, mbar_wait_cl<kHintIdle>(&accf[b], (seg >> 1) & 1u, abortp))) {
+                    fail(4);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const bool last = kt == KT - 1;
+                const int m = crt::kDev.m[mi];
+                for (int c0 = 0; c0 < tcp::BN; c0 += 32) {
+                    uint32_t fv[32], sv[32];
+                    tmem_ld32(tmem + lane_off + b * tcp::BN + c0, fv);
+                    if (!first) tmem_ld32(sums + c0, sv);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int t = 0; t < 32; ++t) {
+                        const int add = __float2int_rn(__uint_as_float(fv[t]));
+                        sv[t] = first ? static_cast<uint32_t>(add) : sv[t] + static_cast<uint32_t>(add);
+                    }
+                    if (!last) {
+                        tmem_st32(sums + c0, sv);
+                    } else {
+                        uint32_t pk[8];
+#pragma unroll
+                        for (int w = 0; w < 8; ++w) pk[w] = 0u;
+#pragma unroll
+                        for (int t = 0; t < 32; ++t) {
+                            const int v = static_cast<int>(sv[t]);
+                            const uint32_t mag = static_cast<uint32_t>(v < 0 ? -v : v);
+                            int rr = static_cast<int>(crt::mod_small(mag, mi));
+                            if (v < 0 && rr) rr = m - rr;
+                            rr = rr >= (m + 1) / 2 ? rr - m : rr;
+                            pk[t >> 2] |= (static_cast<uint32_t>(rr) & 0xffu) << (8 * (t & 3));
+                        }
+                        uint4* dst = reinterpret_cast<uint4*>(g.out + (static_cast<int64_t>(mi) * g.mp + m0 + r) * g.np +
+                                                              n0 + c0);
+                        dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                    }
+                }
+                tmem_wait_st();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(b ? lead_acce1 : lead_acce0);
+                ++seg;
+                first = last;
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    __syncwarp();
+    cluster_sync_all();        // no remote arrival or TMA into this CTA is outstanding
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcp::TMEM_COLS));
+    }
+}
+
 // ------------------------------------------------------- fixed scratch
 
 // Scratch for callers that cannot allocate device memory (see
@@ -2916,7 +3157,7 @@ OzakiLayout crt_layout(int N, int64_t m, int64_t n, int64_t k, int engine)
     OzakiLayout L;
     const int elem_bytes = engine == 1 ? 2 : 1;
     L.S = N;
-    L.mp = round_up(m > 0 ? m : 1, 128);
+    L.mp = round_up(m > 0 ? m : 1, engine == 1 ? 256 : 128);     // tcgen05: 256-row tiles of CTA pairs
     L.np = round_up(n > 0 ? n : 1, 128);
     L.kp = round_up(k > 0 ? k : 1, KPAD);
     L.offA = engine == 1 ? 256 : 0;                    // tcgen05: a 256-byte header (error code)
@@ -2982,8 +3223,34 @@ static cudaError_t crt_residues(const GemmArgs<P>& g, int N, const OzakiLayout& 
     }
 }
 
+// Clusters of two CTAs of a pair kernel with `smem` bytes of dynamic shared
+// memory that fit on the device at once (the attribute is set first).
+template <typename K>
+static cudaError_t max_clusters(K kernel, int smem, int* out)
+{
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2);
+    cfg.blockDim = dim3(192);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    e = cudaOccupancyMaxActiveClusters(&n, kernel, &cfg);
+    if (e != cudaSuccess) return e;
+    if (n < 1) return cudaErrorInvalidConfiguration;
+    *out = n;
+    return cudaSuccess;
+}
+
 template <int P>
-cudaError_t launch_crt(const GemmArgs<P>& g, int N, void* ws, cudaStream_t s, int engine)
+cudaError_t launch_crt(const GemmArgs<P>& g, int N, void* ws, cudaStream_t s, int engine, int variant)
 {
     const int beta = crt_beta(N, g.k);
     if (beta < 1) return cudaErrorInvalidValue;
@@ -3001,16 +3268,42 @@ cudaError_t launch_crt(const GemmArgs<P>& g, int N, void* ws, cudaStream_t s, in
         if (e == cudaSuccess) e = crt_residues<P, uint16_t>(g, N, L, sa, sb, sig, tau, s, beta);
         if (e != cudaSuccess) return e;
         CUtensorMap ma, mb;
-        if (!slice_map(&ma, sa, N, L.mp, L.kp, tcc::BM) || !slice_map(&mb, sb, N, L.np, L.kp, tcc::BN))
-            return cudaErrorInvalidValue;
-        const CrtTcArgs a{rq, L.mp, L.np, L.kp, N, static_cast<int>(L.mp / tcc::BM),
-                          static_cast<int>(L.np / tcc::BN), err, tc_test_abort()};
-        const int smem = tcc::STAGES * tcc::STAGE_BYTES + 1024;
-        e = cudaFuncSetAttribute(crt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        const int tiles = a.tiles_m * a.tiles_n;
-        const int grid = tiles < num_sms() ? tiles : num_sms();
-        crt_tc_kernel<<<grid, 192, smem, s>>>(ma, mb, a);
+        if (variant == 1) {          // one CTA per 128 x 128 tile
+            if (!slice_map(&ma, sa, N, L.mp, L.kp, tcc::BM) || !slice_map(&mb, sb, N, L.np, L.kp, tcc::BN))
+                return cudaErrorInvalidValue;
+            const CrtTcArgs a{rq, L.mp, L.np, L.kp, N, static_cast<int>(L.mp / tcc::BM),
+                              static_cast<int>(L.np / tcc::BN), err, tc_test_abort()};
+            const int smem = tcc::STAGES * tcc::STAGE_BYTES + 1024;
+            e = cudaFuncSetAttribute(crt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            const int tiles = a.tiles_m * a.tiles_n;
+            const int grid = tiles < num_sms() ? tiles : num_sms();
+            crt_tc_kernel<<<grid, 192, smem, s>>>(ma, mb, a);
+        } else {                     // CTA pairs, 256 x 128 tiles
+            if (!slice_map(&ma, sa, N, L.mp, L.kp, tcp::BM) || !slice_map(&mb, sb, N, L.np, L.kp, tcp::BN / 2))
+                return cudaErrorInvalidValue;
+            const CrtTcArgs a{rq, L.mp, L.np, L.kp, N, static_cast<int>(L.mp / (2 * tcp::BM)),
+                              static_cast<int>(L.np / tcp::BN), err, tc_test_abort()};
+            const int smem = tcp::STAGES * tcp::STAGE_BYTES + 1024;
+            int clusters = 0;
+            e = max_clusters(crt_tc_pair_kernel, smem, &clusters);
+            if (e != cudaSuccess) return e;
+            const int tiles = a.tiles_m * a.tiles_n;
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = 2;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(2 * static_cast<unsigned>(tiles < clusters ? tiles : clusters));
+            cfg.blockDim = dim3(192);
+            cfg.dynamicSmemBytes = smem;
+            cfg.stream = s;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            e = cudaLaunchKernelEx(&cfg, crt_tc_pair_kernel, ma, mb, a);
+            if (e != cudaSuccess) return e;
+        }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         return crt_recover<P>(g, N, beta, L, sig, tau, rq, s);
@@ -3062,8 +3355,8 @@ static cudaError_t crt_recover(const GemmArgs<P>& g, int N, int beta, const Ozak
     return cudaGetLastError();
 }
 
-template cudaError_t launch_crt<2>(const GemmArgs<2>&, int, void*, cudaStream_t, int);
-template cudaError_t launch_crt<3>(const GemmArgs<3>&, int, void*, cudaStream_t, int);
-template cudaError_t launch_crt<4>(const GemmArgs<4>&, int, void*, cudaStream_t, int);
+template cudaError_t launch_crt<2>(const GemmArgs<2>&, int, void*, cudaStream_t, int, int);
+template cudaError_t launch_crt<3>(const GemmArgs<3>&, int, void*, cudaStream_t, int, int);
+template cudaError_t launch_crt<4>(const GemmArgs<4>&, int, void*, cudaStream_t, int, int);
 
 }  // namespace mpg
