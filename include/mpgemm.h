@@ -292,15 +292,13 @@ int mpgemm_ex(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k,
  *
  * MPG_ALGO_BF16_CRT: the same residues, products and result (bit-identical
  * to MPG_ALGO_INT8_CRT), with the residues stored as bf16 (exact: |r| <= 128),
- * loaded by TMA and multiplied by tcgen05.mma (kind::f16, fp32 accumulation
- * in tensor memory) -- by default on pairs of SMs (.cta_group::2, M = 256,
- * N = 128 per pair), with opts->tile = 1 on single SMs (M = N = 128); each
- * accumulator is drained into an exact int32 sum after at most 1024 values
- * of k, so every fp32 partial sum is an integer below 2^24.  Workspace: a
- * 256-byte header whose first int32 is 0 after a normal run (else the code of
- * the role whose bounded wait gave up, read by mpgemm_tc_status), then the
- * regions above with mp rounded up to 256 and the residues of op(A) and
- * op(B)^T as bf16 (2 bytes each). */
+ * loaded by TMA and multiplied by tcgen05.mma (kind::f16, M = N = 128, fp32
+ * accumulation in tensor memory); each accumulator is drained into an exact
+ * int32 sum after at most 1024 values of k, so every fp32 partial sum is an
+ * integer below 2^24.  Workspace: a 256-byte header whose first int32 is 0
+ * after a normal run (else the code of the role whose bounded wait gave up,
+ * read by mpgemm_tc_status), then the regions above with the residues of
+ * op(A) and op(B)^T as bf16 (2 bytes each). */
 
 /* beta of the CRT form for N moduli and inner dimension k (>= 1 when the
  * form applies, 0 when the moduli's product is too small); MPG_EINVAL for N

@@ -238,8 +238,7 @@ static int crt_call(const GemmArgs<P>& g, const mpgemm_opts* o)
             overlap(rw, plane_range(g.C[c], g.m, g.n, g.ldc)))
             return fail(MPG_EWORKSPACE, "workspace overlaps an operand");
     }
-    if (o->tile < -1 || o->tile > 2) return fail(MPG_EINVAL, "CRT tile id %d out of range 1..2", o->tile);
-    cudaError_t e = launch_crt<P>(g, N, o->workspace, g_stream, engine, o->tile > 0 ? o->tile : 0);
+    cudaError_t e = launch_crt<P>(g, N, o->workspace, g_stream, engine);
     return e == cudaSuccess ? MPG_OK : cuda_fail(e, "CRT gemm launch");
 }
 

@@ -1087,6 +1087,10 @@ struct CrtRecArgs {
     int N, beta;
     uint32_t M[crt::kRecLimbs];          // the product of the moduli
     uint32_t H[crt::kRecLimbs];          // ceil(M / 2)
+    // the CRT weights W_i = (M / m_i) c_i, c_i = (M / m_i)^-1 mod m_i, so that
+    // X = sum_i r_i W_i - M floor(sum_i r_i c_i / m_i) for residues r_i in [0, m_i)
+    uint32_t W[crt::kMaxModuli][crt::kRecLimbs];
+    float f[crt::kMaxModuli];             // c_i / m_i
 };
 
 // Big unsigned integers of L 32-bit limbs, least significant first, kept in
@@ -1195,70 +1199,112 @@ __device__ __forceinline__ double rn_component(uint32_t (&u)[L], bool& neg, int 
 }
 
 // NB: the moduli count rounded up to a multiple of 8 (the loops below are
-// unrolled NB times and skip moduli i >= N, so the digits stay in registers);
-// L = NB / 4 limbs (at most 11) hold the product of NB moduli <= 256.
+// unrolled NB times and skip moduli i >= N); L = NB / 4 limbs (at most 11)
+// hold the product of NB moduli <= 256.  The integer in [0, M) congruent to
+// the residues is sum_i r_i W_i - q M with q = floor(sum_i r_i c_i / m_i):
+// the sum is accumulated exactly in 64-bit columns (each term below 2^40), q
+// is estimated in binary32 (off by at most one: the sum is below 2^14 and its
+// rounding error far below one) and corrected by one addition or subtraction
+// of M.
 template <int P, int NB>
-__global__ void __launch_bounds__(256) crt_recover_kernel(const CrtRecArgs g)
+__global__ void __launch_bounds__(256) crt_recover_kernel(const __grid_constant__ CrtRecArgs g)
 {
     constexpr int L = NB / 4 < crt::kRecLimbs ? NB / 4 : crt::kRecLimbs;
     const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (t >= g.m * g.n) return;
     const int64_t row = t / g.n, col = t % g.n;
     const int N = g.N;
-    uint32_t v[NB];
+    uint64_t S[L + 1];
+#pragma unroll
+    for (int k = 0; k <= L; ++k) S[k] = 0ull;
+    float qf = 0.0f;
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
-        v[i] = 0u;
         if (i < N) {
             const int mi = crt::kDev.m[i];
             int r = g.res[(static_cast<int64_t>(i) * g.mp + row) * g.np + col];
             if (r < 0) r += mi;
-            uint32_t ts = 0;
+            const uint32_t ru = static_cast<uint32_t>(r);
 #pragma unroll
-            for (int j = 0; j < i; ++j) ts += v[j] * crt::kDev.pm[i][j];
-            const uint32_t d = static_cast<uint32_t>(r) + static_cast<uint32_t>(mi) - crt::mod_small(ts, i);
-            v[i] = crt::mod_small(d * crt::kDev.inv[i], i);
+            for (int k = 0; k < L; ++k) S[k] += static_cast<uint64_t>(g.W[i][k]) * ru;
+            qf = __fmaf_rn(static_cast<float>(r), g.f[i], qf);
         }
     }
-    uint32_t X[L];
+    // carries: S as L + 1 32-bit limbs (S < 2^14 M)
+    uint32_t X[L + 1];
+    uint64_t carry = 0;
 #pragma unroll
-    for (int k = 0; k < L; ++k) X[k] = 0u;
+    for (int k = 0; k <= L; ++k) {
+        const uint64_t v = S[k] + carry;
+        X[k] = static_cast<uint32_t>(v);
+        carry = v >> 32;
+    }
+    // X -= q M, then one correction by M either way
+    const uint32_t q = static_cast<uint32_t>(floorf(qf));
+    uint64_t mc = 0;
+    int64_t borrow = 0;
 #pragma unroll
-    for (int i = NB - 1; i >= 0; --i) {
-        if (i < N) {
-            const uint64_t mi = static_cast<uint64_t>(crt::kDev.m[i]);
-            uint64_t carry = v[i];
+    for (int k = 0; k <= L; ++k) {
+        const uint64_t pm = static_cast<uint64_t>(k < L ? g.M[k] : 0u) * q + mc;
+        mc = pm >> 32;
+        const int64_t d = static_cast<int64_t>(X[k]) - static_cast<int64_t>(static_cast<uint32_t>(pm)) + borrow;
+        X[k] = static_cast<uint32_t>(d);
+        borrow = d >> 32;                              // 0 or -1
+    }
+    if (static_cast<int32_t>(X[L]) < 0) {             // q was one too large: add M back
+        uint64_t c = 0;
 #pragma unroll
-            for (int k = 0; k < L; ++k) {
-                const uint64_t p = static_cast<uint64_t>(X[k]) * mi + carry;
-                X[k] = static_cast<uint32_t>(p);
-                carry = p >> 32;
+        for (int k = 0; k <= L; ++k) {
+            const uint64_t v = static_cast<uint64_t>(X[k]) + (k < L ? g.M[k] : 0u) + c;
+            X[k] = static_cast<uint32_t>(v);
+            c = v >> 32;
+        }
+    } else {                                          // q one too small: X >= M
+        bool ge = X[L] != 0u, decided = X[L] != 0u;
+#pragma unroll
+        for (int k = L - 1; k >= 0; --k) {
+            if (!decided && X[k] != g.M[k]) {
+                ge = X[k] > g.M[k];
+                decided = true;
+            }
+        }
+        if (!decided) ge = true;
+        if (ge) {
+            int64_t b2 = 0;
+#pragma unroll
+            for (int k = 0; k <= L; ++k) {
+                const int64_t d = static_cast<int64_t>(X[k]) - static_cast<int64_t>(k < L ? g.M[k] : 0u) + b2;
+                X[k] = static_cast<uint32_t>(d);
+                b2 = d >> 32;
             }
         }
     }
-    // X >= ceil(M/2): the value is X - M < 0, magnitude M - X
+    uint32_t Y[L];
+#pragma unroll
+    for (int k = 0; k < L; ++k) Y[k] = X[k];
+    // Y >= ceil(M/2): the value is Y - M < 0, magnitude M - Y
     bool ge = true, decided = false;
 #pragma unroll
     for (int k = L - 1; k >= 0; --k) {
-        if (!decided && X[k] != g.H[k]) {
-            ge = X[k] > g.H[k];
+        if (!decided && Y[k] != g.H[k]) {
+            ge = Y[k] > g.H[k];
             decided = true;
         }
     }
     bool neg = false;
     if (ge) {
-        uint64_t borrow = 0;
+        uint64_t bw = 0;
 #pragma unroll
         for (int k = 0; k < L; ++k) {
-            const uint64_t d = static_cast<uint64_t>(g.M[k]) - X[k] - borrow;
-            X[k] = static_cast<uint32_t>(d);
-            borrow = (d >> 63) & 1ull;
+            const uint64_t d = static_cast<uint64_t>(g.M[k]) - Y[k] - bw;
+            Y[k] = static_cast<uint32_t>(d);
+            bw = (d >> 63) & 1ull;
         }
         neg = true;
     }
     const int e = g.sig[row] + g.tau[col] - 2 * g.beta;
 #pragma unroll
-    for (int c = 0; c < P; ++c) g.C[c][row * g.ldc + col] = rn_component<L>(X, neg, e);
+    for (int c = 0; c < P; ++c) g.C[c][row * g.ldc + col] = rn_component<L>(Y, neg, e);
 }
 
 // ------------------------------------------------------- tcgen05 engine
@@ -2518,247 +2564,6 @@ ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
     }
 }
 
-// ------------------------------------------- CRT form on tcgen05 CTA pairs
-//
-// The residue products on pairs of SMs (clusters of two CTAs,
-// tcgen05 .cta_group::2), as the slicing form's DD pair engine: the pair owns
-// a 256 x 128 tile of the products' residues; each CTA loads its 128 rows of
-// the op(A) residue tile and its half (64 rows) of the op(B)^T tile, 128
-// values of k per stage, and signals the leader's barrier; the leader issues
-// M = 256, N = 128 MMAs and releases a stage in both CTAs with one multicast
-// commit.  Each CTA drains its own 128 rows exactly as the single-CTA CRT
-// kernel does.  A CTA receives 48 KB per 2.1 M multiply-adds instead of 64 KB
-// per 2.1 M.  Every wait is bounded; a role that gives up sets the abort flag
-// of both CTAs.
-
-namespace tcp {
-constexpr int BM = 128;                                   // rows per CTA (the pair covers 256)
-constexpr int BN = 128;
-constexpr int KE = 64;
-constexpr int KB = 2;
-constexpr int STAGES = 4;
-constexpr int A_BOX = BM * KE * 2;                        // 16 KB
-constexpr int B_BOX = (BN / 2) * KE * 2;                  // 8 KB
-constexpr int STAGE_BYTES = KB * (A_BOX + B_BOX);         // 48 KB per CTA
-constexpr int SEG_STAGES = 1024 / (KE * KB);
-constexpr int SUM_COL = 2 * BN;
-constexpr int TMEM_COLS = 512;
-constexpr int EPI_ARRIVALS = 8;                           // 4 drain warps in each CTA
-static_assert(SUM_COL + BN <= TMEM_COLS, "TMEM columns");
-}  // namespace tcp
-
-__global__ void __launch_bounds__(192, 1)
-crt_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const CrtTcArgs g)
-{
-    extern __shared__ uint8_t dsm[];
-    __shared__ __align__(8) uint64_t full[tcp::STAGES], empty[tcp::STAGES], accf[2], acce[2], fin;
-    __shared__ uint32_t tmem_base;
-    __shared__ int abort_flag;
-    const uint32_t raw = smem_u32(dsm);
-    uint8_t* stage0 = dsm + (((raw + 1023u) & ~1023u) - raw);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t rank = cluster_rank();
-    volatile int* abortp = &abort_flag;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < tcp::STAGES; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
-        }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&accf[b], 1);
-            mbar_init(&acce[b], tcp::EPI_ARRIVALS);
-        }
-        mbar_init(&fin, 1);
-        abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"(smem_u32(&tmem_base)), "r"(tcp::TMEM_COLS));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
-    }
-    tc_fence_before();
-    __syncthreads();
-    __syncwarp();
-    cluster_sync_all();        // barriers of both CTAs initialised before any remote arrival
-    tc_fence_after();
-    const uint32_t tmem = tmem_base;
-
-    const int KT = static_cast<int>(g.kp / (tcp::KE * tcp::KB));
-    const int per_tile = g.N * KT;
-    const int ntiles = g.tiles_m * g.tiles_n;           // pair tiles: tiles_m counts 256-row blocks
-    const int cid = static_cast<int>(cluster_index()), ncl = static_cast<int>(cluster_count());
-    const uint32_t peer_abort = cluster_addr(&abort_flag, rank ^ 1u);
-    auto fail = [&](int code) {
-        *abortp = 1;
-        st_cluster(peer_abort, 1);
-        atomicCAS(g.err, 0, code);
-    };
-    auto seg_end = [&](int kt, int seg_stages) { return kt == KT - 1 || seg_stages == tcp::SEG_STAGES; };
-
-    if (warp == 0) {
-        if (lane == 0) {
-            uint32_t it = 0;
-            bool ok = true;
-            if (g.test_abort) {
-                fail(1);
-                ok = false;
-            }
-            for (int tile = cid; tile < ntiles && ok; tile += ncl) {
-                const int ma = (tile % g.tiles_m) * 2 * tcp::BM + static_cast<int>(rank) * tcp::BM;
-                const int nb = (tile / g.tiles_m) * tcp::BN + static_cast<int>(rank) * (tcp::BN / 2);
-                for (int i = 0; i < per_tile; ++i, ++it) {
-                    const int mi = i / KT, kt = i % KT;
-                    const uint32_t st = it % tcp::STAGES, ph = (it / tcp::STAGES) & 1u;
-                    if (!mbar_wait_cl<kHintIdle>(&empty[st], ph ^ 1u, abortp)) { fail(1); ok = false; break; }
-                    uint8_t* sa = stage0 + st * tcp::STAGE_BYTES;
-                    const uint32_t bar = cluster_addr(&full[st], 0);
-                    if (rank == 0) mbar_expect_tx(&full[st], 2 * tcp::STAGE_BYTES);
-#pragma unroll
-                    for (int q = 0; q < tcp::KB; ++q) {
-                        const int x = (kt * tcp::KB + q) * tcp::KE;
-                        tma_load_3d_pair(sa + q * tcp::A_BOX, &tmA, x, ma, mi, bar);
-                        tma_load_3d_pair(sa + tcp::KB * tcp::A_BOX + q * tcp::B_BOX, &tmB, x, nb, mi, bar);
-                    }
-                }
-            }
-            // every stage's last release has arrived (the leader's MMAs have
-            // read this CTA's loads) before the CTA may exit
-            for (uint32_t j = 0; j < tcp::STAGES && j < it; ++j) {
-                const uint32_t k = it - 1 - j;
-                const unsigned long long t0 = gtimer();
-                while (!mbar_try_cl(&empty[k % tcp::STAGES], (k / tcp::STAGES) & 1u) &&
-                       gtimer() - t0 < tc::TIMEOUT_NS) {
-                }
-            }
-        }
-    } else if (warp == 1) {
-        if (lane == 0 && rank == 0) {
-            uint32_t it = 0, seg = 0;
-            int pend = -1;
-            bool ok = true;
-            for (int tile = cid; tile < ntiles && ok; tile += ncl) {
-                int seg_stages = 0;
-                uint32_t b = 0;
-                for (int i = 0; i < per_tile; ++i, ++it) {
-                    const int kt = i % KT;
-                    if (seg_stages == 0) {
-                        b = seg & 1u;
-                        if (!mbar_wait_cl<kHintIssue>(&acce[b], ((seg >> 1) & 1u) ^ 1u, abortp)) { fail(2); ok = false; break; }
-                    }
-                    const uint32_t st = it % tcp::STAGES, ph = (it / tcp::STAGES) & 1u;
-                    if (!mbar_wait_cl<kHintIssue>(&full[st], ph, abortp)) { fail(3); ok = false; break; }
-                    tc_fence_after();
-                    if (pend >= 0) {
-                        umma_commit_both(&accf[pend]);
-                        pend = -1;
-                    }
-                    const uint32_t sa = smem_u32(stage0 + st * tcp::STAGE_BYTES);
-#pragma unroll
-                    for (int q = 0; q < tcp::KB; ++q) {
-                        const uint64_t da = umma_desc(sa + q * tcp::A_BOX);
-                        const uint64_t db = umma_desc(sa + tcp::KB * tcp::A_BOX + q * tcp::B_BOX);
-#pragma unroll
-                        for (int kk = 0; kk < tcp::KE / 16; ++kk)
-                            umma_pair(tmem + b * tcp::BN, da + 2ull * kk, db + 2ull * kk,
-                                      (seg_stages > 0 || q > 0 || kk > 0) ? 1u : 0u);
-                    }
-                    umma_commit_both(&empty[st]);
-                    ++seg_stages;
-                    if (seg_end(kt, seg_stages)) {
-                        pend = static_cast<int>(b);
-                        ++seg;
-                        seg_stages = 0;
-                    }
-                }
-            }
-            if (pend >= 0) umma_commit_both(&accf[pend]);
-            // every MMA issued has completed before TMEM is released
-            umma_commit_pair_local(&fin);
-            const unsigned long long t0 = gtimer();
-            while (!mbar_try_cl(&fin, 0u) && gtimer() - t0 < tc::TIMEOUT_NS) {
-            }
-        }
-    } else {
-        const int q = warp & 3;
-        const int r = 32 * q + lane;
-        const uint32_t lane_off = static_cast<uint32_t>(32 * q) << 16;
-        const uint32_t sums = tmem + lane_off + tcp::SUM_COL;
-        const uint32_t lead_acce0 = cluster_addr(&acce[0], 0), lead_acce1 = cluster_addr(&acce[1], 0);
-        uint32_t seg = 0;
-        bool ok = true;
-        for (int tile = cid; tile < ntiles && ok; tile += ncl) {
-            const int m0 = (tile % g.tiles_m) * 2 * tcp::BM + static_cast<int>(rank) * tcp::BM;
-            const int n0 = (tile / g.tiles_m) * tcp::BN;
-            int seg_stages = 0;
-            bool first = true;                            // first segment of a modulus
-            for (int i = 0; i < per_tile; ++i) {
-                const int mi = i / KT, kt = i % KT;
-                ++seg_stages;
-                if (!seg_end(kt, seg_stages)) continue;
-                seg_stages = 0;
-                const uint32_t b = seg & 1u;
-                if (!__all_sync(0xffffffffu, mbar_wait_cl<kHintIdle>(&accf[b], (seg >> 1) & 1u, abortp))) {
-                    fail(4);
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                const bool last = kt == KT - 1;
-                const int m = crt::kDev.m[mi];
-                for (int c0 = 0; c0 < tcp::BN; c0 += 32) {
-                    uint32_t fv[32], sv[32];
-                    tmem_ld32(tmem + lane_off + b * tcp::BN + c0, fv);
-                    if (!first) tmem_ld32(sums + c0, sv);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int t = 0; t < 32; ++t) {
-                        const int add = __float2int_rn(__uint_as_float(fv[t]));
-                        sv[t] = first ? static_cast<uint32_t>(add) : sv[t] + static_cast<uint32_t>(add);
-                    }
-                    if (!last) {
-                        tmem_st32(sums + c0, sv);
-                    } else {
-                        uint32_t pk[8];
-#pragma unroll
-                        for (int w = 0; w < 8; ++w) pk[w] = 0u;
-#pragma unroll
-                        for (int t = 0; t < 32; ++t) {
-                            const int v = static_cast<int>(sv[t]);
-                            const uint32_t mag = static_cast<uint32_t>(v < 0 ? -v : v);
-                            int rr = static_cast<int>(crt::mod_small(mag, mi));
-                            if (v < 0 && rr) rr = m - rr;
-                            rr = rr >= (m + 1) / 2 ? rr - m : rr;
-                            pk[t >> 2] |= (static_cast<uint32_t>(rr) & 0xffu) << (8 * (t & 3));
-                        }
-                        uint4* dst = reinterpret_cast<uint4*>(g.out + (static_cast<int64_t>(mi) * g.mp + m0 + r) * g.np +
-                                                              n0 + c0);
-                        dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                        dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-                    }
-                }
-                tmem_wait_st();
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive_cluster(b ? lead_acce1 : lead_acce0);
-                ++seg;
-                first = last;
-            }
-        }
-    }
-
-    tc_fence_before();
-    __syncthreads();
-    __syncwarp();
-    cluster_sync_all();        // no remote arrival or TMA into this CTA is outstanding
-    if (warp == 1) {
-        tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcp::TMEM_COLS));
-    }
-}
-
 // ------------------------------------------------------- fixed scratch
 
 // Scratch for callers that cannot allocate device memory (see
@@ -3157,7 +2962,7 @@ OzakiLayout crt_layout(int N, int64_t m, int64_t n, int64_t k, int engine)
     OzakiLayout L;
     const int elem_bytes = engine == 1 ? 2 : 1;
     L.S = N;
-    L.mp = round_up(m > 0 ? m : 1, engine == 1 ? 256 : 128);     // tcgen05: 256-row tiles of CTA pairs
+    L.mp = round_up(m > 0 ? m : 1, 128);
     L.np = round_up(n > 0 ? n : 1, 128);
     L.kp = round_up(k > 0 ? k : 1, KPAD);
     L.offA = engine == 1 ? 256 : 0;                    // tcgen05: a 256-byte header (error code)
@@ -3223,34 +3028,8 @@ static cudaError_t crt_residues(const GemmArgs<P>& g, int N, const OzakiLayout& 
     }
 }
 
-// Clusters of two CTAs of a pair kernel with `smem` bytes of dynamic shared
-// memory that fit on the device at once (the attribute is set first).
-template <typename K>
-static cudaError_t max_clusters(K kernel, int smem, int* out)
-{
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 2;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(2);
-    cfg.blockDim = dim3(192);
-    cfg.dynamicSmemBytes = smem;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    int n = 0;
-    e = cudaOccupancyMaxActiveClusters(&n, kernel, &cfg);
-    if (e != cudaSuccess) return e;
-    if (n < 1) return cudaErrorInvalidConfiguration;
-    *out = n;
-    return cudaSuccess;
-}
-
 template <int P>
-cudaError_t launch_crt(const GemmArgs<P>& g, int N, void* ws, cudaStream_t s, int engine, int variant)
+cudaError_t launch_crt(const GemmArgs<P>& g, int N, void* ws, cudaStream_t s, int engine)
 {
     const int beta = crt_beta(N, g.k);
     if (beta < 1) return cudaErrorInvalidValue;
@@ -3268,42 +3047,16 @@ cudaError_t launch_crt(const GemmArgs<P>& g, int N, void* ws, cudaStream_t s, in
         if (e == cudaSuccess) e = crt_residues<P, uint16_t>(g, N, L, sa, sb, sig, tau, s, beta);
         if (e != cudaSuccess) return e;
         CUtensorMap ma, mb;
-        if (variant == 1) {          // one CTA per 128 x 128 tile
-            if (!slice_map(&ma, sa, N, L.mp, L.kp, tcc::BM) || !slice_map(&mb, sb, N, L.np, L.kp, tcc::BN))
-                return cudaErrorInvalidValue;
-            const CrtTcArgs a{rq, L.mp, L.np, L.kp, N, static_cast<int>(L.mp / tcc::BM),
-                              static_cast<int>(L.np / tcc::BN), err, tc_test_abort()};
-            const int smem = tcc::STAGES * tcc::STAGE_BYTES + 1024;
-            e = cudaFuncSetAttribute(crt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            if (e != cudaSuccess) return e;
-            const int tiles = a.tiles_m * a.tiles_n;
-            const int grid = tiles < num_sms() ? tiles : num_sms();
-            crt_tc_kernel<<<grid, 192, smem, s>>>(ma, mb, a);
-        } else {                     // CTA pairs, 256 x 128 tiles
-            if (!slice_map(&ma, sa, N, L.mp, L.kp, tcp::BM) || !slice_map(&mb, sb, N, L.np, L.kp, tcp::BN / 2))
-                return cudaErrorInvalidValue;
-            const CrtTcArgs a{rq, L.mp, L.np, L.kp, N, static_cast<int>(L.mp / (2 * tcp::BM)),
-                              static_cast<int>(L.np / tcp::BN), err, tc_test_abort()};
-            const int smem = tcp::STAGES * tcp::STAGE_BYTES + 1024;
-            int clusters = 0;
-            e = max_clusters(crt_tc_pair_kernel, smem, &clusters);
-            if (e != cudaSuccess) return e;
-            const int tiles = a.tiles_m * a.tiles_n;
-            cudaLaunchConfig_t cfg = {};
-            cudaLaunchAttribute at[1];
-            at[0].id = cudaLaunchAttributeClusterDimension;
-            at[0].val.clusterDim.x = 2;
-            at[0].val.clusterDim.y = 1;
-            at[0].val.clusterDim.z = 1;
-            cfg.gridDim = dim3(2 * static_cast<unsigned>(tiles < clusters ? tiles : clusters));
-            cfg.blockDim = dim3(192);
-            cfg.dynamicSmemBytes = smem;
-            cfg.stream = s;
-            cfg.attrs = at;
-            cfg.numAttrs = 1;
-            e = cudaLaunchKernelEx(&cfg, crt_tc_pair_kernel, ma, mb, a);
-            if (e != cudaSuccess) return e;
-        }
+        if (!slice_map(&ma, sa, N, L.mp, L.kp, tcc::BM) || !slice_map(&mb, sb, N, L.np, L.kp, tcc::BN))
+            return cudaErrorInvalidValue;
+        const CrtTcArgs a{rq, L.mp, L.np, L.kp, N, static_cast<int>(L.mp / tcc::BM),
+                          static_cast<int>(L.np / tcc::BN), err, tc_test_abort()};
+        const int smem = tcc::STAGES * tcc::STAGE_BYTES + 1024;
+        e = cudaFuncSetAttribute(crt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        const int tiles = a.tiles_m * a.tiles_n;
+        const int grid = tiles < num_sms() ? tiles : num_sms();
+        crt_tc_kernel<<<grid, 192, smem, s>>>(ma, mb, a);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         return crt_recover<P>(g, N, beta, L, sig, tau, rq, s);
@@ -3341,6 +3094,30 @@ static cudaError_t crt_recover(const GemmArgs<P>& g, int N, int beta, const Ozak
         if (++M1[k]) break;
     for (int k = 0; k < crt::kRecLimbs; ++k)
         ra_.H[k] = (M1[k] >> 1) | (k + 1 < crt::kRecLimbs ? (M1[k + 1] << 31) : 0u);
+    // W_i = (M / m_i) c_i with c_i the inverse of (M / m_i) mod m_i
+    for (int i = 0; i < N; ++i) {
+        const uint64_t mi = static_cast<uint64_t>(crt::kHost.m[i]);
+        uint32_t Q[crt::kRecLimbs];
+        uint64_t rem = 0;
+        for (int k = crt::kRecLimbs - 1; k >= 0; --k) {      // Q = M / m_i (exact)
+            const uint64_t cur = (rem << 32) | ra_.M[k];
+            Q[k] = static_cast<uint32_t>(cur / mi);
+            rem = cur % mi;
+        }
+        uint64_t qm = 0;                                      // Q mod m_i
+        for (int k = crt::kRecLimbs - 1; k >= 0; --k) qm = ((qm << 32) | Q[k]) % mi;
+        uint64_t c = 0;
+        for (uint64_t x = 1; x < mi; ++x)
+            if ((qm * x) % mi == 1) { c = x; break; }
+        if (mi == 1) c = 0;
+        uint64_t carry = 0;
+        for (int k = 0; k < crt::kRecLimbs; ++k) {
+            const uint64_t v = static_cast<uint64_t>(Q[k]) * c + carry;
+            ra_.W[i][k] = static_cast<uint32_t>(v);
+            carry = v >> 32;
+        }
+        ra_.f[i] = static_cast<float>(static_cast<double>(c) / static_cast<double>(mi));
+    }
     const int64_t outs = g.m * g.n;
     const unsigned grid = blocks_for(outs, 256);
     switch ((N + 7) / 8) {
@@ -3355,8 +3132,8 @@ static cudaError_t crt_recover(const GemmArgs<P>& g, int N, int beta, const Ozak
     return cudaGetLastError();
 }
 
-template cudaError_t launch_crt<2>(const GemmArgs<2>&, int, void*, cudaStream_t, int, int);
-template cudaError_t launch_crt<3>(const GemmArgs<3>&, int, void*, cudaStream_t, int, int);
-template cudaError_t launch_crt<4>(const GemmArgs<4>&, int, void*, cudaStream_t, int, int);
+template cudaError_t launch_crt<2>(const GemmArgs<2>&, int, void*, cudaStream_t, int);
+template cudaError_t launch_crt<3>(const GemmArgs<3>&, int, void*, cudaStream_t, int);
+template cudaError_t launch_crt<4>(const GemmArgs<4>&, int, void*, cudaStream_t, int);
 
 }  // namespace mpg

@@ -42,13 +42,12 @@ cudaError_t launch_ozaki(const GemmArgs<P>& g, int S, void* ws, cudaStream_t s, 
 constexpr int kCrtMaxModuli = 49;
 inline int64_t crt_k_limit() { return (2147483647LL) / (128 * 128); }
 // engine 0: int8 residues (mma.sync); engine 1: bf16 residues after a 256-byte
-// header (tcgen05; rows of op(A) padded to 256 for the CTA pairs).
+// header (tcgen05).
 OzakiLayout crt_layout(int N, int64_t m, int64_t n, int64_t k, int engine = 0);
 // The largest beta with k 2^(2 beta - 1) < m_0 ... m_(N-1); -1 for a bad N.
 int crt_beta(int N, int64_t k);
-// engine 1, variant 1: one CTA per 128 x 128 tile; otherwise CTA pairs on 256 x 128 tiles.
 template <int P>
-cudaError_t launch_crt(const GemmArgs<P>& g, int N, void* ws, cudaStream_t s, int engine = 0, int variant = 0);
+cudaError_t launch_crt(const GemmArgs<P>& g, int N, void* ws, cudaStream_t s, int engine = 0);
 
 // Size of the library's fixed scratch array and its device address on the
 // current device (looked up on first use per device).

@@ -293,7 +293,7 @@ def test_crt_form_host_checks(L):
     for (m, n, k, N) in ((100, 70, 300, 28), (4096, 4096, 4096, 26), (1, 1, 1, 49)):
         for algo, head, eb in ((4, 0, 1), (5, 256, 2)):           # int8; tcgen05: header, bf16 residues
             o = Opts(0, 0, algo, 0, N, 0, None, 0)
-            mp = r(m) if algo == 4 else r256(m)                     # tcgen05: 256-row tiles of CTA pairs
+            mp = r(m)
             want = (head + r256(N * mp * r(k) * eb) + r256(N * r(n) * r(k) * eb) + r256(4 * mp) +
                     r256(4 * r(n)) + r256(N * mp * r(n)))
             assert L.mpgemm_workspace_size(2, ctypes.byref(o), m, n, k) == want, (algo, m, n, k, N)
