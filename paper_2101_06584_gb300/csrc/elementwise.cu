@@ -51,19 +51,20 @@ __global__ void __launch_bounds__(256) vec_kernel(const VecArgs<P> a)
     }
 }
 
-// DD add / mul with two adjacent elements per thread and iteration: the four
-// operand planes are read as double2 (16-byte loads, 512 contiguous bytes per
-// warp and plane) and both elements' loads are issued before either result is
-// stored, so each thread keeps twice the bytes in flight.  A DD operation is
-// only 9-11 FP64 operations per 48 bytes, the least work per byte of all the
-// elementwise operations, and one element per thread leaves the FP64 pipe
-// waiting on memory.  Requires 16-byte aligned planes (checked by the host);
-// an odd last element is done by one thread with scalar loads.
+// DD add / mul with four adjacent elements per thread and iteration: each of
+// the four operand planes is read as two double2 (16-byte loads, 32 bytes per
+// thread, 1 KB contiguous per warp and plane) and all four elements' loads
+// are issued before any result is stored, so each thread keeps four times the
+// bytes in flight.  A DD operation is only 9-11 FP64 operations per 48 bytes,
+// the least work per byte of all the elementwise operations, and one element
+// per thread leaves the FP64 pipe waiting on memory.  Requires 16-byte aligned
+// planes (checked by the host); the last n mod 4 elements are done by one
+// thread with scalar loads.
 template <int OP>
-__global__ void __launch_bounds__(256) vec_dd_x2_kernel(const VecArgs<2> a)
+__global__ void __launch_bounds__(256) vec_dd_x4_kernel(const VecArgs<2> a)
 {
     const mp::Rn f = mp::make_rn();
-    const int64_t pairs = a.n >> 1;
+    const int64_t quads = a.n >> 2;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     const double2* x0 = reinterpret_cast<const double2*>(a.x[0]);
     const double2* x1 = reinterpret_cast<const double2*>(a.x[1]);
@@ -71,27 +72,42 @@ __global__ void __launch_bounds__(256) vec_dd_x2_kernel(const VecArgs<2> a)
     const double2* y1 = reinterpret_cast<const double2*>(a.y[1]);
     double2* r0 = reinterpret_cast<double2*>(a.r[0]);
     double2* r1 = reinterpret_cast<double2*>(a.r[1]);
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < pairs; i += stride) {
-        const double2 u0 = x0[i], u1 = x1[i], v0 = y0[i], v1 = y1[i];
-        double xa[2] = {u0.x, u1.x}, ya[2] = {v0.x, v1.x}, ra[2];
-        double xb[2] = {u0.y, u1.y}, yb[2] = {v0.y, v1.y}, rb[2];
-        if constexpr (OP == 0) {
-            mp::dd_add(f, xa, ya, ra);
-            mp::dd_add(f, xb, yb, rb);
-        } else {
-            mp::dd_mul(f, xa, ya, ra);
-            mp::dd_mul(f, xb, yb, rb);
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < quads; i += stride) {
+        double2 u0[2], u1[2], v0[2], v1[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            u0[h] = x0[2 * i + h];
+            u1[h] = x1[2 * i + h];
+            v0[h] = y0[2 * i + h];
+            v1[h] = y1[2 * i + h];
         }
-        r0[i] = make_double2(ra[0], rb[0]);
-        r1[i] = make_double2(ra[1], rb[1]);
+        double o0[4], o1[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int h = e >> 1;
+            const bool hi = e & 1;
+            double x[2] = {hi ? u0[h].y : u0[h].x, hi ? u1[h].y : u1[h].x};
+            double y[2] = {hi ? v0[h].y : v0[h].x, hi ? v1[h].y : v1[h].x};
+            double r[2];
+            if constexpr (OP == 0) mp::dd_add(f, x, y, r);
+            else mp::dd_mul(f, x, y, r);
+            o0[e] = r[0];
+            o1[e] = r[1];
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            r0[2 * i + h] = make_double2(o0[2 * h], o0[2 * h + 1]);
+            r1[2 * i + h] = make_double2(o1[2 * h], o1[2 * h + 1]);
+        }
     }
-    if ((a.n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
-        const int64_t t = a.n - 1;
-        double x[2] = {a.x[0][t], a.x[1][t]}, y[2] = {a.y[0][t], a.y[1][t]}, r[2];
-        if constexpr (OP == 0) mp::dd_add(f, x, y, r);
-        else mp::dd_mul(f, x, y, r);
-        a.r[0][t] = r[0];
-        a.r[1][t] = r[1];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int64_t t = quads * 4; t < a.n; ++t) {
+            double x[2] = {a.x[0][t], a.x[1][t]}, y[2] = {a.y[0][t], a.y[1][t]}, r[2];
+            if constexpr (OP == 0) mp::dd_add(f, x, y, r);
+            else mp::dd_mul(f, x, y, r);
+            a.r[0][t] = r[0];
+            a.r[1][t] = r[1];
+        }
     }
 }
 
@@ -139,9 +155,9 @@ cudaError_t launch_vec(int op, int64_t n, const double* const* x, const double* 
             aligned = aligned && (reinterpret_cast<uintptr_t>(x[c]) | reinterpret_cast<uintptr_t>(y[c]) |
                                   reinterpret_cast<uintptr_t>(r[c])) % 16 == 0;
         if (aligned && (op == 0 || op == 1)) {
-            const unsigned grid2 = grid_for(n / 2 > 0 ? n / 2 : 1);
-            if (op == 0) vec_dd_x2_kernel<0><<<grid2, 256, 0, s>>>(a);
-            else vec_dd_x2_kernel<1><<<grid2, 256, 0, s>>>(a);
+            const unsigned grid4 = grid_for(n / 4 > 0 ? n / 4 : 1);
+            if (op == 0) vec_dd_x4_kernel<0><<<grid4, 256, 0, s>>>(a);
+            else vec_dd_x4_kernel<1><<<grid4, 256, 0, s>>>(a);
             return cudaGetLastError();
         }
     }

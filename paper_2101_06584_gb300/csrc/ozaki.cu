@@ -1206,31 +1206,14 @@ __device__ __forceinline__ double rn_component(uint32_t (&u)[L], bool& neg, int 
 // is estimated in binary32 (off by at most one: the sum is below 2^14 and its
 // rounding error far below one) and corrected by one addition or subtraction
 // of M.
-template <int P, int NB>
-__global__ void __launch_bounds__(256) crt_recover_kernel(const __grid_constant__ CrtRecArgs g)
+// The integer X in [0, M) from the column sums S (limbs of 64 bits, S < 2^14 M)
+// and the quotient estimate qf; then centred and rounded to the P components
+// of output (row, col).
+template <int P, int L>
+__device__ __forceinline__ void crt_finish(const CrtRecArgs& g, const uint64_t (&S)[L + 1], float qf, int64_t row,
+                                           int64_t col)
 {
-    constexpr int L = NB / 4 < crt::kRecLimbs ? NB / 4 : crt::kRecLimbs;
-    const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (t >= g.m * g.n) return;
-    const int64_t row = t / g.n, col = t % g.n;
-    const int N = g.N;
-    uint64_t S[L + 1];
-#pragma unroll
-    for (int k = 0; k <= L; ++k) S[k] = 0ull;
-    float qf = 0.0f;
-#pragma unroll
-    for (int i = 0; i < NB; ++i) {
-        if (i < N) {
-            const int mi = crt::kDev.m[i];
-            int r = g.res[(static_cast<int64_t>(i) * g.mp + row) * g.np + col];
-            if (r < 0) r += mi;
-            const uint32_t ru = static_cast<uint32_t>(r);
-#pragma unroll
-            for (int k = 0; k < L; ++k) S[k] += static_cast<uint64_t>(g.W[i][k]) * ru;
-            qf = __fmaf_rn(static_cast<float>(r), g.f[i], qf);
-        }
-    }
-    // carries: S as L + 1 32-bit limbs (S < 2^14 M)
+    // carries: S as L + 1 32-bit limbs
     uint32_t X[L + 1];
     uint64_t carry = 0;
 #pragma unroll
@@ -1306,6 +1289,54 @@ __global__ void __launch_bounds__(256) crt_recover_kernel(const __grid_constant_
 #pragma unroll
     for (int c = 0; c < P; ++c) g.C[c][row * g.ldc + col] = rn_component<L>(Y, neg, e);
 }
+
+// NB: the moduli count rounded up to a multiple of 8 (the loops below are
+// unrolled NB times and skip moduli i >= N); L = NB / 4 limbs (at most 11)
+// hold the product of NB moduli <= 256.  The integer in [0, M) congruent to
+// the residues is sum_i r_i W_i - q M with q = floor(sum_i r_i c_i / m_i):
+// the sum is accumulated exactly in 64-bit columns (each term below 2^40), q
+// is estimated in binary32 (off by at most one: the sum is below 2^14 and its
+// rounding error far below one) and corrected by one addition or subtraction
+// of M.  Each thread takes four consecutive outputs of a row (one 4-byte load
+// per modulus; the residue rows are padded to a multiple of 128).
+template <int P, int NB>
+__global__ void __launch_bounds__(256) crt_recover_kernel(const __grid_constant__ CrtRecArgs g)
+{
+    constexpr int L = NB / 4 < crt::kRecLimbs ? NB / 4 : crt::kRecLimbs;
+    const int64_t quads = (g.n + 3) / 4;
+    const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= g.m * quads) return;
+    const int64_t row = t / quads, col0 = (t % quads) * 4;
+    const int N = g.N;
+    uint64_t S[4][L + 1];
+    float qf[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        qf[u] = 0.0f;
+#pragma unroll
+        for (int k = 0; k <= L; ++k) S[u][k] = 0ull;
+    }
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        if (i < N) {
+            const int mi = crt::kDev.m[i];
+            const char4 r4 = *reinterpret_cast<const char4*>(g.res + (static_cast<int64_t>(i) * g.mp + row) * g.np + col0);
+            const int rr[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int r = rr[u] < 0 ? rr[u] + mi : rr[u];
+                const uint32_t ru = static_cast<uint32_t>(r);
+#pragma unroll
+                for (int k = 0; k < L; ++k) S[u][k] += static_cast<uint64_t>(g.W[i][k]) * ru;
+                qf[u] = __fmaf_rn(static_cast<float>(r), g.f[i], qf[u]);
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (col0 + u < g.n) crt_finish<P, L>(g, S[u], qf[u], row, col0 + u);
+}
+
 
 // ------------------------------------------------------- tcgen05 engine
 //
@@ -3118,7 +3149,7 @@ static cudaError_t crt_recover(const GemmArgs<P>& g, int N, int beta, const Ozak
         }
         ra_.f[i] = static_cast<float>(static_cast<double>(c) / static_cast<double>(mi));
     }
-    const int64_t outs = g.m * g.n;
+    const int64_t outs = g.m * ((g.n + 3) / 4);        // four outputs per thread
     const unsigned grid = blocks_for(outs, 256);
     switch ((N + 7) / 8) {
     case 1: crt_recover_kernel<P, 8><<<grid, 256, 0, s>>>(ra_); break;

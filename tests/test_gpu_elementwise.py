@@ -122,12 +122,12 @@ def test_empty_vector(torch):
 
 
 @pytest.mark.parametrize("op", ["add", "mul"])
-@pytest.mark.parametrize("n", [1, 2, 3, 64, 1_000_003, 1_000_004])
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 6, 7, 64, 1_000_003, 1_000_004, 1_000_006])
 def test_dd_paired_path(torch, op, n):
-    """DD add and mul on 16-byte aligned planes take the two-elements-per-
-    thread kernel (double2 loads; an odd last element on its own), also in
-    place and with unaligned planes (the one-element kernel): bit-identical
-    to the oracle in every case."""
+    """DD add and mul on 16-byte aligned planes take the four-elements-per-
+    thread kernel (double2 loads; the last n mod 4 elements on their own),
+    also in place and with unaligned planes (the one-element kernel):
+    bit-identical to the oracle in every case."""
     from paper_2101_06584_gb300 import mpgemm
     rng = np.random.default_rng(250 + n % 97)
     x = I.random_mp(2, n, rng, spread=30)
