@@ -786,6 +786,49 @@ struct Cursor {
     }
 };
 
+// Iteration of the CTA-pair engine: the groups of G weights from the least
+// significant (S+1, ..., S+2-G, then the next G, ...), and inside a group
+// the slice s of op(A) outermost: for s = 1, 2, ..., every weight w of the
+// group with w > s, largest first, then the k tiles of the pair (s, w - s).
+// Consecutive pairs share their A slice, which then stays in L2, while each
+// pair still fills its own accumulator segments; the integer group sums do
+// not depend on the order in which their weights' products arrive.
+struct GroupCursor {
+    int wtop, wbot;     // the current group's weights
+    int s, w, kt;
+    __device__ __forceinline__ void begin(int S, int G, int top)
+    {
+        wtop = top;
+        wbot = top - G + 1 > 2 ? top - G + 1 : 2;
+        s = 1;
+        w = top;
+        kt = 0;
+        (void)S;
+    }
+    // the next stage; pair_end / group_end describe the stage just passed
+    __device__ __forceinline__ void advance(int S, int G, int KT, bool& pair_end, bool& group_end)
+    {
+        pair_end = false;
+        group_end = false;
+        if (++kt < KT) return;
+        kt = 0;
+        pair_end = true;
+        const int wlow = wbot > s + 1 ? wbot : s + 1;
+        if (w - 1 >= wlow) {
+            --w;
+            return;
+        }
+        const int smax = wtop - 1 < S ? wtop - 1 : S;
+        if (s + 1 <= smax) {
+            ++s;
+            w = wtop;
+            return;
+        }
+        group_end = true;
+        if (wbot > 2) begin(S, G, wbot - 1);
+    }
+};
+
 // CTA of WM x WN warps; each warp owns MT x NT fragments of 16 x 8 outputs,
 // so the CTA tile is (WM*MT*16) x (WN*NT*8).  Slice tiles of KS bytes of k
 // are staged through a STG-deep cp.async pipeline.  P output components;
@@ -2323,7 +2366,8 @@ ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
             for (int tile = cid; tile < ntiles && ok; tile += ncl) {
                 const int ma = (tile % g.tiles_m) * 2 * tc2::BM + static_cast<int>(rank) * tc2::BM;
                 const int nb = (tile / g.tiles_m) * BN + static_cast<int>(rank) * (BN / 2);
-                Cursor c{S + 1, 1, 0};
+                GroupCursor c;
+                c.begin(S, kGroup, S + 1);
                 for (int i = 0; i < per_tile; ++i, ++it) {
                     const uint32_t st = it % tc2::STAGES, ph = (it / tc2::STAGES) & 1u;
                     if (!mbar_wait_cl<kHintIdle>(&empty[st], ph ^ 1u, abortp)) { fail(1); ok = false; break; }
@@ -2336,7 +2380,8 @@ ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                         tma_load_3d_pair(sa + q * tc2::A_BOX, &tmA, x, ma, c.s - 1, bar);
                         tma_load_3d_pair(sa + tc2::KB * tc2::A_BOX + q * tc2::B_BOX, &tmB, x, nb, c.w - c.s - 1, bar);
                     }
-                    c.advance(S, KT);
+                    bool pe, ge;
+                    c.advance(S, kGroup, KT, pe, ge);
                 }
             }
             // every stage's last release has arrived (the leader's MMAs have
@@ -2356,7 +2401,8 @@ ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
             int pend = -1;          // accumulator whose commit waits for the next stage
             bool ok = true;
             for (int tile = cid; tile < ntiles && ok; tile += ncl) {
-                Cursor c{S + 1, 1, 0};
+                GroupCursor c;
+                c.begin(S, kGroup, S + 1);
                 int seg_stages = 0;
                 uint32_t b = 0;
                 for (int i = 0; i < per_tile; ++i, ++it) {
@@ -2383,9 +2429,9 @@ ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                     }
                     umma_commit_both(&empty[st]);
                     ++seg_stages;
-                    const int w = c.w;
-                    c.advance(S, KT);
-                    if (c.w != w || seg_stages == tc2::SEG_STAGES) {
+                    bool pair_end, group_end;
+                    c.advance(S, kGroup, KT, pair_end, group_end);
+                    if (pair_end || seg_stages == tc2::SEG_STAGES) {
                         pend = static_cast<int>(b);
                         ++seg;
                         seg_stages = 0;
@@ -2425,15 +2471,16 @@ ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
 #pragma unroll
             for (int c0 = 0; c0 < GW * BN; c0 += 32) tmem_st32(grp + c0, zero32);
             tmem_wait_st();
-            Cursor c{S + 1, 1, 0};
+            GroupCursor c;
+            c.begin(S, kGroup, S + 1);
             int seg_stages = 0;
             bool first_group = true;
             for (int i = 0; i < per_tile; ++i) {
                 ++seg_stages;
                 const int w = c.w;
-                c.advance(S, KT);
-                const bool weight_end = c.w != w;
-                if (!weight_end && seg_stages != tc2::SEG_STAGES) continue;
+                bool pair_end, group_end;
+                c.advance(S, kGroup, KT, pair_end, group_end);
+                if (!pair_end && seg_stages != tc2::SEG_STAGES) continue;
                 seg_stages = 0;
                 const uint32_t b = seg & 1u;
                 // the decision must be warp-uniform: the TMEM loads below are .sync.aligned
@@ -2467,7 +2514,7 @@ ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                 __syncwarp();
                 if (lane == 0) mbar_arrive_cluster(b ? lead_acce1 : lead_acce0);
                 ++seg;
-                if (!(weight_end && (j == kGroup - 1 || w == 2))) continue;
+                if (!group_end) continue;
                 // end of a group: the first of a tile goes to C as it is
                 // (DDadd((0, 0), y) is y exactly: an exact split with no
                 // negative zero); a later one is handed to this quadrant's
