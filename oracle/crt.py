@@ -33,6 +33,19 @@ definition in Python integers:
 The result is deterministic; its error against the exact product comes from
 rounding the scaled entries to integers (about 2^-beta relative to the row
 and column scales) and from the final rounding to P components.
+
+Split integers (halves = 2), for more bits than the moduli's product allows
+one integer product to carry:
+  bits     w = the largest integer with k 2^(2w) < M; beta = 2w.
+  split    A' = A1 2^w + A0 with A0 = the representative of A' mod 2^w in
+           [-2^(w-1), 2^(w-1)) and A1 = (A' - A0) / 2^w (|A1| <= 2^(w-1));
+           B' likewise.
+  products Q_hh,i = r(A1) r(B1)^T, Q_mid,i = r(A1) r(B0)^T + r(A0) r(B1)^T,
+           Q_ll,i = r(A0) r(B0)^T (|Q| <= 2k 2^14 < 2^31 for k < 2^16).
+  recover  P_hh, P_mid, P_ll in [-M/2, M/2) from their residues (each is
+           below k 2^(2w-1) < M/2 in magnitude).
+  output   C' = P_hh 2^(2w) + P_mid 2^w + P_ll (= A'B' exactly), rounded as
+           above.
 """
 import math
 from fractions import Fraction
@@ -54,22 +67,37 @@ MODULI = _coprime_moduli()
 RES_BITS = 14            # |r(a) r(b)| <= 128 * 128 = 2^14
 
 
-def k_limit():
-    """Largest k whose residue products sum exactly in int32."""
-    return (2 ** 31 - 1) // (1 << RES_BITS)
+def k_limit(halves=1):
+    """Largest k whose residue products (two of them summed for the middle
+    product of split integers) sum exactly in int32."""
+    return (2 ** 31 - 1) // (halves * (1 << RES_BITS))
 
 
 def modulus_product(N):
     return math.prod(MODULI[:N])
 
 
-def beta_bits(N, k):
-    """The largest beta with k 2^(2 beta - 1) < M (0 if none)."""
+def beta_bits(N, k, halves=1):
+    """The largest beta with k 2^(2 beta - 1) < M (0 if none); with split
+    integers beta = 2w for the largest w with k 2^(2w) < M."""
     M = modulus_product(N)
+    if halves == 2:
+        w = 0
+        while max(k, 1) * 2 ** (2 * (w + 1)) < M:
+            w += 1
+        return 2 * w
     b = 0
     while max(k, 1) * 2 ** (2 * (b + 1) - 1) < M:
         b += 1
     return b
+
+
+def split(x, w):
+    """(x1, x0) with x = x1 2^w + x0, x0 in [-2^(w-1), 2^(w-1))."""
+    x0 = x % (1 << w)
+    if x0 >= 1 << (w - 1):
+        x0 -= 1 << w
+    return (x - x0) >> w, x0
 
 
 def sym_mod(x, m):
@@ -145,10 +173,52 @@ def residues(planes, N, beta):
                          dtype=np.int64).reshape(N, len(rows), np.asarray(planes).shape[2])
 
 
-def gemm(A, B, N, rows=None, cols=None):
+def _res(vals, N):
+    """int64 array [N][len(vals)][k] of the residues of a list of integer rows."""
+    return np.array([[[sym_mod(a, MODULI[i]) for a in row] for row in vals] for i in range(N)],
+                    dtype=np.int64).reshape(N, len(vals), len(vals[0]) if vals else 0)
+
+
+def gemm2(A, B, N, rows=None, cols=None):
+    """C = A B through the CRT form with split integers (halves = 2).  As gemm;
+    returns C, sigma, tau and beta = 2w."""
+    A = np.asarray(A)
+    B = np.asarray(B)
+    P = A.shape[0]
+    k = A.shape[2]
+    rows = list(range(A.shape[1])) if rows is None else list(rows)
+    cols = list(range(B.shape[2])) if cols is None else list(cols)
+    beta = beta_bits(N, k, halves=2)
+    w = beta // 2
+    assert w >= 1, "too few moduli for this k"
+    sig, Ai = integer_rows(A[:, rows, :], beta)
+    tau, Bi = integer_rows(np.ascontiguousarray(B[:, :, cols].transpose(0, 2, 1)), beta)
+    A1 = [[split(a, w)[0] for a in row] for row in Ai]
+    A0 = [[split(a, w)[1] for a in row] for row in Ai]
+    B1 = [[split(b, w)[0] for b in row] for row in Bi]
+    B0 = [[split(b, w)[1] for b in row] for row in Bi]
+    RA1, RA0, RB1, RB0 = _res(A1, N), _res(A0, N), _res(B1, N), _res(B0, N)
+    Qhh = np.einsum("irk,ick->irc", RA1, RB1)
+    Qmid = np.einsum("irk,ick->irc", RA1, RB0) + np.einsum("irk,ick->irc", RA0, RB1)
+    Qll = np.einsum("irk,ick->irc", RA0, RB0)
+    C = np.zeros((P, len(rows), len(cols)))
+    for r in range(len(rows)):
+        for c in range(len(cols)):
+            hh, mid, ll = (crt_recover([int(Q[i, r, c]) % MODULI[i] for i in range(N)], N)
+                           for Q in (Qhh, Qmid, Qll))
+            Cp = (hh << (2 * w)) + (mid << w) + ll
+            v = Fraction(Cp) * Fraction(2) ** (sig[r] + tau[c] - 2 * beta)
+            C[:, r, c] = nearest_expansion(v, P)
+    return C, sig, tau, beta
+
+
+def gemm(A, B, N, rows=None, cols=None, halves=1):
     """C = A B through the CRT form with N moduli, for the selected rows of A
     and columns of B (all by default).  A (P, m, k), B (P, k, n).  Returns
-    C (P, len(rows), len(cols)), sigma, tau and beta."""
+    C (P, len(rows), len(cols)), sigma, tau and beta.  halves = 2: split
+    integers (gemm2)."""
+    if halves == 2:
+        return gemm2(A, B, N, rows, cols)
     A = np.asarray(A)
     B = np.asarray(B)
     P = A.shape[0]

@@ -162,7 +162,9 @@ MUTANTS = {
         lambda res, N: sum(res[i] * (m.modulus_product(N) // m.MODULI[i]) *
                            pow(m.modulus_product(N) // m.MODULI[i], -1, m.MODULI[i])
                            for i in range(N)) % m.modulus_product(N)),
-    "one bit too many": lambda m: setattr(m, "beta_bits", (lambda f: lambda N, k: f(N, k) + 1)(m.beta_bits)),
+    "one bit too many": lambda m: setattr(m, "beta_bits",
+                                          (lambda f: lambda N, k, halves=1: f(N, k, halves) + 1)(m.beta_bits)),
+    "low half not balanced": lambda m: setattr(m, "split", lambda x, w: (x >> w, x % (1 << w))),
 }
 
 
@@ -172,14 +174,15 @@ def test_planted_mistakes_are_caught(monkeypatch, name):
     import importlib
     import sys
     mod = importlib.import_module("oracle.crt")
-    saved = {k: getattr(mod, k) for k in ("sym_mod", "scaled_integer", "crt_recover", "beta_bits")}
+    saved = {k: getattr(mod, k) for k in ("sym_mod", "scaled_integer", "crt_recover", "beta_bits", "split")}
     try:
         MUTANTS[name](mod)
         caught = False
         for pin, args in ((test_recovery_inverts_residues, ()), (test_beta_is_the_largest_safe_bit_count, ()),
                           (test_residue_route_equals_the_direct_product, ("dd", 26)),
                           (test_error_within_the_scaling_bound, ("dd", 28)), (test_small_integers_are_exact, ()),
-                          (test_integers_round_to_nearest_even, ())):
+                          (test_integers_round_to_nearest_even, ()), (test_split_integers, ()),
+                          (test_split_route_equals_the_direct_product, ("qd", 28))):
             try:
                 pin(*args)
             except (AssertionError, ValueError, OverflowError):
@@ -190,3 +193,44 @@ def test_planted_mistakes_are_caught(monkeypatch, name):
         for k, v in saved.items():
             setattr(mod, k, v)
         assert sys.modules["oracle.crt"] is mod
+
+
+def test_split_integers():
+    """x = x1 2^w + x0 with x0 in [-2^(w-1), 2^(w-1)), for random and boundary
+    values; and w is the largest with k 2^(2w) < M."""
+    rng = np.random.default_rng(46)
+    for w in (1, 7, 64, 101):
+        for x in [0, 1, -1, (1 << (2 * w - 1)), -(1 << (2 * w - 1)), (1 << (w - 1)), -(1 << (w - 1))] + \
+                 [int(rng.integers(-2 ** 62, 2 ** 62)) << int(rng.integers(0, 2 * w)) for _ in range(100)]:
+            x1, x0 = R.split(x, w)
+            assert x1 * (1 << w) + x0 == x and -(1 << (w - 1)) <= x0 < (1 << (w - 1)), (x, w)
+            if abs(x) <= 1 << (2 * w - 1):
+                assert abs(x1) <= 1 << (w - 1)
+    for N in (8, 26, 28, 40):
+        for k in (1, 1024, 4096, 65535):
+            b = R.beta_bits(N, k, halves=2)
+            assert b % 2 == 0 and k * 2 ** b < R.modulus_product(N) <= k * 2 ** (b + 2)
+
+
+@pytest.mark.parametrize("prec,N", [("dd", 12), ("qd", 28), ("td", 20)])
+def test_split_route_equals_the_direct_product(prec, N):
+    """The split-integer route (three products recovered by CRT, combined)
+    equals the nearest expansion of A'B' computed from the integers directly,
+    with beta = 2w; and stays within the scaling bound of the exact product."""
+    P = I.P_OF[prec]
+    rng = np.random.default_rng(47 + N)
+    A, B = I.ill_scaled(P, (4, 33), rng), I.uniform(P, (33, 5), rng)
+    C, sig, tau, beta = R.gemm(A, B, N, halves=2)
+    assert beta == R.beta_bits(N, 33, halves=2)
+    sigd, Ai = R.integer_rows(A, beta)
+    taud, Bi = R.integer_rows(np.ascontiguousarray(B.transpose(0, 2, 1)), beta)
+    ex = X.ExactRows(A, B)
+    for i in range(4):
+        for j in range(5):
+            Cp = sum(x * y for x, y in zip(Ai[i], Bi[j]))
+            want = R.nearest_expansion(Fraction(Cp) * Fraction(2) ** (sigd[i] + taud[j] - 2 * beta), P)
+            assert list(C[:, i, j]) == want, (i, j)
+            c = ex.dot(i, j)
+            bound = 33 * Fraction(2) ** (sig[i] + tau[j] - beta - 1) * (1 + Fraction(1, 2 ** 50)) + \
+                Fraction(1, 2 ** (53 * P - 2)) * abs(c)
+            assert abs(X.value(C[:, i, j]) - c) <= bound, (i, j)
