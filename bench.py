@@ -109,7 +109,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="td_qd",
-                    choices=["td_qd", "dd_small", "dd_int8", "dd_tc", "dd_crt", "dd_crt_int8", "td_crt",
+                    choices=["td_qd", "dd_small", "dd_int8", "dd_tc", "dd_crt", "dd_crt_int8", "td_crt", "qd_crt",
                              "td_qd_int8", "td_qd_tc",
                              "batched", "autograd", "elementwise", "strassen", "autograd_tc"])
     ap.add_argument("--size", type=int, default=None, help="override the workload's m = n = k")
@@ -737,16 +737,18 @@ class TdQdInt8(Workload):
     """The TD and QD GEMMs of td_qd through the slicing form (engine "int8" or "tc")."""
     name = "td_qd_int8"
 
-    ALGO = {"int8": "int8", "tc": "bf16", "crt_tc": "crt_bf16"}
+    ALGO = {"int8": "int8", "tc": "bf16", "crt_tc": "crt_bf16", "crt2_tc": "crt2_bf16"}
     # first count tried (the library's defaults) and the largest, per precision
     START = {"td": (22, 40), "qd": (29, 40)}
     START_CRT = {"td": (44, 49)}
+    START_CRT2 = {"qd": (30, 44)}
 
     def __init__(self, torch, mm, I, rank, n=1024, engine="int8", S=None):
         self.torch, self.mm, self.n, self.engine = torch, mm, n, engine
         self.algo = self.ALGO[engine]
         self.crt = self.algo.startswith("crt")
-        self.precs = ("td",) if self.crt else ("td", "qd")
+        self.split = self.algo.startswith("crt2")
+        self.precs = ("qd",) if self.split else ("td",) if self.crt else ("td", "qd")
         rng = replica_rng(1, rank)
         self.dev, self.host, self.search = {}, {}, {}
         for prec in ("td", "qd"):                 # drawn in this order whichever precisions run
@@ -757,7 +759,7 @@ class TdQdInt8(Workload):
             self.host[prec] = (A, B)
             self.dev[prec] = [torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(),
                               torch.empty((P, n, n), dtype=torch.float64, device="cuda"), None]
-        starts = self.START_CRT if self.crt else self.START
+        starts = self.START_CRT2 if self.split else self.START_CRT if self.crt else self.START
         if S is None and not _ACC["enabled"]:
             S = {p: starts[p][0] if self.crt else FIXED_SLICES[p] for p in self.precs}
         if S is None:
@@ -772,7 +774,15 @@ class TdQdInt8(Workload):
                                             dtype=torch.uint8, device="cuda")
         self.mads = len(self.precs) * n ** 3
         eng = "mma.sync s8 engine" if engine == "int8" else "tcgen05 engine"
-        if self.crt:
+        if self.split:
+            self.launches_per_step = 7
+            self.config = {"workload": "QD GEMM, m=n=k=%d, CRT form with split integers (N = %d moduli, beta = %d "
+                                       "bits, 3N products), %s, inputs of the main workload"
+                                       % (n, self.S["qd"], mm.crt_beta(self.S["qd"], n, split=True), eng),
+                           "m": n, "n": n, "k": n, "slices": self.S, "engine": engine,
+                           "slices_rule": "smallest N meeting n 2^-200 on the sampled entries"
+                           if self.search else "given"}
+        elif self.crt:
             self.launches_per_step = 7
             self.config = {"workload": "TD GEMM, m=n=k=%d, CRT form (N = %d moduli, beta = %d bits), %s, "
                                        "inputs of the main workload" % (n, self.S["td"], mm.crt_beta(self.S["td"], n),
@@ -834,7 +844,9 @@ class TdQdInt8(Workload):
         n = self.n
         dom = self.precs[-1]
         S = self.S[dom]
-        pairs = S if self.crt else S * (S + 1) // 2
+        # residue products per multiply-add: N, or 4N with split integers
+        # (hh, the two halves of mid, ll)
+        pairs = 4 * S if self.split else S if self.crt else S * (S + 1) // 2
         ms = statistics.mean(launch_ms[dom])
         ach = 2.0 * pairs * n ** 3 / (ms * 1e-3)
         plain = {}
@@ -849,7 +861,8 @@ class TdQdInt8(Workload):
         # multiply-add) per output per group of ten weights (S weights; the
         # first group of a tile needs none on the tcgen05 engine)
         fp64_ops = 0 if self.crt else (n * n) * (-(-S // 10)) * FP64_OPS_PER_MAD["qd"] * 87 // 210
-        kern = ("TD CRT form (crt_tc_kernel) incl. residues and recovery" if self.crt
+        kern = ("QD CRT form with split integers (crt_tc_kernel) incl. residues and recovery" if self.split
+                else "TD CRT form (crt_tc_kernel) incl. residues and recovery" if self.crt
                 else "QD slicing form (%s) incl. slicing" % self.engine)
         return {"bound": "tensor", "kernel": kern,
                 "achieved": ach / 1e12, "peak": peak / 1e12, "unit": unit, "peak_source": src,
@@ -879,11 +892,20 @@ class TdQdTc(TdQdInt8):
 
 class TdCrt(TdQdInt8):
     """The TD GEMM of the main workload through the CRT form on tcgen05 (QD
-    needs more bits than 49 moduli of at most 256 give)."""
+    needs more bits than 49 moduli of at most 256 give one integer product)."""
     name = "td_crt"
 
     def __init__(self, torch, mm, I, rank, n=1024):
         super().__init__(torch, mm, I, rank, n=n, engine="crt_tc")
+
+
+class QdCrt(TdQdInt8):
+    """The QD GEMM of the main workload through the CRT form with split
+    integers on tcgen05."""
+    name = "qd_crt"
+
+    def __init__(self, torch, mm, I, rank, n=1024):
+        super().__init__(torch, mm, I, rank, n=n, engine="crt2_tc")
 
 
 class Elementwise(Workload):
@@ -1126,7 +1148,7 @@ class AutogradTc(Autograd):
 
 
 WORKLOADS = {"td_qd": TdQd, "dd_small": DdSmall, "dd_int8": DdInt8, "dd_tc": DdTc, "dd_crt": DdCrt,
-             "dd_crt_int8": DdCrtInt8, "td_crt": TdCrt,
+             "dd_crt_int8": DdCrtInt8, "td_crt": TdCrt, "qd_crt": QdCrt,
              "td_qd_int8": TdQdInt8, "td_qd_tc": TdQdTc, "batched": Batched, "autograd": Autograd,
              "elementwise": Elementwise, "strassen": Strassen, "autograd_tc": AutogradTc}
 
@@ -1274,7 +1296,7 @@ def extras(torch, mm, I, pk, flush):
     """One short measurement of each other workload (rank 0, after the main one)."""
     out = {}
     for name in ("dd_small", "dd_int8", "dd_tc", "dd_crt", "dd_crt_int8", "td_qd_int8", "td_qd_tc", "td_crt",
-                 "batched", "autograd", "autograd_tc", "elementwise", "strassen"):
+                 "qd_crt", "batched", "autograd", "autograd_tc", "elementwise", "strassen"):
         w = WORKLOADS[name](torch, mm, I, 0)
         steps = {"dd_small": 10, "elementwise": 10, "strassen": 1}.get(name, 2)
         total_ms, launch_ms, _, _ = measure(torch, w, steps, 1, 1, 0, flush, sample_clocks=False)

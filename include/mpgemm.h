@@ -60,7 +60,8 @@ void *mpgemm_get_stream(void);
  * mpgemm_default_tile and mpgemm_tc_status to 100; 102 adds mpgemm_d and
  * P = 1 in mpgemm_ex, mpgemm_num_tiles, mpgemm_tile_info and
  * mpgemm_default_tile; 103 adds MPG_ALGO_INT8_CRT, MPG_ALGO_BF16_CRT and
- * mpgemm_crt_beta. */
+ * mpgemm_crt_beta; 104 adds MPG_ALGO_INT8_CRT_SPLIT, MPG_ALGO_BF16_CRT_SPLIT
+ * and mpgemm_crt_split_beta. */
 int mpgemm_version(void);
 
 /* ---------------------------------------------------------------------
@@ -180,7 +181,9 @@ typedef enum mpg_algo {
     MPG_ALGO_INT8_OZAKI = 2, /* DD/TD/QD: error-free INT8 slicing on the tensor cores */
     MPG_ALGO_BF16_SLICES = 3, /* DD/TD/QD: the same digits as bf16 on tcgen05 (TMEM accumulators) */
     MPG_ALGO_INT8_CRT = 4,    /* DD/TD/QD: residues modulo small coprime moduli on the tensor cores */
-    MPG_ALGO_BF16_CRT = 5     /* DD/TD/QD: the same residues as bf16 on tcgen05 (TMEM accumulators) */
+    MPG_ALGO_BF16_CRT = 5,    /* DD/TD/QD: the same residues as bf16 on tcgen05 (TMEM accumulators) */
+    MPG_ALGO_INT8_CRT_SPLIT = 6, /* the CRT form with split integers (about twice the bits), mma.sync */
+    MPG_ALGO_BF16_CRT_SPLIT = 7  /* the same on tcgen05 */
 } mpg_algo;
 
 /* Options of mpgemm_ex.  Zero-initialised options give the plain call. */
@@ -304,6 +307,30 @@ int mpgemm_ex(int P, const mpgemm_opts *opts, int64_t m, int64_t n, int64_t k,
  * form applies, 0 when the moduli's product is too small); MPG_EINVAL for N
  * outside 1..49 or k < 0. */
 int mpgemm_crt_beta(int moduli, int64_t k);
+
+/* MPG_ALGO_INT8_CRT_SPLIT (not in the paper): the CRT form with each scaled
+ * integer split in two, for about twice the bits that one integer product
+ * of the same moduli can carry.  With N = opts->slices moduli (default 16 for
+ * DD, 22 for TD, 30 for QD; 1..49):
+ *   bits    beta = mpgemm_crt_split_beta(N, k) = 2w for the largest w with
+ *           k 2^(2w) < M; MPG_EUNSUPPORTED when there is none or beta > 316.
+ *   integers A', B' as for MPG_ALGO_INT8_CRT with this beta.
+ *   split   A' = A1 2^w + A0 with A0 the representative of A' mod 2^w in
+ *           [-2^(w-1), 2^(w-1)) and A1 = (A' - A0) / 2^w; B' likewise.
+ *   products per modulus m_i, exact in int32 (k <= 65535, else
+ *           MPG_EUNSUPPORTED): hh = r(A1) r(B1)^T, mid = r(A1) r(B0)^T +
+ *           r(A0) r(B1)^T, ll = r(A0) r(B0)^T.
+ *   recover P_hh, P_mid, P_ll = the integers in [-M/2, M/2) congruent to
+ *           them (each is below k 2^(2w-1) < M/2 in magnitude), and
+ *           C' = P_hh 2^(2w) + P_mid 2^w + P_ll = A'B' exactly.
+ *   output  as for MPG_ALGO_INT8_CRT, with 2 beta = 4w.
+ * 3N products of the residues instead of N, for twice the bits: with 30
+ * moduli beta is about 210, enough for QD.  Workspace as for
+ * MPG_ALGO_INT8_CRT with [2N] residue planes per operand (A1's residues for
+ * m_0..m_(N-1), then A0's) and [3N] product planes (hh, mid, ll).
+ * MPG_ALGO_BF16_CRT_SPLIT: the same on tcgen05 as MPG_ALGO_BF16_CRT (the
+ * two middle sub-products add into one exact int32 sum), bit-identical. */
+int mpgemm_crt_split_beta(int moduli, int64_t k);
 
 /* After an MPG_ALGO_BF16_SLICES call with this workspace: synchronises the
  * calling thread's stream and returns the code in the workspace header.  0

@@ -204,23 +204,38 @@ static int ozaki_call(const GemmArgs<P>& g, const mpgemm_opts* o)
     return e == cudaSuccess ? MPG_OK : cuda_fail(e, "slicing gemm launch");
 }
 
-static int crt_default_moduli(int P) { return P == 2 ? 28 : P == 3 ? 44 : kCrtMaxModuli; }
+static bool is_crt(int algo)
+{
+    return algo == MPG_ALGO_INT8_CRT || algo == MPG_ALGO_BF16_CRT || algo == MPG_ALGO_INT8_CRT_SPLIT ||
+           algo == MPG_ALGO_BF16_CRT_SPLIT;
+}
+static int crt_engine(int algo) { return algo == MPG_ALGO_BF16_CRT || algo == MPG_ALGO_BF16_CRT_SPLIT ? 1 : 0; }
+static int crt_halves(int algo) { return algo == MPG_ALGO_INT8_CRT_SPLIT || algo == MPG_ALGO_BF16_CRT_SPLIT ? 2 : 1; }
+static int crt_default_moduli(int P, int halves)
+{
+    if (halves == 2) return P == 2 ? 16 : P == 3 ? 22 : 30;
+    return P == 2 ? 28 : P == 3 ? 44 : kCrtMaxModuli;
+}
 
 template <int P>
 static int crt_call(const GemmArgs<P>& g, const mpgemm_opts* o)
 {
-    const int N = o->slices ? o->slices : crt_default_moduli(P);
+    const int halves = crt_halves(o->algo);
+    const int N = o->slices ? o->slices : crt_default_moduli(P, halves);
     if (N < 1 || N > kCrtMaxModuli)
         return fail(MPG_EINVAL, "the CRT form takes 1..%d moduli (got %d)", kCrtMaxModuli, N);
-    if (g.k > crt_k_limit())
+    if (g.k > crt_k_limit(halves))
         return fail(MPG_EUNSUPPORTED, "k = %lld exceeds %lld, the largest k whose residue products sum "
-                    "exactly in int32", (long long)g.k, (long long)crt_k_limit());
-    const int beta = crt_beta(N, g.k);
+                    "exactly in int32", (long long)g.k, (long long)crt_k_limit(halves));
+    const int beta = crt_beta(N, g.k, halves);
     if (beta < 1)
-        return fail(MPG_EUNSUPPORTED, "%d moduli leave no bits for k = %lld (their product must exceed 2k)", N,
-                    (long long)g.k);
-    const int engine = o->algo == MPG_ALGO_BF16_CRT ? 1 : 0;
-    const OzakiLayout L = crt_layout(N, g.m, g.n, g.k, engine);
+        return fail(MPG_EUNSUPPORTED, "%d moduli leave no bits for k = %lld (their product must exceed %s)", N,
+                    (long long)g.k, halves == 2 ? "4k" : "2k");
+    if (beta > crt_max_beta(halves))
+        return fail(MPG_EUNSUPPORTED, "%d moduli give %d bits at k = %lld, more than the %d the form keeps", N,
+                    beta, (long long)g.k, crt_max_beta(halves));
+    const int engine = crt_engine(o->algo);
+    const OzakiLayout L = crt_layout(N, g.m, g.n, g.k, engine, halves);
     if (L.mp / 128 > 65535) return fail(MPG_EINVAL, "m too large for the CRT form's grid");
     if (!o->workspace) return fail(MPG_EWORKSPACE, "the CRT form needs a workspace of %lld bytes",
                                    (long long)L.total);
@@ -238,7 +253,7 @@ static int crt_call(const GemmArgs<P>& g, const mpgemm_opts* o)
             overlap(rw, plane_range(g.C[c], g.m, g.n, g.ldc)))
             return fail(MPG_EWORKSPACE, "workspace overlaps an operand");
     }
-    cudaError_t e = launch_crt<P>(g, N, o->workspace, g_stream, engine);
+    cudaError_t e = launch_crt<P>(g, N, o->workspace, g_stream, engine, halves);
     return e == cudaSuccess ? MPG_OK : cuda_fail(e, "CRT gemm launch");
 }
 
@@ -263,9 +278,9 @@ static int gemm_call(const mpgemm_opts* o, int64_t m, int64_t n, int64_t k,
     if (m == 0 || n == 0) return MPG_OK;
     const int algo = o ? o->algo : MPG_ALGO_AUTO;
     if (algo != MPG_ALGO_AUTO && algo != MPG_ALGO_FP64_EFT && algo != MPG_ALGO_INT8_OZAKI &&
-        algo != MPG_ALGO_BF16_SLICES && algo != MPG_ALGO_INT8_CRT && algo != MPG_ALGO_BF16_CRT)
+        algo != MPG_ALGO_BF16_SLICES && !is_crt(algo))
         return fail(MPG_EINVAL, "unknown algorithm %d", algo);
-    const bool crt = algo == MPG_ALGO_INT8_CRT || algo == MPG_ALGO_BF16_CRT;
+    const bool crt = is_crt(algo);
     const bool sliced = algo == MPG_ALGO_INT8_OZAKI || algo == MPG_ALGO_BF16_SLICES || crt;
     const int split = o ? o->split_k : 0;
     const int levels = o ? o->strassen : 0;
@@ -341,7 +356,7 @@ int mpgemm_set_stream(void* stream)
 
 void* mpgemm_get_stream(void) { return static_cast<void*>(g_stream); }
 
-int mpgemm_version(void) { return 103; }
+int mpgemm_version(void) { return 104; }
 
 int mp_quick_two_sum(int64_t n, const double* a, const double* b, double* s, double* e)
 { return eft_call(0, n, a, b, s, e); }
@@ -409,10 +424,11 @@ size_t mpgemm_workspace_size(int P, const mpgemm_opts* opts, int64_t m, int64_t 
     if ((opts->algo == MPG_ALGO_AUTO || opts->algo == MPG_ALGO_FP64_EFT) && opts->strassen > 0 &&
         opts->strassen <= kMaxStrassenLevels)
         return static_cast<size_t>(strassen_workspace_elems(P, m, n, k, opts->strassen) * 8);
-    if (opts->algo == MPG_ALGO_INT8_CRT || opts->algo == MPG_ALGO_BF16_CRT) {
-        const int N = opts->slices ? opts->slices : crt_default_moduli(P);
+    if (is_crt(opts->algo)) {
+        const int halves = crt_halves(opts->algo);
+        const int N = opts->slices ? opts->slices : crt_default_moduli(P, halves);
         if (N < 1 || N > kCrtMaxModuli) return 0;
-        return static_cast<size_t>(crt_layout(N, m, n, k, opts->algo == MPG_ALGO_BF16_CRT ? 1 : 0).total);
+        return static_cast<size_t>(crt_layout(N, m, n, k, crt_engine(opts->algo), halves).total);
     }
     if (opts->algo != MPG_ALGO_INT8_OZAKI && opts->algo != MPG_ALGO_BF16_SLICES) return 0;
     const int S = opts->slices ? opts->slices : ozaki_default_slices(P);
@@ -469,6 +485,15 @@ int mpgemm_crt_beta(int moduli, int64_t k)
         return fail(MPG_EINVAL, "moduli must be in 1..%d and k >= 0 (got %d, %lld)", kCrtMaxModuli, moduli,
                     (long long)k);
     return crt_beta(moduli, k);
+}
+
+int mpgemm_crt_split_beta(int moduli, int64_t k)
+{
+    clear_error();
+    if (moduli < 1 || moduli > kCrtMaxModuli || k < 0)
+        return fail(MPG_EINVAL, "moduli must be in 1..%d and k >= 0 (got %d, %lld)", kCrtMaxModuli, moduli,
+                    (long long)k);
+    return crt_beta(moduli, k, 2);
 }
 
 int mpgemm_num_tiles(int P)

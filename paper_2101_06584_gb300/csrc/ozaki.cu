@@ -358,9 +358,10 @@ struct ResidueCursor {
 
 // A' of the P components: each floored at 2^(sigma - beta - 64), summed
 // exactly in 384 bits, rounded to the nearest integer (ties to even) in units
-// of 2^(sigma - beta).
-template <int NL, int P>
-__device__ __forceinline__ ResidueCursor<NL> residue_cursor(const double (&c)[P], int sigma, int beta)
+// of 2^(sigma - beta); in two's complement, five 64-bit words, least
+// significant first (beta <= 316).
+template <int P>
+__device__ __forceinline__ void scaled_integer(const double (&c)[P], int sigma, int beta, uint64_t (&I)[kWideWords - 1])
 {
     Wide W;
 #pragma unroll
@@ -379,7 +380,6 @@ __device__ __forceinline__ ResidueCursor<NL> residue_cursor(const double (&c)[P]
     // integer part (words 1..5, floor) and the fraction in word 0
     const uint64_t f = W.w[0];
     const bool up = f > (1ull << 63) || (f == (1ull << 63) && (W.w[1] & 1ull));
-    uint64_t I[kWideWords - 1];
 #pragma unroll
     for (int i = 0; i < kWideWords - 1; ++i) I[i] = W.w[i + 1];
     uint64_t carry = up ? 1ull : 0ull;
@@ -389,6 +389,13 @@ __device__ __forceinline__ ResidueCursor<NL> residue_cursor(const double (&c)[P]
         carry = (carry && s == 0) ? 1ull : 0ull;
         I[i] = s;
     }
+}
+
+// The residue cursor of a two's-complement integer: its sign and magnitude
+// in NL 16-bit limbs.
+template <int NL>
+__device__ __forceinline__ ResidueCursor<NL> cursor_of(uint64_t (&I)[kWideWords - 1])
+{
     ResidueCursor<NL> cur;
     cur.neg = (I[kWideWords - 2] >> 63) != 0;
     if (cur.neg) {                                   // magnitude: two's complement negation
@@ -402,6 +409,71 @@ __device__ __forceinline__ ResidueCursor<NL> residue_cursor(const double (&c)[P]
     }
 #pragma unroll
     for (int j = 0; j < NL; ++j) cur.limb[j] = static_cast<uint32_t>(I[j / 4] >> (16 * (j % 4))) & 0xffffu;
+    cur.idx = 0;
+    return cur;
+}
+
+template <int NL, int P>
+__device__ __forceinline__ ResidueCursor<NL> residue_cursor(const double (&c)[P], int sigma, int beta)
+{
+    uint64_t I[kWideWords - 1];
+    scaled_integer<P>(c, sigma, beta, I);
+    return cursor_of<NL>(I);
+}
+
+// Word q of a five-word two's-complement integer, its sign beyond the top.
+__device__ __forceinline__ uint64_t word_at(const uint64_t (&x)[kWideWords - 1], int q)
+{
+    uint64_t r = (x[kWideWords - 2] >> 63) ? ~0ull : 0ull;
+#pragma unroll
+    for (int k = 0; k < kWideWords - 1; ++k) r = (k == q) ? x[k] : r;
+    return r;
+}
+
+// Split integers: residues of A1 for moduli 0..N-1, then of A0, where
+// A' = A1 2^w + A0 with A0 in [-2^(w-1), 2^(w-1)).
+template <int NL>
+struct SplitResidueCursor {
+    ResidueCursor<NL> hi, lo;
+    int n, idx;
+    __device__ __forceinline__ int next() { return idx++ < n ? hi.next() : lo.next(); }
+};
+
+template <int NL, int P>
+__device__ __forceinline__ SplitResidueCursor<NL> split_residue_cursor(const double (&c)[P], int sigma, int beta,
+                                                                       int n)
+{
+    constexpr int WW = kWideWords - 1;
+    uint64_t I[WW];
+    scaled_integer<P>(c, sigma, beta, I);
+    const int w = beta / 2;
+    // A0: the low w bits, sign-extended from bit w - 1
+    const int wi = w >> 6, wb = w & 63;
+    const bool low_neg = (word_at(I, (w - 1) >> 6) >> ((w - 1) & 63)) & 1ull;
+    uint64_t A0[WW], D[WW];
+#pragma unroll
+    for (int k = 0; k < WW; ++k) {
+        const uint64_t keep = k < wi ? ~0ull : (k == wi ? (wb ? ((1ull << wb) - 1) : 0ull) : 0ull);
+        A0[k] = (I[k] & keep) | (low_neg ? ~keep : 0ull);
+    }
+    // A1 = (A' - A0) >> w, exact
+    uint64_t borrow = 0;
+#pragma unroll
+    for (int k = 0; k < WW; ++k) {
+        const uint64_t d = I[k] - A0[k] - borrow;
+        borrow = (I[k] < A0[k] || (I[k] == A0[k] && borrow)) ? 1ull : 0ull;
+        D[k] = d;
+    }
+    uint64_t A1[WW];
+#pragma unroll
+    for (int k = 0; k < WW; ++k) {
+        const uint64_t a = word_at(D, k + wi), b = word_at(D, k + wi + 1);
+        A1[k] = wb ? (a >> wb) | (b << (64 - wb)) : a;
+    }
+    SplitResidueCursor<NL> cur;
+    cur.hi = cursor_of<NL>(A1);
+    cur.lo = cursor_of<NL>(A0);
+    cur.n = n;
     cur.idx = 0;
     return cur;
 }
@@ -535,12 +607,19 @@ __device__ __forceinline__ typename CursorOf<P>::T zero_cursor()
 
 // KIND 0: the slicing form's digits (S of them); KIND 1: the CRT form's
 // residues (S moduli, beta bits per scaled entry).
-// KIND 1, 2, 3: residues with 12, 8 or 4 limbs (beta up to 192, 128, 64 bits).
+// KIND 1, 2, 3: residues with 12, 8 or 4 limbs (beta up to 192, 128, 64 bits);
+// KIND 4, 5: split integers (2N planes: A1's residues, then A0's) with 8 or
+// 12 limbs per half (w = beta / 2 up to 128 or 192 bits).
 template <int P, int KIND> struct KindCursor { using T = typename CursorOf<P>::T; };
 template <int P> struct KindCursor<P, 1> { using T = ResidueCursor<12>; };
 template <int P> struct KindCursor<P, 2> { using T = ResidueCursor<8>; };
 template <int P> struct KindCursor<P, 3> { using T = ResidueCursor<4>; };
-constexpr int residue_kind(int beta) { return beta <= 64 ? 3 : beta <= 128 ? 2 : 1; }
+template <int P> struct KindCursor<P, 4> { using T = SplitResidueCursor<8>; };
+template <int P> struct KindCursor<P, 5> { using T = SplitResidueCursor<12>; };
+constexpr int residue_kind(int beta, int halves = 1)
+{
+    return halves == 2 ? (beta / 2 <= 128 ? 4 : 5) : (beta <= 64 ? 3 : beta <= 128 ? 2 : 1);
+}
 
 template <int P, int KIND>
 __device__ __forceinline__ typename KindCursor<P, KIND>::T make_cursor(const Planes<P>& pl, int64_t off, bool valid,
@@ -548,11 +627,16 @@ __device__ __forceinline__ typename KindCursor<P, KIND>::T make_cursor(const Pla
 {
     if constexpr (KIND == 0) {
         return valid ? element_cursor<P>(pl, off, sigma, S) : zero_cursor<P>();
-    } else {
+    } else if constexpr (KIND <= 3) {
         double c[P];
 #pragma unroll
         for (int i = 0; i < P; ++i) c[i] = valid ? pl.c[i][off] : 0.0;
         return residue_cursor<KIND == 1 ? 12 : KIND == 2 ? 8 : 4, P>(c, sigma, beta);
+    } else {
+        double c[P];
+#pragma unroll
+        for (int i = 0; i < P; ++i) c[i] = valid ? pl.c[i][off] : 0.0;
+        return split_residue_cursor<KIND == 4 ? 8 : 12, P>(c, sigma, beta, S / 2);
     }
 }
 
@@ -993,15 +1077,26 @@ __global__ void __launch_bounds__(WM * WN * 32, MINB) ozaki_gemm_kernel(const Oz
 //
 // One modulus per grid z: Q_i = R_A,i R_B,i^T on mma.sync m16n8k32 s8 (exact
 // int32: |Q_i| <= k 2^14 < 2^31), reduced to its symmetric residue mod m_i
-// and stored as int8 [N][mp][np].  CTA of WM x WN warps, MT x NT fragments
+// and stored as int8 [N][mp][np].  With split integers three products per
+// modulus (grid z = 3N): hh = R(A1) R(B1)^T, mid = R(A1) R(B0)^T +
+// R(A0) R(B1)^T (two k loops into one accumulator, |mid| <= 2k 2^14 < 2^31),
+// ll = R(A0) R(B0)^T.  CTA of WM x WN warps, MT x NT fragments
 // of 16 x 8 per warp, KS bytes of k per cp.async stage (STG stages).
 
 struct CrtGemmArgs {
-    const int8_t* ra;       // [N][mp][kp] residues of op(A)
-    const int8_t* rb;       // [N][np][kp] residues of op(B)^T
-    int8_t* out;            // [N][mp][np] residues of the products
+    const int8_t* ra;       // [N][mp][kp] residues of op(A) ([2N]: A1's, then A0's, with split integers)
+    const int8_t* rb;       // [N][np][kp] residues of op(B)^T (likewise)
+    int8_t* out;            // [N][mp][np] residues of the products ([3N]: hh, mid, ll)
     int64_t mp, np, kp;
+    int N, split;
 };
+
+// Split integers: the operand planes of sub-product s of modulus i (s = 0:
+// A1 B1, 1: A1 B0, 2: A0 B1, 3: A0 B0) and the product each one adds to
+// (0: hh, 1: mid, 2: ll).
+__host__ __device__ constexpr int split_plane_a(int s, int i, int N) { return s < 2 ? i : N + i; }
+__host__ __device__ constexpr int split_plane_b(int s, int i, int N) { return (s & 1) ? N + i : i; }
+__host__ __device__ constexpr int split_output(int s) { return s == 0 ? 0 : (s == 3 ? 2 : 1); }
 
 template <int MT, int NT, int WM, int WN, int STG, int KS>
 __global__ void __launch_bounds__(WM * WN * 32) crt_gemm_kernel(const CrtGemmArgs g)
@@ -1021,10 +1116,17 @@ __global__ void __launch_bounds__(WM * WN * 32) crt_gemm_kernel(const CrtGemmArg
     const int wm = warp / WN, wn = warp % WN;
     const int64_t m0 = static_cast<int64_t>(blockIdx.y) * BM;
     const int64_t n0 = static_cast<int64_t>(blockIdx.x) * BN;
-    const int mi = blockIdx.z;
-    const int KT = static_cast<int>(g.kp / KS);
-    const int8_t* a = g.ra + (static_cast<int64_t>(mi) * g.mp + m0) * g.kp;
-    const int8_t* b = g.rb + (static_cast<int64_t>(mi) * g.np + n0) * g.kp;
+    // plane z of the output: modulus z (or, with split integers, product
+    // z / N of modulus z % N, the middle one summing two sub-products)
+    const int z = blockIdx.z;
+    const int mi = g.split ? z % g.N : z;
+    const int o = g.split ? z / g.N : 0;
+    const int s0 = o == 0 ? 0 : (o == 1 ? 1 : 3);
+    const int nsub = o == 1 ? 2 : 1;
+    const int KT1 = static_cast<int>(g.kp / KS);
+    const int KT = nsub * KT1;
+    auto plane_a = [&](int sub) { return g.split ? split_plane_a(s0 + sub, mi, g.N) : mi; };
+    auto plane_b = [&](int sub) { return g.split ? split_plane_b(s0 + sub, mi, g.N) : mi; };
 
     int ci[MT][NT][4];
 #pragma unroll
@@ -1035,14 +1137,18 @@ __global__ void __launch_bounds__(WM * WN * 32) crt_gemm_kernel(const CrtGemmArg
             for (int r = 0; r < 4; ++r) ci[mt][nt][r] = 0;
 
     auto load = [&](int stage, int kt) {
+        const int sub = kt >= KT1 ? 1 : 0;
+        const int kk = kt - sub * KT1;
+        const int8_t* a = g.ra + (static_cast<int64_t>(plane_a(sub)) * g.mp + m0) * g.kp;
+        const int8_t* b = g.rb + (static_cast<int64_t>(plane_b(sub)) * g.np + n0) * g.kp;
         for (int chunk = tid; chunk < (BM + BN) * CPR; chunk += NTHR) {
             const int row = chunk / CPR, col = (chunk % CPR) * 16;
             if (row < BM)
                 cp_async16(As + stage * BM * SROW + row * SROW + col,
-                           a + static_cast<int64_t>(row) * g.kp + static_cast<int64_t>(kt) * KS + col);
+                           a + static_cast<int64_t>(row) * g.kp + static_cast<int64_t>(kk) * KS + col);
             else
                 cp_async16(Bs + stage * BN * SROW + (row - BM) * SROW + col,
-                           b + static_cast<int64_t>(row - BM) * g.kp + static_cast<int64_t>(kt) * KS + col);
+                           b + static_cast<int64_t>(row - BM) * g.kp + static_cast<int64_t>(kk) * KS + col);
         }
     };
 #pragma unroll
@@ -1103,7 +1209,7 @@ __global__ void __launch_bounds__(WM * WN * 32) crt_gemm_kernel(const CrtGemmArg
                 char2 pk;
                 pk.x = rr[0];
                 pk.y = rr[1];
-                *reinterpret_cast<char2*>(g.out + (static_cast<int64_t>(mi) * g.mp + row) * g.np + col) = pk;
+                *reinterpret_cast<char2*>(g.out + (static_cast<int64_t>(z) * g.mp + row) * g.np + col) = pk;
             }
 }
 
@@ -1122,12 +1228,13 @@ constexpr int kRecLimbs = 11;                     // M < 2^352
 }
 
 struct CrtRecArgs {
-    const int8_t* res;      // [N][mp][np] residues of the products
+    const int8_t* res;      // [N][mp][np] residues of the products ([3N]: hh, mid, ll with split integers)
     const int* sig;
     const int* tau;
     double* C[4];
     int64_t ldc, m, n, mp, np;
     int N, beta;
+    int w;                  // split integers: C' = P_hh 2^(2w) + P_mid 2^w + P_ll
     uint32_t M[crt::kRecLimbs];          // the product of the moduli
     uint32_t H[crt::kRecLimbs];          // ceil(M / 2)
     // the CRT weights W_i = (M / m_i) c_i, c_i = (M / m_i)^-1 mod m_i, so that
@@ -1241,20 +1348,13 @@ __device__ __forceinline__ double rn_component(uint32_t (&u)[L], bool& neg, int 
     return __longlong_as_double(static_cast<long long>(sign | bits));
 }
 
-// NB: the moduli count rounded up to a multiple of 8 (the loops below are
-// unrolled NB times and skip moduli i >= N); L = NB / 4 limbs (at most 11)
-// hold the product of NB moduli <= 256.  The integer in [0, M) congruent to
-// the residues is sum_i r_i W_i - q M with q = floor(sum_i r_i c_i / m_i):
-// the sum is accumulated exactly in 64-bit columns (each term below 2^40), q
-// is estimated in binary32 (off by at most one: the sum is below 2^14 and its
-// rounding error far below one) and corrected by one addition or subtraction
-// of M.
 // The integer X in [0, M) from the column sums S (limbs of 64 bits, S < 2^14 M)
-// and the quotient estimate qf; then centred and rounded to the P components
-// of output (row, col).
-template <int P, int L>
-__device__ __forceinline__ void crt_finish(const CrtRecArgs& g, const uint64_t (&S)[L + 1], float qf, int64_t row,
-                                           int64_t col)
+// and the quotient estimate qf (see the recovery kernel below), centred to
+// [-M/2, M/2) as magnitude Y and sign; crt_finish rounds it to the P
+// components of output (row, col).
+template <int L>
+__device__ __forceinline__ void crt_centre(const CrtRecArgs& g, const uint64_t (&S)[L + 1], float qf,
+                                           uint32_t (&Y)[L], bool& neg)
 {
     // carries: S as L + 1 32-bit limbs
     uint32_t X[L + 1];
@@ -1305,7 +1405,6 @@ __device__ __forceinline__ void crt_finish(const CrtRecArgs& g, const uint64_t (
             }
         }
     }
-    uint32_t Y[L];
 #pragma unroll
     for (int k = 0; k < L; ++k) Y[k] = X[k];
     // Y >= ceil(M/2): the value is Y - M < 0, magnitude M - Y
@@ -1317,7 +1416,7 @@ __device__ __forceinline__ void crt_finish(const CrtRecArgs& g, const uint64_t (
             decided = true;
         }
     }
-    bool neg = false;
+    neg = false;
     if (ge) {
         uint64_t bw = 0;
 #pragma unroll
@@ -1328,6 +1427,15 @@ __device__ __forceinline__ void crt_finish(const CrtRecArgs& g, const uint64_t (
         }
         neg = true;
     }
+}
+
+template <int P, int L>
+__device__ __forceinline__ void crt_finish(const CrtRecArgs& g, const uint64_t (&S)[L + 1], float qf, int64_t row,
+                                           int64_t col)
+{
+    uint32_t Y[L];
+    bool neg;
+    crt_centre<L>(g, S, qf, Y, neg);
     const int e = g.sig[row] + g.tau[col] - 2 * g.beta;
 #pragma unroll
     for (int c = 0; c < P; ++c) g.C[c][row * g.ldc + col] = rn_component<L>(Y, neg, e);
@@ -1378,6 +1486,99 @@ __global__ void __launch_bounds__(256) crt_recover_kernel(const __grid_constant_
 #pragma unroll
     for (int u = 0; u < 4; ++u)
         if (col0 + u < g.n) crt_finish<P, L>(g, S[u], qf[u], row, col0 + u);
+}
+
+// Z += (-1)^neg Y 2^shift in two's complement (LC limbs; the sum stays in range).
+template <int L, int LC>
+__device__ __forceinline__ void add_shifted(uint32_t (&Z)[LC], const uint32_t (&Y)[L], bool neg, int shift)
+{
+    const int sw = shift >> 5, sb = shift & 31;
+    uint64_t carry = neg ? 1ull : 0ull;                 // -T = ~T + 1
+#pragma unroll
+    for (int k = 0; k < LC; ++k) {
+        const uint32_t hi = limb_at<L>(Y, k - sw);
+        const uint32_t lo = sb ? limb_at<L>(Y, k - sw - 1) >> (32 - sb) : 0u;
+        uint32_t t = (hi << sb) | lo;
+        if (neg) t = ~t;
+        const uint64_t v = static_cast<uint64_t>(Z[k]) + t + carry;
+        Z[k] = static_cast<uint32_t>(v);
+        carry = v >> 32;
+    }
+}
+
+// Split integers: the three products hh, mid, ll of each output recovered as
+// above (each in [-M/2, M/2)), combined exactly as C' = P_hh 2^(2w) +
+// P_mid 2^w + P_ll in LC = 2L + 1 32-bit limbs (|C'| < M 2^(2w) <= 2^(64L)),
+// and rounded to P components.  Two outputs per thread.
+template <int P, int NB>
+__global__ void __launch_bounds__(256) crt_recover2_kernel(const __grid_constant__ CrtRecArgs g)
+{
+    constexpr int L = NB / 4 < crt::kRecLimbs ? NB / 4 : crt::kRecLimbs;
+    constexpr int LC = 2 * L + 1;
+    const int64_t pairs = (g.n + 1) / 2;
+    const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= g.m * pairs) return;
+    const int64_t row = t / pairs, col0 = (t % pairs) * 2;
+    const int N = g.N;
+    uint32_t Z[2][LC];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int k = 0; k < LC; ++k) Z[u][k] = 0u;
+#pragma unroll 1
+    for (int part = 0; part < 3; ++part) {
+        uint64_t S[2][L + 1];
+        float qf[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            qf[u] = 0.0f;
+#pragma unroll
+            for (int k = 0; k <= L; ++k) S[u][k] = 0ull;
+        }
+        const int8_t* res = g.res + static_cast<int64_t>(part) * N * g.mp * g.np;
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            if (i < N) {
+                const int mi = crt::kDev.m[i];
+                const char2 r2 = *reinterpret_cast<const char2*>(res + (static_cast<int64_t>(i) * g.mp + row) * g.np + col0);
+                const int rr[2] = {r2.x, r2.y};
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int r = rr[u] < 0 ? rr[u] + mi : rr[u];
+                    const uint32_t ru = static_cast<uint32_t>(r);
+#pragma unroll
+                    for (int k = 0; k < L; ++k) S[u][k] += static_cast<uint64_t>(g.W[i][k]) * ru;
+                    qf[u] = __fmaf_rn(static_cast<float>(r), g.f[i], qf[u]);
+                }
+            }
+        }
+        const int shift = (2 - part) * g.w;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            uint32_t Y[L];
+            bool neg;
+            crt_centre<L>(g, S[u], qf[u], Y, neg);
+            add_shifted<L, LC>(Z[u], Y, neg, shift);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int64_t col = col0 + u;
+        if (col >= g.n) continue;
+        bool neg = (Z[u][LC - 1] >> 31) != 0;
+        if (neg) {                                      // magnitude
+            uint64_t c = 1;
+#pragma unroll
+            for (int k = 0; k < LC; ++k) {
+                const uint64_t v = static_cast<uint64_t>(~Z[u][k]) + c;
+                Z[u][k] = static_cast<uint32_t>(v);
+                c = v >> 32;
+            }
+        }
+        const int e = g.sig[row] + g.tau[col] - 2 * g.beta;
+#pragma unroll
+        for (int c = 0; c < P; ++c) g.C[c][row * g.ldc + col] = rn_component<LC>(Z[u], neg, e);
+    }
 }
 
 
@@ -1907,8 +2108,10 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 // drained after at most 1024 values of k (8 stages) while every partial sum
 // is an integer below 2^24, exact in fp32; the drains add it to an exact
 // int32 sum per output kept in tensor memory, and at the end of a modulus the
-// sum's symmetric residue is stored as int8.  Warp roles, barriers, bounded
-// waits and the abort protocol are those of the slicing engine.
+// sum's symmetric residue is stored as int8.  With split integers each
+// modulus runs four sub-products (A1 B1, A1 B0, A0 B1, A0 B0); the two middle
+// ones add into one sum.  Warp roles, barriers, bounded waits and the abort
+// protocol are those of the slicing engine.
 
 namespace tcc {
 constexpr int BM = 128;
@@ -1927,11 +2130,12 @@ constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((static_cast<ui
 }  // namespace tcc
 
 struct CrtTcArgs {
-    int8_t* out;            // [N][mp][np] residues of the products
+    int8_t* out;            // [N][mp][np] residues of the products ([3N] with split integers)
     int64_t mp, np, kp;
     int N, tiles_m, tiles_n;
     int* err;
     int test_abort;
+    int split;              // 1: split integers, four sub-products per modulus
 };
 
 __global__ void __launch_bounds__(192, 1)
@@ -1968,7 +2172,8 @@ crt_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     tc_fence_after();
     const uint32_t tmem = tmem_base;
     const int KT = static_cast<int>(g.kp / (tcc::KE * tcc::KB));
-    const int per_tile = g.N * KT;
+    const int NSUB = g.split ? 4 : 1;                    // sub-products per modulus
+    const int per_tile = g.N * NSUB * KT;
     const int ntiles = g.tiles_m * g.tiles_n;
     auto fail = [&](int code) {
         *abortp = 1;
@@ -1988,7 +2193,9 @@ crt_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
                 const int m0 = (tile % g.tiles_m) * tcc::BM, n0 = (tile / g.tiles_m) * tcc::BN;
                 for (int i = 0; i < per_tile; ++i, ++it) {
-                    const int mi = i / KT, kt = i % KT;
+                    const int mi = i / (NSUB * KT), sub = (i / KT) % NSUB, kt = i % KT;
+                    const int pa = g.split ? split_plane_a(sub, mi, g.N) : mi;
+                    const int pb = g.split ? split_plane_b(sub, mi, g.N) : mi;
                     const uint32_t st = it % tcc::STAGES, ph = (it / tcc::STAGES) & 1u;
                     if (!mbar_wait<kHintIdle>(&empty[st], ph ^ 1u, abortp)) { fail(1); ok = false; break; }
                     uint8_t* sa = stage0 + st * tcc::STAGE_BYTES;
@@ -1996,8 +2203,8 @@ crt_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 #pragma unroll
                     for (int q = 0; q < tcc::KB; ++q) {
                         const int x = (kt * tcc::KB + q) * tcc::KE;
-                        tma_load_3d(sa + q * tcc::BOX, &tmA, x, m0, mi, &full[st]);
-                        tma_load_3d(sa + (tcc::KB + q) * tcc::BOX, &tmB, x, n0, mi, &full[st]);
+                        tma_load_3d(sa + q * tcc::BOX, &tmA, x, m0, pa, &full[st]);
+                        tma_load_3d(sa + (tcc::KB + q) * tcc::BOX, &tmB, x, n0, pb, &full[st]);
                     }
                 }
             }
@@ -2064,9 +2271,9 @@ crt_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
             const int m0 = (tile % g.tiles_m) * tcc::BM, n0 = (tile / g.tiles_m) * tcc::BN;
             int seg_stages = 0;
-            bool first = true;                            // first segment of a modulus
+            bool first = true;                            // first segment of an output product
             for (int i = 0; i < per_tile; ++i) {
-                const int mi = i / KT, kt = i % KT;
+                const int mi = i / (NSUB * KT), sub = (i / KT) % NSUB, kt = i % KT;
                 ++seg_stages;
                 if (!seg_end(kt, seg_stages)) continue;
                 seg_stages = 0;
@@ -2077,7 +2284,9 @@ crt_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     break;
                 }
                 tc_fence_after();
-                const bool last = kt == KT - 1;
+                // the middle product of split integers continues over two sub-products
+                const bool last = kt == KT - 1 && !(g.split && sub == 1);
+                const int plane = g.split ? split_output(sub) * g.N + mi : mi;
                 const int m = crt::kDev.m[mi];
                 for (int c0 = 0; c0 < tcc::BN; c0 += 32) {
                     uint32_t fv[32], sv[32];
@@ -2105,7 +2314,7 @@ crt_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                             rr = rr >= (m + 1) / 2 ? rr - m : rr;
                             pk[t >> 2] |= (static_cast<uint32_t>(rr) & 0xffu) << (8 * (t & 3));
                         }
-                        uint4* dst = reinterpret_cast<uint4*>(g.out + (static_cast<int64_t>(mi) * g.mp + m0 + r) * g.np +
+                        uint4* dst = reinterpret_cast<uint4*>(g.out + (static_cast<int64_t>(plane) * g.mp + m0 + r) * g.np +
                                                               n0 + c0);
                         dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                         dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
@@ -3035,20 +3244,22 @@ template cudaError_t launch_ozaki<4>(const GemmArgs<4>&, int, void*, cudaStream_
 
 // ----------------------------------------------------- CRT form, host side
 
-OzakiLayout crt_layout(int N, int64_t m, int64_t n, int64_t k, int engine)
+OzakiLayout crt_layout(int N, int64_t m, int64_t n, int64_t k, int engine, int halves)
 {
     OzakiLayout L;
     const int elem_bytes = engine == 1 ? 2 : 1;
+    const int64_t planes = static_cast<int64_t>(N) * halves;        // residue planes per operand
+    const int64_t products = halves == 2 ? 3 * static_cast<int64_t>(N) : N;
     L.S = N;
     L.mp = round_up(m > 0 ? m : 1, 128);
     L.np = round_up(n > 0 ? n : 1, 128);
     L.kp = round_up(k > 0 ? k : 1, KPAD);
     L.offA = engine == 1 ? 256 : 0;                    // tcgen05: a 256-byte header (error code)
-    L.offB = L.offA + round_up(static_cast<int64_t>(N) * L.mp * L.kp * elem_bytes, 256);
-    L.offSig = L.offB + round_up(static_cast<int64_t>(N) * L.np * L.kp * elem_bytes, 256);
+    L.offB = L.offA + round_up(planes * L.mp * L.kp * elem_bytes, 256);
+    L.offSig = L.offB + round_up(planes * L.np * L.kp * elem_bytes, 256);
     L.offTau = L.offSig + round_up(L.mp * 4, 256);
-    L.offScr = L.offTau + round_up(L.np * 4, 256);      // [N][mp][np] int8 residues of the products
-    L.total = L.offScr + round_up(static_cast<int64_t>(N) * L.mp * L.np, 256);
+    L.offScr = L.offTau + round_up(L.np * 4, 256);      // [N or 3N][mp][np] int8 residues of the products
+    L.total = L.offScr + round_up(products * L.mp * L.np, 256);
     return L;
 }
 
@@ -3067,9 +3278,9 @@ static void crt_modulus(int N, uint32_t (&M)[crt::kRecLimbs])
     }
 }
 
-int crt_beta(int N, int64_t k)
+int crt_beta(int N, int64_t k, int halves)
 {
-    if (N < 1 || N > crt::kMaxModuli || k < 0) return -1;
+    if (N < 1 || N > crt::kMaxModuli || k < 0 || (halves != 1 && halves != 2)) return -1;
     uint32_t T[crt::kRecLimbs];
     crt_modulus(N, T);
     // T = floor((M - 1) / k): the largest beta with k 2^(2 beta - 1) < M is
@@ -3087,19 +3298,24 @@ int crt_beta(int N, int64_t k)
     int bl = 0;
     for (int w = 0; w < crt::kRecLimbs; ++w)
         if (T[w]) bl = 32 * w + (32 - __builtin_clz(T[w]));
+    // split integers: the largest w with k 2^(2w) < M, i.e. 2^(2w) <= T
+    if (halves == 2) return bl >= 1 ? 2 * ((bl - 1) / 2) : 0;
     return bl / 2;
 }
 
 template <int P>
-static cudaError_t crt_recover(const GemmArgs<P>& g, int N, int beta, const OzakiLayout& L, const int* sig,
-                               const int* tau, const int8_t* rq, cudaStream_t s);
+static cudaError_t crt_recover(const GemmArgs<P>& g, int N, int beta, int halves, const OzakiLayout& L,
+                               const int* sig, const int* tau, const int8_t* rq, cudaStream_t s);
 
-// Residues of both operands, with as few 16-bit limbs as beta needs.
+// Residues of both operands, with as few 16-bit limbs as beta needs (split
+// integers: 2N planes, A1's residues then A0's).
 template <int P, typename T>
-static cudaError_t crt_residues(const GemmArgs<P>& g, int N, const OzakiLayout& L, T* ra, T* rb, int* sig,
-                                int* tau, cudaStream_t s, int beta)
+static cudaError_t crt_residues(const GemmArgs<P>& g, int N, int halves, const OzakiLayout& L, T* ra, T* rb,
+                                int* sig, int* tau, cudaStream_t s, int beta)
 {
-    switch (residue_kind(beta)) {
+    switch (residue_kind(beta, halves)) {
+    case 5: return slice_both<P, T, 5>(g, 2 * N, L, ra, rb, sig, tau, s, beta);
+    case 4: return slice_both<P, T, 4>(g, 2 * N, L, ra, rb, sig, tau, s, beta);
     case 3: return slice_both<P, T, 3>(g, N, L, ra, rb, sig, tau, s, beta);
     case 2: return slice_both<P, T, 2>(g, N, L, ra, rb, sig, tau, s, beta);
     default: return slice_both<P, T, 1>(g, N, L, ra, rb, sig, tau, s, beta);
@@ -3107,11 +3323,12 @@ static cudaError_t crt_residues(const GemmArgs<P>& g, int N, const OzakiLayout& 
 }
 
 template <int P>
-cudaError_t launch_crt(const GemmArgs<P>& g, int N, void* ws, cudaStream_t s, int engine)
+cudaError_t launch_crt(const GemmArgs<P>& g, int N, void* ws, cudaStream_t s, int engine, int halves)
 {
-    const int beta = crt_beta(N, g.k);
-    if (beta < 1) return cudaErrorInvalidValue;
-    const OzakiLayout L = crt_layout(N, g.m, g.n, g.k, engine);
+    const int beta = crt_beta(N, g.k, halves);
+    if (beta < 1 || beta > crt_max_beta(halves)) return cudaErrorInvalidValue;
+    const int planes = N * halves;
+    const OzakiLayout L = crt_layout(N, g.m, g.n, g.k, engine, halves);
     int8_t* base = static_cast<int8_t*>(ws);
     int* sig = reinterpret_cast<int*>(base + L.offSig);
     int* tau = reinterpret_cast<int*>(base + L.offTau);
@@ -3122,13 +3339,13 @@ cudaError_t launch_crt(const GemmArgs<P>& g, int N, void* ws, cudaStream_t s, in
         uint16_t* sa = reinterpret_cast<uint16_t*>(base + L.offA);
         uint16_t* sb = reinterpret_cast<uint16_t*>(base + L.offB);
         e = cudaMemsetAsync(err, 0, sizeof(int), s);
-        if (e == cudaSuccess) e = crt_residues<P, uint16_t>(g, N, L, sa, sb, sig, tau, s, beta);
+        if (e == cudaSuccess) e = crt_residues<P, uint16_t>(g, N, halves, L, sa, sb, sig, tau, s, beta);
         if (e != cudaSuccess) return e;
         CUtensorMap ma, mb;
-        if (!slice_map(&ma, sa, N, L.mp, L.kp, tcc::BM) || !slice_map(&mb, sb, N, L.np, L.kp, tcc::BN))
+        if (!slice_map(&ma, sa, planes, L.mp, L.kp, tcc::BM) || !slice_map(&mb, sb, planes, L.np, L.kp, tcc::BN))
             return cudaErrorInvalidValue;
         const CrtTcArgs a{rq, L.mp, L.np, L.kp, N, static_cast<int>(L.mp / tcc::BM),
-                          static_cast<int>(L.np / tcc::BN), err, tc_test_abort()};
+                          static_cast<int>(L.np / tcc::BN), err, tc_test_abort(), halves == 2 ? 1 : 0};
         const int smem = tcc::STAGES * tcc::STAGE_BYTES + 1024;
         e = cudaFuncSetAttribute(crt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
@@ -3137,11 +3354,11 @@ cudaError_t launch_crt(const GemmArgs<P>& g, int N, void* ws, cudaStream_t s, in
         crt_tc_kernel<<<grid, 192, smem, s>>>(ma, mb, a);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        return crt_recover<P>(g, N, beta, L, sig, tau, rq, s);
+        return crt_recover<P>(g, N, beta, halves, L, sig, tau, rq, s);
     }
     int8_t* ra = base + L.offA;
     int8_t* rb = base + L.offB;
-    e = crt_residues<P, int8_t>(g, N, L, ra, rb, sig, tau, s, beta);
+    e = crt_residues<P, int8_t>(g, N, halves, L, ra, rb, sig, tau, s, beta);
     if (e != cudaSuccess) return e;
     // 128 x 128 CTA tile, 8 warps of 64 x 32, 4 stages of 64 bytes of k
     constexpr int MT = 4, NT = 4, WM = 2, WN = 4, STG = 4, KS = 64;
@@ -3149,20 +3366,23 @@ cudaError_t launch_crt(const GemmArgs<P>& g, int N, void* ws, cudaStream_t s, in
     e = cudaFuncSetAttribute(crt_gemm_kernel<MT, NT, WM, WN, STG, KS>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    const CrtGemmArgs ga{ra, rb, rq, L.mp, L.np, L.kp};
-    const dim3 grid(static_cast<unsigned>(L.np / 128), static_cast<unsigned>(L.mp / 128), static_cast<unsigned>(N));
+    const CrtGemmArgs ga{ra, rb, rq, L.mp, L.np, L.kp, N, halves == 2 ? 1 : 0};
+    const dim3 grid(static_cast<unsigned>(L.np / 128), static_cast<unsigned>(L.mp / 128),
+                    static_cast<unsigned>(halves == 2 ? 3 * N : N));
     crt_gemm_kernel<MT, NT, WM, WN, STG, KS><<<grid, WM * WN * 32, smem, s>>>(ga);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return crt_recover<P>(g, N, beta, L, sig, tau, rq, s);
+    return crt_recover<P>(g, N, beta, halves, L, sig, tau, rq, s);
 }
 
 // The recovery kernel over the products' residues rq.
 template <int P>
-static cudaError_t crt_recover(const GemmArgs<P>& g, int N, int beta, const OzakiLayout& L, const int* sig,
-                               const int* tau, const int8_t* rq, cudaStream_t s)
+static cudaError_t crt_recover(const GemmArgs<P>& g, int N, int beta, int halves, const OzakiLayout& L,
+                               const int* sig, const int* tau, const int8_t* rq, cudaStream_t s)
 {
-    CrtRecArgs ra_{rq, sig, tau, {nullptr, nullptr, nullptr, nullptr}, g.ldc, g.m, g.n, L.mp, L.np, N, beta, {}, {}};
+    CrtRecArgs ra_{rq, sig, tau, {nullptr, nullptr, nullptr, nullptr}, g.ldc, g.m, g.n, L.mp, L.np, N, beta, 0,
+                   {}, {}};
+    if (halves == 2) ra_.w = beta / 2;
     for (int c = 0; c < P; ++c) ra_.C[c] = g.C[c];
     crt_modulus(N, ra_.M);
     // H = ceil(M / 2) = (M + 1) >> 1
@@ -3196,6 +3416,18 @@ static cudaError_t crt_recover(const GemmArgs<P>& g, int N, int beta, const Ozak
         }
         ra_.f[i] = static_cast<float>(static_cast<double>(c) / static_cast<double>(mi));
     }
+    if (halves == 2) {
+        const unsigned grid2 = blocks_for(g.m * ((g.n + 1) / 2), 256);     // two outputs per thread
+        switch ((N + 7) / 8) {
+        case 1: crt_recover2_kernel<P, 8><<<grid2, 256, 0, s>>>(ra_); break;
+        case 2: crt_recover2_kernel<P, 16><<<grid2, 256, 0, s>>>(ra_); break;
+        case 3: crt_recover2_kernel<P, 24><<<grid2, 256, 0, s>>>(ra_); break;
+        case 4: crt_recover2_kernel<P, 32><<<grid2, 256, 0, s>>>(ra_); break;
+        case 5: crt_recover2_kernel<P, 40><<<grid2, 256, 0, s>>>(ra_); break;
+        default: crt_recover2_kernel<P, 48><<<grid2, 256, 0, s>>>(ra_); break;
+        }
+        return cudaGetLastError();
+    }
     const int64_t outs = g.m * ((g.n + 3) / 4);        // four outputs per thread
     const unsigned grid = blocks_for(outs, 256);
     switch ((N + 7) / 8) {
@@ -3210,8 +3442,8 @@ static cudaError_t crt_recover(const GemmArgs<P>& g, int N, int beta, const Ozak
     return cudaGetLastError();
 }
 
-template cudaError_t launch_crt<2>(const GemmArgs<2>&, int, void*, cudaStream_t, int);
-template cudaError_t launch_crt<3>(const GemmArgs<3>&, int, void*, cudaStream_t, int);
-template cudaError_t launch_crt<4>(const GemmArgs<4>&, int, void*, cudaStream_t, int);
+template cudaError_t launch_crt<2>(const GemmArgs<2>&, int, void*, cudaStream_t, int, int);
+template cudaError_t launch_crt<3>(const GemmArgs<3>&, int, void*, cudaStream_t, int, int);
+template cudaError_t launch_crt<4>(const GemmArgs<4>&, int, void*, cudaStream_t, int, int);
 
 }  // namespace mpg

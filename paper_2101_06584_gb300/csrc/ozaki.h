@@ -39,15 +39,23 @@ cudaError_t launch_ozaki(const GemmArgs<P>& g, int S, void* ws, cudaStream_t s, 
 // kCrtMaxModuli), beta bits per scaled entry.  Workspace: residues of op(A)
 // [N][mp][kp] and of op(B)^T [N][np][kp] (int8; mp, np rounded up to 128, kp
 // to 128), int32 exponents, and the products' residues [N][mp][np] (int8).
+// halves = 2 (split integers, A' = A1 2^w + A0): [2N] residue planes per
+// operand (A1's, then A0's) and [3N] product planes (hh, mid, ll).
 constexpr int kCrtMaxModuli = 49;
-inline int64_t crt_k_limit() { return (2147483647LL) / (128 * 128); }
+inline int64_t crt_k_limit(int halves = 1) { return (2147483647LL) / (halves * 128 * 128); }
+// The most bits a scaled entry may keep: 192 for one integer (three 64-bit
+// residue cursors' worth), 316 with split integers (the 384-bit sum of the
+// floored components with its 64 guard bits).
+inline int crt_max_beta(int halves) { return halves == 2 ? 316 : 192; }
 // engine 0: int8 residues (mma.sync); engine 1: bf16 residues after a 256-byte
 // header (tcgen05).
-OzakiLayout crt_layout(int N, int64_t m, int64_t n, int64_t k, int engine = 0);
-// The largest beta with k 2^(2 beta - 1) < m_0 ... m_(N-1); -1 for a bad N.
-int crt_beta(int N, int64_t k);
+OzakiLayout crt_layout(int N, int64_t m, int64_t n, int64_t k, int engine = 0, int halves = 1);
+// The largest beta with k 2^(2 beta - 1) < m_0 ... m_(N-1) (halves = 2:
+// beta = 2w for the largest w with k 2^(2w) < m_0 ... m_(N-1)); -1 for a bad
+// N or halves.
+int crt_beta(int N, int64_t k, int halves = 1);
 template <int P>
-cudaError_t launch_crt(const GemmArgs<P>& g, int N, void* ws, cudaStream_t s, int engine = 0);
+cudaError_t launch_crt(const GemmArgs<P>& g, int N, void* ws, cudaStream_t s, int engine = 0, int halves = 1);
 
 // Size of the library's fixed scratch array and its device address on the
 // current device (looked up on first use per device).

@@ -15,7 +15,7 @@ import torch
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libmpgemm.so")
 P_OF = {"d": 1, "dd": 2, "td": 3, "qd": 4}   # "d": the binary64-only product
-ALGO = {"auto": 0, "fp64": 1, "int8": 2, "bf16": 3, "crt": 4, "crt_bf16": 5}
+ALGO = {"auto": 0, "fp64": 1, "int8": 2, "bf16": 3, "crt": 4, "crt_bf16": 5, "crt2": 6, "crt2_bf16": 7}
 
 _lib = None
 
@@ -77,6 +77,7 @@ def _declare(L):
     L.mpgemm_batch_autotune.argtypes = [i, i, PP, vp, ctypes.c_size_t, i, ctypes.POINTER(i),
                                         ctypes.POINTER(ctypes.c_float)]
     L.mpgemm_crt_beta.argtypes = [i, i64]
+    L.mpgemm_crt_split_beta.argtypes = [i, i64]
     L.mpgemm_num_tiles.argtypes = [i]
     L.mpgemm_default_tile.argtypes = [i, i64, i64, i64]
     L.mpgemm_tc_status.argtypes = [vp]
@@ -251,9 +252,11 @@ def eft(which, a, b):
     return s, e
 
 
-def crt_beta(moduli, k):
-    """Bits per scaled entry of the CRT form with this many moduli at inner dimension k."""
-    b = lib().mpgemm_crt_beta(int(moduli), int(k))
+def crt_beta(moduli, k, split=False):
+    """Bits per scaled entry of the CRT form with this many moduli at inner
+    dimension k (split=True: with split integers)."""
+    f = lib().mpgemm_crt_split_beta if split else lib().mpgemm_crt_beta
+    b = f(int(moduli), int(k))
     check(b if b < 0 else 0)
     return b
 

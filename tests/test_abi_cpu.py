@@ -178,7 +178,7 @@ def test_slicing_options(L):
 
 
 def test_version(L):
-    assert L.mpgemm_version() == 103
+    assert L.mpgemm_version() == 104
 
 
 def test_tc_status_validation(L):
@@ -305,4 +305,42 @@ def test_crt_form_host_checks(L):
     o = Opts(0, 0, 4, 0, 28, 0, None, 0)
     big = 131072
     assert L.mpgemm_ex(2, ctypes.byref(o), 8, 8, big, A, big, B, 8, C, 8) == -4
+    assert "int32" in err(L)
+
+
+def test_crt_split_host_checks(L):
+    """Split integers: the bit count agrees with the oracle's definition
+    (beta = 2w, the largest w with k 2^(2w) < M), the workspace holds 2N
+    residue planes per operand and 3N product planes, and k above 65535, too
+    few moduli and more than 316 bits are refused before any launch."""
+    from oracle import crt as R
+    from paper_2101_06584_gb300.mpgemm import Opts
+    for N in range(1, 50):
+        for k in (1, 2, 127, 1024, 4096, 37449, 65535):
+            assert L.mpgemm_crt_split_beta(N, k) == R.beta_bits(N, k, halves=2), (N, k)
+    assert L.mpgemm_crt_split_beta(0, 8) == -1 and L.mpgemm_crt_split_beta(50, 8) == -1
+    assert R.k_limit(2) == 65535
+    r = lambda x: (x + 127) // 128 * 128
+    r256 = lambda x: (x + 255) // 256 * 256
+    for (m, n, k, N) in ((100, 70, 300, 28), (1024, 1024, 1024, 30), (1, 1, 1, 40)):
+        for algo, head, eb in ((6, 0, 1), (7, 256, 2)):
+            o = Opts(0, 0, algo, 0, N, 0, None, 0)
+            mp = r(m)
+            want = (head + r256(2 * N * mp * r(k) * eb) + r256(2 * N * r(n) * r(k) * eb) + r256(4 * mp) +
+                    r256(4 * r(n)) + r256(3 * N * mp * r(n)))
+            assert L.mpgemm_workspace_size(4, ctypes.byref(o), m, n, k) == want, (algo, m, n, k, N)
+    o = Opts(0, 0, 6, 0, 0, 0, None, 0)                       # default moduli: 16 / 22 / 30
+    for P, N in ((2, 16), (3, 22), (4, 30)):
+        want = r256(2 * N * 128 * 128) * 2 + 2 * 512 + r256(3 * N * 128 * 128)
+        assert L.mpgemm_workspace_size(P, ctypes.byref(o), 64, 64, 64) == want
+    A, B, C = planes(FAKE, 4), planes(2 * FAKE, 4), planes(3 * FAKE, 4)
+    # N = 1: M = 256 leaves w = 0 at k = 200; 49 moduli at k = 8: 2w = 336 > 316
+    for N, k, code, text in ((50, 8, -1, "moduli"), (1, 200, -4, "no bits"), (49, 8, -4, "316"),
+                             (30, 8, -3, "workspace")):
+        o = Opts(0, 0, 6, 0, N, 0, None, 0)
+        assert L.mpgemm_ex(4, ctypes.byref(o), 8, 8, k, A, k, B, 8, C, 8) == code, (N, k)
+        assert text in err(L)
+    o = Opts(0, 0, 7, 0, 30, 0, None, 0)
+    big = 65536
+    assert L.mpgemm_ex(4, ctypes.byref(o), 8, 8, big, A, big, B, 8, C, 8) == -4
     assert "int32" in err(L)
