@@ -70,10 +70,10 @@ def bf16_peak():
 # the sources each recorded kernel is compiled from
 TRAFFIC_SOURCES = {
     "td_qd": ["mp_arith.cuh", "gemm_kernel.cuh", "gemm_qd.cu", "internal.h"],
-    "dd_int8": ["mp_arith.cuh", "ozaki.cu", "ozaki.h", "internal.h"],
-    "dd_tc": ["mp_arith.cuh", "ozaki.cu", "ozaki.h", "internal.h"],
-    "dd_crtint8": ["ozaki.cu", "ozaki.h", "internal.h"],
-    "dd_crttc": ["ozaki.cu", "ozaki.h", "internal.h"],
+    "dd_int8": ["mp_arith.cuh", "ozaki.cu", "ozaki_common.cuh", "ozaki.h", "internal.h"],
+    "dd_tc": ["mp_arith.cuh", "ozaki.cu", "ozaki_common.cuh", "ozaki.h", "internal.h"],
+    "dd_crtint8": ["crt.cu", "ozaki_common.cuh", "ozaki.h", "internal.h"],
+    "dd_crttc": ["crt.cu", "ozaki_common.cuh", "ozaki.h", "internal.h"],
 }
 
 

@@ -1,0 +1,1016 @@
+// ozaki_common.cuh -- what the slicing form (ozaki.cu) and the CRT form (crt.cu)
+// share: the scaled-integer machinery (digit and residue cursors), the
+// scale and slice kernels, the tcgen05/TMA/mbarrier helpers, and the host
+// side of slicing both operands and of the TMA tensor maps of the slices.
+// Included by those two translation units only; everything here has
+// internal linkage or is inline.
+#pragma once
+#include "mp_arith.cuh"
+#include "ozaki.h"
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <cstdlib>
+#include <mutex>
+
+namespace mpg {
+
+
+namespace {
+
+constexpr int TILE = 64;         // padding granularity of the rows of op(A) and op(B)
+constexpr int KPAD = 128;        // padding granularity of k (the largest k-step)
+
+__device__ __forceinline__ uint64_t abs_bits(double x)
+{
+    return static_cast<uint64_t>(__double_as_longlong(x)) & 0x7fffffffffffffffull;
+}
+
+// ilogb of a positive finite binary64 given by its magnitude bits.
+__device__ __forceinline__ int ilogb_bits(uint64_t b)
+{
+    const int E = static_cast<int>(b >> 52);
+    if (E) return E - 1023;
+    const uint64_t frac = b & ((1ull << 52) - 1);
+    return (63 - __clzll(static_cast<long long>(frac))) - 1074;
+}
+
+// Signed integer mantissa and exponent: x = M * 2^e (M = 0 for +-0).
+__device__ __forceinline__ void decompose(double x, int64_t& M, int& e)
+{
+    const uint64_t b = static_cast<uint64_t>(__double_as_longlong(x));
+    const int E = static_cast<int>((b >> 52) & 0x7ff);
+    const uint64_t frac = b & ((1ull << 52) - 1);
+    int64_t m;
+    if (E == 0) { m = static_cast<int64_t>(frac); e = -1074; }
+    else        { m = static_cast<int64_t>(frac | (1ull << 52)); e = E - 1075; }
+    M = (b >> 63) ? -m : m;
+}
+
+// floor(W * 2^sh) and whether bits were dropped, for sh < 0.
+__device__ __forceinline__ __int128 floor_shift(__int128 W, int sh, bool& frac)
+{
+    if (sh >= 0) { frac = false; return W << sh; }
+    if (sh <= -127) { frac = (W != 0); return W < 0 ? -1 : 0; }
+    const int r = -sh;
+    const __int128 mask = (static_cast<__int128>(1) << r) - 1;
+    frac = (W & mask) != 0;
+    return W >> r;   // arithmetic shift: floor
+}
+
+// X = floor((hi + lo) 2^(F - sigma)) exactly, sticky = whether X is inexact.
+__device__ __forceinline__ __int128 fixed_point(double hi, double lo, int sigma, int F, bool& sticky)
+{
+    int64_t Mh, Ml;
+    int eh, el;
+    decompose(hi, Mh, eh);
+    decompose(lo, Ml, el);
+    if (Mh == 0 && Ml != 0) { Mh = Ml; eh = el; Ml = 0; }
+    int sh = eh - sigma + F, sl = el - sigma + F;
+    if (Ml != 0 && sl > sh) {        // unnormalised input: larger exponent first
+        const int64_t tm = Mh; Mh = Ml; Ml = tm;
+        const int ts = sh; sh = sl; sl = ts;
+    }
+    if (Mh == 0) { sticky = false; return 0; }
+    if (Ml == 0) return floor_shift(Mh, sh, sticky);
+    if (sh >= 0) {
+        bool f;
+        const __int128 lowp = floor_shift(Ml, sl, f);
+        sticky = f;
+        return (static_cast<__int128>(Mh) << sh) + lowp;
+    }
+    const int d = sh - sl;            // > 0 here: lo below hi
+    if (d <= 74) {
+        const __int128 W = (static_cast<__int128>(Mh) << d) + Ml;
+        return floor_shift(W, sl, sticky);
+    }
+    // lo lies more than 74 bits below hi's last bit: it only decides the
+    // floor when hi is itself an integer in these units
+    bool fh;
+    __int128 X = floor_shift(Mh, sh, fh);
+    if (!fh && Ml < 0) X -= 1;
+    sticky = true;
+    return X;
+}
+
+}  // namespace
+
+// Digits of a fixed-point value held with the current digit's unit at bit
+// 120 of a 128-bit two's-complement integer (hi, lo): |value| < 2^126.  Each
+// step takes the nearest integer of value / 2^120 (ties to even unless
+// `sticky` says the true value lies above the held one), subtracts it, and
+// moves the next digit's unit up by the 7 bits of the base.
+struct DigitCursor {
+    uint64_t hi, lo;
+    bool sticky;
+    __device__ __forceinline__ int next()
+    {
+        const int64_t t = static_cast<int64_t>(hi + (1ull << 55)) >> 56;          // nearest, ties up
+        const bool tie = lo == 0 && (hi & ((1ull << 56) - 1)) == (1ull << 55);
+        const int64_t d = (tie && !sticky && (t & 1)) ? t - 1 : t;                // ties to even
+        hi -= static_cast<uint64_t>(d) << 56;                                      // |value| <= 2^119
+        hi = (hi << 7) | (lo >> 57);
+        lo <<= 7;
+        return static_cast<int>(d);
+    }
+};
+
+// The digit cursor of (hi + lo) 2^-sigma with S digits: R = floor((hi + lo)
+// 2^(F - sigma)), F = 7S + 12, |R| < 2^(F-1), shifted left by 115 - 7S so that
+// the first digit's unit 2^(F-7) sits at bit 120.
+__device__ __forceinline__ DigitCursor ozaki_cursor(double hi, double lo, int sigma, int S)
+{
+    const int F = 7 * S + 12;
+    bool sticky;
+    const unsigned __int128 R = static_cast<unsigned __int128>(fixed_point(hi, lo, sigma, F, sticky)) << (115 - 7 * S);
+    return DigitCursor{static_cast<uint64_t>(R >> 64), static_cast<uint64_t>(R), sticky};
+}
+
+// ------------------------------------------------- wide digits (TD, QD)
+//
+// For P >= 3 components the S digits need up to 7S + 12 bits below the scale
+// plus guard bits, beyond 128.  Each component is floored to a multiple of
+// 2^(sigma - F - 64) (F = 7S + 12) and the floored parts are summed exactly
+// in a 384-bit two's-complement integer (six 64-bit words, word 0 least
+// significant); the digits are those of that sum, ties to even decided
+// exactly.  Nothing of the method's arithmetic is approximated: the floor is
+// part of the definition, 64 bits below the last digit.
+
+constexpr int kWideWords = 6;
+constexpr int kGuardBits = 64;
+
+struct Wide {
+    uint64_t w[kWideWords];
+};
+
+// W += M * 2^sh for a signed |M| < 2^53 and 0 <= sh (fits by construction).
+__device__ __forceinline__ void wide_add_shifted(Wide& W, int64_t M, int sh)
+{
+    const int wi = sh >> 6, bo = sh & 63;
+    const uint64_t ext = M < 0 ? ~0ull : 0ull;
+    uint64_t part[kWideWords];
+#pragma unroll
+    for (int i = 0; i < kWideWords; ++i) part[i] = i < wi ? 0ull : ext;
+    const uint64_t lo = static_cast<uint64_t>(M) << bo;
+    const uint64_t hi = bo == 0 ? ext : static_cast<uint64_t>(M >> (64 - bo));
+#pragma unroll
+    for (int i = 0; i < kWideWords; ++i) {
+        if (i == wi) part[i] = lo;
+        if (i == wi + 1) part[i] = hi;
+    }
+    uint64_t carry = 0;
+#pragma unroll
+    for (int i = 0; i < kWideWords; ++i) {
+        const uint64_t a = W.w[i], b = part[i];
+        const uint64_t s1 = a + b;
+        const uint64_t c1 = s1 < a;
+        const uint64_t s2 = s1 + carry;
+        const uint64_t c2 = s2 < s1;
+        W.w[i] = s2;
+        carry = c1 | c2;
+    }
+}
+
+// W += v for a small signed v at bit 0.
+__device__ __forceinline__ void wide_add_small(Wide& W, int64_t v)
+{
+    wide_add_shifted(W, v, 0);
+}
+
+// Digits of a 384-bit fixed-point value with the current digit's unit at bit
+// 376 (|value| < 2^382); as DigitCursor, with every tie exact.
+struct WideCursor {
+    uint64_t w[kWideWords];
+    __device__ __forceinline__ int next()
+    {
+        const int64_t t = static_cast<int64_t>(w[5] + (1ull << 55)) >> 56;        // nearest, ties up
+        bool tie = (w[5] & ((1ull << 56) - 1)) == (1ull << 55);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) tie = tie && w[i] == 0;
+        const int64_t d = (tie && (t & 1)) ? t - 1 : t;                           // ties to even
+        w[5] -= static_cast<uint64_t>(d) << 56;
+#pragma unroll
+        for (int i = 5; i > 0; --i) w[i] = (w[i] << 7) | (w[i - 1] >> 57);
+        w[0] <<= 7;
+        return static_cast<int>(d);
+    }
+};
+
+// The digit cursor of the sum of the P components, each floored at
+// 2^(sigma - F - 64), F = 7S + 12: the floored sum W (|W| < 2^(F+63)) shifted
+// left by 307 - 7S so that the first digit's unit 2^(F+57) sits at bit 376.
+template <int P>
+__device__ __forceinline__ WideCursor ozaki_cursor_wide(const double (&c)[P], int sigma, int S)
+{
+    const int F = 7 * S + 12;
+    Wide W;
+#pragma unroll
+    for (int i = 0; i < kWideWords; ++i) W.w[i] = 0ull;
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        int64_t M;
+        int e;
+        decompose(c[i], M, e);
+        if (M == 0) continue;
+        const int sh = e - sigma + F + kGuardBits;
+        if (sh >= 0) wide_add_shifted(W, M, sh);
+        else if (sh > -64) wide_add_small(W, M >> (-sh));      // arithmetic shift: floor
+        else wide_add_small(W, M < 0 ? -1 : 0);
+    }
+    // shift left by L = 307 - 7S (27 <= L <= 300): whole words first, with
+    // unrolled selects so that W stays in registers, then the bits
+    const int L = 307 - 7 * S, ws = L >> 6, bs = L & 63;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (k < ws) {
+#pragma unroll
+            for (int i = kWideWords - 1; i > 0; --i) W.w[i] = W.w[i - 1];
+            W.w[0] = 0ull;
+        }
+    }
+    WideCursor cur;
+#pragma unroll
+    for (int i = kWideWords - 1; i > 0; --i) cur.w[i] = bs ? (W.w[i] << bs) | (W.w[i - 1] >> (64 - bs)) : W.w[i];
+    cur.w[0] = W.w[0] << bs;
+    return cur;
+}
+
+// ------------------------------------------------------- CRT residues
+//
+// The CRT form (Ozaki scheme II; not in the paper): each scaled entry of
+// op(A) and op(B) becomes an integer A' (the nearest integer, ties to even,
+// of the sum of its components each floored to a multiple of
+// 2^(sigma - beta - 64), in units of 2^(sigma - beta)), whose residues modulo
+// N pairwise coprime moduli m_i <= 256 -- symmetric representatives, so
+// |r| <= 128, exact in int8 and in bf16 -- replace the digits of the slicing
+// form.  The product of each residue pair is exact on the tensor cores; the
+// integer product A'B' is recovered from its residues (Garner's mixed radix)
+// and rounded to P binary64 components.
+
+namespace crt {
+constexpr int kMaxModuli = 49;
+constexpr int kLimbs = 12;                        // |A'| < 2^192 in 16-bit limbs
+
+struct Tables {
+    int count;
+    int m[kMaxModuli];                            // 256, 255, 253, 251, 247, ...
+    uint32_t magic[kMaxModuli];                   // floor(2^32 / m) + 1
+    uint32_t pw16[kMaxModuli][kLimbs];            // 2^(16 j) mod m_i
+    uint32_t pm[kMaxModuli][kMaxModuli];          // (m_0 ... m_(j-1)) mod m_i, j < i
+    uint32_t inv[kMaxModuli];                     // (m_0 ... m_(i-1))^-1 mod m_i
+};
+
+constexpr int gcd_c(int a, int b)
+{
+    while (b) {
+        const int t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// The moduli: pairwise coprime integers taken greedily from 256 downward.
+constexpr Tables make_tables()
+{
+    Tables t{};
+    int n = 0;
+    for (int m = 256; m > 1 && n < kMaxModuli; --m) {
+        bool ok = true;
+        for (int i = 0; i < n; ++i) ok = ok && gcd_c(m, t.m[i]) == 1;
+        if (ok) t.m[n++] = m;
+    }
+    t.count = n;
+    for (int i = 0; i < n; ++i) {
+        const uint32_t m = static_cast<uint32_t>(t.m[i]);
+        t.magic[i] = static_cast<uint32_t>((1ull << 32) / m + 1);
+        uint32_t p = 1;
+        for (int j = 0; j < kLimbs; ++j) {
+            t.pw16[i][j] = p;
+            p = static_cast<uint32_t>((static_cast<uint64_t>(p) << 16) % m);
+        }
+        uint32_t q = 1 % m;
+        for (int j = 0; j < i; ++j) {
+            t.pm[i][j] = q;
+            q = static_cast<uint32_t>((static_cast<uint64_t>(q) * static_cast<uint32_t>(t.m[j])) % m);
+        }
+        uint32_t inv = 0;
+        for (uint32_t x = 1; x < m; ++x)
+            if ((static_cast<uint64_t>(q) * x) % m == 1) { inv = x; break; }
+        t.inv[i] = i == 0 ? 1 % m : inv;
+    }
+    return t;
+}
+
+constexpr Tables kHost = make_tables();
+static_assert(kHost.count == kMaxModuli, "49 pairwise coprime moduli up to 256");
+static __constant__ Tables kDev = kHost;
+
+// x mod m_i for x < 2^32 (one Barrett step: the estimate is the quotient or
+// one more).
+__device__ __forceinline__ uint32_t mod_small(uint32_t x, int i)
+{
+    const uint32_t m = static_cast<uint32_t>(kDev.m[i]);
+    const uint32_t q = __umulhi(x, kDev.magic[i]);
+    const int r = static_cast<int>(x - q * m);
+    return static_cast<uint32_t>(r < 0 ? r + static_cast<int>(m) : r);
+}
+}  // namespace crt
+
+// Residues of one scaled entry, one modulus per next(): the symmetric
+// representative of A' mod m_i, i = 0, 1, ...  NL 16-bit limbs hold |A'|
+// (|A'| <= 2^(beta - 1): NL = 4, 8 or 12 for beta up to 64, 128, 192).
+template <int NL>
+struct ResidueCursor {
+    uint32_t limb[NL];                // |A'| in 16-bit limbs, least significant first
+    bool neg;
+    int idx;
+    __device__ __forceinline__ int next()
+    {
+        const int i = idx++;
+        uint32_t s = 0;
+#pragma unroll
+        for (int j = 0; j < NL; ++j) s += limb[j] * crt::kDev.pw16[i][j];
+        const int m = crt::kDev.m[i];
+        int r = static_cast<int>(crt::mod_small(s, i));
+        if (neg && r) r = m - r;
+        return r >= (m + 1) / 2 ? r - m : r;
+    }
+};
+
+// A' of the P components: each floored at 2^(sigma - beta - 64), summed
+// exactly in 384 bits, rounded to the nearest integer (ties to even) in units
+// of 2^(sigma - beta); in two's complement, five 64-bit words, least
+// significant first (beta <= 316).
+template <int P>
+__device__ __forceinline__ void scaled_integer(const double (&c)[P], int sigma, int beta, uint64_t (&I)[kWideWords - 1])
+{
+    Wide W;
+#pragma unroll
+    for (int i = 0; i < kWideWords; ++i) W.w[i] = 0ull;
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        int64_t M;
+        int e;
+        decompose(c[i], M, e);
+        if (M == 0) continue;
+        const int sh = e - sigma + beta + kGuardBits;
+        if (sh >= 0) wide_add_shifted(W, M, sh);
+        else if (sh > -64) wide_add_small(W, M >> (-sh));      // arithmetic shift: floor
+        else wide_add_small(W, M < 0 ? -1 : 0);
+    }
+    // integer part (words 1..5, floor) and the fraction in word 0
+    const uint64_t f = W.w[0];
+    const bool up = f > (1ull << 63) || (f == (1ull << 63) && (W.w[1] & 1ull));
+#pragma unroll
+    for (int i = 0; i < kWideWords - 1; ++i) I[i] = W.w[i + 1];
+    uint64_t carry = up ? 1ull : 0ull;
+#pragma unroll
+    for (int i = 0; i < kWideWords - 1; ++i) {
+        const uint64_t s = I[i] + carry;
+        carry = (carry && s == 0) ? 1ull : 0ull;
+        I[i] = s;
+    }
+}
+
+// The residue cursor of a two's-complement integer: its sign and magnitude
+// in NL 16-bit limbs.
+template <int NL>
+__device__ __forceinline__ ResidueCursor<NL> cursor_of(uint64_t (&I)[kWideWords - 1])
+{
+    ResidueCursor<NL> cur;
+    cur.neg = (I[kWideWords - 2] >> 63) != 0;
+    if (cur.neg) {                                   // magnitude: two's complement negation
+        uint64_t cc = 1;
+#pragma unroll
+        for (int i = 0; i < kWideWords - 1; ++i) {
+            const uint64_t s = ~I[i] + cc;
+            cc = (cc && s == 0) ? 1ull : 0ull;
+            I[i] = s;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NL; ++j) cur.limb[j] = static_cast<uint32_t>(I[j / 4] >> (16 * (j % 4))) & 0xffffu;
+    cur.idx = 0;
+    return cur;
+}
+
+template <int NL, int P>
+__device__ __forceinline__ ResidueCursor<NL> residue_cursor(const double (&c)[P], int sigma, int beta)
+{
+    uint64_t I[kWideWords - 1];
+    scaled_integer<P>(c, sigma, beta, I);
+    return cursor_of<NL>(I);
+}
+
+// Word q of a five-word two's-complement integer, its sign beyond the top.
+__device__ __forceinline__ uint64_t word_at(const uint64_t (&x)[kWideWords - 1], int q)
+{
+    uint64_t r = (x[kWideWords - 2] >> 63) ? ~0ull : 0ull;
+#pragma unroll
+    for (int k = 0; k < kWideWords - 1; ++k) r = (k == q) ? x[k] : r;
+    return r;
+}
+
+// Split integers: residues of A1 for moduli 0..N-1, then of A0, where
+// A' = A1 2^w + A0 with A0 in [-2^(w-1), 2^(w-1)).
+template <int NL>
+struct SplitResidueCursor {
+    ResidueCursor<NL> hi, lo;
+    int n, idx;
+    __device__ __forceinline__ int next() { return idx++ < n ? hi.next() : lo.next(); }
+};
+
+template <int NL, int P>
+__device__ __forceinline__ SplitResidueCursor<NL> split_residue_cursor(const double (&c)[P], int sigma, int beta,
+                                                                       int n)
+{
+    constexpr int WW = kWideWords - 1;
+    uint64_t I[WW];
+    scaled_integer<P>(c, sigma, beta, I);
+    const int w = beta / 2;
+    // A0: the low w bits, sign-extended from bit w - 1
+    const int wi = w >> 6, wb = w & 63;
+    const bool low_neg = (word_at(I, (w - 1) >> 6) >> ((w - 1) & 63)) & 1ull;
+    uint64_t A0[WW], D[WW];
+#pragma unroll
+    for (int k = 0; k < WW; ++k) {
+        const uint64_t keep = k < wi ? ~0ull : (k == wi ? (wb ? ((1ull << wb) - 1) : 0ull) : 0ull);
+        A0[k] = (I[k] & keep) | (low_neg ? ~keep : 0ull);
+    }
+    // A1 = (A' - A0) >> w, exact
+    uint64_t borrow = 0;
+#pragma unroll
+    for (int k = 0; k < WW; ++k) {
+        const uint64_t d = I[k] - A0[k] - borrow;
+        borrow = (I[k] < A0[k] || (I[k] == A0[k] && borrow)) ? 1ull : 0ull;
+        D[k] = d;
+    }
+    uint64_t A1[WW];
+#pragma unroll
+    for (int k = 0; k < WW; ++k) {
+        const uint64_t a = word_at(D, k + wi), b = word_at(D, k + wi + 1);
+        A1[k] = wb ? (a >> wb) | (b << (64 - wb)) : a;
+    }
+    SplitResidueCursor<NL> cur;
+    cur.hi = cursor_of<NL>(A1);
+    cur.lo = cursor_of<NL>(A0);
+    cur.n = n;
+    cur.idx = 0;
+    return cur;
+}
+
+// ------------------------------------------------------------------ scale
+
+// One warp per vector whose elements are contiguous (stride 1, vectors ld apart).
+static __global__ void ozaki_scale_contig(const double* __restrict__ hi, int64_t count, int64_t len,
+                                   int64_t ld, int* __restrict__ out)
+{
+    const int64_t v = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (v >= count) return;
+    uint64_t mx = 0;
+    for (int64_t p = lane; p < len; p += 32) {
+        const uint64_t b = abs_bits(hi[v * ld + p]);
+        mx = b > mx ? b : mx;
+    }
+    for (int off = 16; off; off >>= 1) {
+        const uint64_t o = __shfl_xor_sync(0xffffffffu, mx, off);
+        mx = o > mx ? o : mx;
+    }
+    if (lane == 0) out[v] = mx ? ilogb_bits(mx) + 2 : 0;
+}
+
+// Vectors whose elements are ld apart (vectors adjacent): a block of 32 x 32
+// threads covers 32 vectors, each column of threads a 32-way split of the
+// elements (coalesced rows of 32 vectors), reduced in shared memory.
+static __global__ void __launch_bounds__(1024) ozaki_scale_strided(const double* __restrict__ hi, int64_t count,
+                                                           int64_t len, int64_t ld, int* __restrict__ out)
+{
+    __shared__ unsigned long long smax[32];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t v = static_cast<int64_t>(blockIdx.x) * 32 + tx;
+    if (ty == 0) smax[tx] = 0;
+    __syncthreads();
+    uint64_t mx = 0;
+    if (v < count) {
+#pragma unroll 4
+        for (int64_t p = ty; p < len; p += 32) {
+            const uint64_t b = abs_bits(hi[p * ld + v]);
+            mx = b > mx ? b : mx;
+        }
+    }
+    atomicMax(&smax[tx], static_cast<unsigned long long>(mx));
+    __syncthreads();
+    if (ty == 0 && v < count) {
+        const uint64_t m = smax[tx];
+        out[v] = m ? ilogb_bits(m) + 2 : 0;
+    }
+}
+
+// Zero the exponent padding [count, padded).
+static __global__ void ozaki_fill_int(int* out, int64_t from, int64_t to)
+{
+    const int64_t i = from + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < to) out[i] = 0;
+}
+
+// ------------------------------------------------------------------ slice
+
+// Slice storage: int8 digits for the int8 tensor path, or the same digits as
+// bf16 (exact: |d| <= 64 needs 7 bits of significand) for the bf16 path.
+template <typename T> struct DigitStore;
+template <> struct DigitStore<int8_t> {
+    static __device__ __forceinline__ uint32_t bits(int8_t d) { return static_cast<uint8_t>(d); }
+    static constexpr int kBits = 8;
+};
+template <> struct DigitStore<uint16_t> {
+    static __device__ __forceinline__ uint32_t bits(int8_t d)
+    {
+        return __bfloat16_as_ushort(__float2bfloat16_rn(static_cast<float>(d)));
+    }
+    static constexpr int kBits = 16;
+};
+
+// Four consecutive digits packed little-endian and stored at out (4 * sizeof(T) bytes).
+template <typename T>
+__device__ __forceinline__ void store4(T* out, int8_t d0, int8_t d1, int8_t d2, int8_t d3)
+{
+    if constexpr (sizeof(T) == 1) {
+        *reinterpret_cast<uint32_t*>(out) = DigitStore<T>::bits(d0) | (DigitStore<T>::bits(d1) << 8) |
+                                            (DigitStore<T>::bits(d2) << 16) | (DigitStore<T>::bits(d3) << 24);
+    } else {
+        uint2 v;
+        v.x = DigitStore<T>::bits(d0) | (DigitStore<T>::bits(d1) << 16);
+        v.y = DigitStore<T>::bits(d2) | (DigitStore<T>::bits(d3) << 16);
+        *reinterpret_cast<uint2*>(out) = v;
+    }
+}
+
+// Rows of the sliced operand are contiguous in memory (element (r, p) at
+// base[r*ld + p]).  One thread per 4 consecutive p; rows up to `rows_pad`,
+// columns up to kp, zero outside [rows) x [len).
+template <int P>
+struct Planes {
+    const double* c[P];
+};
+
+// The digit cursor of element `off` of the component planes.
+template <int P> struct CursorOf { using T = WideCursor; };
+template <> struct CursorOf<2> { using T = DigitCursor; };
+
+template <int P>
+__device__ __forceinline__ typename CursorOf<P>::T element_cursor(const Planes<P>& pl, int64_t off, int sigma, int S)
+{
+    if constexpr (P == 2) {
+        return ozaki_cursor(pl.c[0][off], pl.c[1][off], sigma, S);
+    } else {
+        double c[P];
+#pragma unroll
+        for (int i = 0; i < P; ++i) c[i] = pl.c[i][off];
+        return ozaki_cursor_wide<P>(c, sigma, S);
+    }
+}
+// A cursor whose digits are all zero (padding).
+template <int P>
+__device__ __forceinline__ typename CursorOf<P>::T zero_cursor()
+{
+    typename CursorOf<P>::T c;
+    if constexpr (P == 2) {
+        c.hi = 0;
+        c.lo = 0;
+        c.sticky = false;
+    } else {
+#pragma unroll
+        for (int i = 0; i < kWideWords; ++i) c.w[i] = 0;
+    }
+    return c;
+}
+
+// KIND 0: the slicing form's digits (S of them); KIND 1: the CRT form's
+// residues (S moduli, beta bits per scaled entry).
+// KIND 1, 2, 3: residues with 12, 8 or 4 limbs (beta up to 192, 128, 64 bits);
+// KIND 4, 5: split integers (2N planes: A1's residues, then A0's) with 8 or
+// 12 limbs per half (w = beta / 2 up to 128 or 192 bits).
+template <int P, int KIND> struct KindCursor { using T = typename CursorOf<P>::T; };
+template <int P> struct KindCursor<P, 1> { using T = ResidueCursor<12>; };
+template <int P> struct KindCursor<P, 2> { using T = ResidueCursor<8>; };
+template <int P> struct KindCursor<P, 3> { using T = ResidueCursor<4>; };
+template <int P> struct KindCursor<P, 4> { using T = SplitResidueCursor<8>; };
+template <int P> struct KindCursor<P, 5> { using T = SplitResidueCursor<12>; };
+constexpr int residue_kind(int beta, int halves = 1)
+{
+    return halves == 2 ? (beta / 2 <= 128 ? 4 : 5) : (beta <= 64 ? 3 : beta <= 128 ? 2 : 1);
+}
+
+template <int P, int KIND>
+__device__ __forceinline__ typename KindCursor<P, KIND>::T make_cursor(const Planes<P>& pl, int64_t off, bool valid,
+                                                                      int sigma, int S, int beta)
+{
+    if constexpr (KIND == 0) {
+        return valid ? element_cursor<P>(pl, off, sigma, S) : zero_cursor<P>();
+    } else if constexpr (KIND <= 3) {
+        double c[P];
+#pragma unroll
+        for (int i = 0; i < P; ++i) c[i] = valid ? pl.c[i][off] : 0.0;
+        return residue_cursor<KIND == 1 ? 12 : KIND == 2 ? 8 : 4, P>(c, sigma, beta);
+    } else {
+        double c[P];
+#pragma unroll
+        for (int i = 0; i < P; ++i) c[i] = valid ? pl.c[i][off] : 0.0;
+        return split_residue_cursor<KIND == 4 ? 8 : 12, P>(c, sigma, beta, S / 2);
+    }
+}
+
+template <int P, typename T, int KIND = 0>
+__global__ void ozaki_slice_rows(const Planes<P> pl, int64_t rows, int64_t len, int64_t ld,
+                                 const int* __restrict__ sig, int S, int64_t rows_pad, int64_t kp,
+                                 T* __restrict__ out, int beta = 0)
+{
+    const int64_t quads = kp / 4;
+    const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= rows_pad * quads) return;
+    const int64_t r = t / quads;
+    const int64_t p0 = (t % quads) * 4;
+    const int sg = r < rows ? sig[r] : 0;
+    typename KindCursor<P, KIND>::T cur[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int64_t p = p0 + u;
+        cur[u] = make_cursor<P, KIND>(pl, r * ld + p, r < rows && p < len, sg, S, beta);
+    }
+    T* o = out + r * kp + p0;
+    const int64_t plane = rows_pad * kp;
+    for (int s = 0; s < S; ++s, o += plane) {
+        const int d0 = cur[0].next(), d1 = cur[1].next(), d2 = cur[2].next(), d3 = cur[3].next();
+        store4(o, static_cast<int8_t>(d0), static_cast<int8_t>(d1), static_cast<int8_t>(d2), static_cast<int8_t>(d3));
+    }
+}
+
+// Rows of the sliced operand are strided (element (r, p) at base[p*ld + r]):
+// a 32 x 32 tile is read with r fastest, sliced, transposed through shared
+// memory and written with p fastest.
+template <int P, typename T, int KIND = 0>
+__global__ void __launch_bounds__(256)
+ozaki_slice_cols(const Planes<P> pl, int64_t rows, int64_t len, int64_t ld,
+                 const int* __restrict__ sig, int S, int64_t rows_pad, int64_t kp,
+                 T* __restrict__ out, int beta = 0)
+{
+    constexpr int CHUNK = 16;               // digits (residues) staged per pass
+    __shared__ int8_t tile[CHUNK][32][36];
+    const int64_t r0 = static_cast<int64_t>(blockIdx.x) * 32;
+    const int64_t p0 = static_cast<int64_t>(blockIdx.y) * 32;
+    const int tr = threadIdx.x & 31;        // r within the tile
+    const int tp = threadIdx.x >> 5;        // 0..7: p = tp, tp + 8, tp + 16, tp + 24
+    const int64_t r = r0 + tr;
+    const int sg = r < rows ? sig[r] : 0;
+    typename KindCursor<P, KIND>::T cur[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int64_t p = p0 + tp + 8 * u;
+        cur[u] = make_cursor<P, KIND>(pl, p * ld + r, r < rows && p < len, sg, S, beta);
+    }
+    // write: each thread writes 4 consecutive p of one row r
+    const int wr = threadIdx.x >> 3;        // 0..31 row within tile
+    const int wq = (threadIdx.x & 7) * 4;   // p offset
+    const int64_t row = r0 + wr;
+    for (int s0 = 0; s0 < S; s0 += CHUNK) {
+        const int cnt = S - s0 < CHUNK ? S - s0 : CHUNK;
+        for (int s = 0; s < cnt; ++s) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) tile[s][tr][tp + 8 * u] = static_cast<int8_t>(cur[u].next());
+        }
+        __syncthreads();
+        if (row < rows_pad && p0 + wq < kp) {
+            for (int s = 0; s < cnt; ++s)
+                store4(out + (static_cast<int64_t>(s0 + s) * rows_pad + row) * kp + p0 + wq, tile[s][wr][wq],
+                       tile[s][wr][wq + 1], tile[s][wr][wq + 2], tile[s][wr][wq + 3]);
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------- cp.async and mma.sync
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__device__ __forceinline__ void mma_s8(int (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// ------------------------------------------------------- tcgen05 helpers
+
+namespace tc {
+constexpr int BM = 128;
+constexpr int KE = 64;                                   // box width in bf16 elements (128 bytes)
+constexpr int KB = 2;                                    // boxes per stage: 128 values of k
+constexpr int STAGES = 3;
+constexpr int A_BYTES = BM * KE * 2;                     // one A box, 16 KB
+constexpr int SEG_STAGES = 2048 / (KE * KB);             // stages per fp32 segment
+static_assert(KPAD % (KE * KB) == 0, "stage k");
+constexpr int TMEM_COLS = 512;
+constexpr unsigned long long TIMEOUT_NS = 1000000000ull;
+
+// Tile of TD and QD: TMEM holds two sets of two BN-column fp32 accumulators
+// (one per weight of a block) and BN group sums of GW 32-bit words each
+// (4 BN + GW BN <= 512).  A stage holds one A slice tile and the B slice tiles
+// of the block's (at most) two weights.
+template <int P> struct Cfg {
+    static_assert(P == 3 || P == 4, "DD runs on CTA pairs");
+    static constexpr int BN = 64;
+    static constexpr int GW = 4;
+    static constexpr int B_BYTES = BN * KE * 2;                   // one B box, 8 KB
+    static constexpr int A_STAGE = KB * A_BYTES;                  // 32 KB
+    static constexpr int B_STAGE = KB * B_BYTES;                  // 16 KB per weight
+    static constexpr int STAGE_BYTES = A_STAGE + 2 * B_STAGE;     // 64 KB
+    static constexpr int SET_COLS = 2 * BN;                  // accumulator sets at columns 0 and 2 BN
+    static constexpr int GRP_COL = 4 * BN;
+    static_assert(GRP_COL + GW * BN <= TMEM_COLS, "TMEM columns");
+    // instruction descriptor: kind::f16, bf16 A and B (K-major), fp32 D, M = 128, N = BN
+    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
+                                      ((static_cast<uint32_t>(BN) >> 3) << 17) | ((128u >> 4) << 24);
+};
+}  // namespace tc
+
+struct TcArgs {
+    const int* sig;
+    const int* tau;
+    double* C[4];
+    int64_t ldc, m, n, kp;
+    int S, tiles_m, tiles_n;
+    int* err;
+    long long* scratch;     // CTA-pair engine: per CTA, two [BN][BM] buffers of finished group sums
+    int test_abort;         // test of the abort path: the producer gives up before its first load
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// try_wait with a suspend-time hint in ns.  Measured on GB300 in the MMA
+// thread: any hint, against none, frees about 100 cycles per stage.
+template <unsigned HINT>
+__device__ __forceinline__ bool mbar_try_hint(uint64_t* b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity), "r"(HINT)
+        : "memory");
+    return ok != 0;
+}
+constexpr unsigned kHintIssue = 20;        // waits of the MMA-issuing thread
+constexpr unsigned kHintIdle = 10000;      // waits of the producer and the epilogue
+// Bounded wait: false after about a second, or once another role aborted.
+template <unsigned HINT>
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, volatile int* abort_flag)
+{
+    if (mbar_try_hint<HINT>(b, parity)) return true;      // the common case reads no clock
+    const unsigned long long t0 = gtimer();
+    while (!mbar_try_hint<HINT>(b, parity)) {
+        if (*abort_flag) return false;
+        if (gtimer() - t0 > tc::TIMEOUT_NS) return false;
+    }
+    return true;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr)
+{
+    return static_cast<uint64_t>((saddr & 0x3FFFF) >> 4) | (1ull << 16) |
+           (static_cast<uint64_t>(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
+__device__ __forceinline__ void umma(uint32_t d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(d), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_u32(bar)) : "memory");
+}
+#define MPG_R32(r) "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), \
+    "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), \
+    "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), \
+    "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+#define MPG_W32(r) "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), \
+    "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), \
+    "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), \
+    "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+// 32 consecutive 32-bit TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : MPG_R32(r)
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
+        ::"r"(taddr), MPG_W32(r)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// A group sum as GW little-endian 32-bit TMEM words.
+template <typename T, int GW>
+__device__ __forceinline__ T group_load(const uint32_t* w)
+{
+    unsigned __int128 u = 0;
+#pragma unroll
+    for (int i = GW - 1; i >= 0; --i) u = (u << 32) | w[i];
+    return static_cast<T>(u);
+}
+template <typename T, int GW>
+__device__ __forceinline__ void group_store(uint32_t* w, T v)
+{
+#pragma unroll
+    for (int i = 0; i < GW; ++i) w[i] = static_cast<uint32_t>(v >> (32 * i));
+}
+
+// ------------------------------------------------------------------ host
+
+static int64_t round_up(int64_t x, int64_t r) { return (x + r - 1) / r * r; }
+
+static unsigned blocks_for(int64_t threads, int per) { return static_cast<unsigned>((threads + per - 1) / per); }
+
+// Slice one operand: vectors (rows of op(A) or columns of op(B)) of length
+// len; `contig` says whether a vector's elements are adjacent in memory.
+template <int P, typename T, int KIND = 0>
+static cudaError_t slice_operand(const Planes<P>& pl, int64_t count, int64_t len, int64_t ld,
+                                 bool contig, int S, int64_t count_pad, int64_t kp, T* out,
+                                 int* sig, cudaStream_t s, int beta = 0)
+{
+    const double* lead = pl.c[0];
+    if (contig) ozaki_scale_contig<<<blocks_for(count * 32, 256), 256, 0, s>>>(lead, count, len, ld, sig);
+    else ozaki_scale_strided<<<blocks_for(count, 32), 1024, 0, s>>>(lead, count, len, ld, sig);
+    if (count_pad > count)
+        ozaki_fill_int<<<blocks_for(count_pad - count, 256), 256, 0, s>>>(sig, count, count_pad);
+    if (contig) {
+        ozaki_slice_rows<P, T, KIND><<<blocks_for(count_pad * (kp / 4), 128), 128, 0, s>>>(
+            pl, count, len, ld, sig, S, count_pad, kp, out, beta);
+    } else {
+        const dim3 grid(static_cast<unsigned>(count_pad / 32), static_cast<unsigned>(kp / 32));
+        ozaki_slice_cols<P, T, KIND><<<grid, 256, 0, s>>>(pl, count, len, ld, sig, S, count_pad, kp, out, beta);
+    }
+    return cudaGetLastError();
+}
+
+// A second stream for slicing op(B) while op(A) is sliced on the caller's
+// stream (the two are independent and neither fills the GPU alone), with the
+// events that fork it from and join it back to the caller's stream, so the
+// call stays ordered on that stream and can be captured into a CUDA graph.
+// One set per host thread and device: concurrent callers never share events.
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    unsigned long long ctx = 0;     // the context they were created in
+    ~SideStream()
+    {
+        // at thread exit; errors (e.g. a runtime already unloaded) are moot
+        if (join) cudaEventDestroy(join);
+        if (fork) cudaEventDestroy(fork);
+        if (s) cudaStreamDestroy(s);
+    }
+};
+
+// The calling thread's side stream and events on the current device
+// (created on first use; one set per host thread and device).
+cudaError_t side_stream(SideStream** out);
+
+// Slices op(A) on stream s and op(B) on the side stream, joined back to s.
+template <int P, typename T, int KIND = 0>
+static cudaError_t slice_both(const GemmArgs<P>& g, int S, const OzakiLayout& L, T* sa, T* sb, int* sig,
+                              int* tau, cudaStream_t s, int beta = 0)
+{
+    Planes<P> pa, pb;
+    for (int c = 0; c < P; ++c) {
+        pa.c[c] = g.A[c];
+        pb.c[c] = g.B[c];
+    }
+    SideStream* ss = nullptr;
+    cudaError_t e = side_stream(&ss);
+    if (e == cudaSuccess) e = cudaEventRecord(ss->fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ss->s, ss->fork, 0);
+    // op(A) row i: contiguous unless A is stored transposed; op(B) column j:
+    // contiguous only if B is stored transposed
+    if (e == cudaSuccess)
+        e = slice_operand<P, T, KIND>(pb, g.n, g.k, g.ldb, g.trans_b != 0, S, L.np, L.kp, sb, tau, ss->s, beta);
+    if (e == cudaSuccess) e = cudaEventRecord(ss->join, ss->s);
+    if (e == cudaSuccess)
+        e = slice_operand<P, T, KIND>(pa, g.m, g.k, g.lda, !g.trans_a, S, L.mp, L.kp, sa, sig, s, beta);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ss->join, 0);
+    return e;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
+{
+    static std::mutex mu;
+    static EncodeTiledFn fn = nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// A [S][rows][kp] bf16 slice array as a 3-D TMA tensor; boxes of 64 (k) x
+// box_rows x 1, 128-byte swizzle (the UMMA K-major layout).
+static bool slice_map(CUtensorMap* map, void* base, int S, int64_t rows, int64_t kp, int box_rows)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {static_cast<cuuint64_t>(kp), static_cast<cuuint64_t>(rows),
+                                static_cast<cuuint64_t>(S)};
+    const cuuint64_t strides[2] = {static_cast<cuuint64_t>(kp) * 2, static_cast<cuuint64_t>(rows * kp) * 2};
+    const cuuint32_t box[3] = {tc::KE, static_cast<cuuint32_t>(box_rows), 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Test of the tcgen05 engines' abort path: with MPGEMM_TEST_TC_ABORT=1 in the
+// environment the producer gives up before issuing any load, as if its first
+// bounded wait had run out; every other role then finds the abort flag with
+// nothing in flight, the kernel releases TMEM and returns, and the workspace
+// header holds code 1 (C is not computed).
+static int tc_test_abort()
+{
+    const char* v = getenv("MPGEMM_TEST_TC_ABORT");
+    return v && v[0] == '1' && v[1] == '\0';
+}
+
+}  // namespace mpg
