@@ -796,8 +796,10 @@ static cudaError_t crt_residues(const GemmArgs<P>& g, int N, int halves, const O
                                 int* sig, int* tau, cudaStream_t s, int beta)
 {
     switch (residue_kind(beta, halves)) {
+    case 7: return slice_both<P, T, 7>(g, 2 * N, L, ra, rb, sig, tau, s, beta);
+    case 6: return slice_both<P, T, 6>(g, 2 * N, L, ra, rb, sig, tau, s, beta);
     case 5: return slice_both<P, T, 5>(g, 2 * N, L, ra, rb, sig, tau, s, beta);
-    case 4: return slice_both<P, T, 4>(g, 2 * N, L, ra, rb, sig, tau, s, beta);
+    case 4: return slice_both<P, T, 4>(g, N, L, ra, rb, sig, tau, s, beta);
     case 3: return slice_both<P, T, 3>(g, N, L, ra, rb, sig, tau, s, beta);
     case 2: return slice_both<P, T, 2>(g, N, L, ra, rb, sig, tau, s, beta);
     default: return slice_both<P, T, 1>(g, N, L, ra, rb, sig, tau, s, beta);

@@ -258,8 +258,8 @@ struct Tables {
     int m[kMaxModuli];                            // 256, 255, 253, 251, 247, ...
     uint32_t magic[kMaxModuli];                   // floor(2^32 / m) + 1
     uint32_t pw16[kMaxModuli][kLimbs];            // 2^(16 j) mod m_i
-    uint32_t pm[kMaxModuli][kMaxModuli];          // (m_0 ... m_(j-1)) mod m_i, j < i
-    uint32_t inv[kMaxModuli];                     // (m_0 ... m_(i-1))^-1 mod m_i
+    uint32_t big[kMaxModuli];                     // m_i ceil(2^28 / m_i): a multiple of m_i above every limb sum
+    uint32_t half[kMaxModuli];                    // floor(m_i / 2)
 };
 
 constexpr int gcd_c(int a, int b)
@@ -291,15 +291,8 @@ constexpr Tables make_tables()
             t.pw16[i][j] = p;
             p = static_cast<uint32_t>((static_cast<uint64_t>(p) << 16) % m);
         }
-        uint32_t q = 1 % m;
-        for (int j = 0; j < i; ++j) {
-            t.pm[i][j] = q;
-            q = static_cast<uint32_t>((static_cast<uint64_t>(q) * static_cast<uint32_t>(t.m[j])) % m);
-        }
-        uint32_t inv = 0;
-        for (uint32_t x = 1; x < m; ++x)
-            if ((static_cast<uint64_t>(q) * x) % m == 1) { inv = x; break; }
-        t.inv[i] = i == 0 ? 1 % m : inv;
+        t.big[i] = m * (((1u << 28) + m - 1) / m);
+        t.half[i] = m / 2;
     }
     return t;
 }
@@ -318,27 +311,6 @@ __device__ __forceinline__ uint32_t mod_small(uint32_t x, int i)
     return static_cast<uint32_t>(r < 0 ? r + static_cast<int>(m) : r);
 }
 }  // namespace crt
-
-// Residues of one scaled entry, one modulus per next(): the symmetric
-// representative of A' mod m_i, i = 0, 1, ...  NL 16-bit limbs hold |A'|
-// (|A'| <= 2^(beta - 1): NL = 4, 8 or 12 for beta up to 64, 128, 192).
-template <int NL>
-struct ResidueCursor {
-    uint32_t limb[NL];                // |A'| in 16-bit limbs, least significant first
-    bool neg;
-    int idx;
-    __device__ __forceinline__ int next()
-    {
-        const int i = idx++;
-        uint32_t s = 0;
-#pragma unroll
-        for (int j = 0; j < NL; ++j) s += limb[j] * crt::kDev.pw16[i][j];
-        const int m = crt::kDev.m[i];
-        int r = static_cast<int>(crt::mod_small(s, i));
-        if (neg && r) r = m - r;
-        return r >= (m + 1) / 2 ? r - m : r;
-    }
-};
 
 // A' of the P components: each floored at 2^(sigma - beta - 64), summed
 // exactly in 384 bits, rounded to the nearest integer (ties to even) in units
@@ -375,34 +347,78 @@ __device__ __forceinline__ void scaled_integer(const double (&c)[P], int sigma, 
     }
 }
 
-// The residue cursor of a two's-complement integer: its sign and magnitude
-// in NL 16-bit limbs.
+// The magnitude of a scaled integer in NL 16-bit limbs (one per 32-bit
+// register, least significant first) and its sign.
 template <int NL>
-__device__ __forceinline__ ResidueCursor<NL> cursor_of(uint64_t (&I)[kWideWords - 1])
+struct ResLimbs {
+    uint32_t l[NL];
+    bool neg;
+};
+
+template <int NL>
+__device__ __forceinline__ ResLimbs<NL> limbs_of(uint64_t (&I)[kWideWords - 1])
 {
-    ResidueCursor<NL> cur;
-    cur.neg = (I[kWideWords - 2] >> 63) != 0;
-    if (cur.neg) {                                   // magnitude: two's complement negation
+    ResLimbs<NL> x;
+    x.neg = (I[kWideWords - 2] >> 63) != 0;
+    if (x.neg) {                                     // magnitude: two's complement negation
         uint64_t cc = 1;
 #pragma unroll
         for (int i = 0; i < kWideWords - 1; ++i) {
-            const uint64_t s = ~I[i] + cc;
-            cc = (cc && s == 0) ? 1ull : 0ull;
-            I[i] = s;
+            const uint64_t v = ~I[i] + cc;
+            cc = (cc && v == 0) ? 1ull : 0ull;
+            I[i] = v;
         }
     }
 #pragma unroll
-    for (int j = 0; j < NL; ++j) cur.limb[j] = static_cast<uint32_t>(I[j / 4] >> (16 * (j % 4))) & 0xffffu;
-    cur.idx = 0;
-    return cur;
+    for (int j = 0; j < NL; ++j) x.l[j] = static_cast<uint32_t>(I[j / 4] >> (16 * (j % 4))) & 0xffffu;
+    return x;
+}
+
+// The constants of modulus i, read once per plane and shared by the
+// thread's elements.
+template <int NL>
+struct ModConst {
+    uint32_t pw[NL];                                 // 2^(16 j) mod m
+    uint32_t m, magic, big, half;
+};
+
+template <int NL>
+__device__ __forceinline__ ModConst<NL> mod_const(int i)
+{
+    ModConst<NL> k;
+#pragma unroll
+    for (int j = 0; j < NL; ++j) k.pw[j] = crt::kDev.pw16[i][j];
+    k.m = static_cast<uint32_t>(crt::kDev.m[i]);
+    k.magic = crt::kDev.magic[i];
+    k.big = crt::kDev.big[i];
+    k.half = crt::kDev.half[i];
+    return k;
+}
+
+// The symmetric residue of (-1)^neg sum_j l_j 2^(16 j) modulo m, in
+// [-floor(m/2), ceil(m/2) - 1]: s = sum_j l_j (2^(16 j) mod m) < 12 2^24,
+// made nonnegative as big - s for a negative integer, shifted by floor(m/2)
+// and reduced by one Barrett step (the estimate is the quotient or one more,
+// and the unsigned minimum of r and r + m keeps the one in [0, m)).
+template <int NL>
+__device__ __forceinline__ int sym_residue(const ResLimbs<NL>& x, const ModConst<NL>& k)
+{
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < NL; ++j) s += x.l[j] * k.pw[j];
+    s = x.neg ? k.big - s : s;
+    const uint32_t t = s + k.half;
+    const uint32_t r0 = t - __umulhi(t, k.magic) * k.m;
+    const uint32_t r1 = r0 + k.m;
+    return static_cast<int>(r0 < r1 ? r0 : r1) - static_cast<int>(k.half);
 }
 
 template <int NL, int P>
-__device__ __forceinline__ ResidueCursor<NL> residue_cursor(const double (&c)[P], int sigma, int beta)
+__device__ __forceinline__ void residue_limbs(const double (&c)[P], int sigma, int beta, ResLimbs<NL>& hi)
 {
     uint64_t I[kWideWords - 1];
     scaled_integer<P>(c, sigma, beta, I);
-    return cursor_of<NL>(I);
+    hi = limbs_of<NL>(I);
 }
 
 // Word q of a five-word two's-complement integer, its sign beyond the top.
@@ -414,18 +430,11 @@ __device__ __forceinline__ uint64_t word_at(const uint64_t (&x)[kWideWords - 1],
     return r;
 }
 
-// Split integers: residues of A1 for moduli 0..N-1, then of A0, where
-// A' = A1 2^w + A0 with A0 in [-2^(w-1), 2^(w-1)).
-template <int NL>
-struct SplitResidueCursor {
-    ResidueCursor<NL> hi, lo;
-    int n, idx;
-    __device__ __forceinline__ int next() { return idx++ < n ? hi.next() : lo.next(); }
-};
-
+// Split integers: A' = A1 2^w + A0 with A0 in [-2^(w-1), 2^(w-1)); hi gets
+// A1, lo gets A0 (w = beta / 2).
 template <int NL, int P>
-__device__ __forceinline__ SplitResidueCursor<NL> split_residue_cursor(const double (&c)[P], int sigma, int beta,
-                                                                       int n)
+__device__ __forceinline__ void split_limbs(const double (&c)[P], int sigma, int beta, ResLimbs<NL>& hi,
+                                            ResLimbs<NL>& lo)
 {
     constexpr int WW = kWideWords - 1;
     uint64_t I[WW];
@@ -454,12 +463,8 @@ __device__ __forceinline__ SplitResidueCursor<NL> split_residue_cursor(const dou
         const uint64_t a = word_at(D, k + wi), b = word_at(D, k + wi + 1);
         A1[k] = wb ? (a >> wb) | (b << (64 - wb)) : a;
     }
-    SplitResidueCursor<NL> cur;
-    cur.hi = cursor_of<NL>(A1);
-    cur.lo = cursor_of<NL>(A0);
-    cur.n = n;
-    cur.idx = 0;
-    return cur;
+    hi = limbs_of<NL>(A1);
+    lo = limbs_of<NL>(A0);
 }
 
 // ------------------------------------------------------------------ scale
@@ -527,9 +532,12 @@ template <> struct DigitStore<int8_t> {
     static constexpr int kBits = 8;
 };
 template <> struct DigitStore<uint16_t> {
+    // |d| <= 128 is exact in binary32 (1.5 2^23 + d, less 1.5 2^23) and in
+    // bf16, whose bits are then the upper half of the binary32's
     static __device__ __forceinline__ uint32_t bits(int8_t d)
     {
-        return __bfloat16_as_ushort(__float2bfloat16_rn(static_cast<float>(d)));
+        const float f = __int_as_float(0x4B400000 + static_cast<int>(d)) - 12582912.0f;
+        return __float_as_uint(f) >> 16;
     }
     static constexpr int kBits = 16;
 };
@@ -589,39 +597,52 @@ __device__ __forceinline__ typename CursorOf<P>::T zero_cursor()
     return c;
 }
 
-// KIND 0: the slicing form's digits (S of them); KIND 1: the CRT form's
-// residues (S moduli, beta bits per scaled entry).
-// KIND 1, 2, 3: residues with 12, 8 or 4 limbs (beta up to 192, 128, 64 bits);
-// KIND 4, 5: split integers (2N planes: A1's residues, then A0's) with 8 or
-// 12 limbs per half (w = beta / 2 up to 128 or 192 bits).
-template <int P, int KIND> struct KindCursor { using T = typename CursorOf<P>::T; };
-template <int P> struct KindCursor<P, 1> { using T = ResidueCursor<12>; };
-template <int P> struct KindCursor<P, 2> { using T = ResidueCursor<8>; };
-template <int P> struct KindCursor<P, 3> { using T = ResidueCursor<4>; };
-template <int P> struct KindCursor<P, 4> { using T = SplitResidueCursor<8>; };
-template <int P> struct KindCursor<P, 5> { using T = SplitResidueCursor<12>; };
+// KIND 0: the slicing form's digits (S of them).  KIND >= 1: the CRT
+// form's residues, one plane per modulus, from the magnitude of each scaled
+// integer in NL 16-bit limbs: KIND 1-4 one integer (S = N planes) with
+// NL = 6, 8, 10, 12 (beta up to 96, 128, 160, 192 bits); KIND 5-7 split
+// integers (S = 2N planes: A1's residues, then A0's) with NL = 6, 8, 12 per
+// half (w = beta / 2 up to 96, 128, 192 bits).
+constexpr int kind_limbs(int kind)
+{
+    return kind == 1 || kind == 5 ? 6 : kind == 2 || kind == 6 ? 8 : kind == 3 ? 10 : 12;
+}
+constexpr bool kind_split(int kind) { return kind >= 5; }
 constexpr int residue_kind(int beta, int halves = 1)
 {
-    return halves == 2 ? (beta / 2 <= 128 ? 4 : 5) : (beta <= 64 ? 3 : beta <= 128 ? 2 : 1);
+    if (halves == 2) return beta / 2 <= 96 ? 5 : beta / 2 <= 128 ? 6 : 7;
+    return beta <= 96 ? 1 : beta <= 128 ? 2 : beta <= 160 ? 3 : 4;
 }
 
 template <int P, int KIND>
-__device__ __forceinline__ typename KindCursor<P, KIND>::T make_cursor(const Planes<P>& pl, int64_t off, bool valid,
-                                                                      int sigma, int S, int beta)
+__device__ __forceinline__ typename CursorOf<P>::T make_cursor(const Planes<P>& pl, int64_t off, bool valid,
+                                                               int sigma, int S)
 {
-    if constexpr (KIND == 0) {
-        return valid ? element_cursor<P>(pl, off, sigma, S) : zero_cursor<P>();
-    } else if constexpr (KIND <= 3) {
-        double c[P];
+    return valid ? element_cursor<P>(pl, off, sigma, S) : zero_cursor<P>();
+}
+
+// The limbs of element `off` (zero when not valid): hi, and lo with split
+// integers.
+template <int P, int KIND>
+__device__ __forceinline__ void make_limbs(const Planes<P>& pl, int64_t off, bool valid, int sigma, int beta,
+                                           ResLimbs<kind_limbs(KIND)>& hi, ResLimbs<kind_limbs(KIND)>& lo)
+{
+    constexpr int NL = kind_limbs(KIND);
+    double c[P];
 #pragma unroll
-        for (int i = 0; i < P; ++i) c[i] = valid ? pl.c[i][off] : 0.0;
-        return residue_cursor<KIND == 1 ? 12 : KIND == 2 ? 8 : 4, P>(c, sigma, beta);
-    } else {
-        double c[P];
-#pragma unroll
-        for (int i = 0; i < P; ++i) c[i] = valid ? pl.c[i][off] : 0.0;
-        return split_residue_cursor<KIND == 4 ? 8 : 12, P>(c, sigma, beta, S / 2);
-    }
+    for (int i = 0; i < P; ++i) c[i] = valid ? pl.c[i][off] : 0.0;
+    if constexpr (kind_split(KIND)) split_limbs<NL, P>(c, sigma, beta, hi, lo);
+    else residue_limbs<NL, P>(c, sigma, beta, hi);
+}
+
+// Plane s of the residues: modulus i of A1 (or of the one integer) for
+// s < N, of A0 for s >= N with split integers.
+template <int KIND>
+__device__ __forceinline__ void residue_plane(int s, int S, int& i, bool& second)
+{
+    const int n = kind_split(KIND) ? S / 2 : S;
+    second = kind_split(KIND) && s >= n;
+    i = second ? s - n : s;
 }
 
 template <int P, typename T, int KIND = 0>
@@ -635,17 +656,44 @@ __global__ void ozaki_slice_rows(const Planes<P> pl, int64_t rows, int64_t len, 
     const int64_t r = t / quads;
     const int64_t p0 = (t % quads) * 4;
     const int sg = r < rows ? sig[r] : 0;
-    typename KindCursor<P, KIND>::T cur[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int64_t p = p0 + u;
-        cur[u] = make_cursor<P, KIND>(pl, r * ld + p, r < rows && p < len, sg, S, beta);
-    }
     T* o = out + r * kp + p0;
     const int64_t plane = rows_pad * kp;
-    for (int s = 0; s < S; ++s, o += plane) {
-        const int d0 = cur[0].next(), d1 = cur[1].next(), d2 = cur[2].next(), d3 = cur[3].next();
-        store4(o, static_cast<int8_t>(d0), static_cast<int8_t>(d1), static_cast<int8_t>(d2), static_cast<int8_t>(d3));
+    if constexpr (KIND == 0) {
+        typename CursorOf<P>::T cur[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t p = p0 + u;
+            cur[u] = make_cursor<P, KIND>(pl, r * ld + p, r < rows && p < len, sg, S);
+        }
+        for (int s = 0; s < S; ++s, o += plane) {
+            const int d0 = cur[0].next(), d1 = cur[1].next(), d2 = cur[2].next(), d3 = cur[3].next();
+            store4(o, static_cast<int8_t>(d0), static_cast<int8_t>(d1), static_cast<int8_t>(d2),
+                   static_cast<int8_t>(d3));
+        }
+    } else {
+        constexpr int NL = kind_limbs(KIND);
+        ResLimbs<NL> hi[4], lo[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t p = p0 + u;
+            make_limbs<P, KIND>(pl, r * ld + p, r < rows && p < len, sg, beta, hi[u], lo[u]);
+        }
+        for (int s = 0; s < S; ++s, o += plane) {
+            int i;
+            bool second;
+            residue_plane<KIND>(s, S, i, second);
+            const ModConst<NL> k = mod_const<NL>(i);
+            int d[4];
+            if (second) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) d[u] = sym_residue<NL>(lo[u], k);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) d[u] = sym_residue<NL>(hi[u], k);
+            }
+            store4(o, static_cast<int8_t>(d[0]), static_cast<int8_t>(d[1]), static_cast<int8_t>(d[2]),
+                   static_cast<int8_t>(d[3]));
+        }
     }
 }
 
@@ -666,22 +714,11 @@ ozaki_slice_cols(const Planes<P> pl, int64_t rows, int64_t len, int64_t ld,
     const int tp = threadIdx.x >> 5;        // 0..7: p = tp, tp + 8, tp + 16, tp + 24
     const int64_t r = r0 + tr;
     const int sg = r < rows ? sig[r] : 0;
-    typename KindCursor<P, KIND>::T cur[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int64_t p = p0 + tp + 8 * u;
-        cur[u] = make_cursor<P, KIND>(pl, p * ld + r, r < rows && p < len, sg, S, beta);
-    }
     // write: each thread writes 4 consecutive p of one row r
     const int wr = threadIdx.x >> 3;        // 0..31 row within tile
     const int wq = (threadIdx.x & 7) * 4;   // p offset
     const int64_t row = r0 + wr;
-    for (int s0 = 0; s0 < S; s0 += CHUNK) {
-        const int cnt = S - s0 < CHUNK ? S - s0 : CHUNK;
-        for (int s = 0; s < cnt; ++s) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) tile[s][tr][tp + 8 * u] = static_cast<int8_t>(cur[u].next());
-        }
+    auto flush = [&](int s0, int cnt) {
         __syncthreads();
         if (row < rows_pad && p0 + wq < kp) {
             for (int s = 0; s < cnt; ++s)
@@ -689,6 +726,47 @@ ozaki_slice_cols(const Planes<P> pl, int64_t rows, int64_t len, int64_t ld,
                        tile[s][wr][wq + 1], tile[s][wr][wq + 2], tile[s][wr][wq + 3]);
         }
         __syncthreads();
+    };
+    if constexpr (KIND == 0) {
+        typename CursorOf<P>::T cur[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t p = p0 + tp + 8 * u;
+            cur[u] = make_cursor<P, KIND>(pl, p * ld + r, r < rows && p < len, sg, S);
+        }
+        for (int s0 = 0; s0 < S; s0 += CHUNK) {
+            const int cnt = S - s0 < CHUNK ? S - s0 : CHUNK;
+            for (int s = 0; s < cnt; ++s) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) tile[s][tr][tp + 8 * u] = static_cast<int8_t>(cur[u].next());
+            }
+            flush(s0, cnt);
+        }
+    } else {
+        constexpr int NL = kind_limbs(KIND);
+        ResLimbs<NL> hi[4], lo[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t p = p0 + tp + 8 * u;
+            make_limbs<P, KIND>(pl, p * ld + r, r < rows && p < len, sg, beta, hi[u], lo[u]);
+        }
+        for (int s0 = 0; s0 < S; s0 += CHUNK) {
+            const int cnt = S - s0 < CHUNK ? S - s0 : CHUNK;
+            for (int s = 0; s < cnt; ++s) {
+                int i;
+                bool second;
+                residue_plane<KIND>(s0 + s, S, i, second);
+                const ModConst<NL> k = mod_const<NL>(i);
+                if (second) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) tile[s][tr][tp + 8 * u] = static_cast<int8_t>(sym_residue<NL>(lo[u], k));
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) tile[s][tr][tp + 8 * u] = static_cast<int8_t>(sym_residue<NL>(hi[u], k));
+                }
+            }
+            flush(s0, cnt);
+        }
     }
 }
 
