@@ -178,6 +178,7 @@ __global__ void __launch_bounds__(WM * WN * 32) crt_gemm_kernel(const CrtGemmArg
 
 namespace crt {
 constexpr int kRecLimbs = 11;                     // M < 2^352
+constexpr int kRecGroups = (kMaxModuli + 3) / 4;  // moduli in groups of four
 }
 
 struct CrtRecArgs {
@@ -191,9 +192,14 @@ struct CrtRecArgs {
     uint32_t M[crt::kRecLimbs];          // the product of the moduli
     uint32_t H[crt::kRecLimbs];          // ceil(M / 2)
     uint32_t F[crt::kRecLimbs];          // floor(M / 2)
-    // the CRT weights W_i = (M / m_i) c_i, c_i = (M / m_i)^-1 mod m_i
-    uint32_t W[crt::kMaxModuli][crt::kRecLimbs];
-    float f[crt::kMaxModuli];             // c_i / m_i
+    uint32_t M16[2 * crt::kRecLimbs];     // M in 16-bit limbs (one per word)
+    uint32_t K16[2 * crt::kRecLimbs + 1]; // 128 sum_i W_i in 16-bit limbs (the bias of the residues)
+    int64_t KF;                          // 128 sum_i floor(2^24 c_i / m_i)
+    // the CRT weights W_i = (M / m_i) c_i, c_i = (M / m_i)^-1 mod m_i, as bytes:
+    // byte t of Wd[g][j] is byte j of W_(4g+t) (zero for 4g + t >= N)
+    uint32_t Wd[crt::kRecGroups][4 * crt::kRecLimbs];
+    // likewise the three bytes of floor(2^24 c_i / m_i)
+    uint32_t Fd[crt::kRecGroups][3];
 };
 
 constexpr int kRecThreads = 256;
@@ -351,43 +357,66 @@ __device__ __forceinline__ void round_components(const LimbCol& z, const LimbMas
 // The centred integer of one product (its residues r_i at res[i * plane],
 // i < N) as L limbs of two's complement.  NB: N rounded up to a multiple of
 // 8 (the unrolled bound of the loops); L = NB / 4 limbs, at most 11, hold M.
+// The residues, biased to r_i + 128 in [0, 256) (the top bit of each byte
+// flipped) and four to a register, meet the bytes of the CRT weights in
+// dot products of four (dp4a): column j sums (r_i + 128) byte_j(W_i) over the
+// moduli (below 13 * 4 * 255 * 255 < 2^22), so sum_j col_j 2^(8j) - K, with
+// K = 128 sum_i W_i, is S = sum_i r_i W_i, congruent to A'B' modulo M.  Three
+// more columns against the bytes of floor(2^24 c_i / m_i) give 2^24 S / M to
+// within 49 * 128 units, whence q = floor(S / M + 1/2) up to one either way.
+// The columns, paired into 16-bit columns less K and q M, are carried into
+// limbs, and one addition or subtraction of M centres the result.  Residues
+// of moduli i >= N (up to NB) are read from plane N - 1 and meet zero
+// weights.
 template <int NB, int L>
 __device__ __forceinline__ void crt_centred(const CrtRecArgs& g, const int8_t* res, int64_t plane, int N,
                                             uint32_t (&Z)[L])
 {
-    int r8[NB];
+    constexpr int G = NB / 4;
+    constexpr int D = 4 * L;
+    uint32_t r4[G];
+    const uint8_t* rp = reinterpret_cast<const uint8_t*>(res);
 #pragma unroll
-    for (int i = 0; i < NB; ++i) r8[i] = i < N ? static_cast<int>(res[i * plane]) : 0;
-    uint64_t S[L + 1];
+    for (int q4 = 0; q4 < G; ++q4) {
+        uint32_t v = 0;
 #pragma unroll
-    for (int k = 0; k <= L; ++k) S[k] = 0ull;
-    float qf = 0.5f;
+        for (int t = 0; t < 4; ++t) {
+            v |= static_cast<uint32_t>(*rp) << (8 * t);
+            if (4 * q4 + t + 1 < N) rp += plane;
+        }
+        r4[q4] = v ^ 0x80808080u;
+    }
+    unsigned S[D], Q[3] = {0u, 0u, 0u};
 #pragma unroll
-    for (int i = 0; i < NB; ++i) {
-        if (i < N) {
-            const int mi = crt::kDev.m[i];
-            const uint32_t ru = static_cast<uint32_t>(r8[i] < 0 ? r8[i] + mi : r8[i]);
+    for (int j = 0; j < D; ++j) S[j] = 0u;
 #pragma unroll
-            for (int k = 0; k < L; ++k) S[k] += static_cast<uint64_t>(g.W[i][k]) * ru;
-            qf = __fmaf_rn(static_cast<float>(ru), g.f[i], qf);
+    for (int q4 = 0; q4 < G; ++q4) {
+        if (4 * q4 < N) {
+#pragma unroll
+            for (int j = 0; j < D; ++j) S[j] = __dp4a(r4[q4], g.Wd[q4][j], S[j]);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) Q[j] = __dp4a(r4[q4], g.Fd[q4][j], Q[j]);
         }
     }
-    // S as L + 1 limbs (S < 2^14 M), minus q M
-    const uint32_t q = static_cast<uint32_t>(floorf(qf));
+    const int64_t qfix = static_cast<int64_t>(Q[0]) + (static_cast<int64_t>(Q[1]) << 8) +
+                         (static_cast<int64_t>(Q[2]) << 16) - g.KF + (1ll << 23);
+    const int q = static_cast<int>(qfix >> 24);
+    // 16-bit columns of S - q M (|.| < 2^31), carried into L + 1 limbs
     uint32_t X[L + 1];
-    uint64_t carry = 0, mc = 0;
-    int64_t borrow = 0;
+    int carry = 0;
 #pragma unroll
-    for (int k = 0; k <= L; ++k) {
-        const uint64_t v = S[k] + carry;
-        carry = v >> 32;
-        const uint64_t pm = static_cast<uint64_t>(k < L ? g.M[k] : 0u) * q + mc;
-        mc = pm >> 32;
-        const int64_t d = static_cast<int64_t>(static_cast<uint32_t>(v)) -
-                          static_cast<int64_t>(static_cast<uint32_t>(pm)) + borrow;
-        X[k] = static_cast<uint32_t>(d);
-        borrow = d >> 32;
+    for (int k = 0; k <= 2 * L; ++k) {
+        const int c = (k < 2 * L ? static_cast<int>(S[2 * k] + S[2 * k + 1] * 256u) -
+                                       q * static_cast<int>(g.M16[k])
+                                 : 0) -
+                      static_cast<int>(g.K16[k]);
+        const int v = c + carry;
+        carry = v >> 16;                               // arithmetic: floor
+        const uint32_t u = static_cast<uint32_t>(v) & 0xffffu;
+        if (k & 1) X[k >> 1] |= u << 16;
+        else X[k >> 1] = u;
     }
+    X[L] |= static_cast<uint32_t>(carry) << 16;        // the sign above
     // X in [-3M/2, 3M/2): X >= ceil(M/2) -> X - M; X < -floor(M/2) -> X + M
     int64_t b1 = 0, b2 = 0;
 #pragma unroll
@@ -400,8 +429,7 @@ __device__ __forceinline__ void crt_centred(const CrtRecArgs& g, const int8_t* r
         b2 = d2 >> 32;
     }
     const bool ge = b1 >= 0, lt = b2 < 0;              // the signs of X - H and X + F
-    const uint32_t cin = ge ? 1u : 0u;                 // X - M = X + ~M + 1
-    uint64_t c2 = cin;
+    uint64_t c2 = ge ? 1u : 0u;                        // X - M = X + ~M + 1
 #pragma unroll
     for (int k = 0; k < L; ++k) {
         const uint32_t mk = g.M[k];
@@ -884,7 +912,8 @@ static cudaError_t crt_recover(const GemmArgs<P>& g, int N, int beta, int halves
         ra_.F[k] = static_cast<uint32_t>(d);
         bw = d >> 32;
     }
-    // W_i = (M / m_i) c_i with c_i the inverse of (M / m_i) mod m_i
+    for (int k = 0; k < 2 * crt::kRecLimbs; ++k) ra_.M16[k] = (ra_.M[k / 2] >> (16 * (k % 2))) & 0xffffu;
+    // W_i = (M / m_i) c_i with c_i the inverse of (M / m_i) mod m_i, as bytes
     for (int i = 0; i < N; ++i) {
         const uint64_t mi = static_cast<uint64_t>(crt::kHost.m[i]);
         uint32_t Q[crt::kRecLimbs];
@@ -901,12 +930,26 @@ static cudaError_t crt_recover(const GemmArgs<P>& g, int N, int beta, int halves
             if ((qm * x) % mi == 1) { c = x; break; }
         if (mi == 1) c = 0;
         uint64_t carry = 0;
+        const int grp = i / 4, sh = 8 * (i % 4);
+        uint32_t Wfull[crt::kRecLimbs];
         for (int k = 0; k < crt::kRecLimbs; ++k) {
             const uint64_t v = static_cast<uint64_t>(Q[k]) * c + carry;
-            ra_.W[i][k] = static_cast<uint32_t>(v);
+            const uint32_t w = static_cast<uint32_t>(v);
+            Wfull[k] = w;
             carry = v >> 32;
+            for (int t = 0; t < 4; ++t) ra_.Wd[grp][4 * k + t] |= ((w >> (8 * t)) & 0xffu) << sh;
         }
-        ra_.f[i] = static_cast<float>(static_cast<double>(c) / static_cast<double>(mi));
+        const uint32_t fr = static_cast<uint32_t>((c << 24) / mi);     // floor(2^24 c / m_i) < 2^24
+        for (int t = 0; t < 3; ++t) ra_.Fd[grp][t] |= ((fr >> (8 * t)) & 0xffu) << sh;
+        ra_.KF += 128 * static_cast<int64_t>(fr);
+        // K += 128 W_i in 16-bit limbs
+        uint64_t kc = 0;
+        for (int k = 0; k < 2 * crt::kRecLimbs + 1; ++k) {
+            const uint32_t w16 = k / 2 < crt::kRecLimbs ? (Wfull[k / 2] >> (16 * (k % 2))) & 0xffffu : 0u;
+            const uint64_t v = static_cast<uint64_t>(ra_.K16[k]) + 128ull * w16 + kc;
+            ra_.K16[k] = static_cast<uint32_t>(v & 0xffffu);
+            kc = v >> 16;
+        }
     }
     const unsigned grid = blocks_for(g.m * g.n, kRecThreads);         // one output per thread
     if (grid == 0) return cudaSuccess;
