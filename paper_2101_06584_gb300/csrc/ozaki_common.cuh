@@ -313,15 +313,37 @@ __device__ __forceinline__ uint32_t mod_small(uint32_t x, int i)
 }  // namespace crt
 
 // A' of the P components: each floored at 2^(sigma - beta - 64), summed
-// exactly in 384 bits, rounded to the nearest integer (ties to even) in units
-// of 2^(sigma - beta); in two's complement, five 64-bit words, least
-// significant first (beta <= 316).
-template <int P>
-__device__ __forceinline__ void scaled_integer(const double (&c)[P], int sigma, int beta, uint64_t (&I)[kWideWords - 1])
+// exactly in WW 64-bit words (64 fraction bits below the unit 2^(sigma - beta)),
+// rounded to the nearest integer (ties to even); in two's complement, WW - 1
+// words, least significant first.  WW is the fewest words that hold the
+// beta-bit integer with its sign and the fraction word (3 for beta <= 96 up to
+// 6 for beta <= 316).
+template <int WW>
+__device__ __forceinline__ void wide_add_shifted_n(uint64_t (&W)[WW], int64_t M, int sh)
 {
-    Wide W;
+    const int wi = sh >> 6, bo = sh & 63;
+    const uint64_t ext = M < 0 ? ~0ull : 0ull;
+    const uint64_t lo = static_cast<uint64_t>(M) << bo;
+    const uint64_t hi = bo == 0 ? ext : static_cast<uint64_t>(M >> (64 - bo));
+    uint64_t carry = 0;
 #pragma unroll
-    for (int i = 0; i < kWideWords; ++i) W.w[i] = 0ull;
+    for (int i = 0; i < WW; ++i) {
+        const uint64_t b = i < wi ? 0ull : (i == wi ? lo : (i == wi + 1 ? hi : ext));
+        const uint64_t s1 = W[i] + b;
+        const uint64_t c1 = s1 < b;
+        const uint64_t s2 = s1 + carry;
+        const uint64_t c2 = s2 < s1;
+        W[i] = s2;
+        carry = c1 | c2;
+    }
+}
+
+template <int P, int WW>
+__device__ __forceinline__ void scaled_integer(const double (&c)[P], int sigma, int beta, uint64_t (&I)[WW - 1])
+{
+    uint64_t W[WW];
+#pragma unroll
+    for (int i = 0; i < WW; ++i) W[i] = 0ull;
 #pragma unroll
     for (int i = 0; i < P; ++i) {
         int64_t M;
@@ -329,21 +351,19 @@ __device__ __forceinline__ void scaled_integer(const double (&c)[P], int sigma, 
         decompose(c[i], M, e);
         if (M == 0) continue;
         const int sh = e - sigma + beta + kGuardBits;
-        if (sh >= 0) wide_add_shifted(W, M, sh);
-        else if (sh > -64) wide_add_small(W, M >> (-sh));      // arithmetic shift: floor
-        else wide_add_small(W, M < 0 ? -1 : 0);
+        if (sh >= 0) wide_add_shifted_n<WW>(W, M, sh);
+        else if (sh > -64) wide_add_shifted_n<WW>(W, M >> (-sh), 0);      // arithmetic shift: floor
+        else wide_add_shifted_n<WW>(W, M < 0 ? -1 : 0, 0);
     }
-    // integer part (words 1..5, floor) and the fraction in word 0
-    const uint64_t f = W.w[0];
-    const bool up = f > (1ull << 63) || (f == (1ull << 63) && (W.w[1] & 1ull));
-#pragma unroll
-    for (int i = 0; i < kWideWords - 1; ++i) I[i] = W.w[i + 1];
+    // integer part (words 1.., floor) and the fraction in word 0
+    const uint64_t f = W[0];
+    const bool up = f > (1ull << 63) || (f == (1ull << 63) && (W[1] & 1ull));
     uint64_t carry = up ? 1ull : 0ull;
 #pragma unroll
-    for (int i = 0; i < kWideWords - 1; ++i) {
-        const uint64_t s = I[i] + carry;
-        carry = (carry && s == 0) ? 1ull : 0ull;
-        I[i] = s;
+    for (int i = 0; i < WW - 1; ++i) {
+        const uint64_t v = W[i + 1] + carry;
+        carry = (carry && v == 0) ? 1ull : 0ull;
+        I[i] = v;
     }
 }
 
@@ -355,15 +375,16 @@ struct ResLimbs {
     bool neg;
 };
 
-template <int NL>
-__device__ __forceinline__ ResLimbs<NL> limbs_of(uint64_t (&I)[kWideWords - 1])
+template <int NL, int WI>
+__device__ __forceinline__ ResLimbs<NL> limbs_of(uint64_t (&I)[WI])
 {
+    static_assert(NL <= 4 * WI, "limbs beyond the integer");
     ResLimbs<NL> x;
-    x.neg = (I[kWideWords - 2] >> 63) != 0;
+    x.neg = (I[WI - 1] >> 63) != 0;
     if (x.neg) {                                     // magnitude: two's complement negation
         uint64_t cc = 1;
 #pragma unroll
-        for (int i = 0; i < kWideWords - 1; ++i) {
+        for (int i = 0; i < WI; ++i) {
             const uint64_t v = ~I[i] + cc;
             cc = (cc && v == 0) ? 1ull : 0ull;
             I[i] = v;
@@ -413,36 +434,37 @@ __device__ __forceinline__ int sym_residue(const ResLimbs<NL>& x, const ModConst
     return static_cast<int>(r0 < r1 ? r0 : r1) - static_cast<int>(k.half);
 }
 
-template <int NL, int P>
+template <int NL, int P, int WW>
 __device__ __forceinline__ void residue_limbs(const double (&c)[P], int sigma, int beta, ResLimbs<NL>& hi)
 {
-    uint64_t I[kWideWords - 1];
-    scaled_integer<P>(c, sigma, beta, I);
-    hi = limbs_of<NL>(I);
+    uint64_t I[WW - 1];
+    scaled_integer<P, WW>(c, sigma, beta, I);
+    hi = limbs_of<NL, WW - 1>(I);
 }
 
-// Word q of a five-word two's-complement integer, its sign beyond the top.
-__device__ __forceinline__ uint64_t word_at(const uint64_t (&x)[kWideWords - 1], int q)
+// Word q of a WI-word two's-complement integer, its sign beyond the top.
+template <int WI>
+__device__ __forceinline__ uint64_t word_at(const uint64_t (&x)[WI], int q)
 {
-    uint64_t r = (x[kWideWords - 2] >> 63) ? ~0ull : 0ull;
+    uint64_t r = (x[WI - 1] >> 63) ? ~0ull : 0ull;
 #pragma unroll
-    for (int k = 0; k < kWideWords - 1; ++k) r = (k == q) ? x[k] : r;
+    for (int k = 0; k < WI; ++k) r = (k == q) ? x[k] : r;
     return r;
 }
 
 // Split integers: A' = A1 2^w + A0 with A0 in [-2^(w-1), 2^(w-1)); hi gets
 // A1, lo gets A0 (w = beta / 2).
-template <int NL, int P>
+template <int NL, int P, int WWS>
 __device__ __forceinline__ void split_limbs(const double (&c)[P], int sigma, int beta, ResLimbs<NL>& hi,
                                             ResLimbs<NL>& lo)
 {
-    constexpr int WW = kWideWords - 1;
+    constexpr int WW = WWS - 1;
     uint64_t I[WW];
-    scaled_integer<P>(c, sigma, beta, I);
+    scaled_integer<P, WWS>(c, sigma, beta, I);
     const int w = beta / 2;
     // A0: the low w bits, sign-extended from bit w - 1
     const int wi = w >> 6, wb = w & 63;
-    const bool low_neg = (word_at(I, (w - 1) >> 6) >> ((w - 1) & 63)) & 1ull;
+    const bool low_neg = (word_at<WW>(I, (w - 1) >> 6) >> ((w - 1) & 63)) & 1ull;
     uint64_t A0[WW], D[WW];
 #pragma unroll
     for (int k = 0; k < WW; ++k) {
@@ -460,11 +482,11 @@ __device__ __forceinline__ void split_limbs(const double (&c)[P], int sigma, int
     uint64_t A1[WW];
 #pragma unroll
     for (int k = 0; k < WW; ++k) {
-        const uint64_t a = word_at(D, k + wi), b = word_at(D, k + wi + 1);
+        const uint64_t a = word_at<WW>(D, k + wi), b = word_at<WW>(D, k + wi + 1);
         A1[k] = wb ? (a >> wb) | (b << (64 - wb)) : a;
     }
-    hi = limbs_of<NL>(A1);
-    lo = limbs_of<NL>(A0);
+    hi = limbs_of<NL, WW>(A1);
+    lo = limbs_of<NL, WW>(A0);
 }
 
 // ------------------------------------------------------------------ scale
@@ -608,6 +630,11 @@ constexpr int kind_limbs(int kind)
     return kind == 1 || kind == 5 ? 6 : kind == 2 || kind == 6 ? 8 : kind == 3 ? 10 : 12;
 }
 constexpr bool kind_split(int kind) { return kind >= 5; }
+// 64-bit words of the exact sum of the components (fraction word included)
+constexpr int kind_words(int kind)
+{
+    return kind == 1 ? 3 : kind <= 3 ? 4 : kind <= 5 ? 5 : 6;
+}
 constexpr int residue_kind(int beta, int halves = 1)
 {
     if (halves == 2) return beta / 2 <= 96 ? 5 : beta / 2 <= 128 ? 6 : 7;
@@ -631,8 +658,8 @@ __device__ __forceinline__ void make_limbs(const Planes<P>& pl, int64_t off, boo
     double c[P];
 #pragma unroll
     for (int i = 0; i < P; ++i) c[i] = valid ? pl.c[i][off] : 0.0;
-    if constexpr (kind_split(KIND)) split_limbs<NL, P>(c, sigma, beta, hi, lo);
-    else residue_limbs<NL, P>(c, sigma, beta, hi);
+    if constexpr (kind_split(KIND)) split_limbs<NL, P, kind_words(KIND)>(c, sigma, beta, hi, lo);
+    else residue_limbs<NL, P, kind_words(KIND)>(c, sigma, beta, hi);
 }
 
 // Plane s of the residues: modulus i of A1 (or of the one integer) for
