@@ -257,7 +257,7 @@ struct Tables {
     int count;
     int m[kMaxModuli];                            // 256, 255, 253, 251, 247, ...
     uint32_t magic[kMaxModuli];                   // floor(2^32 / m) + 1
-    uint32_t pw16[kMaxModuli][kLimbs];            // 2^(16 j) mod m_i
+    uint32_t pw8[kMaxModuli][kLimbs / 2];         // byte t of word w: 2^(8 (4w + t)) mod m_i
     uint32_t big[kMaxModuli];                     // m_i ceil(2^28 / m_i): a multiple of m_i above every limb sum
     uint32_t half[kMaxModuli];                    // floor(m_i / 2)
 };
@@ -286,10 +286,14 @@ constexpr Tables make_tables()
     for (int i = 0; i < n; ++i) {
         const uint32_t m = static_cast<uint32_t>(t.m[i]);
         t.magic[i] = static_cast<uint32_t>((1ull << 32) / m + 1);
-        uint32_t p = 1;
-        for (int j = 0; j < kLimbs; ++j) {
-            t.pw16[i][j] = p;
-            p = static_cast<uint32_t>((static_cast<uint64_t>(p) << 16) % m);
+        for (int w = 0; w < kLimbs / 2; ++w) {
+            uint32_t word = 0;
+            for (int b = 0; b < 4; ++b) {
+                uint32_t v = 1 % m;
+                for (int e = 0; e < 4 * w + b; ++e) v = static_cast<uint32_t>((static_cast<uint64_t>(v) << 8) % m);
+                word |= v << (8 * b);
+            }
+            t.pw8[i][w] = word;
         }
         t.big[i] = m * (((1u << 28) + m - 1) / m);
         t.half[i] = m / 2;
@@ -367,18 +371,18 @@ __device__ __forceinline__ void scaled_integer(const double (&c)[P], int sigma, 
     }
 }
 
-// The magnitude of a scaled integer in NL 16-bit limbs (one per 32-bit
-// register, least significant first) and its sign.
+// The magnitude of a scaled integer as NL / 2 32-bit words (NL 16-bit limbs),
+// least significant first, and its sign.
 template <int NL>
 struct ResLimbs {
-    uint32_t l[NL];
+    uint32_t l[NL / 2];
     bool neg;
 };
 
 template <int NL, int WI>
 __device__ __forceinline__ ResLimbs<NL> limbs_of(uint64_t (&I)[WI])
 {
-    static_assert(NL <= 4 * WI, "limbs beyond the integer");
+    static_assert(NL % 2 == 0 && NL <= 4 * WI, "limbs beyond the integer");
     ResLimbs<NL> x;
     x.neg = (I[WI - 1] >> 63) != 0;
     if (x.neg) {                                     // magnitude: two's complement negation
@@ -391,7 +395,7 @@ __device__ __forceinline__ ResLimbs<NL> limbs_of(uint64_t (&I)[WI])
         }
     }
 #pragma unroll
-    for (int j = 0; j < NL; ++j) x.l[j] = static_cast<uint32_t>(I[j / 4] >> (16 * (j % 4))) & 0xffffu;
+    for (int j = 0; j < NL / 2; ++j) x.l[j] = static_cast<uint32_t>(I[j / 2] >> (32 * (j % 2)));
     return x;
 }
 
@@ -399,7 +403,7 @@ __device__ __forceinline__ ResLimbs<NL> limbs_of(uint64_t (&I)[WI])
 // thread's elements.
 template <int NL>
 struct ModConst {
-    uint32_t pw[NL];                                 // 2^(16 j) mod m
+    uint32_t pw[NL / 2];                             // bytes 2^(8 j) mod m, four to a word
     uint32_t m, magic, big, half;
 };
 
@@ -408,7 +412,7 @@ __device__ __forceinline__ ModConst<NL> mod_const(int i)
 {
     ModConst<NL> k;
 #pragma unroll
-    for (int j = 0; j < NL; ++j) k.pw[j] = crt::kDev.pw16[i][j];
+    for (int j = 0; j < NL / 2; ++j) k.pw[j] = crt::kDev.pw8[i][j];
     k.m = static_cast<uint32_t>(crt::kDev.m[i]);
     k.magic = crt::kDev.magic[i];
     k.big = crt::kDev.big[i];
@@ -416,17 +420,18 @@ __device__ __forceinline__ ModConst<NL> mod_const(int i)
     return k;
 }
 
-// The symmetric residue of (-1)^neg sum_j l_j 2^(16 j) modulo m, in
-// [-floor(m/2), ceil(m/2) - 1]: s = sum_j l_j (2^(16 j) mod m) < 12 2^24,
-// made nonnegative as big - s for a negative integer, shifted by floor(m/2)
-// and reduced by one Barrett step (the estimate is the quotient or one more,
-// and the unsigned minimum of r and r + m keeps the one in [0, m)).
+// The symmetric residue of (-1)^neg sum_j b_j 2^(8 j) modulo m (b_j the bytes
+// of the magnitude), in [-floor(m/2), ceil(m/2) - 1]: s = sum_j b_j (2^(8 j)
+// mod m), four bytes at a time (dp4a; s < 24 * 255 * 255 < 2^21), made
+// nonnegative as big - s for a negative integer, shifted by floor(m/2) and
+// reduced by one Barrett step (the estimate is the quotient or one more, and
+// the unsigned minimum of r and r + m keeps the one in [0, m)).
 template <int NL>
 __device__ __forceinline__ int sym_residue(const ResLimbs<NL>& x, const ModConst<NL>& k)
 {
     uint32_t s = 0;
 #pragma unroll
-    for (int j = 0; j < NL; ++j) s += x.l[j] * k.pw[j];
+    for (int j = 0; j < NL / 2; ++j) s = __dp4a(x.l[j], k.pw[j], s);
     s = x.neg ? k.big - s : s;
     const uint32_t t = s + k.half;
     const uint32_t r0 = t - __umulhi(t, k.magic) * k.m;
