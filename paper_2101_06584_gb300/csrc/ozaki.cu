@@ -759,106 +759,6 @@ constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((static_cast<ui
                            ((256u >> 4) << 24);
 }  // namespace tc2
 
-__device__ __forceinline__ uint32_t cluster_rank()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ uint32_t cluster_index()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ uint32_t cluster_count()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
-    return r;
-}
-// The shared::cluster address of the same variable in CTA `rank` of the cluster.
-__device__ __forceinline__ uint32_t cluster_addr(const void* p, uint32_t rank)
-{
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
-    return r;
-}
-__device__ __forceinline__ void cluster_sync_all()
-{
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__device__ __forceinline__ bool mbar_try_cl(uint64_t* b, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-template <unsigned HINT>
-__device__ __forceinline__ bool mbar_try_cl_hint(uint64_t* b, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(b)), "r"(parity), "r"(HINT)
-        : "memory");
-    return ok != 0;
-}
-template <unsigned HINT>
-__device__ __forceinline__ bool mbar_wait_cl(uint64_t* b, unsigned parity, volatile int* abort_flag)
-{
-    if (mbar_try_cl_hint<HINT>(b, parity)) return true;
-    const unsigned long long t0 = gtimer();
-    while (!mbar_try_cl_hint<HINT>(b, parity)) {
-        if (*abort_flag) return false;
-        if (gtimer() - t0 > tc::TIMEOUT_NS) return false;
-    }
-    return true;
-}
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t caddr)
-{
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
-}
-__device__ __forceinline__ void st_cluster(uint32_t caddr, int v)
-{
-    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(caddr), "r"(v) : "memory");
-}
-__device__ __forceinline__ void tma_load_3d_pair(void* dst, const CUtensorMap* map, int x, int y, int z,
-                                                 uint32_t bar_caddr)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar_caddr)
-        : "memory");
-}
-__device__ __forceinline__ void umma_pair(uint32_t d, uint64_t da, uint64_t db, uint32_t acc)
-{
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-        ::"r"(d), "l"(da), "l"(db), "r"(tc2::IDESC), "r"(acc));
-}
-// Arrive on the barrier at this address in both CTAs once the MMAs issued so far complete.
-__device__ __forceinline__ void umma_commit_both(uint64_t* bar)
-{
-    asm volatile(
-        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
-        ::"r"(smem_u32(bar)), "h"(static_cast<uint16_t>(3)) : "memory");
-}
-__device__ __forceinline__ void umma_commit_pair_local(uint64_t* bar)
-{
-    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                 ::"r"(smem_u32(bar)) : "memory");
-}
-
 // Bounded wait until the shared counter reaches `target` (false after about a
 // second or once another role aborted).
 __device__ __forceinline__ bool wait_count(const volatile int* f, int target, volatile int* abort_flag)
@@ -1009,7 +909,7 @@ ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                         const uint64_t db = umma_desc(sa + tc2::KB * tc2::A_BOX + q * tc2::B_BOX);
 #pragma unroll
                         for (int kk = 0; kk < tc2::KE / 16; ++kk)
-                            umma_pair(tmem + b * tc2::ACC_COLS, da + 2ull * kk, db + 2ull * kk,
+                            umma_pair(tmem + b * tc2::ACC_COLS, da + 2ull * kk, db + 2ull * kk, tc2::IDESC,
                                       (seg_stages > 0 || q > 0 || kk > 0) ? 1u : 0u);
                     }
                     umma_commit_both(&empty[st]);
