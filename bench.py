@@ -600,7 +600,7 @@ class DdSmall(Workload):
                 "achieved": ach / 1e12, "peak": pk["dfma"] / 1e12, "unit": "TFP64op/s",
                 "frac": ach / pk["dfma"], "traffic": None, "ops_per_unit": 20,
                 "unit_of_work": "DD multiply-add", "units_per_launch": self.mads,
-                "note": "16K entries = 512 warps, at most 4 per SM; "
+                "note": "16K entries = 512 warps, one per SM sub-partition at most (FP64 floor 0.84 of peak); "
                         "warp split-K 8 (not k-sequential) runs at %.3g mad/s" % (self.mads / (ms * 1e-3))}
 
 

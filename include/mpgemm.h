@@ -453,7 +453,8 @@ int mpgemm_tile_info(int P, int id, int info[6]);
 
 /* The FP64-EFT tile id (1-based) that mpgemm_ex uses for an m x n x k product
  * when opts->tile is 0: of the candidates (binary64-only: 64x64, 32x32,
- * 16x16, 8x8; DD: 32x32, 16x16, 8x8; TD/QD: 16x16, 8x8), the first whose CTAs, dealt round-robin to the device's SMs,
+ * 16x16, 8x8; DD: 32x32, 16x16, 8x8 staging 128 values of k; TD/QD: 16x16, 8x8), the first whose CTAs,
+ * dealt round-robin to the device's SMs,
  * keep at least 90% of them busy -- ctas / (sms * ceil(ctas / sms)) -- else
  * the closest.  Uses the current device's SM count (152 when there is no
  * device).  MPG_EINVAL for an unknown P or a negative dimension. */
