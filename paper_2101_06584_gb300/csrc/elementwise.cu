@@ -129,10 +129,23 @@ eft_kernel(int64_t n, const double* a, const double* b, double* s,
     }
 }
 
-static unsigned grid_for(int64_t n)
+// Grid of a grid-stride kernel: enough blocks for n items of 256 threads,
+// at most the blocks that are resident on all SMs at once (from the
+// kernel's occupancy, looked up once per kernel), so every block stays
+// resident to the end and no second, partial wave leaves SM sub-partitions
+// without warps.  Each elementwise op is FP64-bound, and the FP64 pipe of a
+// sub-partition idles when it has no warp ready.
+template <typename K>
+static unsigned grid_for(K kernel, int64_t n)
 {
+    static int per_sm = 0;                 // one cache per kernel instantiation
+    if (per_sm == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, 256, 0) != cudaSuccess || b < 1) b = 1;
+        per_sm = b;
+    }
     int64_t blocks = (n + 255) / 256;
-    const int64_t cap = static_cast<int64_t>(num_sms()) * 8;
+    const int64_t cap = static_cast<int64_t>(num_sms()) * per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     return static_cast<unsigned>(blocks);
@@ -155,24 +168,23 @@ cudaError_t launch_vec(int op, int64_t n, const double* const* x, const double* 
             aligned = aligned && (reinterpret_cast<uintptr_t>(x[c]) | reinterpret_cast<uintptr_t>(y[c]) |
                                   reinterpret_cast<uintptr_t>(r[c])) % 16 == 0;
         if (aligned && (op == 0 || op == 1)) {
-            const unsigned grid4 = grid_for(n / 4 > 0 ? n / 4 : 1);
-            if (op == 0) vec_dd_x4_kernel<0><<<grid4, 256, 0, s>>>(a);
-            else vec_dd_x4_kernel<1><<<grid4, 256, 0, s>>>(a);
+            const int64_t q = n / 4 > 0 ? n / 4 : 1;
+            if (op == 0) vec_dd_x4_kernel<0><<<grid_for(vec_dd_x4_kernel<0>, q), 256, 0, s>>>(a);
+            else vec_dd_x4_kernel<1><<<grid_for(vec_dd_x4_kernel<1>, q), 256, 0, s>>>(a);
             return cudaGetLastError();
         }
     }
-    const unsigned grid = grid_for(n);
     // op codes: 0 add, 1 mul (the GEMM's pair for P); 2 TDadd (Alg. 3),
     // 3 TDmulq, 4 accurate TD product; 5 accurate QD addition
-    if (op == 0) vec_kernel<P, 0><<<grid, 256, 0, s>>>(a);
-    else if (op == 1) vec_kernel<P, 1><<<grid, 256, 0, s>>>(a);
+    if (op == 0) vec_kernel<P, 0><<<grid_for(vec_kernel<P, 0>, n), 256, 0, s>>>(a);
+    else if (op == 1) vec_kernel<P, 1><<<grid_for(vec_kernel<P, 1>, n), 256, 0, s>>>(a);
     else if constexpr (P == 3) {
-        if (op == 2) vec_kernel<P, 2><<<grid, 256, 0, s>>>(a);
-        else if (op == 3) vec_kernel<P, 3><<<grid, 256, 0, s>>>(a);
-        else if (op == 4) vec_kernel<P, 4><<<grid, 256, 0, s>>>(a);
+        if (op == 2) vec_kernel<P, 2><<<grid_for(vec_kernel<P, 2>, n), 256, 0, s>>>(a);
+        else if (op == 3) vec_kernel<P, 3><<<grid_for(vec_kernel<P, 3>, n), 256, 0, s>>>(a);
+        else if (op == 4) vec_kernel<P, 4><<<grid_for(vec_kernel<P, 4>, n), 256, 0, s>>>(a);
         else return cudaErrorInvalidValue;
     } else if constexpr (P == 4) {
-        if (op == 5) vec_kernel<P, 5><<<grid, 256, 0, s>>>(a);
+        if (op == 5) vec_kernel<P, 5><<<grid_for(vec_kernel<P, 5>, n), 256, 0, s>>>(a);
         else return cudaErrorInvalidValue;
     } else {
         return cudaErrorInvalidValue;
@@ -190,11 +202,10 @@ template cudaError_t launch_vec<4>(int, int64_t, const double* const*, const dou
 cudaError_t launch_eft(int which, int64_t n, const double* a, const double* b, double* s,
                        double* e, cudaStream_t st)
 {
-    const unsigned grid = grid_for(n);
     switch (which) {
-    case 0: eft_kernel<0><<<grid, 256, 0, st>>>(n, a, b, s, e); break;
-    case 1: eft_kernel<1><<<grid, 256, 0, st>>>(n, a, b, s, e); break;
-    case 2: eft_kernel<2><<<grid, 256, 0, st>>>(n, a, b, s, e); break;
+    case 0: eft_kernel<0><<<grid_for(eft_kernel<0>, n), 256, 0, st>>>(n, a, b, s, e); break;
+    case 1: eft_kernel<1><<<grid_for(eft_kernel<1>, n), 256, 0, st>>>(n, a, b, s, e); break;
+    case 2: eft_kernel<2><<<grid_for(eft_kernel<2>, n), 256, 0, st>>>(n, a, b, s, e); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
