@@ -111,7 +111,8 @@ def parse_args():
     ap.add_argument("--workload", default="td_qd",
                     choices=["td_qd", "dd_small", "dd_int8", "dd_tc", "dd_crt", "dd_crt_int8", "td_crt", "qd_crt",
                              "td_qd_int8", "td_qd_tc",
-                             "batched", "autograd", "elementwise", "strassen", "autograd_tc"])
+                             "batched", "autograd", "elementwise", "strassen", "autograd_tc",
+                             "autograd_crt"])
     ap.add_argument("--size", type=int, default=None, help="override the workload's m = n = k")
     ap.add_argument("--slices", type=int, default=None,
                     help="slice (or moduli) count of the DD slicing/CRT workloads instead of the search")
@@ -1147,10 +1148,39 @@ class AutogradTc(Autograd):
                 "unit_of_work": "DD multiply-add (%d slice-pair MACs)" % pairs, "units_per_launch": self.n ** 3}
 
 
+class AutogradCrt(Autograd):
+    """DDMatmul forward + backward on the tcgen05 CRT form, 26 moduli: at
+    k = 2048 that keeps 94 bits per scaled entry, so each gradient entry is
+    within n 2^-100 of its own |W| |B| dot product (23 moduli meet the
+    normwise bound at 4096^3 but not every entry's)."""
+    name = "autograd_crt"
+    MODULI = 26
+
+    def __init__(self, torch, mm, I, rank, n=2048):
+        super().__init__(torch, mm, I, rank, n=n)
+        from paper_2101_06584_gb300.autograd import dd_matmul
+        self.f = lambda A, B: dd_matmul(A, B, algo="crt_bf16", slices=self.MODULI)
+        # per product: header clear, scale and residues of both operands, the products, the recovery
+        self.launches_per_step = 3 * 7
+        self.config = dict(self.config, workload=self.config["workload"] + ", tcgen05 CRT form, %d moduli"
+                           % self.MODULI, engine="crt_tc", moduli=self.MODULI)
+
+    def roofline(self, launch_ms, pk):
+        N = self.MODULI
+        ms = statistics.mean(launch_ms["fwd"])
+        ach = 2.0 * N * self.n ** 3 / (ms * 1e-3)
+        peak, src = bf16_peak()
+        return {"bound": "tensor", "kernel": "crt_tc_kernel (forward call incl. residues and recovery)",
+                "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": ach / peak,
+                "peak_source": src, "traffic": None, "ops_per_unit": 2 * N,
+                "unit_of_work": "DD multiply-add (%d residue MACs)" % N, "units_per_launch": self.n ** 3}
+
+
 WORKLOADS = {"td_qd": TdQd, "dd_small": DdSmall, "dd_int8": DdInt8, "dd_tc": DdTc, "dd_crt": DdCrt,
              "dd_crt_int8": DdCrtInt8, "td_crt": TdCrt, "qd_crt": QdCrt,
              "td_qd_int8": TdQdInt8, "td_qd_tc": TdQdTc, "batched": Batched, "autograd": Autograd,
-             "elementwise": Elementwise, "strassen": Strassen, "autograd_tc": AutogradTc}
+             "elementwise": Elementwise, "strassen": Strassen, "autograd_tc": AutogradTc,
+             "autograd_crt": AutogradCrt}
 
 
 def host_of(t):
@@ -1314,7 +1344,7 @@ def extras(torch, mm, I, pk, flush):
     """One short measurement of each other workload (rank 0, after the main one)."""
     out = {}
     for name in ("dd_small", "dd_int8", "dd_tc", "dd_crt", "dd_crt_int8", "td_qd_int8", "td_qd_tc", "td_crt",
-                 "qd_crt", "batched", "autograd", "autograd_tc", "elementwise", "strassen"):
+                 "qd_crt", "batched", "autograd", "autograd_tc", "autograd_crt", "elementwise", "strassen"):
         w = WORKLOADS[name](torch, mm, I, 0)
         steps = {"dd_small": 10, "elementwise": 10, "strassen": 1}.get(name, 2)
         total_ms, launch_ms, _, _ = measure(torch, w, steps, 1, 1, 0, flush, sample_clocks=False)

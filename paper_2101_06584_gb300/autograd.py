@@ -11,9 +11,11 @@ operands (no transpose copies):
 By default each is the k-sequential DD product of Sec. 3, Eq. 1, so the
 gradients are bit-identical to that product evaluated anywhere.  With
 algo="bf16" (or "int8") the forward product and both gradients run the
-error-free slicing form on the tensor cores instead (the form defined in
-include/mpgemm.h): each is bit-identical to that form's steps on the same
-operands and within its DD error bound of the exact product.  The incoming
+error-free slicing form on the tensor cores instead, and with
+algo="crt_bf16" (or "crt") the CRT form, `slices` then counting moduli (the
+forms defined in include/mpgemm.h): each product is bit-identical to that
+form's steps on the same operands and within its DD error bound of the exact
+product.  The incoming
 gradient is itself a DD plane pair: for loss = sum(W * C), call C.backward(W).
 """
 import torch
@@ -53,8 +55,9 @@ class DDMatmul(torch.autograd.Function):
 
 def dd_matmul(A, B, algo="auto", slices=0):
     """C = A B in DD with gradients through the DD kernels (algo "auto" /
-    "fp64") or the slicing form on the tensor cores ("bf16", "int8"; slices
-    0 = the library's default)."""
+    "fp64"), the slicing form on the tensor cores ("bf16", "int8"; slices
+    0 = the library's default) or the CRT form ("crt_bf16", "crt"; slices =
+    moduli, 0 = the library's default)."""
     return DDMatmul.apply(A, B, algo, slices)
 
 
