@@ -515,21 +515,29 @@ static __global__ void ozaki_scale_contig(const double* __restrict__ hi, int64_t
     if (lane == 0) out[v] = mx ? ilogb_bits(mx) + 2 : 0;
 }
 
-// Vectors whose elements are ld apart (vectors adjacent): a block of 32 x 32
-// threads covers 32 vectors, each column of threads a 32-way split of the
-// elements (coalesced rows of 32 vectors), reduced in shared memory.
+// Vectors whose elements are ld apart (vectors adjacent): blocks of 32
+// vectors x 32 warps, each over one chunk of `rows` elements, so that the
+// grid covers the SMs even when the vectors are few (1024 columns are only
+// 32 blocks of all the rows).  A block's maximum per vector goes into
+// out[v] with an integer atomicMax as ilogb + 2 + kScaleBias (out zeroed
+// beforehand; 0 stays for an all-zero vector); ozaki_scale_decode removes
+// the bias.
+constexpr int kScaleBias = 4096;                   // above -(ilogb + 2) of any binary64
 static __global__ void __launch_bounds__(1024) ozaki_scale_strided(const double* __restrict__ hi, int64_t count,
-                                                           int64_t len, int64_t ld, int* __restrict__ out)
+                                                                    int64_t len, int64_t ld, int64_t rows,
+                                                                    int* __restrict__ out)
 {
     __shared__ unsigned long long smax[32];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int64_t v = static_cast<int64_t>(blockIdx.x) * 32 + tx;
+    const int64_t p0 = static_cast<int64_t>(blockIdx.y) * rows;
+    const int64_t p1 = p0 + rows < len ? p0 + rows : len;
     if (ty == 0) smax[tx] = 0;
     __syncthreads();
     uint64_t mx = 0;
     if (v < count) {
 #pragma unroll 4
-        for (int64_t p = ty; p < len; p += 32) {
+        for (int64_t p = p0 + ty; p < p1; p += 32) {
             const uint64_t b = abs_bits(hi[p * ld + v]);
             mx = b > mx ? b : mx;
         }
@@ -538,11 +546,19 @@ static __global__ void __launch_bounds__(1024) ozaki_scale_strided(const double*
     __syncthreads();
     if (ty == 0 && v < count) {
         const uint64_t m = smax[tx];
-        out[v] = m ? ilogb_bits(m) + 2 : 0;
+        if (m) atomicMax(out + v, ilogb_bits(m) + 2 + kScaleBias);
     }
 }
 
-// Zero the exponent padding [count, padded).
+// out[v] for v < count without the bias of ozaki_scale_strided; 0 for the
+// padding up to `padded`.
+static __global__ void ozaki_scale_decode(int* out, int64_t count, int64_t padded)
+{
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < count) out[i] = out[i] ? out[i] - kScaleBias : 0;
+    else if (i < padded) out[i] = 0;
+}
+
 static __global__ void ozaki_fill_int(int* out, int64_t from, int64_t to)
 {
     const int64_t i = from + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -1117,10 +1133,25 @@ static cudaError_t slice_operand(const Planes<P>& pl, int64_t count, int64_t len
                                  int* sig, cudaStream_t s, int beta = 0)
 {
     const double* lead = pl.c[0];
-    if (contig) ozaki_scale_contig<<<blocks_for(count * 32, 256), 256, 0, s>>>(lead, count, len, ld, sig);
-    else ozaki_scale_strided<<<blocks_for(count, 32), 1024, 0, s>>>(lead, count, len, ld, sig);
-    if (count_pad > count)
-        ozaki_fill_int<<<blocks_for(count_pad - count, 256), 256, 0, s>>>(sig, count, count_pad);
+    if (contig) {
+        ozaki_scale_contig<<<blocks_for(count * 32, 256), 256, 0, s>>>(lead, count, len, ld, sig);
+        if (count_pad > count)
+            ozaki_fill_int<<<blocks_for(count_pad - count, 256), 256, 0, s>>>(sig, count, count_pad);
+    } else {
+        // row chunks so that about two blocks per SM run
+        const int64_t col_blocks = (count + 31) / 32;
+        const int64_t want = col_blocks > 0 ? (2 * static_cast<int64_t>(num_sms()) + col_blocks - 1) / col_blocks : 1;
+        int64_t rows = (len + want - 1) / want;
+        rows = rows < 256 ? 256 : (rows + 31) / 32 * 32;
+        const int64_t chunks = len > 0 ? (len + rows - 1) / rows : 1;
+        if (chunks > 65535) return cudaErrorInvalidValue;
+        cudaError_t e = cudaMemsetAsync(sig, 0, static_cast<size_t>(count) * sizeof(int), s);
+        if (e != cudaSuccess) return e;
+        if (count > 0)
+            ozaki_scale_strided<<<dim3(static_cast<unsigned>(col_blocks), static_cast<unsigned>(chunks)), 1024, 0, s>>>(
+            lead, count, len, ld, rows, sig);
+        if (count_pad > 0) ozaki_scale_decode<<<blocks_for(count_pad, 256), 256, 0, s>>>(sig, count, count_pad);
+    }
     if (contig) {
         ozaki_slice_rows<P, T, KIND><<<blocks_for(count_pad * (kp / 4), 128), 128, 0, s>>>(
             pl, count, len, ld, sig, S, count_pad, kp, out, beta);
