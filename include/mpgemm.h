@@ -61,7 +61,8 @@ void *mpgemm_get_stream(void);
  * P = 1 in mpgemm_ex, mpgemm_num_tiles, mpgemm_tile_info and
  * mpgemm_default_tile; 103 adds MPG_ALGO_INT8_CRT, MPG_ALGO_BF16_CRT and
  * mpgemm_crt_beta; 104 adds MPG_ALGO_INT8_CRT_SPLIT, MPG_ALGO_BF16_CRT_SPLIT
- * and mpgemm_crt_split_beta. */
+ * and mpgemm_crt_split_beta; 105 adds mpgemm_autotune, mpgemm_tuned_tile and
+ * mpgemm_tune_cache_reset. */
 int mpgemm_version(void);
 
 /* ---------------------------------------------------------------------
@@ -410,7 +411,9 @@ int mpgemm_batch_plan_destroy(mpgemm_batch_plan *plan);
 
 /* Autotuner: build a plan for every policy, time `reps` graph replays of
  * each on the current stream (writing the problems' C), and return the
- * fastest policy and its time per run in milliseconds. */
+ * fastest policy and its time per run in milliseconds.  The choice is
+ * remembered for this exact list of shapes (see mpgemm_autotune): a later
+ * call for the same list returns it without measuring (and writes no C). */
 int mpgemm_batch_autotune(int P, int count, const mpgemm_problem *problems, void *workspace,
                           size_t workspace_bytes, int reps, int *best_policy, float *best_ms);
 
@@ -445,6 +448,35 @@ int mpgemm_dd_int8_static(int64_t m, int64_t n, int64_t k,
                           const double *const B[2], int64_t ldb,
                           double *const C[2], int64_t ldc, int slices);
 
+/* ---------------------------------------------------------------------
+ * Autotuner (no counterpart in the paper).  Every FP64-EFT tile gives the
+ * same k-sequential result, so the tile is a matter of speed and can be
+ * chosen by measurement.  mpgemm_autotune times every tile id on the caller's
+ * operands (`reps` calls each after one warm-up, CUDA events on the calling
+ * thread's stream, synchronising; C is written with the same result every
+ * time; not for use inside a stream capture), returns the fastest id and
+ * its time in milliseconds, and remembers it for the device (name and SM
+ * count), P and the shape's bucket: m, n and k each rounded up to a power of
+ * two.  mpgemm_ex with algo AUTO or FP64_EFT and tile 0 then takes the
+ * remembered tile of its bucket, before the rule of mpgemm_default_tile.
+ * Choices live in memory and, when the environment variable
+ * MPGEMM_TUNE_CACHE names a file, in that JSON file: read at the first
+ * lookup, rewritten (through a temporary file and a rename) after every new
+ * choice; lines that do not parse are ignored and a file that cannot be
+ * written leaves the choices in memory.  The same cache holds the policies
+ * of mpgemm_batch_autotune.  MPG_EINVAL when no tile can run the call (the
+ * message of the last tile's refusal is kept).
+ * ------------------------------------------------------------------- */
+int mpgemm_autotune(int P, int64_t m, int64_t n, int64_t k,
+                    const double *const *A, int64_t lda, const double *const *B, int64_t ldb,
+                    double *const *C, int64_t ldc, int reps, int *best_tile, float *best_ms);
+/* The remembered tile id (1-based) of the bucket of (P, m, n, k) on the
+ * current device, or 0 if there is none. */
+int mpgemm_tuned_tile(int P, int64_t m, int64_t n, int64_t k);
+/* Forget the choices in memory; the next lookup reads MPGEMM_TUNE_CACHE
+ * (as the environment then has it) again. */
+void mpgemm_tune_cache_reset(void);
+
 /* Number of FP64-EFT tile configurations for precision P (1..4), and a description
  * of configuration id (BM, BN, BK, TM, TN, threads); returns MPG_EINVAL for
  * an unknown id. */
@@ -452,7 +484,7 @@ int mpgemm_num_tiles(int P);
 int mpgemm_tile_info(int P, int id, int info[6]);
 
 /* The FP64-EFT tile id (1-based) that mpgemm_ex uses for an m x n x k product
- * when opts->tile is 0: of the candidates (binary64-only: 64x64, 32x32,
+ * when opts->tile is 0 and the autotuner remembers none: of the candidates (binary64-only: 64x64, 32x32,
  * 16x16, 8x8; DD: 32x32, 16x16, 8x8 staging 128 values of k; TD/QD: 16x16, 8x8), the first whose CTAs,
  * dealt round-robin to the device's SMs,
  * keep at least 90% of them busy -- ctas / (sms * ceil(ctas / sms)) -- else

@@ -330,8 +330,17 @@ static int gemm_call(const mpgemm_opts* o, int64_t m, int64_t n, int64_t k,
     }
     if (split < 0) return fail(MPG_EINVAL, "split_k must be >= 0 (got %d)", split);
     int tile = o ? o->tile : 0;
-    if (tile <= 0) tile = default_tile<P>(m, n, k);
-    else tile -= 1;
+    if (tile <= 0) {
+        // a remembered choice of this shape's bucket, if its grid fits, else the occupancy rule
+        const int tuned = tuned_tile_index(P, m, n, k, num_tiles<P>());
+        tile = default_tile<P>(m, n, k);
+        if (tuned >= 0) {
+            const TileInfo tt = tile_info<P>(tuned);
+            if ((n + tt.bn - 1) / tt.bn <= 2147483647LL && (m + tt.bm - 1) / tt.bm <= 65535LL) tile = tuned;
+        }
+    } else {
+        tile -= 1;
+    }
     if (tile >= num_tiles<P>()) return fail(MPG_EINVAL, "tile id %d out of range", tile + 1);
     const TileInfo ti = tile_info<P>(tile);
     if ((n + ti.bn - 1) / ti.bn > 2147483647LL || (m + ti.bm - 1) / ti.bm > 65535LL)
@@ -356,7 +365,7 @@ int mpgemm_set_stream(void* stream)
 
 void* mpgemm_get_stream(void) { return static_cast<void*>(g_stream); }
 
-int mpgemm_version(void) { return 104; }
+int mpgemm_version(void) { return 105; }
 
 int mp_quick_two_sum(int64_t n, const double* a, const double* b, double* s, double* e)
 { return eft_call(0, n, a, b, s, e); }

@@ -299,6 +299,32 @@ int mpgemm_batch_autotune(int P, int count, const mpgemm_problem* problems, void
     clear_error();
     if (!best_policy) return set_error(MPG_EINVAL, "best_policy must not be NULL");
     if (reps < 1) reps = 1;
+    // a remembered choice for this exact list of shapes (FNV-1a over m, n, k
+    // and the transposes of every problem) is returned without measuring
+    char key[512] = "";
+    if (problems && count > 0) {
+        uint64_t h = 1469598103934665603ull;
+        auto mix = [&](int64_t v) {
+            for (int b = 0; b < 8; ++b) {
+                h ^= static_cast<uint64_t>(v >> (8 * b)) & 0xffu;
+                h *= 1099511628211ull;
+            }
+        };
+        for (int i = 0; i < count; ++i) {
+            mix(problems[i].m);
+            mix(problems[i].n);
+            mix(problems[i].k);
+            mix(problems[i].trans_a * 2 + problems[i].trans_b);
+        }
+        batch_tune_key(P, count, h, key, sizeof(key));
+        int pol = -1;
+        float ms = 0.f;
+        if (tune_lookup(key, &pol, &ms) && pol >= 0 && pol < kNumPolicies) {
+            *best_policy = pol;
+            if (best_ms) *best_ms = ms;
+            return MPG_OK;
+        }
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return set_error(MPG_ECUDA, "event creation failed");
@@ -328,6 +354,7 @@ int mpgemm_batch_autotune(int P, int count, const mpgemm_problem* problems, void
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != MPG_OK) return rc;
+    if (key[0]) tune_store(key, arg, best);
     *best_policy = arg;
     if (best_ms) *best_ms = best;
     return MPG_OK;

@@ -93,4 +93,13 @@ cudaStream_t current_stream();
 void clear_error();
 int set_error(int code, const char* msg);
 
+// Autotuner cache (tune.cu): keys "device|gemm:P:bm:bn:bk" (the bits of m,
+// n, k rounded up to powers of two) and "device|batch:P:count:hash".
+int tune_bucket(int64_t x);
+void gemm_tune_key(int P, int64_t m, int64_t n, int64_t k, char* out, size_t cap);
+void batch_tune_key(int P, int count, uint64_t shapes_hash, char* out, size_t cap);
+bool tune_lookup(const char* key, int* choice, float* ms);
+void tune_store(const char* key, int choice, float ms);
+int tuned_tile_index(int P, int64_t m, int64_t n, int64_t k, int ntiles);
+
 }  // namespace mpg

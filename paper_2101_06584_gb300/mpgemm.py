@@ -78,6 +78,10 @@ def _declare(L):
                                         ctypes.POINTER(ctypes.c_float)]
     L.mpgemm_crt_beta.argtypes = [i, i64]
     L.mpgemm_crt_split_beta.argtypes = [i, i64]
+    L.mpgemm_autotune.argtypes = [i, i64, i64, i64, vp, i64, vp, i64, vp, i64, i, ctypes.POINTER(i),
+                                  ctypes.POINTER(ctypes.c_float)]
+    L.mpgemm_tuned_tile.argtypes = [i, i64, i64, i64]
+    L.mpgemm_tune_cache_reset.restype = None
     L.mpgemm_num_tiles.argtypes = [i]
     L.mpgemm_default_tile.argtypes = [i, i64, i64, i64]
     L.mpgemm_tc_status.argtypes = [vp]
@@ -280,6 +284,36 @@ def default_tile(prec, m, n, k):
     t = lib().mpgemm_default_tile(P_OF[prec], m, n, k)
     check(t if t < 0 else 0)
     return t
+
+
+def autotune(prec, A, B, out=None, reps=3):
+    """Time every FP64-EFT tile on C = A B (A (P, m, k), B (P, k, n), no
+    transposes), remember the fastest for the shape's bucket (and in the file
+    MPGEMM_TUNE_CACHE names) and return (tile id, ms per call)."""
+    P = P_OF[prec]
+    _require(A, "A", P, 3)
+    _require(B, "B", P, 3)
+    m, k, n = A.shape[1], A.shape[2], B.shape[2]
+    if B.shape[1] != k:
+        raise ValueError("inner dimensions differ: %d vs %d" % (k, B.shape[1]))
+    if out is None:
+        out = torch.empty((P, m, n), dtype=torch.float64, device=A.device)
+    _require(out, "out", P, 3)
+    tile, ms = ctypes.c_int(0), ctypes.c_float(0.0)
+    _bind_stream()
+    check(lib().mpgemm_autotune(P, m, n, k, planes(A), _ld(A), planes(B), _ld(B), planes(out), _ld(out),
+                                int(reps), ctypes.byref(tile), ctypes.byref(ms)))
+    return tile.value, ms.value
+
+
+def tuned_tile(prec, m, n, k):
+    """The remembered tile id of the bucket of (m, n, k), or 0."""
+    return lib().mpgemm_tuned_tile(P_OF[prec], m, n, k)
+
+
+def tune_cache_reset():
+    """Forget remembered choices; the next lookup reads MPGEMM_TUNE_CACHE again."""
+    lib().mpgemm_tune_cache_reset()
 
 
 def tile_info(prec, tile):

@@ -178,7 +178,7 @@ def test_slicing_options(L):
 
 
 def test_version(L):
-    assert L.mpgemm_version() == 104
+    assert L.mpgemm_version() == 105
 
 
 def test_tc_status_validation(L):
@@ -344,3 +344,39 @@ def test_crt_split_host_checks(L):
     big = 65536
     assert L.mpgemm_ex(4, ctypes.byref(o), 8, 8, big, A, big, B, 8, C, 8) == -4
     assert "int32" in err(L)
+
+
+def test_tune_cache_file(L, tmp_path, monkeypatch):
+    """The autotuner's cache file: entries of this device ("none" without a
+    GPU) are found by shape bucket (m, n, k rounded up to powers of two),
+    lines that do not parse, other devices' entries and out-of-range tile ids
+    are ignored, a missing file or no MPGEMM_TUNE_CACHE means no choice, and
+    a reset re-reads the environment."""
+    nt = L.mpgemm_num_tiles(2)
+    path = tmp_path / "tune.json"
+    path.write_text(
+        '{\n "version": 1,\n "entries": {\n'
+        '  "none|gemm:2:7:7:7": {"choice": 3, "ms": 0.25},\n'
+        '  "none|gemm:2:12:12:12": {"choice": %d, "ms": 1.5},\n'
+        '  this line is not an entry\n'
+        '  "other GPU/99|gemm:3:10:10:10": {"choice": 1, "ms": 2},\n'
+        '  "none|gemm:4:10:10:10": {"choice": 2, "ms": 9.5}\n'
+        ' }\n}\n' % (nt + 1))
+    monkeypatch.delenv("MPGEMM_TUNE_CACHE", raising=False)
+    L.mpgemm_tune_cache_reset()
+    assert L.mpgemm_tuned_tile(2, 128, 128, 128) == 0               # no file named
+    monkeypatch.setenv("MPGEMM_TUNE_CACHE", str(path))
+    L.mpgemm_tune_cache_reset()
+    assert L.mpgemm_tuned_tile(2, 128, 128, 128) == 3
+    assert L.mpgemm_tuned_tile(2, 65, 100, 127) == 3               # the same bucket: 2^7 each
+    assert L.mpgemm_tuned_tile(2, 129, 128, 128) == 0              # the next bucket of m
+    assert L.mpgemm_tuned_tile(2, 4096, 4096, 4096) == 0           # tile id out of range
+    assert L.mpgemm_tuned_tile(3, 1024, 1024, 1024) == 0           # another device's entry
+    assert L.mpgemm_tuned_tile(4, 1000, 600, 1024) == 2
+    assert L.mpgemm_tuned_tile(4, -1, 600, 1024) == 0
+    monkeypatch.setenv("MPGEMM_TUNE_CACHE", str(tmp_path / "missing.json"))
+    assert L.mpgemm_tuned_tile(2, 128, 128, 128) == 3              # still the choices in memory
+    L.mpgemm_tune_cache_reset()
+    assert L.mpgemm_tuned_tile(2, 128, 128, 128) == 0
+    monkeypatch.delenv("MPGEMM_TUNE_CACHE")
+    L.mpgemm_tune_cache_reset()
