@@ -49,6 +49,41 @@ UNIT = "mad/s"
 # operations on the constant zero fourth components are folded away);
 # QD = QDmul 123 + QDadd 87.
 FP64_OPS_PER_MAD = {"dd": 20, "td": 128, "qd": 210}
+# The same multiply-adds by kind: (TwoSum, FastTwoSum, TwoProd, other
+# rounded operations); a transformation is 6, 3 or 2 binary64 operations as
+# a sequence, so 6 a + 3 b + 2 c + d = FP64_OPS_PER_MAD.
+EFT_MIX = {"dd": (1, 2, 1, 6), "td": (14, 10, 3, 8), "qd": (22, 16, 6, 18)}
+
+
+def kseq_bound(prec, int_ops, pk):
+    """Lower bound in seconds per multiply-add of a k-sequential tile that
+    computes the transformations in `int_ops` (1 TwoSum, 2 FastTwoSum, 4
+    TwoProd) on the integer pipes, at the measured rates `pk`: the larger of
+    the FP64-pipe time of the operations left there and the integer-pipe time
+    of the transformations moved (the two pipes run side by side).  Returns
+    (seconds, FP64-pipe operations per multiply-add)."""
+    ts, qts, tp, other = EFT_MIX[prec]
+    f64 = other + (0 if int_ops & 1 else 6 * ts) + (0 if int_ops & 2 else 3 * qts) + (0 if int_ops & 4 else 2 * tp)
+    t_int = ((ts / pk["int_two_sum"] if int_ops & 1 else 0.0)
+             + (qts / pk["int_fast_two_sum"] if int_ops & 2 else 0.0)
+             + (tp / pk["int_two_prod"] if int_ops & 4 else 0.0))
+    return max(f64 / pk["dfma"], t_int), f64
+
+
+def kseq_roofline(prec, mads, ms, pk, ti):
+    """The roofline fields of a k-sequential GEMM launch on tile `ti`
+    (mpgemm.tile_info): achieved = binary64 operations of the algorithm per
+    second (FP64_OPS_PER_MAD per multiply-add, wherever they run); peak =
+    the same operations at the kseq_bound rate."""
+    bound_s, f64 = kseq_bound(prec, ti["int_ops"], pk)
+    ops = FP64_OPS_PER_MAD[prec]
+    ach = mads * ops / (ms * 1e-3)
+    peak = ops / bound_s
+    return {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFP64op/s",
+            "frac": ach / peak, "ops_per_unit": ops, "int_ops": ti["int_ops"],
+            "fp64_pipe_ops_per_unit": f64, "frac_of_fp64_pipe_alone": ach / pk["dfma"],
+            "peak_source": "max(FP64-pipe operations / measured DFMA rate, integer-pipe transformations / "
+                           "measured TwoSum, FastTwoSum, TwoProd rates) per multiply-add, this run's clocks"}
 L2_FLUSH_BYTES = 256 << 20          # larger than the 129 MB L2
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -69,7 +104,7 @@ def bf16_peak():
 
 # the sources each recorded kernel is compiled from
 TRAFFIC_SOURCES = {
-    "td_qd": ["mp_arith.cuh", "gemm_kernel.cuh", "gemm_qd.cu", "internal.h"],
+    "td_qd": ["mp_arith.cuh", "soft_fp64.cuh", "gemm_kernel.cuh", "gemm_qd.cu", "internal.h"],
     "dd_int8": ["mp_arith.cuh", "ozaki.cu", "ozaki_common.cuh", "ozaki.h", "internal.h"],
     "dd_tc": ["mp_arith.cuh", "ozaki.cu", "ozaki_common.cuh", "ozaki.h", "internal.h"],
     "dd_crtint8": ["crt.cu", "ozaki_common.cuh", "ozaki.h", "internal.h"],
@@ -223,13 +258,15 @@ class ClockSampler:
 
 def peaks(torch, mm):
     """Measured pipe rates at this run's clocks (the roofline denominators):
-    FP64 lane-operations/s for add, mul, fma and int8 ops/s of mma.sync s8."""
+    FP64 lane-operations/s for add, mul, fma, int8 ops/s of mma.sync s8 and
+    TwoSum, FastTwoSum and TwoProd per second on the integer pipes."""
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     blocks = sms * 8
     out = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
     res = {}
     for kind, name, iters, ops in ((0, "dadd", 2048, 8), (1, "dmul", 2048, 8), (2, "dfma", 2048, 8),
-                                   (3, "mma_s8", 4096, 4 * 8192 / 32)):
+                                   (3, "mma_s8", 4096, 4 * 8192 / 32), (4, "int_two_sum", 1024, 4),
+                                   (5, "int_fast_two_sum", 1024, 4), (6, "int_two_prod", 1024, 4)):
         mm.peak_probe(kind, blocks, 16, out)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -491,16 +528,15 @@ class TdQd(Workload):
 
     def roofline(self, launch_ms, pk):
         n = self.n
-        ops = n ** 3 * FP64_OPS_PER_MAD["qd"]
-        ach = ops / (statistics.mean(launch_ms["qd"]) * 1e-3)
-        return {"bound": "alu", "kernel": "gemm_kseq_kernel<4,16,16,16,1,1> (QD)",
-                "achieved": ach / 1e12, "peak": pk["dfma"] / 1e12, "unit": "TFP64op/s",
-                "frac": ach / pk["dfma"], "traffic": recorded_traffic("td_qd_%d:qd" % n),
-                "ops_per_unit": FP64_OPS_PER_MAD["qd"],
-                "unit_of_work": "QD multiply-add", "units_per_launch": n ** 3,
-                "peak_source": "measured FP64 FMA probe with register operands at this run's clocks",
-                "per_precision_mad_s": {p: n ** 3 / (statistics.mean(launch_ms[p]) * 1e-3)
-                                        for p in self.precs}}
+        ti = self.mm.tile_info("qd", self.mm.default_tile("qd", n, n, n))
+        r = kseq_roofline("qd", n ** 3, statistics.mean(launch_ms["qd"]), pk, ti)
+        r.update({"kernel": "gemm_kseq_kernel<4,%d,%d,%d,%d,%d,ints=%d> (QD)" % (
+                      ti["bm"], ti["bn"], ti["bk"], ti["tm"], ti["tn"], ti["int_ops"]),
+                  "traffic": recorded_traffic("td_qd_%d:qd" % n),
+                  "unit_of_work": "QD multiply-add", "units_per_launch": n ** 3,
+                  "per_precision_mad_s": {p: n ** 3 / (statistics.mean(launch_ms[p]) * 1e-3)
+                                          for p in self.precs}})
+        return r
 
     def accuracy(self):
         """Errors of the TD and QD products and of the binary64-only product of
@@ -596,10 +632,10 @@ class DdSmall(Workload):
         # the split-K variant for reference (not bit-identical, within bound)
         ms = _time_call(self.torch, lambda: self.mm.gemm("dd", self.A, self.B, out=self.C, split_k=8), 20)
         ti = self.mm.tile_info("dd", self.mm.default_tile("dd", self.n, self.n, self.n))
-        kern = "gemm_kseq_kernel<2,%d,%d,%d,%d,%d>" % (ti["bm"], ti["bn"], ti["bk"], ti["tm"], ti["tn"])
-        return {"bound": "alu", "kernel": kern,
-                "achieved": ach / 1e12, "peak": pk["dfma"] / 1e12, "unit": "TFP64op/s",
-                "frac": ach / pk["dfma"], "traffic": None, "ops_per_unit": 20,
+        kern = "gemm_kseq_kernel<2,%d,%d,%d,%d,%d,ints=%d>" % (ti["bm"], ti["bn"], ti["bk"], ti["tm"], ti["tn"],
+                                                               ti["int_ops"])
+        r = kseq_roofline("dd", self.mads, statistics.mean(launch_ms["dd"]), pk, ti)
+        return {**r, "kernel": kern, "traffic": None,
                 "unit_of_work": "DD multiply-add", "units_per_launch": self.mads,
                 "note": "16K entries = 512 warps, one per SM sub-partition at most (FP64 floor 0.84 of peak); "
                         "warp split-K 8 (not k-sequential) runs at %.3g mad/s" % (self.mads / (ms * 1e-3))}
@@ -1020,7 +1056,6 @@ class Strassen(Workload):
         return out
 
     def roofline(self, launch_ms, pk):
-        ops = {"dd": FP64_OPS_PER_MAD["dd"], "qd": FP64_OPS_PER_MAD["qd"]}
         plain = {}
         for prec in ("dd", "qd"):
             A, B, C = self.dev[prec]
@@ -1033,12 +1068,16 @@ class Strassen(Workload):
             leaf_mads = 7 ** L * (n // 2 ** L) ** 3
             cases["%s_L%d" % (prec, L)] = {"ms": ms, "nominal_mad_s": n ** 3 / (ms * 1e-3),
                                            "speedup_vs_block": plain[prec] / ms,
-                                           "frac_fp64_of_leaf_work": leaf_mads * ops[prec] / (ms * 1e-3) / pk["dfma"]}
-        worst = min(cases.items(), key=lambda kv: kv[1]["frac_fp64_of_leaf_work"])
+                                           "leaf": kseq_roofline(prec, leaf_mads, ms, pk, self._leaf_tile(prec, L))}
+        worst = min(cases.items(), key=lambda kv: kv[1]["leaf"]["frac"])
+        w = worst[1]["leaf"]
         return {"bound": "alu", "kernel": "gemm_kseq_kernel leaves + mat_addsub_kernel", "unit": "TFP64op/s",
-                "achieved": worst[1]["frac_fp64_of_leaf_work"] * pk["dfma"] / 1e12, "peak": pk["dfma"] / 1e12,
-                "frac": worst[1]["frac_fp64_of_leaf_work"], "frac_of": worst[0], "traffic": None,
-                "block_ms": plain, "cases": cases}
+                "achieved": w["achieved"], "peak": w["peak"], "frac": w["frac"], "frac_of": worst[0],
+                "peak_source": w["peak_source"], "traffic": None, "block_ms": plain, "cases": cases}
+
+    def _leaf_tile(self, prec, L):
+        m = self.n[prec] // 2 ** L
+        return self.mm.tile_info(prec, self.mm.default_tile(prec, m, m, m))
 
 
 class Batched(Workload):
@@ -1117,11 +1156,12 @@ class Autograd(Workload):
         return {"fwd": (e0, e1)}
 
     def roofline(self, launch_ms, pk):
-        ach = self.n ** 3 * 20 / (statistics.mean(launch_ms["fwd"]) * 1e-3)
-        return {"bound": "alu", "kernel": "gemm_kseq_kernel<2,32,32,16,2,2> (DD forward)",
-                "achieved": ach / 1e12, "peak": pk["dfma"] / 1e12, "unit": "TFP64op/s",
-                "frac": ach / pk["dfma"], "traffic": None, "ops_per_unit": 20,
-                "unit_of_work": "DD multiply-add", "units_per_launch": self.n ** 3}
+        n = self.n
+        ti = self.mm.tile_info("dd", self.mm.default_tile("dd", n, n, n))
+        r = kseq_roofline("dd", n ** 3, statistics.mean(launch_ms["fwd"]), pk, ti)
+        return {**r, "kernel": "gemm_kseq_kernel<2,%d,%d,%d,%d,%d,ints=%d> (DD forward)" % (
+                    ti["bm"], ti["bn"], ti["bk"], ti["tm"], ti["tn"], ti["int_ops"]),
+                "traffic": None, "unit_of_work": "DD multiply-add", "units_per_launch": n ** 3}
 
 
 class AutogradTc(Autograd):

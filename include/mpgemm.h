@@ -62,7 +62,8 @@ void *mpgemm_get_stream(void);
  * mpgemm_default_tile; 103 adds MPG_ALGO_INT8_CRT, MPG_ALGO_BF16_CRT and
  * mpgemm_crt_beta; 104 adds MPG_ALGO_INT8_CRT_SPLIT, MPG_ALGO_BF16_CRT_SPLIT
  * and mpgemm_crt_split_beta; 105 adds mpgemm_autotune, mpgemm_tuned_tile and
- * mpgemm_tune_cache_reset. */
+ * mpgemm_tune_cache_reset; 106 adds mpgemm_tile_int_ops and the tiles that
+ * compute error-free transformations on the integer pipes. */
 int mpgemm_version(void);
 
 /* ---------------------------------------------------------------------
@@ -482,6 +483,16 @@ void mpgemm_tune_cache_reset(void);
  * an unknown id. */
 int mpgemm_num_tiles(int P);
 int mpgemm_tile_info(int P, int id, int info[6]);
+/* Which error-free transformations (Sec. 2.1) tile `id` of precision P
+ * computes on the integer pipes instead of as binary64 operation sequences
+ * on the FP64 pipe: a mask of 1 TwoSum, 2 FastTwoSum (QuickTwoSum), 4
+ * TwoProd; 0 for none.  Such a tile forms each transformation's two outputs
+ * from one exact integer sum or product of the significands, with the bits
+ * the operation sequence gives for every input (rare inputs -- non-finite,
+ * overflowing, or a product error below the subnormal range -- run the
+ * sequence itself), so every tile still returns the same C.  MPG_EINVAL for
+ * an unknown id. */
+int mpgemm_tile_int_ops(int P, int id);
 
 /* The FP64-EFT tile id (1-based) that mpgemm_ex uses for an m x n x k product
  * when opts->tile is 0 and the autotuner remembers none: of the candidates (binary64-only: 64x64, 32x32,
@@ -501,6 +512,9 @@ int mpgemm_default_tile(int P, int64_t m, int64_t n, int64_t k);
  *     thread with register operands; lane-operations = blocks*256*iters*8.
  *   kind 3: `iters` rounds of 4 independent mma.sync.m16n8k32 s8 per warp;
  *     int8 operations = blocks*8*iters*4*8192.
+ *   kind 4/5/6: `iters` rounds of 4 independent TwoSum / FastTwoSum /
+ *     TwoProd per thread computed on the integer pipes (the form of the tiles
+ *     mpgemm_tile_int_ops reports); transformations = blocks*256*iters*4.
  * ------------------------------------------------------------------- */
 int mpgemm_peak_probe(int kind, int blocks, int iters, double *out);
 

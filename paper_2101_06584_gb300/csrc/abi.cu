@@ -365,7 +365,7 @@ int mpgemm_set_stream(void* stream)
 
 void* mpgemm_get_stream(void) { return static_cast<void*>(g_stream); }
 
-int mpgemm_version(void) { return 105; }
+int mpgemm_version(void) { return 106; }
 
 int mp_quick_two_sum(int64_t n, const double* a, const double* b, double* s, double* e)
 { return eft_call(0, n, a, b, s, e); }
@@ -558,6 +558,16 @@ int mpgemm_tile_info(int P, int id, int info[6])
                  : P == 3 ? tile_info<3>(id - 1) : tile_info<4>(id - 1);
     info[0] = t.bm; info[1] = t.bn; info[2] = t.bk; info[3] = t.tm; info[4] = t.tn; info[5] = t.threads;
     return MPG_OK;
+}
+
+int mpgemm_tile_int_ops(int P, int id)
+{
+    clear_error();
+    const int nt = mpgemm_num_tiles(P);
+    if (nt == 0 || id < 1 || id > nt) return fail(MPG_EINVAL, "unknown tile %d for P = %d", id, P);
+    const TileInfo t = P == 1 ? tile_info<1>(id - 1) : P == 2 ? tile_info<2>(id - 1)
+                       : P == 3 ? tile_info<3>(id - 1) : tile_info<4>(id - 1);
+    return t.ints;
 }
 
 }  // extern "C"

@@ -12,6 +12,12 @@ const TileInfo kTiles[] = {
     {64, 64, 16, 4, 4, 256},
     {8, 8, 16, 1, 1, 64},
     {8, 8, 128, 1, 1, 64},
+    {32, 32, 16, 2, 2, 256, 3},
+    {16, 16, 16, 1, 1, 256, 7},
+    {8, 8, 16, 1, 1, 64, 3},
+    {16, 16, 16, 1, 1, 256, 3},
+    {32, 32, 16, 2, 2, 256, 7},
+    {8, 8, 128, 1, 1, 64, 3},
 };
 constexpr int kNumTiles = static_cast<int>(sizeof(kTiles) / sizeof(kTiles[0]));
 }  // namespace
@@ -31,7 +37,7 @@ TileInfo tile_info<P>(int t) { return kTiles[t]; }
 template <>
 int default_tile<P>(int64_t m, int64_t n, int64_t)
 {
-    return pick_tile<P>(m, n, {0, 1, 6});
+    return pick_tile<P>(m, n, {7, 10, 12});
 }
 
 template <>
@@ -45,6 +51,12 @@ cudaError_t launch_gemm_kseq<P>(const GemmArgs<P>& g, int tile, cudaStream_t s)
     case 4: return launch_kseq_cfg<P, 64, 64, 16, 4, 4>(g, s);
     case 5: return launch_kseq_cfg<P, 8, 8, 16, 1, 1>(g, s);
     case 6: return launch_kseq_cfg<P, 8, 8, 128, 1, 1>(g, s);
+    case 7: return launch_kseq_cfg<P, 32, 32, 16, 2, 2, 3>(g, s);
+    case 8: return launch_kseq_cfg<P, 16, 16, 16, 1, 1, 7>(g, s);
+    case 9: return launch_kseq_cfg<P, 8, 8, 16, 1, 1, 3>(g, s);
+    case 10: return launch_kseq_cfg<P, 16, 16, 16, 1, 1, 3>(g, s);
+    case 11: return launch_kseq_cfg<P, 32, 32, 16, 2, 2, 7>(g, s);
+    case 12: return launch_kseq_cfg<P, 8, 8, 128, 1, 1, 3>(g, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -33,9 +33,9 @@ struct KseqSmem {
 // (BM/TM)*(BN/TN) threads.  Every entry is accumulated by one thread over
 // p = 0..k-1 in order.  Threads none of whose entries lie inside C skip the
 // arithmetic (they still take part in staging and barriers).
-template <int P, int BM, int BN, int BK, int TM, int TN>
+template <int P, int BM, int BN, int BK, int TM, int TN, class F>
 __device__ __forceinline__ void kseq_tile(const GemmArgs<P>& g, int64_t m0, int64_t n0,
-                                          KseqSmem<P, BM, BN, BK>& sm, const mp::Rn& f)
+                                          KseqSmem<P, BM, BN, BK>& sm, const F& f)
 {
     constexpr int NT = (BM / TM) * (BN / TN);
     constexpr int TX = BN / TN;
@@ -112,12 +112,13 @@ __device__ __forceinline__ void kseq_tile(const GemmArgs<P>& g, int64_t m0, int6
     }
 }
 
-template <int P, int BM, int BN, int BK, int TM, int TN>
+// INTS: the transformations run on the integer pipes (mp::RnInt's mask).
+template <int P, int BM, int BN, int BK, int TM, int TN, unsigned INTS>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 gemm_kseq_kernel(const GemmArgs<P> g)
 {
     __shared__ KseqSmem<P, BM, BN, BK> sm;
-    const mp::Rn f = mp::make_rn();
+    const mp::RnInt<INTS> f(mp::make_rn());
     kseq_tile<P, BM, BN, BK, TM, TN>(g, static_cast<int64_t>(blockIdx.y) * BM,
                                      static_cast<int64_t>(blockIdx.x) * BN, sm, f);
 }
@@ -193,12 +194,12 @@ __global__ void zero_kernel(const GemmArgs<P> g)
     }
 }
 
-template <int P, int BM, int BN, int BK, int TM, int TN>
+template <int P, int BM, int BN, int BK, int TM, int TN, unsigned INTS = 0>
 cudaError_t launch_kseq_cfg(const GemmArgs<P>& g, cudaStream_t s)
 {
     const dim3 grid(static_cast<unsigned>((g.n + BN - 1) / BN),
                     static_cast<unsigned>((g.m + BM - 1) / BM));
-    gemm_kseq_kernel<P, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, s>>>(g);
+    gemm_kseq_kernel<P, BM, BN, BK, TM, TN, INTS><<<grid, (BM / TM) * (BN / TN), 0, s>>>(g);
     return cudaGetLastError();
 }
 

@@ -9,6 +9,11 @@ const TileInfo kTiles[] = {
     {32, 16, 16, 2, 1, 256},
     {32, 32, 16, 2, 2, 256},
     {8, 8, 16, 1, 1, 64},
+    {16, 16, 16, 1, 1, 256, 1},
+    {8, 8, 16, 1, 1, 64, 1},
+    {16, 8, 16, 1, 1, 128, 1},
+    {16, 16, 32, 1, 1, 256, 1},
+    {16, 16, 16, 1, 1, 256, 5},
 };
 constexpr int kNumTiles = static_cast<int>(sizeof(kTiles) / sizeof(kTiles[0]));
 }  // namespace
@@ -24,7 +29,7 @@ TileInfo tile_info<P>(int t) { return kTiles[t]; }
 template <>
 int default_tile<P>(int64_t m, int64_t n, int64_t)
 {
-    return pick_tile<P>(m, n, {0, 3});
+    return pick_tile<P>(m, n, {4, 5});
 }
 
 template <>
@@ -35,6 +40,11 @@ cudaError_t launch_gemm_kseq<P>(const GemmArgs<P>& g, int tile, cudaStream_t s)
     case 1: return launch_kseq_cfg<P, 32, 16, 16, 2, 1>(g, s);
     case 2: return launch_kseq_cfg<P, 32, 32, 16, 2, 2>(g, s);
     case 3: return launch_kseq_cfg<P, 8, 8, 16, 1, 1>(g, s);
+    case 4: return launch_kseq_cfg<P, 16, 16, 16, 1, 1, 1>(g, s);
+    case 5: return launch_kseq_cfg<P, 8, 8, 16, 1, 1, 1>(g, s);
+    case 6: return launch_kseq_cfg<P, 16, 8, 16, 1, 1, 1>(g, s);
+    case 7: return launch_kseq_cfg<P, 16, 16, 32, 1, 1, 1>(g, s);
+    case 8: return launch_kseq_cfg<P, 16, 16, 16, 1, 1, 5>(g, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -17,8 +17,12 @@ struct GemmArgs {
     int trans_a, trans_b;
 };
 
+// A k-sequential tile: CTA tile bm x bn, k slab bk, tm x tn outputs per
+// thread; ints names the transformations run on the integer pipes (the mask
+// of mp::RnInt: 1 TwoSum, 2 FastTwoSum, 4 TwoProd; 0 for none).
 struct TileInfo {
     int bm, bn, bk, tm, tn, threads;
+    int ints;
 };
 
 // k-sequential FP64-EFT GEMM with tile configuration `tile` (0-based).

@@ -6,16 +6,21 @@
 // renormalisation of the QD library and VecSum/VSEB of Fabiano, Muller and
 // Picot, which the paper uses without restating.
 //
-// Every rounded operation is an explicit __dadd_rn/__dsub_rn/__dmul_rn/__fma_rn
-// intrinsic, so the compiler cannot contract or reorder them: each function
-// performs the same sequence of IEEE binary64 operations as the paper's
-// algorithm and therefore returns the same bits as any other faithful
-// implementation.  Data-dependent branches (the nonzero tests of VSEB and
+// Every function takes a policy f that performs the rounded binary64
+// operations (add, sub, mul, fma) and the three transformations of Sec. 2.1
+// (two_sum, quick_two_sum, two_prod).  Rn issues each as an explicit
+// __fma_rn intrinsic, so the compiler cannot contract or reorder them: each
+// function performs the same sequence of IEEE binary64 operations as the
+// paper's algorithm and therefore returns the same bits as any other faithful
+// implementation.  RnInt computes chosen transformations on the integer
+// pipes instead, with the same bits for every input.  Data-dependent branches (the nonzero tests of VSEB and
 // Renorm) are written as selects that pick exactly the value the branch
 // would; the tests themselves look at the bit pattern with integer
 // instructions so they do not occupy the FP64 pipe.
 #pragma once
 #include <cstdint>
+
+#include "soft_fp64.cuh"
 
 namespace mp {
 
@@ -37,6 +42,72 @@ struct Rn {
     __device__ __forceinline__ double sub(double a, double b) const { return __fma_rn(b, -one, a); }
     __device__ __forceinline__ double mul(double a, double b) const { return __fma_rn(a, b, neg_zero); }
     __device__ __forceinline__ double fma(double a, double b, double c) const { return __fma_rn(a, b, c); }
+
+    // Sec. 2.1 as operation sequences on the FP64 pipe.
+    // FastTwoSum (QuickTwoSum): s = fl(a + b), e = b - (s - a).
+    __device__ __forceinline__ void quick_two_sum(double a, double b, double& s, double& e) const
+    {
+        const double sum = add(a, b);
+        e = sub(b, sub(sum, a));
+        s = sum;
+    }
+    // TwoSum: s = fl(a + b) and e = (a + b) - s exactly.
+    __device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) const
+    {
+        const double sum = add(a, b);
+        const double bv = sub(sum, a);
+        const double av = sub(sum, bv);
+        e = add(sub(a, av), sub(b, bv));
+        s = sum;
+    }
+    // TwoProd with FMA: p = fl(a b), e = a b - p exactly.
+    __device__ __forceinline__ void two_prod(double a, double b, double& p, double& e) const
+    {
+        const double prod = mul(a, b);
+        e = fma(a, b, -prod);
+        p = prod;
+    }
+};
+
+// Rn with the transformations that MASK names computed on the integer pipes
+// from one exact sum or product (soft_fp64.cuh): bit 0 TwoSum, bit 1
+// FastTwoSum, bit 2 TwoProd.  Each returns the same bits as Rn's sequence for
+// every input, so a kernel may take any mask; the FP64 pipe then runs only
+// the remaining operations while the integer pipes of the same warps run the
+// rest.  RnInt<0> is Rn.
+template <unsigned MASK>
+struct RnInt : Rn {
+    __device__ __forceinline__ explicit RnInt(const Rn& r) : Rn(r) {}
+    __device__ __forceinline__ void quick_two_sum(double a, double b, double& s, double& e) const
+    {
+        if constexpr ((MASK & 2u) != 0u) {
+            const soft::Pair r = soft::two_sum<true>(a, b);
+            s = r.hi;
+            e = r.lo;
+        } else {
+            Rn::quick_two_sum(a, b, s, e);
+        }
+    }
+    __device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) const
+    {
+        if constexpr ((MASK & 1u) != 0u) {
+            const soft::Pair r = soft::two_sum<false>(a, b);
+            s = r.hi;
+            e = r.lo;
+        } else {
+            Rn::two_sum(a, b, s, e);
+        }
+    }
+    __device__ __forceinline__ void two_prod(double a, double b, double& p, double& e) const
+    {
+        if constexpr ((MASK & 4u) != 0u) {
+            const soft::Pair r = soft::two_prod(a, b);
+            p = r.hi;
+            e = r.lo;
+        } else {
+            Rn::two_prod(a, b, p, e);
+        }
+    }
 };
 
 static __device__ double rn_constants[96] = {
@@ -82,36 +153,30 @@ __device__ __forceinline__ bool abs_ge(double a, double b)
 
 // ------------------------------------------------------------- Sec. 2.1
 
-// QuickTwoSum: s = fl(a + b), e = b - (s - a).
-__device__ __forceinline__ void quick_two_sum(const Rn& f, double a, double b, double& s, double& e)
+// The transformations of Sec. 2.1, as the policy f computes them.
+template <class F>
+__device__ __forceinline__ void quick_two_sum(const F& f, double a, double b, double& s, double& e)
 {
-    const double sum = f.add(a, b);
-    e = f.sub(b, f.sub(sum, a));
-    s = sum;
+    f.quick_two_sum(a, b, s, e);
 }
 
-// TwoSum: s = fl(a + b) and e = (a + b) - s exactly.
-__device__ __forceinline__ void two_sum(const Rn& f, double a, double b, double& s, double& e)
+template <class F>
+__device__ __forceinline__ void two_sum(const F& f, double a, double b, double& s, double& e)
 {
-    const double sum = f.add(a, b);
-    const double bv = f.sub(sum, a);
-    const double av = f.sub(sum, bv);
-    e = f.add(f.sub(a, av), f.sub(b, bv));
-    s = sum;
+    f.two_sum(a, b, s, e);
 }
 
-// TwoProd with FMA: p = fl(a b), e = a b - p exactly.
-__device__ __forceinline__ void two_prod(const Rn& f, double a, double b, double& p, double& e)
+template <class F>
+__device__ __forceinline__ void two_prod(const F& f, double a, double b, double& p, double& e)
 {
-    const double prod = f.mul(a, b);
-    e = f.fma(a, b, -prod);
-    p = prod;
+    f.two_prod(a, b, p, e);
 }
 
 // ------------------------------------------------- helpers of Alg. 3 - 6
 
 // ThreeSum: (a, b, c) -> (a', b', c'), same exact sum.
-__device__ __forceinline__ void three_sum(const Rn& f, double& a, double& b, double& c)
+template <class F>
+__device__ __forceinline__ void three_sum(const F& f, double& a, double& b, double& c)
 {
     double t1, t2, t3;
     two_sum(f, a, b, t1, t2);
@@ -120,7 +185,8 @@ __device__ __forceinline__ void three_sum(const Rn& f, double& a, double& b, dou
 }
 
 // ThreeSum2: as ThreeSum with the two low terms added in one rounding.
-__device__ __forceinline__ void three_sum2(const Rn& f, double& a, double& b, double c)
+template <class F>
+__device__ __forceinline__ void three_sum2(const F& f, double& a, double& b, double c)
 {
     double t1, t2, t3;
     two_sum(f, a, b, t1, t2);
@@ -132,7 +198,8 @@ __device__ __forceinline__ void three_sum2(const Rn& f, double& a, double& b, do
 // top-down pass that emits a component whenever the QuickTwoSum error is
 // nonzero, folding everything after the third emitted component into the
 // fourth.  k counts emitted components; r_k selects stand in for indexing.
-__device__ __forceinline__ void renorm5(const Rn& f, double c0, double c1, double c2, double c3, double c4,
+template <class F>
+__device__ __forceinline__ void renorm5(const F& f, double c0, double c1, double c2, double c3, double c4,
                                         double& r0, double& r1, double& r2, double& r3)
 {
     double s, t0, t1, t2, t3, t4;
@@ -187,7 +254,8 @@ __device__ __forceinline__ void renorm5(const Rn& f, double c0, double c1, doubl
 }
 
 // VecSum of three / four terms: TwoSum chain from the last term up.
-__device__ __forceinline__ void vec_sum3(const Rn& f, double x0, double x1, double x2,
+template <class F>
+__device__ __forceinline__ void vec_sum3(const F& f, double x0, double x1, double x2,
                                          double& e0, double& e1, double& e2)
 {
     double s;
@@ -195,7 +263,8 @@ __device__ __forceinline__ void vec_sum3(const Rn& f, double x0, double x1, doub
     two_sum(f, x0, s, e0, e1);
 }
 
-__device__ __forceinline__ void vec_sum4(const Rn& f, double x0, double x1, double x2, double x3,
+template <class F>
+__device__ __forceinline__ void vec_sum4(const F& f, double x0, double x1, double x2, double x3,
                                          double& e0, double& e1, double& e2, double& e3)
 {
     double s;
@@ -208,7 +277,8 @@ __device__ __forceinline__ void vec_sum4(const Rn& f, double x0, double x1, doub
 // r0 and either moves to r1 (nonzero error) or carries its sum on; the second
 // writes the current slot; after it the loop returns if both slots are done,
 // otherwise a nonzero remainder lands in the current slot.
-__device__ __forceinline__ void vseb2_of3(const Rn& f, double e0, double e1, double e2, double& r0, double& r1)
+template <class F>
+__device__ __forceinline__ void vseb2_of3(const F& f, double e0, double e1, double e2, double& r0, double& r1)
 {
     double h1, l1, h2, l2;
     quick_two_sum(f, e0, e1, h1, l1);
@@ -220,7 +290,8 @@ __device__ __forceinline__ void vseb2_of3(const Rn& f, double e0, double e1, dou
 }
 
 // VSEB(3) on six terms (used by the merge-based TDadd).
-__device__ __forceinline__ void vseb3_of6(const Rn& f, const double e[6], double& r0, double& r1, double& r2)
+template <class F>
+__device__ __forceinline__ void vseb3_of6(const F& f, const double e[6], double& r0, double& r1, double& r2)
 {
     r0 = 0.0; r1 = 0.0; r2 = 0.0;
     int j = 0;
@@ -250,7 +321,8 @@ __device__ __forceinline__ void vseb3_of6(const Rn& f, const double e[6], double
 // ------------------------------------------------------------- Sec. 2.2
 
 // Alg. 1, DDadd.
-__device__ __forceinline__ void dd_add(const Rn& f, const double x[2], const double y[2], double r[2])
+template <class F>
+__device__ __forceinline__ void dd_add(const F& f, const double x[2], const double y[2], double r[2])
 {
     double s, e;
     two_sum(f, x[0], y[0], s, e);
@@ -260,7 +332,8 @@ __device__ __forceinline__ void dd_add(const Rn& f, const double x[2], const dou
 }
 
 // Alg. 2, DDmul.
-__device__ __forceinline__ void dd_mul(const Rn& f, const double x[2], const double y[2], double r[2])
+template <class F>
+__device__ __forceinline__ void dd_mul(const F& f, const double x[2], const double y[2], double r[2])
 {
     double p1, p2;
     two_prod(f, x[0], y[0], p1, p2);
@@ -274,7 +347,8 @@ __device__ __forceinline__ void dd_mul(const Rn& f, const double x[2], const dou
 // ------------------------------------------------------------- Sec. 2.3
 
 // Alg. 4, TDmul (the "fast" triple-word product).
-__device__ __forceinline__ void td_mul(const Rn& f, const double x[3], const double y[3], double r[3])
+template <class F>
+__device__ __forceinline__ void td_mul(const F& f, const double x[3], const double y[3], double r[3])
 {
     double z00up, z00lo, z01up, z01lo, z10up, z10lo;
     two_prod(f, x[0], y[0], z00up, z00lo);
@@ -299,27 +373,18 @@ __device__ __forceinline__ void td_mul(const Rn& f, const double x[3], const dou
 // With ZERO4 the fourth components of both operands are +0 (TDaddq): then
 // s3, v3, u3, w3 and t3 are all exactly +0 in round-to-nearest, and those six
 // operations are replaced by the constant.
-template <bool ZERO4>
-__device__ __forceinline__ void qd_add_impl(const Rn& f, const double x[4], const double y[4], double r[4])
+template <bool ZERO4, class F>
+__device__ __forceinline__ void qd_add_impl(const F& f, const double x[4], const double y[4], double r[4])
 {
-    double s0 = f.add(x[0], y[0]);
-    double s1 = f.add(x[1], y[1]);
-    double s2 = f.add(x[2], y[2]);
-    double s3 = ZERO4 ? f.zero : f.add(x[3], y[3]);
-    const double v0 = f.sub(s0, x[0]);
-    const double v1 = f.sub(s1, x[1]);
-    const double v2 = f.sub(s2, x[2]);
-    const double w0 = f.sub(x[0], f.sub(s0, v0));
-    const double w1 = f.sub(x[1], f.sub(s1, v1));
-    const double w2 = f.sub(x[2], f.sub(s2, v2));
-    double t0 = f.add(w0, f.sub(y[0], v0));
-    double t1 = f.add(w1, f.sub(y[1], v1));
-    double t2 = f.add(w2, f.sub(y[2], v2));
-    double t3 = f.zero;
-    if (!ZERO4) {
-        const double v3 = f.sub(s3, x[3]);
-        const double w3 = f.sub(x[3], f.sub(s3, v3));
-        t3 = f.add(w3, f.sub(y[3], v3));
+    double s0, s1, s2, s3, t0, t1, t2, t3;
+    two_sum(f, x[0], y[0], s0, t0);
+    two_sum(f, x[1], y[1], s1, t1);
+    two_sum(f, x[2], y[2], s2, t2);
+    if (ZERO4) {
+        s3 = f.zero;
+        t3 = f.zero;
+    } else {
+        two_sum(f, x[3], y[3], s3, t3);
     }
     two_sum(f, s1, t0, s1, t0);
     three_sum(f, s2, t0, t1);
@@ -328,14 +393,16 @@ __device__ __forceinline__ void qd_add_impl(const Rn& f, const double x[4], cons
     renorm5(f, s0, s1, s2, s3, t0, r[0], r[1], r[2], r[3]);
 }
 
-__device__ __forceinline__ void qd_add(const Rn& f, const double x[4], const double y[4], double r[4])
+template <class F>
+__device__ __forceinline__ void qd_add(const F& f, const double x[4], const double y[4], double r[4])
 {
     qd_add_impl<false>(f, x, y, r);
 }
 
 // TDaddq (Sec. 2.3): QDadd on operands padded with a zero fourth component,
 // the fourth result component dropped.
-__device__ __forceinline__ void td_addq(const Rn& f, const double x[3], const double y[3], double r[3])
+template <class F>
+__device__ __forceinline__ void td_addq(const F& f, const double x[3], const double y[3], double r[3])
 {
     const double x4[4] = {x[0], x[1], x[2], f.zero};
     const double y4[4] = {y[0], y[1], y[2], f.zero};
@@ -348,7 +415,8 @@ __device__ __forceinline__ void td_addq(const Rn& f, const double x[3], const do
 
 // Alg. 3, TDadd: Merge (by decreasing magnitude, x first on ties), VecSum,
 // VSEB(3).
-__device__ __forceinline__ void td_add_merge(const Rn& f, const double x[3], const double y[3], double r[3])
+template <class F>
+__device__ __forceinline__ void td_add_merge(const F& f, const double x[3], const double y[3], double r[3])
 {
     double z[6];
     int i = 0, j = 0;
@@ -371,7 +439,8 @@ __device__ __forceinline__ void td_add_merge(const Rn& f, const double x[3], con
 }
 
 // Alg. 6, QDmul (sloppy).  The listing's first line is dead and omitted.
-__device__ __forceinline__ void qd_mul(const Rn& f, const double x[4], const double y[4], double r[4])
+template <class F>
+__device__ __forceinline__ void qd_mul(const F& f, const double x[4], const double y[4], double r[4])
 {
     double p0, p1, p2, p3, p4, p5, q0, q1, q2, q3, q4, q5;
     two_prod(f, x[0], y[0], p0, q0);
@@ -406,7 +475,8 @@ __device__ __forceinline__ void qd_mul(const Rn& f, const double x[4], const dou
 // zero fourth component, the fourth result component dropped.  The padding is
 // the register zero, so every operation on it runs as written and the signs
 // of zero results agree with the same steps on the host.
-__device__ __forceinline__ void td_mulq(const Rn& f, const double x[3], const double y[3], double r[3])
+template <class F>
+__device__ __forceinline__ void td_mulq(const F& f, const double x[3], const double y[3], double r[3])
 {
     const double x4[4] = {x[0], x[1], x[2], f.zero};
     const double y4[4] = {y[0], y[1], y[2], f.zero};
@@ -446,8 +516,8 @@ __device__ __forceinline__ void sort_by_magnitude(double z[N])
 // summed into a fifth term with plain additions; if the terms run out first
 // the accumulator's two terms follow the components.  Renorm ends it.  The
 // emission count k selects the slot, so nothing is indexed dynamically.
-template <int N>
-__device__ __forceinline__ void accumulate_sorted(const Rn& f, const double z[N], double r[4])
+template <int N, class F>
+__device__ __forceinline__ void accumulate_sorted(const F& f, const double z[N], double r[4])
 {
     double u, v;
     quick_two_sum(f, z[0], z[1], u, v);
@@ -489,7 +559,8 @@ __device__ __forceinline__ void accumulate_sorted(const Rn& f, const double z[N]
 // and x1 y2 by fma) summed with one rounding each; x2 y2 dropped.  The ten
 // terms, stably sorted by decreasing magnitude, go through the accurate
 // normalisation; the fourth component is dropped.
-__device__ __forceinline__ void td_mul_acc(const Rn& f, const double x[3], const double y[3], double r[3])
+template <class F>
+__device__ __forceinline__ void td_mul_acc(const F& f, const double x[3], const double y[3], double r[3])
 {
     double z[10];
     double q02, q11, q20;
@@ -513,7 +584,8 @@ __device__ __forceinline__ void td_mul_acc(const Rn& f, const double x[3], const
 // Accurate QD addition (the IEEE-style addition of Hida, Li and Bailey): the
 // eight components stably sorted by decreasing magnitude, x first on ties,
 // then the accurate normalisation.
-__device__ __forceinline__ void qd_add_acc(const Rn& f, const double x[4], const double y[4], double r[4])
+template <class F>
+__device__ __forceinline__ void qd_add_acc(const F& f, const double x[4], const double y[4], double r[4])
 {
     double z[8] = {x[0], x[1], x[2], x[3], y[0], y[1], y[2], y[3]};
     sort_by_magnitude<8>(z);
@@ -524,35 +596,34 @@ __device__ __forceinline__ void qd_add_acc(const Rn& f, const double x[4], const
 
 template <int P> struct Ops;
 template <> struct Ops<2> {
-    static __device__ __forceinline__ void mul(const Rn& f, const double* x, const double* y, double* r) { dd_mul(f, x, y, r); }
-    static __device__ __forceinline__ void add(const Rn& f, const double* x, const double* y, double* r) { dd_add(f, x, y, r); }
+    template <class F> static __device__ __forceinline__ void mul(const F& f, const double* x, const double* y, double* r) { dd_mul(f, x, y, r); }
+    template <class F> static __device__ __forceinline__ void add(const F& f, const double* x, const double* y, double* r) { dd_add(f, x, y, r); }
 };
 template <> struct Ops<3> {
-    static __device__ __forceinline__ void mul(const Rn& f, const double* x, const double* y, double* r) { td_mul(f, x, y, r); }
-    static __device__ __forceinline__ void add(const Rn& f, const double* x, const double* y, double* r) { td_addq(f, x, y, r); }
+    template <class F> static __device__ __forceinline__ void mul(const F& f, const double* x, const double* y, double* r) { td_mul(f, x, y, r); }
+    template <class F> static __device__ __forceinline__ void add(const F& f, const double* x, const double* y, double* r) { td_addq(f, x, y, r); }
 };
 template <> struct Ops<4> {
-    static __device__ __forceinline__ void mul(const Rn& f, const double* x, const double* y, double* r) { qd_mul(f, x, y, r); }
-    static __device__ __forceinline__ void add(const Rn& f, const double* x, const double* y, double* r) { qd_add(f, x, y, r); }
+    template <class F> static __device__ __forceinline__ void mul(const F& f, const double* x, const double* y, double* r) { qd_mul(f, x, y, r); }
+    template <class F> static __device__ __forceinline__ void add(const F& f, const double* x, const double* y, double* r) { qd_add(f, x, y, r); }
 };
 
 // acc = add(acc, mul(a, b)): one multiply-add of the GEMM, a from A, b from B.
-template <int P>
-__device__ __forceinline__ void mad(const Rn& f, double* acc, const double* a, const double* b)
+// For P = 1 (the binary64-only product) it is acc = fma(a, b, acc), one
+// rounding per term -- the plain FP64 GEMM the multi-component forms are
+// compared with.
+template <int P, class F>
+__device__ __forceinline__ void mad(const F& f, double* acc, const double* a, const double* b)
 {
-    double prod[P], sum[P];
-    Ops<P>::mul(f, a, b, prod);
-    Ops<P>::add(f, acc, prod, sum);
+    if constexpr (P == 1) {
+        acc[0] = f.fma(a[0], b[0], acc[0]);
+    } else {
+        double prod[P], sum[P];
+        Ops<P>::mul(f, a, b, prod);
+        Ops<P>::add(f, acc, prod, sum);
 #pragma unroll
-    for (int c = 0; c < P; ++c) acc[c] = sum[c];
-}
-
-// The binary64-only product (P = 1): acc = fma(a, b, acc), one rounding per
-// term -- the plain FP64 GEMM the multi-component forms are compared with.
-template <>
-__device__ __forceinline__ void mad<1>(const Rn& f, double* acc, const double* a, const double* b)
-{
-    acc[0] = f.fma(a[0], b[0], acc[0]);
+        for (int c = 0; c < P; ++c) acc[c] = sum[c];
+    }
 }
 
 }  // namespace mp

@@ -9,6 +9,7 @@
 // DADD and DMUL issue at about 0.84x the DFMA rate on GB300.
 #include "mpgemm.h"
 #include "internal.h"
+#include "soft_fp64.cuh"
 
 namespace mpg {
 
@@ -63,20 +64,53 @@ __global__ void __launch_bounds__(256) mma_s8_probe_kernel(int iters, double* ou
     out[static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x] = static_cast<double>(s);
 }
 
+// The integer-pipe rates of the transformations as RnInt computes them
+// (soft_fp64.cuh): each thread runs 4 independent chains of TwoSum (KIND 4),
+// FastTwoSum (5) or TwoProd (6); every error term is folded into a running
+// XOR so none is dead.  Transformations = blocks*256*iters*4.
+template <int KIND>
+__global__ void __launch_bounds__(256) int_eft_probe_kernel(int iters, double* out)
+{
+    const volatile double* pc = probe_constants;
+    const double a = pc[0], b = pc[1];
+    double x[4];
+    long long acc = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) x[j] = 1.0 + threadIdx.x * 1e-3 + j;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            mp::soft::Pair r;
+            if constexpr (KIND == 4) r = mp::soft::two_sum<false>(x[j], b);
+            else if constexpr (KIND == 5) r = mp::soft::two_sum<true>(x[j], b);
+            else r = mp::soft::two_prod(x[j], a);
+            x[j] = r.hi;
+            acc ^= __double_as_longlong(r.lo);
+        }
+    }
+    double s = __longlong_as_double(acc & 0x3fffffffffffffffll);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s = __dadd_rn(s, x[j]);
+    out[static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x] = s;
+}
+
 }  // namespace mpg
 
 extern "C" int mpgemm_peak_probe(int kind, int blocks, int iters, double* out)
 {
     using namespace mpg;
-    if (kind < 0 || kind > 3 || blocks < 1 || iters < 1 || !out)
-        return set_error(MPG_EINVAL, "mpgemm_peak_probe: kind 0..3, blocks >= 1, iters >= 1, out non-NULL");
+    if (kind < 0 || kind > 6 || blocks < 1 || iters < 1 || !out)
+        return set_error(MPG_EINVAL, "mpgemm_peak_probe: kind 0..6, blocks >= 1, iters >= 1, out non-NULL");
     clear_error();
     cudaStream_t s = current_stream();
     switch (kind) {
     case 0: fp64_probe_kernel<0><<<blocks, 256, 0, s>>>(iters, out); break;
     case 1: fp64_probe_kernel<1><<<blocks, 256, 0, s>>>(iters, out); break;
     case 2: fp64_probe_kernel<2><<<blocks, 256, 0, s>>>(iters, out); break;
-    default: mma_s8_probe_kernel<<<blocks, 256, 0, s>>>(iters, out); break;
+    case 3: mma_s8_probe_kernel<<<blocks, 256, 0, s>>>(iters, out); break;
+    case 4: int_eft_probe_kernel<4><<<blocks, 256, 0, s>>>(iters, out); break;
+    case 5: int_eft_probe_kernel<5><<<blocks, 256, 0, s>>>(iters, out); break;
+    default: int_eft_probe_kernel<6><<<blocks, 256, 0, s>>>(iters, out); break;
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MPG_OK : set_error(MPG_ECUDA, cudaGetErrorString(e));

@@ -86,6 +86,7 @@ def _declare(L):
     L.mpgemm_default_tile.argtypes = [i, i64, i64, i64]
     L.mpgemm_tc_status.argtypes = [vp]
     L.mpgemm_tile_info.argtypes = [i, i, ctypes.POINTER(ctypes.c_int * 6)]
+    L.mpgemm_tile_int_ops.argtypes = [i, i]
     return L
 
 
@@ -319,12 +320,18 @@ def tune_cache_reset():
 def tile_info(prec, tile):
     info = (ctypes.c_int * 6)()
     check(lib().mpgemm_tile_info(P_OF[prec], tile, ctypes.byref(info)))
-    return dict(zip(("bm", "bn", "bk", "tm", "tn", "threads"), list(info)))
+    d = dict(zip(("bm", "bn", "bk", "tm", "tn", "threads"), list(info)))
+    ints = lib().mpgemm_tile_int_ops(P_OF[prec], tile)
+    if ints < 0:
+        check(ints)
+    d["int_ops"] = ints
+    return d
 
 
 def peak_probe(kind, blocks, iters, out):
-    """Launch a throughput probe (kind 0 FP64 add, 1 mul, 2 fma, 3 mma.sync s8)
-    writing to ``out`` (a CUDA float64 tensor of blocks*256 elements)."""
+    """Launch a throughput probe (kind 0 FP64 add, 1 mul, 2 fma, 3 mma.sync s8,
+    4/5/6 TwoSum/FastTwoSum/TwoProd on the integer pipes) writing to ``out``
+    (a CUDA float64 tensor of blocks*256 elements)."""
     if out.numel() < blocks * 256 or not out.is_cuda or out.dtype != torch.float64:
         raise ValueError("out must be a CUDA float64 tensor of at least blocks*256 elements")
     lib().mpgemm_peak_probe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]

@@ -178,7 +178,7 @@ def test_slicing_options(L):
 
 
 def test_version(L):
-    assert L.mpgemm_version() == 105
+    assert L.mpgemm_version() == 106
 
 
 def test_tc_status_validation(L):
@@ -204,8 +204,15 @@ def test_tile_table(L):
             assert L.mpgemm_tile_info(P, t, ctypes.byref(info)) == 0
             bm, bn, bk, tm, tn, threads = list(info)
             assert bk > 0 and bm % tm == 0 and bn % tn == 0 and (bm // tm) * (bn // tn) == threads
+            assert 0 <= L.mpgemm_tile_int_ops(P, t) <= 7
         info = (ctypes.c_int * 6)()
         assert L.mpgemm_tile_info(P, nt + 1, ctypes.byref(info)) == -1
+        assert L.mpgemm_tile_int_ops(P, nt + 1) == -1 and L.mpgemm_tile_int_ops(P, 0) == -1
+        # both forms are there: tiles on the FP64 pipe alone and tiles with
+        # TwoSum on the integer pipes
+        masks = [L.mpgemm_tile_int_ops(P, t) for t in range(1, nt + 1)]
+        assert 0 in masks and any(m & 1 for m in masks)
+    assert all(L.mpgemm_tile_int_ops(1, t) == 0 for t in range(1, L.mpgemm_num_tiles(1) + 1))
 
 
 def _tile(L, P, t):
