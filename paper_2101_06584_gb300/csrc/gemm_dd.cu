@@ -34,10 +34,14 @@ TileInfo tile_info<P>(int t) { return kTiles[t]; }
 // 8 x 8 tile stages 128 values of k at a time (34 KB of shared memory): a
 // 128^3 product is then one load and one barrier per CTA instead of eight,
 // 94 -> 90 us back to back and 108 -> 95 us after an L2 flush on GB300.
+//
+// With enough outputs (int_tiles_pay) the 16 x 16 or 8 x 8 tiles that run
+// TwoSum and FastTwoSum on the integer pipes: 19.7 ms at 1024^3 against
+// 34.4 ms for the best FP64-pipe tile.
 template <>
 int default_tile<P>(int64_t m, int64_t n, int64_t)
 {
-    return pick_tile<P>(m, n, {7, 10, 12});
+    return int_tiles_pay(m, n) ? pick_tile<P>(m, n, {10, 9}) : pick_tile<P>(m, n, {0, 1, 6});
 }
 
 template <>

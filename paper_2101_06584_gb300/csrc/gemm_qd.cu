@@ -25,11 +25,12 @@ template <>
 TileInfo tile_info<P>(int t) { return kTiles[t]; }
 
 // 16 x 16, or 8 x 8 where 16 x 16 leaves much of the last wave's SMs idle
-// (one entry per thread either way).
+// (one entry per thread either way); with TwoSum on the integer pipes when
+// the product has enough outputs for them (int_tiles_pay).
 template <>
 int default_tile<P>(int64_t m, int64_t n, int64_t)
 {
-    return pick_tile<P>(m, n, {4, 5});
+    return int_tiles_pay(m, n) ? pick_tile<P>(m, n, {4, 5}) : pick_tile<P>(m, n, {0, 3});
 }
 
 template <>

@@ -93,6 +93,17 @@ int pick_tile(int64_t m, int64_t n, std::initializer_list<int> cands)
     return best;
 }
 
+// Whether an m x n product has enough outputs for the tiles that compute
+// transformations on the integer pipes: a transformation there is a chain of
+// some fifty dependent integer instructions, whose latency takes many warps
+// per SM to hide.  On GB300 they run 1.7-2.0x faster than the FP64-pipe tiles
+// at 1024^2 outputs (about 6900 per SM) and 1.6x slower at 128^2 (about 110
+// per SM); the rule takes them from 512 outputs per SM.
+inline bool int_tiles_pay(int64_t m, int64_t n)
+{
+    return m * n >= static_cast<int64_t>(512) * num_sms();
+}
+
 cudaStream_t current_stream();
 void clear_error();
 int set_error(int code, const char* msg);
