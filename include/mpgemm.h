@@ -499,7 +499,7 @@ int mpgemm_tile_int_ops(int P, int id);
  * 16x16, 8x8; DD: 32x32, 16x16, 8x8 staging 128 values of k; TD/QD: 16x16, 8x8), the first whose CTAs,
  * dealt round-robin to the device's SMs,
  * keep at least 90% of them busy -- ctas / (sms * ceil(ctas / sms)) -- else
- * the closest.  For P = 2, 3, 4 with m * n >= 512 * sms the candidates are
+ * the closest.  For P = 2, 3, 4 with m * n >= 256 * sms the candidates are
  * the 16x16 and 8x8 tiles that compute TwoSum (and for DD FastTwoSum) on the
  * integer pipes (mpgemm_tile_int_ops), which need that many outputs to hide
  * the integer pipes' latency.  Uses the current device's SM count (152 when

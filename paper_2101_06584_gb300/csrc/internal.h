@@ -96,12 +96,13 @@ int pick_tile(int64_t m, int64_t n, std::initializer_list<int> cands)
 // Whether an m x n product has enough outputs for the tiles that compute
 // transformations on the integer pipes: a transformation there is a chain of
 // some fifty dependent integer instructions, whose latency takes many warps
-// per SM to hide.  On GB300 they run 1.7-2.0x faster than the FP64-pipe tiles
-// at 1024^2 outputs (about 6900 per SM) and 1.6x slower at 128^2 (about 110
-// per SM); the rule takes them from 512 outputs per SM.
+// per SM to hide.  On GB300, against the best FP64-pipe tile, they run
+// 1.7-2.0x faster at 1024^2 outputs (about 6900 per SM), 1.2-1.6x faster at
+// 256^2 (about 430 per SM) and 1.6x slower at 128^2 (about 110 per SM); the
+// rule takes them from 256 outputs per SM.
 inline bool int_tiles_pay(int64_t m, int64_t n)
 {
-    return m * n >= static_cast<int64_t>(512) * num_sms();
+    return m * n >= static_cast<int64_t>(256) * num_sms();
 }
 
 cudaStream_t current_stream();

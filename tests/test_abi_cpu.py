@@ -224,22 +224,22 @@ def _tile(L, P, t):
 def test_default_tile_rule(L):
     """Without a device the library assumes 152 SMs: the largest candidate
     tile whose CTAs keep >= 90% of the SMs busy in the last wave, else the
-    closest; from 512 outputs per SM (77824) the candidates are the tiles
+    closest; from 256 outputs per SM (38912) the candidates are the tiles
     with TwoSum (DD: and FastTwoSum) on the integer pipes."""
     def pick(P, m, n):
         t = L.mpgemm_default_tile(P, m, n, 64)
         return _tile(L, P, t) + (L.mpgemm_tile_int_ops(P, t),)
     assert pick(4, 1024, 1024) == (16, 16, 1)       # 4096 CTAs: 27 per SM, 99.8%
     assert pick(3, 1024, 1024) == (16, 16, 1)
-    assert pick(4, 256, 256) == (8, 8, 0)           # 65536 outputs; 16x16: 84%; 8x8: 96%
-    assert pick(3, 279, 279) == (8, 8, 1)           # 77841 outputs: 16x16 71%, 8x8 89.5% (closest)
-    assert pick(3, 278, 278) == (8, 8, 0)           # 77284 outputs: below the threshold
+    assert pick(4, 256, 256) == (8, 8, 1)           # 16x16: 256 CTAs, 84%; 8x8: 1024 CTAs, 96%
+    assert pick(3, 198, 198) == (8, 8, 1)           # 39204 outputs: 16x16 56%, 8x8 82% (closest)
+    assert pick(3, 197, 197) == (8, 8, 0)           # 38809 outputs: below the threshold
     assert pick(2, 4096, 4096) == (16, 16, 3)
     assert pick(2, 2048, 2048) == (16, 16, 3)
-    assert pick(2, 256, 256) == (8, 8, 0)           # 32x32: 42%, 16x16: 84%, 8x8: 96%
-    assert pick(2, 128, 128) == (8, 8, 0)           # none reaches 90%; 8x8 comes closest (84%)
-    assert pick(2, 608, 128) == (16, 16, 3)         # 77824 outputs; 38 x 8 = 304 CTAs: two per SM
-    assert pick(2, 607, 128) == (16, 16, 0)         # 77696 outputs; 32x32: 76 CTAs, 50%; 16x16: 100%
+    assert pick(2, 256, 256) == (8, 8, 3)           # 16x16: 84%, 8x8: 96%
+    assert pick(2, 128, 128) == (8, 8, 0)           # 32x32: 11%, 16x16: 42%, 8x8 staging 128: 84%
+    assert pick(2, 304, 128) == (16, 16, 3)         # 38912 outputs; 19 x 8 = 152 CTAs: one per SM
+    assert pick(2, 303, 128) == (16, 16, 0)         # 38784 outputs; 32x32: 40 CTAs, 26%; 16x16: 100%
     assert pick(2, 640, 256) == (8, 8, 3)           # 16x16: 640 CTAs, 84%; 8x8: 2560 CTAs, 99%
     assert L.mpgemm_default_tile(5, 8, 8, 8) == -1 and "P must be" in err(L)
     assert L.mpgemm_default_tile(2, -1, 8, 8) == -1
