@@ -62,8 +62,8 @@ void *mpgemm_get_stream(void);
  * mpgemm_default_tile; 103 adds MPG_ALGO_INT8_CRT, MPG_ALGO_BF16_CRT and
  * mpgemm_crt_beta; 104 adds MPG_ALGO_INT8_CRT_SPLIT, MPG_ALGO_BF16_CRT_SPLIT
  * and mpgemm_crt_split_beta; 105 adds mpgemm_autotune, mpgemm_tuned_tile and
- * mpgemm_tune_cache_reset; 106 adds mpgemm_tile_int_ops and the tiles that
- * compute error-free transformations on the integer pipes. */
+ * mpgemm_tune_cache_reset; 106 adds mpgemm_tile_int_ops, mp_eft_int and the
+ * tiles that compute error-free transformations on the integer pipes. */
 int mpgemm_version(void);
 
 /* ---------------------------------------------------------------------
@@ -78,6 +78,14 @@ int mpgemm_version(void);
 int mp_quick_two_sum(int64_t n, const double *a, const double *b, double *s, double *e);
 int mp_two_sum(int64_t n, const double *a, const double *b, double *s, double *e);
 int mp_two_prod(int64_t n, const double *a, const double *b, double *s, double *e);
+/* The same three transformations (which: 0 QuickTwoSum, 1 TwoSum, 2 TwoProd)
+ * computed on the integer pipes, the form the tiles of mpgemm_tile_int_ops
+ * use: both outputs from one exact integer sum or product of the
+ * significands, with the bits of the operation sequences above for every
+ * input (non-finite operands, overflow, a product error below the subnormal
+ * range and QuickTwoSum with |b| > |a| run the sequence).  Arguments and
+ * errors as above; a `which` outside 0..2 is MPG_EINVAL. */
+int mp_eft_int(int which, int64_t n, const double *a, const double *b, double *s, double *e);
 
 /* ---------------------------------------------------------------------
  * Elementwise multi-component add/mul of SoA vectors (Sec. 2.5):

@@ -103,9 +103,10 @@ static int vec_call(int op, int64_t n, const double* const* x, const double* con
     return e == cudaSuccess ? MPG_OK : cuda_fail(e, "elementwise launch");
 }
 
-static int eft_call(int which, int64_t n, const double* a, const double* b, double* s, double* e)
+static int eft_call(int which, bool int_pipes, int64_t n, const double* a, const double* b, double* s, double* e)
 {
     clear_error();
+    if (which < 0 || which > 2) return fail(MPG_EINVAL, "which must be 0, 1 or 2 (got %d)", which);
     if (n < 0) return fail(MPG_EINVAL, "n must be >= 0 (got %lld)", (long long)n);
     if (n == 0) return MPG_OK;
     if (!a || !b || !s || !e) return fail(MPG_EINVAL, "NULL pointer with n > 0");
@@ -116,7 +117,7 @@ static int eft_call(int which, int64_t n, const double* a, const double* b, doub
         if ((overlap(rs, ri) && in != s) || (overlap(re, ri) && in != e))
             return fail(MPG_EINVAL, "an output partially overlaps an input");
     }
-    cudaError_t err = launch_eft(which, n, a, b, s, e, g_stream);
+    cudaError_t err = launch_eft(which, int_pipes, n, a, b, s, e, g_stream);
     return err == cudaSuccess ? MPG_OK : cuda_fail(err, "eft launch");
 }
 
@@ -368,11 +369,13 @@ void* mpgemm_get_stream(void) { return static_cast<void*>(g_stream); }
 int mpgemm_version(void) { return 106; }
 
 int mp_quick_two_sum(int64_t n, const double* a, const double* b, double* s, double* e)
-{ return eft_call(0, n, a, b, s, e); }
+{ return eft_call(0, false, n, a, b, s, e); }
 int mp_two_sum(int64_t n, const double* a, const double* b, double* s, double* e)
-{ return eft_call(1, n, a, b, s, e); }
+{ return eft_call(1, false, n, a, b, s, e); }
 int mp_two_prod(int64_t n, const double* a, const double* b, double* s, double* e)
-{ return eft_call(2, n, a, b, s, e); }
+{ return eft_call(2, false, n, a, b, s, e); }
+int mp_eft_int(int which, int64_t n, const double* a, const double* b, double* s, double* e)
+{ return eft_call(which, true, n, a, b, s, e); }
 
 int mp_dd_add(int64_t n, const double* const x[2], const double* const y[2], double* const r[2])
 { return vec_call<2>(0, n, x, y, r); }

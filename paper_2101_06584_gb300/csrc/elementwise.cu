@@ -111,12 +111,14 @@ __global__ void __launch_bounds__(256) vec_dd_x4_kernel(const VecArgs<2> a)
     }
 }
 
-template <int W>
+// INTS: 0 for the operation sequences on the FP64 pipe, 7 for the integer-pipe
+// form of all three transformations (mp::RnInt).
+template <int W, unsigned INTS>
 __global__ void __launch_bounds__(256)
 eft_kernel(int64_t n, const double* a, const double* b, double* s,
            double* e)
 {
-    const mp::Rn f = mp::make_rn();
+    const mp::RnInt<INTS> f(mp::make_rn());
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
          i += stride) {
@@ -199,16 +201,23 @@ template cudaError_t launch_vec<3>(int, int64_t, const double* const*, const dou
 template cudaError_t launch_vec<4>(int, int64_t, const double* const*, const double* const*,
                                    double* const*, cudaStream_t);
 
-cudaError_t launch_eft(int which, int64_t n, const double* a, const double* b, double* s,
-                       double* e, cudaStream_t st)
+template <unsigned INTS>
+static cudaError_t launch_eft_form(int which, int64_t n, const double* a, const double* b, double* s, double* e,
+                                   cudaStream_t st)
 {
     switch (which) {
-    case 0: eft_kernel<0><<<grid_for(eft_kernel<0>, n), 256, 0, st>>>(n, a, b, s, e); break;
-    case 1: eft_kernel<1><<<grid_for(eft_kernel<1>, n), 256, 0, st>>>(n, a, b, s, e); break;
-    case 2: eft_kernel<2><<<grid_for(eft_kernel<2>, n), 256, 0, st>>>(n, a, b, s, e); break;
+    case 0: eft_kernel<0, INTS><<<grid_for(eft_kernel<0, INTS>, n), 256, 0, st>>>(n, a, b, s, e); break;
+    case 1: eft_kernel<1, INTS><<<grid_for(eft_kernel<1, INTS>, n), 256, 0, st>>>(n, a, b, s, e); break;
+    case 2: eft_kernel<2, INTS><<<grid_for(eft_kernel<2, INTS>, n), 256, 0, st>>>(n, a, b, s, e); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_eft(int which, bool int_pipes, int64_t n, const double* a, const double* b, double* s,
+                       double* e, cudaStream_t st)
+{
+    return int_pipes ? launch_eft_form<7>(which, n, a, b, s, e, st) : launch_eft_form<0>(which, n, a, b, s, e, st);
 }
 
 }  // namespace mpg

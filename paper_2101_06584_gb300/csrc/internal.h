@@ -62,8 +62,9 @@ cudaError_t launch_zero(const GemmArgs<P>& g, cudaStream_t s);
 template <int P>
 cudaError_t launch_vec(int op, int64_t n, const double* const* x, const double* const* y,
                        double* const* r, cudaStream_t s);
-// which: 0 QuickTwoSum, 1 TwoSum, 2 TwoProd
-cudaError_t launch_eft(int which, int64_t n, const double* a, const double* b, double* s,
+// which: 0 QuickTwoSum, 1 TwoSum, 2 TwoProd; int_pipes: the integer-pipe form
+// (mp::RnInt) instead of the operation sequence.
+cudaError_t launch_eft(int which, bool int_pipes, int64_t n, const double* a, const double* b, double* s,
                        double* e, cudaStream_t st);
 
 int num_sms();

@@ -58,6 +58,7 @@ def _declare(L):
     L.mpgemm_get_stream.restype = vp
     for f in ("mp_quick_two_sum", "mp_two_sum", "mp_two_prod"):
         getattr(L, f).argtypes = [i64, vp, vp, vp, vp]
+    L.mp_eft_int.argtypes = [i, i64, vp, vp, vp, vp]
     for f in ("mp_dd_add", "mp_dd_mul", "mp_td_add", "mp_td_add_merge", "mp_td_mul", "mp_td_mul_q",
               "mp_td_mul_accurate", "mp_qd_add", "mp_qd_mul", "mp_qd_add_accurate"):
         getattr(L, f).argtypes = [i64, vp, vp, vp]
@@ -244,16 +245,26 @@ def vec(prec, op, x, y, out=None):
     return out
 
 
-def eft(which, a, b):
-    """Elementwise EFT (quick_two_sum | two_sum | two_prod) of 1-D tensors; returns (s, e)."""
+EFT_WHICH = {"quick_two_sum": 0, "two_sum": 1, "two_prod": 2}
+
+
+def eft(which, a, b, int_pipes=False):
+    """Elementwise EFT (quick_two_sum | two_sum | two_prod) of 1-D tensors; returns (s, e).
+
+    With int_pipes the transformations run in their integer-pipe form
+    (mp_eft_int), which returns the same bits."""
     for t, nm in ((a, "a"), (b, "b")):
         _require(t, nm)
     if a.shape != b.shape or a.dim() != 1:
         raise ValueError("a and b must be 1-D of equal length")
     s, e = torch.empty_like(a), torch.empty_like(a)
     _bind_stream()
-    check(getattr(lib(), "mp_" + which)(a.numel(), a.data_ptr(), b.data_ptr(), s.data_ptr(),
-                                        e.data_ptr()))
+    if int_pipes:
+        check(lib().mp_eft_int(EFT_WHICH[which], a.numel(), a.data_ptr(), b.data_ptr(), s.data_ptr(),
+                               e.data_ptr()))
+    else:
+        check(getattr(lib(), "mp_" + which)(a.numel(), a.data_ptr(), b.data_ptr(), s.data_ptr(),
+                                            e.data_ptr()))
     return s, e
 
 

@@ -193,6 +193,13 @@ def test_vector_validation(L):
     assert L.mp_dd_mul(100, x, y, bad) == -1
     assert "overlap" in err(L)
     assert L.mp_two_sum(10, FAKE, 2 * FAKE, 3 * FAKE, 3 * FAKE + 8) == -1
+    # the integer-pipe form validates the same way, and its selector
+    assert L.mp_eft_int(1, 0, None, None, None, None) == 0
+    assert L.mp_eft_int(3, 4, FAKE, 2 * FAKE, 3 * FAKE, 4 * FAKE) == -1 and "which" in err(L)
+    assert L.mp_eft_int(-1, 4, FAKE, 2 * FAKE, 3 * FAKE, 4 * FAKE) == -1
+    assert L.mp_eft_int(2, -1, FAKE, 2 * FAKE, 3 * FAKE, 4 * FAKE) == -1
+    assert L.mp_eft_int(0, 10, FAKE, 2 * FAKE, 3 * FAKE, 3 * FAKE + 8) == -1 and "overlap" in err(L)
+    assert L.mp_eft_int(2, 4, None, 2 * FAKE, 3 * FAKE, 4 * FAKE) == -1
 
 
 def test_tile_table(L):
