@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
+from edge_operands import edge_operands, same_bits
 from gpu_util import assert_bitwise, dev, host, torch_cuda
 from paper_2101_06584_gb300 import inputs as I
 
@@ -35,63 +36,6 @@ def test_eft_bitwise(torch, which):
     assert_bitwise(host(e), we, which + " e")
 
 
-def _bits_to_f64(u):
-    return np.asarray(u, dtype=np.uint64).view(np.float64)
-
-
-def _edge_operands(n, rng):
-    """a, b of 10 * n elements in ten classes: any bit pattern (NaN and
-    infinity included), moderate, tiny (subnormal), huge, near-cancelling,
-    exponent gaps 0-70 in either order, products near the subnormal and the
-    overflow boundaries, zeros of both signs among small values, and short
-    significands (ties)."""
-    def bits(k):
-        return rng.integers(0, 2 ** 64 - 1, k, dtype=np.uint64, endpoint=True)
-
-    def with_exp(k, lo, hi):
-        m = bits(k) & np.uint64(0x800FFFFFFFFFFFFF)
-        e = rng.integers(lo, hi + 1, k).astype(np.uint64) << np.uint64(52)
-        return _bits_to_f64(m | e)
-
-    A, B = [], []
-    a, b = _bits_to_f64(bits(n)), _bits_to_f64(bits(n))
-    special = np.array([np.inf, -np.inf, np.nan, 0.0, -0.0])
-    a[::97] = special[rng.integers(0, 5, a[::97].size)]
-    b[::89] = special[rng.integers(0, 5, b[::89].size)]
-    A.append(a); B.append(b)
-    A.append(with_exp(n, 1003, 1043)); B.append(with_exp(n, 1003, 1043))
-    A.append(with_exp(n, 0, 60)); B.append(with_exp(n, 0, 60))
-    A.append(with_exp(n, 2000, 2046)); B.append(with_exp(n, 1003, 2046))
-    a = with_exp(n, 1003, 1043)
-    b = _bits_to_f64((a.view(np.uint64) ^ np.uint64(1 << 63))
-                     + rng.integers(-32, 33, n).astype(np.int64).view(np.uint64))
-    A.append(a); B.append(b)
-    a = with_exp(n, 1003, 1043)
-    b = np.ldexp(with_exp(n, 1023, 1023), -rng.integers(0, 71, n)) * np.abs(a)
-    sw = rng.integers(0, 2, n).astype(bool)
-    A.append(np.where(sw, b, a)); B.append(np.where(sw, a, b))
-    A.append(np.ldexp(1.0 + rng.random(n), -rng.integers(480, 600, n)) * rng.choice([-1.0, 1.0], n))
-    B.append(np.ldexp(1.0 + rng.random(n), -rng.integers(480, 600, n)))
-    A.append(np.ldexp(1.0 + rng.random(n), rng.integers(500, 530, n)))
-    B.append(np.ldexp(1.0 + rng.random(n), rng.integers(490, 530, n)) * rng.choice([-1.0, 1.0], n))
-    small = np.array([0.0, -0.0, 1.0, -1.0, 5e-324, -5e-324])
-    a = small[rng.integers(0, 6, n)]
-    a = np.where(rng.integers(0, 2, n).astype(bool), with_exp(n, 1003, 1043), a)
-    b = small[rng.integers(0, 6, n)]
-    sw = rng.integers(0, 2, n).astype(bool)
-    A.append(np.where(sw, b, a)); B.append(np.where(sw, a, b))
-    a = rng.integers(0, 2 ** 53, n).astype(np.float64) * np.ldexp(1.0, -rng.integers(0, 60, n))
-    b = np.ldexp(1.0, rng.integers(-30, 30, n)) * rng.choice([1.5, -1.0], n)
-    A.append(a); B.append(b)
-    return np.concatenate(A), np.concatenate(B)
-
-
-def _same_bits(x, y):
-    """Bit-identical, any two NaNs counting as equal."""
-    x, y = np.asarray(x), np.asarray(y)
-    return (x.view(np.uint64) == y.view(np.uint64)) | (np.isnan(x) & np.isnan(y))
-
-
 @pytest.mark.parametrize("which", ["quick_two_sum", "two_sum", "two_prod"])
 def test_eft_integer_pipes_bitwise(torch, which):
     """The integer-pipe form of each transformation (mp_eft_int, the form of
@@ -101,12 +45,12 @@ def test_eft_integer_pipes_bitwise(torch, which):
     |b| > |a|; where every value is finite it also equals the oracle."""
     from paper_2101_06584_gb300 import mpgemm
     rng = np.random.default_rng(300 + len(which))
-    a, b = _edge_operands(100_003, rng)
+    a, b = edge_operands(100_003, rng)
     with np.errstate(all="ignore"):
         si, ei = (host(t) for t in mpgemm.eft(which, dev(torch, a), dev(torch, b), int_pipes=True))
         ss, es = (host(t) for t in mpgemm.eft(which, dev(torch, a), dev(torch, b)))
         for got, want, nm in ((si, ss, "s"), (ei, es, "e")):
-            ok = _same_bits(got, want)
+            ok = same_bits(got, want)
             bad = np.flatnonzero(~ok)
             assert ok.all(), "%s %s: %d mismatches, first a=%r b=%r got %r want %r" % (
                 which, nm, bad.size, a[bad[0]], b[bad[0]], got[bad[0]], want[bad[0]])

@@ -1,0 +1,74 @@
+"""The integer-pipe error-free transformations (the device header
+soft_fp64.cuh, Sec. 2.1's TwoSum, FastTwoSum and TwoProd formed from one
+exact integer sum or product) compiled for the host and checked bit for bit
+against the oracle's operation sequences, on every class of edge_operands:
+NaN and infinity, subnormals, overflow, near-cancellation, exponent gaps
+0-70 in either order, products at the subnormal and overflow boundaries,
+signed zeros and ties.  The same property holds on the GPU
+(test_gpu_elementwise.py); this check runs without one."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from edge_operands import edge_operands, same_bits
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_2101_06584_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def soft(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    out = str(tmp_path_factory.mktemp("soft") / "libsofteft.so")
+    subprocess.run([cxx, "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-I", CSRC,
+                    os.path.join(HERE, "soft_eft_host.cpp"), "-o", out], check=True)
+    L = ctypes.CDLL(out)
+    L.soft_eft_host.argtypes = [ctypes.c_int, ctypes.c_long] + [ctypes.c_void_p] * 4
+    L.soft_eft_host.restype = None
+    return L
+
+
+def _run(L, which, a, b):
+    a, b = np.ascontiguousarray(a), np.ascontiguousarray(b)
+    s, e = np.empty_like(a), np.empty_like(a)
+    idx = {"quick_two_sum": 0, "two_sum": 1, "two_prod": 2}[which]
+    L.soft_eft_host(idx, a.size, a.ctypes.data, b.ctypes.data, s.ctypes.data, e.ctypes.data)
+    return s, e
+
+
+@pytest.mark.parametrize("which", ["quick_two_sum", "two_sum", "two_prod"])
+def test_integer_form_equals_sequence(soft, which):
+    rng = np.random.default_rng(700 + len(which))
+    a, b = edge_operands(50_000, rng)
+    s, e = _run(soft, which, a, b)
+    with np.errstate(all="ignore"):
+        ws, we = oracle.vec_eft(which, a, b)
+    for got, want, nm in ((s, ws, "s"), (e, we, "e")):
+        ok = same_bits(got, want)
+        bad = np.flatnonzero(~ok)
+        assert ok.all(), "%s %s: %d mismatches, first a=%r b=%r got %r want %r" % (
+            which, nm, bad.size, a[bad[0]], b[bad[0]], got[bad[0]], want[bad[0]])
+
+
+def test_signed_zero_errors(soft):
+    """The zero conventions the sequences fix: TwoSum's exact zero error is
+    +0; FastTwoSum returns b itself when b is a zero; TwoProd of a zero
+    operand gives the signed zero product and a +0 error."""
+    a = np.array([1.0, 1.0, -0.0, -0.0, 3.0, -2.5])
+    b = np.array([-0.0, 0.0, -0.0, 0.0, -3.0, 0.0])
+    s, e = _run(soft, "two_sum", a, b)
+    assert same_bits(e, np.zeros(6)).all()
+    assert same_bits(s, np.array([1.0, 1.0, -0.0, 0.0, 0.0, -2.5])).all()
+    s, e = _run(soft, "quick_two_sum", a, b)
+    assert same_bits(e, np.array([-0.0, 0.0, -0.0, 0.0, 0.0, 0.0])).all()
+    s, e = _run(soft, "two_prod", np.array([-0.0, 5.0, -7.0]), np.array([3.0, -0.0, 0.0]))
+    assert same_bits(s, np.array([-0.0, -0.0, -0.0])).all()
+    assert same_bits(e, np.zeros(3)).all()
+
