@@ -400,7 +400,10 @@ size_t mpgemm_batch_workspace_size(int P, int count, const mpgemm_problem *probl
 /* Validate every problem (as mpgemm_ex; a bad one fails the whole call with
  * its message), split them into output tiles -- 16 x 16 for problems with
  * m*n below the policy's threshold, 32 x 32 otherwise; policy 0..4 =
- * threshold 0, 2048, 8192, 32768, never -- sort the tiles by decreasing work,
+ * threshold 0, 2048, 8192, 32768, never; policy 5 = 16 x 16 tiles throughout
+ * with the error-free transformations on the integer pipes (TwoSum, and for
+ * P = 2 FastTwoSum, as in mpgemm_tile_int_ops; same results) -- sort the
+ * tiles by decreasing work,
  * copy the descriptors into `workspace` (device, 256-byte aligned, caller-
  * owned, kept alive and unmodified while the plan is used) on the current
  * stream and wait for that copy, and capture one persistent launch in a CUDA

@@ -13,7 +13,10 @@
 //
 // Tile kinds: 0 = 16 x 16 outputs, 1 thread each; 1 = 32 x 32 outputs, 2 x 2
 // per thread; both 256 threads.  A policy decides the kind per problem:
-// kind 1 when m * n >= threshold(policy), else kind 0.
+// kind 1 when m * n >= threshold(policy), else kind 0.  Policies 0-4 run the
+// arithmetic on the FP64 pipe; policy 5 puts every problem in 16 x 16 tiles
+// whose transformations run on the integer pipes as in the GEMM tiles of
+// mpgemm_tile_int_ops (TwoSum, and for DD FastTwoSum), same bits.
 #include "mpgemm.h"
 #include "gemm_kernel.cuh"
 
@@ -42,8 +45,13 @@ struct BatchDev {
     int n_items;
 };
 
-constexpr int kNumPolicies = 5;
-const int64_t kPolicyThreshold[kNumPolicies] = {0, 2048, 8192, 32768, INT64_MAX};
+constexpr int kNumPolicies = 6;
+constexpr int kIntPolicy = 5;
+const int64_t kPolicyThreshold[kNumPolicies] = {0, 2048, 8192, 32768, INT64_MAX, INT64_MAX};
+
+// The transformations policy kIntPolicy computes on the integer pipes.
+template <int P>
+constexpr unsigned int_mask() { return P == 2 ? 3u : 1u; }
 
 template <int P>
 __host__ __device__ constexpr size_t batch_smem_bytes()
@@ -53,12 +61,14 @@ __host__ __device__ constexpr size_t batch_smem_bytes()
                : sizeof(KseqSmem<P, 16, 16, 16>);
 }
 
-template <int P>
-__global__ void __launch_bounds__(256) batched_kernel(const BatchDev<P> b)
+// The persistent loop.  INTS: the transformations on the integer pipes
+// (mp::RnInt's mask); with a nonzero mask every item is a 16 x 16 tile.
+template <int P, unsigned INTS>
+__device__ __forceinline__ void batched_body(const BatchDev<P>& b)
 {
     __shared__ __align__(16) unsigned char smem[batch_smem_bytes<P>()];
     __shared__ int s_item;
-    const mp::Rn f = mp::make_rn();
+    const mp::RnInt<INTS> f(mp::make_rn());
     for (;;) {
         if (threadIdx.x == 0) s_item = static_cast<int>(atomicAdd(&b.counters[0], 1u));
         __syncthreads();
@@ -67,11 +77,11 @@ __global__ void __launch_bounds__(256) batched_kernel(const BatchDev<P> b)
         if (it >= b.n_items) break;
         const BatchItem w = b.items[it];
         const GemmArgs<P> g = b.probs[w.problem];
-        if (w.kind == 0) {
+        if (INTS != 0u || w.kind == 0) {
             kseq_tile<P, 16, 16, 16, 1, 1>(g, static_cast<int64_t>(w.tile_m) * 16,
                                            static_cast<int64_t>(w.tile_n) * 16,
                                            *reinterpret_cast<KseqSmem<P, 16, 16, 16>*>(smem), f);
-        } else {
+        } else if constexpr (INTS == 0u) {
             kseq_tile<P, 32, 32, 16, 2, 2>(g, static_cast<int64_t>(w.tile_m) * 32,
                                            static_cast<int64_t>(w.tile_n) * 32,
                                            *reinterpret_cast<KseqSmem<P, 32, 32, 16>*>(smem), f);
@@ -85,6 +95,21 @@ __global__ void __launch_bounds__(256) batched_kernel(const BatchDev<P> b)
             atomicExch(&b.counters[1], 0u);
         }
     }
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) batched_kernel(const BatchDev<P> b)
+{
+    batched_body<P, 0u>(b);
+}
+
+// Policy kIntPolicy.  Three CTAs per SM (at most 85 registers, as the GEMM's
+// own 16 x 16 integer-pipe tile uses) give the integer pipes the warps that
+// hide their latency.
+template <int P>
+__global__ void __launch_bounds__(256, 3) batched_int_kernel(const BatchDev<P> b)
+{
+    batched_body<P, int_mask<P>()>(b);
 }
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -173,8 +198,10 @@ static int build_plan(int count, const mpgemm_problem* probs, int policy, void* 
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return set_error(MPG_ECUDA, cudaGetErrorString(e));
 
+    const bool ints = policy == kIntPolicy;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel<P>, 256, 0);
+    e = ints ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_int_kernel<P>, 256, 0)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel<P>, 256, 0);
     if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     int grid = num_sms() * per_sm;
     if (grid > d.n_items) grid = d.n_items > 0 ? d.n_items : 1;
@@ -183,7 +210,8 @@ static int build_plan(int count, const mpgemm_problem* probs, int policy, void* 
     e = cudaStreamCreateWithFlags(&plan->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(plan->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        batched_kernel<P><<<grid, 256, 0, plan->cap_stream>>>(d);
+        if (ints) batched_int_kernel<P><<<grid, 256, 0, plan->cap_stream>>>(d);
+        else batched_kernel<P><<<grid, 256, 0, plan->cap_stream>>>(d);
         const cudaError_t le = cudaGetLastError();
         e = cudaStreamEndCapture(plan->cap_stream, &plan->graph);
         if (le != cudaSuccess) e = le;
@@ -248,7 +276,7 @@ int mpgemm_batch_plan_create(int P, int count, const mpgemm_problem* problems, i
     *out = nullptr;
     if (P < 2 || P > 4) return set_error(MPG_EINVAL, "P must be 2, 3 or 4");
     if (count < 0 || (count > 0 && !problems)) return set_error(MPG_EINVAL, "bad problem list");
-    if (policy < 0 || policy >= kNumPolicies) return set_error(MPG_EINVAL, "policy must be in 0..4");
+    if (policy < 0 || policy >= kNumPolicies) return set_error(MPG_EINVAL, "policy must be in 0..5");
     if (!workspace) return set_error(MPG_EWORKSPACE, "a batch needs a workspace");
     if (reinterpret_cast<uintptr_t>(workspace) % 256)
         return set_error(MPG_EWORKSPACE, "workspace must be 256-byte aligned");
