@@ -1,8 +1,9 @@
-// Host build of the integer-pipe error-free transformations, for the CPU
-// tests: the device header compiled as plain C++, with the CUDA bit-cast,
-// count and high-multiply intrinsics it uses written out for the host and
-// its rare-input sequences on the host's IEEE binary64 operations.  Built
-// with -ffp-contract=off so every operation rounds once.
+// Host build of the device arithmetic, for the CPU tests: soft_fp64.cuh
+// (the integer-pipe error-free transformations) and mp_arith.cuh (the
+// DD/TD/QD operations under each arithmetic policy) compiled as plain C++,
+// with the CUDA bit-cast, count and high-multiply intrinsics they use written
+// out for the host and their binary64 operations on the host's IEEE
+// arithmetic.  Built with -ffp-contract=off so every operation rounds once.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -55,7 +56,12 @@ static inline double __dsub_rn(double a, double b) { return a - b; }
 static inline double __dmul_rn(double a, double b) { return a * b; }
 static inline double __fma_rn(double a, double b, double c) { return std::fma(a, b, c); }
 
-#include "soft_fp64.cuh"
+struct HostThreadIdx {
+    unsigned x;
+};
+static const HostThreadIdx threadIdx = {0u};
+
+#include "mp_arith.cuh"
 
 // which: 0 QuickTwoSum, 1 TwoSum, 2 TwoProd, elementwise over n pairs.
 extern "C" void soft_eft_host(int which, long n, const double* a, const double* b, double* s, double* e)
@@ -67,4 +73,36 @@ extern "C" void soft_eft_host(int which, long n, const double* a, const double* 
         s[i] = r.hi;
         e[i] = r.lo;
     }
+}
+
+// acc := add(acc, mul(a, b)), the GEMM's multiply-add of precision P, on
+// n AoS values (P doubles each), with the transformations in `mask` computed
+// on the integer pipes (mp::RnInt<mask>; 0 = the operation sequences).
+template <int P, unsigned MASK>
+static void mad_n(long n, double* acc, const double* a, const double* b)
+{
+    const mp::RnInt<MASK> f(mp::make_rn());
+    for (long i = 0; i < n; ++i) mp::mad<P>(f, acc + P * i, a + P * i, b + P * i);
+}
+
+template <int P>
+static void mad_mask(unsigned mask, long n, double* acc, const double* a, const double* b)
+{
+    switch (mask) {
+    case 0: mad_n<P, 0>(n, acc, a, b); break;
+    case 1: mad_n<P, 1>(n, acc, a, b); break;
+    case 2: mad_n<P, 2>(n, acc, a, b); break;
+    case 3: mad_n<P, 3>(n, acc, a, b); break;
+    case 4: mad_n<P, 4>(n, acc, a, b); break;
+    case 5: mad_n<P, 5>(n, acc, a, b); break;
+    case 6: mad_n<P, 6>(n, acc, a, b); break;
+    default: mad_n<P, 7>(n, acc, a, b); break;
+    }
+}
+
+extern "C" void mad_host(int P, unsigned mask, long n, double* acc, const double* a, const double* b)
+{
+    if (P == 2) mad_mask<2>(mask, n, acc, a, b);
+    else if (P == 3) mad_mask<3>(mask, n, acc, a, b);
+    else mad_mask<4>(mask, n, acc, a, b);
 }

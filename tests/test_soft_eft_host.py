@@ -4,8 +4,11 @@ exact integer sum or product) compiled for the host and checked bit for bit
 against the oracle's operation sequences, on every class of edge_operands:
 NaN and infinity, subnormals, overflow, near-cancellation, exponent gaps
 0-70 in either order, products at the subnormal and overflow boundaries,
-signed zeros and ties.  The same property holds on the GPU
-(test_gpu_elementwise.py); this check runs without one."""
+signed zeros and ties.  Then the GEMM's whole multiply-add (mp_arith.cuh,
+DDmul + DDadd, TDmul + TDaddq, QDmul + QDadd) under every arithmetic policy
+equals the oracle's, step after step of a k-loop.  The same properties hold
+on the GPU (test_gpu_elementwise.py, and every tile of test_gpu_gemm.py);
+these checks run without one."""
 import ctypes
 import os
 import shutil
@@ -16,6 +19,7 @@ import pytest
 
 import oracle
 from edge_operands import edge_operands, same_bits
+from paper_2101_06584_gb300 import inputs as I
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(os.path.dirname(HERE), "paper_2101_06584_gb300", "csrc")
@@ -32,6 +36,8 @@ def soft(tmp_path_factory):
     L = ctypes.CDLL(out)
     L.soft_eft_host.argtypes = [ctypes.c_int, ctypes.c_long] + [ctypes.c_void_p] * 4
     L.soft_eft_host.restype = None
+    L.mad_host.argtypes = [ctypes.c_int, ctypes.c_uint, ctypes.c_long] + [ctypes.c_void_p] * 3
+    L.mad_host.restype = None
     return L
 
 
@@ -72,3 +78,36 @@ def test_signed_zero_errors(soft):
     assert same_bits(s, np.array([-0.0, -0.0, -0.0])).all()
     assert same_bits(e, np.zeros(3)).all()
 
+
+
+def _mad(L, P, mask, acc, a, b):
+    """acc := add(acc, mul(a, b)) on SoA (P, n) arrays through the host build."""
+    acc_aos = np.ascontiguousarray(acc.T)
+    a_aos, b_aos = np.ascontiguousarray(a.T), np.ascontiguousarray(b.T)
+    L.mad_host(P, mask, acc_aos.shape[0], acc_aos.ctypes.data, a_aos.ctypes.data, b_aos.ctypes.data)
+    return np.ascontiguousarray(acc_aos.T)
+
+
+@pytest.mark.parametrize("prec", ["dd", "td", "qd"])
+def test_multiply_add_every_policy(soft, prec):
+    """Sixteen steps of acc := add(acc, mul(a_j, b_j)) on 4000 random and the
+    edge operand pairs (zeros, cancellation, ties, subnormal values and
+    products): every mask of integer-pipe transformations gives the oracle's
+    bits after every step."""
+    P = I.P_OF[prec]
+    rng = np.random.default_rng(720 + P)
+    ex, ey = I.edge_mp(P)
+    n_edge = ex.shape[1]
+    n = 4000 + n_edge
+    acc = {m: np.zeros((P, n)) for m in (0, 1, 2, 3, 4, 7)}
+    want = np.zeros((P, n))
+    for step in range(16):
+        a = I.random_mp(P, n, rng)
+        b = I.random_mp(P, n, rng)
+        a[:, :n_edge], b[:, :n_edge] = (ex, ey) if step % 2 == 0 else (ey, ex)
+        want = oracle.vec_op(prec, "add", want, oracle.vec_op(prec, "mul", a, b))
+        for m in acc:
+            acc[m] = _mad(soft, P, m, acc[m], a, b)
+            ok = same_bits(acc[m], want)
+            bad = np.argwhere(~ok)
+            assert ok.all(), "%s mask %d step %d: %d mismatches, first %s" % (prec, m, step, len(bad), bad[0])
