@@ -1,10 +1,13 @@
 // gemm_kernel.cuh -- FP64-EFT GEMM kernels, C := op(A) op(B) (Sec. 3, Eq. 1).
 //
-// Both kernels are bound by the FP64 pipe: a DD multiply-add is 20 binary64
-// operations, TD about 130, QD about 210, against roughly two FP64 lanes per
-// clock per SM on GB300, so operand traffic is negligible and the design
-// goal is to keep the FP64 pipe fed with independent work while issuing no
-// FP64 instruction the algorithms do not need.
+// Both kernels are bound by arithmetic, not operand traffic: a DD
+// multiply-add is 20 binary64 operations, TD 128, QD 210, against roughly two
+// FP64 lanes per clock per SM on GB300.  With the operation sequences (policy
+// Rn) the goal is to keep the FP64 pipe fed with independent work while
+// issuing no FP64 instruction the algorithms do not need; with the policy
+// RnInt<mask> the transformations in the mask run on the integer pipes beside
+// it (QD: 78 of the 210 operations stay on the FP64 pipe with TwoSum moved),
+// and the bound becomes the latency of those integer chains.
 //
 // gemm_kseq_kernel: a CTA owns a BM x BN tile of C; each thread owns TM x TN
 //   entries (strided so that smem reads are broadcasts / consecutive) and
