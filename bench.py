@@ -1120,10 +1120,11 @@ class Batched(Workload):
 
     def roofline(self, launch_ms, pk):
         ms = statistics.mean(launch_ms["qd"])
-        ach = self.mads_per * FP64_OPS_PER_MAD["qd"] / (ms * 1e-3)
-        return {"bound": "alu", "kernel": "batched_kernel<4> (QD, persistent)",
-                "achieved": ach / 1e12, "peak": pk["dfma"] / 1e12, "unit": "TFP64op/s",
-                "frac": ach / pk["dfma"], "traffic": None, "ops_per_unit": FP64_OPS_PER_MAD["qd"],
+        policy = self.plans["qd"].policy
+        ints = self.mm.batch_int_ops("qd", policy)
+        r = kseq_roofline("qd", self.mads_per, ms, pk, {"int_ops": ints})
+        kern = "batched_int_kernel<4>" if ints else "batched_kernel<4>"
+        return {**r, "kernel": "%s (QD, persistent, policy %d)" % (kern, policy), "traffic": None,
                 "unit_of_work": "QD multiply-add", "units_per_launch": self.mads_per,
                 "per_precision_mad_s": {p: self.mads_per / (statistics.mean(launch_ms[p]) * 1e-3)
                                         for p in ("dd", "qd")}}

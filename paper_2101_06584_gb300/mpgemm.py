@@ -369,6 +369,18 @@ def _problem(prec, A, B, C, trans_a=False, trans_b=False):
     return q
 
 
+# Batch policies: 0-4 split problems into 16 x 16 or 32 x 32 tiles by an m*n
+# threshold on the FP64-pipe arithmetic; BATCH_INT_POLICY puts every problem
+# in 16 x 16 tiles with TwoSum (and for DD FastTwoSum) on the integer pipes.
+BATCH_POLICIES = 6
+BATCH_INT_POLICY = 5
+
+
+def batch_int_ops(prec, policy):
+    """The mpgemm_tile_int_ops-style mask a batch policy runs with."""
+    return (3 if P_OF[prec] == 2 else 1) if policy == BATCH_INT_POLICY else 0
+
+
 class BatchPlan:
     """A batch of independent products (A_i, B_i, C_i) in precision ``prec``,
     run as one persistent kernel replayed from a CUDA graph.  ``policy`` None

@@ -41,7 +41,7 @@ def test_batch_bitwise_every_policy(torch, prec):
               (7, 0, 3), (9, 12, 0), (33, 31, 65), (48, 16, 1)]
     triples, host_in = _make(torch, prec, shapes, rng, trans=True)
     wants = [oracle.gemm(prec, A, B, nthreads=4) for A, B in host_in]
-    for policy in range(6):                  # 5: integer-pipe transformations
+    for policy in range(mm.BATCH_POLICIES):  # mm.BATCH_INT_POLICY: integer-pipe transformations
         for (_, _, C, _, _) in triples:
             C.fill_(float("nan"))
         plan = mm.BatchPlan(prec, triples, policy=policy)
@@ -64,7 +64,7 @@ def test_autotune_and_large_batch(torch):
     shapes = I.batch_shapes(512, rng)
     triples, host_in = _make(torch, "dd", shapes, rng)
     plan = mm.BatchPlan("dd", triples, policy=None, reps=1)
-    assert 0 <= plan.policy <= 5 and plan.tune_ms > 0
+    assert 0 <= plan.policy < mm.BATCH_POLICIES and plan.tune_ms > 0
     plan.run()
     torch.cuda.synchronize()
     srng = np.random.default_rng(710)
