@@ -121,3 +121,32 @@ def test_bench_exact_products_refuse_extreme_ranges():
     B = np.full((1, 3, 2), 2.0 ** -500)
     with pytest.raises(ValueError):
         bench.ExactReference(A, B, [(0, 0)])
+
+
+def test_eft_mix_adds_up_to_the_operation_counts():
+    """(TwoSum, FastTwoSum, TwoProd, other) per multiply-add, weighted 6, 3, 2
+    and 1 binary64 operations, give the implemented sequences' counts."""
+    for prec, (ts, qts, tp, other) in bench.EFT_MIX.items():
+        assert 6 * ts + 3 * qts + 2 * tp + other == bench.FP64_OPS_PER_MAD[prec]
+
+
+def test_kseq_bound_and_roofline():
+    """The bound of a tile is the larger of its FP64-pipe time and its
+    integer-pipe time; with no transformation moved it is the DFMA time, and
+    the roofline's peak is the algorithm's operations at that bound."""
+    pk = {"dfma": 6.0e11, "int_two_sum": 1.5e11, "int_fast_two_sum": 1.8e11, "int_two_prod": 2.4e11}
+    s, f64 = bench.kseq_bound("qd", 0, pk)
+    assert f64 == 210 and s == pytest.approx(210 / 6.0e11)
+    s, f64 = bench.kseq_bound("qd", 1, pk)                  # 22 TwoSums moved
+    assert f64 == 78 and s == pytest.approx(max(78 / 6.0e11, 22 / 1.5e11))
+    s, f64 = bench.kseq_bound("dd", 3, pk)                  # TwoSum + 2 FastTwoSums moved
+    assert f64 == 8 and s == pytest.approx(max(8 / 6.0e11, 1 / 1.5e11 + 2 / 1.8e11))
+    s, f64 = bench.kseq_bound("td", 7, pk)
+    assert f64 == 8 and s == pytest.approx(14 / 1.5e11 + 10 / 1.8e11 + 3 / 2.4e11)
+    r = bench.kseq_roofline("qd", 10 ** 9, 200.0, pk, {"int_ops": 1})
+    ach = 10 ** 9 * 210 / 0.2
+    assert r["achieved"] == pytest.approx(ach / 1e12)
+    assert r["peak"] == pytest.approx(210 / (22 / 1.5e11) / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["frac_of_fp64_pipe_alone"] == pytest.approx(ach / 6.0e11)
+    assert r["int_ops"] == 1 and r["fp64_pipe_ops_per_unit"] == 78
