@@ -20,14 +20,17 @@
 // an integer significand m < 2^53 and an effective biased exponent e >= 1
 // (m has bit 52 set for normal numbers, e = 1 for subnormal ones).
 //
-// Rounding of a sum: the larger operand's significand is placed at bit 56 (4
-// spare bits), the smaller one aligned below it with one extra bit: the
-// aligned value shifted left by one, its lowest bit set when anything was
-// shifted out.  That bit stands for a remainder strictly inside (0, 2) units
-// of the extra bit, and the difference is odd whenever it is set, so the
-// true sum lies strictly between the two even neighbours of the computed one
-// and the guard and sticky bits three and more places up are those of the
-// exact sum -- for subtraction as well as addition.
+// Rounding of a sum: the larger operand's significand is placed at bit 56,
+// leaving four bits below its last place, and the smaller one is aligned
+// below it with one extra bit.  That is the aligned value shifted left by
+// one, with its lowest bit set when anything was shifted out.  The set bit
+// stands for a remainder strictly inside (0, 2) units of that bit, and the
+// computed sum or difference is then odd, so the exact result lies strictly
+// between the two even integers next to it: the computed bits from bit 1 up
+// are those of the exact result, and the set lowest bit marks its nonzero
+// remainder.  Rounding at bit 4 (guard bit 3, sticky bits 0-2, after at most
+// a one-place normalisation when a bit was shifted out) therefore rounds the
+// exact result, for subtraction as well as addition.
 #pragma once
 #include <cstdint>
 
