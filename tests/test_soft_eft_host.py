@@ -111,3 +111,33 @@ def test_multiply_add_every_policy(soft, prec):
             ok = same_bits(acc[m], want)
             bad = np.argwhere(~ok)
             assert ok.all(), "%s mask %d step %d: %d mismatches, first %s" % (prec, m, step, len(bad), bad[0])
+
+
+def test_boundaries_of_the_shortcuts(soft):
+    """Where the integer form takes a shortcut or hands over to the sequence:
+    TwoSum and FastTwoSum at exponent gaps 52-57 around powers of two (the
+    spacing below a power of two is half the spacing above it, so a gap of 55
+    is the first whose smaller operand never moves the sum), and TwoProd with
+    e_a + e_b from 1070 to 1082 (its error term reaches the subnormal range
+    below 1076, where the sequence runs), each against the oracle."""
+    rng = np.random.default_rng(731)
+    n = 20000
+    big = np.ldexp(1.0, rng.integers(-40, 40, n)) * rng.choice([1.0, -1.0], n)
+    big = np.where(rng.integers(0, 2, n).astype(bool), big, big * (1 + rng.random(n) * 2.0 ** -40))
+    gap = rng.integers(52, 58, n)
+    frac = 1.0 + rng.integers(0, 2 ** 52, n).astype(np.float64) * 2.0 ** -52
+    small = np.ldexp(frac, (np.frexp(big)[1] - 1) - gap) * rng.choice([1.0, -1.0], n)
+    for which in ("two_sum", "quick_two_sum"):
+        s, e = _run(soft, which, big, small)
+        ws, we = oracle.vec_eft(which, big, small)
+        assert same_bits(s, ws).all() and same_bits(e, we).all(), which
+    # products near 2^(e_a + e_b - 2046) with e_a + e_b from 1070 to 1082: their
+    # 53-bit-lower error terms fall from the normal range into the subnormal one
+    t = rng.integers(-40, 40, n)                          # keeps y normal
+    x = np.ldexp(1.0 + rng.random(n), t) * rng.choice([1.0, -1.0], n)
+    y = np.ldexp(1.0 + rng.random(n), rng.integers(1070, 1083, n) - 2046 - t)
+    s, e = _run(soft, "two_prod", x, y)
+    ws, we = oracle.vec_eft("two_prod", x, y)
+    assert same_bits(s, ws).all() and same_bits(e, we).all()
+    # the products do straddle the hand-over: some errors are subnormal or zero
+    assert (np.abs(we) < 2.0 ** -1022).any() and (np.abs(we) >= 2.0 ** -1022).any()
